@@ -1,0 +1,273 @@
+"""ctypes shim of the FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  The oracle defines what the CUDA library must
+compute; it shares no code with it.  Only the tests, the package's smoke
+check and the CPU-baseline leg of the benchmark may import this module.
+
+Layouts: frames [H][W]; per-element arrays [H-1][W-1][2] (two triangles per
+pixel square, t=0 below the (x,y)->(x+1,y+1) diagonal); vectors [3][H][W]
+(u1, u2, m).  Everything is float64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compiles oracle.c into liboracle.so next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=gnu99", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        L = ctypes.CDLL(_LIB)
+        i32, i64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        L.orc_coefficients.argtypes = [i32, i32, _f64p, _f64p, _f64p, _f64p]
+        L.orc_csr_nnz.argtypes = [i32, i32]
+        L.orc_csr_nnz.restype = i64
+        L.orc_csr_pattern.argtypes = [i32, i32, _i64p, _i64p]
+        L.orc_assemble.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _i64p, _i64p, _f64p, _f64p]
+        L.orc_csr_matvec.argtypes = [i64, _i64p, _i64p, _f64p, _f64p, _f64p]
+        L.orc_csr_matvec.restype = None
+        L.orc_apply_elementwise.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p, ctypes.c_void_p]
+        L.orc_band_cholesky_solve.argtypes = [i32, i32, _i64p, _i64p, _f64p, _f64p, _f64p]
+        L.orc_pcg.argtypes = [i32, i32, _i64p, _i64p, _f64p, _f64p, _f64p, f64, i32, ctypes.POINTER(f64)]
+        L.orc_schwarz.argtypes = [i32, i32, _i64p, _i64p, _f64p, _f64p, i32, i32, i32, i32, _f64p, ctypes.c_void_p]
+        L.orc_indicator.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p]
+        L.orc_alpha_update.argtypes = [i64, _f64p, _f64p, f64, f64, f64]
+        L.orc_adjoint_grad.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_num_threads.restype = i32
+        _lib = L
+        return L
+
+
+def _c(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+def coefficients(f1, f2):
+    """(g [H-1][W-1][2][3], ft [H-1][W-1][2]) of every element."""
+    L = _load()
+    f1, f2 = _c(f1), _c(f2)
+    H, W = f1.shape
+    g = np.zeros((H - 1, W - 1, 2, 3))
+    ft = np.zeros((H - 1, W - 1, 2))
+    if L.orc_coefficients(W, H, f1, f2, g, ft):
+        raise ValueError("grid must be at least 2x2")
+    return g, ft
+
+
+class System:
+    """The assembled FP64 system A U = b of one frame pair (CSR, [3][H][W]
+    unknown ordering)."""
+
+    def __init__(self, W, H, g, ft, alpha, lam):
+        L = _load()
+        self.W, self.H, self.lam = int(W), int(H), float(lam)
+        self.g, self.ft, self.alpha = _c(g), _c(ft), _c(alpha)
+        n = 3 * W * H
+        nnz = int(L.orc_csr_nnz(W, H))
+        self.rowptr = np.zeros(n + 1, dtype=np.int64)
+        self.col = np.zeros(nnz, dtype=np.int64)
+        self.val = np.zeros(nnz)
+        self.b = np.zeros(n)
+        L.orc_csr_pattern(W, H, self.rowptr, self.col)
+        rc = L.orc_assemble(W, H, self.g, self.ft, self.alpha, self.lam, self.rowptr, self.col, self.val, self.b)
+        if rc:
+            raise RuntimeError(f"oracle assembly failed ({rc})")
+
+    @classmethod
+    def from_frames(cls, f1, f2, alpha, lam):
+        f1 = _c(f1)
+        H, W = f1.shape
+        alpha = np.broadcast_to(np.asarray(alpha, dtype=np.float64), (H - 1, W - 1, 2))
+        g, ft = coefficients(f1, f2)
+        return cls(W, H, g, ft, alpha, lam)
+
+    @property
+    def n(self) -> int:
+        return 3 * self.W * self.H
+
+    def shape3(self, v):
+        return np.asarray(v).reshape(3, self.H, self.W)
+
+    def dense(self) -> np.ndarray:
+        A = np.zeros((self.n, self.n))
+        for r in range(self.n):
+            s, e = self.rowptr[r], self.rowptr[r + 1]
+            A[r, self.col[s:e]] = self.val[s:e]
+        return A
+
+    def matvec(self, x):
+        L = _load()
+        x = _c(x).ravel()
+        y = np.zeros(self.n)
+        L.orc_csr_matvec(self.n, self.rowptr, self.col, self.val, x, y)
+        return y.reshape(3, self.H, self.W)
+
+    def residual(self, U):
+        return self.b.reshape(3, self.H, self.W) - self.matvec(U)
+
+    def rel_residual(self, U) -> float:
+        return float(np.linalg.norm(self.residual(U)) / np.linalg.norm(self.b))
+
+    def solve_direct(self):
+        """Banded Cholesky (small grids: cost ~ 27 W H min(W,H)^2)."""
+        L = _load()
+        x = np.zeros(self.n)
+        rc = L.orc_band_cholesky_solve(self.W, self.H, self.rowptr, self.col, self.val, self.b, x)
+        if rc == 3:
+            raise np.linalg.LinAlgError("matrix not positive definite")
+        if rc:
+            raise RuntimeError(f"banded Cholesky failed ({rc})")
+        return x.reshape(3, self.H, self.W)
+
+    def solve_pcg(self, tol=1e-12, maxit=100000, x0=None, rhs=None):
+        """Block-Jacobi PCG; returns (U, iterations, final relative residual)."""
+        L = _load()
+        x = np.zeros(self.n) if x0 is None else _c(x0).ravel().copy()
+        b = self.b if rhs is None else _c(rhs).ravel()
+        rr = ctypes.c_double(0.0)
+        it = L.orc_pcg(self.W, self.H, self.rowptr, self.col, self.val, b, x, tol, maxit, ctypes.byref(rr))
+        if it < 0:
+            raise RuntimeError("oracle PCG breakdown")
+        return x.reshape(3, self.H, self.W), int(it), float(rr.value)
+
+    def solve_with(self, rhs, direct=True, tol=1e-13):
+        L = _load()
+        rhs = _c(rhs).ravel()
+        x = np.zeros(self.n)
+        if direct:
+            rc = L.orc_band_cholesky_solve(self.W, self.H, self.rowptr, self.col, self.val, rhs, x)
+            if rc:
+                raise RuntimeError(f"banded Cholesky failed ({rc})")
+            return x.reshape(3, self.H, self.W)
+        U, _, _ = self.solve_pcg(tol=tol, rhs=rhs)
+        return U
+
+    def schwarz(self, px, py, overlap, iters, U0=None):
+        """The paper's Schwarz iteration (Eq. schwarz) with exact subdomain
+        solves; returns (U, history of ||U^k - U^{k-1}||)."""
+        L = _load()
+        U = np.zeros(self.n) if U0 is None else _c(U0).ravel().copy()
+        hist = np.zeros(iters)
+        rc = L.orc_schwarz(self.W, self.H, self.rowptr, self.col, self.val, self.b, px, py, overlap,
+                           iters, U, hist.ctypes.data_as(ctypes.c_void_p))
+        if rc:
+            raise RuntimeError(f"oracle Schwarz failed ({rc})")
+        return U.reshape(3, self.H, self.W), hist
+
+    def indicator(self, U):
+        L = _load()
+        eta = np.zeros((self.H - 1, self.W - 1, 2))
+        L.orc_indicator(self.W, self.H, self.g, self.ft, self.alpha, self.lam, _c(U).ravel(), eta)
+        return eta
+
+
+def apply_elementwise(W, H, g, ft, alpha, lam, U, with_rhs=False):
+    """A U (and b) without storing A, for grids too large for the CSR."""
+    L = _load()
+    y = np.zeros(3 * W * H)
+    b = np.zeros(3 * W * H) if with_rhs else None
+    alpha = _c(np.broadcast_to(np.asarray(alpha, dtype=np.float64), (H - 1, W - 1, 2)))
+    L.orc_apply_elementwise(W, H, _c(g), _c(ft), alpha, float(lam), _c(U).ravel(), y, _ptr(b))
+    y = y.reshape(3, H, W)
+    return (y, b.reshape(3, H, W)) if with_rhs else y
+
+
+def rel_residual_frames(f1, f2, alpha, lam, U) -> float:
+    """||b - A U||_2 / ||b||_2 of a frame pair, formed element by element."""
+    f1 = _c(f1)
+    H, W = f1.shape
+    g, ft = coefficients(f1, f2)
+    AU, b = apply_elementwise(W, H, g, ft, alpha, lam, U, with_rhs=True)
+    return float(np.linalg.norm(b - AU) / np.linalg.norm(b))
+
+
+def indicator(W, H, g, ft, alpha, lam, U):
+    L = _load()
+    eta = np.zeros((H - 1, W - 1, 2))
+    alpha = _c(np.broadcast_to(np.asarray(alpha, dtype=np.float64), (H - 1, W - 1, 2)))
+    L.orc_indicator(W, H, _c(g), _c(ft), alpha, float(lam), _c(U).ravel(), eta)
+    return eta
+
+
+def alpha_update(eta, alpha, kappa, eta_thr, alpha_th):
+    L = _load()
+    a = _c(alpha).copy()
+    L.orc_alpha_update(a.size, _c(eta), a, kappa, eta_thr, alpha_th)
+    return a
+
+
+def adjoint_grad(f1, f2, alpha, lam, U, Lam, want_f1=True):
+    """(dL/dalpha, dL/df2, dL/df1) given U and the adjoint state Lam."""
+    L = _load()
+    f1, f2 = _c(f1), _c(f2)
+    H, W = f1.shape
+    alpha = _c(np.broadcast_to(np.asarray(alpha, dtype=np.float64), (H - 1, W - 1, 2)))
+    da = np.zeros((H - 1, W - 1, 2))
+    d2 = np.zeros((H, W))
+    d1 = np.zeros((H, W)) if want_f1 else None
+    L.orc_adjoint_grad(W, H, f1, f2, alpha, float(lam), _c(U).ravel(), _c(Lam).ravel(),
+                       _ptr(da), _ptr(d2), _ptr(d1))
+    return da, d2, d1
+
+
+def mean_epe(U, flow_gt):
+    """Mean endpoint error (Section 4) of the flow part of U."""
+    d = np.asarray(U[:2], dtype=np.float64) - np.asarray(flow_gt, dtype=np.float64)
+    return float(np.mean(np.sqrt(d[0] ** 2 + d[1] ** 2)))
+
+
+def mean_epe_grad(U, flow_gt):
+    """dL/dU of the mean endpoint error; 0 where the endpoint error is 0."""
+    U = np.asarray(U, dtype=np.float64)
+    d = U[:2] - np.asarray(flow_gt, dtype=np.float64)
+    e = np.sqrt(d[0] ** 2 + d[1] ** 2)
+    n = e.size
+    out = np.zeros_like(U)
+    nz = e > 0
+    out[0][nz] = d[0][nz] / (n * e[nz])
+    out[1][nz] = d[1][nz] / (n * e[nz])
+    return out
+
+
+def aae_deg(U, flow_gt):
+    """Average angular error in degrees (Section 4)."""
+    u, v = np.asarray(U[0], dtype=np.float64), np.asarray(U[1], dtype=np.float64)
+    ue, ve = np.asarray(flow_gt[0], dtype=np.float64), np.asarray(flow_gt[1], dtype=np.float64)
+    c = (u * ue + v * ve + 1.0) / np.sqrt((u * u + v * v + 1.0) * (ue * ue + ve * ve + 1.0))
+    return float(np.degrees(np.mean(np.arccos(np.clip(c, -1.0, 1.0)))))

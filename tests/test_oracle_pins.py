@@ -1,0 +1,416 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here re-calls an oracle routine to check itself: every expected
+value comes from an independent route (generic barycentric geometry and a
+different quadrature rule, closed forms, LAPACK, finite differences, the
+paper's worked example)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1508_02977_gb300 import synth, partition
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+# ------------------------------------------------------ independent route --
+
+def triangles(W, H):
+    """The mesh of Fig. sch-mesh: each pixel square cut by its
+    (x,y)->(x+1,y+1) diagonal; yields (x, y, t, vertices)."""
+    for y in range(H - 1):
+        for x in range(W - 1):
+            yield x, y, 0, [(x, y), (x + 1, y), (x + 1, y + 1)]
+            yield x, y, 1, [(x, y), (x, y + 1), (x + 1, y + 1)]
+
+
+def bary(verts):
+    """Gradients of the barycentric coordinates (rows) and the area, from the
+    inverse of the vertex matrix (no hand-written gradient table)."""
+    M = np.array([[v[0] for v in verts], [v[1] for v in verts], [1.0, 1.0, 1.0]])
+    Minv = np.linalg.inv(M)
+    return Minv[:, :2], abs(np.linalg.det(M)) / 2.0
+
+
+# 3-point interior rule, exact for quadratics (Strang & Fix), barycentric
+QPTS = [(2 / 3, 1 / 6, 1 / 6), (1 / 6, 2 / 3, 1 / 6), (1 / 6, 1 / 6, 2 / 3)]
+
+
+def element_data(f1, f2, verts):
+    """g = (grad f2_h, -f1_h(centroid)), ft = (f2_h - f1_h)(centroid)."""
+    G, _ = bary(verts)
+    v2 = np.array([f2[y, x] for x, y in verts])
+    v1 = np.array([f1[y, x] for x, y in verts])
+    grad2 = G.T @ v2
+    cen = np.array([1 / 3, 1 / 3, 1 / 3])
+    return np.array([grad2[0], grad2[1], -(cen @ v1)]), cen @ (v2 - v1)
+
+
+def bilinear(f1, f2, alpha, lam, U, V):
+    """int (g.U_h)(g.V_h) + sum_c Lambda_c grad U_c . grad V_c  and
+    the load  -int ft g.V_h, by the 3-point rule."""
+    H, W = f1.shape
+    a_uv = 0.0
+    l_v = 0.0
+    for x, y, t, verts in triangles(W, H):
+        g, ft = element_data(f1, f2, verts)
+        G, area = bary(verts)
+        Lam = np.array([alpha[y, x, t], alpha[y, x, t], lam])
+        uv = np.array([[U[c, yy, xx] for c in range(3)] for xx, yy in verts])  # [vertex][c]
+        vv = np.array([[V[c, yy, xx] for c in range(3)] for xx, yy in verts])
+        for q in QPTS:
+            q = np.array(q)
+            a_uv += area / 3.0 * (g @ (q @ uv)) * (g @ (q @ vv))
+            l_v += area / 3.0 * (-ft) * (g @ (q @ vv))
+        for c in range(3):
+            a_uv += area * Lam[c] * (G.T @ uv[:, c]) @ (G.T @ vv[:, c])
+    return a_uv, l_v
+
+
+# ------------------------------------------------------------ assembly ----
+
+def test_coefficients_match_p1_interpolant(oracle):
+    f1, f2 = synth.random_frames(6, 5, 11)
+    g, ft = oracle.coefficients(f1, f2)
+    for x, y, t, verts in triangles(6, 5):
+        ge, fte = element_data(f1, f2, verts)
+        np.testing.assert_allclose(g[y, x, t], ge, rtol=0, atol=1e-14)
+        assert abs(ft[y, x, t] - fte) < 1e-14
+
+
+@pytest.mark.parametrize("W,H", [(4, 3), (5, 5), (3, 6)])
+def test_operator_and_load_equal_weak_form(oracle, W, H):
+    """U^T A V and b^T V equal the weak form (Eq. weakform / discret-form)
+    integrated by an independent rule, for random U, V, alpha."""
+    rng = np.random.default_rng(W * 100 + H)
+    f1, f2 = synth.random_frames(W, H, W + H)
+    alpha = synth.random_alpha(W, H, 7)
+    lam = 0.7
+    S = oracle.System.from_frames(f1, f2, alpha, lam)
+    for _ in range(3):
+        U = rng.standard_normal((3, H, W))
+        V = rng.standard_normal((3, H, W))
+        a_uv, l_v = bilinear(f1, f2, alpha, lam, U, V)
+        assert abs(np.sum(V * S.matvec(U)) - a_uv) < 1e-12 * max(1.0, abs(a_uv))
+        assert abs(S.b @ V.ravel() - l_v) < 1e-13 * max(1.0, abs(l_v))
+
+
+def test_assembled_matrix_symmetric_spd(oracle):
+    for (W, H, seed) in [(5, 4, 1), (7, 5, 2)]:
+        f1, f2 = synth.random_frames(W, H, seed)
+        S = oracle.System.from_frames(f1, f2, synth.random_alpha(W, H, seed), 1.0)
+        A = S.dense()
+        assert np.array_equal(A, A.T)
+        assert np.linalg.eigvalsh(A).min() > 0.0
+
+
+def test_stiffness_annihilates_constants(oracle):
+    """Without data (f1 = f2 = 0) A is the stiffness only: constants are in
+    its kernel (row sums zero) and b = 0."""
+    W, H = 6, 5
+    z = np.zeros((H, W))
+    S = oracle.System.from_frames(z, z, synth.random_alpha(W, H, 3), 2.0)
+    for c in range(3):
+        U = np.zeros((3, H, W))
+        U[c] = 1.0
+        assert np.abs(S.matvec(U)).max() < 1e-15
+    assert np.abs(S.b).max() == 0.0
+
+
+def test_stencil_is_seven_point(oracle):
+    """Couplings only to (+-1,0), (0,+-1) and +-(1,1) (Fig. sch-mesh)."""
+    W, H = 5, 5
+    f1, f2 = synth.random_frames(W, H, 4)
+    S = oracle.System.from_frames(f1, f2, 0.05, 1.0)
+    A = S.dense().reshape(3, H, W, 3, H, W)
+    allowed = {(0, 0), (1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1)}
+    for y in range(H):
+        for x in range(W):
+            blk = A[:, y, x]
+            for yy in range(H):
+                for xx in range(W):
+                    nz = np.abs(blk[:, :, yy, xx]).max() > 0
+                    if (xx - x, yy - y) not in allowed:
+                        assert not nz
+                    elif (xx - x, yy - y) in {(1, 1), (-1, -1)}:
+                        assert nz  # coupled through the data term of the two triangles
+
+
+# --------------------------------------------------------------- solves ----
+
+@pytest.mark.parametrize("W,H", [(4, 3), (3, 5), (6, 6)])
+def test_banded_cholesky_equals_lapack(oracle, W, H):
+    f1, f2 = synth.random_frames(W, H, 20 + W)
+    S = oracle.System.from_frames(f1, f2, synth.random_alpha(W, H, 5), 1.0)
+    x = np.linalg.solve(S.dense(), S.b)
+    U = S.solve_direct()
+    assert np.abs(U.ravel() - x).max() <= 1e-13 * np.abs(x).max()
+
+
+def test_constant_solution_invariant(oracle):
+    """If ft_K = -g_K.c for a constant c then U = c exactly, for any alpha,
+    lambda, solver and Schwarz split (the data residual g.U + ft vanishes and
+    constants carry no stiffness)."""
+    W, H = 12, 9
+    rng = np.random.default_rng(5)
+    g = rng.uniform(-1, 1, (H - 1, W - 1, 2, 3))
+    c = np.array([0.7, -1.3, 0.25])
+    ft = -(g @ c)
+    S = oracle.System(W, H, g, ft, synth.random_alpha(W, H, 9), 0.3)
+    want = np.broadcast_to(c[:, None, None], (3, H, W))
+    assert np.abs(S.solve_direct() - want).max() < 1e-12
+    U, it, rr = S.solve_pcg(tol=1e-14)
+    assert np.abs(U - want).max() < 1e-11
+    U, _ = S.schwarz(2, 2, 2, 80)
+    assert np.abs(U - want).max() < 1e-10
+
+
+@pytest.mark.parametrize("M", [1.1, 0.85])
+def test_pure_gain_recovered_exactly(oracle, M):
+    """f2 = M f1 without motion: U = (0, 0, M - 1) (Eq. deltam, Eq. OF2)."""
+    W, H = 10, 8
+    f1, _ = synth.random_frames(W, H, 31)
+    S = oracle.System.from_frames(f1, M * f1, synth.random_alpha(W, H, 2), 1.0)
+    U = S.solve_direct()
+    assert np.abs(U[0]).max() < 1e-12 and np.abs(U[1]).max() < 1e-12
+    assert np.abs(U[2] - (M - 1.0)).max() < 1e-12
+
+
+def test_pcg_matches_direct_on_blobs(oracle):
+    p = synth.blobs()
+    S = oracle.System.from_frames(p.f1, p.f2, p.alpha0, p.lam)
+    Ud = S.solve_direct()
+    Up, it, rr = S.solve_pcg(tol=1e-13)
+    assert rr <= 1e-13
+    assert np.linalg.norm(Up - Ud) <= 1e-10 * np.linalg.norm(Ud)
+
+
+def test_schwarz_fixed_point_is_global_solution(oracle):
+    """Eq. schwarz: the subdomain iterates converge to the global solution
+    (2x2 parts, 4-node overlap, 64x48 blobs)."""
+    p = synth.blobs()
+    S = oracle.System.from_frames(p.f1, p.f2, p.alpha0, p.lam)
+    Ud = S.solve_direct()
+    U, hist = S.schwarz(2, 2, 4, 70)
+    assert np.linalg.norm(U - Ud) <= 1e-12 * np.linalg.norm(Ud)
+    assert hist[-1] < 1e-12 * hist[0]
+
+
+def test_schwarz_converges_faster_with_more_overlap(oracle):
+    """Section 4, Fig. schwarz-convergence: the rate increases with the
+    overlap."""
+    p = synth.blobs()
+    S = oracle.System.from_frames(p.f1, p.f2, p.alpha0, p.lam)
+    Ud = S.solve_direct()
+    counts = []
+    for ov in (1, 2, 4, 8):
+        U = np.zeros_like(Ud)
+        for k in range(1, 200):
+            U, _ = S.schwarz(2, 2, ov, 1, U0=U)
+            if np.linalg.norm(U - Ud) <= 1e-8 * np.linalg.norm(Ud):
+                break
+        counts.append(k)
+    assert all(a >= b for a, b in zip(counts, counts[1:])), counts
+    assert counts[0] > counts[-1]
+
+
+def test_adjoint_symmetry_identity(oracle):
+    W, H = 7, 6
+    f1, f2 = synth.random_frames(W, H, 8)
+    S = oracle.System.from_frames(f1, f2, synth.random_alpha(W, H, 8), 1.0)
+    rng = np.random.default_rng(0)
+    a, b = rng.standard_normal((2, 3, H, W))
+    lhs = np.sum(S.solve_with(a) * b)
+    rhs = np.sum(a * S.solve_with(b))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+# ------------------------------------------------- indicator / alpha ----
+
+def indicator_independent(f1, f2, alpha, lam, U):
+    """Eq. errind by an independent route: generic geometry, edge neighbours
+    found by shared vertex pairs, normals from the geometry, interior L2 by
+    the 3-point interior rule."""
+    H, W = f1.shape
+    tris = list(triangles(W, H))
+    edges = {}
+    for k, (_, _, _, verts) in enumerate(tris):
+        for i in range(3):
+            key = tuple(sorted([verts[i], verts[(i + 1) % 3]]))
+            edges.setdefault(key, []).append(k)
+    info = []
+    for x, y, t, verts in tris:
+        g, ft = element_data(f1, f2, verts)
+        G, area = bary(verts)
+        Lam = np.array([alpha[y, x, t], alpha[y, x, t], lam])
+        uv = np.array([[U[c, yy, xx] for c in range(3)] for xx, yy in verts])
+        grads = np.array([G.T @ uv[:, c] for c in range(3)])  # [c][2]
+        info.append((g, ft, area, Lam, uv, grads, verts))
+    eta = np.zeros((H - 1, W - 1, 2))
+    for k, (x, y, t, verts) in enumerate(tris):
+        g, ft, area, Lam, uv, grads, _ = info[k]
+        integ = 0.0
+        for q in QPTS:
+            s = g @ (np.array(q) @ uv) + ft
+            R = -g * s
+            integ += area / 3.0 * np.sum(R * R / Lam)
+        hK = max(np.hypot(verts[i][0] - verts[j][0], verts[i][1] - verts[j][1])
+                 for i in range(3) for j in range(3))
+        val = hK * np.sqrt(integ)
+        cen = np.mean(np.array(verts, float), axis=0)
+        for i in range(3):
+            pa, pb = np.array(verts[i], float), np.array(verts[(i + 1) % 3], float)
+            d = pb - pa
+            he = np.hypot(*d)
+            n = np.array([d[1], -d[0]]) / he
+            if n @ ((pa + pb) / 2 - cen) < 0:
+                n = -n
+            key = tuple(sorted([verts[i], verts[(i + 1) % 3]]))
+            nb = [j for j in edges[key] if j != k]
+            fin = Lam * (grads @ n)
+            if nb:
+                Lo = info[nb[0]][3]
+                fout = Lo * (info[nb[0]][5] @ n)
+                Le = np.maximum(Lam, Lo)
+            else:
+                fout = np.zeros(3)
+                Le = Lam
+            J = fout - fin
+            # (1/2) h_e^{1/2} ||Lambda_e^{-1/2} J||_{L2(e)}, J constant on e
+            val += 0.5 * np.sqrt(he) * np.sqrt(he * np.sum(J * J / Le))
+        eta[y, x, t] = val
+    return eta
+
+
+def test_indicator_matches_independent_route(oracle):
+    W, H = 6, 5
+    f1, f2 = synth.random_frames(W, H, 41)
+    alpha = synth.random_alpha(W, H, 42)
+    U = np.random.default_rng(43).standard_normal((3, H, W))
+    S = oracle.System.from_frames(f1, f2, alpha, 0.6)
+    np.testing.assert_allclose(S.indicator(U), indicator_independent(f1, f2, alpha, 0.6, U), rtol=1e-12, atol=1e-14)
+
+
+def test_indicator_closed_forms(oracle):
+    W, H = 6, 5
+    f1, f2 = synth.random_frames(W, H, 44)
+    alpha = synth.random_alpha(W, H, 45)
+    lam = 1.7
+    S = oracle.System.from_frames(f1, f2, alpha, lam)
+    # U = 0: only the interior term, h_K |K|^{1/2} |ft| ||Lambda^{-1/2} g|| = |ft| ||Lambda^{-1/2} g||
+    eta = S.indicator(np.zeros((3, H, W)))
+    lamv = np.stack([alpha, alpha, np.full_like(alpha, lam)], -1)
+    want = np.abs(S.ft) * np.sqrt(np.sum(S.g ** 2 / lamv, -1))
+    np.testing.assert_allclose(eta, want, rtol=1e-13)
+    # no data, u1 = x, constant alpha: only the left/right boundary edges jump,
+    # by alpha, giving (1/2) sqrt(alpha) on the elements that carry them
+    z = np.zeros((H, W))
+    a0 = 0.09
+    S0 = oracle.System.from_frames(z, z, a0, lam)
+    U = np.zeros((3, H, W))
+    U[0] = np.arange(W)[None, :]
+    eta = S0.indicator(U)
+    want = np.zeros((H - 1, W - 1, 2))
+    want[:, W - 2, 0] = 0.5 * np.sqrt(a0)
+    want[:, 0, 1] = 0.5 * np.sqrt(a0)
+    np.testing.assert_allclose(eta, want, atol=1e-15)
+
+
+def test_indicator_zero_on_constant_solution(oracle):
+    W, H = 8, 7
+    rng = np.random.default_rng(6)
+    g = rng.uniform(-1, 1, (H - 1, W - 1, 2, 3))
+    c = np.array([0.3, 0.2, -0.1])
+    S = oracle.System(W, H, g, -(g @ c), synth.random_alpha(W, H, 1), 1.0)
+    U = S.solve_direct()
+    assert np.abs(S.indicator(U)).max() < 1e-13
+    eta = S.indicator(np.broadcast_to(c[:, None, None], (3, H, W)).copy())
+    assert np.abs(eta).max() < 1e-15
+
+
+def test_alpha_update_closed_form(oracle):
+    eta = np.array([0.0, 0.5, 1.0, 2.0])
+    alpha = np.array([1.0, 1.0, 1.0, 0.3])
+    # max eta = 2 -> rel = [-0.25, 0, 0.25, 0.75]
+    out = oracle.alpha_update(eta, alpha, 4.0, 0.25, 0.1)
+    np.testing.assert_allclose(out, [1.0, 1.0, 0.5, 0.1], rtol=1e-15)
+    np.testing.assert_array_equal(oracle.alpha_update(np.zeros(4), alpha, 4.0, 0.25, 0.1), alpha)
+
+
+# ------------------------------------------------------------- adjoint ----
+
+def test_adjoint_gradient_matches_central_differences(oracle):
+    W, H = 7, 6
+    f1, f2 = synth.random_frames(W, H, 51)
+    alpha = synth.random_alpha(W, H, 52)
+    lam = 1.0
+    gt = np.random.default_rng(53).uniform(-1, 1, (2, H, W))
+
+    def loss(f1_, f2_, a_):
+        S_ = oracle.System.from_frames(f1_, f2_, a_, lam)
+        return oracle.mean_epe(S_.solve_direct(), gt)
+
+    S = oracle.System.from_frames(f1, f2, alpha, lam)
+    U = S.solve_direct()
+    Lam = S.solve_with(oracle.mean_epe_grad(U, gt))
+    da, d2, d1 = oracle.adjoint_grad(f1, f2, alpha, lam, U, Lam)
+    h = 1e-4
+    rng = np.random.default_rng(54)
+    for _ in range(6):
+        y, x, t = rng.integers(0, H - 1), rng.integers(0, W - 1), rng.integers(0, 2)
+        ap, am = alpha.copy(), alpha.copy()
+        ap[y, x, t] += h
+        am[y, x, t] -= h
+        fd = (loss(f1, f2, ap) - loss(f1, f2, am)) / (2 * h)
+        assert abs(fd - da[y, x, t]) <= 1e-5 * np.abs(da).max()
+    for which, grad in (("f2", d2), ("f1", d1)):
+        for _ in range(6):
+            y, x = rng.integers(0, H), rng.integers(0, W)
+            fp = (f1 if which == "f1" else f2).copy()
+            fm = fp.copy()
+            fp[y, x] += h
+            fm[y, x] -= h
+            if which == "f1":
+                fd = (loss(fp, f2, alpha) - loss(fm, f2, alpha)) / (2 * h)
+            else:
+                fd = (loss(f1, fp, alpha) - loss(f1, fm, alpha)) / (2 * h)
+            assert abs(fd - grad[y, x]) <= 1e-5 * np.abs(grad).max()
+
+
+# --------------------------------------------------------- elementwise ----
+
+def test_elementwise_apply_equals_csr(oracle):
+    W, H = 9, 7
+    f1, f2 = synth.random_frames(W, H, 61)
+    alpha = synth.random_alpha(W, H, 62)
+    S = oracle.System.from_frames(f1, f2, alpha, 1.3)
+    U = np.random.default_rng(63).standard_normal((3, H, W))
+    AU, b = oracle.apply_elementwise(W, H, S.g, S.ft, alpha, 1.3, U, with_rhs=True)
+    np.testing.assert_allclose(AU, S.matvec(U), rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(b.ravel(), S.b, rtol=1e-13, atol=1e-16)
+
+
+# ------------------------------------------------------------ partition ----
+
+def test_partition_ratio_worked_example():
+    """Fig. ratio: 48x48 grid, twelve parts."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "partition_ratio_48x48_12.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    for px, py, r in rows:
+        got = partition.part_ratio(48, 48, int(px), int(py))
+        assert abs(got - float(r)) < 1e-3, (px, py, got, r)
+    assert partition.best_split(48, 48, 12) in {(4, 3), (3, 4)}
+
+
+def test_metrics_closed_forms(oracle):
+    gt = np.zeros((2, 3, 4))
+    U = np.zeros((3, 3, 4))
+    U[0] = 3.0
+    U[1] = 4.0
+    assert abs(oracle.mean_epe(U, gt) - 5.0) < 1e-15
+    assert oracle.aae_deg(np.concatenate([gt, np.zeros((1, 3, 4))]), gt) == 0.0
+    # u_h = (1, 0), u_e = (0, 0): cos = 1/sqrt(2) -> 45 degrees
+    U2 = np.zeros((3, 3, 4))
+    U2[0] = 1.0
+    assert abs(oracle.aae_deg(U2, gt) - 45.0) < 1e-12
