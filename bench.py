@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Throughput of the adaptive optical-flow solve on GB300.
+
+One step = one pass of the whole path on one synthetic frame pair per GPU:
+reset alpha to alpha_0, solve A U = b to relative residual 1e-6 (FP32 PCG +
+Schwarz preconditioner, FP64 residual and refinement), error indicator and
+alpha update.  Workload: 3840x2160 layered scene (4 textured layers with
+rigid motions up to 6 px, occlusion edges, smooth gain 0.8-1.25), the
+stand-in for the paper's HD sequences.  Inputs (frames, alpha and the Krylov
+vectors, ~1.5 GB) are larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle (block-
+Jacobi PCG to 1e-6 + indicator + alpha update) on a bounded sample of the
+same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s solved to rel. residual 1e-6 (mixed vs FP64 GPU); HBM GB/s vs 8 TB/s"
+UNIT = "Mpixel/s"
+WORKLOAD_W, WORKLOAD_H = 3840, 2160
+# launch configuration of the timed solve (tile, overlap, sweeps, precision)
+WORKLOAD_OPTS = dict(tile=(32, 32), overlap=0, sweeps=2, precision=1)
+FP64_OPTS = dict(tile=(32, 16), overlap=0, sweeps=2, precision=0)
+RTOL = 1e-6
+# algorithmic bytes per pixel of one launch of each solve kernel (FP32 inner
+# vectors; each word read or written once):
+#   pcg_apply: read z, p_old, d (3 x 12) + f1, f2, alpha (16); write p, q, d (3 x 12)
+#   schwarz:   read r, q (2 x 12) + f1, f2, alpha (16);         write r, z (2 x 12)
+#   residual:  read x (24), d, p (2 x 12), f1, f2, alpha (16);  write x (24), r (12)
+ALG_BYTES_PER_PX = {"pcg_apply": 88, "schwarz": 64, "residual": 100}
+KERNEL_NAMES = {"pcg_apply": "k_apply<float,float,float,MODE_PCG>", "schwarz": "k_schwarz<float>",
+                "residual": "k_apply<double,float,float,MODE_RES>"}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    cdir = os.path.join(ROOT, "paper_1508_02977_gb300", "csrc")
+    for f in sorted(os.listdir(cdir)):
+        h.update(open(os.path.join(cdir, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(kind: str):
+    """DRAM bytes per pixel of a kernel from the committed ncu summary, if it
+    was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    k = d.get("kernels", {}).get(kind)
+    return None if k is None else float(k["dram_bytes_per_px"])
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", gpu_id], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_pair(rank: int, W=WORKLOAD_W, H=WORKLOAD_H):
+    from paper_1508_02977_gb300 import synth
+    return synth.layers(W, H, seed=synth.BASE_SEED + 3 + 1000 * rank)
+
+
+def oracle_step(p):
+    """One step of the CPU oracle: solve to 1e-6 (block-Jacobi PCG), indicator,
+    alpha update.  Returns (seconds, iterations, threads)."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_1508_02977_gb300 import synth
+    f1 = p.f1.astype(np.float64)
+    f2 = p.f2.astype(np.float64)
+    t0 = time.perf_counter()
+    sysm = O.System.from_frames(f1, f2, p.alpha0, p.lam)
+    U, it, rr = sysm.solve_pcg(tol=RTOL)
+    eta = sysm.indicator(U)
+    O.alpha_update(eta, sysm.alpha, synth.KAPPA, synth.ETA_THR, synth.ALPHA_TH_FRAC * p.alpha0)
+    return time.perf_counter() - t0, it, O.num_threads()
+
+
+def cpu_sample_pair(W=960, H=540):
+    # the same generator at a bounded size (about 10-30 s of oracle work)
+    return workload_pair(0, W, H)
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    O.build()
+    p = cpu_sample_pair(args.cpu_sample_w, args.cpu_sample_h)
+    for _ in range(args.warmup):
+        oracle_step(p)
+    tot = 0.0
+    its = []
+    cores = 1
+    for _ in range(args.steps):
+        dt, it, cores = oracle_step(p)
+        tot += dt
+        its.append(it)
+    px = p.W * p.H
+    value = px * args.steps / tot / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"layers {p.W}x{p.H} sample of the 3840x2160 layered scene (oracle on host cores)",
+                   "rtol": RTOL, "solver": "FP64 block-Jacobi PCG (CSR, OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{p.W}x{p.H} layered pair, solve to 1e-6 + indicator + alpha update per step, "
+                                   f"{statistics.mean(its):.0f} PCG iterations"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as g
+    g.build()
+    from paper_1508_02977_gb300 import ofsolve as S
+    from paper_1508_02977_gb300 import synth
+
+    p = workload_pair(rank)
+    W, H = p.W, p.H
+    px = W * H
+    kappa, thr, ath = synth.KAPPA, synth.ETA_THR, synth.ALPHA_TH_FRAC * p.alpha0
+    stream = torch.cuda.current_stream(dev)
+    f1 = torch.from_numpy(p.f1).to(dev)
+    f2 = torch.from_numpy(p.f2).to(dev)
+
+    def make(opts):
+        h = S.of_create(local, stream)
+        S.of_setup_grid(h, [(W, H)], **opts)
+        S.of_set_frames(h, 0, f1, f2)
+        return h
+
+    h = make(WORKLOAD_OPTS)
+    U = torch.zeros(3, H, W, dtype=torch.float32, device=dev)
+    infos = []
+
+    def step(hh, Uo, frames=None):
+        if frames is not None:
+            S.of_set_frames(hh, 0, *frames)
+        S.of_set_alpha(hh, 0, None, p.alpha0)
+        st, info = S.of_solve(hh, [Uo], rtol=RTOL)
+        S.of_adapt_alpha(hh, kappa, thr, ath)
+        infos.append(info[0])
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(fn, steps):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    for _ in range(args.warmup):
+        step(h, U)
+    infos.clear()
+    gpu_id = torch.cuda.get_device_properties(dev).uuid
+    gpu_id = f"GPU-{gpu_id}" if not str(gpu_id).startswith("GPU-") else str(gpu_id)
+    clk = ClockSampler(gpu_id)
+    S.of_set_profiling(h, True)
+    ms = timed(lambda: step(h, U), args.steps)
+    prof = S.of_get_profile(h)
+    S.of_set_profiling(h, False)
+    clocks = clk.stop()
+    value = ws * px * args.steps / (ms / 1e3) / 1e6
+    iters = [i["inner_iters"] for i in infos]
+    relres = max(i["rel_residual"] for i in infos)
+
+    # dominant kernel and its roofline (algorithmic bytes / measured launch time)
+    kinds = [k for k in ("pcg_apply", "schwarz", "residual") if prof[k]["launches"]]
+    dom = max(kinds, key=lambda k: prof[k]["ms"])
+    avg_ms = prof[dom]["ms"] / prof[dom]["launches"]
+    alg = ALG_BYTES_PER_PX[dom] * px
+    peak, peak_src = load_peaks()
+    achieved = alg / (avg_ms / 1e3) / 1e9
+    tb = recorded_traffic(dom)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None if tb is None else tb * px, "kernel": KERNEL_NAMES[dom],
+                "alg_bytes_per_launch": alg, "avg_launch_ms": avg_ms, "peak_source": peak_src,
+                "per_kernel": {k: {"launches": prof[k]["launches"], "ms": prof[k]["ms"],
+                                   "GBps": (ALG_BYTES_PER_PX[k] * px / (prof[k]["ms"] / prof[k]["launches"] / 1e3) / 1e9)
+                                   if prof[k]["launches"] else None}
+                               for k in ("pcg_apply", "schwarz", "residual")}}
+    launches = sum(v["launches"] for v in prof.values())
+
+    # end to end through the C ABI with host buffers (pinned)
+    f1h = torch.from_numpy(p.f1).pin_memory()
+    f2h = torch.from_numpy(p.f2).pin_memory()
+    Uh = torch.zeros(3, H, W, dtype=torch.float32).pin_memory()
+    step(h, Uh, (f1h, f2h))
+    infos.clear()
+    ms_e2e = timed(lambda: step(h, Uh, (f1h, f2h)), args.steps)
+    e2e = {"value": ws * px * args.steps / (ms_e2e / 1e3) / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * px * 4, "d2h_bytes_per_step": 3 * px * 4}
+    S.of_destroy(h)
+
+    # the plain FP64 GPU solve at the same residual (the "vs FP64 GPU" half of the metric)
+    fp64 = None
+    if args.fp64_steps > 0:
+        h64 = make(FP64_OPTS)
+        U64 = torch.zeros(3, H, W, dtype=torch.float64, device=dev)
+        step(h64, U64)
+        infos.clear()
+        ms64 = timed(lambda: step(h64, U64), args.fp64_steps)
+        fp64 = {"value": ws * px * args.fp64_steps / (ms64 / 1e3) / 1e6, "unit": UNIT,
+                "ms_per_step": ms64 / args.fp64_steps, "inner_iters": infos[-1]["inner_iters"],
+                "rel_residual": infos[-1]["rel_residual"], "opts": {k: v for k, v in FP64_OPTS.items()}}
+        S.of_destroy(h64)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        ps = cpu_sample_pair(args.cpu_sample_w, args.cpu_sample_h)
+        dt, it, cores = oracle_step(ps)
+        cpu = {"value": ps.W * ps.H / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{ps.W}x{ps.H} layered pair (same generator), one step: FP64 block-Jacobi PCG to 1e-6 "
+                         f"({it} iterations) + indicator + alpha update, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"layers {W}x{H}: 4 textured layers, rigid motions <= 6 px, occlusions, "
+                                   f"gain 0.8-1.25 (one pair per GPU)",
+                       "precision": "FP32 PCG + Schwarz sweeps, FP64 residual/refinement/dots",
+                       "rtol": RTOL, "opts": {k: v for k, v in WORKLOAD_OPTS.items()},
+                       "step": "alpha reset + solve to rtol + indicator + alpha update",
+                       "l2": "inputs larger than L2 (no flush)",
+                       "inner_iters": iters, "rel_residual_max": relres},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "fp64_gpu": fp64,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-w", type=int, default=960)
+    ap.add_argument("--cpu-sample-h", type=int, default=540)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

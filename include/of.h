@@ -1,0 +1,202 @@
+/*
+ * of.h -- C ABI of the GB300 optical-flow solver.
+ *
+ * The library solves, for a batch of frame pairs, the P1 finite-element
+ * system of the Horn-Schunck optical-flow model with an illumination unknown
+ * (Gilliocq-Hirtz & Belhachmi, arXiv 1508.02977):
+ *
+ *   -div(Lambda grad U) + A U = F  in Omega,  dU/dn = 0 on dOmega
+ *                                     (Section 1, Eq. eqpro1illu)
+ *   U = (u1, u2, m),  Lambda = (alpha, alpha, lambda),
+ *   A = g g^T,  F = -ft g,  g = (f_x, f_y, -f)   (Eq. OF2, Eq. BW2, rho = 0)
+ *
+ * discretised by P1 elements on the pixel grid, two triangles per pixel
+ * square (Section 2.2, Eq. discret-form, Fig. sch-mesh), with a per-element
+ * regularisation alpha adapted by the indicator of Section 2.3 (Eq. errind).
+ *
+ * Discretisation conventions shared by every entry point:
+ *  - one node per pixel centre; node (x, y), 0 <= x < W, 0 <= y < H;
+ *  - square (x, y), x < W-1, y < H-1, split along (x,y)->(x+1,y+1):
+ *      t = 0: (x,y) (x+1,y) (x+1,y+1)      t = 1: (x,y) (x,y+1) (x+1,y+1);
+ *  - per element K: g_K = (d/dx, d/dy of the P1 interpolant of frame 2,
+ *    -mean of frame 1 over the 3 vertices), ft_K = mean of (f2 - f1);
+ *  - m is delta m = M - 1 of the illumination law f2(x+u) = M f1(x)
+ *    (Eq. deltam).
+ *
+ * Layouts (all row-major, row pitch in elements, pitch >= row length):
+ *  - frame  [H][pitch]                    (f1, f2, dL/df1, dL/df2)
+ *  - alpha  [H-1][W-1][2] contiguous      (element (x,y,t) at (y*(W-1)+x)*2+t)
+ *  - vector [3][H][W] contiguous planes   (U, dL/dU; u1, u2, m)
+ *
+ * Pointers: unless stated otherwise an array argument may be a device
+ * pointer or a host pointer (pinned host memory gives asynchronous copies);
+ * the library tells them apart through unified addressing.  All work is
+ * ordered on the stream given to of_create; an input must stay valid until
+ * that stream has passed the call, an output is valid once it has (the
+ * entry points that return host-side results synchronise the stream
+ * themselves and say so).  Arrays stay owned by the caller; the library owns
+ * only its own workspace, released by of_destroy.
+ *
+ * Errors: every entry point returns an of_status; no entry point aborts,
+ * traps or prints.  of_last_error gives a message for the last non-OK status
+ * of a handle.  A CUDA error inside a call returns OF_ERR_CUDA.
+ */
+#ifndef OF_H_
+#define OF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct of_ctx *of_handle;
+
+typedef enum {
+    OF_OK = 0,
+    OF_ERR_ARG = 1,            /* invalid argument (null handle, bad size, pair out of range) */
+    OF_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    OF_ERR_OOM = 3,            /* device allocation failed */
+    OF_ERR_STATE = 4,          /* call out of order (e.g. of_solve before of_set_frames) */
+    OF_ERR_NOT_CONVERGED = 5,  /* iteration cap reached; the best iterate is written */
+    OF_ERR_BREAKDOWN = 6,      /* non-finite or non-positive CG scalar (singular/indefinite data) */
+    OF_ERR_TIMEOUT = 7         /* a bounded device wait ran out */
+} of_status;
+
+typedef enum { OF_F32 = 0, OF_F64 = 1 } of_dtype;
+
+typedef enum {
+    OF_PREC_FP64 = 0,   /* every step in FP64 (frames, alpha and vectors stored in FP64) */
+    OF_PREC_MIXED = 1   /* FP32 inner PCG + Schwarz sweeps; FP64 residual, dots, refinement */
+} of_precision;
+
+typedef enum {
+    OF_PC_SCHWARZ = 0,  /* overlapping Schwarz, symmetric variant, as the PCG preconditioner */
+    OF_PC_JACOBI = 1    /* node-block Jacobi (3x3 blocks); no subdomains */
+} of_preconditioner;
+
+/* Grid options.  A field left at 0 takes the default in brackets. */
+typedef struct {
+    int tile_x, tile_y;      /* owned subdomain tile in nodes, multiples of 4 [32 x 32] */
+    int overlap;             /* extension of each subdomain on interior sides, nodes (0: none) */
+    int sweeps;              /* symmetric 3-colour block Gauss-Seidel sweeps per local solve [1] */
+    of_precision precision;  /* [OF_PREC_FP64] */
+    double lambda;           /* regularisation of m (Eq. BW2) [1.0] */
+    of_preconditioner preconditioner;  /* [OF_PC_SCHWARZ] */
+} of_grid_opts;
+
+/* Solve options.  A field left at 0 takes the default in brackets. */
+typedef struct {
+    double rtol;       /* stop when ||b - A U||_2 <= rtol ||b||_2 (FP64 residual) [1e-6] */
+    int max_outer;     /* refinement passes (mixed) [20] */
+    int max_inner;     /* PCG iterations per pass (mixed) or in total (FP64) [2000] */
+    int warm_start;    /* 1: start from the U passed in; 0: start from U = 0 */
+    double inner_rtol; /* mixed: inner PCG reduces its residual by this factor [1e-4] */
+} of_solve_opts;
+
+/* Per-pair result of of_solve / of_adjoint (host memory, written on return). */
+typedef struct {
+    int status;           /* of_status of this pair */
+    int outer_iters;      /* FP64 residual evaluations after the first */
+    int inner_iters;      /* PCG iterations in total */
+    double rel_residual;  /* final ||b - A U||_2 / ||b||_2, FP64, from the device */
+    float ms;             /* device time of the whole call (same for every pair) */
+} of_solve_info;
+
+/* Creates a handle bound to `device` and `cuda_stream` (a cudaStream_t, may
+ * be NULL for the legacy default stream).  *h receives the handle. */
+of_status of_create(of_handle *h, int device, void *cuda_stream);
+
+/* Declares a batch of `batch` frame pairs, pair p of W[p] x H[p] nodes
+ * (W, H >= 2; host arrays), and allocates the device workspace for them.
+ * Frames, alpha and solutions of earlier setups are discarded.  Returns
+ * OF_ERR_ARG for bad sizes or options, OF_ERR_OOM if the workspace does not
+ * fit. */
+of_status of_setup_grid(of_handle h, int batch, const int32_t *W, const int32_t *H, const of_grid_opts *o);
+
+/* Copies the two frames of pair `pair` ([H][pitch], dtype dt, pitch >=
+ * W) into the workspace, converting to the storage precision (FP32 for
+ * OF_PREC_MIXED, FP64 for OF_PREC_FP64).  Frames are the images f(., t) and
+ * f(., t+1) of Section 1 (already smoothed: K_sigma is the identity). */
+of_status of_set_frames(of_handle h, int pair, const void *f1, const void *f2, of_dtype dt, int64_t row_pitch_elems);
+
+/* Sets the per-element alpha of pair `pair` from `alpha` ([H-1][W-1][2],
+ * dtype dt), or, if alpha is NULL, to the constant alpha_const (> 0). */
+of_status of_set_alpha(of_handle h, int pair, const void *alpha, double alpha_const, of_dtype dt);
+
+/* Copies the current per-element alpha of a pair out ([H-1][W-1][2]). */
+of_status of_get_alpha(of_handle h, int pair, void *alpha, of_dtype dt);
+
+/* Solves A U = b for every pair (Section 2.2, Eq. discret-form): PCG with
+ * the overlapping Schwarz preconditioner of Section 3.2 (Eq. schwarz, one
+ * subdomain per CTA), in FP64 or in FP32 with FP64 iterative refinement.
+ * U[p] ([3][H][W], dtype dt) receives the solution; with warm_start it is
+ * also the initial guess.  info (host, `batch` entries, may be NULL)
+ * receives per-pair results.  Synchronises the stream.  Returns the worst
+ * per-pair status (OF_ERR_NOT_CONVERGED / OF_ERR_BREAKDOWN) or OF_OK. */
+of_status of_solve(of_handle h, const of_solve_opts *o, void *const *U, of_dtype dt, of_solve_info *info);
+
+/* Error indicator eta_K of Section 2.3 (Eq. errind) for the last solution
+ * of every pair, then the alpha update of Section 2.3:
+ *   alpha_K <- max(alpha_K / (1 + kappa max(eta_K / ||eta||_inf - eta_thr, 0)), alpha_th)
+ * (no change for a pair whose eta is identically 0).  Requires a previous
+ * of_solve.  eta (optional, per pair [H-1][W-1][2], dtype dt, may be NULL)
+ * receives eta_K before the update. */
+of_status of_adapt_alpha(of_handle h, double kappa, double eta_thr, double alpha_th, void *const *eta, of_dtype dt);
+
+/* Gradients of a scalar loss L(U) through the solve (implicit
+ * differentiation of A(theta) U = b(theta)): solves A Lam = dL/dU (A is
+ * symmetric, so the adjoint system is the same operator) with the options
+ * of the last of_solve, then forms per element
+ *   dL/dalpha_K = -|K| sum_{c=u1,u2} grad Lam_c . grad U_c
+ * and, through g_K and ft_K, dL/df2 and dL/df1 at the nodes.  dLdU[p] is
+ * [3][H][W]; dLdalpha[p] is [H-1][W-1][2]; dLdf2[p], dLdf1[p] are [H][W]
+ * (row pitch W); any output array list may be NULL.  Requires a previous
+ * of_solve (its U is the linearisation point).  Synchronises the stream. */
+of_status of_adjoint(of_handle h, void *const *dLdU, void *const *dLdalpha, void *const *dLdf2,
+                     void *const *dLdf1, of_dtype dt, of_solve_info *info);
+
+/* q = A p for one pair with the operator of Section 2.2 applied matrix-free
+ * (p, q: [3][H][W], dtype dt; FP64 handles apply in FP64, mixed handles in
+ * FP32).  The load vector b of the same system is written to b if b is not
+ * NULL. */
+of_status of_apply(of_handle h, int pair, const void *p, void *q, void *b, of_dtype dt);
+
+/* z = M^{-1} r with the Schwarz preconditioner of the handle (symmetric
+ * restricted overlapping Schwarz, Section 3.2, local solves by symmetric
+ * block Gauss-Seidel sweeps) for one pair; r, z: [3][H][W]. */
+of_status of_precondition(of_handle h, int pair, const void *r, void *z, of_dtype dt);
+
+/* FP64 relative residual ||b - A U||_2 / ||b||_2 of a pair for a given U
+ * ([3][H][W], dtype dt), computed on the device in FP64.  Synchronises. */
+of_status of_residual(of_handle h, int pair, const void *U, of_dtype dt, double *rel_residual);
+
+/* Kernel timing of the solve path, for measurement.  When enabled, every
+ * kernel launch of of_solve / of_adjoint / of_adapt_alpha is counted, and the
+ * launches of the three solve kernels are bracketed by CUDA events on the
+ * handle's stream; the totals accumulate until read.  Index 0: PCG apply
+ * (p, d, q and p.q), 1: Schwarz preconditioner (r, z, r.r, r.z), 2: FP64
+ * residual / refinement, 3: every other kernel (copies, indicator, alpha
+ * update, adjoint gradients; counted, not timed). */
+typedef struct {
+    int launches[4];
+    double ms[4];
+} of_profile;
+
+/* Turns kernel timing on (1) or off (0); turning it on clears the totals. */
+of_status of_set_profiling(of_handle h, int on);
+
+/* Copies the accumulated totals out and clears them. */
+of_status of_get_profile(of_handle h, of_profile *out);
+
+/* Releases the workspace and the handle (NULL is accepted). */
+of_status of_destroy(of_handle h);
+
+/* Message for the last non-OK status of h (or of a failed of_create when h
+ * is NULL); never NULL. */
+const char *of_last_error(of_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OF_H_ */

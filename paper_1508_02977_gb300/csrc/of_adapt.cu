@@ -1,0 +1,326 @@
+// Error indicator and alpha update (Section 2.3, Eq. errind and the update
+// formula that follows it), and the adjoint gradients of a loss through the
+// solve (implicit differentiation of A(theta) U = b(theta)).
+#include <cuda_runtime.h>
+
+#include "of_common.cuh"
+#include "of_launch.h"
+
+namespace ofl {
+
+using namespace ofk;
+
+// U (3 components) at node (x, y) of the FP64 solution planes, as R.
+template <typename R>
+struct UView {
+    const double* u;
+    long long plane;
+    int pitch;
+    __device__ __forceinline__ void at(int x, int y, R v[3]) const {
+        const long long o = (long long)y * pitch + x;
+        v[0] = (R)u[o];
+        v[1] = (R)u[o + plane];
+        v[2] = (R)u[o + 2 * plane];
+    }
+};
+
+// gradient of the P1 interpolant of U on triangle t of square (X,Y) from the
+// corner values A=(X,Y) B=(X+1,Y) C=(X+1,Y+1) D=(X,Y+1)
+template <typename R>
+__device__ __forceinline__ void tri_grad(int t, const R A[3], const R B[3], const R C[3], const R D[3], R gx[3],
+                                         R gy[3]) {
+    for (int c = 0; c < 3; ++c) {
+        if (t == 0) { gx[c] = B[c] - A[c]; gy[c] = C[c] - B[c]; }
+        else        { gx[c] = C[c] - D[c]; gy[c] = D[c] - A[c]; }
+    }
+}
+
+// ------------------------------------------------------------ indicator --
+// One thread per square; eta of both triangles.
+//   interior: h_K || Lambda^{-1/2} R ||_{L2(K)},  R = -g (g.U_h + ft), by the
+//             edge-midpoint rule (exact here): (|K|/3) G sum_m s_m^2,
+//             G = sum_c g_c^2 / Lambda_c, s_m = ft + g.U_h(midpoint m);
+//   edges:    (1/2) h_e |Lambda_e^{-1/2} J_e|  (J_e constant on the edge, so
+//             h_e^{1/2} ||.||_{L2(e)} = h_e |.|), J_e = outside - inside flux,
+//             outside flux 0 on the image boundary, Lambda_e = max of the two.
+template <typename R>
+__global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict__ f1a, const R* __restrict__ f2a,
+                            const R* __restrict__ ala, const double* __restrict__ ua, R* __restrict__ etaa, double lam_d,
+                            unsigned long long* __restrict__ etamax_bits) {
+    const PairDesc pd = pairs[pair];
+    const int W = pd.W, H = pd.H, pitch = pd.pitch;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    double lmax = 0.0;
+    if (x < W - 1 && y < H - 1) {
+        const R* f1 = f1a + pd.frame_off;
+        const R* f2 = f2a + pd.frame_off;
+        const R* al = ala + 2 * pd.frame_off;
+        UView<R> U{ua + pd.vec_off, (long long)H * pitch, pitch};
+        const R lam = (R)lam_d;
+        auto F1 = [&](int xx, int yy) { return f1[(long long)yy * pitch + xx]; };
+        auto F2 = [&](int xx, int yy) { return f2[(long long)yy * pitch + xx]; };
+        auto AL = [&](int xx, int yy, int t) { return al[2 * ((long long)yy * pitch + xx) + t]; };
+        R uA[3], uB[3], uC[3], uD[3];
+        U.at(x, y, uA); U.at(x + 1, y, uB); U.at(x + 1, y + 1, uC); U.at(x, y + 1, uD);
+        R gxK[2][3], gyK[2][3];
+        tri_grad<R>(0, uA, uB, uC, uD, gxK[0], gyK[0]);
+        tri_grad<R>(1, uA, uB, uC, uD, gxK[1], gyK[1]);
+        const R aK[2] = {AL(x, y, 0), AL(x, y, 1)};
+        const R third = R(1) / R(3);
+        const R sq2 = R(1.4142135623730951);
+        R* eta = etaa + 2 * pd.frame_off;
+        for (int t = 0; t < 2; ++t) {
+            // element data
+            const R* V1 = (t == 0) ? uB : uD;  // middle vertex
+            R g0, g1, g2, ft;
+            if (t == 0) {
+                g0 = F2(x + 1, y) - F2(x, y); g1 = F2(x + 1, y + 1) - F2(x + 1, y);
+                g2 = -(F1(x, y) + F1(x + 1, y) + F1(x + 1, y + 1)) * third;
+                ft = ((F2(x, y) - F1(x, y)) + (F2(x + 1, y) - F1(x + 1, y)) + (F2(x + 1, y + 1) - F1(x + 1, y + 1))) * third;
+            } else {
+                g0 = F2(x + 1, y + 1) - F2(x, y + 1); g1 = F2(x, y + 1) - F2(x, y);
+                g2 = -(F1(x, y) + F1(x, y + 1) + F1(x + 1, y + 1)) * third;
+                ft = ((F2(x, y) - F1(x, y)) + (F2(x, y + 1) - F1(x, y + 1)) + (F2(x + 1, y + 1) - F1(x + 1, y + 1))) * third;
+            }
+            const R Lk[3] = {aK[t], aK[t], lam};
+            const R G = g0 * g0 / Lk[0] + g1 * g1 / Lk[1] + g2 * g2 / Lk[2];
+            // midpoints of the 3 edges: (A,V1), (V1,C), (C,A)
+            R sm2 = R(0);
+            const R* P0[3] = {uA, V1, uC};
+            for (int e = 0; e < 3; ++e) {
+                const R* Pa = P0[e];
+                const R* Pb = P0[(e + 1) % 3];
+                const R s = ft + R(0.5) * (g0 * (Pa[0] + Pb[0]) + g1 * (Pa[1] + Pb[1]) + g2 * (Pa[2] + Pb[2]));
+                sm2 += s * s;
+            }
+            R val = sq2 * sqrt(R(0.5) / R(3) * G * sm2);
+            // edges: normal, length, neighbour (square, t) or none
+            for (int e = 0; e < 3; ++e) {
+                R nx, ny, he;
+                int nbx = 0, nby = 0, nbt = 0;
+                bool has = false;
+                if (t == 0) {
+                    if (e == 0) { nx = 0; ny = -1; he = 1; has = y >= 1; nbx = x; nby = y - 1; nbt = 1; }
+                    else if (e == 1) { nx = 1; ny = 0; he = 1; has = x + 1 <= W - 2; nbx = x + 1; nby = y; nbt = 1; }
+                    else { nx = -R(0.7071067811865476); ny = R(0.7071067811865476); he = sq2; has = true; nbx = x; nby = y; nbt = 1; }
+                } else {
+                    if (e == 0) { nx = -1; ny = 0; he = 1; has = x >= 1; nbx = x - 1; nby = y; nbt = 0; }
+                    else if (e == 1) { nx = 0; ny = 1; he = 1; has = y + 1 <= H - 2; nbx = x; nby = y + 1; nbt = 0; }
+                    else { nx = R(0.7071067811865476); ny = -R(0.7071067811865476); he = sq2; has = true; nbx = x; nby = y; nbt = 0; }
+                }
+                R ngx[3] = {0, 0, 0}, ngy[3] = {0, 0, 0};
+                R aO = R(0);
+                if (has) {
+                    R qA[3], qB[3], qC[3], qD[3];
+                    if (nbx == x && nby == y) {
+                        for (int c = 0; c < 3; ++c) { ngx[c] = gxK[nbt][c]; ngy[c] = gyK[nbt][c]; }
+                    } else {
+                        U.at(nbx, nby, qA); U.at(nbx + 1, nby, qB); U.at(nbx + 1, nby + 1, qC); U.at(nbx, nby + 1, qD);
+                        tri_grad<R>(nbt, qA, qB, qC, qD, ngx, ngy);
+                    }
+                    aO = AL(nbx, nby, nbt);
+                }
+                R q = R(0);
+                for (int c = 0; c < 3; ++c) {
+                    const R lk = Lk[c];
+                    const R lo = (c < 2) ? aO : lam;
+                    const R fin = lk * (gxK[t][c] * nx + gyK[t][c] * ny);
+                    const R fout = has ? lo * (ngx[c] * nx + ngy[c] * ny) : R(0);
+                    const R le = has ? (lo > lk ? lo : lk) : lk;
+                    const R J = fout - fin;
+                    q += J * J / le;
+                }
+                val += R(0.5) * he * sqrt(q);
+            }
+            eta[2 * ((long long)y * pitch + x) + t] = val;
+            const double dv = (double)val;
+            lmax = dv > lmax ? dv : lmax;
+        }
+    }
+    lmax = warp_max(lmax);
+    if ((threadIdx.x & 31) == 0 && lmax > 0.0) atomicMax(etamax_bits + pair, (unsigned long long)__double_as_longlong(lmax));
+}
+
+template <typename R>
+__global__ void k_alpha_update(const PairDesc* pairs, int pair, R* __restrict__ ala, const R* __restrict__ etaa,
+                               const unsigned long long* __restrict__ etamax_bits, double kappa, double eta_thr,
+                               double alpha_th) {
+    const PairDesc pd = pairs[pair];
+    const int W = pd.W, pitch = pd.pitch;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const double m = __longlong_as_double((long long)etamax_bits[pair]);
+    if (x >= W - 1 || !(m > 0.0)) return;
+    R* al = ala + 2 * pd.frame_off;
+    const R* eta = etaa + 2 * pd.frame_off;
+    for (int t = 0; t < 2; ++t) {
+        const long long o = 2 * ((long long)y * pitch + x) + t;
+        const R rel = (R)((double)eta[o] / m) - (R)eta_thr;
+        const R a = al[o] / (R(1) + (R)kappa * (rel > R(0) ? rel : R(0)));
+        al[o] = a > (R)alpha_th ? a : (R)alpha_th;
+    }
+}
+
+cudaError_t launch_indicator(const AdaptBufs& A, int pair, int H, int W, cudaStream_t st) {
+    dim3 grid((W - 1 + 127) / 128, H - 1);
+    if (A.fp64)
+        k_indicator<double><<<grid, 128, 0, st>>>(A.pairs, pair, (const double*)A.f1, (const double*)A.f2,
+                                                  (const double*)A.alpha, A.u, (double*)A.eta, A.lam,
+                                                  (unsigned long long*)A.etamax);
+    else
+        k_indicator<float><<<grid, 128, 0, st>>>(A.pairs, pair, (const float*)A.f1, (const float*)A.f2,
+                                                 (const float*)A.alpha, A.u, (float*)A.eta, A.lam,
+                                                 (unsigned long long*)A.etamax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_alpha_update(const AdaptBufs& A, int pair, int H, int W, double kappa, double eta_thr,
+                                double alpha_th, cudaStream_t st) {
+    dim3 grid((W - 1 + 127) / 128, H - 1);
+    if (A.fp64)
+        k_alpha_update<double><<<grid, 128, 0, st>>>(A.pairs, pair, (double*)A.alpha, (const double*)A.eta,
+                                                     (const unsigned long long*)A.etamax, kappa, eta_thr, alpha_th);
+    else
+        k_alpha_update<float><<<grid, 128, 0, st>>>(A.pairs, pair, (float*)A.alpha, (const float*)A.eta,
+                                                    (const unsigned long long*)A.etamax, kappa, eta_thr, alpha_th);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- adjoint --
+// Per element, with s_i = g.U_i, t_i = g.Lam_i (vertex i), the adjoint-weighted
+// element residual is
+//   E_K = |K|/12 sum_ij (1+d_ij) t_i s_j + |K|/3 ft sum_i t_i
+//         + |K| sum_c Lambda_c grad Lam_c . grad U_c
+// and dL/dtheta = -dE_K/dtheta.  Through g and ft:
+//   dE/dg_c = |K|/12 [sum_i (Lam_ic s_i + t_i U_ic) + (sum_i Lam_ic)(sum s)
+//             + (sum t)(sum_i U_ic)] + |K|/3 ft sum_i Lam_ic,
+//   dE/dft  = |K|/3 sum t.
+template <typename R>
+__device__ __forceinline__ void elem_adjoint(const R u[3][3], const R l[3][3], const R g[3], R ft, R dEdg[3], R& dEdft) {
+    R s[3], tt[3];
+    for (int i = 0; i < 3; ++i) {
+        s[i] = g[0] * u[i][0] + g[1] * u[i][1] + g[2] * u[i][2];
+        tt[i] = g[0] * l[i][0] + g[1] * l[i][1] + g[2] * l[i][2];
+    }
+    const R Ss = s[0] + s[1] + s[2], St = tt[0] + tt[1] + tt[2];
+    const R k12 = R(0.5) / R(12), k3 = R(0.5) / R(3);
+    for (int c = 0; c < 3; ++c) {
+        R a = R(0), Lc = R(0), Uc = R(0);
+        for (int i = 0; i < 3; ++i) {
+            a += l[i][c] * s[i] + tt[i] * u[i][c];
+            Lc += l[i][c];
+            Uc += u[i][c];
+        }
+        dEdg[c] = k12 * (a + Lc * Ss + St * Uc) + k3 * ft * Lc;
+    }
+    dEdft = k3 * St;
+}
+
+// dL/dalpha: one thread per square, both triangles.
+template <typename R, typename O>
+__global__ void k_adjoint_alpha(const PairDesc* pairs, int pair, const double* __restrict__ ua,
+                                const double* __restrict__ la, O* __restrict__ out) {
+    const PairDesc pd = pairs[pair];
+    const int W = pd.W, H = pd.H, pitch = pd.pitch;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W - 1 || y >= H - 1) return;
+    UView<R> U{ua + pd.vec_off, (long long)H * pitch, pitch};
+    UView<R> L{la + pd.vec_off, (long long)H * pitch, pitch};
+    R uA[3], uB[3], uC[3], uD[3], lA[3], lB[3], lC[3], lD[3];
+    U.at(x, y, uA); U.at(x + 1, y, uB); U.at(x + 1, y + 1, uC); U.at(x, y + 1, uD);
+    L.at(x, y, lA); L.at(x + 1, y, lB); L.at(x + 1, y + 1, lC); L.at(x, y + 1, lD);
+    for (int t = 0; t < 2; ++t) {
+        R ugx[3], ugy[3], lgx[3], lgy[3];
+        tri_grad<R>(t, uA, uB, uC, uD, ugx, ugy);
+        tri_grad<R>(t, lA, lB, lC, lD, lgx, lgy);
+        R s = R(0);
+        for (int c = 0; c < 2; ++c) s += lgx[c] * ugx[c] + lgy[c] * ugy[c];
+        out[((long long)y * (W - 1) + x) * 2 + t] = (O)(-R(0.5) * s);
+    }
+}
+
+// dL/df2 and dL/df1: one thread per node, gathering its 6 elements
+//   E1 = sq(x,y).t0 (node is a), E2 = sq(x,y).t1 (a), E3 = sq(x-1,y-1).t0 (c),
+//   E4 = sq(x-1,y-1).t1 (c), E5 = sq(x-1,y).t0 (b), E6 = sq(x,y-1).t1 (d),
+// with the node's basis gradient in each: (-1,0) (0,-1) (0,1) (1,0) (1,-1) (-1,1).
+template <typename R, typename O>
+__global__ void k_adjoint_frames(const PairDesc* pairs, int pair, const R* __restrict__ f1a, const R* __restrict__ f2a,
+                                 const double* __restrict__ ua, const double* __restrict__ la, O* __restrict__ df2,
+                                 O* __restrict__ df1) {
+    const PairDesc pd = pairs[pair];
+    const int W = pd.W, H = pd.H, pitch = pd.pitch;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W) return;
+    const R* f1 = f1a + pd.frame_off;
+    const R* f2 = f2a + pd.frame_off;
+    UView<R> U{ua + pd.vec_off, (long long)H * pitch, pitch};
+    UView<R> L{la + pd.vec_off, (long long)H * pitch, pitch};
+    const int sqx[6] = {x, x, x - 1, x - 1, x - 1, x};
+    const int sqy[6] = {y, y, y - 1, y - 1, y, y - 1};
+    const int sqt[6] = {0, 1, 0, 1, 0, 1};
+    const R phx[6] = {-1, 0, 0, 1, 1, -1};
+    const R phy[6] = {0, -1, 1, 0, -1, 1};
+    const R third = R(1) / R(3);
+    R a2 = R(0), a1 = R(0);
+    for (int e = 0; e < 6; ++e) {
+        const int X = sqx[e], Y = sqy[e], t = sqt[e];
+        if (X < 0 || Y < 0 || X >= W - 1 || Y >= H - 1) continue;
+        // vertices of the triangle: A=(X,Y), middle (B or D), C=(X+1,Y+1)
+        const int mx = (t == 0) ? X + 1 : X, my = (t == 0) ? Y : Y + 1;
+        const int vx[3] = {X, mx, X + 1}, vy[3] = {Y, my, Y + 1};
+        R u[3][3], l[3][3], fa[3], fb[3];
+        for (int i = 0; i < 3; ++i) {
+            U.at(vx[i], vy[i], u[i]);
+            L.at(vx[i], vy[i], l[i]);
+            fa[i] = f1[(long long)vy[i] * pitch + vx[i]];
+            fb[i] = f2[(long long)vy[i] * pitch + vx[i]];
+        }
+        R g[3];
+        if (t == 0) { g[0] = fb[1] - fb[0]; g[1] = fb[2] - fb[1]; }
+        else        { g[0] = fb[2] - fb[1]; g[1] = fb[1] - fb[0]; }
+        g[2] = -(fa[0] + fa[1] + fa[2]) * third;
+        const R ft = ((fb[0] - fa[0]) + (fb[1] - fa[1]) + (fb[2] - fa[2])) * third;
+        R dEdg[3], dEdft;
+        elem_adjoint<R>(u, l, g, ft, dEdg, dEdft);
+        a2 -= dEdg[0] * phx[e] + dEdg[1] * phy[e] + dEdft * third;
+        a1 += (dEdg[2] + dEdft) * third;
+    }
+    if (df2) df2[(long long)y * W + x] = (O)a2;
+    if (df1) df1[(long long)y * W + x] = (O)a1;
+}
+
+cudaError_t launch_adjoint_grad(const AdaptBufs& A, int pair, int H, int W, const double* lamv, void* dalpha,
+                                void* df2, void* df1, int out_type, cudaStream_t st) {
+    if (dalpha) {
+        dim3 grid((W - 1 + 127) / 128, H - 1);
+        if (A.fp64) {
+            if (out_type == T_F64) k_adjoint_alpha<double, double><<<grid, 128, 0, st>>>(A.pairs, pair, A.u, lamv, (double*)dalpha);
+            else k_adjoint_alpha<double, float><<<grid, 128, 0, st>>>(A.pairs, pair, A.u, lamv, (float*)dalpha);
+        } else {
+            if (out_type == T_F64) k_adjoint_alpha<float, double><<<grid, 128, 0, st>>>(A.pairs, pair, A.u, lamv, (double*)dalpha);
+            else k_adjoint_alpha<float, float><<<grid, 128, 0, st>>>(A.pairs, pair, A.u, lamv, (float*)dalpha);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (df2 || df1) {
+        dim3 grid((W + 127) / 128, H);
+        if (A.fp64) {
+            if (out_type == T_F64)
+                k_adjoint_frames<double, double><<<grid, 128, 0, st>>>(A.pairs, pair, (const double*)A.f1, (const double*)A.f2, A.u, lamv, (double*)df2, (double*)df1);
+            else
+                k_adjoint_frames<double, float><<<grid, 128, 0, st>>>(A.pairs, pair, (const double*)A.f1, (const double*)A.f2, A.u, lamv, (float*)df2, (float*)df1);
+        } else {
+            if (out_type == T_F64)
+                k_adjoint_frames<float, double><<<grid, 128, 0, st>>>(A.pairs, pair, (const float*)A.f1, (const float*)A.f2, A.u, lamv, (double*)df2, (double*)df1);
+            else
+                k_adjoint_frames<float, float><<<grid, 128, 0, st>>>(A.pairs, pair, (const float*)A.f1, (const float*)A.f2, A.u, lamv, (float*)df2, (float*)df1);
+        }
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ofl

@@ -1,0 +1,868 @@
+// C ABI of the optical-flow solver: handle, workspace, the mixed-precision
+// PCG driver, adaptation and adjoint entry points.  Declarations and the
+// contract of every entry point are in include/of.h.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "of.h"
+#include "of_launch.h"
+#include "of_schwarz.cuh"
+
+using ofk::PairDesc;
+using ofk::PairScalars;
+
+struct of_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    // grid
+    int batch = 0;
+    of_grid_opts opts{};
+    int fp64 = 1;
+    size_t es = 8;  // storage element size (frames, alpha, inner vectors)
+    std::vector<PairDesc> pd;
+    std::vector<int4> blocks, tiles;
+    std::vector<int> blk0, nblk, tile0, ntile;
+    long long frame_elems = 0, vec_elems = 0;
+    int nblk_total = 0, ntiles_total = 0, rows_per_block = 32;
+    // device memory
+    std::vector<void*> allocs;
+    void *f1 = nullptr, *f2 = nullptr, *alpha = nullptr, *eta = nullptr;
+    double *x[2] = {nullptr, nullptr}, *usol = nullptr, *cvec = nullptr;
+    void *r = nullptr, *z = nullptr, *q = nullptr, *d = nullptr, *p0 = nullptr, *p1 = nullptr;
+    PairDesc* pd_dev = nullptr;
+    int4 *blocks_dev = nullptr, *tiles_dev = nullptr;
+    CUtensorMap* tmaps_dev = nullptr;
+    PairScalars* sc_dev = nullptr;
+    PairScalars* sc_host = nullptr;  // pinned
+    double *partA = nullptr, *partS = nullptr, *etamax = nullptr;
+    unsigned *cntA = nullptr, *cntS = nullptr;
+    int* err_dev = nullptr;
+    void* staging = nullptr;
+    size_t staging_bytes = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // kernel timing (of_set_profiling)
+    struct ProfRec { int kind; cudaEvent_t a, b; };
+    bool prof = false;
+    std::vector<cudaEvent_t> evpool;
+    std::vector<ProfRec> recs;
+    of_profile ptot{};
+    // state
+    std::vector<char> frames_set, alpha_set;
+    bool solved = false;
+    of_solve_opts last_opts{};
+};
+
+static thread_local std::string g_create_err;
+
+namespace {
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DevGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+of_status fail(of_ctx* h, of_status s, const std::string& m) {
+    if (h) h->err = m;
+    else g_create_err = m;
+    return s;
+}
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) {                                                                     \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? OF_ERR_OOM : OF_ERR_CUDA,               \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+        }                                                                                            \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int tcode(of_dtype dt) { return dt == OF_F64 ? ofl::T_F64 : ofl::T_F32; }
+size_t tsize(of_dtype dt) { return dt == OF_F64 ? 8 : 4; }
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+void free_all(of_ctx* h) {
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    if (h->sc_host) cudaFreeHost(h->sc_host);
+    h->sc_host = nullptr;
+    h->f1 = h->f2 = h->alpha = h->eta = nullptr;
+    h->x[0] = h->x[1] = h->usol = h->cvec = nullptr;
+    h->r = h->z = h->q = h->d = h->p0 = h->p1 = nullptr;
+    h->batch = 0;
+    h->solved = false;
+}
+
+template <typename T>
+cudaError_t dalloc(of_ctx* h, T** p, size_t bytes) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, bytes < 256 ? 256 : bytes);
+    if (e != cudaSuccess) return e;
+    h->allocs.push_back(v);
+    *p = (T*)v;
+    return cudaSuccess;
+}
+
+cudaEvent_t pool_event(of_ctx* h) {
+    if (!h->evpool.empty()) {
+        cudaEvent_t e = h->evpool.back();
+        h->evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch `fn` (returns cudaError_t), bracketed by events when profiling.
+template <typename F>
+cudaError_t timed(of_ctx* h, int kind, F fn) {
+    if (!h->prof) return fn();
+    cudaEvent_t a = pool_event(h), b = pool_event(h);
+    cudaEventRecord(a, h->stream);
+    cudaError_t e = fn();
+    cudaEventRecord(b, h->stream);
+    h->recs.push_back({kind, a, b});
+    return e;
+}
+
+void count_other(of_ctx* h, int n) {
+    if (h->prof) h->ptot.launches[3] += n;
+}
+
+// Accumulates recorded launches (the stream must have passed them).
+void prof_flush(of_ctx* h) {
+    for (auto& r : h->recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) h->ptot.ms[r.kind] += ms;
+        h->ptot.launches[r.kind] += 1;
+        h->evpool.push_back(r.a);
+        h->evpool.push_back(r.b);
+    }
+    h->recs.clear();
+}
+
+template <typename... A>
+cudaError_t cp2d(of_ctx* h, A... a) {
+    count_other(h, 1);
+    return ofl::copy2d(a...);
+}
+template <typename... A>
+cudaError_t fl2d(of_ctx* h, A... a) {
+    count_other(h, 1);
+    return ofl::fill2d(a...);
+}
+
+ofl::SolveBufs solve_bufs(of_ctx* h) {
+    ofl::SolveBufs B;
+    memset(&B, 0, sizeof(B));
+    B.pairs = h->pd_dev;
+    B.blocks = h->blocks_dev;
+    B.tiles = h->tiles_dev;
+    B.tmaps = h->tmaps_dev;
+    B.sc = h->sc_dev;
+    B.partA = h->partA;
+    B.partS = h->partS;
+    B.cntA = h->cntA;
+    B.cntS = h->cntS;
+    B.err = h->err_dev;
+    B.f1 = h->f1;
+    B.f2 = h->f2;
+    B.alpha = h->alpha;
+    B.r = h->r;
+    B.z = h->z;
+    B.q = h->q;
+    B.d = h->d;
+    B.p0 = h->p0;
+    B.p1 = h->p1;
+    B.nblk = h->nblk_total;
+    B.ntiles = h->ntiles_total;
+    B.rows_per_block = h->rows_per_block;
+    B.Tx = h->opts.tile_x;
+    B.Ty = h->opts.tile_y;
+    B.ov = h->opts.overlap;
+    B.sweeps = h->opts.sweeps;
+    B.lam = h->opts.lambda;
+    B.fp64 = h->fp64;
+    B.spin_limit = 4000000000LL;  // ~2 s at 2 GHz
+    return B;
+}
+
+ofl::AdaptBufs adapt_bufs(of_ctx* h) {
+    ofl::AdaptBufs A;
+    memset(&A, 0, sizeof(A));
+    A.pairs = h->pd_dev;
+    A.f1 = h->f1;
+    A.f2 = h->f2;
+    A.alpha = h->alpha;
+    A.u = h->usol;
+    A.eta = h->eta;
+    A.etamax = h->etamax;
+    A.lam = h->opts.lambda;
+    A.fp64 = h->fp64;
+    return A;
+}
+
+of_status check_pair(of_ctx* h, int pair) {
+    if (!h) return OF_ERR_ARG;
+    if (h->batch == 0) return fail(h, OF_ERR_STATE, "of_setup_grid has not been called");
+    if (pair < 0 || pair >= h->batch) return fail(h, OF_ERR_ARG, "pair index out of range");
+    return OF_OK;
+}
+
+// Copy a user array (rows x cols, row pitch upitch, dtype dt, host or device)
+// into a workspace array (dtype of the handle, row pitch wpitch).
+of_status copy_in(of_ctx* h, const void* src, of_dtype dt, long long upitch, void* dst, long long wpitch,
+                  long long rows, long long cols) {
+    const int st = tcode(dt), wt = h->fp64 ? ofl::T_F64 : ofl::T_F32;
+    if (is_device_ptr(src)) {
+        CK(cp2d(h, src, st, upitch, dst, wt, wpitch, rows, cols, h->stream));
+    } else {
+        const size_t need = (size_t)rows * cols * tsize(dt);
+        if (need > h->staging_bytes) return fail(h, OF_ERR_ARG, "host array larger than the staging buffer");
+        CK(cudaMemcpy2DAsync(h->staging, cols * tsize(dt), src, upitch * tsize(dt), cols * tsize(dt), rows,
+                             cudaMemcpyHostToDevice, h->stream));
+        CK(cp2d(h, h->staging, st, cols, dst, wt, wpitch, rows, cols, h->stream));
+    }
+    return OF_OK;
+}
+
+// Copy a workspace array (type wt) out to a user array (dtype dt, contiguous
+// rows x cols), host or device.
+of_status copy_out(of_ctx* h, const void* src, int wt, long long wpitch, void* dst, of_dtype dt, long long rows,
+                   long long cols) {
+    const int dtc = tcode(dt);
+    if (is_device_ptr(dst)) {
+        CK(cp2d(h, src, wt, wpitch, dst, dtc, cols, rows, cols, h->stream));
+    } else {
+        const size_t need = (size_t)rows * cols * tsize(dt);
+        if (need > h->staging_bytes) return fail(h, OF_ERR_ARG, "host array larger than the staging buffer");
+        CK(cp2d(h, src, wt, wpitch, h->staging, dtc, cols, rows, cols, h->stream));
+        CK(cudaMemcpyAsync(dst, h->staging, need, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));  // the staging buffer is reused by the next copy
+    }
+    return OF_OK;
+}
+
+of_status encode_maps(of_ctx* h) {
+    auto enc = get_encode();
+    if (!enc) return fail(h, OF_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const int Tx = h->opts.tile_x, Ty = h->opts.tile_y, ov = h->opts.overlap;
+    const int BW = ofk::sch_bw(Tx, ov), BH = ofk::sch_bh(Ty, ov);
+    const CUtensorMapDataType dtp = h->fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const size_t es = h->es;
+    std::vector<CUtensorMap> maps((size_t)h->batch * ofk::TM_PER_PAIR);
+    for (int p = 0; p < h->batch; ++p) {
+        const PairDesc& d = h->pd[p];
+        CUtensorMap* m = &maps[(size_t)p * ofk::TM_PER_PAIR];
+        const cuuint32_t es1[3] = {1, 1, 1};
+        {  // frames
+            const cuuint64_t dims[2] = {(cuuint64_t)d.W, (cuuint64_t)d.H};
+            const cuuint64_t str[1] = {(cuuint64_t)d.pitch * es};
+            const cuuint32_t box[2] = {(cuuint32_t)BW, (cuuint32_t)BH};
+            for (int k = 0; k < 2; ++k) {
+                char* base = (char*)(k == 0 ? h->f1 : h->f2) + d.frame_off * es;
+                CUresult rc = enc(&m[k == 0 ? ofk::TM_F1 : ofk::TM_F2], dtp, 2, base, dims, str, box, es1,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (rc != CUDA_SUCCESS) return fail(h, OF_ERR_CUDA, "tensor map (frames) encoding failed");
+            }
+        }
+        {  // alpha, viewed as [H-1][2(W-1)] scalars with row stride 2 pitch
+            const cuuint64_t dims[2] = {(cuuint64_t)(2 * (d.W - 1)), (cuuint64_t)(d.H - 1)};
+            const cuuint64_t str[1] = {(cuuint64_t)2 * d.pitch * es};
+            const cuuint32_t box[2] = {(cuuint32_t)(2 * BW), (cuuint32_t)(BH - 1)};
+            char* base = (char*)h->alpha + 2 * d.frame_off * es;
+            CUresult rc = enc(&m[ofk::TM_AL], dtp, 2, base, dims, str, box, es1, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (rc != CUDA_SUCCESS) return fail(h, OF_ERR_CUDA, "tensor map (alpha) encoding failed");
+        }
+        {  // r and q planes
+            const cuuint64_t dims[3] = {(cuuint64_t)d.W, (cuuint64_t)d.H, 3};
+            const cuuint64_t str[2] = {(cuuint64_t)d.pitch * es, (cuuint64_t)d.H * d.pitch * es};
+            const cuuint32_t box[3] = {(cuuint32_t)Tx, (cuuint32_t)Ty, 3};
+            for (int k = 0; k < 2; ++k) {
+                char* base = (char*)(k == 0 ? h->r : h->q) + d.vec_off * es;
+                CUresult rc = enc(&m[k == 0 ? ofk::TM_R : ofk::TM_Q], dtp, 3, base, dims, str, box, es1,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (rc != CUDA_SUCCESS) return fail(h, OF_ERR_CUDA, "tensor map (vectors) encoding failed");
+            }
+        }
+    }
+    CUtensorMap* dev = nullptr;
+    CK(dalloc(h, &dev, maps.size() * sizeof(CUtensorMap)));
+    CK(cudaMemcpyAsync(dev, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, h->stream));
+    h->tmaps_dev = dev;
+    return OF_OK;
+}
+
+// The solve driver shared by of_solve and of_adjoint.  rhs == NULL: b from
+// the frames; otherwise the FP64 right-hand side planes.  On return x[cur]
+// holds the solution.
+of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* cur_out, std::vector<int>& passes_out) {
+    ofl::SolveBufs B = solve_bufs(h);
+    cudaStream_t st = h->stream;
+    int cur = 0;
+    const int chunk = 8;
+    passes_out.assign(h->batch, 0);
+    CK(cudaMemsetAsync(h->cntA, 0, sizeof(unsigned) * h->batch, st));
+    CK(cudaMemsetAsync(h->cntS, 0, sizeof(unsigned) * h->batch, st));
+    CK(cudaMemsetAsync(h->sc_dev, 0, sizeof(PairScalars) * h->batch, st));
+    for (int pass = 0;; ++pass) {
+        const int first = (pass == 0);
+        double* xout = first ? nullptr : h->x[1 - cur];
+        CK(timed(h, 2, [&] { return ofl::launch_residual(B, h->x[cur], xout, rhs, first, o.rtol, o.inner_rtol, o.max_inner, st); }));
+        if (!first) cur = 1 - cur;
+        if (pass == o.max_outer) {
+            CK(cudaMemcpyAsync(h->sc_host, h->sc_dev, sizeof(PairScalars) * h->batch, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            break;
+        }
+        CK(timed(h, 1, [&] { return ofl::launch_precond_first(B, st); }));
+        int it = 0;
+        bool all_done = false;
+        while (!all_done) {
+            for (int c = 0; c < chunk; ++c, ++it) {
+                CK(timed(h, 0, [&] { return ofl::launch_pcg_apply(B, it == 0, st); }));
+                CK(timed(h, 1, [&] { return ofl::launch_pcg_precond(B, st); }));
+            }
+            CK(cudaMemcpyAsync(h->sc_host, h->sc_dev, sizeof(PairScalars) * h->batch, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            all_done = true;
+            for (int p = 0; p < h->batch; ++p) all_done = all_done && h->sc_host[p].done;
+            if (it >= o.max_inner + chunk) all_done = true;
+        }
+        bool all_conv = true;
+        for (int p = 0; p < h->batch; ++p) {
+            const bool conv = h->sc_host[p].pad[0] != 0;
+            const bool broke = h->sc_host[p].status == 6 && h->sc_host[p].it == 0 && !conv;
+            if (!conv && !broke) {
+                all_conv = false;
+                passes_out[p] = pass + 1;
+            }
+        }
+        if (all_conv) break;
+    }
+    *cur_out = cur;
+    prof_flush(h);
+    int errw = 0;
+    CK(cudaMemcpy(&errw, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (errw) return fail(h, OF_ERR_TIMEOUT, "a bounded device wait (TMA staging) ran out");
+    return OF_OK;
+}
+
+void fill_info(of_ctx* h, const std::vector<int>& passes, float ms, of_solve_info* info, of_status* worst) {
+    *worst = OF_OK;
+    for (int p = 0; p < h->batch; ++p) {
+        const PairScalars& s = h->sc_host[p];
+        of_status st = OF_OK;
+        if (s.pad[0]) st = OF_OK;
+        else if (s.status == 6 || !std::isfinite(s.res2)) st = OF_ERR_BREAKDOWN;
+        else st = OF_ERR_NOT_CONVERGED;
+        if (st == OF_ERR_BREAKDOWN || (st == OF_ERR_NOT_CONVERGED && *worst == OF_OK)) *worst = st;
+        if (info) {
+            info[p].status = st;
+            info[p].outer_iters = passes[p];
+            info[p].inner_iters = s.it_total;
+            info[p].rel_residual = s.bnorm2 > 0 ? std::sqrt(s.res2 / s.bnorm2) : std::sqrt(s.res2);
+            info[p].ms = ms;
+        }
+    }
+}
+
+of_solve_opts with_defaults(const of_solve_opts* o, int fp64) {
+    of_solve_opts r{};
+    if (o) r = *o;
+    if (r.rtol <= 0) r.rtol = 1e-6;
+    if (r.max_outer <= 0) r.max_outer = 20;
+    if (r.max_inner <= 0) r.max_inner = 2000;
+    if (r.inner_rtol <= 0) r.inner_rtol = fp64 ? 1e-12 : 1e-4;
+    return r;
+}
+
+}  // namespace
+
+extern "C" {
+
+of_status of_create(of_handle* hp, int device, void* cuda_stream) {
+    if (!hp) return fail(nullptr, OF_ERR_ARG, "null handle pointer");
+    *hp = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return fail(nullptr, OF_ERR_CUDA, "no CUDA device");
+    }
+    if (device < 0 || device >= n) return fail(nullptr, OF_ERR_ARG, "device out of range");
+    of_ctx* h = new of_ctx();
+    h->device = device;
+    h->stream = (cudaStream_t)cuda_stream;
+    DevGuard g(device);
+    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+        delete h;
+        return fail(nullptr, OF_ERR_CUDA, "event creation failed");
+    }
+    *hp = h;
+    return OF_OK;
+}
+
+of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t* H, const of_grid_opts* o) {
+    if (!h) return OF_ERR_ARG;
+    if (batch < 1 || !W || !H) return fail(h, OF_ERR_ARG, "batch must be >= 1 with W and H arrays");
+    DevGuard g(h->device);
+    of_grid_opts opt{};
+    if (o) opt = *o;
+    if (opt.precision != OF_PREC_FP64 && opt.precision != OF_PREC_MIXED) return fail(h, OF_ERR_ARG, "bad precision");
+    if (opt.tile_x == 0) opt.tile_x = 32;
+    if (opt.tile_y == 0) opt.tile_y = 32;
+    if (opt.lambda == 0) opt.lambda = 1.0;
+    if (opt.preconditioner == OF_PC_JACOBI) {
+        opt.overlap = 0;
+        opt.sweeps = 0;
+    } else {
+        if (opt.sweeps == 0) opt.sweeps = 1;
+    }
+    if (!(opt.lambda > 0)) return fail(h, OF_ERR_ARG, "lambda must be > 0");
+    if (opt.tile_x < 4 || opt.tile_y < 4 || opt.tile_x % 4 || opt.tile_y % 4 || opt.tile_x > 256 || opt.tile_y > 256)
+        return fail(h, OF_ERR_ARG, "tile sizes must be multiples of 4 in [4, 256]");
+    if (opt.overlap < 0 || opt.overlap > 32 || opt.sweeps < 0 || opt.sweeps > 64)
+        return fail(h, OF_ERR_ARG, "overlap must be in [0, 32] and sweeps in [0, 64]");
+    if (2 * ofk::sch_bw(opt.tile_x, opt.overlap) > 256 || ofk::sch_bh(opt.tile_y, opt.overlap) > 256)
+        return fail(h, OF_ERR_ARG, "tile + overlap too large for one staged window (tile_x + 2 overlap <= 118)");
+    for (int p = 0; p < batch; ++p)
+        if (W[p] < 2 || H[p] < 2 || W[p] > (1 << 20) || H[p] > (1 << 20))
+            return fail(h, OF_ERR_ARG, "every frame must be at least 2x2 and at most 2^20 per side");
+    const int fp64 = opt.precision == OF_PREC_FP64;
+    const size_t smem = ofl::schwarz_smem_bytes(fp64, opt.tile_x, opt.tile_y, opt.overlap);
+    int smax = 0;
+    CK(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (smem > (size_t)smax) return fail(h, OF_ERR_ARG, "tile/overlap need more shared memory than one CTA has");
+
+    CK(cudaStreamSynchronize(h->stream));
+    free_all(h);
+    h->opts = opt;
+    h->fp64 = fp64;
+    h->es = fp64 ? 8 : 4;
+    h->batch = batch;
+    h->pd.assign(batch, PairDesc{});
+    h->blocks.clear();
+    h->tiles.clear();
+    h->blk0.assign(batch, 0);
+    h->nblk.assign(batch, 0);
+    h->tile0.assign(batch, 0);
+    h->ntile.assign(batch, 0);
+    long long fo = 0, vo = 0;
+    size_t stage = 0;
+    const int cols_per_block = 31 * 4;
+    for (int p = 0; p < batch; ++p) {
+        PairDesc& d = h->pd[p];
+        d.W = W[p];
+        d.H = H[p];
+        d.pitch = (W[p] + 31) / 32 * 32;
+        d.frame_off = fo;
+        d.vec_off = vo;
+        d.tiles_x = (W[p] + opt.tile_x - 1) / opt.tile_x;
+        d.tiles_y = (H[p] + opt.tile_y - 1) / opt.tile_y;
+        d.tile0 = (int)h->tiles.size();
+        for (int ty = 0; ty < d.tiles_y; ++ty)
+            for (int tx = 0; tx < d.tiles_x; ++tx) h->tiles.push_back(make_int4(p, tx, ty, (int)h->tiles.size()));
+        const int bx = (W[p] + cols_per_block - 1) / cols_per_block;
+        const int by = (H[p] + h->rows_per_block - 1) / h->rows_per_block;
+        d.blk0 = (int)h->blocks.size();
+        d.nblk = bx * by;
+        for (int yb = 0; yb < by; ++yb)
+            for (int xb = 0; xb < bx; ++xb) h->blocks.push_back(make_int4(p, xb, yb, (int)h->blocks.size()));
+        h->blk0[p] = d.blk0;
+        h->nblk[p] = d.nblk;
+        h->tile0[p] = d.tile0;
+        h->ntile[p] = d.tiles_x * d.tiles_y;
+        fo += (long long)H[p] * d.pitch;
+        vo += 3LL * H[p] * d.pitch;
+        stage = std::max(stage, (size_t)3 * W[p] * H[p] * 8);
+    }
+    h->frame_elems = fo;
+    h->vec_elems = vo;
+    h->nblk_total = (int)h->blocks.size();
+    h->ntiles_total = (int)h->tiles.size();
+    const size_t es = h->es;
+    CK(dalloc(h, &h->f1, fo * es));
+    CK(dalloc(h, &h->f2, fo * es));
+    CK(dalloc(h, &h->alpha, 2 * fo * es));
+    CK(dalloc(h, &h->eta, 2 * fo * es));
+    for (int k = 0; k < 2; ++k) CK(dalloc(h, &h->x[k], vo * sizeof(double)));
+    CK(dalloc(h, &h->usol, vo * sizeof(double)));
+    CK(dalloc(h, &h->cvec, vo * sizeof(double)));
+    CK(dalloc(h, &h->r, vo * es));
+    CK(dalloc(h, &h->z, vo * es));
+    CK(dalloc(h, &h->q, vo * es));
+    CK(dalloc(h, &h->d, vo * es));
+    CK(dalloc(h, &h->p0, vo * es));
+    CK(dalloc(h, &h->p1, vo * es));
+    CK(dalloc(h, &h->pd_dev, sizeof(PairDesc) * batch));
+    CK(dalloc(h, &h->blocks_dev, sizeof(int4) * h->blocks.size()));
+    CK(dalloc(h, &h->tiles_dev, sizeof(int4) * h->tiles.size()));
+    CK(dalloc(h, &h->sc_dev, sizeof(PairScalars) * batch));
+    CK(dalloc(h, &h->partA, sizeof(double) * 2 * h->blocks.size()));
+    CK(dalloc(h, &h->partS, sizeof(double) * 2 * h->tiles.size()));
+    CK(dalloc(h, &h->etamax, sizeof(double) * batch));
+    CK(dalloc(h, &h->cntA, sizeof(unsigned) * batch));
+    CK(dalloc(h, &h->cntS, sizeof(unsigned) * batch));
+    CK(dalloc(h, &h->err_dev, sizeof(int)));
+    CK(dalloc(h, &h->staging, stage));
+    h->staging_bytes = stage;
+    CK(cudaMallocHost((void**)&h->sc_host, sizeof(PairScalars) * batch));
+    cudaStream_t st = h->stream;
+    CK(cudaMemcpyAsync(h->pd_dev, h->pd.data(), sizeof(PairDesc) * batch, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->blocks_dev, h->blocks.data(), sizeof(int4) * h->blocks.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->tiles_dev, h->tiles.data(), sizeof(int4) * h->tiles.size(), cudaMemcpyHostToDevice, st));
+    for (void* v : {(void*)h->x[0], (void*)h->x[1], (void*)h->usol, (void*)h->cvec})
+        CK(cudaMemsetAsync(v, 0, vo * sizeof(double), st));
+    for (void* v : {h->r, h->z, h->q, h->d, h->p0, h->p1}) CK(cudaMemsetAsync(v, 0, vo * es, st));
+    CK(cudaMemsetAsync(h->f1, 0, fo * es, st));
+    CK(cudaMemsetAsync(h->f2, 0, fo * es, st));
+    CK(cudaMemsetAsync(h->alpha, 0, 2 * fo * es, st));
+    CK(cudaMemsetAsync(h->sc_dev, 0, sizeof(PairScalars) * batch, st));
+    CK(cudaMemsetAsync(h->cntA, 0, sizeof(unsigned) * batch, st));
+    CK(cudaMemsetAsync(h->cntS, 0, sizeof(unsigned) * batch, st));
+    CK(cudaMemsetAsync(h->err_dev, 0, sizeof(int), st));
+    of_status s = encode_maps(h);
+    if (s != OF_OK) return s;
+    CK(ofl::schwarz_configure(fp64, smem));
+    h->frames_set.assign(batch, 0);
+    h->alpha_set.assign(batch, 0);
+    h->solved = false;
+    CK(cudaStreamSynchronize(st));
+    return OF_OK;
+}
+
+of_status of_set_frames(of_handle h, int pair, const void* f1, const void* f2, of_dtype dt, int64_t pitch) {
+    of_status s = check_pair(h, pair);
+    if (s != OF_OK) return s;
+    const PairDesc& d = h->pd[pair];
+    if (!f1 || !f2 || pitch < d.W) return fail(h, OF_ERR_ARG, "null frame or row pitch < W");
+    DevGuard g(h->device);
+    const size_t es = h->es;
+    s = copy_in(h, f1, dt, pitch, (char*)h->f1 + d.frame_off * es, d.pitch, d.H, d.W);
+    if (s != OF_OK) return s;
+    s = copy_in(h, f2, dt, pitch, (char*)h->f2 + d.frame_off * es, d.pitch, d.H, d.W);
+    if (s != OF_OK) return s;
+    h->frames_set[pair] = 1;
+    h->solved = false;
+    return OF_OK;
+}
+
+of_status of_set_alpha(of_handle h, int pair, const void* alpha, double alpha_const, of_dtype dt) {
+    of_status s = check_pair(h, pair);
+    if (s != OF_OK) return s;
+    const PairDesc& d = h->pd[pair];
+    DevGuard g(h->device);
+    void* dst = (char*)h->alpha + 2 * d.frame_off * h->es;
+    if (!alpha) {
+        if (!(alpha_const > 0) || !std::isfinite(alpha_const)) return fail(h, OF_ERR_ARG, "alpha_const must be > 0");
+        CK(fl2d(h, dst, h->fp64 ? ofl::T_F64 : ofl::T_F32, 2LL * d.pitch, d.H - 1, 2LL * (d.W - 1), alpha_const,
+                       h->stream));
+    } else {
+        s = copy_in(h, alpha, dt, 2LL * (d.W - 1), dst, 2LL * d.pitch, d.H - 1, 2LL * (d.W - 1));
+        if (s != OF_OK) return s;
+    }
+    h->alpha_set[pair] = 1;
+    h->solved = false;
+    return OF_OK;
+}
+
+of_status of_get_alpha(of_handle h, int pair, void* alpha, of_dtype dt) {
+    of_status s = check_pair(h, pair);
+    if (s != OF_OK) return s;
+    if (!alpha) return fail(h, OF_ERR_ARG, "null alpha");
+    const PairDesc& d = h->pd[pair];
+    DevGuard g(h->device);
+    return copy_out(h, (char*)h->alpha + 2 * d.frame_off * h->es, h->fp64 ? ofl::T_F64 : ofl::T_F32, 2LL * d.pitch,
+                    alpha, dt, d.H - 1, 2LL * (d.W - 1));
+}
+
+of_status of_solve(of_handle h, const of_solve_opts* o, void* const* U, of_dtype dt, of_solve_info* info) {
+    if (!h) return OF_ERR_ARG;
+    if (h->batch == 0) return fail(h, OF_ERR_STATE, "of_setup_grid has not been called");
+    for (int p = 0; p < h->batch; ++p)
+        if (!h->frames_set[p] || !h->alpha_set[p]) return fail(h, OF_ERR_STATE, "frames or alpha not set for a pair");
+    if (!U) return fail(h, OF_ERR_ARG, "null solution array list");
+    for (int p = 0; p < h->batch; ++p)
+        if (!U[p]) return fail(h, OF_ERR_ARG, "null solution array");
+    DevGuard g(h->device);
+    const of_solve_opts opt = with_defaults(o, h->fp64);
+    cudaStream_t st = h->stream;
+    CK(cudaEventRecord(h->ev0, st));
+    for (int p = 0; p < h->batch; ++p) {
+        const PairDesc& d = h->pd[p];
+        double* x0 = h->x[0] + d.vec_off;
+        if (opt.warm_start) {
+            // [3][H][W] user planes -> [3][H][pitch] FP64 planes
+            if (is_device_ptr(U[p])) {
+                CK(cp2d(h, U[p], tcode(dt), d.W, x0, ofl::T_F64, d.pitch, 3LL * d.H, d.W, st));
+            } else {
+                CK(cudaMemcpyAsync(h->staging, U[p], 3ULL * d.H * d.W * tsize(dt), cudaMemcpyHostToDevice, st));
+                CK(cp2d(h, h->staging, tcode(dt), d.W, x0, ofl::T_F64, d.pitch, 3LL * d.H, d.W, st));
+            }
+        } else {
+            CK(cudaMemsetAsync(x0, 0, 3ULL * d.H * d.pitch * sizeof(double), st));
+        }
+    }
+    int cur = 0;
+    std::vector<int> passes;
+    of_status s = run_solve(h, opt, nullptr, &cur, passes);
+    if (s != OF_OK) return s;
+    CK(cudaMemcpyAsync(h->usol, h->x[cur], h->vec_elems * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (int p = 0; p < h->batch; ++p) {
+        const PairDesc& d = h->pd[p];
+        s = copy_out(h, h->x[cur] + d.vec_off, ofl::T_F64, d.pitch, U[p], dt, 3LL * d.H, d.W);
+        if (s != OF_OK) return s;
+    }
+    CK(cudaEventRecord(h->ev1, st));
+    CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    of_status worst;
+    fill_info(h, passes, ms, info, &worst);
+    h->solved = true;
+    h->last_opts = opt;
+    if (worst != OF_OK) return fail(h, worst, worst == OF_ERR_BREAKDOWN ? "CG breakdown (singular or indefinite data)"
+                                                                       : "not converged within the iteration caps");
+    return OF_OK;
+}
+
+of_status of_adapt_alpha(of_handle h, double kappa, double eta_thr, double alpha_th, void* const* eta, of_dtype dt) {
+    if (!h) return OF_ERR_ARG;
+    if (!h->solved) return fail(h, OF_ERR_STATE, "of_adapt_alpha needs a previous of_solve");
+    if (!(kappa >= 0) || !(alpha_th > 0)) return fail(h, OF_ERR_ARG, "kappa must be >= 0 and alpha_th > 0");
+    DevGuard g(h->device);
+    ofl::AdaptBufs A = adapt_bufs(h);
+    cudaStream_t st = h->stream;
+    CK(cudaMemsetAsync(h->etamax, 0, sizeof(double) * h->batch, st));
+    for (int p = 0; p < h->batch; ++p) {
+        const PairDesc& d = h->pd[p];
+        CK(ofl::launch_indicator(A, p, d.H, d.W, st));
+        count_other(h, 1);
+        if (eta && eta[p]) {
+            of_status s = copy_out(h, (char*)h->eta + 2 * d.frame_off * h->es, h->fp64 ? ofl::T_F64 : ofl::T_F32,
+                                   2LL * d.pitch, eta[p], dt, d.H - 1, 2LL * (d.W - 1));
+            if (s != OF_OK) return s;
+        }
+        CK(ofl::launch_alpha_update(A, p, d.H, d.W, kappa, eta_thr, alpha_th, st));
+        count_other(h, 1);
+    }
+    CK(cudaStreamSynchronize(st));
+    h->solved = false;  // alpha changed: the stored solution no longer belongs to it
+    return OF_OK;
+}
+
+of_status of_adjoint(of_handle h, void* const* dLdU, void* const* dLdalpha, void* const* dLdf2, void* const* dLdf1,
+                     of_dtype dt, of_solve_info* info) {
+    if (!h) return OF_ERR_ARG;
+    if (!h->solved) return fail(h, OF_ERR_STATE, "of_adjoint needs a previous of_solve");
+    if (!dLdU) return fail(h, OF_ERR_ARG, "null dL/dU list");
+    DevGuard g(h->device);
+    cudaStream_t st = h->stream;
+    CK(cudaEventRecord(h->ev0, st));
+    for (int p = 0; p < h->batch; ++p) {
+        const PairDesc& d = h->pd[p];
+        if (!dLdU[p]) return fail(h, OF_ERR_ARG, "null dL/dU array");
+        double* c = h->cvec + d.vec_off;
+        if (is_device_ptr(dLdU[p])) {
+            CK(cp2d(h, dLdU[p], tcode(dt), d.W, c, ofl::T_F64, d.pitch, 3LL * d.H, d.W, st));
+        } else {
+            CK(cudaMemcpyAsync(h->staging, dLdU[p], 3ULL * d.H * d.W * tsize(dt), cudaMemcpyHostToDevice, st));
+            CK(cp2d(h, h->staging, tcode(dt), d.W, c, ofl::T_F64, d.pitch, 3LL * d.H, d.W, st));
+        }
+        CK(cudaMemsetAsync(h->x[0] + d.vec_off, 0, 3ULL * d.H * d.pitch * sizeof(double), st));
+    }
+    of_solve_opts opt = h->last_opts;
+    int cur = 0;
+    std::vector<int> passes;
+    of_status s = run_solve(h, opt, h->cvec, &cur, passes);
+    if (s != OF_OK) return s;
+    ofl::AdaptBufs A = adapt_bufs(h);
+    for (int p = 0; p < h->batch; ++p) {
+        const PairDesc& d = h->pd[p];
+        void* da = dLdalpha ? dLdalpha[p] : nullptr;
+        void* d2 = dLdf2 ? dLdf2[p] : nullptr;
+        void* d1 = dLdf1 ? dLdf1[p] : nullptr;
+        // device outputs are written directly; host outputs go through the staging buffer
+        const bool host_any = (da && !is_device_ptr(da)) || (d2 && !is_device_ptr(d2)) || (d1 && !is_device_ptr(d1));
+        if (!host_any) {
+            CK(ofl::launch_adjoint_grad(A, p, d.H, d.W, h->x[cur], da, d2, d1, tcode(dt), st));
+        } else {
+            // one output at a time through the staging buffer
+            const size_t esz = tsize(dt);
+            struct Item { void* dst; int kind; size_t n; } items[3] = {
+                {da, 0, (size_t)2 * (d.W - 1) * (d.H - 1)}, {d2, 1, (size_t)d.W * d.H}, {d1, 2, (size_t)d.W * d.H}};
+            for (auto& it : items) {
+                if (!it.dst) continue;
+                if (is_device_ptr(it.dst)) {
+                    CK(ofl::launch_adjoint_grad(A, p, d.H, d.W, h->x[cur], it.kind == 0 ? it.dst : nullptr,
+                                                it.kind == 1 ? it.dst : nullptr, it.kind == 2 ? it.dst : nullptr,
+                                                tcode(dt), st));
+                } else {
+                    CK(ofl::launch_adjoint_grad(A, p, d.H, d.W, h->x[cur], it.kind == 0 ? h->staging : nullptr,
+                                                it.kind == 1 ? h->staging : nullptr,
+                                                it.kind == 2 ? h->staging : nullptr, tcode(dt), st));
+                    CK(cudaMemcpyAsync(it.dst, h->staging, it.n * esz, cudaMemcpyDeviceToHost, st));
+                    CK(cudaStreamSynchronize(st));
+                }
+            }
+        }
+    }
+    CK(cudaEventRecord(h->ev1, st));
+    CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    of_status worst;
+    fill_info(h, passes, ms, info, &worst);
+    if (worst != OF_OK) return fail(h, worst, "adjoint solve did not converge");
+    return OF_OK;
+}
+
+of_status of_apply(of_handle h, int pair, const void* p, void* q, void* b, of_dtype dt) {
+    of_status s = check_pair(h, pair);
+    if (s != OF_OK) return s;
+    if (!p || !q) return fail(h, OF_ERR_ARG, "null p or q");
+    if (!h->frames_set[pair] || !h->alpha_set[pair]) return fail(h, OF_ERR_STATE, "frames or alpha not set");
+    DevGuard g(h->device);
+    const PairDesc& d = h->pd[pair];
+    const size_t es = h->es;
+    const int wt = h->fp64 ? ofl::T_F64 : ofl::T_F32;
+    void* zin = (char*)h->z + d.vec_off * es;
+    s = copy_in(h, p, dt, d.W, zin, d.pitch, 3LL * d.H, d.W);
+    if (s != OF_OK) return s;
+    ofl::SolveBufs B = solve_bufs(h);
+    CK(ofl::launch_apply(B, pair, h->blk0[pair], h->nblk[pair], h->z, h->q, b ? h->d : nullptr, h->stream));
+    s = copy_out(h, (char*)h->q + d.vec_off * es, wt, d.pitch, q, dt, 3LL * d.H, d.W);
+    if (s != OF_OK) return s;
+    if (b) {
+        s = copy_out(h, (char*)h->d + d.vec_off * es, wt, d.pitch, b, dt, 3LL * d.H, d.W);
+        if (s != OF_OK) return s;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return OF_OK;
+}
+
+of_status of_precondition(of_handle h, int pair, const void* r, void* z, of_dtype dt) {
+    of_status s = check_pair(h, pair);
+    if (s != OF_OK) return s;
+    if (!r || !z) return fail(h, OF_ERR_ARG, "null r or z");
+    if (!h->frames_set[pair] || !h->alpha_set[pair]) return fail(h, OF_ERR_STATE, "frames or alpha not set");
+    DevGuard g(h->device);
+    const PairDesc& d = h->pd[pair];
+    const size_t es = h->es;
+    s = copy_in(h, r, dt, d.W, (char*)h->r + d.vec_off * es, d.pitch, 3LL * d.H, d.W);
+    if (s != OF_OK) return s;
+    ofl::SolveBufs B = solve_bufs(h);
+    CK(ofl::launch_precond_only(B, h->tile0[pair], h->ntile[pair], h->stream));
+    s = copy_out(h, (char*)h->z + d.vec_off * es, h->fp64 ? ofl::T_F64 : ofl::T_F32, d.pitch, z, dt, 3LL * d.H, d.W);
+    if (s != OF_OK) return s;
+    CK(cudaStreamSynchronize(h->stream));
+    int errw = 0;
+    CK(cudaMemcpy(&errw, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (errw) return fail(h, OF_ERR_TIMEOUT, "a bounded device wait (TMA staging) ran out");
+    return OF_OK;
+}
+
+of_status of_residual(of_handle h, int pair, const void* U, of_dtype dt, double* rel) {
+    of_status s = check_pair(h, pair);
+    if (s != OF_OK) return s;
+    if (!U || !rel) return fail(h, OF_ERR_ARG, "null U or result");
+    if (!h->frames_set[pair] || !h->alpha_set[pair]) return fail(h, OF_ERR_STATE, "frames or alpha not set");
+    DevGuard g(h->device);
+    const PairDesc& d = h->pd[pair];
+    cudaStream_t st = h->stream;
+    double* c = h->cvec + d.vec_off;
+    if (is_device_ptr(U)) {
+        CK(cp2d(h, U, tcode(dt), d.W, c, ofl::T_F64, d.pitch, 3LL * d.H, d.W, st));
+    } else {
+        CK(cudaMemcpyAsync(h->staging, U, 3ULL * d.H * d.W * tsize(dt), cudaMemcpyHostToDevice, st));
+        CK(cp2d(h, h->staging, tcode(dt), d.W, c, ofl::T_F64, d.pitch, 3LL * d.H, d.W, st));
+    }
+    ofl::SolveBufs B = solve_bufs(h);
+    B.blocks = h->blocks_dev + h->blk0[pair];
+    B.nblk = h->nblk[pair];
+    CK(ofl::launch_residual(B, h->cvec, nullptr, nullptr, 1, 1e-300, 1e-300, 1, st));
+    PairScalars sc;
+    CK(cudaMemcpyAsync(&sc, h->sc_dev + pair, sizeof(sc), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *rel = sc.bnorm2 > 0 ? std::sqrt(sc.res2 / sc.bnorm2) : std::sqrt(sc.res2);
+    return OF_OK;
+}
+
+of_status of_set_profiling(of_handle h, int on) {
+    if (!h) return OF_ERR_ARG;
+    h->prof = on != 0;
+    h->ptot = of_profile{};
+    return OF_OK;
+}
+
+of_status of_get_profile(of_handle h, of_profile* out) {
+    if (!h || !out) return OF_ERR_ARG;
+    DevGuard g(h->device);
+    CK(cudaStreamSynchronize(h->stream));
+    prof_flush(h);
+    *out = h->ptot;
+    h->ptot = of_profile{};
+    return OF_OK;
+}
+
+of_status of_destroy(of_handle h) {
+    if (!h) return OF_OK;
+    {
+        DevGuard g(h->device);
+        cudaStreamSynchronize(h->stream);
+        prof_flush(h);
+        for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+        h->evpool.clear();
+        free_all(h);
+        if (h->ev0) cudaEventDestroy(h->ev0);
+        if (h->ev1) cudaEventDestroy(h->ev1);
+    }
+    delete h;
+    return OF_OK;
+}
+
+const char* of_last_error(of_handle h) {
+    if (!h) return g_create_err.c_str();
+    return h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,313 @@
+// Matrix-free apply of the P1 operator of Section 2.2 (Eq. discret-form),
+// element by element, streamed down pixel columns.
+//
+// Layout of the work: a warp owns 32 consecutive square columns; lane l
+// computes the two triangles of square (cx, sy) for cx = X0 + 31 w - 1 + l
+// while walking down the rows.  The 4 corner contributions of a square are
+// combined across lanes with one shuffle (left corners of square cx+1 come
+// from lane l+1) and across rows with a register carry (top corners of row
+// sy are the bottom corners' partners of row sy+1), so every element is
+// formed exactly once and every input word is read once per warp (plus a
+// one-column halo).  Lane 31 only helps: each warp outputs 31 columns.
+//
+// Modes (template MODE):
+//   APPLY : out = A in                                  (+ optional load b)
+//   PCG   : in = z + beta p_old  (p_new stored),  d += a_prev p_old,
+//           out q = A in,  partial sum p.q  -> pair scalar a = rz / pq
+//   RES   : in = x + d + a p  (x_new stored),  out r = rhs - A in,
+//           rhs = b (frames) or a given vector,  partial ||r||^2, ||rhs||^2
+#pragma once
+#include "of_common.cuh"
+
+namespace ofk {
+
+enum { MODE_APPLY = 0, MODE_PCG = 1, MODE_RES = 2 };
+
+template <typename R> struct V3 { R a, b, c; };
+template <typename R> __device__ __forceinline__ V3<R> v3(R a, R b, R c) { V3<R> v; v.a = a; v.b = b; v.c = c; return v; }
+template <typename R> __device__ __forceinline__ V3<R> operator+(V3<R> x, V3<R> y) { return v3(x.a + y.a, x.b + y.b, x.c + y.c); }
+template <typename R> __device__ __forceinline__ V3<R> shfl_down3(V3<R> x) { return v3(shfl_down(x.a, 1), shfl_down(x.b, 1), shfl_down(x.c, 1)); }
+
+template <typename R> struct NodeVal { V3<R> p; R f1, f2; };
+
+// Contributions of the two triangles of one square to its corners
+// A=(x,y) B=(x+1,y) C=(x+1,y+1) D=(x,y+1): sign * (A_K p)_i, and, when WANT_B,
+// the load -|K|/3 ft g of each triangle (same for its 3 vertices).
+template <typename R, bool WANT_B>
+__device__ __forceinline__ void square_contrib(const NodeVal<R>& A, const NodeVal<R>& B, const NodeVal<R>& C,
+                                               const NodeVal<R>& D, R al0, R al1, R lam, bool valid,
+                                               V3<R>& cA, V3<R>& cB, V3<R>& cC, V3<R>& cD,
+                                               V3<R>& bA, V3<R>& bB, V3<R>& bC, V3<R>& bD) {
+    const R third = R(1) / R(3);
+    const R w24 = R(1) / R(24);
+    const R h = R(OF_STIFF_HALF);
+    // ---- t = 0: A, B, C
+    R g0x = B.f2 - A.f2, g0y = C.f2 - B.f2, g0m = -(A.f1 + B.f1 + C.f1) * third;
+    R sA = g0x * A.p.a + g0y * A.p.b + g0m * A.p.c;
+    R sB = g0x * B.p.a + g0y * B.p.b + g0m * B.p.c;
+    R sC = g0x * C.p.a + g0y * C.p.b + g0m * C.p.c;
+    R S0 = sA + sB + sC;
+    R wA = (sA + S0) * w24, wB = (sB + S0) * w24, wC = (sC + S0) * w24;
+    // ---- t = 1: A, D, C
+    R g1x = C.f2 - D.f2, g1y = D.f2 - A.f2, g1m = -(A.f1 + D.f1 + C.f1) * third;
+    R tA = g1x * A.p.a + g1y * A.p.b + g1m * A.p.c;
+    R tD = g1x * D.p.a + g1y * D.p.b + g1m * D.p.c;
+    R tC = g1x * C.p.a + g1y * C.p.b + g1m * C.p.c;
+    R S1 = tA + tD + tC;
+    R vA = (tA + S1) * w24, vD = (tD + S1) * w24, vC = (tC + S1) * w24;
+    // stiffness: legs A-B, B-C (t=0) and A-D, D-C (t=1), weight 1/2 each
+    R a0 = h * al0, a1 = h * al1, l0 = h * lam;
+    V3<R> dAB = v3(A.p.a - B.p.a, A.p.b - B.p.b, A.p.c - B.p.c);
+    V3<R> dCB = v3(C.p.a - B.p.a, C.p.b - B.p.b, C.p.c - B.p.c);
+    V3<R> dAD = v3(A.p.a - D.p.a, A.p.b - D.p.b, A.p.c - D.p.c);
+    V3<R> dCD = v3(C.p.a - D.p.a, C.p.b - D.p.b, C.p.c - D.p.c);
+    cA.a = wA * g0x + vA * g1x + a0 * dAB.a + a1 * dAD.a;
+    cA.b = wA * g0y + vA * g1y + a0 * dAB.b + a1 * dAD.b;
+    cA.c = wA * g0m + vA * g1m + l0 * (dAB.c + dAD.c);
+    cB.a = wB * g0x - a0 * (dAB.a + dCB.a);
+    cB.b = wB * g0y - a0 * (dAB.b + dCB.b);
+    cB.c = wB * g0m - l0 * (dAB.c + dCB.c);
+    cC.a = wC * g0x + vC * g1x + a0 * dCB.a + a1 * dCD.a;
+    cC.b = wC * g0y + vC * g1y + a0 * dCB.b + a1 * dCD.b;
+    cC.c = wC * g0m + vC * g1m + l0 * (dCB.c + dCD.c);
+    cD.a = vD * g1x - a1 * (dAD.a + dCD.a);
+    cD.b = vD * g1y - a1 * (dAD.b + dCD.b);
+    cD.c = vD * g1m - l0 * (dAD.c + dCD.c);
+    if (WANT_B) {
+        const R sixth = R(1) / R(6);
+        R ft0 = ((A.f2 - A.f1) + (B.f2 - B.f1) + (C.f2 - C.f1)) * third;
+        R ft1 = ((A.f2 - A.f1) + (D.f2 - D.f1) + (C.f2 - C.f1)) * third;
+        R k0 = -sixth * ft0, k1 = -sixth * ft1;
+        V3<R> b0 = v3(k0 * g0x, k0 * g0y, k0 * g0m);
+        V3<R> b1 = v3(k1 * g1x, k1 * g1y, k1 * g1m);
+        bA = b0 + b1; bB = b0; bC = b0 + b1; bD = b1;
+    }
+    if (!valid) {
+        cA = cB = cC = cD = v3(R(0), R(0), R(0));
+        if (WANT_B) bA = bB = bC = bD = v3(R(0), R(0), R(0));
+    }
+}
+
+template <typename R, typename C, typename RI>
+struct ApplyParams {
+    const PairDesc* pairs;
+    const int4* blocks;        // per block: (pair, column block, row block, global block index)
+    const PairScalars* sc_in;  // PCG: beta, a_prev, it; RES: a
+    PairScalars* sc;           // scalars written by the last block
+    double* partial;           // [nblocks][2]
+    unsigned* counter;         // [batch]
+    const C* f1; const C* f2; const C* alpha;
+    R lam;
+    int rows_per_block;
+    // vectors ([3][H][pitch] planes at pair vec_off)
+    const R* in;        // APPLY: p;  PCG: z;  RES: x (double)
+    RI* p_buf0;         // PCG: p buffers (even / odd);  RES: p buffers of the inner solve
+    RI* p_buf1;
+    RI* dcorr;          // PCG: d (in/out);  RES: d (in)
+    R* out;             // APPLY: q; PCG: q; RES: x_new
+    RI* rout;           // RES: r (inner precision)
+    R* bout;            // APPLY: optional b
+    const R* rhs_vec;   // RES: rhs vector instead of the frame load (adjoint), or null
+    int first;          // PCG: first iteration of a pass (p = z, d = 0);  RES: no correction
+    double rtol, inner_rtol;
+    int max_inner;
+};
+
+template <typename R, typename C, typename RI, int MODE, bool WANT_B, int NW>
+__global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P) {
+    constexpr int NT = NW * 32;
+    __shared__ double sh_red[NT / 32];
+    __shared__ int sh_last;
+    const int4 bi = P.blocks[blockIdx.x];
+    const int pair = bi.x;
+    const PairDesc pd = P.pairs[pair];
+    const int W = pd.W, H = pd.H, pitch = pd.pitch;
+    const long long plane = (long long)H * pitch;
+
+    R beta = R(0);
+    R a_prev = R(0);
+    int it = 0;
+    bool corr = false;  // RES: fold the inner correction d + a p into x
+    if (MODE == MODE_PCG) {
+        if (P.sc_in[pair].done) return;  // uniform over the pair's blocks
+        beta = (R)P.sc_in[pair].beta;
+        a_prev = (R)P.sc_in[pair].a;
+        it = P.sc_in[pair].it;
+    }
+    if (MODE == MODE_RES) {
+        it = P.sc_in[pair].it;
+        corr = !P.first && it > 0;
+        a_prev = corr ? (R)P.sc_in[pair].a : R(0);
+    }
+
+    const C* f1 = P.f1 + pd.frame_off;
+    const C* f2 = P.f2 + pd.frame_off;
+    const C* al = P.alpha + 2 * pd.frame_off;
+    const long long vo = pd.vec_off;
+    const R* vin = P.in + vo;
+    const RI* pold = nullptr;
+    RI* pnew = nullptr;
+    if (MODE == MODE_PCG) {
+        pold = ((it & 1) ? P.p_buf1 : P.p_buf0) + vo;
+        pnew = ((it & 1) ? P.p_buf0 : P.p_buf1) + vo;
+    }
+    if (MODE == MODE_RES) pold = ((it & 1) ? P.p_buf1 : P.p_buf0) + vo;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int X0 = bi.y * (31 * NW);
+    const int cx = X0 + 31 * warp - 1 + lane;  // square column / load column of this lane
+    const int Y0 = bi.z * P.rows_per_block;
+    const int Y1 = min(Y0 + P.rows_per_block, H);
+    const bool mycol_owned = (lane >= 1) && (cx < W) && (cx >= 0);  // side-effect writes
+    const bool out_col = (lane < 31) && (cx + 1 < W);
+    const R lam = P.lam;
+
+    // load node (x, y) of the input vector + frames, with the mode's fused
+    // update; side effects (p_new, d, x_new) only for owned nodes
+    auto load = [&](int x, int y, bool owner) -> NodeVal<R> {
+        NodeVal<R> v;
+        const bool in = (x >= 0) && (x < W) && (y >= 0) && (y < H);
+        if (!in) { v.p = v3(R(0), R(0), R(0)); v.f1 = R(0); v.f2 = R(0); return v; }
+        const long long o = (long long)y * pitch + x;
+        v.f1 = (R)f1[o];
+        v.f2 = (R)f2[o];
+        R p0 = vin[o], p1 = vin[o + plane], p2 = vin[o + 2 * plane];
+        if (MODE == MODE_PCG) {
+            if (!P.first) {
+                R q0 = pold[o], q1 = pold[o + plane], q2 = pold[o + 2 * plane];
+                if (owner) {
+                    RI* d = P.dcorr + vo;
+                    d[o] += (RI)(a_prev * q0);
+                    d[o + plane] += (RI)(a_prev * q1);
+                    d[o + 2 * plane] += (RI)(a_prev * q2);
+                }
+                p0 = p0 + beta * q0; p1 = p1 + beta * q1; p2 = p2 + beta * q2;
+            } else if (owner) {
+                RI* d = P.dcorr + vo;
+                d[o] = RI(0); d[o + plane] = RI(0); d[o + 2 * plane] = RI(0);
+            }
+            if (owner) { pnew[o] = p0; pnew[o + plane] = p1; pnew[o + 2 * plane] = p2; }
+        }
+        if (MODE == MODE_RES) {
+            if (corr) {
+                const RI* d = P.dcorr + vo;
+                p0 = p0 + ((R)d[o] + a_prev * (R)pold[o]);
+                p1 = p1 + ((R)d[o + plane] + a_prev * (R)pold[o + plane]);
+                p2 = p2 + ((R)d[o + 2 * plane] + a_prev * (R)pold[o + 2 * plane]);
+            }
+            if (owner && P.out) {
+                R* xn = P.out + vo;
+                xn[o] = p0; xn[o + plane] = p1; xn[o + 2 * plane] = p2;
+            }
+        }
+        v.p = v3(p0, p1, p2);
+        return v;
+    };
+    auto shfl_node = [&](const NodeVal<R>& v) -> NodeVal<R> {
+        NodeVal<R> w;
+        w.p = shfl_down3(v.p);
+        w.f1 = shfl_down(v.f1, 1);
+        w.f2 = shfl_down(v.f2, 1);
+        return w;
+    };
+
+    R acc = R(0);          // PCG: per-thread partial of p.q (inner precision)
+    double accd = 0.0, acc_b = 0.0;  // RES: FP64 norms
+    // prologue: node row Y0-1
+    NodeVal<R> cur = load(cx, Y0 - 1, false);
+    NodeVal<R> ncur = shfl_node(cur);
+    if (lane == 31) ncur = load(cx + 1, Y0 - 1, false);
+    V3<R> carry = v3(R(0), R(0), R(0)), carry_b = v3(R(0), R(0), R(0));
+    for (int sy = Y0 - 1; sy < Y1; ++sy) {
+        const bool row_owned = (sy + 1 >= Y0) && (sy + 1 < Y1);
+        NodeVal<R> nxt = load(cx, sy + 1, mycol_owned && row_owned);
+        NodeVal<R> nnxt = shfl_node(nxt);
+        if (lane == 31) nnxt = load(cx + 1, sy + 1, false);
+        const bool valid = (cx >= 0) && (cx < W - 1) && (sy >= 0) && (sy < H - 1);
+        const R al0 = valid ? (R)al[2 * ((long long)sy * pitch + cx)] : R(0);
+        const R al1 = valid ? (R)al[2 * ((long long)sy * pitch + cx) + 1] : R(0);
+        V3<R> cA, cB, cC, cD, bA, bB, bC, bD;
+        square_contrib<R, WANT_B || (MODE == MODE_RES)>(cur, ncur, nnxt, nxt, al0, al1, lam, valid,
+                                                         cA, cB, cC, cD, bA, bB, bC, bD);
+        V3<R> left = shfl_down3(cA);
+        V3<R> res = carry + cB + left;  // node (cx+1, sy) complete
+        V3<R> resb;
+        constexpr bool NEED_B = WANT_B || (MODE == MODE_RES);
+        if (NEED_B) resb = carry_b + bB + shfl_down3(bA);
+        if (sy >= Y0 && out_col) {
+            const long long o = (long long)sy * pitch + (cx + 1);
+            if (MODE == MODE_APPLY || MODE == MODE_PCG) {
+                R* q = P.out + vo;
+                q[o] = res.a; q[o + plane] = res.b; q[o + 2 * plane] = res.c;
+                if (MODE == MODE_PCG) acc += ncur.p.a * res.a + ncur.p.b * res.b + ncur.p.c * res.c;
+                if (WANT_B && P.bout) {
+                    R* bo = P.bout + vo;
+                    bo[o] = resb.a; bo[o + plane] = resb.b; bo[o + 2 * plane] = resb.c;
+                }
+            }
+            if (MODE == MODE_RES) {
+                V3<R> rhs;
+                if (P.rhs_vec) {
+                    const R* c = P.rhs_vec + vo;
+                    rhs = v3(c[o], c[o + plane], c[o + 2 * plane]);
+                } else {
+                    rhs = resb;
+                }
+                V3<R> r = v3(rhs.a - res.a, rhs.b - res.b, rhs.c - res.c);
+                RI* ro = P.rout + vo;
+                ro[o] = (RI)r.a; ro[o + plane] = (RI)r.b; ro[o + 2 * plane] = (RI)r.c;
+                accd += (double)r.a * (double)r.a + (double)r.b * (double)r.b + (double)r.c * (double)r.c;
+                acc_b += (double)rhs.a * (double)rhs.a + (double)rhs.b * (double)rhs.b + (double)rhs.c * (double)rhs.c;
+            }
+        }
+        carry = cC + shfl_down3(cD);
+        if (NEED_B) carry_b = bC + shfl_down3(bD);
+        cur = nxt;
+        ncur = nnxt;
+    }
+
+    if (MODE == MODE_APPLY) return;
+    // ---- block partials and last-block reduction of the pair
+    double s0 = block_sum<NT>((MODE == MODE_PCG) ? (double)acc : accd, sh_red);
+    double s1 = (MODE == MODE_RES) ? block_sum<NT>(acc_b, sh_red) : 0.0;
+    if (threadIdx.x == 0) {
+        P.partial[2 * (long long)bi.w] = s0;
+        P.partial[2 * (long long)bi.w + 1] = s1;
+    }
+    if (!arrive_last(&P.counter[pair], (unsigned)pd.nblk, &sh_last)) return;
+    double t0 = ordered_sum<NT>(P.partial + 2 * (long long)pd.blk0, pd.nblk, 2, sh_red);
+    double t1 = (MODE == MODE_RES) ? ordered_sum<NT>(P.partial + 2 * (long long)pd.blk0 + 1, pd.nblk, 2, sh_red) : 0.0;
+    if (threadIdx.x == 0) {
+        PairScalars* s = P.sc + pair;
+        if (MODE == MODE_PCG) {
+            s->pq = t0;
+            if (!(t0 > 0.0) || !isfinite(t0) || !isfinite(s->rz)) {
+                s->a = 0.0;
+                s->done = 1;
+                s->status = 6;
+            } else {
+                s->a = s->rz / t0;
+            }
+        } else {  // MODE_RES: set up the inner pass
+            s->res2 = t0;
+            if (P.first) s->bnorm2 = t1;
+            const double b2 = s->bnorm2;
+            const bool conv = (t0 <= P.rtol * P.rtol * b2) || (t0 == 0.0);
+            double rel = 0.5 * P.rtol * sqrt(b2 / (t0 > 0.0 ? t0 : 1.0));
+            if (rel < P.inner_rtol) rel = P.inner_rtol;
+            if (rel > 0.5) rel = 0.5;
+            s->tol2 = rel * rel * t0;
+            s->it = 0;
+            s->done = conv ? 1 : 0;
+            s->status = isfinite(t0) ? 0 : 6;
+            if (!isfinite(t0)) s->done = 1;
+            s->max_it = P.max_inner;
+            s->a = 0.0;
+            s->pad[0] = conv ? 1 : 0;  // outer convergence flag
+        }
+        __threadfence();
+        P.counter[pair] = 0u;
+    }
+}
+
+}  // namespace ofk

@@ -1,0 +1,105 @@
+// Shared device-side definitions of the optical-flow solver (sm_103a).
+//
+// Discretisation (Section 2.2, Fig. sch-mesh): one node per pixel centre,
+// square (x,y) cut along (x,y)->(x+1,y+1) into
+//   t=0: a=(x,y) b=(x+1,y) c=(x+1,y+1)     t=1: a=(x,y) d=(x,y+1) c=(x+1,y+1)
+// with |K| = 1/2.  Per element the data of Eq. OF2 are
+//   g = (d/dx f2_h, d/dy f2_h, -mean f1),   ft = mean (f2 - f1)
+// and the element matrix of the weak form (Eq. discret-form) is
+//   |K|/12 (1+delta_ij) g g^T  +  |K| Lambda grad phi_i . grad phi_j,
+// Lambda = (alpha_K, alpha_K, lambda), load -|K|/3 ft g.  On these right
+// triangles the stiffness couples only the two legs of each triangle, each
+// with weight |K| = 1/2, so the node stencil is 7-point.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ofk {
+
+// Workspace layouts (device):
+//   frame  [H][pitch]          Real
+//   alpha  [H][pitch][2]       Real   (square (x,y) of rows 0..H-2, cols 0..W-2)
+//   vector [3][H][pitch]       Real   (plane stride H*pitch)
+struct PairDesc {
+    int W, H, pitch;
+    int tiles_x, tiles_y;   // Schwarz tiles of this pair
+    int tile0;              // first Schwarz work item of this pair
+    int blk0, nblk;         // first apply block of this pair, number of apply blocks
+    long long frame_off;    // element offset of this pair's frames in the frame arrays
+    long long vec_off;      // element offset of this pair's planes in the vector arrays
+};
+
+// Per-pair scalars of the Krylov loop (device memory, FP64).
+struct PairScalars {
+    double rz;        // r.z of the current iterate
+    double pq;        // p.q
+    double a;         // step a = rz / pq of the current iteration
+    double a_prev;    // step of the previous iteration (deferred x update)
+    double beta;      // rz_new / rz_old
+    double rr;        // ||r||^2 of the inner (recursive) residual
+    double tol2;      // inner stop: rr <= tol2
+    double bnorm2;    // ||b||^2 (FP64)
+    double res2;      // ||b - A x||^2 of the last FP64 residual evaluation
+    int it;           // inner iterations done in this pass
+    int it_total;     // inner iterations in total
+    int done;         // inner loop finished (converged, capped or broken down)
+    int status;       // 0 ok, 5 not converged, 6 breakdown
+    int max_it;       // inner iteration cap of this pass
+    int pad[3];
+};
+
+#define OF_STIFF_HALF 0.5   // |K| * |grad phi|^2 weight of a triangle leg
+
+template <typename T> __device__ __forceinline__ T ld_or0(const T* p, bool ok) { return ok ? *p : T(0); }
+
+__device__ __forceinline__ float shfl_down(float v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ double shfl_down(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename T> __device__ __forceinline__ T warp_max(T v) {
+    for (int o = 16; o > 0; o >>= 1) { T w = __shfl_xor_sync(0xffffffffu, v, o); v = w > v ? w : v; }
+    return v;
+}
+
+// Deterministic block sum of one double per thread (fixed tree order).
+template <int NT> __device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = (l < NT / 32) ? sh[l] : 0.0;
+        s = warp_sum(s);
+    }
+    return s;  // valid in thread 0
+}
+
+// "Last block of the pair" protocol: every block writes its partial, fences,
+// and bumps the pair counter; the block that sees count == n-1 reduces all
+// partials of the pair in index order (deterministic) and resets the
+// counter for the next launch.
+__device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned n, int* sh_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned prev = atomicAdd(counter, 1u);
+        *sh_flag = (prev == n - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (*sh_flag) { __threadfence(); return true; }
+    return false;
+}
+
+// Sum of n doubles (stride `stride`) in fixed order by one block.
+template <int NT> __device__ double ordered_sum(const double* p, int n, int stride, double* sh) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += NT) s += __ldcg(p + (long long)i * stride);
+    return block_sum<NT>(s, sh);
+}
+
+}  // namespace ofk

@@ -1,0 +1,89 @@
+// Host-side launch interface between the C ABI (of_api.cu) and the kernels
+// (of_kernels.cu, of_adapt.cu).  Internal to the library.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "of_common.cuh"
+
+namespace ofl {
+
+// element types of a copy
+enum { T_F32 = 0, T_F64 = 1 };
+
+// Strided 2D copy with conversion: dst[r*dpitch + c] = src[r*spitch + c].
+cudaError_t copy2d(const void* src, int stype, long long spitch, void* dst, int dtype, long long dpitch,
+                   long long rows, long long cols, cudaStream_t st);
+// Fill rows x cols of a strided array with a constant.
+cudaError_t fill2d(void* dst, int dtype, long long dpitch, long long rows, long long cols, double v, cudaStream_t st);
+
+struct SolveBufs {
+    const ofk::PairDesc* pairs;
+    const int4* blocks;
+    const int4* tiles;
+    const CUtensorMap* tmaps;
+    ofk::PairScalars* sc;
+    double* partA;
+    double* partS;
+    unsigned* cntA;
+    unsigned* cntS;
+    int* err;
+    const void* f1;
+    const void* f2;
+    const void* alpha;
+    void* r;
+    void* z;
+    void* q;
+    void* d;
+    void* p0;
+    void* p1;
+    int nblk, ntiles, rows_per_block;
+    int Tx, Ty, ov, sweeps;
+    double lam;
+    int fp64;            // 1: everything FP64; 0: FP32 inner with FP64 residual
+    long long spin_limit;
+};
+
+// Pass start: xout = xin + d + a p (unless first), r = rhs - A xout,
+// ||r||^2, ||rhs||^2 (first) and the inner-pass set-up per pair.
+cudaError_t launch_residual(const SolveBufs& B, const double* xin, double* xout, const double* rhs_vec, int first,
+                            double rtol, double inner_rtol, int max_inner, cudaStream_t st);
+// z = M r at the start of a pass (rz, rr, convergence check).
+cudaError_t launch_precond_first(const SolveBufs& B, cudaStream_t st);
+// One PCG iteration = launch_pcg_apply (p, d, q, a) then launch_pcg_precond
+// (r, z, rz, beta, stop).
+cudaError_t launch_pcg_apply(const SolveBufs& B, int first, cudaStream_t st);
+cudaError_t launch_pcg_precond(const SolveBufs& B, cudaStream_t st);
+// Stand-alone operator apply (q = A p, optional b) in the inner precision
+// (fp64 = 0: FP32) or FP64 for one pair (blocks of that pair only).
+cudaError_t launch_apply(const SolveBufs& B, int pair, int blk0, int nblk, const void* p, void* q, void* b,
+                         cudaStream_t st);
+// Stand-alone preconditioner z = M r for one pair (tiles of that pair only);
+// r must already be in B.r.
+cudaError_t launch_precond_only(const SolveBufs& B, int tile0, int ntiles, cudaStream_t st);
+size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov);
+cudaError_t schwarz_configure(int fp64, size_t smem);
+
+// ---- adaptation (of_adapt.cu)
+struct AdaptBufs {
+    const ofk::PairDesc* pairs;
+    const void* f1;
+    const void* f2;
+    void* alpha;
+    const double* u;     // solution planes (FP64)
+    void* eta;           // per element [H][pitch][2] (storage precision)
+    double* partial;     // per block maxima
+    double* etamax;      // [batch]
+    unsigned* cnt;
+    double lam;
+    int fp64;
+};
+cudaError_t launch_indicator(const AdaptBufs& A, int pair, int H, int W, cudaStream_t st);
+cudaError_t launch_alpha_update(const AdaptBufs& A, int pair, int H, int W, double kappa, double eta_thr,
+                                double alpha_th, cudaStream_t st);
+// adjoint gradients for one pair: u = solution, lam = adjoint state (FP64 planes)
+cudaError_t launch_adjoint_grad(const AdaptBufs& A, int pair, int H, int W, const double* lamv, void* dalpha,
+                                void* df2, void* df1, int out_type, cudaStream_t st);
+
+}  // namespace ofl

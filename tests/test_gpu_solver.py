@@ -1,0 +1,431 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs."""
+import numpy as np
+import pytest
+
+from paper_1508_02977_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+sp = pytest.importorskip("scipy.sparse")
+
+EPS32 = np.finfo(np.float32).eps
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1508_02977_gb300 import ofsolve
+    return ofsolve
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def handle(S, sizes, **kw):
+    h = S.of_create(0)
+    S.of_setup_grid(h, sizes, **kw)
+    return h
+
+
+def csr_abs_matvec(sysm, x):
+    A = sp.csr_matrix((np.abs(sysm.val), sysm.col, sysm.rowptr), shape=(sysm.n, sysm.n))
+    return (A @ np.abs(np.asarray(x).ravel())).reshape(3, sysm.H, sysm.W)
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+# ------------------------------------------------------------------ apply --
+
+APPLY_SIZES = [(64, 48), (7, 5), (130, 67), (2, 2), (2, 9), (9, 2), (300, 40)]
+
+
+@pytest.mark.parametrize("W,H", APPLY_SIZES)
+def test_apply_fp64_matches_oracle(S, oracle, W, H):
+    f1, f2 = synth.random_frames(W, H, W * 7 + H)
+    alpha = synth.random_alpha(W, H, W + 3 * H)
+    lam = 0.8
+    sysm = oracle.System.from_frames(f1, f2, alpha, lam)
+    p = np.random.default_rng(W * H).standard_normal((3, H, W))
+    h = handle(S, [(W, H)], precision=S.OF_PREC_FP64, lam=lam)
+    try:
+        S.of_set_frames(h, 0, dev(f1), dev(f2))
+        S.of_set_alpha(h, 0, dev(alpha))
+        q = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+        b = torch.zeros_like(q)
+        S.of_apply(h, 0, dev(p), q, b)
+        q, b = q.cpu().numpy(), b.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    want = sysm.matvec(p)
+    scale = csr_abs_matvec(sysm, p)
+    assert np.all(np.abs(q - want) <= 1e-13 * scale + 1e-300)
+    bw = sysm.b.reshape(3, H, W)
+    assert np.abs(b - bw).max() <= 1e-14 * max(np.abs(bw).max(), 1e-300)
+
+
+@pytest.mark.parametrize("W,H", APPLY_SIZES)
+def test_apply_fp32_matches_oracle(S, oracle, W, H):
+    f1, f2 = synth.random_frames(W, H, W * 5 + H)
+    f1, f2 = f32(f1), f32(f2)
+    alpha = f32(synth.random_alpha(W, H, W + 5 * H))
+    p = f32(np.random.default_rng(W + H).standard_normal((3, H, W)))
+    sysm = oracle.System.from_frames(f1, f2, alpha, 1.0)
+    h = handle(S, [(W, H)], precision=S.OF_PREC_MIXED)
+    try:
+        S.of_set_frames(h, 0, dev(f1, torch.float32), dev(f2, torch.float32))
+        S.of_set_alpha(h, 0, dev(alpha, torch.float32))
+        q = torch.zeros(3, H, W, dtype=torch.float32, device="cuda")
+        S.of_apply(h, 0, dev(p, torch.float32), q)
+        q = q.cpu().numpy().astype(np.float64)
+    finally:
+        S.of_destroy(h)
+    want = sysm.matvec(p)
+    # FP32 evaluation of a sum of O(60) terms: error <= c eps32 (|A| |p|)
+    scale = csr_abs_matvec(sysm, p)
+    assert np.all(np.abs(q - want) <= 64 * EPS32 * scale)
+
+
+# ---------------------------------------------------------- preconditioner --
+
+@pytest.mark.parametrize("ov,sw", [(0, 1), (2, 1), (0, 2), (4, 3)])
+def test_schwarz_preconditioner_symmetric_positive(S, ov, sw):
+    W, H = 75, 53
+    f1, f2 = synth.random_frames(W, H, 3)
+    alpha = synth.random_alpha(W, H, 4)
+    h = handle(S, [(W, H)], tile=(16, 12), overlap=ov, sweeps=sw, precision=S.OF_PREC_FP64)
+    rng = np.random.default_rng(ov * 10 + sw)
+    try:
+        S.of_set_frames(h, 0, dev(f1), dev(f2))
+        S.of_set_alpha(h, 0, dev(alpha))
+        a = rng.standard_normal((3, H, W))
+        b = rng.standard_normal((3, H, W))
+        Ma = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+        Mb = torch.zeros_like(Ma)
+        S.of_precondition(h, 0, dev(a), Ma)
+        S.of_precondition(h, 0, dev(b), Mb)
+        Ma, Mb = Ma.cpu().numpy(), Mb.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    lhs, rhs = np.sum(Ma * b), np.sum(a * Mb)
+    assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + abs(rhs))
+    assert np.sum(Ma * a) > 0 and np.sum(Mb * b) > 0
+
+
+def test_jacobi_preconditioner_is_block_inverse(S, oracle):
+    """Node-block Jacobi: M^{-1} r solves the 3x3 diagonal blocks exactly."""
+    W, H = 19, 11
+    f1, f2 = synth.random_frames(W, H, 12)
+    alpha = synth.random_alpha(W, H, 13)
+    sysm = oracle.System.from_frames(f1, f2, alpha, 1.0)
+    r = np.random.default_rng(1).standard_normal((3, H, W))
+    h = handle(S, [(W, H)], precision=S.OF_PREC_FP64, preconditioner=S.OF_PC_JACOBI)
+    try:
+        S.of_set_frames(h, 0, dev(f1), dev(f2))
+        S.of_set_alpha(h, 0, dev(alpha))
+        z = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+        S.of_precondition(h, 0, dev(r), z)
+        z = z.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    A = sysm.dense().reshape(3, H, W, 3, H, W)
+    for y in range(H):
+        for x in range(W):
+            blk = A[:, y, x, :, y, x]
+            assert np.allclose(blk @ z[:, y, x], r[:, y, x], rtol=1e-12, atol=1e-13)
+
+
+# ------------------------------------------------------------------ solves --
+
+@pytest.mark.parametrize("tile,ov,sw,pc", [((32, 24), 4, 1, 0), ((16, 16), 0, 2, 0), ((32, 32), 0, 1, 1)])
+def test_fp64_solve_blobs_matches_cholesky(S, oracle, tile, ov, sw, pc):
+    """64x48 blobs (FP64): GPU flow equals the banded-Cholesky solution to
+    1e-10 relative."""
+    p = synth.blobs()
+    sysm = oracle.System.from_frames(p.f1, p.f2, p.alpha0, p.lam)
+    Ud = sysm.solve_direct()
+    h = handle(S, [(p.W, p.H)], tile=tile, overlap=ov, sweeps=sw, precision=S.OF_PREC_FP64, preconditioner=pc)
+    try:
+        S.of_set_frames(h, 0, dev(p.f1), dev(p.f2))
+        S.of_set_alpha(h, 0, None, p.alpha0)
+        U = torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda")
+        st, info = S.of_solve(h, [U], rtol=1e-14, max_inner=20000)
+        U = U.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    assert info[0]["rel_residual"] <= 1e-14
+    assert np.linalg.norm(U - Ud) <= 1e-10 * np.linalg.norm(Ud)
+
+
+@pytest.mark.parametrize("W,H", [(2, 2), (2, 50), (50, 2), (33, 17), (129, 35)])
+def test_fp64_solve_edge_shapes(S, oracle, W, H):
+    f1, f2 = synth.random_frames(W, H, W * 3 + H)
+    alpha = synth.random_alpha(W, H, 17)
+    sysm = oracle.System.from_frames(f1, f2, alpha, 1.0)
+    Ud = sysm.solve_direct()
+    h = handle(S, [(W, H)], tile=(16, 8), overlap=2, sweeps=1, precision=S.OF_PREC_FP64)
+    try:
+        S.of_set_frames(h, 0, dev(f1), dev(f2))
+        S.of_set_alpha(h, 0, dev(alpha))
+        U = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+        st, info = S.of_solve(h, [U], rtol=1e-14, max_inner=20000)
+        U = U.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    assert np.linalg.norm(U - Ud) <= 1e-10 * np.linalg.norm(Ud)
+
+
+def test_mixed_solve_texture_640x480(S, oracle):
+    """640x480 texture, FP32 sweeps + FP64 refinement: residual (recomputed by
+    the oracle) <= 1e-6 and flow within 1e-4 px of the oracle's solve."""
+    p = synth.texture()
+    f1, f2 = f32(p.f1), f32(p.f2)
+    h = handle(S, [(p.W, p.H)], tile=(32, 32), overlap=0, sweeps=2, precision=S.OF_PREC_MIXED)
+    try:
+        S.of_set_frames(h, 0, dev(p.f1, torch.float32), dev(p.f2, torch.float32))
+        S.of_set_alpha(h, 0, None, p.alpha0)
+        U = torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda")
+        st, info = S.of_solve(h, [U], rtol=1e-6)
+        U = U.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    rr = oracle.rel_residual_frames(f1, f2, p.alpha0, p.lam, U)
+    assert rr <= 1e-6
+    assert abs(rr - info[0]["rel_residual"]) <= 1e-3 * rr
+    sysm = oracle.System.from_frames(f1, f2, p.alpha0, p.lam)
+    Uo, _, _ = sysm.solve_pcg(tol=1e-12)
+    assert np.abs(U[:2] - Uo[:2]).max() <= 1e-4
+
+
+def test_mixed_solve_layers_full_size(S, oracle):
+    """3840x2160 layered scene, the benchmark's launch configuration: the
+    oracle's FP64 residual of the GPU solution is <= 1e-6."""
+    from bench import WORKLOAD_OPTS
+    p = synth.layers()
+    h = handle(S, [(p.W, p.H)], **WORKLOAD_OPTS)
+    try:
+        S.of_set_frames(h, 0, dev(p.f1, torch.float32), dev(p.f2, torch.float32))
+        S.of_set_alpha(h, 0, None, p.alpha0)
+        U = torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda")
+        st, info = S.of_solve(h, [U], rtol=1e-6)
+        U = U.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    rr = oracle.rel_residual_frames(f32(p.f1), f32(p.f2), p.alpha0, p.lam, U)
+    assert rr <= 1e-6, (rr, info)
+
+
+def test_pure_gain_recovered(S):
+    W, H = 70, 45
+    f1, _ = synth.random_frames(W, H, 99)
+    for prec, tol in ((0, 1e-10), (1, 1e-5)):
+        h = handle(S, [(W, H)], precision=prec, tile=(16, 16), sweeps=1)
+        try:
+            S.of_set_frames(h, 0, dev(f1), dev(1.1 * f1))
+            S.of_set_alpha(h, 0, None, 0.05)
+            U = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+            S.of_solve(h, [U], rtol=1e-12 if prec == 0 else 1e-7)
+            U = U.cpu().numpy()
+        finally:
+            S.of_destroy(h)
+        assert np.abs(U[:2]).max() <= tol
+        assert np.abs(U[2] - 0.1).max() <= tol
+
+
+def test_batch_of_mixed_sizes_equals_single_solves(S):
+    sizes = [(96, 64), (33, 70), (150, 20)]
+    pairs = [synth.texture(W, H, seed=40 + i) for i, (W, H) in enumerate(sizes)]
+    kw = dict(tile=(32, 16), overlap=1, sweeps=1, precision=S.OF_PREC_MIXED)
+    h = handle(S, sizes, **kw)
+    try:
+        Us = []
+        for i, p in enumerate(pairs):
+            S.of_set_frames(h, i, dev(p.f1, torch.float32), dev(p.f2, torch.float32))
+            S.of_set_alpha(h, i, None, 0.05)
+            Us.append(torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda"))
+        st, info = S.of_solve(h, Us)
+        batch = [u.cpu().numpy() for u in Us]
+    finally:
+        S.of_destroy(h)
+    for i, p in enumerate(pairs):
+        h = handle(S, [sizes[i]], **kw)
+        try:
+            S.of_set_frames(h, 0, dev(p.f1, torch.float32), dev(p.f2, torch.float32))
+            S.of_set_alpha(h, 0, None, 0.05)
+            U = torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda")
+            st, inf1 = S.of_solve(h, [U])
+            assert np.array_equal(U.cpu().numpy(), batch[i])
+            assert inf1[0]["inner_iters"] == info[i]["inner_iters"]
+        finally:
+            S.of_destroy(h)
+
+
+def test_host_buffers_round_trip(S, oracle):
+    """Host (numpy) inputs and outputs go through the same path."""
+    W, H = 40, 30
+    f1, f2 = synth.random_frames(W, H, 5)
+    sysm = oracle.System.from_frames(f1, f2, 0.05, 1.0)
+    h = handle(S, [(W, H)], precision=S.OF_PREC_FP64, tile=(16, 16))
+    try:
+        S.of_set_frames(h, 0, f1, f2)
+        S.of_set_alpha(h, 0, None, 0.05)
+        U = np.zeros((3, H, W))
+        S.of_solve(h, [U], rtol=1e-13)
+        a = np.zeros((H - 1, W - 1, 2))
+        S.of_get_alpha(h, 0, a)
+    finally:
+        S.of_destroy(h)
+    assert np.all(a == 0.05)
+    Ud = sysm.solve_direct()
+    assert np.linalg.norm(U - Ud) <= 1e-9 * np.linalg.norm(Ud)
+
+
+def test_status_codes(S):
+    W, H = 20, 16
+    f1, f2 = synth.random_frames(W, H, 1)
+    h = S.of_create(0)
+    try:
+        with pytest.raises(S.OFError) as e:
+            S.of_setup_grid(h, [(W, H)], tile=(30, 32))
+        assert e.value.status == S.OF_ERR_ARG
+        S.of_setup_grid(h, [(W, H)], tile=(16, 16), precision=S.OF_PREC_MIXED)
+        U = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+        with pytest.raises(S.OFError) as e:
+            S.of_solve(h, [U])
+        assert e.value.status == S.OF_ERR_STATE
+        with pytest.raises(S.OFError) as e:
+            S.of_set_alpha(h, 5, None, 0.1)
+        assert e.value.status == S.OF_ERR_ARG
+        S.of_set_frames(h, 0, dev(f1), dev(f2))
+        S.of_set_alpha(h, 0, None, 0.05)
+        st, info = S.of_solve(h, [U], max_outer=1, max_inner=2, raise_on=False)
+        assert st == S.OF_ERR_NOT_CONVERGED and info[0]["status"] == S.OF_ERR_NOT_CONVERGED
+        bad = f1.copy()
+        bad[3, 4] = np.nan
+        S.of_set_frames(h, 0, dev(bad), dev(f2))
+        st, info = S.of_solve(h, [U], raise_on=False)
+        assert st == S.OF_ERR_BREAKDOWN
+        # the handle stays usable after a failed solve
+        S.of_set_frames(h, 0, dev(f1), dev(f2))
+        st, info = S.of_solve(h, [U])
+        assert st == S.OF_OK and info[0]["rel_residual"] <= 1e-6
+    finally:
+        S.of_destroy(h)
+
+
+# ------------------------------------------------------ indicator / alpha --
+
+def test_indicator_and_alpha_update_match_oracle(S, oracle):
+    p = synth.blobs()
+    alpha = synth.random_alpha(p.W, p.H, 77, 0.02, 0.08)
+    h = handle(S, [(p.W, p.H)], precision=S.OF_PREC_FP64, tile=(32, 24))
+    try:
+        S.of_set_frames(h, 0, dev(p.f1), dev(p.f2))
+        S.of_set_alpha(h, 0, dev(alpha))
+        U = torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda")
+        S.of_solve(h, [U], rtol=1e-12)
+        eta = torch.zeros(p.H - 1, p.W - 1, 2, dtype=torch.float64, device="cuda")
+        S.of_adapt_alpha(h, 4.0, 0.25, 1e-3, [eta])
+        a_new = torch.zeros_like(eta)
+        S.of_get_alpha(h, 0, a_new)
+        U, eta, a_new = U.cpu().numpy(), eta.cpu().numpy(), a_new.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    sysm = oracle.System.from_frames(p.f1, p.f2, alpha, p.lam)
+    eta_o = sysm.indicator(U)
+    assert np.abs(eta - eta_o).max() <= 1e-12 * eta_o.max()
+    a_o = oracle.alpha_update(eta_o, alpha, 4.0, 0.25, 1e-3)
+    assert np.abs(a_new - a_o).max() <= 1e-12 * a_o.max()
+    assert (a_new < alpha).any()
+
+
+def test_adaptation_three_passes_texture(S, oracle):
+    """640x480 texture, 3 adaptation passes (solve -> indicator -> alpha):
+    GPU alpha fields against the oracle's own 3 passes."""
+    p = synth.texture()
+    f1, f2 = f32(p.f1), f32(p.f2)
+    kappa, thr, ath = synth.KAPPA, synth.ETA_THR, synth.ALPHA_TH_FRAC * p.alpha0
+    h = handle(S, [(p.W, p.H)], tile=(32, 32), sweeps=2, precision=S.OF_PREC_MIXED)
+    try:
+        S.of_set_frames(h, 0, dev(p.f1, torch.float32), dev(p.f2, torch.float32))
+        S.of_set_alpha(h, 0, None, p.alpha0)
+        U = torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            S.of_solve(h, [U], rtol=1e-8, warm_start=True)
+            S.of_adapt_alpha(h, kappa, thr, ath)
+        a_gpu = torch.zeros(p.H - 1, p.W - 1, 2, dtype=torch.float32, device="cuda")
+        S.of_get_alpha(h, 0, a_gpu)
+        a_gpu = a_gpu.cpu().numpy().astype(np.float64)
+    finally:
+        S.of_destroy(h)
+    a = np.full((p.H - 1, p.W - 1, 2), p.alpha0)
+    Uo = None
+    for _ in range(3):
+        sysm = oracle.System.from_frames(f1, f2, a, p.lam)
+        Uo, _, _ = sysm.solve_pcg(tol=1e-11, x0=Uo)
+        a = oracle.alpha_update(sysm.indicator(Uo), a, kappa, thr, ath)
+    rel = np.abs(a_gpu - a) / a
+    assert np.median(rel) <= 1e-5
+    assert np.mean(rel > 1e-3) <= 1e-3, np.mean(rel > 1e-3)
+    assert (a < p.alpha0).mean() > 0.01
+
+
+# -------------------------------------------------------------- adjoint ----
+
+def test_adjoint_matches_oracle_and_differences(S, oracle):
+    W, H = 24, 20
+    f1, f2 = synth.random_frames(W, H, 201)
+    alpha = synth.random_alpha(W, H, 202)
+    gt = np.random.default_rng(203).uniform(-1, 1, (2, H, W))
+    sysm = oracle.System.from_frames(f1, f2, alpha, 1.0)
+    Uo = sysm.solve_direct()
+    Lo = sysm.solve_with(oracle.mean_epe_grad(Uo, gt))
+    da_o, d2_o, d1_o = oracle.adjoint_grad(f1, f2, alpha, 1.0, Uo, Lo)
+
+    def gpu_grad(f1_, f2_, a_):
+        h = handle(S, [(W, H)], precision=S.OF_PREC_FP64, tile=(16, 16))
+        try:
+            S.of_set_frames(h, 0, dev(f1_), dev(f2_))
+            S.of_set_alpha(h, 0, dev(a_))
+            U = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+            S.of_solve(h, [U], rtol=1e-14, max_inner=20000)
+            Un = U.cpu().numpy()
+            g = dev(oracle.mean_epe_grad(Un, gt))
+            da = torch.zeros(H - 1, W - 1, 2, dtype=torch.float64, device="cuda")
+            d2 = torch.zeros(H, W, dtype=torch.float64, device="cuda")
+            d1 = torch.zeros_like(d2)
+            S.of_adjoint(h, [g], [da], [d2], [d1])
+            return Un, da.cpu().numpy(), d2.cpu().numpy(), d1.cpu().numpy()
+        finally:
+            S.of_destroy(h)
+
+    U, da, d2, d1 = gpu_grad(f1, f2, alpha)
+    for got, want in ((da, da_o), (d2, d2_o), (d1, d1_o)):
+        assert np.abs(got - want).max() <= 1e-8 * np.abs(want).max()
+    h_fd = 1e-4
+    rng = np.random.default_rng(204)
+
+    def loss(f1_, f2_, a_):
+        return oracle.mean_epe(gpu_grad(f1_, f2_, a_)[0], gt)
+
+    for _ in range(3):
+        y, x, t = rng.integers(0, H - 1), rng.integers(0, W - 1), rng.integers(0, 2)
+        ap, am = alpha.copy(), alpha.copy()
+        ap[y, x, t] += h_fd
+        am[y, x, t] -= h_fd
+        fd = (loss(f1, f2, ap) - loss(f1, f2, am)) / (2 * h_fd)
+        assert abs(fd - da[y, x, t]) <= 1e-5 * np.abs(da).max()
+    for _ in range(3):
+        y, x = rng.integers(0, H), rng.integers(0, W)
+        fp, fm = f2.copy(), f2.copy()
+        fp[y, x] += h_fd
+        fm[y, x] -= h_fd
+        fd = (loss(f1, fp, alpha) - loss(f1, fm, alpha)) / (2 * h_fd)
+        assert abs(fd - d2[y, x]) <= 1e-5 * np.abs(d2).max()
