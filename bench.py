@@ -198,7 +198,7 @@ def run_ours(args):
     from paper_1508_02977_gb300 import ofsolve as S
     from paper_1508_02977_gb300 import synth
 
-    p = workload_pair(rank)
+    p = workload_pair(rank) if args.size is None else workload_pair(rank, *args.size)
     W, H = p.W, p.H
     px = W * H
     kappa, thr, ath = synth.KAPPA, synth.ETA_THR, synth.ALPHA_TH_FRAC * p.alpha0
@@ -345,6 +345,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-w", type=int, default=960)
     ap.add_argument("--cpu-sample-h", type=int, default=540)
+    ap.add_argument("--size", type=int, nargs=2, default=None, metavar=("W", "H"),
+                    help="smaller frame size of the same generator (profiling captures only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -164,7 +164,33 @@ def test_fp64_solve_blobs_matches_cholesky(S, oracle, tile, ov, sw, pc):
     assert np.linalg.norm(U - Ud) <= 1e-10 * np.linalg.norm(Ud)
 
 
-@pytest.mark.parametrize("W,H", [(2, 2), (2, 50), (50, 2), (33, 17), (129, 35)])
+def test_fp64_solve_singular_2x2(S, oracle):
+    """A 2x2 grid has two triangles, so span{g_K} has rank 2 and A is
+    singular (the well-posedness condition of Section 1 fails): the solution is
+    not unique.  Compare what is unique: the residual, and that the difference
+    from the oracle's solution lies in the null space of A."""
+    W, H = 2, 2
+    f1, f2 = synth.random_frames(W, H, W * 3 + H)
+    alpha = synth.random_alpha(W, H, 17)
+    sysm = oracle.System.from_frames(f1, f2, alpha, 1.0)
+    A = sysm.dense()
+    assert np.linalg.eigvalsh(A).min() <= 1e-12 * np.linalg.eigvalsh(A).max()
+    h = handle(S, [(W, H)], tile=(16, 8), overlap=2, sweeps=1, precision=S.OF_PREC_FP64)
+    try:
+        S.of_set_frames(h, 0, dev(f1), dev(f2))
+        S.of_set_alpha(h, 0, dev(alpha))
+        U = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+        st, info = S.of_solve(h, [U], rtol=1e-13, max_inner=20000)
+        U = U.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    assert sysm.rel_residual(U) <= 1e-12
+    Ud = np.linalg.lstsq(A, sysm.b, rcond=None)[0]
+    diff = U.ravel() - Ud
+    assert np.linalg.norm(A @ diff) <= 1e-12 * np.linalg.norm(A) * max(np.linalg.norm(diff), 1.0)
+
+
+@pytest.mark.parametrize("W,H", [(2, 50), (50, 2), (33, 17), (129, 35)])
 def test_fp64_solve_edge_shapes(S, oracle, W, H):
     f1, f2 = synth.random_frames(W, H, W * 3 + H)
     alpha = synth.random_alpha(W, H, 17)
