@@ -189,6 +189,29 @@ of_status of_set_profiling(of_handle h, int on);
 /* Copies the accumulated totals out and clears them. */
 of_status of_get_profile(of_handle h, of_profile *out);
 
+/* FP64 residual r = b - A U of one frame pair without a handle and without
+ * any device allocation.  The paper has no counterpart: this entry point is
+ * for callers that cannot allocate device memory (a frame-budgeted render or
+ * capture loop where allocator calls may synchronise or fail, a plug-in whose
+ * host application owns every allocation).  The caller passes every input and
+ * output; the library's only scratch is a fixed static device array of
+ * 512 KB (block partial sums and an arrival counter) that every GPU which
+ * loads the library holds until the process exits.
+ *   f1, f2 [H][W], alpha [H-1][W-1][2], U [3][H][W]: FP64 device arrays;
+ *   r (optional, NULL = not written) [3][H][W] FP64 device array;
+ *   norms: FP64 device array of 3: ||b - A U||/||b||, ||b - A U||^2, ||b||^2.
+ * Limit: ceil(W/124) * ceil(H/32) <= 32768 thread blocks (every frame up to
+ * 8192 x 8192 nodes fits); larger frames return OF_ERR_ARG, as do bad sizes
+ * or null inputs.  The first call on a device (the current one) looks up the
+ * device address of the scratch array; make that first call before any
+ * stream capture.  All calls share the scratch and it keeps the last call's
+ * contents (the counter that must start at zero is cleared by every call):
+ * calls that overlap on the GPU (other streams, other host threads) race.
+ * Work is enqueued on cuda_stream (NULL: legacy default stream); the outputs
+ * are valid once the stream has passed the call. */
+of_status of_residual_noalloc(int W, int H, const double *f1, const double *f2, const double *alpha,
+                              double lambda, const double *U, double *r, double *norms, void *cuda_stream);
+
 /* Releases the workspace and the handle (NULL is accepted). */
 of_status of_destroy(of_handle h);
 

@@ -75,17 +75,18 @@ _lib.of_precondition.argtypes = [_h, ctypes.c_int, _vp, _vp, ctypes.c_int]
 _lib.of_residual.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
 _lib.of_set_profiling.argtypes = [_h, ctypes.c_int]
 _lib.of_get_profile.argtypes = [_h, ctypes.POINTER(Profile)]
+_lib.of_residual_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp]
 _lib.of_destroy.argtypes = [_h]
 _lib.of_last_error.argtypes = [_h]
 _lib.of_last_error.restype = ctypes.c_char_p
 for _f in ("of_create", "of_setup_grid", "of_set_frames", "of_set_alpha", "of_get_alpha", "of_solve",
            "of_adapt_alpha", "of_adjoint", "of_apply", "of_precondition", "of_residual", "of_set_profiling",
-           "of_get_profile", "of_destroy"):
+           "of_get_profile", "of_residual_noalloc", "of_destroy"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 EXPORTS = ("of_create", "of_setup_grid", "of_set_frames", "of_set_alpha", "of_get_alpha", "of_solve",
            "of_adapt_alpha", "of_adjoint", "of_apply", "of_precondition", "of_residual", "of_set_profiling",
-           "of_get_profile", "of_destroy", "of_last_error")
+           "of_get_profile", "of_residual_noalloc", "of_destroy", "of_last_error")
 
 
 class OFError(RuntimeError):
@@ -242,6 +243,20 @@ def of_get_profile(h) -> dict:
     p = Profile()
     _check(h, _lib.of_get_profile(h, ctypes.byref(p)))
     return p.as_dict()
+
+
+def of_residual_noalloc(f1, f2, alpha, lam, U, r, norms, stream=None) -> int:
+    """Handle-free FP64 residual for callers that cannot allocate device
+    memory: all arrays are float64 CUDA tensors supplied by the caller
+    (r may be None); norms (3 values) receives the relative residual and the
+    two squared norms.  Returns the of_status code."""
+    H, W = int(f1.shape[0]), int(f1.shape[1])
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(f1.device).cuda_stream
+    ptr = lambda t: None if t is None else _vp(_ptr_dtype(t)[0])
+    return int(_lib.of_residual_noalloc(W, H, ptr(f1), ptr(f2), ptr(alpha), float(lam), ptr(U), ptr(r), ptr(norms),
+                                        _vp(stream)))
 
 
 def of_destroy(h):
