@@ -41,6 +41,8 @@ struct of_ctx {
     PairDesc* pd_dev = nullptr;
     int4 *blocks_dev = nullptr, *tiles_dev = nullptr;
     CUtensorMap* tmaps_dev = nullptr;
+    uint32_t* ntab_dev = nullptr;
+    int sch_threads = 0, sch_npt = 1;
     PairScalars* sc_dev = nullptr;
     PairScalars* sc_host = nullptr;  // pinned
     double *partA = nullptr, *partS = nullptr, *etamax = nullptr;
@@ -194,6 +196,9 @@ ofl::SolveBufs solve_bufs(of_ctx* h) {
     B.blocks = h->blocks_dev;
     B.tiles = h->tiles_dev;
     B.tmaps = h->tmaps_dev;
+    B.ntab = h->ntab_dev;
+    B.sch_threads = h->sch_threads;
+    B.sch_npt = h->sch_npt;
     B.sc = h->sc_dev;
     B.partA = h->partA;
     B.partS = h->partS;
@@ -469,6 +474,10 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
             return fail(h, OF_ERR_ARG, "every frame must be at least 2x2 and at most 2^20 per side");
     const int fp64 = opt.precision == OF_PREC_FP64;
     const size_t smem = ofl::schwarz_smem_bytes(fp64, opt.tile_x, opt.tile_y, opt.overlap);
+    std::vector<uint32_t> ntab;
+    int sch_threads = 0, sch_npt = 1;
+    if (!ofl::schwarz_node_table(fp64, opt.tile_x, opt.tile_y, opt.overlap, ntab, sch_threads, sch_npt))
+        return fail(h, OF_ERR_ARG, "extended tile too large for one CTA (more than 2 nodes per thread and colour)");
     int smax = 0;
     CK(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     if (smem > (size_t)smax) return fail(h, OF_ERR_ARG, "tile/overlap need more shared memory than one CTA has");
@@ -562,7 +571,11 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     CK(cudaMemsetAsync(h->err_dev, 0, sizeof(int), st));
     of_status s = encode_maps(h);
     if (s != OF_OK) return s;
-    CK(ofl::schwarz_configure(fp64, smem));
+    CK(dalloc(h, &h->ntab_dev, ntab.size() * sizeof(uint32_t)));
+    CK(cudaMemcpyAsync(h->ntab_dev, ntab.data(), ntab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    h->sch_threads = sch_threads;
+    h->sch_npt = sch_npt;
+    CK(ofl::schwarz_configure(fp64, sch_npt, smem));
     h->frames_set.assign(batch, 0);
     h->alpha_set.assign(batch, 0);
     h->solved = false;

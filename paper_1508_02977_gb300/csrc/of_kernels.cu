@@ -8,7 +8,6 @@ namespace ofl {
 using namespace ofk;
 
 static constexpr int APPLY_NW = 4;    // warps per apply block (124 output columns)
-static constexpr int SCHWARZ_NT = 256;
 
 // ------------------------------------------------------------ copy2d --
 template <typename S, typename D>
@@ -109,6 +108,7 @@ static SchwarzParams schwarz_params(const SolveBufs& B) {
     S.pairs = B.pairs;
     S.tiles = B.tiles;
     S.tmaps = B.tmaps;
+    S.ntab = B.ntab;
     S.sc = B.sc;
     S.partial = B.partS;
     S.counter = B.cntS;
@@ -128,16 +128,56 @@ size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov) {
     return fp64 ? sch_smem_bytes<double>(Tx, Ty, ov) : sch_smem_bytes<float>(Tx, Ty, ov);
 }
 
-cudaError_t schwarz_configure(int fp64, size_t smem) {
-    if (fp64)
-        return cudaFuncSetAttribute(k_schwarz<double, SCHWARZ_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaFuncSetAttribute(k_schwarz<float, SCHWARZ_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t schwarz_configure(int fp64, int npt, size_t smem) {
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (fp64) return npt == 1 ? cudaFuncSetAttribute(k_schwarz<double, 1>, attr, (int)smem)
+                              : cudaFuncSetAttribute(k_schwarz<double, 2>, attr, (int)smem);
+    return npt == 1 ? cudaFuncSetAttribute(k_schwarz<float, 1>, attr, (int)smem)
+                    : cudaFuncSetAttribute(k_schwarz<float, 2>, attr, (int)smem);
+}
+
+bool schwarz_node_table(int fp64, int Tx, int Ty, int ov, std::vector<uint32_t>& tab, int& threads, int& npt) {
+    const int Ex = Tx + 2 * ov, Ey = Ty + 2 * ov, RW = sch_rw(Tx, ov);
+    const int nbank = fp64 ? 16 : 32;  // 8-byte words: 16 banks of pairs
+    std::vector<std::vector<uint32_t>> slots[3];  // [colour][slot] -> up to 32 nodes, distinct banks
+    int maxslots = 0;
+    for (int c = 0; c < 3; ++c) {
+        std::vector<std::vector<uint32_t>> bucket(nbank);
+        for (int j = 0; j < Ey; ++j)
+            for (int i = 0; i < Ex; ++i)
+                if ((i + j) % 3 == c) bucket[((j + 1) * RW + (i + 1)) % nbank].push_back((uint32_t)i | ((uint32_t)j << 16));
+        size_t ns = 0;
+        for (auto& b : bucket) ns = std::max(ns, b.size());
+        // with 16 banks of 8-byte words, a warp takes two nodes per bank pair (two wavefronts anyway)
+        const int per = 32 / nbank;
+        slots[c].assign((ns + per - 1) / per, std::vector<uint32_t>(32, 0xffffffffu));
+        for (int b = 0; b < nbank; ++b)
+            for (size_t k = 0; k < bucket[b].size(); ++k) slots[c][k / per][b + nbank * (k % per)] = bucket[b][k];
+        maxslots = std::max(maxslots, (int)slots[c].size());
+    }
+    const int nwarps = std::min(sch_max_threads(fp64 != 0) / 32, maxslots);
+    npt = (maxslots + nwarps - 1) / nwarps;
+    if (npt > 2) return false;
+    threads = 32 * nwarps;
+    tab.assign((size_t)3 * npt * threads, 0xffffffffu);
+    for (int c = 0; c < 3; ++c)
+        for (size_t s = 0; s < slots[c].size(); ++s) {
+            const int k = (int)s / nwarps, w = (int)s % nwarps;
+            for (int l = 0; l < 32; ++l) tab[((size_t)c * npt + k) * threads + w * 32 + l] = slots[c][s][l];
+        }
+    return true;
 }
 
 static cudaError_t schwarz_launch(const SolveBufs& B, const SchwarzParams& S, int ntiles, cudaStream_t st) {
     const size_t smem = schwarz_smem_bytes(B.fp64, B.Tx, B.Ty, B.ov);
-    if (B.fp64) k_schwarz<double, SCHWARZ_NT><<<ntiles, SCHWARZ_NT, smem, st>>>(S);
-    else k_schwarz<float, SCHWARZ_NT><<<ntiles, SCHWARZ_NT, smem, st>>>(S);
+    const int nt = B.sch_threads;
+    if (B.fp64) {
+        if (B.sch_npt == 1) k_schwarz<double, 1><<<ntiles, nt, smem, st>>>(S);
+        else k_schwarz<double, 2><<<ntiles, nt, smem, st>>>(S);
+    } else {
+        if (B.sch_npt == 1) k_schwarz<float, 1><<<ntiles, nt, smem, st>>>(S);
+        else k_schwarz<float, 2><<<ntiles, nt, smem, st>>>(S);
+    }
     return cudaGetLastError();
 }
 

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "of_common.cuh"
 
 namespace ofl {
@@ -23,6 +25,8 @@ struct SolveBufs {
     const int4* blocks;
     const int4* tiles;
     const CUtensorMap* tmaps;
+    const uint32_t* ntab;  // Schwarz thread -> node table (see schwarz_node_table)
+    int sch_threads, sch_npt;
     ofk::PairScalars* sc;
     double* partA;
     double* partS;
@@ -63,7 +67,11 @@ cudaError_t launch_apply(const SolveBufs& B, int pair, int blk0, int nblk, const
 // r must already be in B.r.
 cudaError_t launch_precond_only(const SolveBufs& B, int tile0, int ntiles, cudaStream_t st);
 size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov);
-cudaError_t schwarz_configure(int fp64, size_t smem);
+cudaError_t schwarz_configure(int fp64, int npt, size_t smem);
+// Host-built assignment of the extended tile's nodes to (colour, slot,
+// thread) such that the 32 lanes of a warp touch 32 distinct shared-memory
+// banks.  Returns false if a tile needs more than 2 slots per thread.
+bool schwarz_node_table(int fp64, int Tx, int Ty, int ov, std::vector<uint32_t>& tab, int& threads, int& npt);
 
 // ---- adaptation (of_adapt.cu)
 struct AdaptBufs {

@@ -17,13 +17,29 @@
 // which is symmetric positive definite (block diagonal over owned tiles of
 // SPD blocks).  With sweeps = 0 and overlap 0 it is node-block Jacobi.
 //
-// Staging: the coefficient window (frames over the extended tile plus a
-// one-node halo, alpha of every square touching it) and the owned tiles of r
-// and q arrive by TMA (cp.async.bulk.tensor) on one mbarrier with a bounded
-// wait.  The update r <- r - a q, the norms r.r and r.z (FP64 partials,
-// deterministic last-CTA reduction per pair) are fused in.
+// Work of one CTA:
+//  1. TMA (cp.async.bulk.tensor) stages the coefficient window -- frames
+//     over the extended tile plus a one-node halo, alpha of every square
+//     touching it -- and the owned tiles of r and q, on one mbarrier with a
+//     bounded wait.
+//  2. Per square of the window: h = g / sqrt(24) of both triangles and the
+//     alpha-weights of the two edges leaving its lower-left node, packed in
+//     shared memory (FP16 pairs for the FP32 path; the preconditioner only
+//     has to be a fixed SPD operator, and the diagonal blocks below are
+//     formed from the same rounded values, so the sweeps are exact block
+//     Gauss-Seidel on the rounded local operator).
+//  3. Each thread owns, per colour, the nodes of a host-built table that
+//     gives every warp 32 distinct shared-memory banks; it keeps their
+//     LDL^T-factored 3x3 diagonal blocks and right-hand sides in registers
+//     (r <- r - a q fused here).
+//  4. Sweeps: one block update per owned node and colour step,
+//     z_n = D_n^{-1} (r_n - sum_K h_K (h_K . (z_j + z_k)) + sum_e w_e z_e).
+//  5. Coalesced write-out of z and r on the owned tile, FP64 partials of
+//     r.r and r.z, deterministic last-CTA reduction per pair.
 #pragma once
 #include <cuda.h>
+#include <cuda_fp16.h>
+
 #include "of_common.cuh"
 
 namespace ofk {
@@ -34,6 +50,7 @@ struct SchwarzParams {
     const PairDesc* pairs;
     const int4* tiles;        // per work item: (pair, tile x, tile y, global tile index)
     const CUtensorMap* tmaps; // [batch][TM_PER_PAIR], 64-byte aligned
+    const uint32_t* ntab;     // [3][npt][blockDim] node of each (colour, slot, thread): i | j << 16, or ~0
     PairScalars* sc;
     double* partial;          // [ntiles][2]
     unsigned* counter;        // [batch]
@@ -50,19 +67,44 @@ struct SchwarzParams {
 __host__ __device__ inline int sch_padl(int ov) { return ((ov + 1) + 3) & ~3; }
 __host__ __device__ inline int sch_bw(int Tx, int ov) { return (sch_padl(ov) + Tx + ov + 1 + 3) & ~3; }
 __host__ __device__ inline int sch_bh(int Ty, int ov) { return Ty + 2 * ov + 2; }
+// cell grid: the extended tile plus a one-node ring, row pitch RW
+__host__ __device__ inline int sch_rw(int Tx, int ov) { return Tx + 2 * ov + 2; }
+__host__ __device__ inline int sch_rh(int Ty, int ov) { return Ty + 2 * ov + 2; }
+
+// Per-cell element data: FP32 path packs 4 planes of half2
+// (h0x,h0y) (h0m,wE) (h1x,h1y) (h1m,wN); FP64 path 8 planes of double.
+template <typename R> struct CellBytes;
+template <> struct CellBytes<float> { static constexpr int value = 16; };
+template <> struct CellBytes<double> { static constexpr int value = 64; };
+
+struct SchLayout {
+    size_t bar, f1, f2, al, rs, qs, cells, zs, total;
+};
+
+template <typename R>
+__host__ __device__ inline SchLayout sch_layout(int Tx, int Ty, int ov) {
+    auto al = [](size_t b) { return (b + 127) & ~(size_t)127; };
+    const int BW = sch_bw(Tx, ov), BH = sch_bh(Ty, ov);
+    const size_t nc = (size_t)sch_rw(Tx, ov) * sch_rh(Ty, ov);
+    SchLayout L;
+    L.bar = 0;
+    L.f1 = 128;
+    L.f2 = L.f1 + al((size_t)BW * BH * sizeof(R));
+    L.al = L.f2 + al((size_t)BW * BH * sizeof(R));
+    size_t stage_end = L.al + al(2 * (size_t)BW * BH * sizeof(R));
+    L.zs = L.f1;  // z planes reuse the coefficient staging once the cells are built
+    const size_t z_end = L.zs + al(3 * nc * sizeof(R));
+    if (z_end > stage_end) stage_end = z_end;
+    L.rs = stage_end;
+    L.qs = L.rs + al(3 * (size_t)Tx * Ty * sizeof(R));
+    L.cells = L.qs + al(3 * (size_t)Tx * Ty * sizeof(R));
+    L.total = L.cells + al(nc * CellBytes<R>::value) + 128;  // + alignment slack
+    return L;
+}
 
 template <typename R>
 __host__ __device__ inline size_t sch_smem_bytes(int Tx, int Ty, int ov) {
-    const int BW = sch_bw(Tx, ov), BH = sch_bh(Ty, ov);
-    const size_t zw = (size_t)(Tx + 2 * ov + 2), zh = (size_t)(Ty + 2 * ov + 2);
-    auto al = [](size_t b) { return (b + 127) & ~(size_t)127; };
-    size_t s = 256;                                   // alignment slack + mbarrier
-    s += al(3 * (size_t)Tx * Ty * sizeof(R));         // R
-    s += al(3 * (size_t)Tx * Ty * sizeof(R));         // Q
-    s += al(3 * zw * zh * sizeof(R));                 // Z (zero ring)
-    s += 2 * al((size_t)BW * BH * sizeof(R));         // F1, F2
-    s += al(2 * (size_t)BW * BH * sizeof(R));         // AL
-    return s;
+    return sch_layout<R>(Tx, Ty, ov).total;
 }
 
 // ---------------------------------------------------------------- PTX --
@@ -113,96 +155,170 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, long long limit
 
 template <typename R> __device__ __forceinline__ R rcp(R x) { return R(1) / x; }
 
-// One block Gauss-Seidel update of node (gx, gy): solve the node's 3x3 block
-// of the local operator for the new z, with the neighbours' current z.
+// ------------------------------------------------------------ cell data --
+template <typename R> struct Cells;
+
+template <> struct Cells<float> {
+    __half2* p0;
+    __half2* p1;
+    __half2* p2;
+    __half2* p3;
+    __device__ void init(unsigned char* base, int nc) {
+        p0 = reinterpret_cast<__half2*>(base);
+        p1 = p0 + nc;
+        p2 = p1 + nc;
+        p3 = p2 + nc;
+    }
+    __device__ void store(int c, const float h0[3], float wE, const float h1[3], float wN) {
+        p0[c] = __floats2half2_rn(h0[0], h0[1]);
+        p1[c] = __floats2half2_rn(h0[2], wE);
+        p2[c] = __floats2half2_rn(h1[0], h1[1]);
+        p3[c] = __floats2half2_rn(h1[2], wN);
+    }
+    // triangle t=0 of cell c, with the E-edge weight of the cell's node
+    __device__ __forceinline__ void t0(int c, float h[3], float& w) const {
+        const float2 a = __half22float2(p0[c]), b = __half22float2(p1[c]);
+        h[0] = a.x; h[1] = a.y; h[2] = b.x; w = b.y;
+    }
+    // triangle t=1 of cell c, with the N-edge weight of the cell's node
+    __device__ __forceinline__ void t1(int c, float h[3], float& w) const {
+        const float2 a = __half22float2(p2[c]), b = __half22float2(p3[c]);
+        h[0] = a.x; h[1] = a.y; h[2] = b.x; w = b.y;
+    }
+};
+
+template <> struct Cells<double> {
+    double* p;
+    int nc;
+    __device__ void init(unsigned char* base, int nc_) {
+        p = reinterpret_cast<double*>(base);
+        nc = nc_;
+    }
+    __device__ void store(int c, const double h0[3], double wE, const double h1[3], double wN) {
+        p[c] = h0[0]; p[c + nc] = h0[1]; p[c + 2 * nc] = h0[2]; p[c + 3 * nc] = wE;
+        p[c + 4 * nc] = h1[0]; p[c + 5 * nc] = h1[1]; p[c + 6 * nc] = h1[2]; p[c + 7 * nc] = wN;
+    }
+    __device__ __forceinline__ void t0(int c, double h[3], double& w) const {
+        h[0] = p[c]; h[1] = p[c + nc]; h[2] = p[c + 2 * nc]; w = p[c + 3 * nc];
+    }
+    __device__ __forceinline__ void t1(int c, double h[3], double& w) const {
+        h[0] = p[c + 4 * nc]; h[1] = p[c + 5 * nc]; h[2] = p[c + 6 * nc]; w = p[c + 7 * nc];
+    }
+};
+
+// LDL^T factors of a node's 3x3 diagonal block: 1/d0, l10, l20, 1/d1, l21, 1/d2
+template <typename R> struct Blk { R i0, l10, l20, i1, l21, i2; };
+
 template <typename R>
-__device__ __forceinline__ void node_update(int gx, int gy, int W, int H, const R* F1, const R* F2, const R* AL,
-                                            int ci, int BW, R* Z, int zi, int ZW, int zplane, R r0, R r1, R r2,
-                                            R lam) {
-    const R third = R(1) / R(3), w24 = R(1) / R(24), w12 = R(1) / R(12), h = R(OF_STIFF_HALF);
-    // frames at n, E, W, N, S, NE, SW
-    const R f2n = F2[ci], f2E = F2[ci + 1], f2W = F2[ci - 1], f2N = F2[ci + BW], f2S = F2[ci - BW];
-    const R f2NE = F2[ci + BW + 1], f2SW = F2[ci - BW - 1];
-    const R f1n = F1[ci], f1E = F1[ci + 1], f1W = F1[ci - 1], f1N = F1[ci + BW], f1S = F1[ci - BW];
-    const R f1NE = F1[ci + BW + 1], f1SW = F1[ci - BW - 1];
-    // squares (x,y), (x-1,y-1), (x-1,y), (x,y-1)
-    const bool vc = (gx < W - 1) && (gy < H - 1);
-    const bool vsw = (gx >= 1) && (gy >= 1);
-    const bool vw = (gx >= 1) && (gy < H - 1);
-    const bool vs = (gx < W - 1) && (gy >= 1);
-    const R a1 = vc ? AL[2 * ci] : R(0), a2 = vc ? AL[2 * ci + 1] : R(0);
-    const R a3 = vsw ? AL[2 * (ci - BW - 1)] : R(0), a4 = vsw ? AL[2 * (ci - BW - 1) + 1] : R(0);
-    const R a5 = vw ? AL[2 * (ci - 1)] : R(0);
-    const R a6 = vs ? AL[2 * (ci - BW) + 1] : R(0);
-    // neighbours' z
+__device__ __forceinline__ Blk<R> ldl3(R D00, R D01, R D02, R D11, R D12, R D22) {
+    Blk<R> b;
+    b.i0 = rcp(D00);
+    b.l10 = D01 * b.i0;
+    b.l20 = D02 * b.i0;
+    const R d1 = D11 - b.l10 * D01;
+    b.i1 = rcp(d1);
+    b.l21 = (D12 - b.l20 * D01) * b.i1;
+    const R d2 = D22 - b.l20 * D02 - b.l21 * b.l21 * d1;
+    b.i2 = rcp(d2);
+    return b;
+}
+
+// The six elements around node n = cell c (x, y):
+//   E1 t0 of (x,y)      others E, NE        E4 t1 of (x-1,y-1) others SW, W
+//   E2 t1 of (x,y)      others N, NE        E5 t0 of (x-1,y)   others W, N
+//   E3 t0 of (x-1,y-1)  others SW, S        E6 t1 of (x,y-1)   others S, E
+// Edge weights: n-E = wE(c), n-N = wN(c), n-W = wE(c-1), n-S = wN(c-RW).
+template <typename R>
+__device__ __forceinline__ void node_block(const Cells<R>& C, int c, int RW, R lE, R lN, R lW, R lS, Blk<R>& B) {
+    R h[6][3], wE, wN, wW, wS, dummy;
+    C.t0(c, h[0], wE);
+    C.t1(c, h[1], wN);
+    C.t0(c - RW - 1, h[2], dummy);
+    C.t1(c - RW - 1, h[3], dummy);
+    C.t0(c - 1, h[4], wW);
+    C.t1(c - RW, h[5], wS);
+    R D00 = 0, D01 = 0, D02 = 0, D11 = 0, D12 = 0, D22 = 0;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        D00 += 2 * h[e][0] * h[e][0]; D01 += 2 * h[e][0] * h[e][1]; D02 += 2 * h[e][0] * h[e][2];
+        D11 += 2 * h[e][1] * h[e][1]; D12 += 2 * h[e][1] * h[e][2]; D22 += 2 * h[e][2] * h[e][2];
+    }
+    const R ws = wE + wN + wW + wS;
+    B = ldl3<R>(D00 + ws, D01, D02, D11 + ws, D12, D22 + (lE + lN + lW + lS));
+}
+
+template <typename R>
+__device__ __forceinline__ void node_sweep(const Cells<R>& C, R* __restrict__ Z, int zplane, int c, int RW, R lE,
+                                           R lN, R lW, R lS, const Blk<R>& B, R b0, R b1, R b2) {
     const R* z0 = Z;
     const R* z1 = Z + zplane;
     const R* z2 = Z + 2 * zplane;
-    const int iE = zi + 1, iW = zi - 1, iN = zi + ZW, iS = zi - ZW, iNE = zi + ZW + 1, iSW = zi - ZW - 1;
+    const int iE = c + 1, iW = c - 1, iN = c + RW, iS = c - RW, iNE = c + RW + 1, iSW = c - RW - 1;
     const R zE0 = z0[iE], zE1 = z1[iE], zE2 = z2[iE];
     const R zW0 = z0[iW], zW1 = z1[iW], zW2 = z2[iW];
     const R zN0 = z0[iN], zN1 = z1[iN], zN2 = z2[iN];
     const R zS0 = z0[iS], zS1 = z1[iS], zS2 = z2[iS];
     const R zNE0 = z0[iNE], zNE1 = z1[iNE], zNE2 = z2[iNE];
     const R zSW0 = z0[iSW], zSW1 = z1[iSW], zSW2 = z2[iSW];
-
-    R b0 = r0, b1 = r1, b2 = r2;
-    R D00 = 0, D01 = 0, D02 = 0, D11 = 0, D12 = 0, D22 = 0;
-    auto elem = [&](bool v, R gx_, R gy_, R gm_, R s0, R s1, R s2) {
-        if (!v) return;
-        const R s = gx_ * s0 + gy_ * s1 + gm_ * s2;
-        const R k = s * w24;
-        b0 -= k * gx_; b1 -= k * gy_; b2 -= k * gm_;
-        D00 += w12 * gx_ * gx_; D01 += w12 * gx_ * gy_; D02 += w12 * gx_ * gm_;
-        D11 += w12 * gy_ * gy_; D12 += w12 * gy_ * gm_; D22 += w12 * gm_ * gm_;
+    R h[3] = {R(0), R(0), R(0)}, wE, wN, wW, wS, dummy;
+    auto elem = [&](R s0, R s1, R s2) {
+        const R s = h[0] * s0 + h[1] * s1 + h[2] * s2;
+        b0 -= s * h[0];
+        b1 -= s * h[1];
+        b2 -= s * h[2];
     };
-    // E1: square (x,y) t=0, others E, NE
-    elem(vc, f2E - f2n, f2NE - f2E, -(f1n + f1E + f1NE) * third, zE0 + zNE0, zE1 + zNE1, zE2 + zNE2);
-    // E2: square (x,y) t=1, others N, NE
-    elem(vc, f2NE - f2N, f2N - f2n, -(f1n + f1N + f1NE) * third, zN0 + zNE0, zN1 + zNE1, zN2 + zNE2);
-    // E3: square (x-1,y-1) t=0, others SW, S
-    elem(vsw, f2S - f2SW, f2n - f2S, -(f1SW + f1S + f1n) * third, zSW0 + zS0, zSW1 + zS1, zSW2 + zS2);
-    // E4: square (x-1,y-1) t=1, others SW, W
-    elem(vsw, f2n - f2W, f2W - f2SW, -(f1SW + f1W + f1n) * third, zSW0 + zW0, zSW1 + zW1, zSW2 + zW2);
-    // E5: square (x-1,y) t=0, others W, N
-    elem(vw, f2n - f2W, f2N - f2n, -(f1W + f1n + f1N) * third, zW0 + zN0, zW1 + zN1, zW2 + zN2);
-    // E6: square (x,y-1) t=1, others S, E
-    elem(vs, f2E - f2n, f2n - f2S, -(f1S + f1n + f1E) * third, zS0 + zE0, zS1 + zE1, zS2 + zE2);
-    // stiffness legs: n-E (E1, E6), n-N (E2, E5), n-W (E4, E5), n-S (E3, E6)
-    const R wE = h * (a1 + a6), wN = h * (a2 + a5), wWe = h * (a4 + a5), wS = h * (a3 + a6);
-    const R lE = h * lam * (R(vc) + R(vs)), lN = h * lam * (R(vc) + R(vw));
-    const R lW = h * lam * (R(vsw) + R(vw)), lS = h * lam * (R(vsw) + R(vs));
-    b0 += wE * zE0 + wN * zN0 + wWe * zW0 + wS * zS0;
-    b1 += wE * zE1 + wN * zN1 + wWe * zW1 + wS * zS1;
+    C.t0(c, h, wE);             elem(zE0 + zNE0, zE1 + zNE1, zE2 + zNE2);  // E1
+    C.t1(c, h, wN);             elem(zN0 + zNE0, zN1 + zNE1, zN2 + zNE2);  // E2
+    C.t0(c - RW - 1, h, dummy); elem(zSW0 + zS0, zSW1 + zS1, zSW2 + zS2);  // E3
+    C.t1(c - RW - 1, h, dummy); elem(zSW0 + zW0, zSW1 + zW1, zSW2 + zW2);  // E4
+    C.t0(c - 1, h, wW);         elem(zW0 + zN0, zW1 + zN1, zW2 + zN2);     // E5
+    C.t1(c - RW, h, wS);        elem(zS0 + zE0, zS1 + zE1, zS2 + zE2);     // E6
+    b0 += wE * zE0 + wN * zN0 + wW * zW0 + wS * zS0;
+    b1 += wE * zE1 + wN * zN1 + wW * zW1 + wS * zS1;
     b2 += lE * zE2 + lN * zN2 + lW * zW2 + lS * zS2;
-    D00 += wE + wN + wWe + wS;
-    D11 += wE + wN + wWe + wS;
-    D22 += lE + lN + lW + lS;
-    // 3x3 SPD solve by LDL^T
-    const R i0 = rcp(D00);
-    const R l10 = D01 * i0, l20 = D02 * i0;
-    const R d1 = D11 - l10 * D01;
-    const R i1 = rcp(d1);
-    const R l21 = (D12 - l20 * D01) * i1;
-    const R d2 = D22 - l20 * D02 - l21 * l21 * d1;
-    const R i2 = rcp(d2);
-    const R y0 = b0, y1 = b1 - l10 * y0, y2 = b2 - l20 * y0 - l21 * y1;
-    const R x2 = y2 * i2;
-    const R x1 = y1 * i1 - l21 * x2;
-    const R x0 = y0 * i0 - l10 * x1 - l20 * x2;
-    Z[zi] = x0;
-    Z[zi + zplane] = x1;
-    Z[zi + 2 * zplane] = x2;
+    const R y1 = b1 - B.l10 * b0, y2 = b2 - B.l20 * b0 - B.l21 * y1;
+    const R x2 = y2 * B.i2;
+    const R x1 = y1 * B.i1 - B.l21 * x2;
+    const R x0 = b0 * B.i0 - B.l10 * x1 - B.l20 * x2;
+    Z[c] = x0;
+    Z[c + zplane] = x1;
+    Z[c + 2 * zplane] = x2;
 }
 
-template <typename R, int NT>
-__global__ void __launch_bounds__(NT) k_schwarz(const SchwarzParams P) {
+__device__ __forceinline__ double block_sum_rt(double v, double* sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = (l < nw) ? sh[l] : 0.0;
+        s = warp_sum(s);
+    }
+    return s;
+}
+
+__device__ __forceinline__ double ordered_sum_rt(const double* p, int n, int stride, double* sh) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(p + (long long)i * stride);
+    return block_sum_rt(s, sh);
+}
+
+// Largest CTA the host may build a node table for (registers: the owned
+// nodes' blocks and right-hand sides live in registers).
+__host__ __device__ constexpr int sch_max_threads(bool fp64) { return fp64 ? 384 : 384; }
+
+template <typename R, int NPT>
+__global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 8 ? 1 : 2)
+    k_schwarz(const SchwarzParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ double sh_red[NT / 32];
+    __shared__ double sh_red[32];
     __shared__ int sh_last, sh_fail;
     const int4 ti = P.tiles[blockIdx.x];
     const int pair = ti.x;
     if (!P.apply_only && P.sc[pair].done) return;  // uniform over the pair's tiles
+    const int NT = blockDim.x;
     const PairDesc pd = P.pairs[pair];
     const int W = pd.W, H = pd.H, pitch = pd.pitch;
     const long long plane = (long long)H * pitch;
@@ -211,22 +327,26 @@ __global__ void __launch_bounds__(NT) k_schwarz(const SchwarzParams P) {
     const int tw = min(Tx, W - x0), th = min(Ty, H - y0);
     const int BW = sch_bw(Tx, ov), BH = sch_bh(Ty, ov);
     const int xs = x0 - sch_padl(ov), ys = y0 - ov - 1;
-    const int ZW = Tx + 2 * ov + 2, ZH = Ty + 2 * ov + 2;
-    const int zplane = ZW * ZH;
+    const int RW = sch_rw(Tx, ov), RH = sch_rh(Ty, ov);
+    const int nc = RW * RH;
+    const int cx0 = x0 - ov - 1, cy0 = y0 - ov - 1;  // global node of cell (0, 0)
+    const int ex0 = max(x0 - ov, 0), ex1 = min(x0 + tw + ov, W);
+    const int ey0 = max(y0 - ov, 0), ey1 = min(y0 + th + ov, H);
     const bool need_q = !P.first && !P.apply_only;
 
-    auto al = [](size_t b) { return (b + 127) & ~(size_t)127; };
-    // TMA destinations on 128-byte boundaries whatever the base alignment
+    const SchLayout L = sch_layout<R>(Tx, Ty, ov);
     unsigned char* base = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(base);
-    size_t off = 128;
-    R* Rs = reinterpret_cast<R*>(base + off); off += al(3 * (size_t)Tx * Ty * sizeof(R));
-    R* Qs = reinterpret_cast<R*>(base + off); off += al(3 * (size_t)Tx * Ty * sizeof(R));
-    R* Zs = reinterpret_cast<R*>(base + off); off += al(3 * (size_t)zplane * sizeof(R));
-    R* F1s = reinterpret_cast<R*>(base + off); off += al((size_t)BW * BH * sizeof(R));
-    R* F2s = reinterpret_cast<R*>(base + off); off += al((size_t)BW * BH * sizeof(R));
-    R* ALs = reinterpret_cast<R*>(base + off);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + L.bar);
+    R* F1s = reinterpret_cast<R*>(base + L.f1);
+    R* F2s = reinterpret_cast<R*>(base + L.f2);
+    R* ALs = reinterpret_cast<R*>(base + L.al);
+    R* Rs = reinterpret_cast<R*>(base + L.rs);
+    R* Qs = reinterpret_cast<R*>(base + L.qs);
+    R* Zs = reinterpret_cast<R*>(base + L.zs);
+    Cells<R> C;
+    C.init(base + L.cells, nc);
 
+    // ---- 1. staging
     const CUtensorMap* tm = P.tmaps + (size_t)pair * TM_PER_PAIR;
     if (threadIdx.x == 0) {
         sh_fail = 0;
@@ -243,10 +363,6 @@ __global__ void __launch_bounds__(NT) k_schwarz(const SchwarzParams P) {
         tma_load_2d(ALs, tm + TM_AL, 2 * xs, ys, bar);
         tma_load_3d(Rs, tm + TM_R, x0, y0, 0, bar);
         if (need_q) tma_load_3d(Qs, tm + TM_Q, x0, y0, 0, bar);
-    }
-    // zero the local solution (and its ring) while the copies are in flight
-    for (int i = threadIdx.x; i < 3 * zplane; i += NT) Zs[i] = R(0);
-    if (threadIdx.x == 0) {
         if (!mbar_wait_bounded(bar, P.spin_limit)) {
             sh_fail = 1;
             atomicOr(P.err, 1);
@@ -255,90 +371,150 @@ __global__ void __launch_bounds__(NT) k_schwarz(const SchwarzParams P) {
     }
     __syncthreads();
     if (sh_fail) return;
-    // every thread observes the completed phase (visibility of the async copies)
-    if (!mbar_wait_bounded(bar, P.spin_limit)) atomicOr(P.err, 1);
+    if (!mbar_wait_bounded(bar, P.spin_limit)) atomicOr(P.err, 1);  // every thread observes the phase
 
-    // r <- r - a q on the owned tile; write r back; partial r.r
-    const R a = need_q ? (R)P.sc[pair].a : R(0);
-    R* rg = reinterpret_cast<R*>(P.r) + pd.vec_off;
-    R rr = R(0);  // per-thread partials in the working precision, FP64 across threads
-    const int ntile = tw * th;
-    for (int k = threadIdx.x; k < ntile; k += NT) {
-        const int j = k / tw, i = k - j * tw;
-        const int si = j * Tx + i;
-        R v0 = Rs[si], v1 = Rs[si + Tx * Ty], v2 = Rs[si + 2 * Tx * Ty];
-        if (need_q) {
-            v0 = v0 - a * Qs[si];
-            v1 = v1 - a * Qs[si + Tx * Ty];
-            v2 = v2 - a * Qs[si + 2 * Tx * Ty];
-            Rs[si] = v0; Rs[si + Tx * Ty] = v1; Rs[si + 2 * Tx * Ty] = v2;
-            const long long o = (long long)(y0 + j) * pitch + (x0 + i);
-            rg[o] = v0; rg[o + plane] = v1; rg[o + 2 * plane] = v2;
+    // ---- 2. element data per cell (square at the cell's node)
+    const R isq24 = R(0.20412414523193151);  // 1/sqrt(24)
+    const R third = R(1) / R(3), half = R(0.5);
+    for (int c = threadIdx.x; c < nc; c += NT) {
+        const int j = c / RW, i = c - j * RW;
+        const int sx = cx0 + i, sy = cy0 + j;
+        R h0[3] = {0, 0, 0}, h1[3] = {0, 0, 0}, wE = 0, wN = 0;
+        if (i < RW - 1 && j < RH - 1) {
+            const int fx = sx - xs, fy = sy - ys;
+            if (sx >= 0 && sx < W - 1 && sy >= 0 && sy < H - 1) {
+                const int f = fy * BW + fx;
+                const R a2 = F2s[f], b2 = F2s[f + 1], c2 = F2s[f + BW + 1], d2 = F2s[f + BW];
+                const R a1 = F1s[f], b1 = F1s[f + 1], c1 = F1s[f + BW + 1], d1 = F1s[f + BW];
+                h0[0] = (b2 - a2) * isq24;
+                h0[1] = (c2 - b2) * isq24;
+                h0[2] = -(a1 + b1 + c1) * third * isq24;
+                h1[0] = (c2 - d2) * isq24;
+                h1[1] = (d2 - a2) * isq24;
+                h1[2] = -(a1 + d1 + c1) * third * isq24;
+            }
+            // alpha outside the image reads as 0 (TMA fill): missing triangles add nothing
+            const int a = 2 * (fy * BW + fx);
+            if (j >= 1) wE = half * (ALs[a] + ALs[a - 2 * BW + 1]);
+            if (i >= 1) wN = half * (ALs[a + 1] + ALs[a - 2]);
         }
-        rr += v0 * v0 + v1 * v1 + v2 * v2;
+        C.store(c, h0, wE, h1, wN);
     }
     __syncthreads();
 
-    // local solve on the extended tile
-    const int ex0 = max(x0 - ov, 0), ex1 = min(x0 + tw + ov, W);
-    const int ey0 = max(y0 - ov, 0), ey1 = min(y0 + th + ov, H);
-    const int Ew = ex1 - ex0, Eh = ey1 - ey0;
-    const R lam = (R)P.lam;
-    const int ncol = (P.sweeps > 0) ? 1 + 4 * P.sweeps : 1;
-    for (int step = 0; step < ncol; ++step) {
-        int col = -1;  // -1: every node at once (block Jacobi)
-        if (P.sweeps > 0) {
-            const int m = step % 4;  // 0,1,2,1 repeating, then the final 0
-            col = (m == 0) ? 0 : (m == 1 ? 1 : (m == 2 ? 2 : 1));
-        }
-        const int M = (col < 0) ? Ew : (Ew + 2) / 3;
-        const int nwork = M * Eh;
-        for (int k = threadIdx.x; k < nwork; k += NT) {
-            const int j = k / M, m = k - j * M;
-            int i;
-            if (col < 0) i = m;
-            else {
-                const int base = ((col - (ex0 + ey0 + j)) % 3 + 3) % 3;
-                i = base + 3 * m;
-                if (i >= Ew) continue;
-            }
-            const int gx = ex0 + i, gy = ey0 + j;
-            R r0 = R(0), r1 = R(0), r2 = R(0);
+    // ---- 3. owned nodes: diagonal blocks, right-hand sides, r <- r - a q
+    const R a = need_q ? (R)P.sc[pair].a : R(0);
+    const R hl = half * (R)P.lam;
+    // per owned node: cell index (low 24 bits) and the number of existing
+    // triangles on its E, N, W, S legs (2 bits each, high byte)
+    int cell[3][NPT];
+    R rhs[3][NPT][3];
+    Blk<R> blk[3][NPT];
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const uint32_t e = P.ntab[(col * NPT + k) * NT + threadIdx.x];
+            cell[col][k] = -1;
+            rhs[col][k][0] = rhs[col][k][1] = rhs[col][k][2] = R(0);
+            blk[col][k] = Blk<R>{R(0), R(0), R(0), R(0), R(0), R(0)};
+            if (e == 0xffffffffu) continue;
+            const int li = (int)(e & 0xffffu), lj = (int)(e >> 16);
+            const int gx = x0 - ov + li, gy = y0 - ov + lj;
+            if (gx < ex0 || gx >= ex1 || gy < ey0 || gy >= ey1) continue;
+            const int c = (lj + 1) * RW + (li + 1);
+            // existing triangles on the four legs (the lambda weight is 1/2 lambda each)
+            const int vc = (gx < W - 1 && gy < H - 1), vsw = (gx >= 1 && gy >= 1);
+            const int vw = (gx >= 1 && gy < H - 1), vs = (gx < W - 1 && gy >= 1);
+            const int nE = vc + vs, nN = vc + vw, nW = vsw + vw, nS = vsw + vs;
+            cell[col][k] = c | (nE << 24) | (nN << 26) | (nW << 28) | (nS << 30);
+            node_block<R>(C, c, RW, hl * nE, hl * nN, hl * nW, hl * nS, blk[col][k]);
             if (gx >= x0 && gx < x0 + tw && gy >= y0 && gy < y0 + th) {
                 const int si = (gy - y0) * Tx + (gx - x0);
-                r0 = Rs[si]; r1 = Rs[si + Tx * Ty]; r2 = Rs[si + 2 * Tx * Ty];
+                R v0 = Rs[si], v1 = Rs[si + Tx * Ty], v2 = Rs[si + 2 * Tx * Ty];
+                if (need_q) {
+                    v0 -= a * Qs[si];
+                    v1 -= a * Qs[si + Tx * Ty];
+                    v2 -= a * Qs[si + 2 * Tx * Ty];
+                    Rs[si] = v0;
+                    Rs[si + Tx * Ty] = v1;
+                    Rs[si + 2 * Tx * Ty] = v2;
+                }
+                rhs[col][k][0] = v0;
+                rhs[col][k][1] = v1;
+                rhs[col][k][2] = v2;
             }
-            const int ci = (gy - ys) * BW + (gx - xs);
-            const int zi = (gy - (y0 - ov) + 1) * ZW + (gx - (x0 - ov) + 1);
-            node_update<R>(gx, gy, W, H, F1s, F2s, ALs, ci, BW, Zs, zi, ZW, zplane, r0, r1, r2, lam);
+        }
+    }
+    __syncthreads();  // staging reads done before z (which reuses it) is cleared
+    for (int i = threadIdx.x; i < 3 * nc; i += NT) Zs[i] = R(0);
+    __syncthreads();
+
+    // ---- 4. sweeps (colour order 0,1,2,1,0,1,2,1,0,...; sweeps = 0: block Jacobi)
+    const int nsteps = (P.sweeps > 0) ? 1 + 4 * P.sweeps : 1;
+    for (int step = 0; step < nsteps; ++step) {
+        const int m = step & 3;
+        const int col = (m == 0) ? 0 : (m == 2 ? 2 : 1);
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            if (P.sweeps > 0 && cc != col) continue;  // Jacobi: every colour at once
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                if (cell[cc][k] == -1) continue;
+                const int c = cell[cc][k] & 0xffffff;
+                const unsigned nb = (unsigned)cell[cc][k] >> 24;
+                if (P.sweeps == 0) {  // block Jacobi: z = D^{-1} r, no neighbour terms
+                    const Blk<R>& B = blk[cc][k];
+                    const R b0 = rhs[cc][k][0];
+                    const R y1 = rhs[cc][k][1] - B.l10 * b0, y2 = rhs[cc][k][2] - B.l20 * b0 - B.l21 * y1;
+                    const R x2 = y2 * B.i2, x1 = y1 * B.i1 - B.l21 * x2, x0 = b0 * B.i0 - B.l10 * x1 - B.l20 * x2;
+                    Zs[c] = x0;
+                    Zs[c + nc] = x1;
+                    Zs[c + 2 * nc] = x2;
+                    continue;
+                }
+                node_sweep<R>(C, Zs, nc, c, RW, hl * R(nb & 3u), hl * R((nb >> 2) & 3u), hl * R((nb >> 4) & 3u),
+                              hl * R(nb >> 6), blk[cc][k], rhs[cc][k][0], rhs[cc][k][1], rhs[cc][k][2]);
+            }
         }
         __syncthreads();
     }
 
-    // write the owned part of z; partial r.z
+    // ---- 5. write-out of the owned tile (coalesced), partials r.r and r.z
     R* zg = reinterpret_cast<R*>(P.z) + pd.vec_off;
-    R rz = R(0);
+    R* rg = reinterpret_cast<R*>(P.r) + pd.vec_off;
+    R rr = R(0), rz = R(0);
+    const int ntile = tw * th;
     for (int k = threadIdx.x; k < ntile; k += NT) {
         const int j = k / tw, i = k - j * tw;
         const int si = j * Tx + i;
-        const int zi = (y0 + j - (y0 - ov) + 1) * ZW + (x0 + i - (x0 - ov) + 1);
-        const R v0 = Zs[zi], v1 = Zs[zi + zplane], v2 = Zs[zi + 2 * zplane];
+        const int c = (j + ov + 1) * RW + (i + ov + 1);
+        const R v0 = Zs[c], v1 = Zs[c + nc], v2 = Zs[c + 2 * nc];
+        const R r0 = Rs[si], r1 = Rs[si + Tx * Ty], r2 = Rs[si + 2 * Tx * Ty];
         const long long o = (long long)(y0 + j) * pitch + (x0 + i);
-        zg[o] = v0; zg[o + plane] = v1; zg[o + 2 * plane] = v2;
-        rz += Rs[si] * v0 + Rs[si + Tx * Ty] * v1 + Rs[si + 2 * Tx * Ty] * v2;
+        zg[o] = v0;
+        zg[o + plane] = v1;
+        zg[o + 2 * plane] = v2;
+        if (need_q) {
+            rg[o] = r0;
+            rg[o + plane] = r1;
+            rg[o + 2 * plane] = r2;
+        }
+        rr += r0 * r0 + r1 * r1 + r2 * r2;
+        rz += r0 * v0 + r1 * v1 + r2 * v2;
     }
     if (P.apply_only) return;
 
-    const double s_rr = block_sum<NT>((double)rr, sh_red);
-    const double s_rz = block_sum<NT>((double)rz, sh_red);
+    const double s_rr = block_sum_rt((double)rr, sh_red);
+    const double s_rz = block_sum_rt((double)rz, sh_red);
     if (threadIdx.x == 0) {
         P.partial[2 * (long long)ti.w] = s_rr;
         P.partial[2 * (long long)ti.w + 1] = s_rz;
     }
     const int ntiles = pd.tiles_x * pd.tiles_y;
     if (!arrive_last(&P.counter[pair], (unsigned)ntiles, &sh_last)) return;
-    const double t_rr = ordered_sum<NT>(P.partial + 2 * (long long)pd.tile0, ntiles, 2, sh_red);
-    const double t_rz = ordered_sum<NT>(P.partial + 2 * (long long)pd.tile0 + 1, ntiles, 2, sh_red);
+    const double t_rr = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0, ntiles, 2, sh_red);
+    const double t_rz = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0 + 1, ntiles, 2, sh_red);
     if (threadIdx.x == 0) {
         PairScalars* s = P.sc + pair;
         if (P.first) {
