@@ -32,7 +32,7 @@ struct of_ctx {
     std::vector<int4> blocks, tiles;
     std::vector<int> blk0, nblk, tile0, ntile;
     long long frame_elems = 0, vec_elems = 0;
-    int nblk_total = 0, ntiles_total = 0, rows_per_block = 32;
+    int nblk_total = 0, ntiles_total = 0, rows_per_block = 16;
     // device memory
     std::vector<void*> allocs;
     void *f1 = nullptr, *f2 = nullptr, *alpha = nullptr, *eta = nullptr;
@@ -575,7 +575,7 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     CK(cudaMemcpyAsync(h->ntab_dev, ntab.data(), ntab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     h->sch_threads = sch_threads;
     h->sch_npt = sch_npt;
-    CK(ofl::schwarz_configure(fp64, sch_npt, smem));
+    CK(ofl::schwarz_configure(fp64, sch_npt, ofk::sch_rw(opt.tile_x, opt.overlap), smem));
     h->frames_set.assign(batch, 0);
     h->alpha_set.assign(batch, 0);
     h->solved = false;

@@ -128,12 +128,25 @@ size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov) {
     return fp64 ? sch_smem_bytes<double>(Tx, Ty, ov) : sch_smem_bytes<float>(Tx, Ty, ov);
 }
 
-cudaError_t schwarz_configure(int fp64, int npt, size_t smem) {
-    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if (fp64) return npt == 1 ? cudaFuncSetAttribute(k_schwarz<double, 1>, attr, (int)smem)
-                              : cudaFuncSetAttribute(k_schwarz<double, 2>, attr, (int)smem);
-    return npt == 1 ? cudaFuncSetAttribute(k_schwarz<float, 1>, attr, (int)smem)
-                    : cudaFuncSetAttribute(k_schwarz<float, 2>, attr, (int)smem);
+// Shapes with a compile-time row pitch (tile_x + 2 overlap + 2): 32-wide tiles
+// with overlap 0 (34) or 2 (38); other shapes use the runtime pitch.
+template <typename R, int NPT, typename F>
+static cudaError_t with_schwarz(int rw, F f) {
+    if (rw == 34) return f(k_schwarz<R, NPT, 34>);
+    if (rw == 38) return f(k_schwarz<R, NPT, 38>);
+    return f(k_schwarz<R, NPT, 0>);
+}
+
+template <typename F>
+static cudaError_t with_schwarz_all(int fp64, int npt, int rw, F f) {
+    if (fp64) return npt == 1 ? with_schwarz<double, 1>(rw, f) : with_schwarz<double, 2>(rw, f);
+    return npt == 1 ? with_schwarz<float, 1>(rw, f) : with_schwarz<float, 2>(rw, f);
+}
+
+cudaError_t schwarz_configure(int fp64, int npt, int rw, size_t smem) {
+    return with_schwarz_all(fp64, npt, rw, [&](auto kern) {
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
 }
 
 bool schwarz_node_table(int fp64, int Tx, int Ty, int ov, std::vector<uint32_t>& tab, int& threads, int& npt) {
@@ -171,14 +184,10 @@ bool schwarz_node_table(int fp64, int Tx, int Ty, int ov, std::vector<uint32_t>&
 static cudaError_t schwarz_launch(const SolveBufs& B, const SchwarzParams& S, int ntiles, cudaStream_t st) {
     const size_t smem = schwarz_smem_bytes(B.fp64, B.Tx, B.Ty, B.ov);
     const int nt = B.sch_threads;
-    if (B.fp64) {
-        if (B.sch_npt == 1) k_schwarz<double, 1><<<ntiles, nt, smem, st>>>(S);
-        else k_schwarz<double, 2><<<ntiles, nt, smem, st>>>(S);
-    } else {
-        if (B.sch_npt == 1) k_schwarz<float, 1><<<ntiles, nt, smem, st>>>(S);
-        else k_schwarz<float, 2><<<ntiles, nt, smem, st>>>(S);
-    }
-    return cudaGetLastError();
+    return with_schwarz_all(B.fp64, B.sch_npt, sch_rw(B.Tx, B.ov), [&](auto kern) {
+        kern<<<ntiles, nt, smem, st>>>(S);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_precond_first(const SolveBufs& B, cudaStream_t st) {

@@ -67,7 +67,7 @@ cudaError_t launch_apply(const SolveBufs& B, int pair, int blk0, int nblk, const
 // r must already be in B.r.
 cudaError_t launch_precond_only(const SolveBufs& B, int tile0, int ntiles, cudaStream_t st);
 size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov);
-cudaError_t schwarz_configure(int fp64, int npt, size_t smem);
+cudaError_t schwarz_configure(int fp64, int npt, int rw, size_t smem);
 // Host-built assignment of the extended tile's nodes to (colour, slot,
 // thread) such that the 32 lanes of a warp touch 32 distinct shared-memory
 // banks.  Returns false if a tile needs more than 2 slots per thread.

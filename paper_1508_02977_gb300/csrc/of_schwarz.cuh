@@ -23,11 +23,8 @@
 //     touching it -- and the owned tiles of r and q, on one mbarrier with a
 //     bounded wait.
 //  2. Per square of the window: h = g / sqrt(24) of both triangles and the
-//     alpha-weights of the two edges leaving its lower-left node, packed in
-//     shared memory (FP16 pairs for the FP32 path; the preconditioner only
-//     has to be a fixed SPD operator, and the diagonal blocks below are
-//     formed from the same rounded values, so the sweeps are exact block
-//     Gauss-Seidel on the rounded local operator).
+//     alpha-weights of the two edges leaving its lower-left node, in shared
+//     memory planes.
 //  3. Each thread owns, per colour, the nodes of a host-built table that
 //     gives every warp 32 distinct shared-memory banks; it keeps their
 //     LDL^T-factored 3x3 diagonal blocks and right-hand sides in registers
@@ -38,7 +35,6 @@
 //     r.r and r.z, deterministic last-CTA reduction per pair.
 #pragma once
 #include <cuda.h>
-#include <cuda_fp16.h>
 
 #include "of_common.cuh"
 
@@ -71,11 +67,8 @@ __host__ __device__ inline int sch_bh(int Ty, int ov) { return Ty + 2 * ov + 2; 
 __host__ __device__ inline int sch_rw(int Tx, int ov) { return Tx + 2 * ov + 2; }
 __host__ __device__ inline int sch_rh(int Ty, int ov) { return Ty + 2 * ov + 2; }
 
-// Per-cell element data: FP32 path packs 4 planes of half2
-// (h0x,h0y) (h0m,wE) (h1x,h1y) (h1m,wN); FP64 path 8 planes of double.
-template <typename R> struct CellBytes;
-template <> struct CellBytes<float> { static constexpr int value = 16; };
-template <> struct CellBytes<double> { static constexpr int value = 64; };
+// Per-cell element data: 8 planes h0x h0y h0m wE h1x h1y h1m wN.
+template <typename R> struct CellBytes { static constexpr int value = 8 * sizeof(R); };
 
 struct SchLayout {
     size_t bar, f1, f2, al, rs, qs, cells, zs, total;
@@ -153,55 +146,32 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, long long limit
     return true;
 }
 
-template <typename R> __device__ __forceinline__ R rcp(R x) { return R(1) / x; }
+// Reciprocal of a diagonal pivot.  FP32: the hardware approximation (about 1
+// ulp): the preconditioner only has to be one fixed linear operator, which a
+// deterministic approximation keeps.  FP64: exact division.
+__device__ __forceinline__ float rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
 // ------------------------------------------------------------ cell data --
-template <typename R> struct Cells;
-
-template <> struct Cells<float> {
-    __half2* p0;
-    __half2* p1;
-    __half2* p2;
-    __half2* p3;
-    __device__ void init(unsigned char* base, int nc) {
-        p0 = reinterpret_cast<__half2*>(base);
-        p1 = p0 + nc;
-        p2 = p1 + nc;
-        p3 = p2 + nc;
-    }
-    __device__ void store(int c, const float h0[3], float wE, const float h1[3], float wN) {
-        p0[c] = __floats2half2_rn(h0[0], h0[1]);
-        p1[c] = __floats2half2_rn(h0[2], wE);
-        p2[c] = __floats2half2_rn(h1[0], h1[1]);
-        p3[c] = __floats2half2_rn(h1[2], wN);
-    }
-    // triangle t=0 of cell c, with the E-edge weight of the cell's node
-    __device__ __forceinline__ void t0(int c, float h[3], float& w) const {
-        const float2 a = __half22float2(p0[c]), b = __half22float2(p1[c]);
-        h[0] = a.x; h[1] = a.y; h[2] = b.x; w = b.y;
-    }
-    // triangle t=1 of cell c, with the N-edge weight of the cell's node
-    __device__ __forceinline__ void t1(int c, float h[3], float& w) const {
-        const float2 a = __half22float2(p2[c]), b = __half22float2(p3[c]);
-        h[0] = a.x; h[1] = a.y; h[2] = b.x; w = b.y;
-    }
-};
-
-template <> struct Cells<double> {
-    double* p;
+template <typename R> struct Cells {
+    R* p;
     int nc;
     __device__ void init(unsigned char* base, int nc_) {
-        p = reinterpret_cast<double*>(base);
+        p = reinterpret_cast<R*>(base);
         nc = nc_;
     }
-    __device__ void store(int c, const double h0[3], double wE, const double h1[3], double wN) {
+    __device__ void store(int c, const R h0[3], R wE, const R h1[3], R wN) {
         p[c] = h0[0]; p[c + nc] = h0[1]; p[c + 2 * nc] = h0[2]; p[c + 3 * nc] = wE;
         p[c + 4 * nc] = h1[0]; p[c + 5 * nc] = h1[1]; p[c + 6 * nc] = h1[2]; p[c + 7 * nc] = wN;
     }
-    __device__ __forceinline__ void t0(int c, double h[3], double& w) const {
+    __device__ __forceinline__ void t0(int c, R h[3], R& w) const {
         h[0] = p[c]; h[1] = p[c + nc]; h[2] = p[c + 2 * nc]; w = p[c + 3 * nc];
     }
-    __device__ __forceinline__ void t1(int c, double h[3], double& w) const {
+    __device__ __forceinline__ void t1(int c, R h[3], R& w) const {
         h[0] = p[c + 4 * nc]; h[1] = p[c + 5 * nc]; h[2] = p[c + 6 * nc]; w = p[c + 7 * nc];
     }
 };
@@ -309,7 +279,7 @@ __device__ __forceinline__ double ordered_sum_rt(const double* p, int n, int str
 // nodes' blocks and right-hand sides live in registers).
 __host__ __device__ constexpr int sch_max_threads(bool fp64) { return fp64 ? 384 : 384; }
 
-template <typename R, int NPT>
+template <typename R, int NPT, int RWC>
 __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 8 ? 1 : 2)
     k_schwarz(const SchwarzParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -327,7 +297,8 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 
     const int tw = min(Tx, W - x0), th = min(Ty, H - y0);
     const int BW = sch_bw(Tx, ov), BH = sch_bh(Ty, ov);
     const int xs = x0 - sch_padl(ov), ys = y0 - ov - 1;
-    const int RW = sch_rw(Tx, ov), RH = sch_rh(Ty, ov);
+    const int RW = RWC ? RWC : sch_rw(Tx, ov);  // compile-time when the tile is one of the tuned shapes
+    const int RH = sch_rh(Ty, ov);
     const int nc = RW * RH;
     const int cx0 = x0 - ov - 1, cy0 = y0 - ov - 1;  // global node of cell (0, 0)
     const int ex0 = max(x0 - ov, 0), ex1 = min(x0 + tw + ov, W);
