@@ -42,7 +42,9 @@ struct of_ctx {
     int4 *blocks_dev = nullptr, *tiles_dev = nullptr;
     CUtensorMap* tmaps_dev = nullptr;
     uint32_t* ntab_dev = nullptr;
-    int sch_threads = 0, sch_npt = 1;
+    int sch_threads = 0, sch_npt = 1, sch_grid = 1;
+    void *cell0 = nullptr, *cell1 = nullptr;  // preconditioner element records [H][pitch]
+    bool cells_dirty = true;
     PairScalars* sc_dev = nullptr;
     PairScalars* sc_host = nullptr;  // pinned
     double *partA = nullptr, *partS = nullptr, *etamax = nullptr;
@@ -199,6 +201,7 @@ ofl::SolveBufs solve_bufs(of_ctx* h) {
     B.ntab = h->ntab_dev;
     B.sch_threads = h->sch_threads;
     B.sch_npt = h->sch_npt;
+    B.sch_grid = h->sch_grid;
     B.sc = h->sc_dev;
     B.partA = h->partA;
     B.partS = h->partS;
@@ -287,7 +290,6 @@ of_status encode_maps(of_ctx* h) {
     auto enc = get_encode();
     if (!enc) return fail(h, OF_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const int Tx = h->opts.tile_x, Ty = h->opts.tile_y, ov = h->opts.overlap;
-    const int BW = ofk::sch_bw(Tx, ov), BH = ofk::sch_bh(Ty, ov);
     const CUtensorMapDataType dtp = h->fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const size_t es = h->es;
     std::vector<CUtensorMap> maps((size_t)h->batch * ofk::TM_PER_PAIR);
@@ -295,27 +297,19 @@ of_status encode_maps(of_ctx* h) {
         const PairDesc& d = h->pd[p];
         CUtensorMap* m = &maps[(size_t)p * ofk::TM_PER_PAIR];
         const cuuint32_t es1[3] = {1, 1, 1};
-        {  // frames
-            const cuuint64_t dims[2] = {(cuuint64_t)d.W, (cuuint64_t)d.H};
-            const cuuint64_t str[1] = {(cuuint64_t)d.pitch * es};
-            const cuuint32_t box[2] = {(cuuint32_t)BW, (cuuint32_t)BH};
+        {  // preconditioner cell records, viewed as 8-byte units: u units per record
+            const int u = h->fp64 ? 4 : 1;
+            const int RW = ofk::sch_rw(Tx, ov), RH = ofk::sch_rh(Ty, ov);
+            const cuuint64_t dims[2] = {(cuuint64_t)d.W * u, (cuuint64_t)d.H};
+            const cuuint64_t str[1] = {(cuuint64_t)d.pitch * u * 8};
+            const cuuint32_t box[2] = {(cuuint32_t)(RW * u), (cuuint32_t)RH};
             for (int k = 0; k < 2; ++k) {
-                char* base = (char*)(k == 0 ? h->f1 : h->f2) + d.frame_off * es;
-                CUresult rc = enc(&m[k == 0 ? ofk::TM_F1 : ofk::TM_F2], dtp, 2, base, dims, str, box, es1,
-                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                char* base = (char*)(k == 0 ? h->cell0 : h->cell1) + d.frame_off * u * 8;
+                CUresult rc = enc(&m[k == 0 ? ofk::TM_C0 : ofk::TM_C1], CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, base, dims,
+                                  str, box, es1, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-                if (rc != CUDA_SUCCESS) return fail(h, OF_ERR_CUDA, "tensor map (frames) encoding failed");
+                if (rc != CUDA_SUCCESS) return fail(h, OF_ERR_CUDA, "tensor map (cells) encoding failed");
             }
-        }
-        {  // alpha, viewed as [H-1][2(W-1)] scalars with row stride 2 pitch
-            const cuuint64_t dims[2] = {(cuuint64_t)(2 * (d.W - 1)), (cuuint64_t)(d.H - 1)};
-            const cuuint64_t str[1] = {(cuuint64_t)2 * d.pitch * es};
-            const cuuint32_t box[2] = {(cuuint32_t)(2 * BW), (cuuint32_t)(BH - 1)};
-            char* base = (char*)h->alpha + 2 * d.frame_off * es;
-            CUresult rc = enc(&m[ofk::TM_AL], dtp, 2, base, dims, str, box, es1, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (rc != CUDA_SUCCESS) return fail(h, OF_ERR_CUDA, "tensor map (alpha) encoding failed");
         }
         {  // r and q planes
             const cuuint64_t dims[3] = {(cuuint64_t)d.W, (cuuint64_t)d.H, 3};
@@ -337,10 +331,27 @@ of_status encode_maps(of_ctx* h) {
     return OF_OK;
 }
 
+// Recomputes the preconditioner's element records if frames or alpha changed.
+of_status refresh_cells(of_ctx* h) {
+    if (!h->cells_dirty) return OF_OK;
+    ofl::SolveBufs B = solve_bufs(h);
+    const size_t rb = h->fp64 ? 32 : 8;
+    for (int p = 0; p < h->batch; ++p) {
+        const PairDesc& d = h->pd[p];
+        CK(ofl::launch_cells(B, p, d.W, d.H, (char*)h->cell0, (char*)h->cell1, h->stream));
+        count_other(h, 1);
+        (void)rb;
+    }
+    h->cells_dirty = false;
+    return OF_OK;
+}
+
 // The solve driver shared by of_solve and of_adjoint.  rhs == NULL: b from
 // the frames; otherwise the FP64 right-hand side planes.  On return x[cur]
 // holds the solution.
 of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* cur_out, std::vector<int>& passes_out) {
+    of_status cs = refresh_cells(h);
+    if (cs != OF_OK) return cs;
     ofl::SolveBufs B = solve_bufs(h);
     cudaStream_t st = h->stream;
     int cur = 0;
@@ -467,8 +478,9 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
         return fail(h, OF_ERR_ARG, "tile sizes must be multiples of 4 in [4, 256]");
     if (opt.overlap < 0 || opt.overlap > 32 || opt.sweeps < 0 || opt.sweeps > 64)
         return fail(h, OF_ERR_ARG, "overlap must be in [0, 32] and sweeps in [0, 64]");
-    if (2 * ofk::sch_bw(opt.tile_x, opt.overlap) > 256 || ofk::sch_bh(opt.tile_y, opt.overlap) > 256)
-        return fail(h, OF_ERR_ARG, "tile + overlap too large for one staged window (tile_x + 2 overlap <= 118)");
+    if (ofk::sch_rw(opt.tile_x, opt.overlap) * (opt.precision == OF_PREC_FP64 ? 4 : 1) > 256 ||
+        ofk::sch_rh(opt.tile_y, opt.overlap) > 256)
+        return fail(h, OF_ERR_ARG, "tile + overlap too large for one staged window");
     for (int p = 0; p < batch; ++p)
         if (W[p] < 2 || H[p] < 2 || W[p] > (1 << 20) || H[p] > (1 << 20))
             return fail(h, OF_ERR_ARG, "every frame must be at least 2x2 and at most 2^20 per side");
@@ -533,6 +545,8 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     CK(dalloc(h, &h->f2, fo * es));
     CK(dalloc(h, &h->alpha, 2 * fo * es));
     CK(dalloc(h, &h->eta, 2 * fo * es));
+    CK(dalloc(h, &h->cell0, fo * (h->fp64 ? 32 : 8)));
+    CK(dalloc(h, &h->cell1, fo * (h->fp64 ? 32 : 8)));
     for (int k = 0; k < 2; ++k) CK(dalloc(h, &h->x[k], vo * sizeof(double)));
     CK(dalloc(h, &h->usol, vo * sizeof(double)));
     CK(dalloc(h, &h->cvec, vo * sizeof(double)));
@@ -576,6 +590,8 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     h->sch_threads = sch_threads;
     h->sch_npt = sch_npt;
     CK(ofl::schwarz_configure(fp64, sch_npt, ofk::sch_rw(opt.tile_x, opt.overlap), smem));
+    h->sch_grid = ofl::schwarz_max_grid(fp64, sch_npt, ofk::sch_rw(opt.tile_x, opt.overlap), sch_threads, smem);
+    h->cells_dirty = true;
     h->frames_set.assign(batch, 0);
     h->alpha_set.assign(batch, 0);
     h->solved = false;
@@ -596,6 +612,7 @@ of_status of_set_frames(of_handle h, int pair, const void* f1, const void* f2, o
     if (s != OF_OK) return s;
     h->frames_set[pair] = 1;
     h->solved = false;
+    h->cells_dirty = true;
     return OF_OK;
 }
 
@@ -615,6 +632,7 @@ of_status of_set_alpha(of_handle h, int pair, const void* alpha, double alpha_co
     }
     h->alpha_set[pair] = 1;
     h->solved = false;
+    h->cells_dirty = true;
     return OF_OK;
 }
 
@@ -700,6 +718,7 @@ of_status of_adapt_alpha(of_handle h, double kappa, double eta_thr, double alpha
     }
     CK(cudaStreamSynchronize(st));
     h->solved = false;  // alpha changed: the stored solution no longer belongs to it
+    h->cells_dirty = true;
     return OF_OK;
 }
 
@@ -802,6 +821,8 @@ of_status of_precondition(of_handle h, int pair, const void* r, void* z, of_dtyp
     const PairDesc& d = h->pd[pair];
     const size_t es = h->es;
     s = copy_in(h, r, dt, d.W, (char*)h->r + d.vec_off * es, d.pitch, 3LL * d.H, d.W);
+    if (s != OF_OK) return s;
+    s = refresh_cells(h);
     if (s != OF_OK) return s;
     ofl::SolveBufs B = solve_bufs(h);
     CK(ofl::launch_precond_only(B, h->tile0[pair], h->ntile[pair], h->stream));

@@ -107,6 +107,7 @@ static SchwarzParams schwarz_params(const SolveBufs& B) {
     memset(&S, 0, sizeof(S));
     S.pairs = B.pairs;
     S.tiles = B.tiles;
+    S.ntiles = B.ntiles;
     S.tmaps = B.tmaps;
     S.ntab = B.ntab;
     S.sc = B.sc;
@@ -128,12 +129,12 @@ size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov) {
     return fp64 ? sch_smem_bytes<double>(Tx, Ty, ov) : sch_smem_bytes<float>(Tx, Ty, ov);
 }
 
-// Shapes with a compile-time row pitch (tile_x + 2 overlap + 2): 32-wide tiles
-// with overlap 0 (34) or 2 (38); other shapes use the runtime pitch.
+// Shapes with a compile-time cell-row pitch (sch_rw): 32-wide tiles with
+// overlap 0 (36) or 2 (40); other shapes use the runtime pitch.
 template <typename R, int NPT, typename F>
 static cudaError_t with_schwarz(int rw, F f) {
-    if (rw == 34) return f(k_schwarz<R, NPT, 34>);
-    if (rw == 38) return f(k_schwarz<R, NPT, 38>);
+    if (rw == 36) return f(k_schwarz<R, NPT, 36>);
+    if (rw == 40) return f(k_schwarz<R, NPT, 40>);
     return f(k_schwarz<R, NPT, 0>);
 }
 
@@ -149,8 +150,31 @@ cudaError_t schwarz_configure(int fp64, int npt, int rw, size_t smem) {
     });
 }
 
+int schwarz_max_grid(int fp64, int npt, int rw, int threads, size_t smem) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    with_schwarz_all(fp64, npt, rw, [&](auto kern) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem);
+    });
+    if (per < 1) per = 1;
+    return per * (sms > 0 ? sms : 1);
+}
+
+template <typename R>
+static cudaError_t cells_t(const SolveBufs& B, int pair, int W, int H, void* c0, void* c1, cudaStream_t st) {
+    dim3 grid((W + 127) / 128, H);
+    k_cells<R><<<grid, 128, 0, st>>>(B.pairs, pair, (const R*)B.f1, (const R*)B.f2, (const R*)B.alpha,
+                                    (typename CellT<R>::type*)c0, (typename CellT<R>::type*)c1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cells(const SolveBufs& B, int pair, int W, int H, void* c0, void* c1, cudaStream_t st) {
+    return B.fp64 ? cells_t<double>(B, pair, W, H, c0, c1, st) : cells_t<float>(B, pair, W, H, c0, c1, st);
+}
+
 bool schwarz_node_table(int fp64, int Tx, int Ty, int ov, std::vector<uint32_t>& tab, int& threads, int& npt) {
-    const int Ex = Tx + 2 * ov, Ey = Ty + 2 * ov, RW = sch_rw(Tx, ov);
+    const int Ex = Tx + 2 * ov, Ey = Ty + 2 * ov, RW = sch_rw(Tx, ov), cpad = sch_cpad(ov);
     const int nbank = fp64 ? 16 : 32;  // 8-byte words: 16 banks of pairs
     std::vector<std::vector<uint32_t>> slots[3];  // [colour][slot] -> up to 32 nodes, distinct banks
     int maxslots = 0;
@@ -158,7 +182,8 @@ bool schwarz_node_table(int fp64, int Tx, int Ty, int ov, std::vector<uint32_t>&
         std::vector<std::vector<uint32_t>> bucket(nbank);
         for (int j = 0; j < Ey; ++j)
             for (int i = 0; i < Ex; ++i)
-                if ((i + j) % 3 == c) bucket[((j + 1) * RW + (i + 1)) % nbank].push_back((uint32_t)i | ((uint32_t)j << 16));
+                if ((i + j) % 3 == c)
+                    bucket[((j + 1) * RW + (i + cpad - ov)) % nbank].push_back((uint32_t)i | ((uint32_t)j << 16));
         size_t ns = 0;
         for (auto& b : bucket) ns = std::max(ns, b.size());
         // with 16 banks of 8-byte words, a warp takes two nodes per bank pair (two wavefronts anyway)
@@ -184,8 +209,12 @@ bool schwarz_node_table(int fp64, int Tx, int Ty, int ov, std::vector<uint32_t>&
 static cudaError_t schwarz_launch(const SolveBufs& B, const SchwarzParams& S, int ntiles, cudaStream_t st) {
     const size_t smem = schwarz_smem_bytes(B.fp64, B.Tx, B.Ty, B.ov);
     const int nt = B.sch_threads;
+    const int grid = ntiles < B.sch_grid ? ntiles : B.sch_grid;
+    if (grid <= 0) return cudaSuccess;
+    SchwarzParams S2 = S;
+    S2.ntiles = ntiles;
     return with_schwarz_all(B.fp64, B.sch_npt, sch_rw(B.Tx, B.ov), [&](auto kern) {
-        kern<<<ntiles, nt, smem, st>>>(S);
+        kern<<<grid, nt, smem, st>>>(S2);
         return cudaGetLastError();
     });
 }

@@ -26,7 +26,7 @@ struct SolveBufs {
     const int4* tiles;
     const CUtensorMap* tmaps;
     const uint32_t* ntab;  // Schwarz thread -> node table (see schwarz_node_table)
-    int sch_threads, sch_npt;
+    int sch_threads, sch_npt, sch_grid;  // CTA size, nodes per thread and colour, persistent grid
     ofk::PairScalars* sc;
     double* partA;
     double* partS;
@@ -67,6 +67,11 @@ cudaError_t launch_apply(const SolveBufs& B, int pair, int blk0, int nblk, const
 // r must already be in B.r.
 cudaError_t launch_precond_only(const SolveBufs& B, int tile0, int ntiles, cudaStream_t st);
 size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov);
+// Cell records (element data of the preconditioner) of one pair, from the
+// frames and alpha in the workspace; c0, c1: [H][pitch] records.
+cudaError_t launch_cells(const SolveBufs& B, int pair, int W, int H, void* c0, void* c1, cudaStream_t st);
+// Persistent CTAs of the Schwarz kernel that fit on the device at once.
+int schwarz_max_grid(int fp64, int npt, int rw, int threads, size_t smem);
 cudaError_t schwarz_configure(int fp64, int npt, int rw, size_t smem);
 // Host-built assignment of the extended tile's nodes to (colour, slot,
 // thread) such that the 32 lanes of a warp touch 32 distinct shared-memory

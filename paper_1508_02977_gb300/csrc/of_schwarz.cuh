@@ -1,5 +1,8 @@
-// Overlapping Schwarz preconditioner (Section 3.2, Eq. schwarz), one CTA per
-// subdomain, fused with the residual update of the Krylov loop.
+// Overlapping Schwarz preconditioner (Section 3.2, Eq. schwarz), fused with
+// the residual update of the Krylov loop.  One subdomain is solved by one CTA
+// at a time; the grid is persistent (a few CTAs per SM walk the subdomain
+// list) and streams the next subdomain's data in by TMA while the current one
+// is swept.
 //
 // Subdomain i owns a tile T_x x T_y of nodes; its extended tile adds `o`
 // node layers on every side that is not on the image boundary (the overlap
@@ -17,34 +20,44 @@
 // which is symmetric positive definite (block diagonal over owned tiles of
 // SPD blocks).  With sweeps = 0 and overlap 0 it is node-block Jacobi.
 //
-// Work of one CTA:
-//  1. TMA (cp.async.bulk.tensor) stages the coefficient window -- frames
-//     over the extended tile plus a one-node halo, alpha of every square
-//     touching it -- and the owned tiles of r and q, on one mbarrier with a
-//     bounded wait.
-//  2. Per square of the window: h = g / sqrt(24) of both triangles and the
-//     alpha-weights of the two edges leaving its lower-left node, in shared
-//     memory planes.
-//  3. Each thread owns, per colour, the nodes of a host-built table that
-//     gives every warp 32 distinct shared-memory banks; it keeps their
-//     LDL^T-factored 3x3 diagonal blocks and right-hand sides in registers
-//     (r <- r - a q fused here).
-//  4. Sweeps: one block update per owned node and colour step,
+// Element data ("cells"): per node (x, y), the square (x, y) gives two
+// records, t=0 and t=1, each (h, w) with h = g_K / sqrt(24) of that triangle
+// and w the alpha-weight of one edge leaving the node (t=0: the edge to
+// (x+1,y); t=1: the edge to (x,y+1)).  They depend on the frames and alpha
+// only, so k_cells forms them once per solve (FP16 for the FP32 path: the
+// preconditioner only has to be one fixed SPD operator, and the diagonal
+// blocks are formed from the same rounded values, so the sweeps are exact
+// block Gauss-Seidel on the rounded local operator).  Outside the image the
+// records are zero (TMA fills out-of-range boxes with zeros), so missing
+// triangles contribute nothing.
+//
+// Per subdomain:
+//  1. TMA (cp.async.bulk.tensor) brings the two cell planes over the
+//     extended tile plus a one-node ring and the owned tiles of r and q into
+//     one of two stages (one mbarrier each, bounded waits); the next
+//     subdomain's copies are issued before this one is processed.
+//  2. Each thread owns, per colour, the nodes of a host-built table that
+//     gives the 32 lanes of a warp 32 distinct shared-memory banks; it forms
+//     their LDL^T-factored 3x3 diagonal blocks and right-hand sides in
+//     registers (r <- r - a q fused here).
+//  3. Sweeps: one block update per owned node and colour step,
 //     z_n = D_n^{-1} (r_n - sum_K h_K (h_K . (z_j + z_k)) + sum_e w_e z_e).
-//  5. Coalesced write-out of z and r on the owned tile, FP64 partials of
+//  4. Coalesced write-out of z and r on the owned tile, FP64 partials of
 //     r.r and r.z, deterministic last-CTA reduction per pair.
 #pragma once
 #include <cuda.h>
+#include <cuda_fp16.h>
 
 #include "of_common.cuh"
 
 namespace ofk {
 
-enum { TM_F1 = 0, TM_F2 = 1, TM_AL = 2, TM_R = 3, TM_Q = 4, TM_PER_PAIR = 5 };
+enum { TM_C0 = 0, TM_C1 = 1, TM_R = 2, TM_Q = 3, TM_PER_PAIR = 4 };
 
 struct SchwarzParams {
     const PairDesc* pairs;
     const int4* tiles;        // per work item: (pair, tile x, tile y, global tile index)
+    int ntiles;               // work items of this launch
     const CUtensorMap* tmaps; // [batch][TM_PER_PAIR], 64-byte aligned
     const uint32_t* ntab;     // [3][npt][blockDim] node of each (colour, slot, thread): i | j << 16, or ~0
     PairScalars* sc;
@@ -60,38 +73,37 @@ struct SchwarzParams {
     long long spin_limit;     // bounded mbarrier wait, in clock64 cycles
 };
 
-__host__ __device__ inline int sch_padl(int ov) { return ((ov + 1) + 3) & ~3; }
-__host__ __device__ inline int sch_bw(int Tx, int ov) { return (sch_padl(ov) + Tx + ov + 1 + 3) & ~3; }
-__host__ __device__ inline int sch_bh(int Ty, int ov) { return Ty + 2 * ov + 2; }
-// cell grid: the extended tile plus a one-node ring, row pitch RW
-__host__ __device__ inline int sch_rw(int Tx, int ov) { return Tx + 2 * ov + 2; }
+// Cell grid of a subdomain: columns from cx0 = x0 - sch_cpad(o) (even, so
+// that TMA boxes of 8-byte records start 16-byte aligned) to at least the
+// ring column x0 + T_x + o; rows from y0 - o - 1 to y0 + T_y + o.
+__host__ __device__ inline int sch_cpad(int ov) { return (ov + 2) & ~1; }
+__host__ __device__ inline int sch_rw(int Tx, int ov) { return (sch_cpad(ov) + Tx + ov + 1 + 1) & ~1; }
 __host__ __device__ inline int sch_rh(int Ty, int ov) { return Ty + 2 * ov + 2; }
 
-// Per-cell element data: 8 planes h0x h0y h0m wE h1x h1y h1m wN.
-template <typename R> struct CellBytes { static constexpr int value = 8 * sizeof(R); };
+// One cell record: float path 4 halves (8 bytes), FP64 path 4 doubles.
+template <typename R> struct CellT;
+template <> struct CellT<float> { using type = uint2; static constexpr int units = 1; };
+template <> struct CellT<double> { using type = double4_32a; static constexpr int units = 4; };
+template <typename R> __host__ __device__ constexpr int cell_bytes() { return (int)sizeof(typename CellT<R>::type); }
 
 struct SchLayout {
-    size_t bar, f1, f2, al, rs, qs, cells, zs, total;
+    size_t bar, stage0, stage_bytes, c0, c1, rs, qs, zs, total;
 };
 
 template <typename R>
 __host__ __device__ inline SchLayout sch_layout(int Tx, int Ty, int ov) {
     auto al = [](size_t b) { return (b + 127) & ~(size_t)127; };
-    const int BW = sch_bw(Tx, ov), BH = sch_bh(Ty, ov);
     const size_t nc = (size_t)sch_rw(Tx, ov) * sch_rh(Ty, ov);
     SchLayout L;
     L.bar = 0;
-    L.f1 = 128;
-    L.f2 = L.f1 + al((size_t)BW * BH * sizeof(R));
-    L.al = L.f2 + al((size_t)BW * BH * sizeof(R));
-    size_t stage_end = L.al + al(2 * (size_t)BW * BH * sizeof(R));
-    L.zs = L.f1;  // z planes reuse the coefficient staging once the cells are built
-    const size_t z_end = L.zs + al(3 * nc * sizeof(R));
-    if (z_end > stage_end) stage_end = z_end;
-    L.rs = stage_end;
+    L.c0 = 0;
+    L.c1 = al(nc * cell_bytes<R>());
+    L.rs = L.c1 + al(nc * cell_bytes<R>());
     L.qs = L.rs + al(3 * (size_t)Tx * Ty * sizeof(R));
-    L.cells = L.qs + al(3 * (size_t)Tx * Ty * sizeof(R));
-    L.total = L.cells + al(nc * CellBytes<R>::value) + 128;  // + alignment slack
+    L.stage_bytes = L.qs + al(3 * (size_t)Tx * Ty * sizeof(R));
+    L.stage0 = 128;
+    L.zs = L.stage0 + 2 * L.stage_bytes;
+    L.total = L.zs + al(3 * nc * sizeof(R)) + 128;  // + alignment slack
     return L;
 }
 
@@ -156,25 +168,67 @@ __device__ __forceinline__ float rcp(float x) {
 }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
+
+__device__ __forceinline__ bool mbar_wait_phase_bounded(uint64_t* bar, unsigned phase, long long limit) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, phase)) {
+        if (clock64() - t0 > limit) return false;
+    }
+    return true;
+}
+
 // ------------------------------------------------------------ cell data --
-template <typename R> struct Cells {
-    R* p;
-    int nc;
-    __device__ void init(unsigned char* base, int nc_) {
-        p = reinterpret_cast<R*>(base);
-        nc = nc_;
+template <typename R> struct CellView;
+
+template <> struct CellView<float> {
+    const uint2* c0;
+    const uint2* c1;
+    __device__ __forceinline__ static void unpack(uint2 v, float h[3], float& w) {
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+        h[0] = a.x; h[1] = a.y; h[2] = b.x; w = b.y;
     }
-    __device__ void store(int c, const R h0[3], R wE, const R h1[3], R wN) {
-        p[c] = h0[0]; p[c + nc] = h0[1]; p[c + 2 * nc] = h0[2]; p[c + 3 * nc] = wE;
-        p[c + 4 * nc] = h1[0]; p[c + 5 * nc] = h1[1]; p[c + 6 * nc] = h1[2]; p[c + 7 * nc] = wN;
+    __device__ __forceinline__ void t0(int c, float h[3], float& w) const { unpack(c0[c], h, w); }
+    __device__ __forceinline__ void t1(int c, float h[3], float& w) const { unpack(c1[c], h, w); }
+};
+
+template <> struct CellView<double> {
+    const double4_32a* c0;
+    const double4_32a* c1;
+    __device__ __forceinline__ void t0(int c, double h[3], double& w) const {
+        const double4_32a v = c0[c];
+        h[0] = v.x; h[1] = v.y; h[2] = v.z; w = v.w;
     }
-    __device__ __forceinline__ void t0(int c, R h[3], R& w) const {
-        h[0] = p[c]; h[1] = p[c + nc]; h[2] = p[c + 2 * nc]; w = p[c + 3 * nc];
-    }
-    __device__ __forceinline__ void t1(int c, R h[3], R& w) const {
-        h[0] = p[c + 4 * nc]; h[1] = p[c + 5 * nc]; h[2] = p[c + 6 * nc]; w = p[c + 7 * nc];
+    __device__ __forceinline__ void t1(int c, double h[3], double& w) const {
+        const double4_32a v = c1[c];
+        h[0] = v.x; h[1] = v.y; h[2] = v.z; w = v.w;
     }
 };
+
+// Cell records of node (x, y) from the frames and alpha (workspace layouts).
+template <typename R>
+__device__ __forceinline__ void cell_records(int x, int y, int W, int H, int pitch, const R* f1, const R* f2,
+                                             const R* al, R h0[3], R& wE, R h1[3], R& wN) {
+    const R isq24 = R(0.20412414523193151);  // 1/sqrt(24)
+    const R third = R(1) / R(3), half = R(0.5);
+    const bool vc = (x < W - 1) && (y < H - 1);
+    h0[0] = h0[1] = h0[2] = h1[0] = h1[1] = h1[2] = R(0);
+    const long long o = (long long)y * pitch + x;
+    if (vc) {
+        const R a2 = f2[o], b2 = f2[o + 1], c2 = f2[o + pitch + 1], d2 = f2[o + pitch];
+        const R a1 = f1[o], b1 = f1[o + 1], c1 = f1[o + pitch + 1], d1 = f1[o + pitch];
+        h0[0] = (b2 - a2) * isq24;
+        h0[1] = (c2 - b2) * isq24;
+        h0[2] = -(a1 + b1 + c1) * third * isq24;
+        h1[0] = (c2 - d2) * isq24;
+        h1[1] = (d2 - a2) * isq24;
+        h1[2] = -(a1 + d1 + c1) * third * isq24;
+    }
+    // edge to (x+1,y): t0 of square (x,y) and t1 of square (x,y-1)
+    wE = half * ((vc ? al[2 * o] : R(0)) + ((x < W - 1 && y >= 1) ? al[2 * (o - pitch) + 1] : R(0)));
+    // edge to (x,y+1): t1 of square (x,y) and t0 of square (x-1,y)
+    wN = half * ((vc ? al[2 * o + 1] : R(0)) + ((x >= 1 && y < H - 1) ? al[2 * (o - 1)] : R(0)));
+}
 
 // LDL^T factors of a node's 3x3 diagonal block: 1/d0, l10, l20, 1/d1, l21, 1/d2
 template <typename R> struct Blk { R i0, l10, l20, i1, l21, i2; };
@@ -193,13 +247,14 @@ __device__ __forceinline__ Blk<R> ldl3(R D00, R D01, R D02, R D11, R D12, R D22)
     return b;
 }
 
+
 // The six elements around node n = cell c (x, y):
 //   E1 t0 of (x,y)      others E, NE        E4 t1 of (x-1,y-1) others SW, W
 //   E2 t1 of (x,y)      others N, NE        E5 t0 of (x-1,y)   others W, N
 //   E3 t0 of (x-1,y-1)  others SW, S        E6 t1 of (x,y-1)   others S, E
 // Edge weights: n-E = wE(c), n-N = wN(c), n-W = wE(c-1), n-S = wN(c-RW).
 template <typename R>
-__device__ __forceinline__ void node_block(const Cells<R>& C, int c, int RW, R lE, R lN, R lW, R lS, Blk<R>& B) {
+__device__ __forceinline__ void node_block(const CellView<R>& C, int c, int RW, R lE, R lN, R lW, R lS, Blk<R>& B) {
     R h[6][3], wE, wN, wW, wS, dummy;
     C.t0(c, h[0], wE);
     C.t1(c, h[1], wN);
@@ -218,7 +273,7 @@ __device__ __forceinline__ void node_block(const Cells<R>& C, int c, int RW, R l
 }
 
 template <typename R>
-__device__ __forceinline__ void node_sweep(const Cells<R>& C, R* __restrict__ Z, int zplane, int c, int RW, R lE,
+__device__ __forceinline__ void node_sweep(const CellView<R>& C, R* __restrict__ Z, int zplane, int c, int RW, R lE,
                                            R lN, R lW, R lS, const Blk<R>& B, R b0, R b1, R b2) {
     const R* z0 = Z;
     const R* z1 = Z + zplane;
@@ -275,6 +330,7 @@ __device__ __forceinline__ double ordered_sum_rt(const double* p, int n, int str
     return block_sum_rt(s, sh);
 }
 
+
 // Largest CTA the host may build a node table for (registers: the owned
 // nodes' blocks and right-hand sides live in registers).
 __host__ __device__ constexpr int sch_max_threads(bool fp64) { return fp64 ? 384 : 384; }
@@ -285,229 +341,254 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ double sh_red[32];
     __shared__ int sh_last, sh_fail;
-    const int4 ti = P.tiles[blockIdx.x];
-    const int pair = ti.x;
-    if (!P.apply_only && P.sc[pair].done) return;  // uniform over the pair's tiles
     const int NT = blockDim.x;
-    const PairDesc pd = P.pairs[pair];
-    const int W = pd.W, H = pd.H, pitch = pd.pitch;
-    const long long plane = (long long)H * pitch;
     const int Tx = P.Tx, Ty = P.Ty, ov = P.ov;
-    const int x0 = ti.y * Tx, y0 = ti.z * Ty;
-    const int tw = min(Tx, W - x0), th = min(Ty, H - y0);
-    const int BW = sch_bw(Tx, ov), BH = sch_bh(Ty, ov);
-    const int xs = x0 - sch_padl(ov), ys = y0 - ov - 1;
-    const int RW = RWC ? RWC : sch_rw(Tx, ov);  // compile-time when the tile is one of the tuned shapes
+    const int RW = RWC ? RWC : sch_rw(Tx, ov);  // compile-time for the tuned tile shapes
     const int RH = sch_rh(Ty, ov);
     const int nc = RW * RH;
-    const int cx0 = x0 - ov - 1, cy0 = y0 - ov - 1;  // global node of cell (0, 0)
-    const int ex0 = max(x0 - ov, 0), ex1 = min(x0 + tw + ov, W);
-    const int ey0 = max(y0 - ov, 0), ey1 = min(y0 + th + ov, H);
-    const bool need_q = !P.first && !P.apply_only;
-
+    const int cpad = sch_cpad(ov);
     const SchLayout L = sch_layout<R>(Tx, Ty, ov);
     unsigned char* base = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(base + L.bar);
-    R* F1s = reinterpret_cast<R*>(base + L.f1);
-    R* F2s = reinterpret_cast<R*>(base + L.f2);
-    R* ALs = reinterpret_cast<R*>(base + L.al);
-    R* Rs = reinterpret_cast<R*>(base + L.rs);
-    R* Qs = reinterpret_cast<R*>(base + L.qs);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bar);
     R* Zs = reinterpret_cast<R*>(base + L.zs);
-    Cells<R> C;
-    C.init(base + L.cells, nc);
+    const unsigned box_rq = (unsigned)(3 * (size_t)Tx * Ty * sizeof(R));
+    const unsigned box_c = (unsigned)(nc * cell_bytes<R>());
 
-    // ---- 1. staging
-    const CUtensorMap* tm = P.tmaps + (size_t)pair * TM_PER_PAIR;
     if (threadIdx.x == 0) {
         sh_fail = 0;
-        mbar_init(bar, 1);
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned bytes = (unsigned)(2 * (size_t)BW * BH + 2 * (size_t)BW * (BH - 1) + 3 * (size_t)Tx * Ty) * sizeof(R);
-        if (need_q) bytes += (unsigned)(3 * (size_t)Tx * Ty * sizeof(R));
-        mbar_expect_tx(bar, bytes);
-        tma_load_2d(F1s, tm + TM_F1, xs, ys, bar);
-        tma_load_2d(F2s, tm + TM_F2, xs, ys, bar);
-        tma_load_2d(ALs, tm + TM_AL, 2 * xs, ys, bar);
-        tma_load_3d(Rs, tm + TM_R, x0, y0, 0, bar);
-        if (need_q) tma_load_3d(Qs, tm + TM_Q, x0, y0, 0, bar);
-        if (!mbar_wait_bounded(bar, P.spin_limit)) {
+
+    // a work item is processed unless its pair has finished (a pair's flag is
+    // only set after all of its items have been processed in this launch)
+    auto active = [&](int t) { return P.apply_only || !P.sc[P.tiles[t].x].done; };
+    auto issue = [&](int t, int s) {
+        const int4 ti = P.tiles[t];
+        const CUtensorMap* tm = P.tmaps + (size_t)ti.x * TM_PER_PAIR;
+        const int x0 = ti.y * Tx, y0 = ti.z * Ty;
+        const bool need_q = !P.first && !P.apply_only;
+        unsigned char* st = base + L.stage0 + (size_t)s * L.stage_bytes;
+        // order this stage's earlier generic-proxy reads before the async-proxy writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bars[s], 2 * box_c + box_rq + (need_q ? box_rq : 0u));
+        const int cx = (x0 - cpad) * CellT<R>::units, cy = y0 - ov - 1;
+        tma_load_2d(st + L.c0, tm + TM_C0, cx, cy, &bars[s]);
+        tma_load_2d(st + L.c1, tm + TM_C1, cx, cy, &bars[s]);
+        tma_load_3d(st + L.rs, tm + TM_R, x0, y0, 0, &bars[s]);
+        if (need_q) tma_load_3d(st + L.qs, tm + TM_Q, x0, y0, 0, &bars[s]);
+    };
+
+    const int G = gridDim.x;
+    int t = blockIdx.x;
+    while (t < P.ntiles && !active(t)) t += G;
+    if (t >= P.ntiles) return;
+    if (threadIdx.x == 0) issue(t, 0);
+    unsigned phase[2] = {0u, 0u};
+    int s = 0;
+    for (; t < P.ntiles;) {
+        // the next active item of this CTA goes into the other stage
+        int tn = t + G;
+        while (tn < P.ntiles && !active(tn)) tn += G;
+        if (tn < P.ntiles && threadIdx.x == 0) issue(tn, s ^ 1);
+
+        if (threadIdx.x == 0 && !mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit)) {
             sh_fail = 1;
             atomicOr(P.err, 1);
-            mbar_wait_bounded(bar, P.spin_limit);  // give copies in flight a last chance to land
-        }
-    }
-    __syncthreads();
-    if (sh_fail) return;
-    if (!mbar_wait_bounded(bar, P.spin_limit)) atomicOr(P.err, 1);  // every thread observes the phase
-
-    // ---- 2. element data per cell (square at the cell's node)
-    const R isq24 = R(0.20412414523193151);  // 1/sqrt(24)
-    const R third = R(1) / R(3), half = R(0.5);
-    for (int c = threadIdx.x; c < nc; c += NT) {
-        const int j = c / RW, i = c - j * RW;
-        const int sx = cx0 + i, sy = cy0 + j;
-        R h0[3] = {0, 0, 0}, h1[3] = {0, 0, 0}, wE = 0, wN = 0;
-        if (i < RW - 1 && j < RH - 1) {
-            const int fx = sx - xs, fy = sy - ys;
-            if (sx >= 0 && sx < W - 1 && sy >= 0 && sy < H - 1) {
-                const int f = fy * BW + fx;
-                const R a2 = F2s[f], b2 = F2s[f + 1], c2 = F2s[f + BW + 1], d2 = F2s[f + BW];
-                const R a1 = F1s[f], b1 = F1s[f + 1], c1 = F1s[f + BW + 1], d1 = F1s[f + BW];
-                h0[0] = (b2 - a2) * isq24;
-                h0[1] = (c2 - b2) * isq24;
-                h0[2] = -(a1 + b1 + c1) * third * isq24;
-                h1[0] = (c2 - d2) * isq24;
-                h1[1] = (d2 - a2) * isq24;
-                h1[2] = -(a1 + d1 + c1) * third * isq24;
-            }
-            // alpha outside the image reads as 0 (TMA fill): missing triangles add nothing
-            const int a = 2 * (fy * BW + fx);
-            if (j >= 1) wE = half * (ALs[a] + ALs[a - 2 * BW + 1]);
-            if (i >= 1) wN = half * (ALs[a + 1] + ALs[a - 2]);
-        }
-        C.store(c, h0, wE, h1, wN);
-    }
-    __syncthreads();
-
-    // ---- 3. owned nodes: diagonal blocks, right-hand sides, r <- r - a q
-    const R a = need_q ? (R)P.sc[pair].a : R(0);
-    const R hl = half * (R)P.lam;
-    // per owned node: cell index (low 24 bits) and the number of existing
-    // triangles on its E, N, W, S legs (2 bits each, high byte)
-    int cell[3][NPT];
-    R rhs[3][NPT][3];
-    Blk<R> blk[3][NPT];
-#pragma unroll
-    for (int col = 0; col < 3; ++col) {
-#pragma unroll
-        for (int k = 0; k < NPT; ++k) {
-            const uint32_t e = P.ntab[(col * NPT + k) * NT + threadIdx.x];
-            cell[col][k] = -1;
-            rhs[col][k][0] = rhs[col][k][1] = rhs[col][k][2] = R(0);
-            blk[col][k] = Blk<R>{R(0), R(0), R(0), R(0), R(0), R(0)};
-            if (e == 0xffffffffu) continue;
-            const int li = (int)(e & 0xffffu), lj = (int)(e >> 16);
-            const int gx = x0 - ov + li, gy = y0 - ov + lj;
-            if (gx < ex0 || gx >= ex1 || gy < ey0 || gy >= ey1) continue;
-            const int c = (lj + 1) * RW + (li + 1);
-            // existing triangles on the four legs (the lambda weight is 1/2 lambda each)
-            const int vc = (gx < W - 1 && gy < H - 1), vsw = (gx >= 1 && gy >= 1);
-            const int vw = (gx >= 1 && gy < H - 1), vs = (gx < W - 1 && gy >= 1);
-            const int nE = vc + vs, nN = vc + vw, nW = vsw + vw, nS = vsw + vs;
-            cell[col][k] = c | (nE << 24) | (nN << 26) | (nW << 28) | (nS << 30);
-            node_block<R>(C, c, RW, hl * nE, hl * nN, hl * nW, hl * nS, blk[col][k]);
-            if (gx >= x0 && gx < x0 + tw && gy >= y0 && gy < y0 + th) {
-                const int si = (gy - y0) * Tx + (gx - x0);
-                R v0 = Rs[si], v1 = Rs[si + Tx * Ty], v2 = Rs[si + 2 * Tx * Ty];
-                if (need_q) {
-                    v0 -= a * Qs[si];
-                    v1 -= a * Qs[si + Tx * Ty];
-                    v2 -= a * Qs[si + 2 * Tx * Ty];
-                    Rs[si] = v0;
-                    Rs[si + Tx * Ty] = v1;
-                    Rs[si + 2 * Tx * Ty] = v2;
-                }
-                rhs[col][k][0] = v0;
-                rhs[col][k][1] = v1;
-                rhs[col][k][2] = v2;
-            }
-        }
-    }
-    __syncthreads();  // staging reads done before z (which reuses it) is cleared
-    for (int i = threadIdx.x; i < 3 * nc; i += NT) Zs[i] = R(0);
-    __syncthreads();
-
-    // ---- 4. sweeps (colour order 0,1,2,1,0,1,2,1,0,...; sweeps = 0: block Jacobi)
-    const int nsteps = (P.sweeps > 0) ? 1 + 4 * P.sweeps : 1;
-    for (int step = 0; step < nsteps; ++step) {
-        const int m = step & 3;
-        const int col = (m == 0) ? 0 : (m == 2 ? 2 : 1);
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-            if (P.sweeps > 0 && cc != col) continue;  // Jacobi: every colour at once
-#pragma unroll
-            for (int k = 0; k < NPT; ++k) {
-                if (cell[cc][k] == -1) continue;
-                const int c = cell[cc][k] & 0xffffff;
-                const unsigned nb = (unsigned)cell[cc][k] >> 24;
-                if (P.sweeps == 0) {  // block Jacobi: z = D^{-1} r, no neighbour terms
-                    const Blk<R>& B = blk[cc][k];
-                    const R b0 = rhs[cc][k][0];
-                    const R y1 = rhs[cc][k][1] - B.l10 * b0, y2 = rhs[cc][k][2] - B.l20 * b0 - B.l21 * y1;
-                    const R x2 = y2 * B.i2, x1 = y1 * B.i1 - B.l21 * x2, x0 = b0 * B.i0 - B.l10 * x1 - B.l20 * x2;
-                    Zs[c] = x0;
-                    Zs[c + nc] = x1;
-                    Zs[c + 2 * nc] = x2;
-                    continue;
-                }
-                node_sweep<R>(C, Zs, nc, c, RW, hl * R(nb & 3u), hl * R((nb >> 2) & 3u), hl * R((nb >> 4) & 3u),
-                              hl * R(nb >> 6), blk[cc][k], rhs[cc][k][0], rhs[cc][k][1], rhs[cc][k][2]);
-            }
         }
         __syncthreads();
-    }
-
-    // ---- 5. write-out of the owned tile (coalesced), partials r.r and r.z
-    R* zg = reinterpret_cast<R*>(P.z) + pd.vec_off;
-    R* rg = reinterpret_cast<R*>(P.r) + pd.vec_off;
-    R rr = R(0), rz = R(0);
-    const int ntile = tw * th;
-    for (int k = threadIdx.x; k < ntile; k += NT) {
-        const int j = k / tw, i = k - j * tw;
-        const int si = j * Tx + i;
-        const int c = (j + ov + 1) * RW + (i + ov + 1);
-        const R v0 = Zs[c], v1 = Zs[c + nc], v2 = Zs[c + 2 * nc];
-        const R r0 = Rs[si], r1 = Rs[si + Tx * Ty], r2 = Rs[si + 2 * Tx * Ty];
-        const long long o = (long long)(y0 + j) * pitch + (x0 + i);
-        zg[o] = v0;
-        zg[o + plane] = v1;
-        zg[o + 2 * plane] = v2;
-        if (need_q) {
-            rg[o] = r0;
-            rg[o + plane] = r1;
-            rg[o + 2 * plane] = r2;
+        if (sh_fail) {
+            // give the copies in flight a last chance to land before leaving
+            if (threadIdx.x == 0) {
+                mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit);
+                if (tn < P.ntiles) mbar_wait_phase_bounded(&bars[s ^ 1], phase[s ^ 1], P.spin_limit);
+            }
+            return;
         }
-        rr += r0 * r0 + r1 * r1 + r2 * r2;
-        rz += r0 * v0 + r1 * v1 + r2 * v2;
-    }
-    if (P.apply_only) return;
+        if (!mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit)) atomicOr(P.err, 1);
+        phase[s] ^= 1u;
 
-    const double s_rr = block_sum_rt((double)rr, sh_red);
-    const double s_rz = block_sum_rt((double)rz, sh_red);
-    if (threadIdx.x == 0) {
-        P.partial[2 * (long long)ti.w] = s_rr;
-        P.partial[2 * (long long)ti.w + 1] = s_rz;
-    }
-    const int ntiles = pd.tiles_x * pd.tiles_y;
-    if (!arrive_last(&P.counter[pair], (unsigned)ntiles, &sh_last)) return;
-    const double t_rr = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0, ntiles, 2, sh_red);
-    const double t_rz = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0 + 1, ntiles, 2, sh_red);
-    if (threadIdx.x == 0) {
-        PairScalars* s = P.sc + pair;
-        if (P.first) {
-            s->rz = t_rz;
-            s->rr = t_rr;
-            s->beta = 0.0;
-            if (!isfinite(t_rr) || !isfinite(t_rz)) { s->status = 6; s->done = 1; }
-            else if (t_rr <= s->tol2 || t_rr == 0.0) { s->done = 1; }
-            else if (!(t_rz > 0.0)) { s->status = 6; s->done = 1; }
-        } else {
-            s->beta = t_rz / s->rz;
-            s->rz = t_rz;
-            s->rr = t_rr;
-            s->it += 1;
-            s->it_total += 1;
-            if (!isfinite(t_rr) || !isfinite(t_rz)) { s->status = 6; s->done = 1; }
-            else if (t_rr <= s->tol2) { s->done = 1; }
-            else if (!(t_rz > 0.0)) { s->status = 6; s->done = 1; }
-            else if (s->it >= s->max_it) { s->status = 5; s->done = 1; }
+        unsigned char* st = base + L.stage0 + (size_t)s * L.stage_bytes;
+        CellView<R> C;
+        C.c0 = reinterpret_cast<const typename CellT<R>::type*>(st + L.c0);
+        C.c1 = reinterpret_cast<const typename CellT<R>::type*>(st + L.c1);
+        R* Rs = reinterpret_cast<R*>(st + L.rs);
+        const R* Qs = reinterpret_cast<const R*>(st + L.qs);
+
+        const int4 ti = P.tiles[t];
+        const int pair = ti.x;
+        const PairDesc pd = P.pairs[pair];
+        const int W = pd.W, H = pd.H, pitch = pd.pitch;
+        const long long plane = (long long)H * pitch;
+        const int x0 = ti.y * Tx, y0 = ti.z * Ty;
+        const int tw = min(Tx, W - x0), th = min(Ty, H - y0);
+        const int ex0 = max(x0 - ov, 0), ex1 = min(x0 + tw + ov, W);
+        const int ey0 = max(y0 - ov, 0), ey1 = min(y0 + th + ov, H);
+        const bool need_q = !P.first && !P.apply_only;
+
+        // ---- owned nodes: diagonal blocks, right-hand sides, r <- r - a q
+        const R a = need_q ? (R)P.sc[pair].a : R(0);
+        const R hl = R(0.5) * (R)P.lam;
+        int cell[3][NPT];
+        R rhs[3][NPT][3];
+        Blk<R> blk[3][NPT];
+#pragma unroll
+        for (int col = 0; col < 3; ++col) {
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const uint32_t e = P.ntab[(col * NPT + k) * NT + threadIdx.x];
+                cell[col][k] = -1;
+                rhs[col][k][0] = rhs[col][k][1] = rhs[col][k][2] = R(0);
+                blk[col][k] = Blk<R>{R(0), R(0), R(0), R(0), R(0), R(0)};
+                if (e == 0xffffffffu) continue;
+                const int li = (int)(e & 0xffffu), lj = (int)(e >> 16);
+                const int gx = x0 - ov + li, gy = y0 - ov + lj;
+                if (gx < ex0 || gx >= ex1 || gy < ey0 || gy >= ey1) continue;
+                const int c = (lj + 1) * RW + (li + cpad - ov);
+                // existing triangles on the four legs (the lambda weight is 1/2 lambda each)
+                const int vc = (gx < W - 1 && gy < H - 1), vsw = (gx >= 1 && gy >= 1);
+                const int vw = (gx >= 1 && gy < H - 1), vs = (gx < W - 1 && gy >= 1);
+                const int nE = vc + vs, nN = vc + vw, nW = vsw + vw, nS = vsw + vs;
+                cell[col][k] = c | (nE << 24) | (nN << 26) | (nW << 28) | (nS << 30);
+                node_block<R>(C, c, RW, hl * nE, hl * nN, hl * nW, hl * nS, blk[col][k]);
+                if (gx >= x0 && gx < x0 + tw && gy >= y0 && gy < y0 + th) {
+                    const int si = (gy - y0) * Tx + (gx - x0);
+                    R v0 = Rs[si], v1 = Rs[si + Tx * Ty], v2 = Rs[si + 2 * Tx * Ty];
+                    if (need_q) {
+                        v0 -= a * Qs[si];
+                        v1 -= a * Qs[si + Tx * Ty];
+                        v2 -= a * Qs[si + 2 * Tx * Ty];
+                        Rs[si] = v0;
+                        Rs[si + Tx * Ty] = v1;
+                        Rs[si + 2 * Tx * Ty] = v2;
+                    }
+                    rhs[col][k][0] = v0;
+                    rhs[col][k][1] = v1;
+                    rhs[col][k][2] = v2;
+                }
+            }
         }
-        __threadfence();
-        P.counter[pair] = 0u;
+        for (int i = threadIdx.x; i < 3 * nc; i += NT) Zs[i] = R(0);
+        __syncthreads();
+
+        // ---- sweeps (colour order 0,1,2,1,0,1,2,1,0,...; sweeps = 0: block Jacobi)
+        const int nsteps = (P.sweeps > 0) ? 1 + 4 * P.sweeps : 1;
+        for (int step = 0; step < nsteps; ++step) {
+            const int m = step & 3;
+            const int col = (m == 0) ? 0 : (m == 2 ? 2 : 1);
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                if (P.sweeps > 0 && cc != col) continue;  // Jacobi: every colour at once
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    if (cell[cc][k] == -1) continue;
+                    const int c = cell[cc][k] & 0xffffff;
+                    const unsigned nb = (unsigned)cell[cc][k] >> 24;
+                    if (P.sweeps == 0) {  // block Jacobi: z = D^{-1} r, no neighbour terms
+                        const Blk<R>& B = blk[cc][k];
+                        const R b0 = rhs[cc][k][0];
+                        const R y1 = rhs[cc][k][1] - B.l10 * b0, y2 = rhs[cc][k][2] - B.l20 * b0 - B.l21 * y1;
+                        const R x2 = y2 * B.i2, x1 = y1 * B.i1 - B.l21 * x2, xx = b0 * B.i0 - B.l10 * x1 - B.l20 * x2;
+                        Zs[c] = xx;
+                        Zs[c + nc] = x1;
+                        Zs[c + 2 * nc] = x2;
+                        continue;
+                    }
+                    node_sweep<R>(C, Zs, nc, c, RW, hl * R(nb & 3u), hl * R((nb >> 2) & 3u),
+                                  hl * R((nb >> 4) & 3u), hl * R(nb >> 6), blk[cc][k], rhs[cc][k][0], rhs[cc][k][1],
+                                  rhs[cc][k][2]);
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---- write-out of the owned tile (coalesced), partials r.r and r.z
+        R* zg = reinterpret_cast<R*>(P.z) + pd.vec_off;
+        R* rg = reinterpret_cast<R*>(P.r) + pd.vec_off;
+        R rr = R(0), rz = R(0);
+        const int ntile = tw * th;
+        for (int k = threadIdx.x; k < ntile; k += NT) {
+            const int j = k / tw, i = k - j * tw;
+            const int si = j * Tx + i;
+            const int c = (j + ov + 1) * RW + (i + cpad);
+            const R v0 = Zs[c], v1 = Zs[c + nc], v2 = Zs[c + 2 * nc];
+            const R r0 = Rs[si], r1 = Rs[si + Tx * Ty], r2 = Rs[si + 2 * Tx * Ty];
+            const long long o = (long long)(y0 + j) * pitch + (x0 + i);
+            zg[o] = v0;
+            zg[o + plane] = v1;
+            zg[o + 2 * plane] = v2;
+            if (need_q) {
+                rg[o] = r0;
+                rg[o + plane] = r1;
+                rg[o + 2 * plane] = r2;
+            }
+            rr += r0 * r0 + r1 * r1 + r2 * r2;
+            rz += r0 * v0 + r1 * v1 + r2 * v2;
+        }
+        if (!P.apply_only) {
+            const double s_rr = block_sum_rt((double)rr, sh_red);
+            const double s_rz = block_sum_rt((double)rz, sh_red);
+            if (threadIdx.x == 0) {
+                P.partial[2 * (long long)ti.w] = s_rr;
+                P.partial[2 * (long long)ti.w + 1] = s_rz;
+            }
+            const int ntp = pd.tiles_x * pd.tiles_y;
+            if (arrive_last(&P.counter[pair], (unsigned)ntp, &sh_last)) {
+                const double t_rr = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0, ntp, 2, sh_red);
+                const double t_rz = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0 + 1, ntp, 2, sh_red);
+                if (threadIdx.x == 0) {
+                    PairScalars* sp = P.sc + pair;
+                    if (P.first) {
+                        sp->rz = t_rz;
+                        sp->rr = t_rr;
+                        sp->beta = 0.0;
+                        if (!isfinite(t_rr) || !isfinite(t_rz)) { sp->status = 6; sp->done = 1; }
+                        else if (t_rr <= sp->tol2 || t_rr == 0.0) { sp->done = 1; }
+                        else if (!(t_rz > 0.0)) { sp->status = 6; sp->done = 1; }
+                    } else {
+                        sp->beta = t_rz / sp->rz;
+                        sp->rz = t_rz;
+                        sp->rr = t_rr;
+                        sp->it += 1;
+                        sp->it_total += 1;
+                        if (!isfinite(t_rr) || !isfinite(t_rz)) { sp->status = 6; sp->done = 1; }
+                        else if (t_rr <= sp->tol2) { sp->done = 1; }
+                        else if (!(t_rz > 0.0)) { sp->status = 6; sp->done = 1; }
+                        else if (sp->it >= sp->max_it) { sp->status = 5; sp->done = 1; }
+                    }
+                    __threadfence();
+                    P.counter[pair] = 0u;
+                }
+            }
+        }
+        __syncthreads();  // this stage and z are free for the next item
+        t = tn;
+        s ^= 1;
+    }
+}
+
+// Cell records for every node of every pair (once per solve).
+template <typename R>
+__global__ void k_cells(const PairDesc* pairs, int pair, const R* __restrict__ f1a, const R* __restrict__ f2a,
+                        const R* __restrict__ ala, typename CellT<R>::type* __restrict__ c0a,
+                        typename CellT<R>::type* __restrict__ c1a) {
+    const PairDesc pd = pairs[pair];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= pd.W) return;
+    R h0[3], h1[3], wE, wN;
+    cell_records<R>(x, y, pd.W, pd.H, pd.pitch, f1a + pd.frame_off, f2a + pd.frame_off, ala + 2 * pd.frame_off, h0,
+                    wE, h1, wN);
+    const long long o = pd.frame_off + (long long)y * pd.pitch + x;
+    if constexpr (sizeof(R) == 4) {
+        const __half2 a = __floats2half2_rn(h0[0], h0[1]), b = __floats2half2_rn(h0[2], wE);
+        const __half2 c = __floats2half2_rn(h1[0], h1[1]), d = __floats2half2_rn(h1[2], wN);
+        c0a[o] = make_uint2(*reinterpret_cast<const unsigned*>(&a), *reinterpret_cast<const unsigned*>(&b));
+        c1a[o] = make_uint2(*reinterpret_cast<const unsigned*>(&c), *reinterpret_cast<const unsigned*>(&d));
+    } else {
+        c0a[o] = make_double4_32a(h0[0], h0[1], h0[2], wE);
+        c1a[o] = make_double4_32a(h1[0], h1[1], h1[2], wN);
     }
 }
 
