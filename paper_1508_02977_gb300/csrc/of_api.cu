@@ -42,7 +42,7 @@ struct of_ctx {
     int4 *blocks_dev = nullptr, *tiles_dev = nullptr;
     CUtensorMap* tmaps_dev = nullptr;
     uint32_t* ntab_dev = nullptr;
-    int sch_threads = 0, sch_npt = 1, sch_grid = 1;
+    int sch_threads = 0, sch_npt = 1, sch_grid = 1, sch_nstage = 2;
     void *cell0 = nullptr, *cell1 = nullptr;  // preconditioner element records [H][pitch]
     bool cells_dirty = true;
     PairScalars* sc_dev = nullptr;
@@ -202,6 +202,7 @@ ofl::SolveBufs solve_bufs(of_ctx* h) {
     B.sch_threads = h->sch_threads;
     B.sch_npt = h->sch_npt;
     B.sch_grid = h->sch_grid;
+    B.sch_nstage = h->sch_nstage;
     B.sc = h->sc_dev;
     B.partA = h->partA;
     B.partS = h->partS;
@@ -485,13 +486,19 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
         if (W[p] < 2 || H[p] < 2 || W[p] > (1 << 20) || H[p] > (1 << 20))
             return fail(h, OF_ERR_ARG, "every frame must be at least 2x2 and at most 2^20 per side");
     const int fp64 = opt.precision == OF_PREC_FP64;
-    const size_t smem = ofl::schwarz_smem_bytes(fp64, opt.tile_x, opt.tile_y, opt.overlap);
+    int smax = 0;
+    CK(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    // two TMA stages (prefetch of the next subdomain) when they fit, else one
+    int nstage = 2;
+    size_t smem = ofl::schwarz_smem_bytes(fp64, opt.tile_x, opt.tile_y, opt.overlap, 2);
+    if (smem > (size_t)smax) {
+        nstage = 1;
+        smem = ofl::schwarz_smem_bytes(fp64, opt.tile_x, opt.tile_y, opt.overlap, 1);
+    }
     std::vector<uint32_t> ntab;
     int sch_threads = 0, sch_npt = 1;
     if (!ofl::schwarz_node_table(fp64, opt.tile_x, opt.tile_y, opt.overlap, ntab, sch_threads, sch_npt))
         return fail(h, OF_ERR_ARG, "extended tile too large for one CTA (more than 2 nodes per thread and colour)");
-    int smax = 0;
-    CK(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     if (smem > (size_t)smax) return fail(h, OF_ERR_ARG, "tile/overlap need more shared memory than one CTA has");
 
     CK(cudaStreamSynchronize(h->stream));
@@ -589,6 +596,7 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     CK(cudaMemcpyAsync(h->ntab_dev, ntab.data(), ntab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     h->sch_threads = sch_threads;
     h->sch_npt = sch_npt;
+    h->sch_nstage = nstage;
     CK(ofl::schwarz_configure(fp64, sch_npt, ofk::sch_rw(opt.tile_x, opt.overlap), smem));
     h->sch_grid = ofl::schwarz_max_grid(fp64, sch_npt, ofk::sch_rw(opt.tile_x, opt.overlap), sch_threads, smem);
     h->cells_dirty = true;

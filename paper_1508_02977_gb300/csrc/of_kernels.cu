@@ -121,12 +121,13 @@ static SchwarzParams schwarz_params(const SolveBufs& B) {
     S.Ty = B.Ty;
     S.ov = B.ov;
     S.sweeps = B.sweeps;
+    S.nstage = B.sch_nstage;
     S.spin_limit = B.spin_limit;
     return S;
 }
 
-size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov) {
-    return fp64 ? sch_smem_bytes<double>(Tx, Ty, ov) : sch_smem_bytes<float>(Tx, Ty, ov);
+size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov, int nstage) {
+    return fp64 ? sch_smem_bytes<double>(Tx, Ty, ov, nstage) : sch_smem_bytes<float>(Tx, Ty, ov, nstage);
 }
 
 // Shapes with a compile-time cell-row pitch (sch_rw): 32-wide tiles with
@@ -207,7 +208,7 @@ bool schwarz_node_table(int fp64, int Tx, int Ty, int ov, std::vector<uint32_t>&
 }
 
 static cudaError_t schwarz_launch(const SolveBufs& B, const SchwarzParams& S, int ntiles, cudaStream_t st) {
-    const size_t smem = schwarz_smem_bytes(B.fp64, B.Tx, B.Ty, B.ov);
+    const size_t smem = schwarz_smem_bytes(B.fp64, B.Tx, B.Ty, B.ov, B.sch_nstage);
     const int nt = B.sch_threads;
     const int grid = ntiles < B.sch_grid ? ntiles : B.sch_grid;
     if (grid <= 0) return cudaSuccess;

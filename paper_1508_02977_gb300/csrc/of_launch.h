@@ -26,7 +26,7 @@ struct SolveBufs {
     const int4* tiles;
     const CUtensorMap* tmaps;
     const uint32_t* ntab;  // Schwarz thread -> node table (see schwarz_node_table)
-    int sch_threads, sch_npt, sch_grid;  // CTA size, nodes per thread and colour, persistent grid
+    int sch_threads, sch_npt, sch_grid, sch_nstage;  // CTA size, nodes per thread and colour, grid, TMA stages
     ofk::PairScalars* sc;
     double* partA;
     double* partS;
@@ -66,7 +66,7 @@ cudaError_t launch_apply(const SolveBufs& B, int pair, int blk0, int nblk, const
 // Stand-alone preconditioner z = M r for one pair (tiles of that pair only);
 // r must already be in B.r.
 cudaError_t launch_precond_only(const SolveBufs& B, int tile0, int ntiles, cudaStream_t st);
-size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov);
+size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov, int nstage);
 // Cell records (element data of the preconditioner) of one pair, from the
 // frames and alpha in the workspace; c0, c1: [H][pitch] records.
 cudaError_t launch_cells(const SolveBufs& B, int pair, int W, int H, void* c0, void* c1, cudaStream_t st);

@@ -70,6 +70,7 @@ struct SchwarzParams {
     int Tx, Ty, ov, sweeps;
     int first;                // no r update (start of a pass): z = M r only
     int apply_only;           // of_precondition: z = M r, no scalars
+    int nstage;               // 2: the next item streams in during this one; 1: after it
     long long spin_limit;     // bounded mbarrier wait, in clock64 cycles
 };
 
@@ -91,7 +92,7 @@ struct SchLayout {
 };
 
 template <typename R>
-__host__ __device__ inline SchLayout sch_layout(int Tx, int Ty, int ov) {
+__host__ __device__ inline SchLayout sch_layout(int Tx, int Ty, int ov, int nstage) {
     auto al = [](size_t b) { return (b + 127) & ~(size_t)127; };
     const size_t nc = (size_t)sch_rw(Tx, ov) * sch_rh(Ty, ov);
     SchLayout L;
@@ -102,14 +103,14 @@ __host__ __device__ inline SchLayout sch_layout(int Tx, int Ty, int ov) {
     L.qs = L.rs + al(3 * (size_t)Tx * Ty * sizeof(R));
     L.stage_bytes = L.qs + al(3 * (size_t)Tx * Ty * sizeof(R));
     L.stage0 = 128;
-    L.zs = L.stage0 + 2 * L.stage_bytes;
+    L.zs = L.stage0 + (size_t)nstage * L.stage_bytes;
     L.total = L.zs + al(3 * nc * sizeof(R)) + 128;  // + alignment slack
     return L;
 }
 
 template <typename R>
-__host__ __device__ inline size_t sch_smem_bytes(int Tx, int Ty, int ov) {
-    return sch_layout<R>(Tx, Ty, ov).total;
+__host__ __device__ inline size_t sch_smem_bytes(int Tx, int Ty, int ov, int nstage) {
+    return sch_layout<R>(Tx, Ty, ov, nstage).total;
 }
 
 // ---------------------------------------------------------------- PTX --
@@ -347,7 +348,8 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 
     const int RH = sch_rh(Ty, ov);
     const int nc = RW * RH;
     const int cpad = sch_cpad(ov);
-    const SchLayout L = sch_layout<R>(Tx, Ty, ov);
+    const int nstage = P.nstage;
+    const SchLayout L = sch_layout<R>(Tx, Ty, ov, nstage);
     unsigned char* base = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bar);
     R* Zs = reinterpret_cast<R*>(base + L.zs);
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 
         // the next active item of this CTA goes into the other stage
         int tn = t + G;
         while (tn < P.ntiles && !active(tn)) tn += G;
-        if (tn < P.ntiles && threadIdx.x == 0) issue(tn, s ^ 1);
+        if (nstage == 2 && tn < P.ntiles && threadIdx.x == 0) issue(tn, s ^ 1);
 
         if (threadIdx.x == 0 && !mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit)) {
             sh_fail = 1;
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 
             // give the copies in flight a last chance to land before leaving
             if (threadIdx.x == 0) {
                 mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit);
-                if (tn < P.ntiles) mbar_wait_phase_bounded(&bars[s ^ 1], phase[s ^ 1], P.spin_limit);
+                if (nstage == 2 && tn < P.ntiles) mbar_wait_phase_bounded(&bars[s ^ 1], phase[s ^ 1], P.spin_limit);
             }
             return;
         }
@@ -565,7 +567,8 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 
         }
         __syncthreads();  // this stage and z are free for the next item
         t = tn;
-        s ^= 1;
+        if (nstage == 2) s ^= 1;
+        else if (t < P.ntiles && threadIdx.x == 0) issue(t, 0);
     }
 }
 
