@@ -220,6 +220,7 @@ ofl::SolveBufs solve_bufs(of_ctx* h) {
     B.p1 = h->p1;
     B.nblk = h->nblk_total;
     B.ntiles = h->ntiles_total;
+    B.npairs = h->batch;
     B.rows_per_block = h->rows_per_block;
     B.Tx = h->opts.tile_x;
     B.Ty = h->opts.tile_y;

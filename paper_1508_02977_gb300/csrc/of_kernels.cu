@@ -108,6 +108,7 @@ static SchwarzParams schwarz_params(const SolveBufs& B) {
     S.pairs = B.pairs;
     S.tiles = B.tiles;
     S.ntiles = B.ntiles;
+    S.npairs = B.npairs;
     S.tmaps = B.tmaps;
     S.ntab = B.ntab;
     S.sc = B.sc;

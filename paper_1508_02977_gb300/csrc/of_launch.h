@@ -42,7 +42,7 @@ struct SolveBufs {
     void* d;
     void* p0;
     void* p1;
-    int nblk, ntiles, rows_per_block;
+    int nblk, ntiles, rows_per_block, npairs;
     int Tx, Ty, ov, sweeps;
     double lam;
     int fp64;            // 1: everything FP64; 0: FP32 inner with FP64 residual

@@ -62,7 +62,8 @@ struct SchwarzParams {
     const uint32_t* ntab;     // [3][npt][blockDim] node of each (colour, slot, thread): i | j << 16, or ~0
     PairScalars* sc;
     double* partial;          // [ntiles][2]
-    unsigned* counter;        // [batch]
+    unsigned* counter;        // one arrival counter per launch (reset by the last CTA)
+    int npairs;               // pairs of the batch (the last CTA updates each one's scalars)
     int* err;                 // device error word (bit 0: TMA wait timed out)
     void* r;                  // inner residual planes (written back on owned nodes)
     void* z;                  // preconditioned residual planes (owned nodes)
@@ -383,11 +384,17 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 
         if (need_q) tma_load_3d(st + L.qs, tm + TM_Q, x0, y0, 0, &bars[s]);
     };
 
+    // this thread's nodes of the (unclipped) extended tile, per colour
+    uint32_t tab[3][NPT];
+#pragma unroll
+    for (int col = 0; col < 3; ++col)
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) tab[col][k] = P.ntab[(col * NPT + k) * NT + threadIdx.x];
+
     const int G = gridDim.x;
     int t = blockIdx.x;
     while (t < P.ntiles && !active(t)) t += G;
-    if (t >= P.ntiles) return;
-    if (threadIdx.x == 0) issue(t, 0);
+    if (t < P.ntiles && threadIdx.x == 0) issue(t, 0);
     unsigned phase[2] = {0u, 0u};
     int s = 0;
     for (; t < P.ntiles;) {
@@ -440,7 +447,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 
         for (int col = 0; col < 3; ++col) {
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
-                const uint32_t e = P.ntab[(col * NPT + k) * NT + threadIdx.x];
+                const uint32_t e = tab[col][k];
                 cell[col][k] = -1;
                 rhs[col][k][0] = rhs[col][k][1] = rhs[col][k][2] = R(0);
                 blk[col][k] = Blk<R>{R(0), R(0), R(0), R(0), R(0), R(0)};
@@ -536,39 +543,48 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 
                 P.partial[2 * (long long)ti.w] = s_rr;
                 P.partial[2 * (long long)ti.w + 1] = s_rz;
             }
-            const int ntp = pd.tiles_x * pd.tiles_y;
-            if (arrive_last(&P.counter[pair], (unsigned)ntp, &sh_last)) {
-                const double t_rr = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0, ntp, 2, sh_red);
-                const double t_rz = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0 + 1, ntp, 2, sh_red);
-                if (threadIdx.x == 0) {
-                    PairScalars* sp = P.sc + pair;
-                    if (P.first) {
-                        sp->rz = t_rz;
-                        sp->rr = t_rr;
-                        sp->beta = 0.0;
-                        if (!isfinite(t_rr) || !isfinite(t_rz)) { sp->status = 6; sp->done = 1; }
-                        else if (t_rr <= sp->tol2 || t_rr == 0.0) { sp->done = 1; }
-                        else if (!(t_rz > 0.0)) { sp->status = 6; sp->done = 1; }
-                    } else {
-                        sp->beta = t_rz / sp->rz;
-                        sp->rz = t_rz;
-                        sp->rr = t_rr;
-                        sp->it += 1;
-                        sp->it_total += 1;
-                        if (!isfinite(t_rr) || !isfinite(t_rz)) { sp->status = 6; sp->done = 1; }
-                        else if (t_rr <= sp->tol2) { sp->done = 1; }
-                        else if (!(t_rz > 0.0)) { sp->status = 6; sp->done = 1; }
-                        else if (sp->it >= sp->max_it) { sp->status = 5; sp->done = 1; }
-                    }
-                    __threadfence();
-                    P.counter[pair] = 0u;
-                }
-            }
         }
         __syncthreads();  // this stage and z are free for the next item
         t = tn;
         if (nstage == 2) s ^= 1;
         else if (t < P.ntiles && threadIdx.x == 0) issue(t, 0);
+    }
+    if (P.apply_only) return;
+    // one arrival per CTA; the last CTA reduces the items of every pair that
+    // took part, in item order (deterministic), and updates its scalars
+    if (!arrive_last(P.counter, gridDim.x, &sh_last)) return;
+    for (int pi = 0; pi < P.npairs; ++pi) {
+        PairScalars* sp = P.sc + pi;
+        if (sp->done) continue;  // finished before this launch: nothing of it ran
+        const PairDesc pd = P.pairs[pi];
+        const int ntp = pd.tiles_x * pd.tiles_y;
+        const double t_rr = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0, ntp, 2, sh_red);
+        const double t_rz = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0 + 1, ntp, 2, sh_red);
+        if (threadIdx.x == 0) {
+            if (P.first) {
+                sp->rz = t_rz;
+                sp->rr = t_rr;
+                sp->beta = 0.0;
+                if (!isfinite(t_rr) || !isfinite(t_rz)) { sp->status = 6; sp->done = 1; }
+                else if (t_rr <= sp->tol2 || t_rr == 0.0) { sp->done = 1; }
+                else if (!(t_rz > 0.0)) { sp->status = 6; sp->done = 1; }
+            } else {
+                sp->beta = t_rz / sp->rz;
+                sp->rz = t_rz;
+                sp->rr = t_rr;
+                sp->it += 1;
+                sp->it_total += 1;
+                if (!isfinite(t_rr) || !isfinite(t_rz)) { sp->status = 6; sp->done = 1; }
+                else if (t_rr <= sp->tol2) { sp->done = 1; }
+                else if (!(t_rz > 0.0)) { sp->status = 6; sp->done = 1; }
+                else if (sp->it >= sp->max_it) { sp->status = 5; sp->done = 1; }
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        *P.counter = 0u;
     }
 }
 
