@@ -598,8 +598,8 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     h->sch_threads = sch_threads;
     h->sch_npt = sch_npt;
     h->sch_nstage = nstage;
-    CK(ofl::schwarz_configure(fp64, sch_npt, ofk::sch_rw(opt.tile_x, opt.overlap), smem));
-    h->sch_grid = ofl::schwarz_max_grid(fp64, sch_npt, ofk::sch_rw(opt.tile_x, opt.overlap), sch_threads, smem);
+    CK(ofl::schwarz_configure(fp64, sch_npt, opt.tile_x, opt.tile_y, opt.overlap, smem));
+    h->sch_grid = ofl::schwarz_max_grid(fp64, sch_npt, opt.tile_x, opt.tile_y, opt.overlap, sch_threads, smem);
     h->cells_dirty = true;
     h->frames_set.assign(batch, 0);
     h->alpha_set.assign(batch, 0);

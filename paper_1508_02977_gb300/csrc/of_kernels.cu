@@ -131,32 +131,32 @@ size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov, int nstage) {
     return fp64 ? sch_smem_bytes<double>(Tx, Ty, ov, nstage) : sch_smem_bytes<float>(Tx, Ty, ov, nstage);
 }
 
-// Shapes with a compile-time cell-row pitch (sch_rw): 32-wide tiles with
-// overlap 0 (36) or 2 (40); other shapes use the runtime pitch.
+// Tile shapes compiled with a compile-time geometry (the tuned ones);
+// every other shape uses the runtime-geometry instantiation.
 template <typename R, int NPT, typename F>
-static cudaError_t with_schwarz(int rw, F f) {
-    if (rw == 36) return f(k_schwarz<R, NPT, 36>);
-    if (rw == 40) return f(k_schwarz<R, NPT, 40>);
-    return f(k_schwarz<R, NPT, 0>);
+static cudaError_t with_schwarz(int tx, int ty, int ov, F f) {
+    if (NPT == 1 && tx == 32 && ty == 32 && ov == 0) return f(k_schwarz<R, NPT, 32, 32, 0>);
+    if (NPT == 2 && tx == 48 && ty == 48 && ov == 0) return f(k_schwarz<R, NPT, 48, 48, 0>);
+    return f(k_schwarz<R, NPT, 0, 0, 0>);
 }
 
 template <typename F>
-static cudaError_t with_schwarz_all(int fp64, int npt, int rw, F f) {
-    if (fp64) return npt == 1 ? with_schwarz<double, 1>(rw, f) : with_schwarz<double, 2>(rw, f);
-    return npt == 1 ? with_schwarz<float, 1>(rw, f) : with_schwarz<float, 2>(rw, f);
+static cudaError_t with_schwarz_all(int fp64, int npt, int tx, int ty, int ov, F f) {
+    if (fp64) return npt == 1 ? with_schwarz<double, 1>(tx, ty, ov, f) : with_schwarz<double, 2>(tx, ty, ov, f);
+    return npt == 1 ? with_schwarz<float, 1>(tx, ty, ov, f) : with_schwarz<float, 2>(tx, ty, ov, f);
 }
 
-cudaError_t schwarz_configure(int fp64, int npt, int rw, size_t smem) {
-    return with_schwarz_all(fp64, npt, rw, [&](auto kern) {
+cudaError_t schwarz_configure(int fp64, int npt, int tx, int ty, int ov, size_t smem) {
+    return with_schwarz_all(fp64, npt, tx, ty, ov, [&](auto kern) {
         return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     });
 }
 
-int schwarz_max_grid(int fp64, int npt, int rw, int threads, size_t smem) {
+int schwarz_max_grid(int fp64, int npt, int tx, int ty, int ov, int threads, size_t smem) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    with_schwarz_all(fp64, npt, rw, [&](auto kern) {
+    with_schwarz_all(fp64, npt, tx, ty, ov, [&](auto kern) {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem);
     });
     if (per < 1) per = 1;
@@ -215,7 +215,7 @@ static cudaError_t schwarz_launch(const SolveBufs& B, const SchwarzParams& S, in
     if (grid <= 0) return cudaSuccess;
     SchwarzParams S2 = S;
     S2.ntiles = ntiles;
-    return with_schwarz_all(B.fp64, B.sch_npt, sch_rw(B.Tx, B.ov), [&](auto kern) {
+    return with_schwarz_all(B.fp64, B.sch_npt, B.Tx, B.Ty, B.ov, [&](auto kern) {
         kern<<<grid, nt, smem, st>>>(S2);
         return cudaGetLastError();
     });

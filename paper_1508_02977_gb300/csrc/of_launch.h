@@ -71,8 +71,8 @@ size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov, int nstage);
 // frames and alpha in the workspace; c0, c1: [H][pitch] records.
 cudaError_t launch_cells(const SolveBufs& B, int pair, int W, int H, void* c0, void* c1, cudaStream_t st);
 // Persistent CTAs of the Schwarz kernel that fit on the device at once.
-int schwarz_max_grid(int fp64, int npt, int rw, int threads, size_t smem);
-cudaError_t schwarz_configure(int fp64, int npt, int rw, size_t smem);
+int schwarz_max_grid(int fp64, int npt, int tx, int ty, int ov, int threads, size_t smem);
+cudaError_t schwarz_configure(int fp64, int npt, int tx, int ty, int ov, size_t smem);
 // Host-built assignment of the extended tile's nodes to (colour, slot,
 // thread) such that the 32 lanes of a warp touch 32 distinct shared-memory
 // banks.  Returns false if a tile needs more than 2 slots per thread.

@@ -337,15 +337,51 @@ __device__ __forceinline__ double ordered_sum_rt(const double* p, int n, int str
 // nodes' blocks and right-hand sides live in registers).
 __host__ __device__ constexpr int sch_max_threads(bool fp64) { return fp64 ? 384 : 384; }
 
-template <typename R, int NPT, int RWC>
+// Per-node sweep state kept in registers by the owning thread.
+template <typename R> struct NodeState {
+    int c;            // cell index, -1: no node
+    R lE, lN, lW, lS; // lambda weights of the four legs
+    R b0, b1, b2;     // right-hand side
+    Blk<R> B;         // LDL^T factors of the diagonal block
+};
+
+// Block update of every node of one colour that this thread owns.
+template <typename R, int NPT>
+__device__ __forceinline__ void colour_step(const CellView<R>& C, R* Zs, int nc, int RW, const NodeState<R> (&ns)[NPT]) {
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const NodeState<R>& n = ns[k];
+        if (n.c < 0) continue;
+        node_sweep<R>(C, Zs, nc, n.c, RW, n.lE, n.lN, n.lW, n.lS, n.B, n.b0, n.b1, n.b2);
+    }
+}
+
+// Block Jacobi: z = D^{-1} r, no neighbour terms.
+template <typename R, int NPT>
+__device__ __forceinline__ void jacobi_step(R* Zs, int nc, const NodeState<R> (&ns)[NPT]) {
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const NodeState<R>& n = ns[k];
+        if (n.c < 0) continue;
+        const Blk<R>& B = n.B;
+        const R y1 = n.b1 - B.l10 * n.b0, y2 = n.b2 - B.l20 * n.b0 - B.l21 * y1;
+        const R x2 = y2 * B.i2, x1 = y1 * B.i1 - B.l21 * x2, x0 = n.b0 * B.i0 - B.l10 * x1 - B.l20 * x2;
+        Zs[n.c] = x0;
+        Zs[n.c + nc] = x1;
+        Zs[n.c + 2 * nc] = x2;
+    }
+}
+
+template <typename R, int NPT, int TXC, int TYC, int OVC>
 __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 8 ? 1 : 2)
     k_schwarz(const SchwarzParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ double sh_red[32];
     __shared__ int sh_last, sh_fail;
     const int NT = blockDim.x;
-    const int Tx = P.Tx, Ty = P.Ty, ov = P.ov;
-    const int RW = RWC ? RWC : sch_rw(Tx, ov);  // compile-time for the tuned tile shapes
+    // compile-time for the tuned tile shapes (TXC > 0), runtime otherwise
+    const int Tx = TXC ? TXC : P.Tx, Ty = TXC ? TYC : P.Ty, ov = TXC ? OVC : P.ov;
+    const int RW = sch_rw(Tx, ov);
     const int RH = sch_rh(Ty, ov);
     const int nc = RW * RH;
     const int cpad = sch_cpad(ov);
@@ -440,28 +476,31 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 
         // ---- owned nodes: diagonal blocks, right-hand sides, r <- r - a q
         const R a = need_q ? (R)P.sc[pair].a : R(0);
         const R hl = R(0.5) * (R)P.lam;
-        int cell[3][NPT];
-        R rhs[3][NPT][3];
-        Blk<R> blk[3][NPT];
+        NodeState<R> ns[3][NPT];
 #pragma unroll
         for (int col = 0; col < 3; ++col) {
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
                 const uint32_t e = tab[col][k];
-                cell[col][k] = -1;
-                rhs[col][k][0] = rhs[col][k][1] = rhs[col][k][2] = R(0);
-                blk[col][k] = Blk<R>{R(0), R(0), R(0), R(0), R(0), R(0)};
+                NodeState<R>& n = ns[col][k];
+                n.c = -1;
+                n.b0 = n.b1 = n.b2 = R(0);
+                n.lE = n.lN = n.lW = n.lS = R(0);
+                n.B = Blk<R>{R(0), R(0), R(0), R(0), R(0), R(0)};
                 if (e == 0xffffffffu) continue;
                 const int li = (int)(e & 0xffffu), lj = (int)(e >> 16);
                 const int gx = x0 - ov + li, gy = y0 - ov + lj;
                 if (gx < ex0 || gx >= ex1 || gy < ey0 || gy >= ey1) continue;
                 const int c = (lj + 1) * RW + (li + cpad - ov);
-                // existing triangles on the four legs (the lambda weight is 1/2 lambda each)
-                const int vc = (gx < W - 1 && gy < H - 1), vsw = (gx >= 1 && gy >= 1);
-                const int vw = (gx >= 1 && gy < H - 1), vs = (gx < W - 1 && gy >= 1);
-                const int nE = vc + vs, nN = vc + vw, nW = vsw + vw, nS = vsw + vs;
-                cell[col][k] = c | (nE << 24) | (nN << 26) | (nW << 28) | (nS << 30);
-                node_block<R>(C, c, RW, hl * nE, hl * nN, hl * nW, hl * nS, blk[col][k]);
+                // existing triangles on the four legs: 1/2 lambda each
+                const R vc = (gx < W - 1 && gy < H - 1) ? hl : R(0), vsw = (gx >= 1 && gy >= 1) ? hl : R(0);
+                const R vw = (gx >= 1 && gy < H - 1) ? hl : R(0), vs = (gx < W - 1 && gy >= 1) ? hl : R(0);
+                n.c = c;
+                n.lE = vc + vs;
+                n.lN = vc + vw;
+                n.lW = vsw + vw;
+                n.lS = vsw + vs;
+                node_block<R>(C, c, RW, n.lE, n.lN, n.lW, n.lS, n.B);
                 if (gx >= x0 && gx < x0 + tw && gy >= y0 && gy < y0 + th) {
                     const int si = (gy - y0) * Tx + (gx - x0);
                     R v0 = Rs[si], v1 = Rs[si + Tx * Ty], v2 = Rs[si + 2 * Tx * Ty];
@@ -473,9 +512,9 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 
                         Rs[si + Tx * Ty] = v1;
                         Rs[si + 2 * Tx * Ty] = v2;
                     }
-                    rhs[col][k][0] = v0;
-                    rhs[col][k][1] = v1;
-                    rhs[col][k][2] = v2;
+                    n.b0 = v0;
+                    n.b1 = v1;
+                    n.b2 = v2;
                 }
             }
         }
@@ -483,33 +522,23 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 
         __syncthreads();
 
         // ---- sweeps (colour order 0,1,2,1,0,1,2,1,0,...; sweeps = 0: block Jacobi)
-        const int nsteps = (P.sweeps > 0) ? 1 + 4 * P.sweeps : 1;
-        for (int step = 0; step < nsteps; ++step) {
-            const int m = step & 3;
-            const int col = (m == 0) ? 0 : (m == 2 ? 2 : 1);
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                if (P.sweeps > 0 && cc != col) continue;  // Jacobi: every colour at once
-#pragma unroll
-                for (int k = 0; k < NPT; ++k) {
-                    if (cell[cc][k] == -1) continue;
-                    const int c = cell[cc][k] & 0xffffff;
-                    const unsigned nb = (unsigned)cell[cc][k] >> 24;
-                    if (P.sweeps == 0) {  // block Jacobi: z = D^{-1} r, no neighbour terms
-                        const Blk<R>& B = blk[cc][k];
-                        const R b0 = rhs[cc][k][0];
-                        const R y1 = rhs[cc][k][1] - B.l10 * b0, y2 = rhs[cc][k][2] - B.l20 * b0 - B.l21 * y1;
-                        const R x2 = y2 * B.i2, x1 = y1 * B.i1 - B.l21 * x2, xx = b0 * B.i0 - B.l10 * x1 - B.l20 * x2;
-                        Zs[c] = xx;
-                        Zs[c + nc] = x1;
-                        Zs[c + 2 * nc] = x2;
-                        continue;
-                    }
-                    node_sweep<R>(C, Zs, nc, c, RW, hl * R(nb & 3u), hl * R((nb >> 2) & 3u),
-                                  hl * R((nb >> 4) & 3u), hl * R(nb >> 6), blk[cc][k], rhs[cc][k][0], rhs[cc][k][1],
-                                  rhs[cc][k][2]);
-                }
+        if (P.sweeps == 0) {
+            jacobi_step<R, NPT>(Zs, nc, ns[0]);
+            jacobi_step<R, NPT>(Zs, nc, ns[1]);
+            jacobi_step<R, NPT>(Zs, nc, ns[2]);
+            __syncthreads();
+        } else {
+            for (int sw = 0; sw < P.sweeps; ++sw) {
+                colour_step<R, NPT>(C, Zs, nc, RW, ns[0]);
+                __syncthreads();
+                colour_step<R, NPT>(C, Zs, nc, RW, ns[1]);
+                __syncthreads();
+                colour_step<R, NPT>(C, Zs, nc, RW, ns[2]);
+                __syncthreads();
+                colour_step<R, NPT>(C, Zs, nc, RW, ns[1]);
+                __syncthreads();
             }
+            colour_step<R, NPT>(C, Zs, nc, RW, ns[0]);
             __syncthreads();
         }
 
