@@ -135,7 +135,7 @@ size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov, int nstage) {
 // every other shape uses the runtime-geometry instantiation.
 template <typename R, int NPT, typename F>
 static cudaError_t with_schwarz(int tx, int ty, int ov, F f) {
-    if (NPT == 1 && tx == 32 && ty == 32 && ov == 0) return f(k_schwarz<R, NPT, 32, 32, 0>);
+    if (NPT == 2 && tx == 32 && ty == 32 && ov == 0) return f(k_schwarz<R, NPT, 32, 32, 0>);
     if (NPT == 2 && tx == 48 && ty == 48 && ov == 0) return f(k_schwarz<R, NPT, 48, 48, 0>);
     return f(k_schwarz<R, NPT, 0, 0, 0>);
 }
@@ -195,7 +195,10 @@ bool schwarz_node_table(int fp64, int Tx, int Ty, int ov, std::vector<uint32_t>&
             for (size_t k = 0; k < bucket[b].size(); ++k) slots[c][k / per][b + nbank * (k % per)] = bucket[b][k];
         maxslots = std::max(maxslots, (int)slots[c].size());
     }
-    const int nwarps = std::min(sch_max_threads(fp64 != 0) / 32, maxslots);
+    // two nodes per thread and colour (independent updates in flight), as
+    // many warps as that needs, at most the CTA cap
+    int nwarps = (maxslots + 1) / 2;
+    nwarps = std::min(std::max(nwarps, 1), sch_max_threads(fp64 != 0) / 32);
     npt = (maxslots + nwarps - 1) / nwarps;
     if (npt > 2) return false;
     threads = 32 * nwarps;

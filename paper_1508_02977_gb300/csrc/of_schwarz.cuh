@@ -339,42 +339,35 @@ __host__ __device__ constexpr int sch_max_threads(bool fp64) { return fp64 ? 384
 
 // Per-node sweep state kept in registers by the owning thread.
 template <typename R> struct NodeState {
-    int c;            // cell index, -1: no node
-    R lE, lN, lW, lS; // lambda weights of the four legs
+    int c;            // cell index (low 24 bits; -1: no node) | triangles on the E,N,W,S legs (2 bits each)
     R b0, b1, b2;     // right-hand side
     Blk<R> B;         // LDL^T factors of the diagonal block
 };
 
-// Block update of every node of one colour that this thread owns.
-template <typename R, int NPT>
-__device__ __forceinline__ void colour_step(const CellView<R>& C, R* Zs, int nc, int RW, const NodeState<R> (&ns)[NPT]) {
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-        const NodeState<R>& n = ns[k];
-        if (n.c < 0) continue;
-        node_sweep<R>(C, Zs, nc, n.c, RW, n.lE, n.lN, n.lW, n.lS, n.B, n.b0, n.b1, n.b2);
-    }
+template <typename R>
+__device__ __forceinline__ void node_step(const CellView<R>& C, R* Zs, int nc, int RW, R hl, const NodeState<R>& n) {
+    if (n.c == -1) return;
+    const int c = n.c & 0xffffff;
+    const unsigned nb = (unsigned)n.c >> 24;
+    node_sweep<R>(C, Zs, nc, c, RW, hl * R(nb & 3u), hl * R((nb >> 2) & 3u), hl * R((nb >> 4) & 3u),
+                  hl * R(nb >> 6), n.B, n.b0, n.b1, n.b2);
 }
 
 // Block Jacobi: z = D^{-1} r, no neighbour terms.
-template <typename R, int NPT>
-__device__ __forceinline__ void jacobi_step(R* Zs, int nc, const NodeState<R> (&ns)[NPT]) {
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-        const NodeState<R>& n = ns[k];
-        if (n.c < 0) continue;
-        const Blk<R>& B = n.B;
-        const R y1 = n.b1 - B.l10 * n.b0, y2 = n.b2 - B.l20 * n.b0 - B.l21 * y1;
-        const R x2 = y2 * B.i2, x1 = y1 * B.i1 - B.l21 * x2, x0 = n.b0 * B.i0 - B.l10 * x1 - B.l20 * x2;
-        Zs[n.c] = x0;
-        Zs[n.c + nc] = x1;
-        Zs[n.c + 2 * nc] = x2;
-    }
+template <typename R>
+__device__ __forceinline__ void node_jacobi(R* Zs, int nc, const NodeState<R>& n) {
+    if (n.c == -1) return;
+    const int c = n.c & 0xffffff;
+    const Blk<R>& B = n.B;
+    const R y1 = n.b1 - B.l10 * n.b0, y2 = n.b2 - B.l20 * n.b0 - B.l21 * y1;
+    const R x2 = y2 * B.i2, x1 = y1 * B.i1 - B.l21 * x2, x0 = n.b0 * B.i0 - B.l10 * x1 - B.l20 * x2;
+    Zs[c] = x0;
+    Zs[c + nc] = x1;
+    Zs[c + 2 * nc] = x2;
 }
 
 template <typename R, int NPT, int TXC, int TYC, int OVC>
-__global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 8 ? 1 : 2)
-    k_schwarz(const SchwarzParams P) {
+__global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(const SchwarzParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ double sh_red[32];
     __shared__ int sh_last, sh_fail;
@@ -485,22 +478,18 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 
                 NodeState<R>& n = ns[col][k];
                 n.c = -1;
                 n.b0 = n.b1 = n.b2 = R(0);
-                n.lE = n.lN = n.lW = n.lS = R(0);
                 n.B = Blk<R>{R(0), R(0), R(0), R(0), R(0), R(0)};
                 if (e == 0xffffffffu) continue;
                 const int li = (int)(e & 0xffffu), lj = (int)(e >> 16);
                 const int gx = x0 - ov + li, gy = y0 - ov + lj;
                 if (gx < ex0 || gx >= ex1 || gy < ey0 || gy >= ey1) continue;
                 const int c = (lj + 1) * RW + (li + cpad - ov);
-                // existing triangles on the four legs: 1/2 lambda each
-                const R vc = (gx < W - 1 && gy < H - 1) ? hl : R(0), vsw = (gx >= 1 && gy >= 1) ? hl : R(0);
-                const R vw = (gx >= 1 && gy < H - 1) ? hl : R(0), vs = (gx < W - 1 && gy >= 1) ? hl : R(0);
-                n.c = c;
-                n.lE = vc + vs;
-                n.lN = vc + vw;
-                n.lW = vsw + vw;
-                n.lS = vsw + vs;
-                node_block<R>(C, c, RW, n.lE, n.lN, n.lW, n.lS, n.B);
+                // existing triangles on the four legs (the lambda weight is 1/2 lambda each)
+                const int vc = (gx < W - 1 && gy < H - 1), vsw = (gx >= 1 && gy >= 1);
+                const int vw = (gx >= 1 && gy < H - 1), vs = (gx < W - 1 && gy >= 1);
+                const int nE = vc + vs, nN = vc + vw, nW = vsw + vw, nS = vsw + vs;
+                n.c = c | (nE << 24) | (nN << 26) | (nW << 28) | (nS << 30);
+                node_block<R>(C, c, RW, hl * R(nE), hl * R(nN), hl * R(nW), hl * R(nS), n.B);
                 if (gx >= x0 && gx < x0 + tw && gy >= y0 && gy < y0 + th) {
                     const int si = (gy - y0) * Tx + (gx - x0);
                     R v0 = Rs[si], v1 = Rs[si + Tx * Ty], v2 = Rs[si + 2 * Tx * Ty];
@@ -522,48 +511,52 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), sizeof(R) == 
         __syncthreads();
 
         // ---- sweeps (colour order 0,1,2,1,0,1,2,1,0,...; sweeps = 0: block Jacobi)
+#define OF_STEP(col)                                                 \
+    {                                                                \
+        _Pragma("unroll") for (int k = 0; k < NPT; ++k)              \
+            node_step<R>(C, Zs, nc, RW, hl, ns[col][k]);             \
+        __syncthreads();                                             \
+    }
         if (P.sweeps == 0) {
-            jacobi_step<R, NPT>(Zs, nc, ns[0]);
-            jacobi_step<R, NPT>(Zs, nc, ns[1]);
-            jacobi_step<R, NPT>(Zs, nc, ns[2]);
+#pragma unroll
+            for (int col = 0; col < 3; ++col)
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) node_jacobi<R>(Zs, nc, ns[col][k]);
             __syncthreads();
         } else {
             for (int sw = 0; sw < P.sweeps; ++sw) {
-                colour_step<R, NPT>(C, Zs, nc, RW, ns[0]);
-                __syncthreads();
-                colour_step<R, NPT>(C, Zs, nc, RW, ns[1]);
-                __syncthreads();
-                colour_step<R, NPT>(C, Zs, nc, RW, ns[2]);
-                __syncthreads();
-                colour_step<R, NPT>(C, Zs, nc, RW, ns[1]);
-                __syncthreads();
+                OF_STEP(0)
+                OF_STEP(1)
+                OF_STEP(2)
+                OF_STEP(1)
             }
-            colour_step<R, NPT>(C, Zs, nc, RW, ns[0]);
-            __syncthreads();
+            OF_STEP(0)
         }
+#undef OF_STEP
 
         // ---- write-out of the owned tile (coalesced), partials r.r and r.z
         R* zg = reinterpret_cast<R*>(P.z) + pd.vec_off;
         R* rg = reinterpret_cast<R*>(P.r) + pd.vec_off;
         R rr = R(0), rz = R(0);
-        const int ntile = tw * th;
-        for (int k = threadIdx.x; k < ntile; k += NT) {
-            const int j = k / tw, i = k - j * tw;
-            const int si = j * Tx + i;
-            const int c = (j + ov + 1) * RW + (i + cpad);
-            const R v0 = Zs[c], v1 = Zs[c + nc], v2 = Zs[c + 2 * nc];
-            const R r0 = Rs[si], r1 = Rs[si + Tx * Ty], r2 = Rs[si + 2 * Tx * Ty];
-            const long long o = (long long)(y0 + j) * pitch + (x0 + i);
-            zg[o] = v0;
-            zg[o + plane] = v1;
-            zg[o + 2 * plane] = v2;
-            if (need_q) {
-                rg[o] = r0;
-                rg[o + plane] = r1;
-                rg[o + 2 * plane] = r2;
+        const int nwarps = NT >> 5, lane = threadIdx.x & 31;
+        for (int j = threadIdx.x >> 5; j < th; j += nwarps) {
+            for (int i = lane; i < tw; i += 32) {
+                const int si = j * Tx + i;
+                const int c = (j + ov + 1) * RW + (i + cpad);
+                const R v0 = Zs[c], v1 = Zs[c + nc], v2 = Zs[c + 2 * nc];
+                const R r0 = Rs[si], r1 = Rs[si + Tx * Ty], r2 = Rs[si + 2 * Tx * Ty];
+                const long long o = (long long)(y0 + j) * pitch + (x0 + i);
+                zg[o] = v0;
+                zg[o + plane] = v1;
+                zg[o + 2 * plane] = v2;
+                if (need_q) {
+                    rg[o] = r0;
+                    rg[o + plane] = r1;
+                    rg[o + 2 * plane] = r2;
+                }
+                rr += r0 * r0 + r1 * r1 + r2 * r2;
+                rz += r0 * v0 + r1 * v1 + r2 * v2;
             }
-            rr += r0 * r0 + r1 * r1 + r2 * r2;
-            rz += r0 * v0 + r1 * v1 + r2 * v2;
         }
         if (!P.apply_only) {
             const double s_rr = block_sum_rt((double)rr, sh_red);
