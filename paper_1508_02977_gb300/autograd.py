@@ -1,0 +1,86 @@
+"""torch.autograd.Function over of_solve / of_adjoint.
+
+    U = ofsolve_fn(f1, f2, alpha, solver)
+
+U solves the P1 system of Section 2.2 for one frame pair; backward solves
+the adjoint system (the operator is symmetric, so it is the same solve with
+dL/dU as right-hand side) and forms dL/dalpha per element and dL/df1,
+dL/df2 per pixel in the CUDA library.  Only marshalling happens here.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import ofsolve as S
+
+
+class Solver:
+    """A handle set up for frames of one size (W, H), kept between calls."""
+
+    def __init__(self, W: int, H: int, device: int = 0, precision: int = S.OF_PREC_MIXED, tile=(48, 48),
+                 overlap: int = 0, sweeps: int = 2, lam: float = 1.0, rtol: float = 1e-6):
+        self.W, self.H, self.rtol = int(W), int(H), float(rtol)
+        self.precision = precision
+        self.h = S.of_create(device)
+        S.of_setup_grid(self.h, [(self.W, self.H)], tile=tile, overlap=overlap, sweeps=sweeps,
+                        precision=precision, lam=lam)
+
+    def close(self):
+        if self.h is not None:
+            S.of_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class OFSolve(torch.autograd.Function):
+    """U = A(f1, f2, alpha)^{-1} b(f1, f2): forward of_solve, backward
+    of_adjoint (implicit differentiation)."""
+
+    @staticmethod
+    def forward(ctx, f1, f2, alpha, solver: Solver):
+        dt = torch.float64 if solver.precision == S.OF_PREC_FP64 else torch.float32
+        f1c = f1.detach().to(dt).contiguous()
+        f2c = f2.detach().to(dt).contiguous()
+        S.of_set_frames(solver.h, 0, f1c, f2c)
+        S.of_set_alpha(solver.h, 0, alpha.detach().to(dt).contiguous())
+        U = torch.zeros(3, solver.H, solver.W, dtype=torch.float64, device=f1.device)
+        S.of_solve(solver.h, [U], rtol=solver.rtol)
+        ctx.solver = solver
+        ctx.in_dtypes = (f1.dtype, f2.dtype, alpha.dtype)
+        # the handle keeps only its last solve: backward re-solves if another
+        # forward used the same solver in between
+        solver._token = object()
+        ctx.token = solver._token
+        ctx.save_for_backward(f1c, f2c, alpha.detach().to(dt).contiguous())
+        return U.to(f1.dtype)
+
+    @staticmethod
+    def backward(ctx, gU):
+        solver = ctx.solver
+        dev = gU.device
+        if getattr(solver, "_token", None) is not ctx.token:
+            f1c, f2c, ac = ctx.saved_tensors
+            S.of_set_frames(solver.h, 0, f1c, f2c)
+            S.of_set_alpha(solver.h, 0, ac)
+            U = torch.zeros(3, solver.H, solver.W, dtype=torch.float64, device=dev)
+            S.of_solve(solver.h, [U], rtol=solver.rtol)
+            solver._token = ctx.token
+        gU = gU.detach().to(torch.float64).contiguous()
+        da = torch.zeros(solver.H - 1, solver.W - 1, 2, dtype=torch.float64, device=dev)
+        d2 = torch.zeros(solver.H, solver.W, dtype=torch.float64, device=dev)
+        d1 = torch.zeros_like(d2)
+        need = ctx.needs_input_grad
+        S.of_adjoint(solver.h, [gU], [da] if need[2] else None, [d2] if need[1] else None,
+                     [d1] if need[0] else None)
+        t1, t2, ta = ctx.in_dtypes
+        return (d1.to(t1) if need[0] else None, d2.to(t2) if need[1] else None,
+                da.to(ta) if need[2] else None, None)
+
+
+def ofsolve_fn(f1, f2, alpha, solver: Solver):
+    return OFSolve.apply(f1, f2, alpha, solver)

@@ -455,3 +455,31 @@ def test_adjoint_matches_oracle_and_differences(S, oracle):
         fm[y, x] -= h_fd
         fd = (loss(f1, fp, alpha) - loss(f1, fm, alpha)) / (2 * h_fd)
         assert abs(fd - d2[y, x]) <= 1e-5 * np.abs(d2).max()
+
+
+def test_autograd_function_matches_oracle_gradients(S, oracle):
+    """torch.autograd through OFSolve (FP64 handle): gradients of the mean
+    endpoint error w.r.t. alpha, f2 and f1 equal the oracle's adjoint."""
+    from paper_1508_02977_gb300.autograd import Solver, ofsolve_fn
+    W, H = 30, 22
+    f1, f2 = synth.random_frames(W, H, 301)
+    alpha = synth.random_alpha(W, H, 302)
+    gt = np.random.default_rng(303).uniform(-1, 1, (2, H, W))
+    solver = Solver(W, H, precision=S.OF_PREC_FP64, tile=(16, 16), sweeps=1, rtol=1e-14)
+    try:
+        t1 = dev(f1).requires_grad_(True)
+        t2 = dev(f2).requires_grad_(True)
+        ta = dev(alpha).requires_grad_(True)
+        U = ofsolve_fn(t1, t2, ta, solver)
+        d = U[:2] - dev(gt)
+        loss = torch.sqrt(d[0] ** 2 + d[1] ** 2).mean()
+        loss.backward()
+    finally:
+        solver.close()
+    sysm = oracle.System.from_frames(f1, f2, alpha, 1.0)
+    Uo = sysm.solve_direct()
+    Lo = sysm.solve_with(oracle.mean_epe_grad(Uo, gt))
+    da, d2, d1 = oracle.adjoint_grad(f1, f2, alpha, 1.0, Uo, Lo)
+    for got, want in ((ta.grad, da), (t2.grad, d2), (t1.grad, d1)):
+        got = got.cpu().numpy()
+        assert np.abs(got - want).max() <= 1e-8 * np.abs(want).max()
