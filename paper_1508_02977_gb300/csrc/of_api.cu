@@ -365,7 +365,9 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
     for (int pass = 0;; ++pass) {
         const int first = (pass == 0);
         double* xout = first ? nullptr : h->x[1 - cur];
-        CK(timed(h, 2, [&] { return ofl::launch_residual(B, h->x[cur], xout, rhs, first, o.rtol, o.inner_rtol, o.max_inner, st); }));
+        // a cold start (x = 0) needs only the load vector for its first residual
+        const double* xin = (first && !o.warm_start) ? nullptr : h->x[cur];
+        CK(timed(h, 2, [&] { return ofl::launch_residual(B, xin, xout, rhs, first, o.rtol, o.inner_rtol, o.max_inner, st); }));
         if (!first) cur = 1 - cur;
         if (pass == o.max_outer) {
             CK(cudaMemcpyAsync(h->sc_host, h->sc_dev, sizeof(PairScalars) * h->batch, cudaMemcpyDeviceToHost, st));
@@ -752,6 +754,7 @@ of_status of_adjoint(of_handle h, void* const* dLdU, void* const* dLdalpha, void
         CK(cudaMemsetAsync(h->x[0] + d.vec_off, 0, 3ULL * d.H * d.pitch * sizeof(double), st));
     }
     of_solve_opts opt = h->last_opts;
+    opt.warm_start = 0;  // the adjoint state starts from zero
     int cur = 0;
     std::vector<int> passes;
     of_status s = run_solve(h, opt, h->cvec, &cur, passes);

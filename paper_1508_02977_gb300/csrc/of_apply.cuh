@@ -21,7 +21,8 @@
 
 namespace ofk {
 
-enum { MODE_APPLY = 0, MODE_PCG = 1, MODE_RES = 2 };
+enum { MODE_APPLY = 0, MODE_PCG = 1, MODE_RES = 2, MODE_RESB = 3 };
+// MODE_RESB: MODE_RES for x = 0 (cold start): r = rhs, only the load is formed.
 
 template <typename R> struct V3 { R a, b, c; };
 template <typename R> __device__ __forceinline__ V3<R> v3(R a, R b, R c) { V3<R> v; v.a = a; v.b = b; v.c = c; return v; }
@@ -33,7 +34,7 @@ template <typename R> struct NodeVal { V3<R> p; R f1, f2; };
 // Contributions of the two triangles of one square to its corners
 // A=(x,y) B=(x+1,y) C=(x+1,y+1) D=(x,y+1): sign * (A_K p)_i, and, when WANT_B,
 // the load -|K|/3 ft g of each triangle (same for its 3 vertices).
-template <typename R, bool WANT_B>
+template <typename R, bool WANT_B, bool WANT_A = true>
 __device__ __forceinline__ void square_contrib(const NodeVal<R>& A, const NodeVal<R>& B, const NodeVal<R>& C,
                                                const NodeVal<R>& D, R al0, R al1, R lam, bool valid,
                                                V3<R>& cA, V3<R>& cB, V3<R>& cC, V3<R>& cD,
@@ -43,13 +44,16 @@ __device__ __forceinline__ void square_contrib(const NodeVal<R>& A, const NodeVa
     const R h = R(OF_STIFF_HALF);
     // ---- t = 0: A, B, C
     R g0x = B.f2 - A.f2, g0y = C.f2 - B.f2, g0m = -(A.f1 + B.f1 + C.f1) * third;
+    R g1x = C.f2 - D.f2, g1y = D.f2 - A.f2, g1m = -(A.f1 + D.f1 + C.f1) * third;
+    if constexpr (!WANT_A) {
+        cA = cB = cC = cD = v3(R(0), R(0), R(0));
+    } else {
     R sA = g0x * A.p.a + g0y * A.p.b + g0m * A.p.c;
     R sB = g0x * B.p.a + g0y * B.p.b + g0m * B.p.c;
     R sC = g0x * C.p.a + g0y * C.p.b + g0m * C.p.c;
     R S0 = sA + sB + sC;
     R wA = (sA + S0) * w24, wB = (sB + S0) * w24, wC = (sC + S0) * w24;
     // ---- t = 1: A, D, C
-    R g1x = C.f2 - D.f2, g1y = D.f2 - A.f2, g1m = -(A.f1 + D.f1 + C.f1) * third;
     R tA = g1x * A.p.a + g1y * A.p.b + g1m * A.p.c;
     R tD = g1x * D.p.a + g1y * D.p.b + g1m * D.p.c;
     R tC = g1x * C.p.a + g1y * C.p.b + g1m * C.p.c;
@@ -73,6 +77,7 @@ __device__ __forceinline__ void square_contrib(const NodeVal<R>& A, const NodeVa
     cD.a = vD * g1x - a1 * (dAD.a + dCD.a);
     cD.b = vD * g1y - a1 * (dAD.b + dCD.b);
     cD.c = vD * g1m - l0 * (dAD.c + dCD.c);
+    }
     if (WANT_B) {
         const R sixth = R(1) / R(6);
         R ft0 = ((A.f2 - A.f1) + (B.f2 - B.f1) + (C.f2 - C.f1)) * third;
@@ -139,6 +144,7 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
         corr = !P.first && it > 0;
         a_prev = corr ? (R)P.sc_in[pair].a : R(0);
     }
+    constexpr bool IS_RES = (MODE == MODE_RES) || (MODE == MODE_RESB);
 
     const C* f1 = P.f1 + pd.frame_off;
     const C* f2 = P.f2 + pd.frame_off;
@@ -171,6 +177,10 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
         const long long o = (long long)y * pitch + x;
         v.f1 = (R)f1[o];
         v.f2 = (R)f2[o];
+        if (MODE == MODE_RESB) {
+            v.p = v3(R(0), R(0), R(0));
+            return v;
+        }
         R p0 = vin[o], p1 = vin[o + plane], p2 = vin[o + 2 * plane];
         if (MODE == MODE_PCG) {
             if (!P.first) {
@@ -227,12 +237,12 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
         const R al0 = valid ? (R)al[2 * ((long long)sy * pitch + cx)] : R(0);
         const R al1 = valid ? (R)al[2 * ((long long)sy * pitch + cx) + 1] : R(0);
         V3<R> cA, cB, cC, cD, bA, bB, bC, bD;
-        square_contrib<R, WANT_B || (MODE == MODE_RES)>(cur, ncur, nnxt, nxt, al0, al1, lam, valid,
-                                                         cA, cB, cC, cD, bA, bB, bC, bD);
+        square_contrib<R, WANT_B || IS_RES, MODE != MODE_RESB>(cur, ncur, nnxt, nxt, al0, al1, lam, valid, cA, cB,
+                                                                  cC, cD, bA, bB, bC, bD);
         V3<R> left = shfl_down3(cA);
         V3<R> res = carry + cB + left;  // node (cx+1, sy) complete
         V3<R> resb;
-        constexpr bool NEED_B = WANT_B || (MODE == MODE_RES);
+        constexpr bool NEED_B = WANT_B || IS_RES;
         if (NEED_B) resb = carry_b + bB + shfl_down3(bA);
         if (sy >= Y0 && out_col) {
             const long long o = (long long)sy * pitch + (cx + 1);
@@ -245,7 +255,7 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
                     bo[o] = resb.a; bo[o + plane] = resb.b; bo[o + 2 * plane] = resb.c;
                 }
             }
-            if (MODE == MODE_RES) {
+            if (IS_RES) {
                 V3<R> rhs;
                 if (P.rhs_vec) {
                     const R* c = P.rhs_vec + vo;
@@ -269,14 +279,14 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
     if (MODE == MODE_APPLY) return;
     // ---- block partials and last-block reduction of the pair
     double s0 = block_sum<NT>((MODE == MODE_PCG) ? (double)acc : accd, sh_red);
-    double s1 = (MODE == MODE_RES) ? block_sum<NT>(acc_b, sh_red) : 0.0;
+    double s1 = IS_RES ? block_sum<NT>(acc_b, sh_red) : 0.0;
     if (threadIdx.x == 0) {
         P.partial[2 * (long long)bi.w] = s0;
         P.partial[2 * (long long)bi.w + 1] = s1;
     }
     if (!arrive_last(&P.counter[pair], (unsigned)pd.nblk, &sh_last)) return;
     double t0 = ordered_sum<NT>(P.partial + 2 * (long long)pd.blk0, pd.nblk, 2, sh_red);
-    double t1 = (MODE == MODE_RES) ? ordered_sum<NT>(P.partial + 2 * (long long)pd.blk0 + 1, pd.nblk, 2, sh_red) : 0.0;
+    double t1 = IS_RES ? ordered_sum<NT>(P.partial + 2 * (long long)pd.blk0 + 1, pd.nblk, 2, sh_red) : 0.0;
     if (threadIdx.x == 0) {
         PairScalars* s = P.sc + pair;
         if (MODE == MODE_PCG) {
@@ -290,7 +300,7 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
             }
         } else {  // MODE_RES: set up the inner pass
             s->res2 = t0;
-            if (P.first) s->bnorm2 = t1;
+            if (P.first || MODE == MODE_RESB) s->bnorm2 = t1;
             const double b2 = s->bnorm2;
             const bool conv = (t0 <= P.rtol * P.rtol * b2) || (t0 == 0.0);
             double rel = 0.5 * P.rtol * sqrt(b2 / (t0 > 0.0 ? t0 : 1.0));

@@ -92,7 +92,8 @@ static cudaError_t residual_t(const SolveBufs& B, const double* xin, double* xou
     P.rtol = rtol;
     P.inner_rtol = inner_rtol;
     P.max_inner = max_inner;
-    k_apply<double, C, RI, MODE_RES, false, APPLY_NW><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+    if (xin) k_apply<double, C, RI, MODE_RES, false, APPLY_NW><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+    else k_apply<double, C, RI, MODE_RESB, false, APPLY_NW><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
     return cudaGetLastError();
 }
 

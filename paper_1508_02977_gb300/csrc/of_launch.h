@@ -50,7 +50,8 @@ struct SolveBufs {
 };
 
 // Pass start: xout = xin + d + a p (unless first), r = rhs - A xout,
-// ||r||^2, ||rhs||^2 (first) and the inner-pass set-up per pair.
+// ||r||^2, ||rhs||^2 (first) and the inner-pass set-up per pair.  xin = NULL
+// means x = 0 (cold start): r = rhs, only the load is formed.
 cudaError_t launch_residual(const SolveBufs& B, const double* xin, double* xout, const double* rhs_vec, int first,
                             double rtol, double inner_rtol, int max_inner, cudaStream_t st);
 // z = M r at the start of a pass (rz, rr, convergence check).
