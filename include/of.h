@@ -171,19 +171,21 @@ of_status of_precondition(of_handle h, int pair, const void *r, void *z, of_dtyp
  * ([3][H][W], dtype dt), computed on the device in FP64.  Synchronises. */
 of_status of_residual(of_handle h, int pair, const void *U, of_dtype dt, double *rel_residual);
 
-/* Kernel timing of the solve path, for measurement.  When enabled, every
- * kernel launch of of_solve / of_adjoint / of_adapt_alpha is counted, and the
+/* Kernel counts and timing of the solve path, for measurement.  Every kernel
+ * launch of of_solve / of_adjoint / of_adapt_alpha is counted (inside the
+ * inner-loop CUDA graph, from the iteration count); with profiling on, the
+ * inner loop is launched kernel by kernel instead of as the graph and the
  * launches of the three solve kernels are bracketed by CUDA events on the
- * handle's stream; the totals accumulate until read.  Index 0: PCG apply
- * (p, d, q and p.q), 1: Schwarz preconditioner (r, z, r.r, r.z), 2: FP64
- * residual / refinement, 3: every other kernel (copies, indicator, alpha
- * update, adjoint gradients; counted, not timed). */
+ * handle's stream.  Totals accumulate until read.  Index 0: PCG apply (p, d,
+ * q and p.q), 1: Schwarz preconditioner (r, z, r.r, r.z), 2: FP64 residual /
+ * refinement, 3: every other kernel (copies, element records, indicator,
+ * alpha update, adjoint gradients; counted, not timed). */
 typedef struct {
     int launches[4];
     double ms[4];
 } of_profile;
 
-/* Turns kernel timing on (1) or off (0); turning it on clears the totals. */
+/* Turns kernel timing on (1) or off (0); either call clears the totals. */
 of_status of_set_profiling(of_handle h, int on);
 
 /* Copies the accumulated totals out and clears them. */

@@ -45,6 +45,10 @@ struct of_ctx {
     int sch_threads = 0, sch_npt = 1, sch_grid = 1, sch_nstage = 2;
     void *cell0 = nullptr, *cell1 = nullptr;  // preconditioner element records [H][pitch]
     bool cells_dirty = true;
+    // inner PCG loop as a CUDA graph: while(any pair iterating) { apply; Schwarz }
+    cudaGraph_t loop_graph = nullptr;
+    cudaGraphExec_t loop_exec = nullptr;
+    cudaGraphConditionalHandle loop_cond = 0;
     PairScalars* sc_dev = nullptr;
     PairScalars* sc_host = nullptr;  // pinned
     double *partA = nullptr, *partS = nullptr, *etamax = nullptr;
@@ -120,6 +124,10 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 void free_all(of_ctx* h) {
+    if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
+    if (h->loop_graph) cudaGraphDestroy(h->loop_graph);
+    h->loop_exec = nullptr;
+    h->loop_graph = nullptr;
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
     if (h->sc_host) cudaFreeHost(h->sc_host);
@@ -155,7 +163,10 @@ cudaEvent_t pool_event(of_ctx* h) {
 // Launch `fn` (returns cudaError_t), bracketed by events when profiling.
 template <typename F>
 cudaError_t timed(of_ctx* h, int kind, F fn) {
-    if (!h->prof) return fn();
+    if (!h->prof) {
+        h->ptot.launches[kind] += 1;  // launches are counted always, timed only when profiling
+        return fn();
+    }
     cudaEvent_t a = pool_event(h), b = pool_event(h);
     cudaEventRecord(a, h->stream);
     cudaError_t e = fn();
@@ -164,9 +175,7 @@ cudaError_t timed(of_ctx* h, int kind, F fn) {
     return e;
 }
 
-void count_other(of_ctx* h, int n) {
-    if (h->prof) h->ptot.launches[3] += n;
-}
+void count_other(of_ctx* h, int n) { h->ptot.launches[3] += n; }
 
 // Accumulates recorded launches (the stream must have passed them).
 void prof_flush(of_ctx* h) {
@@ -333,6 +342,55 @@ of_status encode_maps(of_ctx* h) {
     return OF_OK;
 }
 
+// Builds the inner-loop graph: a while-node whose body is one PCG iteration
+// (apply, then Schwarz); the Schwarz kernel's last CTA sets the condition
+// once no pair is iterating.  Returns false (and leaves no graph) if the
+// driver cannot build it; the solve then polls from the host.
+bool build_loop_graph(of_ctx* h) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+    ok = ok && cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    alignas(cudaGraphNodeParams) unsigned char cp_buf[sizeof(cudaGraphNodeParams)] = {};
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_buf);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    ok = ok && cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ok = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+             cudaSuccess;
+        if (ok) {
+            ofl::SolveBufs B = solve_bufs(h);
+            B.use_cond = 1;
+            B.cond = cond;
+            cudaError_t e1 = ofl::launch_pcg_apply(B, cs);
+            cudaError_t e2 = ofl::launch_pcg_precond(B, cs);
+            cudaGraph_t out = nullptr;
+            cudaError_t e3 = cudaStreamEndCapture(cs, &out);
+            ok = e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess;
+        }
+    }
+    ok = ok && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (cs) cudaStreamDestroy(cs);
+    if (!ok) {
+        if (ex) cudaGraphExecDestroy(ex);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return false;
+    }
+    h->loop_graph = g;
+    h->loop_exec = ex;
+    h->loop_cond = cond;
+    return true;
+}
+
 // Recomputes the preconditioner's element records if frames or alpha changed.
 of_status refresh_cells(of_ctx* h) {
     if (!h->cells_dirty) return OF_OK;
@@ -375,18 +433,29 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
             break;
         }
         CK(timed(h, 1, [&] { return ofl::launch_precond_first(B, st); }));
-        int it = 0;
-        bool all_done = false;
-        while (!all_done) {
-            for (int c = 0; c < chunk; ++c, ++it) {
-                CK(timed(h, 0, [&] { return ofl::launch_pcg_apply(B, it == 0, st); }));
-                CK(timed(h, 1, [&] { return ofl::launch_pcg_precond(B, st); }));
-            }
+        if (h->loop_exec && !h->prof) {
+            // the whole inner loop on the device; one read-back per pass
+            CK(cudaGraphLaunch(h->loop_exec, st));
             CK(cudaMemcpyAsync(h->sc_host, h->sc_dev, sizeof(PairScalars) * h->batch, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            all_done = true;
-            for (int p = 0; p < h->batch; ++p) all_done = all_done && h->sc_host[p].done;
-            if (it >= o.max_inner + chunk) all_done = true;
+            int body = 0;  // loop iterations = the most iterations any pair took in this pass
+            for (int p = 0; p < h->batch; ++p) body = std::max(body, h->sc_host[p].it);
+            h->ptot.launches[0] += body;
+            h->ptot.launches[1] += body;
+        } else {
+            int it = 0;
+            bool all_done = false;
+            while (!all_done) {
+                for (int c = 0; c < chunk; ++c, ++it) {
+                    CK(timed(h, 0, [&] { return ofl::launch_pcg_apply(B, st); }));
+                    CK(timed(h, 1, [&] { return ofl::launch_pcg_precond(B, st); }));
+                }
+                CK(cudaMemcpyAsync(h->sc_host, h->sc_dev, sizeof(PairScalars) * h->batch, cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                all_done = true;
+                for (int p = 0; p < h->batch; ++p) all_done = all_done && h->sc_host[p].done;
+                if (it >= o.max_inner + chunk) all_done = true;
+            }
         }
         bool all_conv = true;
         for (int p = 0; p < h->batch; ++p) {
@@ -607,6 +676,7 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     h->alpha_set.assign(batch, 0);
     h->solved = false;
     CK(cudaStreamSynchronize(st));
+    build_loop_graph(h);
     return OF_OK;
 }
 

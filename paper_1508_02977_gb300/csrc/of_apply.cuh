@@ -113,7 +113,7 @@ struct ApplyParams {
     RI* rout;           // RES: r (inner precision)
     R* bout;            // APPLY: optional b
     const R* rhs_vec;   // RES: rhs vector instead of the frame load (adjoint), or null
-    int first;          // PCG: first iteration of a pass (p = z, d = 0);  RES: no correction
+    int first;          // RES: first residual of a solve (no correction, ||b|| formed)
     double rtol, inner_rtol;
     int max_inner;
 };
@@ -133,11 +133,13 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
     R a_prev = R(0);
     int it = 0;
     bool corr = false;  // RES: fold the inner correction d + a p into x
+    bool pcg_first = false;  // PCG: first iteration of a pass (p = z, d = 0)
     if (MODE == MODE_PCG) {
         if (P.sc_in[pair].done) return;  // uniform over the pair's blocks
         beta = (R)P.sc_in[pair].beta;
         a_prev = (R)P.sc_in[pair].a;
         it = P.sc_in[pair].it;
+        pcg_first = (it == 0);
     }
     if (MODE == MODE_RES) {
         it = P.sc_in[pair].it;
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
         }
         R p0 = vin[o], p1 = vin[o + plane], p2 = vin[o + 2 * plane];
         if (MODE == MODE_PCG) {
-            if (!P.first) {
+            if (!pcg_first) {
                 R q0 = pold[o], q1 = pold[o + plane], q2 = pold[o + 2 * plane];
                 if (owner) {
                     RI* d = P.dcorr + vo;

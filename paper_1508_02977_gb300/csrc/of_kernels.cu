@@ -125,6 +125,8 @@ static SchwarzParams schwarz_params(const SolveBufs& B) {
     S.sweeps = B.sweeps;
     S.nstage = B.sch_nstage;
     S.spin_limit = B.spin_limit;
+    S.use_cond = B.use_cond;
+    S.cond = B.cond;
     return S;
 }
 
@@ -232,20 +234,19 @@ cudaError_t launch_precond_first(const SolveBufs& B, cudaStream_t st) {
 }
 
 template <typename R>
-static cudaError_t pcg_apply_t(const SolveBufs& B, int first, cudaStream_t st) {
+static cudaError_t pcg_apply_t(const SolveBufs& B, cudaStream_t st) {
     auto P = base_params<R, R, R>(B);
     P.in = (const R*)B.z;
     P.p_buf0 = (R*)B.p0;
     P.p_buf1 = (R*)B.p1;
     P.dcorr = (R*)B.d;
     P.out = (R*)B.q;
-    P.first = first;
     k_apply<R, R, R, MODE_PCG, false, APPLY_NW><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_apply(const SolveBufs& B, int first, cudaStream_t st) {
-    return B.fp64 ? pcg_apply_t<double>(B, first, st) : pcg_apply_t<float>(B, first, st);
+cudaError_t launch_pcg_apply(const SolveBufs& B, cudaStream_t st) {
+    return B.fp64 ? pcg_apply_t<double>(B, st) : pcg_apply_t<float>(B, st);
 }
 
 cudaError_t launch_pcg_precond(const SolveBufs& B, cudaStream_t st) {

@@ -47,6 +47,8 @@ struct SolveBufs {
     double lam;
     int fp64;            // 1: everything FP64; 0: FP32 inner with FP64 residual
     long long spin_limit;
+    int use_cond;        // Schwarz launches inside the inner-loop graph set its condition
+    cudaGraphConditionalHandle cond;
 };
 
 // Pass start: xout = xin + d + a p (unless first), r = rhs - A xout,
@@ -58,7 +60,7 @@ cudaError_t launch_residual(const SolveBufs& B, const double* xin, double* xout,
 cudaError_t launch_precond_first(const SolveBufs& B, cudaStream_t st);
 // One PCG iteration = launch_pcg_apply (p, d, q, a) then launch_pcg_precond
 // (r, z, rz, beta, stop).
-cudaError_t launch_pcg_apply(const SolveBufs& B, int first, cudaStream_t st);
+cudaError_t launch_pcg_apply(const SolveBufs& B, cudaStream_t st);
 cudaError_t launch_pcg_precond(const SolveBufs& B, cudaStream_t st);
 // Stand-alone operator apply (q = A p, optional b) in the inner precision
 // (fp64 = 0: FP32) or FP64 for one pair (blocks of that pair only).

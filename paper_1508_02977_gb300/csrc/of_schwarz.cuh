@@ -73,6 +73,8 @@ struct SchwarzParams {
     int apply_only;           // of_precondition: z = M r, no scalars
     int nstage;               // 2: the next item streams in during this one; 1: after it
     long long spin_limit;     // bounded mbarrier wait, in clock64 cycles
+    int use_cond;             // launched in the inner-loop graph: set its while condition
+    cudaGraphConditionalHandle cond;
 };
 
 // Cell grid of a subdomain: columns from cx0 = x0 - sch_cpad(o) (even, so
@@ -438,12 +440,13 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         }
         __syncthreads();
         if (sh_fail) {
-            // give the copies in flight a last chance to land before leaving
+            // give the copies in flight a last chance to land, then stop
+            // processing (the CTA still arrives below, so the launch ends)
             if (threadIdx.x == 0) {
                 mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit);
                 if (nstage == 2 && tn < P.ntiles) mbar_wait_phase_bounded(&bars[s ^ 1], phase[s ^ 1], P.spin_limit);
             }
-            return;
+            break;
         }
         if (!mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit)) atomicOr(P.err, 1);
         phase[s] ^= 1u;
@@ -605,6 +608,13 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        if (P.use_cond) {
+            // keep looping while a pair is still iterating and no wait ran out
+            int more = 0;
+            for (int pi = 0; pi < P.npairs; ++pi) more |= !P.sc[pi].done;
+            if (*(volatile int*)P.err) more = 0;
+            cudaGraphSetConditional(P.cond, more ? 1u : 0u);
+        }
         __threadfence();
         *P.counter = 0u;
     }
