@@ -125,6 +125,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, ws: int, device=None) -> float:
+    """The slowest rank's time (every rank gets it): the whole job ends when
+    the last rank does."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(px_per_rank: int, ws: int, steps: int, ms: float) -> float:
+    """Mpixel/s of the whole job: every rank solves its own pair each step."""
+    return ws * px_per_rank * steps / (ms / 1e3) / 1e6
+
+
 def workload_pair(rank: int, W=WORKLOAD_W, H=WORKLOAD_H):
     from paper_1508_02977_gb300 import synth
     return synth.layers(W, H, seed=synth.BASE_SEED + 3 + 1000 * rank)
@@ -238,13 +255,7 @@ def run_ours(args):
             fn()
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1), ws, dev)
 
     for _ in range(args.warmup):
         step(h, U)
@@ -257,7 +268,7 @@ def run_ours(args):
     ms = timed(lambda: step(h, U), args.steps)
     clocks = clk.stop()
     launches = sum(v["launches"] for v in S.of_get_profile(h).values())
-    value = ws * px * args.steps / (ms / 1e3) / 1e6
+    value = whole_job_value(px, ws, args.steps, ms)
     iters = [i["inner_iters"] for i in infos]
     relres = max(i["rel_residual"] for i in infos)
 
@@ -290,7 +301,7 @@ def run_ours(args):
     step(h, Uh, (f1h, f2h))
     infos.clear()
     ms_e2e = timed(lambda: step(h, Uh, (f1h, f2h)), args.steps)
-    e2e = {"value": ws * px * args.steps / (ms_e2e / 1e3) / 1e6, "unit": UNIT,
+    e2e = {"value": whole_job_value(px, ws, args.steps, ms_e2e), "unit": UNIT,
            "h2d_bytes_per_step": 2 * px * 4, "d2h_bytes_per_step": 3 * px * 4}
     S.of_destroy(h)
 

@@ -483,3 +483,83 @@ def test_autograd_function_matches_oracle_gradients(S, oracle):
     for got, want in ((ta.grad, da), (t2.grad, d2), (t1.grad, d1)):
         got = got.cpu().numpy()
         assert np.abs(got - want).max() <= 1e-8 * np.abs(want).max()
+
+
+@pytest.mark.slow
+def test_batched_mixed_sizes_64_pairs(S, oracle):
+    """64 layered pairs of seeded mixed sizes in one handle (one launch per
+    kernel for the whole batch): every pair's residual, recomputed by the
+    oracle, is <= 1e-6."""
+    sizes = synth.batch_sizes(64)
+    h = handle(S, sizes, tile=(48, 48), overlap=0, sweeps=3, precision=S.OF_PREC_MIXED)
+    pairs, Us = [], []
+    try:
+        for i, (W, H) in enumerate(sizes):
+            p = synth.layers(W, H, seed=(synth.BASE_SEED + 4) * 1000 + i)
+            pairs.append(p)
+            S.of_set_frames(h, i, dev(p.f1, torch.float32), dev(p.f2, torch.float32))
+            S.of_set_alpha(h, i, None, p.alpha0)
+            Us.append(torch.zeros(3, H, W, dtype=torch.float64, device="cuda"))
+        st, info = S.of_solve(h, Us)
+        Uh = [u.cpu().numpy() for u in Us]
+    finally:
+        S.of_destroy(h)
+    assert st == S.OF_OK
+    for p, U, inf in zip(pairs, Uh, info):
+        rr = oracle.rel_residual_frames(f32(p.f1), f32(p.f2), p.alpha0, p.lam, U)
+        assert rr <= 1e-6, (p.name, rr, inf)
+
+
+@pytest.mark.slow
+def test_adjoint_smooth_flow_512(S, oracle):
+    """Adjoint workload (8 pairs 512x512, smooth known flow, gain 1.1, mean
+    endpoint error): the FP64 GPU gradient of one pair against the oracle's
+    adjoint (PCG to 1e-13) and central differences on a few entries."""
+    p = synth.smooth(npairs=1)[0]
+    W, H = p.W, p.H
+    f1, f2 = p.f1.astype(np.float64), p.f2.astype(np.float64)
+    alpha = np.full((H - 1, W - 1, 2), p.alpha0)
+
+    def run(f1_, f2_, a_, grads=True):
+        h = handle(S, [(W, H)], precision=S.OF_PREC_FP64, tile=(32, 16), sweeps=3)
+        try:
+            S.of_set_frames(h, 0, dev(f1_), dev(f2_))
+            S.of_set_alpha(h, 0, dev(a_))
+            U = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+            S.of_solve(h, [U], rtol=1e-13, max_inner=20000)
+            Un = U.cpu().numpy()
+            if not grads:
+                return Un, None, None
+            da = torch.zeros(H - 1, W - 1, 2, dtype=torch.float64, device="cuda")
+            d2 = torch.zeros(H, W, dtype=torch.float64, device="cuda")
+            S.of_adjoint(h, [dev(oracle.mean_epe_grad(Un, p.flow_gt))], [da], [d2])
+            return Un, da.cpu().numpy(), d2.cpu().numpy()
+        finally:
+            S.of_destroy(h)
+
+    U, da, d2 = run(f1, f2, alpha)
+    sysm = oracle.System.from_frames(f1, f2, alpha, p.lam)
+    Uo, _, _ = sysm.solve_pcg(tol=1e-13)
+    Lo, _, _ = sysm.solve_pcg(tol=1e-13, rhs=oracle.mean_epe_grad(Uo, p.flow_gt))
+    da_o, d2_o, _ = oracle.adjoint_grad(f1, f2, alpha, p.lam, Uo, Lo, want_f1=False)
+    assert np.abs(da - da_o).max() <= 1e-8 * np.abs(da_o).max()
+    assert np.abs(d2 - d2_o).max() <= 1e-8 * np.abs(d2_o).max()
+    rng = np.random.default_rng(505)
+    hfd = 1e-4
+    for _ in range(2):
+        y, x, t = rng.integers(0, H - 1), rng.integers(0, W - 1), rng.integers(0, 2)
+        ap, am = alpha.copy(), alpha.copy()
+        ap[y, x, t] += hfd
+        am[y, x, t] -= hfd
+        fd = (oracle.mean_epe(run(f1, f2, ap, False)[0], p.flow_gt)
+              - oracle.mean_epe(run(f1, f2, am, False)[0], p.flow_gt)) / (2 * hfd)
+        assert abs(fd - da[y, x, t]) <= 1e-5 * np.abs(da).max()
+
+
+def test_autotuner_picks_a_measured_candidate(S, tmp_path):
+    from paper_1508_02977_gb300 import autotune
+    path = str(tmp_path / "tune.json")
+    best = autotune.autotune(320, 240, candidates=[((32, 32), 0, 1), ((48, 48), 0, 2)], reps=1, path=path)
+    assert best in ({"tile": (32, 32), "overlap": 0, "sweeps": 1}, {"tile": (48, 48), "overlap": 0, "sweeps": 2})
+    name = torch.cuda.get_device_name(0)
+    assert autotune.lookup(320, 240, 1, name, path) == best
