@@ -326,9 +326,10 @@ of_status encode_maps(of_ctx* h) {
             const cuuint64_t dims[3] = {(cuuint64_t)d.W, (cuuint64_t)d.H, 3};
             const cuuint64_t str[2] = {(cuuint64_t)d.pitch * es, (cuuint64_t)d.H * d.pitch * es};
             const cuuint32_t box[3] = {(cuuint32_t)Tx, (cuuint32_t)Ty, 3};
-            for (int k = 0; k < 2; ++k) {
-                char* base = (char*)(k == 0 ? h->r : h->q) + d.vec_off * es;
-                CUresult rc = enc(&m[k == 0 ? ofk::TM_R : ofk::TM_Q], dtp, 3, base, dims, str, box, es1,
+            for (int k = 0; k < 3; ++k) {
+                void* buf = k == 0 ? h->r : (k == 1 ? h->q : h->z);
+                char* base = (char*)buf + d.vec_off * es;
+                CUresult rc = enc(&m[k == 0 ? ofk::TM_R : (k == 1 ? ofk::TM_Q : ofk::TM_Z)], dtp, 3, base, dims, str, box, es1,
                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
                 if (rc != CUDA_SUCCESS) return fail(h, OF_ERR_CUDA, "tensor map (vectors) encoding failed");

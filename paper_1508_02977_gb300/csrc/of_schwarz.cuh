@@ -52,7 +52,7 @@
 
 namespace ofk {
 
-enum { TM_C0 = 0, TM_C1 = 1, TM_R = 2, TM_Q = 3, TM_PER_PAIR = 4 };
+enum { TM_C0 = 0, TM_C1 = 1, TM_R = 2, TM_Q = 3, TM_Z = 4, TM_PER_PAIR = 5 };
 
 struct SchwarzParams {
     const PairDesc* pairs;
@@ -151,6 +151,18 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
         "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, int x, int y, int z, const void* src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     (uint64_t)tm),
+                 "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory sources of every committed bulk store have been read
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed bulk store has completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Bounded wait on phase 0 of the staging barrier: returns false after
 // `limit` cycles (the caller records the timeout and stops).
@@ -398,14 +410,14 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
 
     // a work item is processed unless its pair has finished (a pair's flag is
     // only set after all of its items have been processed in this launch)
-    auto active = [&](int t) { return P.apply_only || !P.sc[P.tiles[t].x].done; };
-    auto issue = [&](int t, int s) {
-        const int4 ti = P.tiles[t];
+    auto issue = [&](const int4 ti, int s) {
         const CUtensorMap* tm = P.tmaps + (size_t)ti.x * TM_PER_PAIR;
         const int x0 = ti.y * Tx, y0 = ti.z * Ty;
         const bool need_q = !P.first && !P.apply_only;
         unsigned char* st = base + L.stage0 + (size_t)s * L.stage_bytes;
-        // order this stage's earlier generic-proxy reads before the async-proxy writes
+        // the stores that read this stage last time are done reading; order this
+        // stage's earlier generic-proxy accesses before the async-proxy writes
+        bulk_wait_read();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&bars[s], 2 * box_c + box_rq + (need_q ? box_rq : 0u));
         const int cx = (x0 - cpad) * CellT<R>::units, cy = y0 - ov - 1;
@@ -413,6 +425,16 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         tma_load_2d(st + L.c1, tm + TM_C1, cx, cy, &bars[s]);
         tma_load_3d(st + L.rs, tm + TM_R, x0, y0, 0, &bars[s]);
         if (need_q) tma_load_3d(st + L.qs, tm + TM_Q, x0, y0, 0, &bars[s]);
+    };
+    const int G = gridDim.x;
+    // next active item at or after t (slow path: loads until an active one)
+    auto advance = [&](int t, int4& ti) {
+        while (t < P.ntiles) {
+            ti = P.tiles[t];
+            if (P.apply_only || !P.sc[ti.x].done) return t;
+            t += G;
+        }
+        return t;
     };
 
     // this thread's nodes of the (unclipped) extended tile, per colour
@@ -422,17 +444,24 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
 #pragma unroll
         for (int k = 0; k < NPT; ++k) tab[col][k] = P.ntab[(col * NPT + k) * NT + threadIdx.x];
 
-    const int G = gridDim.x;
-    int t = blockIdx.x;
-    while (t < P.ntiles && !active(t)) t += G;
-    if (t < P.ntiles && threadIdx.x == 0) issue(t, 0);
+    int4 ti = make_int4(0, 0, 0, 0), tin = make_int4(0, 0, 0, 0);
+    int t = advance(blockIdx.x, ti);
+    int tn = (t < P.ntiles) ? advance(t + G, tin) : P.ntiles;
+    if (t < P.ntiles && threadIdx.x == 0) issue(ti, 0);
     unsigned phase[2] = {0u, 0u};
     int s = 0;
     for (; t < P.ntiles;) {
         // the next active item of this CTA goes into the other stage
-        int tn = t + G;
-        while (tn < P.ntiles && !active(tn)) tn += G;
-        if (nstage == 2 && tn < P.ntiles && threadIdx.x == 0) issue(tn, s ^ 1);
+        if (nstage == 2 && tn < P.ntiles && threadIdx.x == 0) issue(tin, s ^ 1);
+        // software pipelining: the item after next is fetched now and used one
+        // iteration later, so its descriptor loads overlap this item's work
+        const int tc = tn + G;
+        int4 tic = make_int4(0, 0, 0, 0);
+        int dc = 0;
+        if (tn < P.ntiles && tc < P.ntiles) {
+            tic = P.tiles[tc];
+            dc = P.apply_only ? 0 : P.sc[tic.x].done;
+        }
 
         if (threadIdx.x == 0 && !mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit)) {
             sh_fail = 1;
@@ -458,11 +487,9 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         R* Rs = reinterpret_cast<R*>(st + L.rs);
         const R* Qs = reinterpret_cast<const R*>(st + L.qs);
 
-        const int4 ti = P.tiles[t];
         const int pair = ti.x;
         const PairDesc pd = P.pairs[pair];
-        const int W = pd.W, H = pd.H, pitch = pd.pitch;
-        const long long plane = (long long)H * pitch;
+        const int W = pd.W, H = pd.H;
         const int x0 = ti.y * Tx, y0 = ti.z * Ty;
         const int tw = min(Tx, W - x0), th = min(Ty, H - y0);
         const int ex0 = max(x0 - ov, 0), ex1 = min(x0 + tw + ov, W);
@@ -537,43 +564,63 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         }
 #undef OF_STEP
 
-        // ---- write-out of the owned tile (coalesced), partials r.r and r.z
-        R* zg = reinterpret_cast<R*>(P.z) + pd.vec_off;
-        R* rg = reinterpret_cast<R*>(P.r) + pd.vec_off;
+        // ---- owned z into the q buffer of this stage (q is no longer needed),
+        //      partials r.r and r.z from the owners' registers, FP32 within the
+        //      CTA (FP64 arithmetic runs at a small fraction of the FP32 rate)
+        R* Zo = reinterpret_cast<R*>(st + L.qs);
         R rr = R(0), rz = R(0);
-        const int nwarps = NT >> 5, lane = threadIdx.x & 31;
-        for (int j = threadIdx.x >> 5; j < th; j += nwarps) {
-            for (int i = lane; i < tw; i += 32) {
-                const int si = j * Tx + i;
-                const int c = (j + ov + 1) * RW + (i + cpad);
+#pragma unroll
+        for (int col = 0; col < 3; ++col) {
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const NodeState<R>& n = ns[col][k];
+                if (n.c == -1) continue;
+                const int c = n.c & 0xffffff;
+                const uint32_t e = tab[col][k];
+                const int gx = x0 - ov + (int)(e & 0xffffu), gy = y0 - ov + (int)(e >> 16);
+                if (gx < x0 || gx >= x0 + tw || gy < y0 || gy >= y0 + th) continue;
+                const int si = (gy - y0) * Tx + (gx - x0);
                 const R v0 = Zs[c], v1 = Zs[c + nc], v2 = Zs[c + 2 * nc];
-                const R r0 = Rs[si], r1 = Rs[si + Tx * Ty], r2 = Rs[si + 2 * Tx * Ty];
-                const long long o = (long long)(y0 + j) * pitch + (x0 + i);
-                zg[o] = v0;
-                zg[o + plane] = v1;
-                zg[o + 2 * plane] = v2;
-                if (need_q) {
-                    rg[o] = r0;
-                    rg[o + plane] = r1;
-                    rg[o + 2 * plane] = r2;
+                Zo[si] = v0;
+                Zo[si + Tx * Ty] = v1;
+                Zo[si + 2 * Tx * Ty] = v2;
+                rr += n.b0 * n.b0 + n.b1 * n.b1 + n.b2 * n.b2;
+                rz += n.b0 * v0 + n.b1 * v1 + n.b2 * v2;
+            }
+        }
+        const float wrr = warp_sum((float)rr), wrz = warp_sum((float)rz);
+        if ((threadIdx.x & 31) == 0) {
+            sh_red[threadIdx.x >> 5] = (double)wrr;
+            sh_red[16 + (threadIdx.x >> 5)] = (double)wrz;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // bulk stores of the owned tile: z from the q buffer, updated r
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const CUtensorMap* tm = P.tmaps + (size_t)pair * TM_PER_PAIR;
+            tma_store_3d(tm + TM_Z, x0, y0, 0, Zo);
+            if (need_q) tma_store_3d(tm + TM_R, x0, y0, 0, Rs);
+            bulk_commit();
+            if (!P.apply_only) {
+                double a2 = 0.0, b2 = 0.0;
+                for (int w = 0; w < (NT >> 5); ++w) {
+                    a2 += sh_red[w];
+                    b2 += sh_red[16 + w];
                 }
-                rr += r0 * r0 + r1 * r1 + r2 * r2;
-                rz += r0 * v0 + r1 * v1 + r2 * v2;
+                P.partial[2 * (long long)ti.w] = a2;
+                P.partial[2 * (long long)ti.w + 1] = b2;
             }
         }
-        if (!P.apply_only) {
-            const double s_rr = block_sum_rt((double)rr, sh_red);
-            const double s_rz = block_sum_rt((double)rz, sh_red);
-            if (threadIdx.x == 0) {
-                P.partial[2 * (long long)ti.w] = s_rr;
-                P.partial[2 * (long long)ti.w + 1] = s_rz;
-            }
-        }
-        __syncthreads();  // this stage and z are free for the next item
+        __syncthreads();  // z and the partial slots are free for the next item
         t = tn;
+        ti = tin;
+        tn = tc;
+        tin = tic;
+        if (tn < P.ntiles && dc) tn = advance(tn + G, tin);  // the fetched item's pair has finished
         if (nstage == 2) s ^= 1;
-        else if (t < P.ntiles && threadIdx.x == 0) issue(t, 0);
+        else if (t < P.ntiles && threadIdx.x == 0) issue(ti, 0);
     }
+    if (threadIdx.x == 0) bulk_wait_all();  // the last stores have landed before the CTA leaves
     if (P.apply_only) return;
     // one arrival per CTA; the last CTA reduces the items of every pair that
     // took part, in item order (deterministic), and updates its scalars
