@@ -343,7 +343,10 @@ of_status encode_maps(of_ctx* h) {
     return OF_OK;
 }
 
-// Builds the inner-loop graph: a while-node whose body is one PCG iteration
+constexpr int kLoopUnroll = 4;
+
+// Builds the inner-loop graph: a while-node whose body is kLoopUnroll PCG
+// iterations
 // (apply, then Schwarz); the Schwarz kernel's last CTA sets the condition
 // once no pair is iterating.  Returns false (and leaves no graph) if the
 // driver cannot build it; the solve then polls from the host.
@@ -371,8 +374,14 @@ bool build_loop_graph(of_ctx* h) {
             ofl::SolveBufs B = solve_bufs(h);
             B.use_cond = 1;
             B.cond = cond;
-            cudaError_t e1 = ofl::launch_pcg_apply(B, cs);
-            cudaError_t e2 = ofl::launch_pcg_precond(B, cs);
+            // several iterations per check of the condition: iterations after a
+            // pair has finished return at once (their kernels test its flag)
+            cudaError_t e1 = cudaSuccess, e2 = cudaSuccess;
+            for (int u = 0; u < kLoopUnroll; ++u) {
+                B.use_cond = (u == kLoopUnroll - 1);  // only the last sets the condition
+                if (e1 == cudaSuccess) e1 = ofl::launch_pcg_apply(B, cs);
+                if (e2 == cudaSuccess) e2 = ofl::launch_pcg_precond(B, cs);
+            }
             cudaGraph_t out = nullptr;
             cudaError_t e3 = cudaStreamEndCapture(cs, &out);
             ok = e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess;
@@ -434,13 +443,14 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
             break;
         }
         CK(timed(h, 1, [&] { return ofl::launch_precond_first(B, st); }));
-        if (h->loop_exec && !h->prof) {
+        if (h->loop_exec && !h->prof && !o.host_loop) {
             // the whole inner loop on the device; one read-back per pass
             CK(cudaGraphLaunch(h->loop_exec, st));
             CK(cudaMemcpyAsync(h->sc_host, h->sc_dev, sizeof(PairScalars) * h->batch, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             int body = 0;  // loop iterations = the most iterations any pair took in this pass
             for (int p = 0; p < h->batch; ++p) body = std::max(body, h->sc_host[p].it);
+            body = (body + kLoopUnroll - 1) / kLoopUnroll * kLoopUnroll;  // whole bodies run
             h->ptot.launches[0] += body;
             h->ptot.launches[1] += body;
         } else {

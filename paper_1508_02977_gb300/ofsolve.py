@@ -38,7 +38,7 @@ class GridOpts(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
-                ("warm_start", ctypes.c_int), ("inner_rtol", ctypes.c_double)]
+                ("warm_start", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("host_loop", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -171,14 +171,16 @@ def of_get_alpha(h, pair, out):
     return _check(h, _lib.of_get_alpha(h, int(pair), _vp(p), dt))
 
 
-def of_solve(h, U, rtol=1e-6, max_outer=20, max_inner=2000, warm_start=False, inner_rtol=0.0, raise_on=True):
+def of_solve(h, U, rtol=1e-6, max_outer=20, max_inner=2000, warm_start=False, inner_rtol=0.0, raise_on=True,
+             host_loop=False):
     """U: list of [3][H][W] arrays (one per pair, same dtype).  Returns
     (status, [info dict per pair])."""
     ptrs = [_ptr_dtype(u) for u in U]
     dt = ptrs[0][1]
     arr = (_vp * len(U))(*[p for p, _ in ptrs])
     info = (SolveInfo * len(U))()
-    o = SolveOpts(float(rtol), int(max_outer), int(max_inner), int(bool(warm_start)), float(inner_rtol))
+    o = SolveOpts(float(rtol), int(max_outer), int(max_inner), int(bool(warm_start)), float(inner_rtol),
+                  int(bool(host_loop)))
     st = _lib.of_solve(h, ctypes.byref(o), arr, dt, info)
     if raise_on:
         _check(h, st)
