@@ -425,7 +425,9 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
     ofl::SolveBufs B = solve_bufs(h);
     cudaStream_t st = h->stream;
     int cur = 0;
-    const int chunk = 8;
+    // host-driven loop: poll every 8 iterations; when timing kernels, after
+    // every iteration so that no launch past convergence enters the averages
+    const int chunk = h->prof ? 1 : 8;
     passes_out.assign(h->batch, 0);
     CK(cudaMemsetAsync(h->cntA, 0, sizeof(unsigned) * h->batch, st));
     CK(cudaMemsetAsync(h->cntS, 0, sizeof(unsigned) * h->batch, st));
