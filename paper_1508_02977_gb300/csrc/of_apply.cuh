@@ -323,3 +323,258 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
 }
 
 }  // namespace ofk
+
+namespace ofk {
+
+// FP32 apply with four columns per lane (PCG and APPLY modes).
+//
+// One warp per block covers 124 output columns x rows_per_block rows: lane l
+// loads columns X0 - 4 + 4l .. X0 - 1 + 4l as float4 (lane 0's columns are a
+// halo) and forms the two triangles of the four squares whose left corners
+// are those columns.  The fourth square needs the next lane's first column
+// (one shuffle of 5 values); the first node of a lane receives the right
+// corners of the previous lane's last square (one shuffle of 2 x 3 values).
+// Lane 31's last square needs column X0 + 124, loaded separately.  Every
+// element is formed once; every word is read once per warp plus a 4-column
+// halo and the row above the block.
+struct Node4 {
+    float4 p0, p1, p2, f1, f2;
+};
+
+__device__ __forceinline__ NodeVal<float> pick(const Node4& n, int j) {
+    NodeVal<float> v;
+    const float* a = reinterpret_cast<const float*>(&n.p0);
+    const float* b = reinterpret_cast<const float*>(&n.p1);
+    const float* c = reinterpret_cast<const float*>(&n.p2);
+    const float* d = reinterpret_cast<const float*>(&n.f1);
+    const float* e = reinterpret_cast<const float*>(&n.f2);
+    v.p = v3(a[j], b[j], c[j]);
+    v.f1 = d[j];
+    v.f2 = e[j];
+    return v;
+}
+
+__device__ __forceinline__ float4 f4(float a) { return make_float4(a, a, a, a); }
+__device__ __forceinline__ float4 fma4(float s, float4 x, float4 y) {
+    return make_float4(fmaf(s, x.x, y.x), fmaf(s, x.y, y.y), fmaf(s, x.z, y.z), fmaf(s, x.w, y.w));
+}
+__device__ __forceinline__ float4 mask4(float4 v, int c0, int W) {
+    // zero the columns at or beyond W (pitch padding)
+    if (c0 + 0 >= W) v.x = 0.f;
+    if (c0 + 1 >= W) v.y = 0.f;
+    if (c0 + 2 >= W) v.z = 0.f;
+    if (c0 + 3 >= W) v.w = 0.f;
+    return v;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(32) k_apply4(const ApplyParams<float, float, float> P) {
+    const int4 bi = P.blocks[blockIdx.x];
+    const int pair = bi.x;
+    const PairDesc pd = P.pairs[pair];
+    const int W = pd.W, H = pd.H, pitch = pd.pitch;
+    const long long plane = (long long)H * pitch;
+    float beta = 0.f, a_prev = 0.f;
+    int it = 0;
+    bool first = false;
+    if (MODE == MODE_PCG) {
+        if (P.sc_in[pair].done) return;
+        beta = (float)P.sc_in[pair].beta;
+        a_prev = (float)P.sc_in[pair].a;
+        it = P.sc_in[pair].it;
+        first = (it == 0);
+    }
+    const float* f1 = P.f1 + pd.frame_off;
+    const float* f2 = P.f2 + pd.frame_off;
+    const float* al = P.alpha + 2 * pd.frame_off;
+    const long long vo = pd.vec_off;
+    const float* vin = P.in + vo;
+    const float* pold = nullptr;
+    float* pnew = nullptr;
+    if (MODE == MODE_PCG) {
+        pold = ((it & 1) ? P.p_buf1 : P.p_buf0) + vo;
+        pnew = ((it & 1) ? P.p_buf0 : P.p_buf1) + vo;
+    }
+    const int lane = threadIdx.x;
+    const int X0 = bi.y * 124;
+    const int c0 = X0 - 4 + 4 * lane;      // first of this lane's four columns
+    const int Y0 = bi.z * P.rows_per_block;
+    const int Y1 = min(Y0 + P.rows_per_block, H);
+    const bool own = lane >= 1 && c0 < W;  // this lane's columns are output columns
+    const float lam = P.lam;
+
+    // node row y at this lane's four columns, with the fused PCG updates
+    auto load4 = [&](int y, bool owner) -> Node4 {
+        Node4 n;
+        const float4 zero = f4(0.f);
+        if (y < 0 || y >= H || c0 < 0 || c0 >= W) {
+            n.p0 = n.p1 = n.p2 = n.f1 = n.f2 = zero;
+            return n;
+        }
+        const long long o = (long long)y * pitch + c0;
+        n.f1 = mask4(*reinterpret_cast<const float4*>(f1 + o), c0, W);
+        n.f2 = mask4(*reinterpret_cast<const float4*>(f2 + o), c0, W);
+        float4 a = *reinterpret_cast<const float4*>(vin + o);
+        float4 b = *reinterpret_cast<const float4*>(vin + o + plane);
+        float4 c = *reinterpret_cast<const float4*>(vin + o + 2 * plane);
+        if (MODE == MODE_PCG) {
+            // pitch padding of p_new and d is written too (as zeros / unchanged)
+            float* d = P.dcorr + vo;
+            if (!first) {
+                const float4 qa = *reinterpret_cast<const float4*>(pold + o);
+                const float4 qb = *reinterpret_cast<const float4*>(pold + o + plane);
+                const float4 qc = *reinterpret_cast<const float4*>(pold + o + 2 * plane);
+                if (owner) {
+                    float4* d0 = reinterpret_cast<float4*>(d + o);
+                    float4* d1 = reinterpret_cast<float4*>(d + o + plane);
+                    float4* d2 = reinterpret_cast<float4*>(d + o + 2 * plane);
+                    *d0 = fma4(a_prev, qa, *d0);
+                    *d1 = fma4(a_prev, qb, *d1);
+                    *d2 = fma4(a_prev, qc, *d2);
+                }
+                a = mask4(fma4(beta, qa, a), c0, W);
+                b = mask4(fma4(beta, qb, b), c0, W);
+                c = mask4(fma4(beta, qc, c), c0, W);
+            } else if (owner) {
+                *reinterpret_cast<float4*>(d + o) = zero;
+                *reinterpret_cast<float4*>(d + o + plane) = zero;
+                *reinterpret_cast<float4*>(d + o + 2 * plane) = zero;
+            }
+            if (first) {
+                a = mask4(a, c0, W);
+                b = mask4(b, c0, W);
+                c = mask4(c, c0, W);
+            }
+            if (owner) {
+                *reinterpret_cast<float4*>(pnew + o) = a;
+                *reinterpret_cast<float4*>(pnew + o + plane) = b;
+                *reinterpret_cast<float4*>(pnew + o + 2 * plane) = c;
+            }
+        }
+        if (MODE == MODE_PCG) {
+            n.p0 = a; n.p1 = b; n.p2 = c;
+        } else {
+            n.p0 = mask4(a, c0, W); n.p1 = mask4(b, c0, W); n.p2 = mask4(c, c0, W);
+        }
+        return n;
+    };
+    // one extra column X0 + 124 for lane 31
+    auto load1 = [&](int x, int y) -> NodeVal<float> {
+        NodeVal<float> v;
+        if (x < 0 || x >= W || y < 0 || y >= H) {
+            v.p = v3(0.f, 0.f, 0.f);
+            v.f1 = v.f2 = 0.f;
+            return v;
+        }
+        const long long o = (long long)y * pitch + x;
+        v.f1 = f1[o];
+        v.f2 = f2[o];
+        float p0 = vin[o], p1 = vin[o + plane], p2 = vin[o + 2 * plane];
+        if (MODE == MODE_PCG && !first) {
+            p0 = fmaf(beta, pold[o], p0);
+            p1 = fmaf(beta, pold[o + plane], p1);
+            p2 = fmaf(beta, pold[o + 2 * plane], p2);
+        }
+        v.p = v3(p0, p1, p2);
+        return v;
+    };
+    auto right = [&](const Node4& n, int y) -> NodeVal<float> {
+        // first column of the next lane (lane 31: column X0 + 124)
+        NodeVal<float> v;
+        v.p = v3(__shfl_down_sync(0xffffffffu, n.p0.x, 1), __shfl_down_sync(0xffffffffu, n.p1.x, 1),
+                 __shfl_down_sync(0xffffffffu, n.p2.x, 1));
+        v.f1 = __shfl_down_sync(0xffffffffu, n.f1.x, 1);
+        v.f2 = __shfl_down_sync(0xffffffffu, n.f2.x, 1);
+        if (lane == 31) v = load1(c0 + 4, y);
+        return v;
+    };
+
+    float acc = 0.f;
+    Node4 cur = load4(Y0 - 1, false);
+    NodeVal<float> rcur = right(cur, Y0 - 1);
+    V3<float> carry[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) carry[j] = v3(0.f, 0.f, 0.f);
+    for (int sy = Y0 - 1; sy < Y1; ++sy) {
+        const bool row_owned = (sy + 1 >= Y0) && (sy + 1 < Y1);
+        Node4 nxt = load4(sy + 1, own && row_owned);
+        NodeVal<float> rnxt = right(nxt, sy + 1);
+        float4 alA = f4(0.f), alB = f4(0.f);  // alpha of squares c0..c0+1 and c0+2..c0+3
+        const bool rowv = (sy >= 0) && (sy < H - 1) && c0 >= 0 && c0 < W - 1;
+        if (rowv) {
+            const float* ap = al + 2 * ((long long)sy * pitch + c0);
+            alA = *reinterpret_cast<const float4*>(ap);
+            alB = *reinterpret_cast<const float4*>(ap + 4);
+        }
+        const float alv[8] = {alA.x, alA.y, alA.z, alA.w, alB.x, alB.y, alB.z, alB.w};
+        V3<float> cA[4], cB[4], cC[4], cD[4], bdum;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int cx = c0 + j;
+            const bool valid = rowv && (cx < W - 1);
+            const NodeVal<float> A = pick(cur, j), D = pick(nxt, j);
+            const NodeVal<float> B = (j < 3) ? pick(cur, j + 1) : rcur;
+            const NodeVal<float> C = (j < 3) ? pick(nxt, j + 1) : rnxt;
+            square_contrib<float, false>(A, B, C, D, alv[2 * j], alv[2 * j + 1], lam, valid, cA[j], cB[j], cC[j],
+                                         cD[j], bdum, bdum, bdum, bdum);
+        }
+        // right corners of the previous lane's last square
+        const V3<float> pB = v3(__shfl_up_sync(0xffffffffu, cB[3].a, 1), __shfl_up_sync(0xffffffffu, cB[3].b, 1),
+                                __shfl_up_sync(0xffffffffu, cB[3].c, 1));
+        const V3<float> pC = v3(__shfl_up_sync(0xffffffffu, cC[3].a, 1), __shfl_up_sync(0xffffffffu, cC[3].b, 1),
+                                __shfl_up_sync(0xffffffffu, cC[3].c, 1));
+        V3<float> out[4];
+        out[0] = carry[0] + cA[0] + pB;
+#pragma unroll
+        for (int j = 1; j < 4; ++j) out[j] = carry[j] + cA[j] + cB[j - 1];
+        if (sy >= Y0 && own) {
+            const long long o = (long long)sy * pitch + c0;
+            float* q = P.out + vo;
+            *reinterpret_cast<float4*>(q + o) = make_float4(out[0].a, out[1].a, out[2].a, out[3].a);
+            *reinterpret_cast<float4*>(q + o + plane) = make_float4(out[0].b, out[1].b, out[2].b, out[3].b);
+            *reinterpret_cast<float4*>(q + o + 2 * plane) = make_float4(out[0].c, out[1].c, out[2].c, out[3].c);
+            if (MODE == MODE_PCG) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const NodeVal<float> pj = pick(cur, j);
+                    acc += pj.p.a * out[j].a + pj.p.b * out[j].b + pj.p.c * out[j].c;
+                }
+            }
+        }
+        carry[0] = cD[0] + pC;
+#pragma unroll
+        for (int j = 1; j < 4; ++j) carry[j] = cD[j] + cC[j - 1];
+        cur = nxt;
+        rcur = rnxt;
+    }
+    if (MODE == MODE_APPLY) return;
+    // warp partial (FP32 within the warp), then the pair's last block reduces
+    // the block partials in order in FP64
+    const float s0 = warp_sum(acc);
+    __shared__ double sh_red[1];
+    __shared__ int sh_last;
+    if (lane == 0) {
+        P.partial[2 * (long long)bi.w] = (double)s0;
+        P.partial[2 * (long long)bi.w + 1] = 0.0;
+    }
+    if (!arrive_last(&P.counter[pair], (unsigned)pd.nblk, &sh_last)) return;
+    double t0 = 0.0;
+    for (int i = lane; i < pd.nblk; i += 32) t0 += __ldcg(P.partial + 2 * (long long)(pd.blk0 + i));
+    t0 = warp_sum(t0);
+    (void)sh_red;
+    if (lane == 0) {
+        PairScalars* s = P.sc + pair;
+        s->pq = t0;
+        if (!(t0 > 0.0) || !isfinite(t0) || !isfinite(s->rz)) {
+            s->a = 0.0;
+            s->done = 1;
+            s->status = 6;
+        } else {
+            s->a = s->rz / t0;
+        }
+        __threadfence();
+        P.counter[pair] = 0u;
+    }
+}
+
+}  // namespace ofk
