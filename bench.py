@@ -335,7 +335,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"layers {W}x{H}: 4 textured layers, rigid motions <= 6 px, occlusions, "
                                    f"gain 0.8-1.25 (one pair per GPU)",
-                       "precision": "FP32 PCG + Schwarz sweeps, FP64 residual/refinement/dots",
+                       "precision": "FP32 PCG + Schwarz sweeps; outer residual b - A x in double-float (~48-bit) arithmetic; x, refinement and cross-block dots in FP64",
                        "rtol": RTOL, "opts": {k: v for k, v in WORKLOAD_OPTS.items()},
                        "step": "alpha reset + solve to rtol + indicator + alpha update",
                        "l2": "inputs larger than L2 (no flush)",

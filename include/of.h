@@ -87,7 +87,8 @@ typedef struct {
 
 /* Solve options.  A field left at 0 takes the default in brackets. */
 typedef struct {
-    double rtol;       /* stop when ||b - A U||_2 <= rtol ||b||_2 (FP64 residual) [1e-6] */
+    double rtol;       /* stop when ||b - A U||_2 <= rtol ||b||_2 [1e-6]; the residual is formed in
+                          FP64 (FP64 path) or double-float arithmetic (mixed path, ~48 bits) */
     int max_outer;     /* refinement passes (mixed) [20] */
     int max_inner;     /* PCG iterations per pass (mixed) or in total (FP64) [2000] */
     int warm_start;    /* 1: start from the U passed in; 0: start from U = 0 */

@@ -18,6 +18,7 @@
 //           rhs = b (frames) or a given vector,  partial ||r||^2, ||rhs||^2
 #pragma once
 #include "of_common.cuh"
+#include "of_df.cuh"
 
 namespace ofk {
 
@@ -39,14 +40,15 @@ __device__ __forceinline__ void square_contrib(const NodeVal<R>& A, const NodeVa
                                                const NodeVal<R>& D, R al0, R al1, R lam, bool valid,
                                                V3<R>& cA, V3<R>& cB, V3<R>& cC, V3<R>& cD,
                                                V3<R>& bA, V3<R>& bB, V3<R>& bC, V3<R>& bD) {
-    const R third = R(1) / R(3);
-    const R w24 = R(1) / R(24);
-    const R h = R(OF_STIFF_HALF);
+    const R third = kconst<R>(1.0 / 3.0);
+    const R w24 = kconst<R>(1.0 / 24.0);
+    const R h = kconst<R>(OF_STIFF_HALF);
+    const R zero = kconst<R>(0.0);
     // ---- t = 0: A, B, C
     R g0x = B.f2 - A.f2, g0y = C.f2 - B.f2, g0m = -(A.f1 + B.f1 + C.f1) * third;
     R g1x = C.f2 - D.f2, g1y = D.f2 - A.f2, g1m = -(A.f1 + D.f1 + C.f1) * third;
     if constexpr (!WANT_A) {
-        cA = cB = cC = cD = v3(R(0), R(0), R(0));
+        cA = cB = cC = cD = v3(zero, zero, zero);
     } else {
     R sA = g0x * A.p.a + g0y * A.p.b + g0m * A.p.c;
     R sB = g0x * B.p.a + g0y * B.p.b + g0m * B.p.c;
@@ -78,8 +80,8 @@ __device__ __forceinline__ void square_contrib(const NodeVal<R>& A, const NodeVa
     cD.b = vD * g1y - a1 * (dAD.b + dCD.b);
     cD.c = vD * g1m - l0 * (dAD.c + dCD.c);
     }
-    if (WANT_B) {
-        const R sixth = R(1) / R(6);
+    if constexpr (WANT_B) {
+        const R sixth = kconst<R>(1.0 / 6.0);
         R ft0 = ((A.f2 - A.f1) + (B.f2 - B.f1) + (C.f2 - C.f1)) * third;
         R ft1 = ((A.f2 - A.f1) + (D.f2 - D.f1) + (C.f2 - C.f1)) * third;
         R k0 = -sixth * ft0, k1 = -sixth * ft1;
@@ -88,8 +90,8 @@ __device__ __forceinline__ void square_contrib(const NodeVal<R>& A, const NodeVa
         bA = b0 + b1; bB = b0; bC = b0 + b1; bD = b1;
     }
     if (!valid) {
-        cA = cB = cC = cD = v3(R(0), R(0), R(0));
-        if (WANT_B) bA = bB = bC = bD = v3(R(0), R(0), R(0));
+        cA = cB = cC = cD = v3(zero, zero, zero);
+        if constexpr (WANT_B) bA = bB = bC = bD = v3(zero, zero, zero);
     }
 }
 
@@ -118,8 +120,11 @@ struct ApplyParams {
     int max_inner;
 };
 
-template <typename R, typename C, typename RI, int MODE, bool WANT_B, int NW>
+template <typename R, typename C, typename RI, int MODE, bool WANT_B, int NW, typename T = R>
 __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P) {
+    // R: storage type of in/out (and of the PCG scalars); T: arithmetic of
+    // the element contributions (R itself, or double-float for the residual
+    // of the FP32 path)
     constexpr int NT = NW * 32;
     __shared__ double sh_red[NT / 32];
     __shared__ int sh_last;
@@ -168,19 +173,20 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
     const int Y1 = min(Y0 + P.rows_per_block, H);
     const bool mycol_owned = (lane >= 1) && (cx < W) && (cx >= 0);  // side-effect writes
     const bool out_col = (lane < 31) && (cx + 1 < W);
-    const R lam = P.lam;
+    const T lam = Cvt<T>::from(P.lam);
+    const T zero = kconst<T>(0.0);
 
     // load node (x, y) of the input vector + frames, with the mode's fused
     // update; side effects (p_new, d, x_new) only for owned nodes
-    auto load = [&](int x, int y, bool owner) -> NodeVal<R> {
-        NodeVal<R> v;
+    auto load = [&](int x, int y, bool owner) -> NodeVal<T> {
+        NodeVal<T> v;
         const bool in = (x >= 0) && (x < W) && (y >= 0) && (y < H);
-        if (!in) { v.p = v3(R(0), R(0), R(0)); v.f1 = R(0); v.f2 = R(0); return v; }
+        if (!in) { v.p = v3(zero, zero, zero); v.f1 = zero; v.f2 = zero; return v; }
         const long long o = (long long)y * pitch + x;
-        v.f1 = (R)f1[o];
-        v.f2 = (R)f2[o];
+        v.f1 = Cvt<T>::from(f1[o]);
+        v.f2 = Cvt<T>::from(f2[o]);
         if (MODE == MODE_RESB) {
-            v.p = v3(R(0), R(0), R(0));
+            v.p = v3(zero, zero, zero);
             return v;
         }
         R p0 = vin[o], p1 = vin[o + plane], p2 = vin[o + 2 * plane];
@@ -212,11 +218,11 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
                 xn[o] = p0; xn[o + plane] = p1; xn[o + 2 * plane] = p2;
             }
         }
-        v.p = v3(p0, p1, p2);
+        v.p = v3(Cvt<T>::from(p0), Cvt<T>::from(p1), Cvt<T>::from(p2));
         return v;
     };
-    auto shfl_node = [&](const NodeVal<R>& v) -> NodeVal<R> {
-        NodeVal<R> w;
+    auto shfl_node = [&](const NodeVal<T>& v) -> NodeVal<T> {
+        NodeVal<T> w;
         w.p = shfl_down3(v.p);
         w.f1 = shfl_down(v.f1, 1);
         w.f2 = shfl_down(v.f2, 1);
@@ -224,64 +230,71 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
     };
 
     R acc = R(0);          // PCG: per-thread partial of p.q (inner precision)
-    double accd = 0.0, acc_b = 0.0;  // RES: FP64 norms
+    T acc_r = zero, acc_b = zero;  // RES: per-thread ||r||^2, ||rhs||^2
     // prologue: node row Y0-1
-    NodeVal<R> cur = load(cx, Y0 - 1, false);
-    NodeVal<R> ncur = shfl_node(cur);
+    NodeVal<T> cur = load(cx, Y0 - 1, false);
+    NodeVal<T> ncur = shfl_node(cur);
     if (lane == 31) ncur = load(cx + 1, Y0 - 1, false);
-    V3<R> carry = v3(R(0), R(0), R(0)), carry_b = v3(R(0), R(0), R(0));
+    V3<T> carry = v3(zero, zero, zero), carry_b = v3(zero, zero, zero);
     for (int sy = Y0 - 1; sy < Y1; ++sy) {
         const bool row_owned = (sy + 1 >= Y0) && (sy + 1 < Y1);
-        NodeVal<R> nxt = load(cx, sy + 1, mycol_owned && row_owned);
-        NodeVal<R> nnxt = shfl_node(nxt);
+        NodeVal<T> nxt = load(cx, sy + 1, mycol_owned && row_owned);
+        NodeVal<T> nnxt = shfl_node(nxt);
         if (lane == 31) nnxt = load(cx + 1, sy + 1, false);
         const bool valid = (cx >= 0) && (cx < W - 1) && (sy >= 0) && (sy < H - 1);
-        const R al0 = valid ? (R)al[2 * ((long long)sy * pitch + cx)] : R(0);
-        const R al1 = valid ? (R)al[2 * ((long long)sy * pitch + cx) + 1] : R(0);
-        V3<R> cA, cB, cC, cD, bA, bB, bC, bD;
-        square_contrib<R, WANT_B || IS_RES, MODE != MODE_RESB>(cur, ncur, nnxt, nxt, al0, al1, lam, valid, cA, cB,
+        const T al0 = valid ? Cvt<T>::from(al[2 * ((long long)sy * pitch + cx)]) : zero;
+        const T al1 = valid ? Cvt<T>::from(al[2 * ((long long)sy * pitch + cx) + 1]) : zero;
+        V3<T> cA, cB, cC, cD, bA, bB, bC, bD;
+        square_contrib<T, WANT_B || IS_RES, MODE != MODE_RESB>(cur, ncur, nnxt, nxt, al0, al1, lam, valid, cA, cB,
                                                                   cC, cD, bA, bB, bC, bD);
-        V3<R> left = shfl_down3(cA);
-        V3<R> res = carry + cB + left;  // node (cx+1, sy) complete
-        V3<R> resb;
+        V3<T> left = shfl_down3(cA);
+        V3<T> res = carry + cB + left;  // node (cx+1, sy) complete
+        V3<T> resb = v3(zero, zero, zero);
         constexpr bool NEED_B = WANT_B || IS_RES;
-        if (NEED_B) resb = carry_b + bB + shfl_down3(bA);
+        if constexpr (NEED_B) resb = carry_b + bB + shfl_down3(bA);
         if (sy >= Y0 && out_col) {
             const long long o = (long long)sy * pitch + (cx + 1);
-            if (MODE == MODE_APPLY || MODE == MODE_PCG) {
+            if constexpr (MODE == MODE_APPLY || MODE == MODE_PCG) {
                 R* q = P.out + vo;
                 q[o] = res.a; q[o + plane] = res.b; q[o + 2 * plane] = res.c;
-                if (MODE == MODE_PCG) acc += ncur.p.a * res.a + ncur.p.b * res.b + ncur.p.c * res.c;
-                if (WANT_B && P.bout) {
-                    R* bo = P.bout + vo;
-                    bo[o] = resb.a; bo[o + plane] = resb.b; bo[o + 2 * plane] = resb.c;
+                if constexpr (MODE == MODE_PCG) acc += ncur.p.a * res.a + ncur.p.b * res.b + ncur.p.c * res.c;
+                if constexpr (WANT_B) {
+                    if (P.bout) {
+                        R* bo = P.bout + vo;
+                        bo[o] = resb.a; bo[o + plane] = resb.b; bo[o + 2 * plane] = resb.c;
+                    }
                 }
             }
-            if (IS_RES) {
-                V3<R> rhs;
+            if constexpr (IS_RES) {
+                V3<T> rhs;
                 if (P.rhs_vec) {
                     const R* c = P.rhs_vec + vo;
-                    rhs = v3(c[o], c[o + plane], c[o + 2 * plane]);
+                    rhs = v3(Cvt<T>::from(c[o]), Cvt<T>::from(c[o + plane]), Cvt<T>::from(c[o + 2 * plane]));
                 } else {
                     rhs = resb;
                 }
-                V3<R> r = v3(rhs.a - res.a, rhs.b - res.b, rhs.c - res.c);
+                V3<T> r = v3(rhs.a - res.a, rhs.b - res.b, rhs.c - res.c);
                 RI* ro = P.rout + vo;
-                ro[o] = (RI)r.a; ro[o + plane] = (RI)r.b; ro[o + 2 * plane] = (RI)r.c;
-                accd += (double)r.a * (double)r.a + (double)r.b * (double)r.b + (double)r.c * (double)r.c;
-                acc_b += (double)rhs.a * (double)rhs.a + (double)rhs.b * (double)rhs.b + (double)rhs.c * (double)rhs.c;
+                ro[o] = Cvt<RI>::from(r.a); ro[o + plane] = Cvt<RI>::from(r.b); ro[o + 2 * plane] = Cvt<RI>::from(r.c);
+                acc_r = acc_r + (r.a * r.a + r.b * r.b + r.c * r.c);
+                acc_b = acc_b + (rhs.a * rhs.a + rhs.b * rhs.b + rhs.c * rhs.c);
             }
         }
         carry = cC + shfl_down3(cD);
-        if (NEED_B) carry_b = bC + shfl_down3(bD);
+        if constexpr (NEED_B) carry_b = bC + shfl_down3(bD);
         cur = nxt;
         ncur = nnxt;
     }
 
-    if (MODE == MODE_APPLY) return;
+    if constexpr (MODE == MODE_APPLY) return;
     // ---- block partials and last-block reduction of the pair
-    double s0 = block_sum<NT>((MODE == MODE_PCG) ? (double)acc : accd, sh_red);
-    double s1 = IS_RES ? block_sum<NT>(acc_b, sh_red) : 0.0;
+    double s0, s1 = 0.0;
+    if constexpr (MODE == MODE_PCG) {
+        s0 = block_sum<NT>((double)acc, sh_red);
+    } else {
+        s0 = block_sum<NT>(Cvt<double>::from(acc_r), sh_red);
+        s1 = block_sum<NT>(Cvt<double>::from(acc_b), sh_red);
+    }
     if (threadIdx.x == 0) {
         P.partial[2 * (long long)bi.w] = s0;
         P.partial[2 * (long long)bi.w + 1] = s1;

@@ -1,0 +1,82 @@
+// Double-float ("float-float") arithmetic for the outer residual of the
+// FP32 path.
+//
+// A value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2,
+// about 48 significant bits.  The operations are the classical error-free
+// transformations: Knuth's TwoSum (exact a + b = s + e for any a, b),
+// Dekker's FastTwoSum (the same when |a| >= |b|) and the FMA form of
+// Dekker's TwoProduct (p = fl(a b), e = fma(a, b, -p), a b = p + e exactly).
+// The sum below is the short variant (one TwoSum on the high parts, the low
+// parts added in float): its absolute error is a small multiple of
+// 2^-46 (|a| + |b|), which is the measure that matters for r = b - A x (the
+// error relative to |b| + |A| |x|).  The FP32 pipe runs these at the full
+// FP32 rate; FP64 arithmetic runs at a small fraction of it on this GPU.
+//
+// Every primitive uses the _rn intrinsics so that the compiler neither
+// contracts a product into a later sum nor reassociates.
+#pragma once
+
+namespace ofk {
+
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float v = __fsub_rn(s, a);
+    return DF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v))};
+}
+
+__device__ __forceinline__ DF operator+(DF a, DF b) {
+    const DF s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF operator-(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF operator-(DF a, DF b) { return a + (-b); }
+__device__ __forceinline__ DF operator*(DF a, DF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+
+// double -> double-float: hi is x rounded to float, lo the rounded remainder
+__device__ __forceinline__ DF df_from_double(double x) {
+    const float h = __double2float_rn(x);
+    return DF{h, __double2float_rn(x - (double)h)};
+}
+
+__device__ __forceinline__ DF shfl_down(DF v, int d) {
+    return DF{__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
+}
+
+// Conversions between the storage types (float, double) and an arithmetic
+// type T (float, double or DF).
+template <typename T>
+struct Cvt {
+    template <typename S>
+    __device__ __forceinline__ static T from(S x) { return (T)x; }
+    __device__ __forceinline__ static T from(DF x) { return (T)x.hi + (T)x.lo; }
+};
+template <>
+struct Cvt<DF> {
+    __device__ __forceinline__ static DF from(float x) { return DF{x, 0.f}; }
+    __device__ __forceinline__ static DF from(double x) { return df_from_double(x); }
+    __device__ __forceinline__ static DF from(DF x) { return x; }
+};
+
+// A constant in type T, folded at compile time (x is a literal).
+template <typename T> __device__ __forceinline__ T kconst(double x) { return (T)x; }
+template <> __device__ __forceinline__ DF kconst<DF>(double x) {
+    const float h = (float)x;
+    return DF{h, (float)(x - (double)h)};
+}
+
+}  // namespace ofk

@@ -1,4 +1,6 @@
 // Kernel instantiations and launchers of the solve path.
+#include <type_traits>
+
 #include "of_apply.cuh"
 #include "of_launch.h"
 #include "of_schwarz.cuh"
@@ -92,8 +94,10 @@ static cudaError_t residual_t(const SolveBufs& B, const double* xin, double* xou
     P.rtol = rtol;
     P.inner_rtol = inner_rtol;
     P.max_inner = max_inner;
-    if (xin) k_apply<double, C, RI, MODE_RES, false, APPLY_NW><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
-    else k_apply<double, C, RI, MODE_RESB, false, APPLY_NW><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+    // the FP32 path forms A x and b in double-float: FP64-grade residual on the FP32 pipe
+    using T = typename std::conditional<sizeof(C) == 4, DF, double>::type;
+    if (xin) k_apply<double, C, RI, MODE_RES, false, APPLY_NW, T><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+    else k_apply<double, C, RI, MODE_RESB, false, APPLY_NW, T><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
     return cudaGetLastError();
 }
 

@@ -44,9 +44,12 @@ def test_binding_wraps_every_export(lib):
 
 def test_struct_layouts_match_header():
     from paper_1508_02977_gb300 import ofsolve as S
-    # of_grid_opts: 4 ints, enum, (pad), double, enum (+ pad) ; of_solve_opts: double, 3 ints, double
+    # of_grid_opts: 4 ints, enum, (pad), double, enum (+ pad) ;
+    # of_solve_opts: double, 3 ints, (pad), double, int (+ pad)
     assert ctypes.sizeof(S.GridOpts) == 40
-    assert ctypes.sizeof(S.SolveOpts) == 32
+    assert ctypes.sizeof(S.SolveOpts) == 40
+    assert [getattr(S.SolveOpts, f).offset for f in
+            ("rtol", "max_outer", "max_inner", "warm_start", "inner_rtol", "host_loop")] == [0, 8, 12, 16, 24, 32]
     assert ctypes.sizeof(S.SolveInfo) == 32
 
 

@@ -93,6 +93,30 @@ def test_apply_fp32_matches_oracle(S, oracle, W, H):
     assert np.all(np.abs(q - want) <= 64 * EPS32 * scale)
 
 
+@pytest.mark.parametrize("W,H", [(130, 67), (300, 40)])
+def test_mixed_residual_is_fp64_grade(S, oracle, W, H):
+    """The FP32 path forms its outer residual b - A x in double-float
+    arithmetic.  Near the solution (||r|| ~ 1e-8 of the terms of A x, heavy
+    cancellation) its norm must match the FP64 oracle's closely; FP32
+    arithmetic would be wrong by O(1) there."""
+    f1, f2 = synth.random_frames(W, H, 71 * W + H)
+    f1, f2 = f32(f1), f32(f2)
+    alpha = f32(synth.random_alpha(W, H, 3 * W + H))
+    sysm = oracle.System.from_frames(f1, f2, alpha, 1.0)
+    Ud = sysm.solve_direct()
+    rng = np.random.default_rng(W * H)
+    U = Ud + 1e-8 * np.abs(Ud).max() * rng.standard_normal(Ud.shape)
+    want = sysm.rel_residual(U)
+    h = handle(S, [(W, H)], precision=S.OF_PREC_MIXED)
+    try:
+        S.of_set_frames(h, 0, dev(f1, torch.float32), dev(f2, torch.float32))
+        S.of_set_alpha(h, 0, dev(alpha, torch.float32))
+        got = S.of_residual(h, 0, dev(U))
+    finally:
+        S.of_destroy(h)
+    assert abs(got - want) <= 1e-4 * want
+
+
 # ---------------------------------------------------------- preconditioner --
 
 @pytest.mark.parametrize("ov,sw", [(0, 1), (2, 1), (0, 2), (4, 3)])
