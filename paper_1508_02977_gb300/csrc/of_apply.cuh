@@ -342,14 +342,19 @@ namespace ofk {
 // FP32 apply with four columns per lane (PCG and APPLY modes).
 //
 // One warp per block covers 124 output columns x rows_per_block rows: lane l
-// loads columns X0 - 4 + 4l .. X0 - 1 + 4l as float4 (lane 0's columns are a
+// holds columns X0 - 4 + 4l .. X0 - 1 + 4l as float4 (lane 0's columns are a
 // halo) and forms the two triangles of the four squares whose left corners
 // are those columns.  The fourth square needs the next lane's first column
 // (one shuffle of 5 values); the first node of a lane receives the right
 // corners of the previous lane's last square (one shuffle of 2 x 3 values).
-// Lane 31's last square needs column X0 + 124, loaded separately.  Every
+// Lane 31's last square needs column X0 + 124, fetched separately.  Every
 // element is formed once; every word is read once per warp plus a 4-column
 // halo and the row above the block.
+//
+// Rows stream through a per-warp ring of three shared-memory stages filled
+// with cp.async (16-byte LDGSTS, zero-filled outside the image): while node
+// row y is combined with row y-1, row y+1 is already in flight, without
+// holding those loads in registers.
 struct Node4 {
     float4 p0, p1, p2, f1, f2;
 };
@@ -380,8 +385,27 @@ __device__ __forceinline__ float4 mask4(float4 v, int c0, int W) {
     return v;
 }
 
+// cp.async with a source size of 0 writes zeros and reads nothing
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+constexpr int A4_NS = 3;     // ring stages
+constexpr int A4_NARR = 13;  // float4 slots per lane, row and stage
+enum { A4_F1, A4_F2, A4_Z0, A4_Z1, A4_Z2, A4_Q0, A4_Q1, A4_Q2, A4_D0, A4_D1, A4_D2, A4_AL0, A4_AL1 };
+constexpr int A4_EXTRA = 8;  // floats of column X0 + 124 per stage: f1, f2, z0..z2, q0..q2
+__host__ __device__ constexpr int apply4_smem_bytes() { return A4_NS * (A4_NARR * 32 * 16 + A4_EXTRA * 4); }
+
 template <int MODE>
 __global__ void __launch_bounds__(32) k_apply4(const ApplyParams<float, float, float> P) {
+    extern __shared__ float4 a4_ring[];
     const int4 bi = P.blocks[blockIdx.x];
     const int pair = bi.x;
     const PairDesc pd = P.pairs[pair];
@@ -397,166 +421,193 @@ __global__ void __launch_bounds__(32) k_apply4(const ApplyParams<float, float, f
         it = P.sc_in[pair].it;
         first = (it == 0);
     }
+    const bool use_q = (MODE == MODE_PCG) && !first;  // p = z + beta p_old, d += a_prev p_old
     const float* f1 = P.f1 + pd.frame_off;
     const float* f2 = P.f2 + pd.frame_off;
     const float* al = P.alpha + 2 * pd.frame_off;
     const long long vo = pd.vec_off;
     const float* vin = P.in + vo;
-    const float* pold = nullptr;
+    const float* pold = vin;
     float* pnew = nullptr;
+    float* dcor = nullptr;
     if (MODE == MODE_PCG) {
         pold = ((it & 1) ? P.p_buf1 : P.p_buf0) + vo;
         pnew = ((it & 1) ? P.p_buf0 : P.p_buf1) + vo;
+        dcor = P.dcorr + vo;
     }
     const int lane = threadIdx.x;
     const int X0 = bi.y * 124;
     const int c0 = X0 - 4 + 4 * lane;      // first of this lane's four columns
     const int Y0 = bi.z * P.rows_per_block;
     const int Y1 = min(Y0 + P.rows_per_block, H);
+    const int nrows = Y1 - Y0 + 2;         // node rows Y0 - 1 .. Y1
     const bool own = lane >= 1 && c0 < W;  // this lane's columns are output columns
     const float lam = P.lam;
+    float* extra = reinterpret_cast<float*>(a4_ring + A4_NS * A4_NARR * 32);
 
-    // node row y at this lane's four columns, with the fused PCG updates
-    auto load4 = [&](int y, bool owner) -> Node4 {
+    auto slot = [&](int s, int a) -> float4* { return a4_ring + (s * A4_NARR + a) * 32 + lane; };
+    // node row j (y = Y0 - 1 + j) and square row y of alpha into stage j mod 3
+    auto issue = [&](int j) {
+        const int s = j % A4_NS, y = Y0 - 1 + j;
+        const bool rv = y >= 0 && y < H && c0 >= 0 && c0 < W;
+        const long long o = rv ? (long long)y * pitch + c0 : 0;
+        cp_async16(slot(s, A4_F1), f1 + o, rv);
+        cp_async16(slot(s, A4_F2), f2 + o, rv);
+        cp_async16(slot(s, A4_Z0), vin + o, rv);
+        cp_async16(slot(s, A4_Z1), vin + o + plane, rv);
+        cp_async16(slot(s, A4_Z2), vin + o + 2 * plane, rv);
+        if (use_q) {
+            cp_async16(slot(s, A4_Q0), pold + o, rv);
+            cp_async16(slot(s, A4_Q1), pold + o + plane, rv);
+            cp_async16(slot(s, A4_Q2), pold + o + 2 * plane, rv);
+            if (own && y >= Y0 && y < Y1) {
+                cp_async16(slot(s, A4_D0), dcor + o, true);
+                cp_async16(slot(s, A4_D1), dcor + o + plane, true);
+                cp_async16(slot(s, A4_D2), dcor + o + 2 * plane, true);
+            }
+        }
+        if (j < nrows - 1) {  // square row y is used
+            const bool av = y >= 0 && y < H - 1 && c0 >= 0 && c0 < W - 1;
+            const long long oa = av ? 2 * ((long long)y * pitch + c0) : 0;
+            cp_async16(slot(s, A4_AL0), al + oa, av);
+            cp_async16(slot(s, A4_AL1), al + oa + 4, av);
+        }
+        if (lane == 31) {
+            const int x = c0 + 4;
+            const bool ev = y >= 0 && y < H && x < W;
+            const long long oe = ev ? (long long)y * pitch + x : 0;
+            float* e = extra + s * A4_EXTRA;
+            cp_async4(e + 0, f1 + oe, ev);
+            cp_async4(e + 1, f2 + oe, ev);
+            cp_async4(e + 2, vin + oe, ev);
+            cp_async4(e + 3, vin + oe + plane, ev);
+            cp_async4(e + 4, vin + oe + 2 * plane, ev);
+            if (use_q) {
+                cp_async4(e + 5, pold + oe, ev);
+                cp_async4(e + 6, pold + oe + plane, ev);
+                cp_async4(e + 7, pold + oe + 2 * plane, ev);
+            }
+        }
+    };
+    // node row j from its stage, with the fused PCG updates (owned rows)
+    auto finish = [&](int j) -> Node4 {
+        const int s = j % A4_NS, y = Y0 - 1 + j;
         Node4 n;
-        const float4 zero = f4(0.f);
-        if (y < 0 || y >= H || c0 < 0 || c0 >= W) {
-            n.p0 = n.p1 = n.p2 = n.f1 = n.f2 = zero;
-            return n;
+        n.f1 = mask4(*slot(s, A4_F1), c0, W);
+        n.f2 = mask4(*slot(s, A4_F2), c0, W);
+        float4 a = *slot(s, A4_Z0), b = *slot(s, A4_Z1), c = *slot(s, A4_Z2);
+        float4 qa = f4(0.f), qb = f4(0.f), qc = f4(0.f);
+        if (use_q) {
+            qa = *slot(s, A4_Q0);
+            qb = *slot(s, A4_Q1);
+            qc = *slot(s, A4_Q2);
+            a = fma4(beta, qa, a);
+            b = fma4(beta, qb, b);
+            c = fma4(beta, qc, c);
         }
-        const long long o = (long long)y * pitch + c0;
-        n.f1 = mask4(*reinterpret_cast<const float4*>(f1 + o), c0, W);
-        n.f2 = mask4(*reinterpret_cast<const float4*>(f2 + o), c0, W);
-        float4 a = *reinterpret_cast<const float4*>(vin + o);
-        float4 b = *reinterpret_cast<const float4*>(vin + o + plane);
-        float4 c = *reinterpret_cast<const float4*>(vin + o + 2 * plane);
-        if (MODE == MODE_PCG) {
-            // pitch padding of p_new and d is written too (as zeros / unchanged)
-            float* d = P.dcorr + vo;
-            if (!first) {
-                const float4 qa = *reinterpret_cast<const float4*>(pold + o);
-                const float4 qb = *reinterpret_cast<const float4*>(pold + o + plane);
-                const float4 qc = *reinterpret_cast<const float4*>(pold + o + 2 * plane);
-                if (owner) {
-                    float4* d0 = reinterpret_cast<float4*>(d + o);
-                    float4* d1 = reinterpret_cast<float4*>(d + o + plane);
-                    float4* d2 = reinterpret_cast<float4*>(d + o + 2 * plane);
-                    *d0 = fma4(a_prev, qa, *d0);
-                    *d1 = fma4(a_prev, qb, *d1);
-                    *d2 = fma4(a_prev, qc, *d2);
-                }
-                a = mask4(fma4(beta, qa, a), c0, W);
-                b = mask4(fma4(beta, qb, b), c0, W);
-                c = mask4(fma4(beta, qc, c), c0, W);
-            } else if (owner) {
-                *reinterpret_cast<float4*>(d + o) = zero;
-                *reinterpret_cast<float4*>(d + o + plane) = zero;
-                *reinterpret_cast<float4*>(d + o + 2 * plane) = zero;
+        // pitch padding of p_new is written as zeros
+        a = mask4(a, c0, W);
+        b = mask4(b, c0, W);
+        c = mask4(c, c0, W);
+        if (MODE == MODE_PCG && own && y >= Y0 && y < Y1) {
+            const long long o = (long long)y * pitch + c0;
+            if (use_q) {
+                *reinterpret_cast<float4*>(dcor + o) = fma4(a_prev, qa, *slot(s, A4_D0));
+                *reinterpret_cast<float4*>(dcor + o + plane) = fma4(a_prev, qb, *slot(s, A4_D1));
+                *reinterpret_cast<float4*>(dcor + o + 2 * plane) = fma4(a_prev, qc, *slot(s, A4_D2));
+            } else {
+                *reinterpret_cast<float4*>(dcor + o) = f4(0.f);
+                *reinterpret_cast<float4*>(dcor + o + plane) = f4(0.f);
+                *reinterpret_cast<float4*>(dcor + o + 2 * plane) = f4(0.f);
             }
-            if (first) {
-                a = mask4(a, c0, W);
-                b = mask4(b, c0, W);
-                c = mask4(c, c0, W);
-            }
-            if (owner) {
-                *reinterpret_cast<float4*>(pnew + o) = a;
-                *reinterpret_cast<float4*>(pnew + o + plane) = b;
-                *reinterpret_cast<float4*>(pnew + o + 2 * plane) = c;
-            }
+            *reinterpret_cast<float4*>(pnew + o) = a;
+            *reinterpret_cast<float4*>(pnew + o + plane) = b;
+            *reinterpret_cast<float4*>(pnew + o + 2 * plane) = c;
         }
-        if (MODE == MODE_PCG) {
-            n.p0 = a; n.p1 = b; n.p2 = c;
-        } else {
-            n.p0 = mask4(a, c0, W); n.p1 = mask4(b, c0, W); n.p2 = mask4(c, c0, W);
-        }
+        n.p0 = a;
+        n.p1 = b;
+        n.p2 = c;
         return n;
     };
-    // one extra column X0 + 124 for lane 31
-    auto load1 = [&](int x, int y) -> NodeVal<float> {
-        NodeVal<float> v;
-        if (x < 0 || x >= W || y < 0 || y >= H) {
-            v.p = v3(0.f, 0.f, 0.f);
-            v.f1 = v.f2 = 0.f;
-            return v;
-        }
-        const long long o = (long long)y * pitch + x;
-        v.f1 = f1[o];
-        v.f2 = f2[o];
-        float p0 = vin[o], p1 = vin[o + plane], p2 = vin[o + 2 * plane];
-        if (MODE == MODE_PCG && !first) {
-            p0 = fmaf(beta, pold[o], p0);
-            p1 = fmaf(beta, pold[o + plane], p1);
-            p2 = fmaf(beta, pold[o + 2 * plane], p2);
-        }
-        v.p = v3(p0, p1, p2);
-        return v;
-    };
-    auto right = [&](const Node4& n, int y) -> NodeVal<float> {
-        // first column of the next lane (lane 31: column X0 + 124)
+    // first column of the next lane (lane 31: column X0 + 124 from its slot)
+    auto right = [&](const Node4& n, int j) -> NodeVal<float> {
         NodeVal<float> v;
         v.p = v3(__shfl_down_sync(0xffffffffu, n.p0.x, 1), __shfl_down_sync(0xffffffffu, n.p1.x, 1),
                  __shfl_down_sync(0xffffffffu, n.p2.x, 1));
         v.f1 = __shfl_down_sync(0xffffffffu, n.f1.x, 1);
         v.f2 = __shfl_down_sync(0xffffffffu, n.f2.x, 1);
-        if (lane == 31) v = load1(c0 + 4, y);
+        if (lane == 31) {
+            const float* e = extra + (j % A4_NS) * A4_EXTRA;
+            float p0 = e[2], p1 = e[3], p2 = e[4];
+            if (use_q) {
+                p0 = fmaf(beta, e[5], p0);
+                p1 = fmaf(beta, e[6], p1);
+                p2 = fmaf(beta, e[7], p2);
+            }
+            v.p = v3(p0, p1, p2);
+            v.f1 = e[0];
+            v.f2 = e[1];
+        }
         return v;
     };
 
     float acc = 0.f;
-    Node4 cur = load4(Y0 - 1, false);
-    NodeVal<float> rcur = right(cur, Y0 - 1);
     V3<float> carry[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) carry[j] = v3(0.f, 0.f, 0.f);
-    for (int sy = Y0 - 1; sy < Y1; ++sy) {
-        const bool row_owned = (sy + 1 >= Y0) && (sy + 1 < Y1);
-        Node4 nxt = load4(sy + 1, own && row_owned);
-        NodeVal<float> rnxt = right(nxt, sy + 1);
-        float4 alA = f4(0.f), alB = f4(0.f);  // alpha of squares c0..c0+1 and c0+2..c0+3
-        const bool rowv = (sy >= 0) && (sy < H - 1) && c0 >= 0 && c0 < W - 1;
-        if (rowv) {
-            const float* ap = al + 2 * ((long long)sy * pitch + c0);
-            alA = *reinterpret_cast<const float4*>(ap);
-            alB = *reinterpret_cast<const float4*>(ap + 4);
-        }
-        const float alv[8] = {alA.x, alA.y, alA.z, alA.w, alB.x, alB.y, alB.z, alB.w};
-        V3<float> cA[4], cB[4], cC[4], cD[4], bdum;
+    Node4 cur;
+    NodeVal<float> rcur;
+    issue(0);
+    cp_async_commit();
+    for (int j = 0; j < nrows; ++j) {
+        if (j + 1 < nrows) issue(j + 1);
+        cp_async_commit();  // one group per row (possibly empty): row j is the older one
+        cp_async_wait1();
+        const Node4 nxt = finish(j);
+        const NodeVal<float> rnxt = right(nxt, j);
+        if (j >= 1) {
+            // square row sy between node rows sy (cur) and sy + 1 (nxt)
+            const int sy = Y0 - 2 + j;
+            const bool rowv = (sy >= 0) && (sy < H - 1) && c0 >= 0 && c0 < W - 1;
+            const float4 alA = *slot((j - 1) % A4_NS, A4_AL0), alB = *slot((j - 1) % A4_NS, A4_AL1);
+            const float alv[8] = {alA.x, alA.y, alA.z, alA.w, alB.x, alB.y, alB.z, alB.w};
+            V3<float> cA[4], cB[4], cC[4], cD[4], bdum;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int cx = c0 + j;
-            const bool valid = rowv && (cx < W - 1);
-            const NodeVal<float> A = pick(cur, j), D = pick(nxt, j);
-            const NodeVal<float> B = (j < 3) ? pick(cur, j + 1) : rcur;
-            const NodeVal<float> C = (j < 3) ? pick(nxt, j + 1) : rnxt;
-            square_contrib<float, false>(A, B, C, D, alv[2 * j], alv[2 * j + 1], lam, valid, cA[j], cB[j], cC[j],
-                                         cD[j], bdum, bdum, bdum, bdum);
-        }
-        // right corners of the previous lane's last square
-        const V3<float> pB = v3(__shfl_up_sync(0xffffffffu, cB[3].a, 1), __shfl_up_sync(0xffffffffu, cB[3].b, 1),
-                                __shfl_up_sync(0xffffffffu, cB[3].c, 1));
-        const V3<float> pC = v3(__shfl_up_sync(0xffffffffu, cC[3].a, 1), __shfl_up_sync(0xffffffffu, cC[3].b, 1),
-                                __shfl_up_sync(0xffffffffu, cC[3].c, 1));
-        V3<float> out[4];
-        out[0] = carry[0] + cA[0] + pB;
+            for (int k = 0; k < 4; ++k) {
+                const bool valid = rowv && (c0 + k < W - 1);
+                const NodeVal<float> A = pick(cur, k), D = pick(nxt, k);
+                const NodeVal<float> B = (k < 3) ? pick(cur, k + 1) : rcur;
+                const NodeVal<float> C = (k < 3) ? pick(nxt, k + 1) : rnxt;
+                square_contrib<float, false>(A, B, C, D, alv[2 * k], alv[2 * k + 1], lam, valid, cA[k], cB[k], cC[k],
+                                             cD[k], bdum, bdum, bdum, bdum);
+            }
+            // right corners of the previous lane's last square
+            const V3<float> pB = v3(__shfl_up_sync(0xffffffffu, cB[3].a, 1), __shfl_up_sync(0xffffffffu, cB[3].b, 1),
+                                    __shfl_up_sync(0xffffffffu, cB[3].c, 1));
+            const V3<float> pC = v3(__shfl_up_sync(0xffffffffu, cC[3].a, 1), __shfl_up_sync(0xffffffffu, cC[3].b, 1),
+                                    __shfl_up_sync(0xffffffffu, cC[3].c, 1));
+            V3<float> out[4];
+            out[0] = carry[0] + cA[0] + pB;
 #pragma unroll
-        for (int j = 1; j < 4; ++j) out[j] = carry[j] + cA[j] + cB[j - 1];
-        if (sy >= Y0 && own) {
-            const long long o = (long long)sy * pitch + c0;
-            float* q = P.out + vo;
-            *reinterpret_cast<float4*>(q + o) = make_float4(out[0].a, out[1].a, out[2].a, out[3].a);
-            *reinterpret_cast<float4*>(q + o + plane) = make_float4(out[0].b, out[1].b, out[2].b, out[3].b);
-            *reinterpret_cast<float4*>(q + o + 2 * plane) = make_float4(out[0].c, out[1].c, out[2].c, out[3].c);
-            if (MODE == MODE_PCG) {
+            for (int k = 1; k < 4; ++k) out[k] = carry[k] + cA[k] + cB[k - 1];
+            if (sy >= Y0 && own) {
+                const long long o = (long long)sy * pitch + c0;
+                float* q = P.out + vo;
+                *reinterpret_cast<float4*>(q + o) = make_float4(out[0].a, out[1].a, out[2].a, out[3].a);
+                *reinterpret_cast<float4*>(q + o + plane) = make_float4(out[0].b, out[1].b, out[2].b, out[3].b);
+                *reinterpret_cast<float4*>(q + o + 2 * plane) = make_float4(out[0].c, out[1].c, out[2].c, out[3].c);
+                if (MODE == MODE_PCG) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const NodeVal<float> pj = pick(cur, j);
-                    acc += pj.p.a * out[j].a + pj.p.b * out[j].b + pj.p.c * out[j].c;
+                    for (int k = 0; k < 4; ++k) {
+                        const NodeVal<float> pk = pick(cur, k);
+                        acc += pk.p.a * out[k].a + pk.p.b * out[k].b + pk.p.c * out[k].c;
+                    }
                 }
             }
-        }
-        carry[0] = cD[0] + pC;
+            carry[0] = cD[0] + pC;
 #pragma unroll
-        for (int j = 1; j < 4; ++j) carry[j] = cD[j] + cC[j - 1];
+            for (int k = 1; k < 4; ++k) carry[k] = cD[k] + cC[k - 1];
+        }
         cur = nxt;
         rcur = rnxt;
     }
@@ -564,7 +615,6 @@ __global__ void __launch_bounds__(32) k_apply4(const ApplyParams<float, float, f
     // warp partial (FP32 within the warp), then the pair's last block reduces
     // the block partials in order in FP64
     const float s0 = warp_sum(acc);
-    __shared__ double sh_red[1];
     __shared__ int sh_last;
     if (lane == 0) {
         P.partial[2 * (long long)bi.w] = (double)s0;
@@ -574,7 +624,6 @@ __global__ void __launch_bounds__(32) k_apply4(const ApplyParams<float, float, f
     double t0 = 0.0;
     for (int i = lane; i < pd.nblk; i += 32) t0 += __ldcg(P.partial + 2 * (long long)(pd.blk0 + i));
     t0 = warp_sum(t0);
-    (void)sh_red;
     if (lane == 0) {
         PairScalars* s = P.sc + pair;
         s->pq = t0;

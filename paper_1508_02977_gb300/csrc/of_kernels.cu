@@ -245,7 +245,7 @@ static cudaError_t pcg_apply_t(const SolveBufs& B, cudaStream_t st) {
     P.p_buf1 = (R*)B.p1;
     P.dcorr = (R*)B.d;
     P.out = (R*)B.q;
-    if constexpr (sizeof(R) == 4) k_apply4<MODE_PCG><<<B.nblk, 32, 0, st>>>(P);  // FP32: four columns per lane
+    if constexpr (sizeof(R) == 4) k_apply4<MODE_PCG><<<B.nblk, 32, apply4_smem_bytes(), st>>>(P);  // FP32: four columns per lane
     else k_apply<R, R, R, MODE_PCG, false, APPLY_NW><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
     return cudaGetLastError();
 }
@@ -267,7 +267,7 @@ static cudaError_t apply_t(const SolveBufs& B, int blk0, int nblk, const void* p
     P.out = (R*)q;
     P.bout = (R*)b;
     if (b) k_apply<R, R, R, MODE_APPLY, true, APPLY_NW><<<nblk, APPLY_NW * 32, 0, st>>>(P);
-    else if constexpr (sizeof(R) == 4) k_apply4<MODE_APPLY><<<nblk, 32, 0, st>>>(P);
+    else if constexpr (sizeof(R) == 4) k_apply4<MODE_APPLY><<<nblk, 32, apply4_smem_bytes(), st>>>(P);
     else k_apply<R, R, R, MODE_APPLY, false, APPLY_NW><<<nblk, APPLY_NW * 32, 0, st>>>(P);
     return cudaGetLastError();
 }

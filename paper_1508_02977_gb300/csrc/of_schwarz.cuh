@@ -35,13 +35,16 @@
 //  1. TMA (cp.async.bulk.tensor) brings the two cell planes over the
 //     extended tile plus a one-node ring and the owned tiles of r and q into
 //     one of two stages (one mbarrier each, bounded waits); the next
-//     subdomain's copies are issued before this one is processed.
+//     subdomain's copies are issued as soon as this one's setup is done, so
+//     they stream in during its sweeps.
 //  2. Each thread owns, per colour, the nodes of a host-built table that
 //     gives the 32 lanes of a warp 32 distinct shared-memory banks; it forms
 //     their LDL^T-factored 3x3 diagonal blocks and right-hand sides in
-//     registers (r <- r - a q fused here).
+//     registers (r <- r - a q fused here).  The first colour step from z = 0
+//     is block Jacobi, z_n = D_n^{-1} r_n, done right here for colour 0.
 //  3. Sweeps: one block update per owned node and colour step,
-//     z_n = D_n^{-1} (r_n - sum_K h_K (h_K . (z_j + z_k)) + sum_e w_e z_e).
+//     z_n = D_n^{-1} (r_n - sum_K h_K (h_K . (z_j + z_k)) + sum_e w_e z_e);
+//     the first colour-1 step skips the colour-2 neighbours (still zero).
 //  4. Coalesced write-out of z and r on the owned tile, FP64 partials of
 //     r.r and r.z, deterministic last-CTA reduction per pair.
 #pragma once
@@ -288,9 +291,25 @@ __device__ __forceinline__ void node_block(const CellView<R>& C, int c, int RW, 
     B = ldl3<R>(D00 + ws, D01, D02, D11 + ws, D12, D22 + (lE + lN + lW + lS));
 }
 
+// lambda weight of a leg: 1/2 lambda per triangle on it (legs: 2-bit counts
+// E, N, W, S); away from the image border every leg has two
 template <typename R>
-__device__ __forceinline__ void node_sweep(const CellView<R>& C, R* __restrict__ Z, int zplane, int c, int RW, R lE,
-                                           R lN, R lW, R lS, const Blk<R>& B, R b0, R b1, R b2) {
+__device__ __forceinline__ R lam_edges(unsigned legs, R hl, R zE2, R zN2, R zW2, R zS2) {
+    if (legs == 0xAAu) return (hl + hl) * ((zE2 + zN2) + (zW2 + zS2));
+    return hl * (R(legs & 3u) * zE2 + R((legs >> 2) & 3u) * zN2 + R((legs >> 4) & 3u) * zW2 + R(legs >> 6) * zS2);
+}
+
+template <typename R>
+__device__ __forceinline__ void block_solve(const Blk<R>& B, R b0, R b1, R b2, R& x0, R& x1, R& x2) {
+    const R y1 = b1 - B.l10 * b0, y2 = b2 - B.l20 * b0 - B.l21 * y1;
+    x2 = y2 * B.i2;
+    x1 = y1 * B.i1 - B.l21 * x2;
+    x0 = b0 * B.i0 - B.l10 * x1 - B.l20 * x2;
+}
+
+template <typename R>
+__device__ __forceinline__ void node_sweep(const CellView<R>& C, R* __restrict__ Z, int zplane, int c, int RW,
+                                           unsigned legs, R hl, const Blk<R>& B, R b0, R b1, R b2) {
     const R* z0 = Z;
     const R* z1 = Z + zplane;
     const R* z2 = Z + 2 * zplane;
@@ -316,11 +335,46 @@ __device__ __forceinline__ void node_sweep(const CellView<R>& C, R* __restrict__
     C.t1(c - RW, h, wS);        elem(zS0 + zE0, zS1 + zE1, zS2 + zE2);     // E6
     b0 += wE * zE0 + wN * zN0 + wW * zW0 + wS * zS0;
     b1 += wE * zE1 + wN * zN1 + wW * zW1 + wS * zS1;
-    b2 += lE * zE2 + lN * zN2 + lW * zW2 + lS * zS2;
-    const R y1 = b1 - B.l10 * b0, y2 = b2 - B.l20 * b0 - B.l21 * y1;
-    const R x2 = y2 * B.i2;
-    const R x1 = y1 * B.i1 - B.l21 * x2;
-    const R x0 = b0 * B.i0 - B.l10 * x1 - B.l20 * x2;
+    b2 += lam_edges(legs, hl, zE2, zN2, zW2, zS2);
+    R x0, x1, x2;
+    block_solve(B, b0, b1, b2, x0, x1, x2);
+    Z[c] = x0;
+    Z[c + zplane] = x1;
+    Z[c + 2 * zplane] = x2;
+}
+
+// The first colour-1 update of a sweep sequence that starts from z = 0 and
+// a colour-0 block-Jacobi step: the colour-2 neighbours (E, N, SW) are still
+// zero, so only the W, S and NE values enter.
+template <typename R>
+__device__ __forceinline__ void node_sweep_first1(const CellView<R>& C, R* __restrict__ Z, int zplane, int c, int RW,
+                                                  unsigned legs, R hl, const Blk<R>& B, R b0, R b1, R b2) {
+    const R* z0 = Z;
+    const R* z1 = Z + zplane;
+    const R* z2 = Z + 2 * zplane;
+    const int iW = c - 1, iS = c - RW, iNE = c + RW + 1;
+    const R zW0 = z0[iW], zW1 = z1[iW], zW2 = z2[iW];
+    const R zS0 = z0[iS], zS1 = z1[iS], zS2 = z2[iS];
+    const R zNE0 = z0[iNE], zNE1 = z1[iNE], zNE2 = z2[iNE];
+    R h[3] = {R(0), R(0), R(0)}, wW, wS, dummy;
+    auto elem = [&](R s0, R s1, R s2) {
+        const R s = h[0] * s0 + h[1] * s1 + h[2] * s2;
+        b0 -= s * h[0];
+        b1 -= s * h[1];
+        b2 -= s * h[2];
+    };
+    C.t0(c, h, dummy);          elem(zNE0, zNE1, zNE2);  // E1
+    C.t1(c, h, dummy);          elem(zNE0, zNE1, zNE2);  // E2
+    C.t0(c - RW - 1, h, dummy); elem(zS0, zS1, zS2);     // E3
+    C.t1(c - RW - 1, h, dummy); elem(zW0, zW1, zW2);     // E4
+    C.t0(c - 1, h, wW);         elem(zW0, zW1, zW2);     // E5
+    C.t1(c - RW, h, wS);        elem(zS0, zS1, zS2);     // E6
+    b0 += wW * zW0 + wS * zS0;
+    b1 += wW * zW1 + wS * zS1;
+    const R z = R(0);
+    b2 += lam_edges(legs, hl, z, z, zW2, zS2);
+    R x0, x1, x2;
+    block_solve(B, b0, b1, b2, x0, x1, x2);
     Z[c] = x0;
     Z[c + zplane] = x1;
     Z[c + 2 * zplane] = x2;
@@ -361,10 +415,13 @@ template <typename R> struct NodeState {
 template <typename R>
 __device__ __forceinline__ void node_step(const CellView<R>& C, R* Zs, int nc, int RW, R hl, const NodeState<R>& n) {
     if (n.c == -1) return;
-    const int c = n.c & 0xffffff;
-    const unsigned nb = (unsigned)n.c >> 24;
-    node_sweep<R>(C, Zs, nc, c, RW, hl * R(nb & 3u), hl * R((nb >> 2) & 3u), hl * R((nb >> 4) & 3u),
-                  hl * R(nb >> 6), n.B, n.b0, n.b1, n.b2);
+    node_sweep<R>(C, Zs, nc, n.c & 0xffffff, RW, (unsigned)n.c >> 24, hl, n.B, n.b0, n.b1, n.b2);
+}
+template <typename R>
+__device__ __forceinline__ void node_step_first1(const CellView<R>& C, R* Zs, int nc, int RW, R hl,
+                                                 const NodeState<R>& n) {
+    if (n.c == -1) return;
+    node_sweep_first1<R>(C, Zs, nc, n.c & 0xffffff, RW, (unsigned)n.c >> 24, hl, n.B, n.b0, n.b1, n.b2);
 }
 
 // Block Jacobi: z = D^{-1} r, no neighbour terms.
@@ -372,9 +429,8 @@ template <typename R>
 __device__ __forceinline__ void node_jacobi(R* Zs, int nc, const NodeState<R>& n) {
     if (n.c == -1) return;
     const int c = n.c & 0xffffff;
-    const Blk<R>& B = n.B;
-    const R y1 = n.b1 - B.l10 * n.b0, y2 = n.b2 - B.l20 * n.b0 - B.l21 * y1;
-    const R x2 = y2 * B.i2, x1 = y1 * B.i1 - B.l21 * x2, x0 = n.b0 * B.i0 - B.l10 * x1 - B.l20 * x2;
+    R x0, x1, x2;
+    block_solve(n.B, n.b0, n.b1, n.b2, x0, x1, x2);
     Zs[c] = x0;
     Zs[c + nc] = x1;
     Zs[c + 2 * nc] = x2;
@@ -406,6 +462,10 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         mbar_init(&bars[1], 1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    // the ring around the extended tile is never written: the Dirichlet zeros
+    // of every item.  Inside the extended tile every position is written by its
+    // owner before it is read (zeros where the tile is clipped by the image).
+    for (int i = threadIdx.x; i < 3 * nc; i += NT) Zs[i] = R(0);
     __syncthreads();
 
     // a work item is processed unless its pair has finished (a pair's flag is
@@ -427,11 +487,24 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         if (need_q) tma_load_3d(st + L.qs, tm + TM_Q, x0, y0, 0, &bars[s]);
     };
     const int G = gridDim.x;
+    // A pair's done flag only changes in the last CTA, after every item of
+    // the launch: read the first 32 once (a register mask), so that skipping
+    // finished pairs costs no dependent global load per item.
+    unsigned done_mask = 0u;
+    if (!P.apply_only && P.npairs <= 32) {
+        const int l = threadIdx.x & 31;
+        done_mask = __ballot_sync(0xffffffffu, l < P.npairs && P.sc[l].done != 0);
+    }
+    auto pair_done = [&](int pair) -> bool {
+        if (P.apply_only) return false;
+        if (P.npairs <= 32) return (done_mask >> pair) & 1u;
+        return P.sc[pair].done != 0;
+    };
     // next active item at or after t (slow path: loads until an active one)
     auto advance = [&](int t, int4& ti) {
         while (t < P.ntiles) {
             ti = P.tiles[t];
-            if (P.apply_only || !P.sc[ti.x].done) return t;
+            if (!pair_done(ti.x)) return t;
             t += G;
         }
         return t;
@@ -451,8 +524,6 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
     unsigned phase[2] = {0u, 0u};
     int s = 0;
     for (; t < P.ntiles;) {
-        // the next active item of this CTA goes into the other stage
-        if (nstage == 2 && tn < P.ntiles && threadIdx.x == 0) issue(tin, s ^ 1);
         // software pipelining: the item after next is fetched now and used one
         // iteration later, so its descriptor loads overlap this item's work
         const int tc = tn + G;
@@ -460,7 +531,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         int dc = 0;
         if (tn < P.ntiles && tc < P.ntiles) {
             tic = P.tiles[tc];
-            dc = P.apply_only ? 0 : P.sc[tic.x].done;
+            dc = pair_done(tic.x);
         }
 
         if (threadIdx.x == 0 && !mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit)) {
@@ -471,10 +542,8 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         if (sh_fail) {
             // give the copies in flight a last chance to land, then stop
             // processing (the CTA still arrives below, so the launch ends)
-            if (threadIdx.x == 0) {
-                mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit);
-                if (nstage == 2 && tn < P.ntiles) mbar_wait_phase_bounded(&bars[s ^ 1], phase[s ^ 1], P.spin_limit);
-            }
+            // (the next item's copies are only issued after the setup below)
+            if (threadIdx.x == 0) mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit);
             break;
         }
         if (!mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit)) atomicOr(P.err, 1);
@@ -512,8 +581,13 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
                 if (e == 0xffffffffu) continue;
                 const int li = (int)(e & 0xffffu), lj = (int)(e >> 16);
                 const int gx = x0 - ov + li, gy = y0 - ov + lj;
-                if (gx < ex0 || gx >= ex1 || gy < ey0 || gy >= ey1) continue;
                 const int c = (lj + 1) * RW + (li + cpad - ov);
+                if (gx < ex0 || gx >= ex1 || gy < ey0 || gy >= ey1) {
+                    Zs[c] = R(0);
+                    Zs[c + nc] = R(0);
+                    Zs[c + 2 * nc] = R(0);
+                    continue;
+                }
                 // existing triangles on the four legs (the lambda weight is 1/2 lambda each)
                 const int vc = (gx < W - 1 && gy < H - 1), vsw = (gx >= 1 && gy >= 1);
                 const int vw = (gx >= 1 && gy < H - 1), vs = (gx < W - 1 && gy >= 1);
@@ -535,10 +609,14 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
                     n.b1 = v1;
                     n.b2 = v2;
                 }
+                // the first colour step from z = 0 is block Jacobi on colour 0
+                if (col == 0) node_jacobi<R>(Zs, nc, n);
             }
         }
-        for (int i = threadIdx.x; i < 3 * nc; i += NT) Zs[i] = R(0);
         __syncthreads();
+        // the next active item of this CTA goes into the other stage (the bulk
+        // stores that read that stage were issued an item ago and are done by now)
+        if (nstage == 2 && tn < P.ntiles && threadIdx.x == 0) issue(tin, s ^ 1);
 
         // ---- sweeps (colour order 0,1,2,1,0,1,2,1,0,...; sweeps = 0: block Jacobi)
 #define OF_STEP(col)                                                 \
@@ -549,12 +627,18 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
     }
         if (P.sweeps == 0) {
 #pragma unroll
-            for (int col = 0; col < 3; ++col)
+            for (int col = 1; col < 3; ++col)
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) node_jacobi<R>(Zs, nc, ns[col][k]);
             __syncthreads();
         } else {
-            for (int sw = 0; sw < P.sweeps; ++sw) {
+            // colour 0 of the first sweep was the Jacobi step above
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) node_step_first1<R>(C, Zs, nc, RW, hl, ns[1][k]);
+            __syncthreads();
+            OF_STEP(2)
+            OF_STEP(1)
+            for (int sw = 1; sw < P.sweeps; ++sw) {
                 OF_STEP(0)
                 OF_STEP(1)
                 OF_STEP(2)
@@ -601,12 +685,13 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
             tma_store_3d(tm + TM_Z, x0, y0, 0, Zo);
             if (need_q) tma_store_3d(tm + TM_R, x0, y0, 0, Rs);
             bulk_commit();
-            if (!P.apply_only) {
-                double a2 = 0.0, b2 = 0.0;
-                for (int w = 0; w < (NT >> 5); ++w) {
-                    a2 += sh_red[w];
-                    b2 += sh_red[16 + w];
-                }
+        }
+        if (!P.apply_only && threadIdx.x < 32) {
+            // the item's partials: warp sums of the CTA in a fixed order
+            const int l = threadIdx.x;
+            const bool w = l < (NT >> 5);
+            const double a2 = warp_sum(w ? sh_red[l] : 0.0), b2 = warp_sum(w ? sh_red[16 + l] : 0.0);
+            if (l == 0) {
                 P.partial[2 * (long long)ti.w] = a2;
                 P.partial[2 * (long long)ti.w + 1] = b2;
             }
