@@ -43,8 +43,8 @@ RTOL = 1e-6
 #   schwarz:   read r, q (2 x 12) + f1, f2, alpha (16);         write r, z (2 x 12)
 #   residual:  read x (24), d, p (2 x 12), f1, f2, alpha (16);  write x (24), r (12)
 ALG_BYTES_PER_PX = {"pcg_apply": 88, "schwarz": 64, "residual": 100}
-KERNEL_NAMES = {"pcg_apply": "k_apply<float,float,float,MODE_PCG>", "schwarz": "k_schwarz<float>",
-                "residual": "k_apply<double,float,float,MODE_RES>"}
+KERNEL_NAMES = {"pcg_apply": "k_apply4<MODE_PCG>", "schwarz": "k_schwarz<float,2,48,48,0>",
+                "residual": "k_apply<double,float,float,MODE_RES,DF>"}
 
 
 def kernel_source_hash() -> str:
