@@ -34,8 +34,8 @@ METRIC = "Mpixel/s solved to rel. residual 1e-6 (mixed vs FP64 GPU); HBM GB/s vs
 UNIT = "Mpixel/s"
 WORKLOAD_W, WORKLOAD_H = 3840, 2160
 # launch configuration of the timed solve (tile, overlap, sweeps, precision)
-WORKLOAD_OPTS = dict(tile=(48, 48), overlap=0, sweeps=3, precision=1)
-FP64_OPTS = dict(tile=(32, 16), overlap=0, sweeps=3, precision=0)
+WORKLOAD_OPTS = dict(tile=(48, 48), overlap=0, sweeps=4, precision=1, omega=1.6)
+FP64_OPTS = dict(tile=(32, 16), overlap=0, sweeps=3, precision=0, omega=1.6)
 RTOL = 1e-6
 # algorithmic bytes per pixel of one launch of each solve kernel (FP32 inner
 # vectors; each word read or written once):

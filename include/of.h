@@ -79,10 +79,13 @@ typedef enum {
 typedef struct {
     int tile_x, tile_y;      /* owned subdomain tile in nodes, multiples of 4 [32 x 32] */
     int overlap;             /* extension of each subdomain on interior sides, nodes (0: none) */
-    int sweeps;              /* symmetric 3-colour block Gauss-Seidel sweeps per local solve [1] */
+    int sweeps;              /* symmetric 3-colour block SOR sweeps per local solve [1] */
     of_precision precision;  /* [OF_PREC_FP64] */
     double lambda;           /* regularisation of m (Eq. BW2) [1.0] */
     of_preconditioner preconditioner;  /* [OF_PC_SCHWARZ] */
+    double omega;            /* relaxation factor of the local sweeps, 0 < omega < 2 [1.0: block
+                                Gauss-Seidel]; any such value keeps the preconditioner symmetric
+                                positive definite (the colour order is a palindrome) */
 } of_grid_opts;
 
 /* Solve options.  A field left at 0 takes the default in brackets. */

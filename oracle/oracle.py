@@ -190,6 +190,69 @@ class System:
             raise RuntimeError(f"oracle Schwarz failed ({rc})")
         return U.reshape(3, self.H, self.W), hist
 
+    def _sparse(self):
+        import scipy.sparse as sp
+        if getattr(self, "_A", None) is None:
+            self._A = sp.csr_matrix((self.val, self.col, self.rowptr), shape=(self.n, self.n))
+        return self._A
+
+    def schwarz_sweeps(self, r, tile, overlap, sweeps, omega=1.0):
+        """The symmetric restricted Schwarz preconditioner z = M r with
+        approximate local solves, written out plainly (the CUDA path's
+        subdomain solver; the paper solves each subdomain exactly, Section 3.2).
+
+        Owned tiles T_i of tile[0] x tile[1] nodes from the origin, clipped at
+        the image edge; extended tiles E_i = T_i plus `overlap` node layers,
+        clipped.  Local problem: A restricted to E_i (zero Dirichlet values
+        outside E_i), right-hand side r on T_i and 0 on the rest of E_i.  It is
+        solved from z = 0 by symmetric 3-colour block SOR: colour (i + j) mod 3
+        in the coordinates of the unclipped extended tile (nodes of one colour
+        are not coupled), colours visited 0,1,2,1 `sweeps` times and then 0;
+        a visit sets z_n <- z_n + omega (D_n^{-1} (b_n - sum_{m != n} A_nm z_m)
+        - z_n) for every node n of the colour, D_n the 3x3 diagonal block.
+        sweeps = 0 is block Jacobi, z_n = D_n^{-1} b_n.  z is the sum over i
+        of the owned part of each local solution."""
+        A = self._sparse()
+        W, H, HW = self.W, self.H, self.W * self.H
+        r = _c(r).ravel()
+        z = np.zeros(self.n)
+        tx, ty = int(tile[0]), int(tile[1])
+        seq = [0, 1, 2, 1] * int(sweeps) + [0]
+        for y0 in range(0, H, ty):
+            for x0 in range(0, W, tx):
+                ox1, oy1 = min(x0 + tx, W), min(y0 + ty, H)
+                ex0, ey0 = max(x0 - overlap, 0), max(y0 - overlap, 0)
+                ex1, ey1 = min(ox1 + overlap, W), min(oy1 + overlap, H)
+                ys, xs = np.mgrid[ey0:ey1, ex0:ex1]
+                ys, xs = ys.ravel(), xs.ravel()
+                m = xs.size
+                idx = np.concatenate([ys * W + xs + c * HW for c in range(3)])
+                Ai = A[idx][:, idx].tocsr()
+                owned = (xs >= x0) & (xs < ox1) & (ys >= y0) & (ys < oy1)
+                own3 = np.tile(owned, 3)
+                b = np.where(own3, r[idx], 0.0)
+                colour = ((xs - (x0 - overlap)) + (ys - (y0 - overlap))) % 3
+                D = np.empty((m, 3, 3))
+                dense_diag = {}
+                for c in range(3):
+                    for d in range(3):
+                        dense_diag[c, d] = np.asarray(Ai[c * m + np.arange(m), d * m + np.arange(m)]).ravel()
+                        D[:, c, d] = dense_diag[c, d]
+                zi = np.zeros((3, m))
+                bi = b.reshape(3, m)
+                if sweeps == 0:
+                    zi = np.linalg.solve(D, bi.T[..., None])[..., 0].T
+                else:
+                    for c in seq:
+                        sel = np.nonzero(colour == c)[0]
+                        y = (Ai @ zi.ravel()).reshape(3, m)
+                        zn = zi[:, sel].T
+                        rhs = bi[:, sel].T - y[:, sel].T + np.einsum("kij,kj->ki", D[sel], zn)
+                        x = np.linalg.solve(D[sel], rhs[..., None])[..., 0]
+                        zi[:, sel] = (zn + omega * (x - zn)).T
+                z[idx[own3]] = zi.ravel()[own3]
+        return z.reshape(3, H, W)
+
     def indicator(self, U):
         L = _load()
         eta = np.zeros((self.H - 1, self.W - 1, 2))

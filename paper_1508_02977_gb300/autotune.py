@@ -1,4 +1,4 @@
-"""Autotuner for the subdomain tile, overlap and sweep count.
+"""Autotuner for the subdomain tile, overlap, sweep count and relaxation factor.
 
 For a frame size class it times complete solves (to the same relative
 residual) of a representative pair for each candidate configuration and
@@ -15,11 +15,19 @@ import time
 
 from . import partition
 
+# (tile, overlap, sweeps[, omega]); omega defaults to 1 (block Gauss-Seidel)
 DEFAULT_CANDIDATES = (
-    ((48, 48), 0, 3), ((48, 48), 0, 2), ((32, 32), 0, 3), ((32, 32), 0, 2), ((40, 40), 0, 3),
-    ((48, 48), 0, 4), ((64, 32), 0, 3), ((32, 32), 2, 2), ((48, 48), 2, 3), ((32, 32), 0, 1),
+    ((48, 48), 0, 4, 1.6), ((48, 48), 0, 3, 1.6), ((48, 48), 0, 3, 1.0), ((48, 48), 0, 2, 1.5),
+    ((48, 48), 0, 4, 1.7), ((32, 32), 0, 3, 1.6), ((64, 32), 0, 3, 1.6), ((40, 40), 0, 3, 1.6),
+    ((32, 32), 2, 2, 1.0), ((32, 32), 0, 1, 1.0),
 )
-FALLBACK = {"tile": (48, 48), "overlap": 0, "sweeps": 3}
+FALLBACK = {"tile": (48, 48), "overlap": 0, "sweeps": 4, "omega": 1.6}
+
+
+def _norm(c):
+    (tx, ty), ov, sw = c[0], c[1], c[2]
+    om = float(c[3]) if len(c) > 3 else 1.0
+    return (int(tx), int(ty)), int(ov), int(sw), om
 
 
 def size_class(W: int, H: int) -> str:
@@ -37,7 +45,7 @@ def prior_order(candidates, W: int, H: int):
     """Candidates sorted by the Section 3.1 prior: larger area/perimeter of
     the owned tile first (then fewer overlap nodes, then fewer sweeps)."""
     def key(c):
-        (tx, ty), ov, sw = c
+        (tx, ty), ov, sw, _ = _norm(c)
         return (-partition.part_ratio(tx, ty, 1, 1), partition.overlap_inflation(tx, ty, ov), sw)
     return sorted(candidates, key=key)
 
@@ -68,7 +76,8 @@ def lookup(W: int, H: int, precision: int = 1, device_name: str = "", path=None)
     """The cached best configuration for this size class, else the default."""
     d = load_cache(path).get(_key(W, H, precision, device_name))
     if d:
-        return {"tile": tuple(d["tile"]), "overlap": int(d["overlap"]), "sweeps": int(d["sweeps"])}
+        return {"tile": tuple(d["tile"]), "overlap": int(d["overlap"]), "sweeps": int(d["sweeps"]),
+                "omega": float(d.get("omega", 1.0))}
     return dict(FALLBACK)
 
 
@@ -91,11 +100,13 @@ def autotune(W: int, H: int, f1=None, f2=None, alpha0: float = 0.05, lam: float 
     t2 = torch.as_tensor(f2).to(dev, dt).contiguous()
     results = []
     stream = torch.cuda.current_stream(dev)
-    for (tile, ov, sw) in prior_order(candidates or DEFAULT_CANDIDATES, W, H):
+    for cand in prior_order(candidates or DEFAULT_CANDIDATES, W, H):
+        tile, ov, sw, om = _norm(cand)
         h = S.of_create(device, stream)
         try:
             try:
-                S.of_setup_grid(h, [(W, H)], tile=tile, overlap=ov, sweeps=sw, precision=precision, lam=lam)
+                S.of_setup_grid(h, [(W, H)], tile=tile, overlap=ov, sweeps=sw, precision=precision, lam=lam,
+                                omega=om)
             except S.OFError:
                 continue  # shape not supported for this precision (shared memory / registers)
             S.of_set_frames(h, 0, t1, t2)
@@ -109,7 +120,7 @@ def autotune(W: int, H: int, f1=None, f2=None, alpha0: float = 0.05, lam: float 
             e1.record(stream)
             torch.cuda.synchronize(dev)
             ms = e0.elapsed_time(e1) / reps
-            results.append({"tile": list(tile), "overlap": ov, "sweeps": sw, "ms": ms,
+            results.append({"tile": list(tile), "overlap": ov, "sweeps": sw, "omega": om, "ms": ms,
                             "iters": info[0]["inner_iters"]})
             if verbose:
                 print(json.dumps(results[-1]), flush=True)
@@ -118,7 +129,7 @@ def autotune(W: int, H: int, f1=None, f2=None, alpha0: float = 0.05, lam: float 
     if not results:
         return dict(FALLBACK)
     best = min(results, key=lambda r: r["ms"])
-    out = {"tile": tuple(best["tile"]), "overlap": best["overlap"], "sweeps": best["sweeps"]}
+    out = {"tile": tuple(best["tile"]), "overlap": best["overlap"], "sweeps": best["sweeps"], "omega": best["omega"]}
     if cache:
         name = torch.cuda.get_device_name(dev)
         d = load_cache(path)

@@ -236,6 +236,7 @@ ofl::SolveBufs solve_bufs(of_ctx* h) {
     B.ov = h->opts.overlap;
     B.sweeps = h->opts.sweeps;
     B.lam = h->opts.lambda;
+    B.omega = h->opts.omega;
     B.fp64 = h->fp64;
     B.spin_limit = 4000000000LL;  // ~2 s at 2 GHz
     return B;
@@ -553,6 +554,7 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     if (opt.tile_x == 0) opt.tile_x = 32;
     if (opt.tile_y == 0) opt.tile_y = 32;
     if (opt.lambda == 0) opt.lambda = 1.0;
+    if (opt.omega == 0) opt.omega = 1.0;
     if (opt.preconditioner == OF_PC_JACOBI) {
         opt.overlap = 0;
         opt.sweeps = 0;
@@ -560,6 +562,7 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
         if (opt.sweeps == 0) opt.sweeps = 1;
     }
     if (!(opt.lambda > 0)) return fail(h, OF_ERR_ARG, "lambda must be > 0");
+    if (!(opt.omega > 0 && opt.omega < 2)) return fail(h, OF_ERR_ARG, "omega must be in (0, 2)");
     if (opt.tile_x < 4 || opt.tile_y < 4 || opt.tile_x % 4 || opt.tile_y % 4 || opt.tile_x > 256 || opt.tile_y > 256)
         return fail(h, OF_ERR_ARG, "tile sizes must be multiples of 4 in [4, 256]");
     if (opt.overlap < 0 || opt.overlap > 32 || opt.sweeps < 0 || opt.sweeps > 64)

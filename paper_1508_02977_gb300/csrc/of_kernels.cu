@@ -123,6 +123,7 @@ static SchwarzParams schwarz_params(const SolveBufs& B) {
     S.r = B.r;
     S.z = B.z;
     S.lam = B.lam;
+    S.omega = B.omega;
     S.Tx = B.Tx;
     S.Ty = B.Ty;
     S.ov = B.ov;

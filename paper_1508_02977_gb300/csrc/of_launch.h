@@ -45,6 +45,7 @@ struct SolveBufs {
     int nblk, ntiles, rows_per_block, npairs;
     int Tx, Ty, ov, sweeps;
     double lam;
+    double omega;  // relaxation factor of the local block SOR sweeps
     int fp64;            // 1: everything FP64; 0: FP32 inner with FP64 residual
     long long spin_limit;
     int use_cond;        // Schwarz launches inside the inner-loop graph set its condition

@@ -10,10 +10,14 @@
 // restricted to the extended tile with homogeneous Dirichlet values outside
 // it (the algebraic form of the Dirichlet transmission condition on
 // Gamma_ij) and the natural Neumann condition on the image boundary.  It is
-// solved approximately by `s` symmetric 3-colour block Gauss-Seidel sweeps
-// from zero (colours (x+y) mod 3 make the 7-point stencil conflict free;
-// the colour order 0,1,2,1,0,1,2,1,0,... is a palindrome, so the sweep
-// operator is symmetric).  For CG the preconditioner must be symmetric, so
+// solved approximately by `s` symmetric 3-colour block SOR sweeps from zero
+// (colours (x+y) mod 3 make the 7-point stencil conflict free; a visit of
+// colour c sets z_n <- z_n + omega (D_n^{-1}(b_n - sum_m A_nm z_m) - z_n) for
+// all its nodes at once; omega = 1 is block Gauss-Seidel).  Each visit's
+// error propagator I - omega P_c is self-adjoint in the A inner product with
+// norm <= 1 for 0 < omega < 2, and the colour order 0,1,2,1,0,1,2,1,0,... is
+// a palindrome, so the sweep operator is symmetric and the preconditioner
+// positive definite for any such omega.  For CG the preconditioner must be symmetric, so
 // the subdomain right-hand side is the residual on the owned nodes only and
 // only the owned part of the local solution is kept:
 //   z = sum_i R~_i^T  A_i^{-1}(approx)  R~_i r        (R~_i: owned nodes)
@@ -71,6 +75,7 @@ struct SchwarzParams {
     void* r;                  // inner residual planes (written back on owned nodes)
     void* z;                  // preconditioned residual planes (owned nodes)
     double lam;
+    double omega;             // relaxation factor of the sweeps (1: block Gauss-Seidel)
     int Tx, Ty, ov, sweeps;
     int first;                // no r update (start of a pass): z = M r only
     int apply_only;           // of_precondition: z = M r, no scalars
@@ -307,9 +312,25 @@ __device__ __forceinline__ void block_solve(const Blk<R>& B, R b0, R b1, R b2, R
     x0 = b0 * B.i0 - B.l10 * x1 - B.l20 * x2;
 }
 
-template <typename R>
+// z_n <- z_n + omega (x - z_n); FRESH: first visit of the colour in this
+// subdomain, z_n is still zero (its shared-memory slot holds another item's data)
+template <typename R, bool FRESH>
+__device__ __forceinline__ void relax(const R* Z, int zplane, int c, R om, R& x0, R& x1, R& x2) {
+    if (FRESH) {
+        x0 *= om;
+        x1 *= om;
+        x2 *= om;
+    } else {
+        const R o0 = Z[c], o1 = Z[c + zplane], o2 = Z[c + 2 * zplane];
+        x0 = o0 + om * (x0 - o0);
+        x1 = o1 + om * (x1 - o1);
+        x2 = o2 + om * (x2 - o2);
+    }
+}
+
+template <typename R, bool FRESH = false>
 __device__ __forceinline__ void node_sweep(const CellView<R>& C, R* __restrict__ Z, int zplane, int c, int RW,
-                                           unsigned legs, R hl, const Blk<R>& B, R b0, R b1, R b2) {
+                                           unsigned legs, R hl, R om, const Blk<R>& B, R b0, R b1, R b2) {
     const R* z0 = Z;
     const R* z1 = Z + zplane;
     const R* z2 = Z + 2 * zplane;
@@ -338,6 +359,7 @@ __device__ __forceinline__ void node_sweep(const CellView<R>& C, R* __restrict__
     b2 += lam_edges(legs, hl, zE2, zN2, zW2, zS2);
     R x0, x1, x2;
     block_solve(B, b0, b1, b2, x0, x1, x2);
+    if (om != R(1)) relax<R, FRESH>(Z, zplane, c, om, x0, x1, x2);
     Z[c] = x0;
     Z[c + zplane] = x1;
     Z[c + 2 * zplane] = x2;
@@ -348,7 +370,7 @@ __device__ __forceinline__ void node_sweep(const CellView<R>& C, R* __restrict__
 // zero, so only the W, S and NE values enter.
 template <typename R>
 __device__ __forceinline__ void node_sweep_first1(const CellView<R>& C, R* __restrict__ Z, int zplane, int c, int RW,
-                                                  unsigned legs, R hl, const Blk<R>& B, R b0, R b1, R b2) {
+                                                  unsigned legs, R hl, R om, const Blk<R>& B, R b0, R b1, R b2) {
     const R* z0 = Z;
     const R* z1 = Z + zplane;
     const R* z2 = Z + 2 * zplane;
@@ -375,6 +397,7 @@ __device__ __forceinline__ void node_sweep_first1(const CellView<R>& C, R* __res
     b2 += lam_edges(legs, hl, z, z, zW2, zS2);
     R x0, x1, x2;
     block_solve(B, b0, b1, b2, x0, x1, x2);
+    if (om != R(1)) relax<R, true>(Z, zplane, c, om, x0, x1, x2);
     Z[c] = x0;
     Z[c + zplane] = x1;
     Z[c + 2 * zplane] = x2;
@@ -412,25 +435,31 @@ template <typename R> struct NodeState {
     Blk<R> B;         // LDL^T factors of the diagonal block
 };
 
-template <typename R>
-__device__ __forceinline__ void node_step(const CellView<R>& C, R* Zs, int nc, int RW, R hl, const NodeState<R>& n) {
+template <typename R, bool FRESH = false>
+__device__ __forceinline__ void node_step(const CellView<R>& C, R* Zs, int nc, int RW, R hl, R om,
+                                          const NodeState<R>& n) {
     if (n.c == -1) return;
-    node_sweep<R>(C, Zs, nc, n.c & 0xffffff, RW, (unsigned)n.c >> 24, hl, n.B, n.b0, n.b1, n.b2);
+    node_sweep<R, FRESH>(C, Zs, nc, n.c & 0xffffff, RW, (unsigned)n.c >> 24, hl, om, n.B, n.b0, n.b1, n.b2);
 }
 template <typename R>
-__device__ __forceinline__ void node_step_first1(const CellView<R>& C, R* Zs, int nc, int RW, R hl,
+__device__ __forceinline__ void node_step_first1(const CellView<R>& C, R* Zs, int nc, int RW, R hl, R om,
                                                  const NodeState<R>& n) {
     if (n.c == -1) return;
-    node_sweep_first1<R>(C, Zs, nc, n.c & 0xffffff, RW, (unsigned)n.c >> 24, hl, n.B, n.b0, n.b1, n.b2);
+    node_sweep_first1<R>(C, Zs, nc, n.c & 0xffffff, RW, (unsigned)n.c >> 24, hl, om, n.B, n.b0, n.b1, n.b2);
 }
 
 // Block Jacobi: z = D^{-1} r, no neighbour terms.
 template <typename R>
-__device__ __forceinline__ void node_jacobi(R* Zs, int nc, const NodeState<R>& n) {
+__device__ __forceinline__ void node_jacobi(R* Zs, int nc, const NodeState<R>& n, R om = R(1)) {
     if (n.c == -1) return;
     const int c = n.c & 0xffffff;
     R x0, x1, x2;
     block_solve(n.B, n.b0, n.b1, n.b2, x0, x1, x2);
+    if (om != R(1)) {
+        x0 *= om;
+        x1 *= om;
+        x2 *= om;
+    }
     Zs[c] = x0;
     Zs[c + nc] = x1;
     Zs[c + 2 * nc] = x2;
@@ -568,6 +597,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         // ---- owned nodes: diagonal blocks, right-hand sides, r <- r - a q
         const R a = need_q ? (R)P.sc[pair].a : R(0);
         const R hl = R(0.5) * (R)P.lam;
+        const R om = (R)P.omega;
         NodeState<R> ns[3][NPT];
 #pragma unroll
         for (int col = 0; col < 3; ++col) {
@@ -609,8 +639,8 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
                     n.b1 = v1;
                     n.b2 = v2;
                 }
-                // the first colour step from z = 0 is block Jacobi on colour 0
-                if (col == 0) node_jacobi<R>(Zs, nc, n);
+                // the first colour step from z = 0 is (relaxed) block Jacobi on colour 0
+                if (col == 0) node_jacobi<R>(Zs, nc, n, P.sweeps > 0 ? om : R(1));
             }
         }
         __syncthreads();
@@ -622,7 +652,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
 #define OF_STEP(col)                                                 \
     {                                                                \
         _Pragma("unroll") for (int k = 0; k < NPT; ++k)              \
-            node_step<R>(C, Zs, nc, RW, hl, ns[col][k]);             \
+            node_step<R>(C, Zs, nc, RW, hl, om, ns[col][k]);         \
         __syncthreads();                                             \
     }
         if (P.sweeps == 0) {
@@ -632,11 +662,14 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
                 for (int k = 0; k < NPT; ++k) node_jacobi<R>(Zs, nc, ns[col][k]);
             __syncthreads();
         } else {
-            // colour 0 of the first sweep was the Jacobi step above
+            // colour 0 of the first sweep was the Jacobi step above; colours 1
+            // and 2 start from zero on their first visit
 #pragma unroll
-            for (int k = 0; k < NPT; ++k) node_step_first1<R>(C, Zs, nc, RW, hl, ns[1][k]);
+            for (int k = 0; k < NPT; ++k) node_step_first1<R>(C, Zs, nc, RW, hl, om, ns[1][k]);
             __syncthreads();
-            OF_STEP(2)
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) node_step<R, true>(C, Zs, nc, RW, hl, om, ns[2][k]);
+            __syncthreads();
             OF_STEP(1)
             for (int sw = 1; sw < P.sweeps; ++sw) {
                 OF_STEP(0)

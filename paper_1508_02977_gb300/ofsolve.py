@@ -33,7 +33,7 @@ OF_PC_SCHWARZ, OF_PC_JACOBI = 0, 1
 class GridOpts(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("overlap", ctypes.c_int),
                 ("sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("lam", ctypes.c_double),
-                ("preconditioner", ctypes.c_int)]
+                ("preconditioner", ctypes.c_int), ("omega", ctypes.c_double)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -144,12 +144,14 @@ def of_create(device: int = 0, stream=None):
 
 
 def of_setup_grid(h, sizes, tile=(32, 32), overlap=0, sweeps=1, precision=OF_PREC_MIXED, lam=1.0,
-                  preconditioner=OF_PC_SCHWARZ):
-    """sizes: list of (W, H)."""
+                  preconditioner=OF_PC_SCHWARZ, omega=1.0):
+    """sizes: list of (W, H); omega: relaxation factor of the local block SOR
+    sweeps, in (0, 2)."""
     n = len(sizes)
     Wa = (ctypes.c_int32 * n)(*[int(w) for w, _ in sizes])
     Ha = (ctypes.c_int32 * n)(*[int(hh) for _, hh in sizes])
-    o = GridOpts(int(tile[0]), int(tile[1]), int(overlap), int(sweeps), int(precision), float(lam), int(preconditioner))
+    o = GridOpts(int(tile[0]), int(tile[1]), int(overlap), int(sweeps), int(precision), float(lam), int(preconditioner),
+                 float(omega))
     return _check(h, _lib.of_setup_grid(h, n, Wa, Ha, ctypes.byref(o)))
 
 

@@ -20,7 +20,10 @@ def test_cache_round_trip(tmp_path):
     d = autotune.load_cache(path)
     d[autotune._key(640, 480, 1, "GB300")] = {"tile": [32, 32], "overlap": 0, "sweeps": 2, "ms": 1.0}
     autotune.save_cache(d, path)
-    assert autotune.lookup(700, 500, 1, "GB300", path) == {"tile": (32, 32), "overlap": 0, "sweeps": 2}
+    assert autotune.lookup(700, 500, 1, "GB300", path) == {"tile": (32, 32), "overlap": 0, "sweeps": 2, "omega": 1.0}
+    d[autotune._key(640, 480, 1, "GB300")]["omega"] = 1.6
+    autotune.save_cache(d, path)
+    assert autotune.lookup(700, 500, 1, "GB300", path)["omega"] == 1.6
     # another size class or precision is not matched
     assert autotune.lookup(3840, 2160, 1, "GB300", path) == autotune.FALLBACK
     assert autotune.lookup(640, 480, 0, "GB300", path) == autotune.FALLBACK

@@ -197,6 +197,79 @@ def test_schwarz_fixed_point_is_global_solution(oracle):
     assert hist[-1] < 1e-12 * hist[0]
 
 
+def _small_system(oracle, W, H, seed):
+    f1, f2 = synth.random_frames(W, H, seed)
+    alpha = synth.random_alpha(W, H, seed + 1)
+    return oracle.System.from_frames(f1, f2, alpha, 0.8)
+
+
+@pytest.mark.parametrize("omega", [1.0, 1.5])
+def test_sweep_preconditioner_one_tile_converges_to_direct_solve(oracle, omega):
+    """Block SOR on an SPD matrix converges for 0 < omega < 2: one tile over
+    the whole image and many sweeps give A^{-1} r (banded Cholesky)."""
+    S = _small_system(oracle, 17, 13, 5)
+    r = np.random.default_rng(1).standard_normal((3, 13, 17))
+    zd = S.solve_with(r)
+    z = S.schwarz_sweeps(r, (32, 32), 0, 400, omega)
+    assert np.linalg.norm(z - zd) <= 1e-11 * np.linalg.norm(zd)
+
+
+def test_sweep_preconditioner_exact_local_solves(oracle):
+    """Many sweeps per tile give the restricted exact-solve preconditioner
+    sum_i R~_i^T A_i^{-1} R~_i r, built here from dense sub-blocks of the
+    assembled matrix and LAPACK solves."""
+    W, H, tx, ty, ov = 20, 15, 8, 6, 1
+    S = _small_system(oracle, W, H, 7)
+    A = S.dense()
+    r = np.random.default_rng(2).standard_normal((3, H, W))
+    want = np.zeros(3 * W * H)
+    for y0 in range(0, H, ty):
+        for x0 in range(0, W, tx):
+            ext = [(x, y) for y in range(max(y0 - ov, 0), min(y0 + ty + ov, H))
+                   for x in range(max(x0 - ov, 0), min(x0 + tx + ov, W))]
+            idx = np.array([c * W * H + y * W + x for c in range(3) for (x, y) in ext])
+            own = np.array([x0 <= x < x0 + tx and y0 <= y < y0 + ty for c in range(3) for (x, y) in ext])
+            b = np.where(own, r.ravel()[idx], 0.0)
+            zi = np.linalg.solve(A[np.ix_(idx, idx)], b)
+            want[idx[own]] = zi[own]
+    z = S.schwarz_sweeps(r, (tx, ty), ov, 600, 1.3)
+    assert np.linalg.norm(z.ravel() - want) <= 1e-10 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("sweeps,omega", [(1, 1.0), (2, 1.4), (3, 1.8)])
+def test_sweep_preconditioner_symmetric_positive(oracle, sweeps, omega):
+    """The palindromic colour order makes M symmetric and positive definite for
+    any 0 < omega < 2 (the property the CUDA preconditioner relies on for CG):
+    the matrix of r -> z, column by column, on a 9x7 grid, 4x3 tiles,
+    overlap 1."""
+    W, H = 9, 7
+    S = _small_system(oracle, W, H, 11)
+    n = 3 * W * H
+    M = np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = 1.0
+        M[:, k] = S.schwarz_sweeps(e.reshape(3, H, W), (4, 3), 1, sweeps, omega).ravel()
+    assert np.abs(M - M.T).max() <= 1e-12 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+def test_sweep_preconditioner_zero_sweeps_is_block_jacobi(oracle):
+    """sweeps = 0: z_n = D_n^{-1} r_n with D_n the 3x3 diagonal block of the
+    dense assembled matrix, whatever the tiling."""
+    W, H = 11, 9
+    S = _small_system(oracle, W, H, 13)
+    A = S.dense()
+    r = np.random.default_rng(3).standard_normal((3, H, W))
+    want = np.zeros((3, H, W))
+    for y in range(H):
+        for x in range(W):
+            i = [c * W * H + y * W + x for c in range(3)]
+            want[:, y, x] = np.linalg.solve(A[np.ix_(i, i)], r[:, y, x])
+    z = S.schwarz_sweeps(r, (4, 4), 2, 0)
+    assert np.abs(z - want).max() <= 1e-13 * np.abs(want).max()
+
+
 def test_schwarz_converges_faster_with_more_overlap(oracle):
     """Section 4, Fig. schwarz-convergence: the rate increases with the
     overlap."""
