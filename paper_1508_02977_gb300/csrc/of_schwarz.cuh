@@ -330,7 +330,8 @@ __device__ __forceinline__ void relax(const R* Z, int zplane, int c, R om, R& x0
 
 template <typename R, bool FRESH = false>
 __device__ __forceinline__ void node_sweep(const CellView<R>& C, R* __restrict__ Z, int zplane, int c, int RW,
-                                           unsigned legs, R hl, R om, const Blk<R>& B, R b0, R b1, R b2) {
+                                           unsigned legs, R hl, R om, const Blk<R>& B, R b0, R b1, R b2, R& x0,
+                                           R& x1, R& x2) {
     const R* z0 = Z;
     const R* z1 = Z + zplane;
     const R* z2 = Z + 2 * zplane;
@@ -357,7 +358,6 @@ __device__ __forceinline__ void node_sweep(const CellView<R>& C, R* __restrict__
     b0 += wE * zE0 + wN * zN0 + wW * zW0 + wS * zS0;
     b1 += wE * zE1 + wN * zN1 + wW * zW1 + wS * zS1;
     b2 += lam_edges(legs, hl, zE2, zN2, zW2, zS2);
-    R x0, x1, x2;
     block_solve(B, b0, b1, b2, x0, x1, x2);
     if (om != R(1)) relax<R, FRESH>(Z, zplane, c, om, x0, x1, x2);
     Z[c] = x0;
@@ -435,11 +435,34 @@ template <typename R> struct NodeState {
     Blk<R> B;         // LDL^T factors of the diagonal block
 };
 
-template <typename R, bool FRESH = false>
+// Output of the last visit of a colour: the owned part of the local
+// solution into the dense tile that is bulk-stored, and the partial r.z.
+template <typename R>
+struct ZOut {
+    R* zo;       // [3][Ty][Tx] tile of z
+    int Tx, plane, tw, th, ov, cpad, RW;
+    R rz;
+    __device__ __forceinline__ void emit(const NodeState<R>& n, R x0, R x1, R x2) {
+        const int c = n.c & 0xffffff;
+        const int row = c / RW;                      // lj + 1
+        const int ox = c - row * RW - cpad, oy = row - 1 - ov;  // position in the owned tile
+        if (ox < 0 || ox >= tw || oy < 0 || oy >= th) return;
+        const int si = oy * Tx + ox;
+        zo[si] = x0;
+        zo[si + plane] = x1;
+        zo[si + 2 * plane] = x2;
+        rz += n.b0 * x0 + n.b1 * x1 + n.b2 * x2;
+    }
+};
+
+template <typename R, bool FRESH = false, bool LAST = false>
 __device__ __forceinline__ void node_step(const CellView<R>& C, R* Zs, int nc, int RW, R hl, R om,
-                                          const NodeState<R>& n) {
+                                          const NodeState<R>& n, ZOut<R>& out) {
     if (n.c == -1) return;
-    node_sweep<R, FRESH>(C, Zs, nc, n.c & 0xffffff, RW, (unsigned)n.c >> 24, hl, om, n.B, n.b0, n.b1, n.b2);
+    R x0, x1, x2;
+    node_sweep<R, FRESH>(C, Zs, nc, n.c & 0xffffff, RW, (unsigned)n.c >> 24, hl, om, n.B, n.b0, n.b1, n.b2, x0, x1,
+                         x2);
+    if (LAST) out.emit(n, x0, x1, x2);
 }
 template <typename R>
 __device__ __forceinline__ void node_step_first1(const CellView<R>& C, R* Zs, int nc, int RW, R hl, R om,
@@ -557,11 +580,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         // iteration later, so its descriptor loads overlap this item's work
         const int tc = tn + G;
         int4 tic = make_int4(0, 0, 0, 0);
-        int dc = 0;
-        if (tn < P.ntiles && tc < P.ntiles) {
-            tic = P.tiles[tc];
-            dc = pair_done(tic.x);
-        }
+        if (tn < P.ntiles && tc < P.ntiles) tic = P.tiles[tc];  // used at the end of this item
 
         if (threadIdx.x == 0 && !mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit)) {
             sh_fail = 1;
@@ -598,6 +617,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         const R a = need_q ? (R)P.sc[pair].a : R(0);
         const R hl = R(0.5) * (R)P.lam;
         const R om = (R)P.omega;
+        R rr = R(0);  // partial r.r of the owned nodes
         NodeState<R> ns[3][NPT];
 #pragma unroll
         for (int col = 0; col < 3; ++col) {
@@ -638,6 +658,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
                     n.b0 = v0;
                     n.b1 = v1;
                     n.b2 = v2;
+                    rr += v0 * v0 + v1 * v1 + v2 * v2;
                 }
                 // the first colour step from z = 0 is (relaxed) block Jacobi on colour 0
                 if (col == 0) node_jacobi<R>(Zs, nc, n, P.sweeps > 0 ? om : R(1));
@@ -648,12 +669,25 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         // stores that read that stage were issued an item ago and are done by now)
         if (nstage == 2 && tn < P.ntiles && threadIdx.x == 0) issue(tin, s ^ 1);
 
-        // ---- sweeps (colour order 0,1,2,1,0,1,2,1,0,...; sweeps = 0: block Jacobi)
-#define OF_STEP(col)                                                 \
-    {                                                                \
-        _Pragma("unroll") for (int k = 0; k < NPT; ++k)              \
-            node_step<R>(C, Zs, nc, RW, hl, om, ns[col][k]);         \
-        __syncthreads();                                             \
+        // ---- sweeps (colour order 0,1,2,1,0,1,2,1,0,...; sweeps = 0: block Jacobi).
+        // The last visit of each colour also writes the owned z into the q
+        // buffer of this stage (q was consumed in the setup) for the bulk
+        // store, and accumulates r.z.
+        ZOut<R> zout;
+        zout.zo = reinterpret_cast<R*>(st + L.qs);
+        zout.Tx = Tx;
+        zout.plane = Tx * Ty;
+        zout.tw = tw;
+        zout.th = th;
+        zout.ov = ov;
+        zout.cpad = cpad;
+        zout.RW = RW;
+        zout.rz = R(0);
+#define OF_STEP(col, FRESH, LAST)                                                 \
+    {                                                                             \
+        _Pragma("unroll") for (int k = 0; k < NPT; ++k)                           \
+            node_step<R, FRESH, LAST>(C, Zs, nc, RW, hl, om, ns[col][k], zout);   \
+        __syncthreads();                                                          \
     }
         if (P.sweeps == 0) {
 #pragma unroll
@@ -661,50 +695,45 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
 #pragma unroll
                 for (int k = 0; k < NPT; ++k) node_jacobi<R>(Zs, nc, ns[col][k]);
             __syncthreads();
+#pragma unroll
+            for (int col = 0; col < 3; ++col)
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    const NodeState<R>& n = ns[col][k];
+                    if (n.c == -1) continue;
+                    const int c = n.c & 0xffffff;
+                    zout.emit(n, Zs[c], Zs[c + nc], Zs[c + 2 * nc]);
+                }
         } else {
             // colour 0 of the first sweep was the Jacobi step above; colours 1
             // and 2 start from zero on their first visit
 #pragma unroll
             for (int k = 0; k < NPT; ++k) node_step_first1<R>(C, Zs, nc, RW, hl, om, ns[1][k]);
             __syncthreads();
-#pragma unroll
-            for (int k = 0; k < NPT; ++k) node_step<R, true>(C, Zs, nc, RW, hl, om, ns[2][k]);
-            __syncthreads();
-            OF_STEP(1)
-            for (int sw = 1; sw < P.sweeps; ++sw) {
-                OF_STEP(0)
-                OF_STEP(1)
-                OF_STEP(2)
-                OF_STEP(1)
+            if (P.sweeps == 1) {
+                OF_STEP(2, true, true)
+                OF_STEP(1, false, true)
+                OF_STEP(0, false, true)
+            } else {
+                OF_STEP(2, true, false)
+                OF_STEP(1, false, false)
+                for (int sw = 2; sw < P.sweeps; ++sw) {
+                    OF_STEP(0, false, false)
+                    OF_STEP(1, false, false)
+                    OF_STEP(2, false, false)
+                    OF_STEP(1, false, false)
+                }
+                OF_STEP(0, false, false)
+                OF_STEP(1, false, false)
+                OF_STEP(2, false, true)
+                OF_STEP(1, false, true)
+                OF_STEP(0, false, true)
             }
-            OF_STEP(0)
         }
 #undef OF_STEP
 
-        // ---- owned z into the q buffer of this stage (q is no longer needed),
-        //      partials r.r and r.z from the owners' registers, FP32 within the
-        //      CTA (FP64 arithmetic runs at a small fraction of the FP32 rate)
-        R* Zo = reinterpret_cast<R*>(st + L.qs);
-        R rr = R(0), rz = R(0);
-#pragma unroll
-        for (int col = 0; col < 3; ++col) {
-#pragma unroll
-            for (int k = 0; k < NPT; ++k) {
-                const NodeState<R>& n = ns[col][k];
-                if (n.c == -1) continue;
-                const int c = n.c & 0xffffff;
-                const uint32_t e = tab[col][k];
-                const int gx = x0 - ov + (int)(e & 0xffffu), gy = y0 - ov + (int)(e >> 16);
-                if (gx < x0 || gx >= x0 + tw || gy < y0 || gy >= y0 + th) continue;
-                const int si = (gy - y0) * Tx + (gx - x0);
-                const R v0 = Zs[c], v1 = Zs[c + nc], v2 = Zs[c + 2 * nc];
-                Zo[si] = v0;
-                Zo[si + Tx * Ty] = v1;
-                Zo[si + 2 * Tx * Ty] = v2;
-                rr += n.b0 * n.b0 + n.b1 * n.b1 + n.b2 * n.b2;
-                rz += n.b0 * v0 + n.b1 * v1 + n.b2 * v2;
-            }
-        }
+        R* Zo = zout.zo;
+        const R rz = zout.rz;
         const float wrr = warp_sum((float)rr), wrz = warp_sum((float)rz);
         if ((threadIdx.x & 31) == 0) {
             sh_red[threadIdx.x >> 5] = (double)wrr;
@@ -734,7 +763,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         ti = tin;
         tn = tc;
         tin = tic;
-        if (tn < P.ntiles && dc) tn = advance(tn + G, tin);  // the fetched item's pair has finished
+        if (tn < P.ntiles && pair_done(tin.x)) tn = advance(tn + G, tin);  // the fetched item's pair has finished
         if (nstage == 2) s ^= 1;
         else if (t < P.ntiles && threadIdx.x == 0) issue(ti, 0);
     }
