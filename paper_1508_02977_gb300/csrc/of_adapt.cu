@@ -10,10 +10,11 @@ namespace ofl {
 
 using namespace ofk;
 
-// U (3 components) at node (x, y) of the FP64 solution planes, as R.
-template <typename R>
+// U (3 components) at node (x, y) of the solution planes (FP64, or an FP32
+// copy on the FP32 path), as R.
+template <typename R, typename UT>
 struct UView {
-    const double* u;
+    const UT* u;
     long long plane;
     int pitch;
     __device__ __forceinline__ void at(int x, int y, R v[3]) const {
@@ -43,9 +44,9 @@ __device__ __forceinline__ void tri_grad(int t, const R A[3], const R B[3], cons
 //   edges:    (1/2) h_e |Lambda_e^{-1/2} J_e|  (J_e constant on the edge, so
 //             h_e^{1/2} ||.||_{L2(e)} = h_e |.|), J_e = outside - inside flux,
 //             outside flux 0 on the image boundary, Lambda_e = max of the two.
-template <typename R>
+template <typename R, typename UT>
 __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict__ f1a, const R* __restrict__ f2a,
-                            const R* __restrict__ ala, const double* __restrict__ ua, R* __restrict__ etaa, double lam_d,
+                            const R* __restrict__ ala, const UT* __restrict__ ua, R* __restrict__ etaa, double lam_d,
                             unsigned long long* __restrict__ etamax_bits) {
     const PairDesc pd = pairs[pair];
     const int W = pd.W, H = pd.H, pitch = pd.pitch;
@@ -56,8 +57,9 @@ __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict
         const R* f1 = f1a + pd.frame_off;
         const R* f2 = f2a + pd.frame_off;
         const R* al = ala + 2 * pd.frame_off;
-        UView<R> U{ua + pd.vec_off, (long long)H * pitch, pitch};
+        UView<R, UT> U{ua + pd.vec_off, (long long)H * pitch, pitch};
         const R lam = (R)lam_d;
+        const R ilam = R(1) / lam;  // Lambda^{-1} enters as products with reciprocals
         auto F1 = [&](int xx, int yy) { return f1[(long long)yy * pitch + xx]; };
         auto F2 = [&](int xx, int yy) { return f2[(long long)yy * pitch + xx]; };
         auto AL = [&](int xx, int yy, int t) { return al[2 * ((long long)yy * pitch + xx) + t]; };
@@ -84,7 +86,9 @@ __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict
                 ft = ((F2(x, y) - F1(x, y)) + (F2(x, y + 1) - F1(x, y + 1)) + (F2(x + 1, y + 1) - F1(x + 1, y + 1))) * third;
             }
             const R Lk[3] = {aK[t], aK[t], lam};
-            const R G = g0 * g0 / Lk[0] + g1 * g1 / Lk[1] + g2 * g2 / Lk[2];
+            const R iaK = R(1) / aK[t];
+            const R iLk[3] = {iaK, iaK, ilam};
+            const R G = (g0 * g0 + g1 * g1) * iaK + g2 * g2 * ilam;
             // midpoints of the 3 edges: (A,V1), (V1,C), (C,A)
             R sm2 = R(0);
             const R* P0[3] = {uA, V1, uC};
@@ -110,7 +114,7 @@ __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict
                     else { nx = R(0.7071067811865476); ny = -R(0.7071067811865476); he = sq2; has = true; nbx = x; nby = y; nbt = 0; }
                 }
                 R ngx[3] = {0, 0, 0}, ngy[3] = {0, 0, 0};
-                R aO = R(0);
+                R aO = R(0), iaO = R(0);
                 if (has) {
                     R qA[3], qB[3], qC[3], qD[3];
                     if (nbx == x && nby == y) {
@@ -120,6 +124,7 @@ __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict
                         tri_grad<R>(nbt, qA, qB, qC, qD, ngx, ngy);
                     }
                     aO = AL(nbx, nby, nbt);
+                    iaO = R(1) / aO;
                 }
                 R q = R(0);
                 for (int c = 0; c < 3; ++c) {
@@ -127,9 +132,11 @@ __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict
                     const R lo = (c < 2) ? aO : lam;
                     const R fin = lk * (gxK[t][c] * nx + gyK[t][c] * ny);
                     const R fout = has ? lo * (ngx[c] * nx + ngy[c] * ny) : R(0);
-                    const R le = has ? (lo > lk ? lo : lk) : lk;
+                    // 1 / max(lo, lk) = min(1/lo, 1/lk)
+                    const R ilo = (c < 2) ? iaO : ilam;
+                    const R ile = has ? (ilo < iLk[c] ? ilo : iLk[c]) : iLk[c];
                     const R J = fout - fin;
-                    q += J * J / le;
+                    q += J * J * ile;
                 }
                 val += R(0.5) * he * sqrt(q);
             }
@@ -154,9 +161,10 @@ __global__ void k_alpha_update(const PairDesc* pairs, int pair, R* __restrict__ 
     if (x >= W - 1 || !(m > 0.0)) return;
     R* al = ala + 2 * pd.frame_off;
     const R* eta = etaa + 2 * pd.frame_off;
+    const R im = (R)(1.0 / m);
     for (int t = 0; t < 2; ++t) {
         const long long o = 2 * ((long long)y * pitch + x) + t;
-        const R rel = (R)((double)eta[o] / m) - (R)eta_thr;
+        const R rel = eta[o] * im - (R)eta_thr;
         const R a = al[o] / (R(1) + (R)kappa * (rel > R(0) ? rel : R(0)));
         al[o] = a > (R)alpha_th ? a : (R)alpha_th;
     }
@@ -165,13 +173,13 @@ __global__ void k_alpha_update(const PairDesc* pairs, int pair, R* __restrict__ 
 cudaError_t launch_indicator(const AdaptBufs& A, int pair, int H, int W, cudaStream_t st) {
     dim3 grid((W - 1 + 127) / 128, H - 1);
     if (A.fp64)
-        k_indicator<double><<<grid, 128, 0, st>>>(A.pairs, pair, (const double*)A.f1, (const double*)A.f2,
-                                                  (const double*)A.alpha, A.u, (double*)A.eta, A.lam,
-                                                  (unsigned long long*)A.etamax);
+        k_indicator<double, double><<<grid, 128, 0, st>>>(A.pairs, pair, (const double*)A.f1, (const double*)A.f2,
+                                                          (const double*)A.alpha, A.u, (double*)A.eta, A.lam,
+                                                          (unsigned long long*)A.etamax);
     else
-        k_indicator<float><<<grid, 128, 0, st>>>(A.pairs, pair, (const float*)A.f1, (const float*)A.f2,
-                                                 (const float*)A.alpha, A.u, (float*)A.eta, A.lam,
-                                                 (unsigned long long*)A.etamax);
+        k_indicator<float, float><<<grid, 128, 0, st>>>(A.pairs, pair, (const float*)A.f1, (const float*)A.f2,
+                                                        (const float*)A.alpha, A.u32, (float*)A.eta, A.lam,
+                                                        (unsigned long long*)A.etamax);
     return cudaGetLastError();
 }
 
@@ -226,8 +234,8 @@ __global__ void k_adjoint_alpha(const PairDesc* pairs, int pair, const double* _
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= W - 1 || y >= H - 1) return;
-    UView<R> U{ua + pd.vec_off, (long long)H * pitch, pitch};
-    UView<R> L{la + pd.vec_off, (long long)H * pitch, pitch};
+    UView<R, double> U{ua + pd.vec_off, (long long)H * pitch, pitch};
+    UView<R, double> L{la + pd.vec_off, (long long)H * pitch, pitch};
     R uA[3], uB[3], uC[3], uD[3], lA[3], lB[3], lC[3], lD[3];
     U.at(x, y, uA); U.at(x + 1, y, uB); U.at(x + 1, y + 1, uC); U.at(x, y + 1, uD);
     L.at(x, y, lA); L.at(x + 1, y, lB); L.at(x + 1, y + 1, lC); L.at(x, y + 1, lD);
@@ -256,8 +264,8 @@ __global__ void k_adjoint_frames(const PairDesc* pairs, int pair, const R* __res
     if (x >= W) return;
     const R* f1 = f1a + pd.frame_off;
     const R* f2 = f2a + pd.frame_off;
-    UView<R> U{ua + pd.vec_off, (long long)H * pitch, pitch};
-    UView<R> L{la + pd.vec_off, (long long)H * pitch, pitch};
+    UView<R, double> U{ua + pd.vec_off, (long long)H * pitch, pitch};
+    UView<R, double> L{la + pd.vec_off, (long long)H * pitch, pitch};
     const int sqx[6] = {x, x, x - 1, x - 1, x - 1, x};
     const int sqy[6] = {y, y, y - 1, y - 1, y, y - 1};
     const int sqt[6] = {0, 1, 0, 1, 0, 1};

@@ -250,6 +250,7 @@ ofl::AdaptBufs adapt_bufs(of_ctx* h) {
     A.f2 = h->f2;
     A.alpha = h->alpha;
     A.u = h->usol;
+    A.u32 = h->fp64 ? nullptr : (const float*)h->z;  // filled by of_adapt_alpha (z is free after a solve)
     A.eta = h->eta;
     A.etamax = h->etamax;
     A.lam = h->opts.lambda;
@@ -803,6 +804,9 @@ of_status of_adapt_alpha(of_handle h, double kappa, double eta_thr, double alpha
     CK(cudaMemsetAsync(h->etamax, 0, sizeof(double) * h->batch, st));
     for (int p = 0; p < h->batch; ++p) {
         const PairDesc& d = h->pd[p];
+        if (!h->fp64)  // the FP32 path's indicator reads an FP32 copy of the solution
+            CK(cp2d(h, h->usol + d.vec_off, ofl::T_F64, d.pitch, (float*)h->z + d.vec_off, ofl::T_F32, d.pitch,
+                    3LL * d.H, d.W, st));
         CK(ofl::launch_indicator(A, p, d.H, d.W, st));
         count_other(h, 1);
         if (eta && eta[p]) {

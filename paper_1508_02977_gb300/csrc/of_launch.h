@@ -89,6 +89,7 @@ struct AdaptBufs {
     const void* f2;
     void* alpha;
     const double* u;     // solution planes (FP64)
+    const float* u32;    // FP32 copy of the solution planes (FP32 path)
     void* eta;           // per element [H][pitch][2] (storage precision)
     double* partial;     // per block maxima
     double* etamax;      // [batch]

@@ -451,6 +451,31 @@ def test_indicator_and_alpha_update_match_oracle(S, oracle):
     assert (a_new < alpha).any()
 
 
+def test_indicator_mixed_matches_oracle(S, oracle):
+    """FP32 path: the indicator reads an FP32 copy of the solution and works in
+    FP32.  Against the FP64 oracle on the same (FP64) solution: element
+    gradients are differences of neighbouring U values, so the FP32 rounding
+    of U (2^-24 |U|) is amplified by |U| / |grad U|; 1e-3 of max eta bounds
+    that on this texture."""
+    p = synth.texture(160, 120)
+    f1, f2 = f32(p.f1), f32(p.f2)
+    h = handle(S, [(p.W, p.H)], tile=(48, 48), sweeps=4, omega=1.6, precision=S.OF_PREC_MIXED)
+    try:
+        S.of_set_frames(h, 0, dev(p.f1, torch.float32), dev(p.f2, torch.float32))
+        S.of_set_alpha(h, 0, None, p.alpha0)
+        U = torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda")
+        S.of_solve(h, [U], rtol=1e-8)
+        eta = torch.zeros(p.H - 1, p.W - 1, 2, dtype=torch.float32, device="cuda")
+        S.of_adapt_alpha(h, synth.KAPPA, synth.ETA_THR, synth.ALPHA_TH_FRAC * p.alpha0, [eta])
+        U, eta = U.cpu().numpy(), eta.cpu().numpy().astype(np.float64)
+    finally:
+        S.of_destroy(h)
+    sysm = oracle.System.from_frames(f1, f2, np.float32(p.alpha0), p.lam)
+    eta_o = sysm.indicator(U)
+    err = np.abs(eta - eta_o).max() / eta_o.max()
+    assert err <= 1e-3, err
+
+
 def test_adaptation_three_passes_texture(S, oracle):
     """640x480 texture, 3 adaptation passes (solve -> indicator -> alpha):
     GPU alpha fields against the oracle's own 3 passes."""
