@@ -75,6 +75,12 @@ typedef enum {
     OF_PC_JACOBI = 1    /* node-block Jacobi (3x3 blocks); no subdomains */
 } of_preconditioner;
 
+typedef enum {
+    OF_MODEL_ILLUMINATION = 0,  /* (u1, u2, m): brightness change m, Eq. OF2 and Eq. eqpro1illu */
+    OF_MODEL_CONSTANT = 1       /* brightness constancy (Horn and Schunck, Eq. BW without m): the
+                                   illumination column of the data term is dropped; m stays 0 */
+} of_model;
+
 /* Grid options.  A field left at 0 takes the default in brackets. */
 typedef struct {
     int tile_x, tile_y;      /* owned subdomain tile in nodes, multiples of 4 [32 x 32] */
@@ -86,6 +92,11 @@ typedef struct {
     double omega;            /* relaxation factor of the local sweeps, 0 < omega < 2 [1.0: block
                                 Gauss-Seidel]; any such value keeps the preconditioner symmetric
                                 positive definite (the colour order is a palindrome) */
+    double sigma;            /* K_sigma pre-smoothing of the frames (Section 1), standard deviation
+                                in pixels, 0 <= sigma <= 16 [0: frames used as given]; sampled
+                                Gaussian of radius ceil(3 sigma) along x then y, each pass normalised
+                                over the taps inside the image */
+    of_model model;          /* [OF_MODEL_ILLUMINATION] */
 } of_grid_opts;
 
 /* Solve options.  A field left at 0 takes the default in brackets. */
@@ -123,9 +134,15 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t *W, const int32_t 
 
 /* Copies the two frames of pair `pair` ([H][pitch], dtype dt, pitch >=
  * W) into the workspace, converting to the storage precision (FP32 for
- * OF_PREC_MIXED, FP64 for OF_PREC_FP64).  Frames are the images f(., t) and
- * f(., t+1) of Section 1 (already smoothed: K_sigma is the identity). */
+ * OF_PREC_MIXED, FP64 for OF_PREC_FP64), and smooths them with K_sigma when
+ * the grid options give sigma > 0: the stored frames are f = K_sigma * I of
+ * Section 1. */
 of_status of_set_frames(of_handle h, int pair, const void *f1, const void *f2, of_dtype dt, int64_t row_pitch_elems);
+
+/* Copies the stored (smoothed) frames f(., t), f(., t+1) of pair `pair` out
+ * as dense [H][W] arrays of dtype dt (host or device).  Returns OF_ERR_STATE
+ * before of_set_frames. */
+of_status of_get_frames(of_handle h, int pair, void *f1, void *f2, of_dtype dt);
 
 /* Sets the per-element alpha of pair `pair` from `alpha` ([H-1][W-1][2],
  * dtype dt), or, if alpha is NULL, to the constant alpha_const (> 0). */

@@ -621,8 +621,11 @@ int orc_alpha_update(int64_t ne, const double *eta, double *alpha, double kappa,
  * Outputs dL/dalpha [H-1][W-1][2], dL/df2 and dL/df1 [H][W] (either may be
  * NULL).  Frames enter through g_K and ft_K (see orc_coefficients). */
 int orc_adjoint_grad(int W, int H, const double *f1, const double *f2, const double *alpha, double lambda,
-                     const double *U, const double *Lam, double *dalpha, double *df2, double *df1)
+                     const double *U, const double *Lam, double *dalpha, double *df2, double *df1, int model)
 {
+    /* model 1 (brightness constancy): the data term has no illumination
+     * column, g = (f2_x, f2_y, 0), so f1 enters through f_t only */
+    const double gms = model == 1 ? 0.0 : 1.0;
     (void)lambda;
     long N = (long)W * H;
     if (df2) memset(df2, 0, sizeof(double) * N);
@@ -642,7 +645,7 @@ int orc_adjoint_grad(int W, int H, const double *f1, const double *f2, const dou
                     for (int c = 0; c < 3; c++) { u[i][c] = U[c * N + nd]; l[i][c] = Lam[c * N + nd]; }
                     g[0] += f2[nd] * gx[i];
                     g[1] += f2[nd] * gy[i];
-                    g[2] -= f1[nd] / 3.0;
+                    g[2] -= gms * f1[nd] / 3.0;
                     ftv += (f2[nd] - f1[nd]) / 3.0;
                 }
                 /* stiffness part: d/dalpha_K of Lam^T S_K U (u1, u2 only) */
@@ -677,7 +680,7 @@ int orc_adjoint_grad(int W, int H, const double *f1, const double *f2, const dou
                 for (int i = 0; i < 3; i++) {
                     long nd = (long)vy[i] * W + vx[i];
                     if (df2) df2[nd] -= dEdg[0] * gx[i] + dEdg[1] * gy[i] + dEdft / 3.0;
-                    if (df1) df1[nd] -= dEdg[2] * (-1.0 / 3.0) + dEdft * (-1.0 / 3.0);
+                    if (df1) df1[nd] -= dEdg[2] * (-gms / 3.0) + dEdft * (-1.0 / 3.0);
                 }
             }
     return 0;

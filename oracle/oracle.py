@@ -60,7 +60,7 @@ def _load():
         L.orc_indicator.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p]
         L.orc_alpha_update.argtypes = [i64, _f64p, _f64p, f64, f64, f64]
         L.orc_adjoint_grad.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p,
-                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, i32]
         L.orc_num_threads.restype = i32
         _lib = L
         return L
@@ -78,8 +78,10 @@ def num_threads() -> int:
     return int(_load().orc_num_threads())
 
 
-def coefficients(f1, f2):
-    """(g [H-1][W-1][2][3], ft [H-1][W-1][2]) of every element."""
+def coefficients(f1, f2, model=0):
+    """(g [H-1][W-1][2][3], ft [H-1][W-1][2]) of every element.  model 1 is
+    brightness constancy (Horn and Schunck, Eq. BW without m): the
+    illumination column g_m of the data term is dropped."""
     L = _load()
     f1, f2 = _c(f1), _c(f2)
     H, W = f1.shape
@@ -87,6 +89,8 @@ def coefficients(f1, f2):
     ft = np.zeros((H - 1, W - 1, 2))
     if L.orc_coefficients(W, H, f1, f2, g, ft):
         raise ValueError("grid must be at least 2x2")
+    if model == 1:
+        g[..., 2] = 0.0
     return g, ft
 
 
@@ -110,12 +114,14 @@ class System:
             raise RuntimeError(f"oracle assembly failed ({rc})")
 
     @classmethod
-    def from_frames(cls, f1, f2, alpha, lam):
+    def from_frames(cls, f1, f2, alpha, lam, model=0):
         f1 = _c(f1)
         H, W = f1.shape
         alpha = np.broadcast_to(np.asarray(alpha, dtype=np.float64), (H - 1, W - 1, 2))
-        g, ft = coefficients(f1, f2)
-        return cls(W, H, g, ft, alpha, lam)
+        g, ft = coefficients(f1, f2, model)
+        S = cls(W, H, g, ft, alpha, lam)
+        S.model = int(model)
+        return S
 
     @property
     def n(self) -> int:
@@ -144,8 +150,25 @@ class System:
     def rel_residual(self, U) -> float:
         return float(np.linalg.norm(self.residual(U)) / np.linalg.norm(self.b))
 
+    def _solve_flow_block(self, rhs):
+        """Brightness constancy: the m block is the pure-Neumann lambda
+        Laplacian (singular, constants in its kernel), decoupled from (u1, u2)
+        and without load.  Solve the (u1, u2) block with a sparse direct
+        solver; m = 0 (the minimum-norm solution)."""
+        import scipy.sparse.linalg as spla
+        n2 = 2 * self.W * self.H
+        rhs = _c(rhs).ravel()
+        if np.abs(rhs[n2:]).max() > 0.0:
+            raise ValueError("the m equations carry no data in this model: their right-hand side must be 0")
+        A = self._sparse()[:n2, :n2].tocsc()
+        x = np.zeros(self.n)
+        x[:n2] = spla.spsolve(A, rhs[:n2])
+        return x.reshape(3, self.H, self.W)
+
     def solve_direct(self):
         """Banded Cholesky (small grids: cost ~ 27 W H min(W,H)^2)."""
+        if getattr(self, "model", 0) == 1:
+            return self._solve_flow_block(self.b)
         L = _load()
         x = np.zeros(self.n)
         rc = L.orc_band_cholesky_solve(self.W, self.H, self.rowptr, self.col, self.val, self.b, x)
@@ -167,6 +190,8 @@ class System:
         return x.reshape(3, self.H, self.W), int(it), float(rr.value)
 
     def solve_with(self, rhs, direct=True, tol=1e-13):
+        if getattr(self, "model", 0) == 1 and direct:
+            return self._solve_flow_block(rhs)
         L = _load()
         rhs = _c(rhs).ravel()
         x = np.zeros(self.n)
@@ -260,6 +285,50 @@ class System:
         return eta
 
 
+def _gauss_taps(sigma):
+    r = int(np.ceil(3.0 * sigma))
+    k = np.arange(-r, r + 1)
+    return k, np.exp(-(k.astype(np.float64) ** 2) / (2.0 * sigma * sigma))
+
+
+def _smooth_axis(A, axis, sigma, transpose=False):
+    """One normalised pass of K_sigma along `axis`: out(x) = sum over the taps
+    k with 0 <= x+k < n of w_k A(x+k), divided by the sum of those w_k; the
+    transposed pass divides each input by the normaliser of the position it
+    comes from instead."""
+    A = np.moveaxis(np.asarray(A, dtype=np.float64), axis, -1)
+    n = A.shape[-1]
+    k, w = _gauss_taps(sigma)
+    norm = np.zeros(n)
+    for kk, wk in zip(k, w):
+        lo, hi = max(0, -kk), min(n, n - kk)
+        norm[lo:hi] += wk
+    src = A / norm if transpose else A
+    out = np.zeros_like(A)
+    for kk, wk in zip(k, w):
+        lo, hi = max(0, -kk), min(n, n - kk)
+        out[..., lo:hi] += wk * src[..., lo + kk:hi + kk]
+    if not transpose:
+        out = out / norm
+    return np.moveaxis(out, -1, axis)
+
+
+def smooth(I, sigma):
+    """f = K_sigma * I (Section 1): sampled Gaussian w_k = exp(-k^2/(2 sigma^2)),
+    |k| <= ceil(3 sigma), along x then along y, each pass normalised over the
+    taps inside the image.  sigma = 0 returns I."""
+    if sigma <= 0:
+        return np.array(I, dtype=np.float64)
+    return _smooth_axis(_smooth_axis(I, 1, sigma), 0, sigma)
+
+
+def smooth_transpose(G, sigma):
+    """The transpose of `smooth` (x-pass then y-pass, so S^T = S_x^T S_y^T)."""
+    if sigma <= 0:
+        return np.array(G, dtype=np.float64)
+    return _smooth_axis(_smooth_axis(G, 0, sigma, True), 1, sigma, True)
+
+
 def apply_elementwise(W, H, g, ft, alpha, lam, U, with_rhs=False):
     """A U (and b) without storing A, for grids too large for the CSR."""
     L = _load()
@@ -271,11 +340,11 @@ def apply_elementwise(W, H, g, ft, alpha, lam, U, with_rhs=False):
     return (y, b.reshape(3, H, W)) if with_rhs else y
 
 
-def rel_residual_frames(f1, f2, alpha, lam, U) -> float:
+def rel_residual_frames(f1, f2, alpha, lam, U, model=0) -> float:
     """||b - A U||_2 / ||b||_2 of a frame pair, formed element by element."""
     f1 = _c(f1)
     H, W = f1.shape
-    g, ft = coefficients(f1, f2)
+    g, ft = coefficients(f1, f2, model)
     AU, b = apply_elementwise(W, H, g, ft, alpha, lam, U, with_rhs=True)
     return float(np.linalg.norm(b - AU) / np.linalg.norm(b))
 
@@ -295,7 +364,7 @@ def alpha_update(eta, alpha, kappa, eta_thr, alpha_th):
     return a
 
 
-def adjoint_grad(f1, f2, alpha, lam, U, Lam, want_f1=True):
+def adjoint_grad(f1, f2, alpha, lam, U, Lam, want_f1=True, model=0):
     """(dL/dalpha, dL/df2, dL/df1) given U and the adjoint state Lam."""
     L = _load()
     f1, f2 = _c(f1), _c(f2)
@@ -305,7 +374,7 @@ def adjoint_grad(f1, f2, alpha, lam, U, Lam, want_f1=True):
     d2 = np.zeros((H, W))
     d1 = np.zeros((H, W)) if want_f1 else None
     L.orc_adjoint_grad(W, H, f1, f2, alpha, float(lam), _c(U).ravel(), _c(Lam).ravel(),
-                       _ptr(da), _ptr(d2), _ptr(d1))
+                       _ptr(da), _ptr(d2), _ptr(d1), int(model))
     return da, d2, d1
 
 

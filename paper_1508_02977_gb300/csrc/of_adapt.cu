@@ -47,7 +47,7 @@ __device__ __forceinline__ void tri_grad(int t, const R A[3], const R B[3], cons
 template <typename R, typename UT>
 __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict__ f1a, const R* __restrict__ f2a,
                             const R* __restrict__ ala, const UT* __restrict__ ua, R* __restrict__ etaa, double lam_d,
-                            unsigned long long* __restrict__ etamax_bits) {
+                            double gms_d, unsigned long long* __restrict__ etamax_bits) {
     const PairDesc pd = pairs[pair];
     const int W = pd.W, H = pd.H, pitch = pd.pitch;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -60,6 +60,7 @@ __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict
         UView<R, UT> U{ua + pd.vec_off, (long long)H * pitch, pitch};
         const R lam = (R)lam_d;
         const R ilam = R(1) / lam;  // Lambda^{-1} enters as products with reciprocals
+        const R gms = (R)gms_d;      // illumination column scale (of_model)
         auto F1 = [&](int xx, int yy) { return f1[(long long)yy * pitch + xx]; };
         auto F2 = [&](int xx, int yy) { return f2[(long long)yy * pitch + xx]; };
         auto AL = [&](int xx, int yy, int t) { return al[2 * ((long long)yy * pitch + xx) + t]; };
@@ -78,11 +79,11 @@ __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict
             R g0, g1, g2, ft;
             if (t == 0) {
                 g0 = F2(x + 1, y) - F2(x, y); g1 = F2(x + 1, y + 1) - F2(x + 1, y);
-                g2 = -(F1(x, y) + F1(x + 1, y) + F1(x + 1, y + 1)) * third;
+                g2 = -(F1(x, y) + F1(x + 1, y) + F1(x + 1, y + 1)) * third * gms;
                 ft = ((F2(x, y) - F1(x, y)) + (F2(x + 1, y) - F1(x + 1, y)) + (F2(x + 1, y + 1) - F1(x + 1, y + 1))) * third;
             } else {
                 g0 = F2(x + 1, y + 1) - F2(x, y + 1); g1 = F2(x, y + 1) - F2(x, y);
-                g2 = -(F1(x, y) + F1(x, y + 1) + F1(x + 1, y + 1)) * third;
+                g2 = -(F1(x, y) + F1(x, y + 1) + F1(x + 1, y + 1)) * third * gms;
                 ft = ((F2(x, y) - F1(x, y)) + (F2(x, y + 1) - F1(x, y + 1)) + (F2(x + 1, y + 1) - F1(x + 1, y + 1))) * third;
             }
             const R Lk[3] = {aK[t], aK[t], lam};
@@ -174,11 +175,11 @@ cudaError_t launch_indicator(const AdaptBufs& A, int pair, int H, int W, cudaStr
     dim3 grid((W - 1 + 127) / 128, H - 1);
     if (A.fp64)
         k_indicator<double, double><<<grid, 128, 0, st>>>(A.pairs, pair, (const double*)A.f1, (const double*)A.f2,
-                                                          (const double*)A.alpha, A.u, (double*)A.eta, A.lam,
+                                                          (const double*)A.alpha, A.u, (double*)A.eta, A.lam, A.gms,
                                                           (unsigned long long*)A.etamax);
     else
         k_indicator<float, float><<<grid, 128, 0, st>>>(A.pairs, pair, (const float*)A.f1, (const float*)A.f2,
-                                                        (const float*)A.alpha, A.u32, (float*)A.eta, A.lam,
+                                                        (const float*)A.alpha, A.u32, (float*)A.eta, A.lam, A.gms,
                                                         (unsigned long long*)A.etamax);
     return cudaGetLastError();
 }
@@ -256,8 +257,9 @@ __global__ void k_adjoint_alpha(const PairDesc* pairs, int pair, const double* _
 template <typename R, typename O>
 __global__ void k_adjoint_frames(const PairDesc* pairs, int pair, const R* __restrict__ f1a, const R* __restrict__ f2a,
                                  const double* __restrict__ ua, const double* __restrict__ la, O* __restrict__ df2,
-                                 O* __restrict__ df1) {
+                                 O* __restrict__ df1, double gms_d) {
     const PairDesc pd = pairs[pair];
+    const R gms = (R)gms_d;
     const int W = pd.W, H = pd.H, pitch = pd.pitch;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -289,12 +291,12 @@ __global__ void k_adjoint_frames(const PairDesc* pairs, int pair, const R* __res
         R g[3];
         if (t == 0) { g[0] = fb[1] - fb[0]; g[1] = fb[2] - fb[1]; }
         else        { g[0] = fb[2] - fb[1]; g[1] = fb[1] - fb[0]; }
-        g[2] = -(fa[0] + fa[1] + fa[2]) * third;
+        g[2] = -(fa[0] + fa[1] + fa[2]) * third * gms;
         const R ft = ((fb[0] - fa[0]) + (fb[1] - fa[1]) + (fb[2] - fa[2])) * third;
         R dEdg[3], dEdft;
         elem_adjoint<R>(u, l, g, ft, dEdg, dEdft);
         a2 -= dEdg[0] * phx[e] + dEdg[1] * phy[e] + dEdft * third;
-        a1 += (dEdg[2] + dEdft) * third;
+        a1 += (dEdg[2] * gms + dEdft) * third;
     }
     if (df2) df2[(long long)y * W + x] = (O)a2;
     if (df1) df1[(long long)y * W + x] = (O)a1;
@@ -318,14 +320,14 @@ cudaError_t launch_adjoint_grad(const AdaptBufs& A, int pair, int H, int W, cons
         dim3 grid((W + 127) / 128, H);
         if (A.fp64) {
             if (out_type == T_F64)
-                k_adjoint_frames<double, double><<<grid, 128, 0, st>>>(A.pairs, pair, (const double*)A.f1, (const double*)A.f2, A.u, lamv, (double*)df2, (double*)df1);
+                k_adjoint_frames<double, double><<<grid, 128, 0, st>>>(A.pairs, pair, (const double*)A.f1, (const double*)A.f2, A.u, lamv, (double*)df2, (double*)df1, A.gms);
             else
-                k_adjoint_frames<double, float><<<grid, 128, 0, st>>>(A.pairs, pair, (const double*)A.f1, (const double*)A.f2, A.u, lamv, (float*)df2, (float*)df1);
+                k_adjoint_frames<double, float><<<grid, 128, 0, st>>>(A.pairs, pair, (const double*)A.f1, (const double*)A.f2, A.u, lamv, (float*)df2, (float*)df1, A.gms);
         } else {
             if (out_type == T_F64)
-                k_adjoint_frames<float, double><<<grid, 128, 0, st>>>(A.pairs, pair, (const float*)A.f1, (const float*)A.f2, A.u, lamv, (double*)df2, (double*)df1);
+                k_adjoint_frames<float, double><<<grid, 128, 0, st>>>(A.pairs, pair, (const float*)A.f1, (const float*)A.f2, A.u, lamv, (double*)df2, (double*)df1, A.gms);
             else
-                k_adjoint_frames<float, float><<<grid, 128, 0, st>>>(A.pairs, pair, (const float*)A.f1, (const float*)A.f2, A.u, lamv, (float*)df2, (float*)df1);
+                k_adjoint_frames<float, float><<<grid, 128, 0, st>>>(A.pairs, pair, (const float*)A.f1, (const float*)A.f2, A.u, lamv, (float*)df2, (float*)df1, A.gms);
         }
     }
     return cudaGetLastError();

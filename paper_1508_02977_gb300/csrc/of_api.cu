@@ -26,6 +26,7 @@ struct of_ctx {
     // grid
     int batch = 0;
     of_grid_opts opts{};
+    ofl::SmoothTaps taps{};  // K_sigma (r = 0: none)
     int fp64 = 1;
     size_t es = 8;  // storage element size (frames, alpha, inner vectors)
     std::vector<PairDesc> pd;
@@ -237,6 +238,7 @@ ofl::SolveBufs solve_bufs(of_ctx* h) {
     B.sweeps = h->opts.sweeps;
     B.lam = h->opts.lambda;
     B.omega = h->opts.omega;
+    B.gms = h->opts.model == OF_MODEL_CONSTANT ? 0.0 : 1.0;
     B.fp64 = h->fp64;
     B.spin_limit = 4000000000LL;  // ~2 s at 2 GHz
     return B;
@@ -254,6 +256,7 @@ ofl::AdaptBufs adapt_bufs(of_ctx* h) {
     A.eta = h->eta;
     A.etamax = h->etamax;
     A.lam = h->opts.lambda;
+    A.gms = h->opts.model == OF_MODEL_CONSTANT ? 0.0 : 1.0;
     A.fp64 = h->fp64;
     return A;
 }
@@ -564,6 +567,8 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     }
     if (!(opt.lambda > 0)) return fail(h, OF_ERR_ARG, "lambda must be > 0");
     if (!(opt.omega > 0 && opt.omega < 2)) return fail(h, OF_ERR_ARG, "omega must be in (0, 2)");
+    if (!(opt.sigma >= 0 && opt.sigma <= 16)) return fail(h, OF_ERR_ARG, "sigma must be in [0, 16]");
+    if (opt.model != OF_MODEL_ILLUMINATION && opt.model != OF_MODEL_CONSTANT) return fail(h, OF_ERR_ARG, "bad model");
     if (opt.tile_x < 4 || opt.tile_y < 4 || opt.tile_x % 4 || opt.tile_y % 4 || opt.tile_x > 256 || opt.tile_y > 256)
         return fail(h, OF_ERR_ARG, "tile sizes must be multiples of 4 in [4, 256]");
     if (opt.overlap < 0 || opt.overlap > 32 || opt.sweeps < 0 || opt.sweeps > 64)
@@ -593,6 +598,18 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     CK(cudaStreamSynchronize(h->stream));
     free_all(h);
     h->opts = opt;
+    // K_sigma taps: w_k = exp(-k^2 / (2 sigma^2)), |k| <= ceil(3 sigma)
+    h->taps = ofl::SmoothTaps{};
+    if (opt.sigma > 0) {
+        const int r = std::min((int)std::ceil(3.0 * opt.sigma), ofl::OF_SMOOTH_RMAX);
+        h->taps.r = r;
+        h->taps.cw[0] = 0.0;
+        for (int j = 0; j <= 2 * r; ++j) {
+            const double k = j - r;
+            h->taps.w[j] = std::exp(-k * k / (2.0 * opt.sigma * opt.sigma));
+            h->taps.cw[j + 1] = h->taps.cw[j] + h->taps.w[j];
+        }
+    }
     h->fp64 = fp64;
     h->es = fp64 ? 8 : 4;
     h->batch = batch;
@@ -708,9 +725,34 @@ of_status of_set_frames(of_handle h, int pair, const void* f1, const void* f2, o
     if (s != OF_OK) return s;
     s = copy_in(h, f2, dt, pitch, (char*)h->f2 + d.frame_off * es, d.pitch, d.H, d.W);
     if (s != OF_OK) return s;
+    if (h->opts.sigma > 0) {  // f = K_sigma * I; the r vector of the pair is scratch here
+        const int ty = h->fp64 ? ofl::T_F64 : ofl::T_F32;
+        void* scratch = (char*)h->r + d.vec_off * es;
+        CK(ofl::launch_smooth((char*)h->f1 + d.frame_off * es, scratch, ty, d.W, d.H, d.pitch, h->taps, false,
+                              h->stream));
+        CK(ofl::launch_smooth((char*)h->f2 + d.frame_off * es, scratch, ty, d.W, d.H, d.pitch, h->taps, false,
+                              h->stream));
+        count_other(h, 4);
+    }
     h->frames_set[pair] = 1;
     h->solved = false;
     h->cells_dirty = true;
+    return OF_OK;
+}
+
+of_status of_get_frames(of_handle h, int pair, void* f1, void* f2, of_dtype dt) {
+    of_status s = check_pair(h, pair);
+    if (s != OF_OK) return s;
+    if (!f1 || !f2) return fail(h, OF_ERR_ARG, "null frame");
+    if (!h->frames_set[pair]) return fail(h, OF_ERR_STATE, "frames not set");
+    DevGuard g(h->device);
+    const PairDesc& d = h->pd[pair];
+    const int ty = h->fp64 ? ofl::T_F64 : ofl::T_F32;
+    s = copy_out(h, (char*)h->f1 + d.frame_off * h->es, ty, d.pitch, f1, dt, d.H, d.W);
+    if (s != OF_OK) return s;
+    s = copy_out(h, (char*)h->f2 + d.frame_off * h->es, ty, d.pitch, f2, dt, d.H, d.W);
+    if (s != OF_OK) return s;
+    CK(cudaStreamSynchronize(h->stream));
     return OF_OK;
 }
 
@@ -857,8 +899,17 @@ of_status of_adjoint(of_handle h, void* const* dLdU, void* const* dLdalpha, void
         void* d1 = dLdf1 ? dLdf1[p] : nullptr;
         // device outputs are written directly; host outputs go through the staging buffer
         const bool host_any = (da && !is_device_ptr(da)) || (d2 && !is_device_ptr(d2)) || (d1 && !is_device_ptr(d1));
+        // with K_sigma, the frame gradients are taken w.r.t. the images I given to
+        // of_set_frames: dL/dI = S^T dL/df (S = K_sigma), applied in place
+        void* sscr = (char*)h->q + d.vec_off * h->es;  // H x W values of dt fit in the q planes
+        auto smooth_t = [&](void* g) {
+            return h->opts.sigma > 0 ? ofl::launch_smooth(g, sscr, tcode(dt), d.W, d.H, d.W, h->taps, true, st)
+                                     : cudaSuccess;
+        };
         if (!host_any) {
             CK(ofl::launch_adjoint_grad(A, p, d.H, d.W, h->x[cur], da, d2, d1, tcode(dt), st));
+            if (d2) CK(smooth_t(d2));
+            if (d1) CK(smooth_t(d1));
         } else {
             // one output at a time through the staging buffer
             const size_t esz = tsize(dt);
@@ -870,10 +921,12 @@ of_status of_adjoint(of_handle h, void* const* dLdU, void* const* dLdalpha, void
                     CK(ofl::launch_adjoint_grad(A, p, d.H, d.W, h->x[cur], it.kind == 0 ? it.dst : nullptr,
                                                 it.kind == 1 ? it.dst : nullptr, it.kind == 2 ? it.dst : nullptr,
                                                 tcode(dt), st));
+                    if (it.kind != 0) CK(smooth_t(it.dst));
                 } else {
                     CK(ofl::launch_adjoint_grad(A, p, d.H, d.W, h->x[cur], it.kind == 0 ? h->staging : nullptr,
                                                 it.kind == 1 ? h->staging : nullptr,
                                                 it.kind == 2 ? h->staging : nullptr, tcode(dt), st));
+                    if (it.kind != 0) CK(smooth_t(h->staging));
                     CK(cudaMemcpyAsync(it.dst, h->staging, it.n * esz, cudaMemcpyDeviceToHost, st));
                     CK(cudaStreamSynchronize(st));
                 }

@@ -34,10 +34,12 @@ template <typename R> struct NodeVal { V3<R> p; R f1, f2; };
 
 // Contributions of the two triangles of one square to its corners
 // A=(x,y) B=(x+1,y) C=(x+1,y+1) D=(x,y+1): sign * (A_K p)_i, and, when WANT_B,
-// the load -|K|/3 ft g of each triangle (same for its 3 vertices).
+// the load -|K|/3 ft g of each triangle (same for its 3 vertices).  gms
+// scales the illumination column g_m of the element data: 1 for the model
+// with brightness change, 0 for brightness constancy.
 template <typename R, bool WANT_B, bool WANT_A = true>
 __device__ __forceinline__ void square_contrib(const NodeVal<R>& A, const NodeVal<R>& B, const NodeVal<R>& C,
-                                               const NodeVal<R>& D, R al0, R al1, R lam, bool valid,
+                                               const NodeVal<R>& D, R al0, R al1, R lam, R gms, bool valid,
                                                V3<R>& cA, V3<R>& cB, V3<R>& cC, V3<R>& cD,
                                                V3<R>& bA, V3<R>& bB, V3<R>& bC, V3<R>& bD) {
     const R third = kconst<R>(1.0 / 3.0);
@@ -45,8 +47,8 @@ __device__ __forceinline__ void square_contrib(const NodeVal<R>& A, const NodeVa
     const R h = kconst<R>(OF_STIFF_HALF);
     const R zero = kconst<R>(0.0);
     // ---- t = 0: A, B, C
-    R g0x = B.f2 - A.f2, g0y = C.f2 - B.f2, g0m = -(A.f1 + B.f1 + C.f1) * third;
-    R g1x = C.f2 - D.f2, g1y = D.f2 - A.f2, g1m = -(A.f1 + D.f1 + C.f1) * third;
+    R g0x = B.f2 - A.f2, g0y = C.f2 - B.f2, g0m = -(A.f1 + B.f1 + C.f1) * third * gms;
+    R g1x = C.f2 - D.f2, g1y = D.f2 - A.f2, g1m = -(A.f1 + D.f1 + C.f1) * third * gms;
     if constexpr (!WANT_A) {
         cA = cB = cC = cD = v3(zero, zero, zero);
     } else {
@@ -105,6 +107,7 @@ struct ApplyParams {
     unsigned* counter;         // [batch]
     const C* f1; const C* f2; const C* alpha;
     R lam;
+    R gms;                     // illumination column scale (1: model with m, 0: brightness constancy)
     int rows_per_block;
     // vectors ([3][H][pitch] planes at pair vec_off)
     const R* in;        // APPLY: p;  PCG: z;  RES: x (double)
@@ -174,6 +177,7 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
     const bool mycol_owned = (lane >= 1) && (cx < W) && (cx >= 0);  // side-effect writes
     const bool out_col = (lane < 31) && (cx + 1 < W);
     const T lam = Cvt<T>::from(P.lam);
+    const T gms = Cvt<T>::from(P.gms);
     const T zero = kconst<T>(0.0);
 
     // load node (x, y) of the input vector + frames, with the mode's fused
@@ -245,8 +249,8 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
         const T al0 = valid ? Cvt<T>::from(al[2 * ((long long)sy * pitch + cx)]) : zero;
         const T al1 = valid ? Cvt<T>::from(al[2 * ((long long)sy * pitch + cx) + 1]) : zero;
         V3<T> cA, cB, cC, cD, bA, bB, bC, bD;
-        square_contrib<T, WANT_B || IS_RES, MODE != MODE_RESB>(cur, ncur, nnxt, nxt, al0, al1, lam, valid, cA, cB,
-                                                                  cC, cD, bA, bB, bC, bD);
+        square_contrib<T, WANT_B || IS_RES, MODE != MODE_RESB>(cur, ncur, nnxt, nxt, al0, al1, lam, gms, valid, cA,
+                                                                  cB, cC, cD, bA, bB, bC, bD);
         V3<T> left = shfl_down3(cA);
         V3<T> res = carry + cB + left;  // node (cx+1, sy) complete
         V3<T> resb = v3(zero, zero, zero);
@@ -442,7 +446,7 @@ __global__ void __launch_bounds__(32) k_apply4(const ApplyParams<float, float, f
     const int Y1 = min(Y0 + P.rows_per_block, H);
     const int nrows = Y1 - Y0 + 2;         // node rows Y0 - 1 .. Y1
     const bool own = lane >= 1 && c0 < W;  // this lane's columns are output columns
-    const float lam = P.lam;
+    const float lam = P.lam, gms = P.gms;
     float* extra = reinterpret_cast<float*>(a4_ring + A4_NS * A4_NARR * 32);
 
     auto slot = [&](int s, int a) -> float4* { return a4_ring + (s * A4_NARR + a) * 32 + lane; };
@@ -578,8 +582,8 @@ __global__ void __launch_bounds__(32) k_apply4(const ApplyParams<float, float, f
                 const NodeVal<float> A = pick(cur, k), D = pick(nxt, k);
                 const NodeVal<float> B = (k < 3) ? pick(cur, k + 1) : rcur;
                 const NodeVal<float> C = (k < 3) ? pick(nxt, k + 1) : rnxt;
-                square_contrib<float, false>(A, B, C, D, alv[2 * k], alv[2 * k + 1], lam, valid, cA[k], cB[k], cC[k],
-                                             cD[k], bdum, bdum, bdum, bdum);
+                square_contrib<float, false>(A, B, C, D, alv[2 * k], alv[2 * k + 1], lam, gms, valid, cA[k], cB[k],
+                                             cC[k], cD[k], bdum, bdum, bdum, bdum);
             }
             // right corners of the previous lane's last square
             const V3<float> pB = v3(__shfl_up_sync(0xffffffffu, cB[3].a, 1), __shfl_up_sync(0xffffffffu, cB[3].b, 1),

@@ -75,6 +75,7 @@ static ApplyParams<R, C, RI> base_params(const SolveBufs& B) {
     P.f2 = (const C*)B.f2;
     P.alpha = (const C*)B.alpha;
     P.lam = (R)B.lam;
+    P.gms = (R)B.gms;
     P.rows_per_block = B.rows_per_block;
     return P;
 }
@@ -174,7 +175,7 @@ int schwarz_max_grid(int fp64, int npt, int tx, int ty, int ov, int threads, siz
 template <typename R>
 static cudaError_t cells_t(const SolveBufs& B, int pair, int W, int H, void* c0, void* c1, cudaStream_t st) {
     dim3 grid((W + 127) / 128, H);
-    k_cells<R><<<grid, 128, 0, st>>>(B.pairs, pair, (const R*)B.f1, (const R*)B.f2, (const R*)B.alpha,
+    k_cells<R><<<grid, 128, 0, st>>>(B.pairs, pair, (R)B.gms, (const R*)B.f1, (const R*)B.f2, (const R*)B.alpha,
                                     (typename CellT<R>::type*)c0, (typename CellT<R>::type*)c1);
     return cudaGetLastError();
 }

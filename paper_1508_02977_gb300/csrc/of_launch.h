@@ -46,6 +46,7 @@ struct SolveBufs {
     int Tx, Ty, ov, sweeps;
     double lam;
     double omega;  // relaxation factor of the local block SOR sweeps
+    double gms;    // illumination column scale of the element data (1 or 0, see of_model)
     int fp64;            // 1: everything FP64; 0: FP32 inner with FP64 residual
     long long spin_limit;
     int use_cond;        // Schwarz launches inside the inner-loop graph set its condition
@@ -95,9 +96,23 @@ struct AdaptBufs {
     double* etamax;      // [batch]
     unsigned* cnt;
     double lam;
+    double gms;
     int fp64;
 };
 cudaError_t launch_indicator(const AdaptBufs& A, int pair, int H, int W, cudaStream_t st);
+
+// K_sigma pre-smoothing: sampled Gaussian taps w_j of offsets j - r, j = 0..2r,
+// and the prefix sums cw[i] = w_0 + ... + w_{i-1}
+constexpr int OF_SMOOTH_RMAX = 48;
+struct SmoothTaps {
+    int r;
+    double w[2 * OF_SMOOTH_RMAX + 1];
+    double cw[2 * OF_SMOOTH_RMAX + 2];
+};
+// f ([H][pitch], type T_F32/T_F64) <- S f (or S^T f with transpose); scratch
+// holds H x pitch values of the same type
+cudaError_t launch_smooth(void* f, void* scratch, int type, int W, int H, long long pitch, const SmoothTaps& T,
+                          bool transpose, cudaStream_t st);
 cudaError_t launch_alpha_update(const AdaptBufs& A, int pair, int H, int W, double kappa, double eta_thr,
                                 double alpha_th, cudaStream_t st);
 // adjoint gradients for one pair: u = solution, lam = adjoint state (FP64 planes)

@@ -83,7 +83,8 @@ __global__ void __launch_bounds__(NA_NW * 32)
         const long long ao = 2 * ((long long)sy * (W - 1) + cx);
         const double al0 = valid ? alpha[ao] : 0.0, al1 = valid ? alpha[ao + 1] : 0.0;
         V3<double> cA, cB, cC, cD, bA, bB, bC, bD;
-        square_contrib<double, true>(cur, ncur, nnxt, nxt, al0, al1, lam, valid, cA, cB, cC, cD, bA, bB, bC, bD);
+        square_contrib<double, true>(cur, ncur, nnxt, nxt, al0, al1, lam, 1.0, valid, cA, cB, cC, cD, bA, bB, bC,
+                                     bD);
         const V3<double> res = carry + cB + shfl_down3(cA);
         const V3<double> rhs = carry_b + bB + shfl_down3(bA);
         if (sy >= Y0 && out_col) {

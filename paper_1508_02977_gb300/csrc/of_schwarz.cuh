@@ -231,7 +231,7 @@ template <> struct CellView<double> {
 
 // Cell records of node (x, y) from the frames and alpha (workspace layouts).
 template <typename R>
-__device__ __forceinline__ void cell_records(int x, int y, int W, int H, int pitch, const R* f1, const R* f2,
+__device__ __forceinline__ void cell_records(int x, int y, int W, int H, int pitch, R gms, const R* f1, const R* f2,
                                              const R* al, R h0[3], R& wE, R h1[3], R& wN) {
     const R isq24 = R(0.20412414523193151);  // 1/sqrt(24)
     const R third = R(1) / R(3), half = R(0.5);
@@ -243,10 +243,10 @@ __device__ __forceinline__ void cell_records(int x, int y, int W, int H, int pit
         const R a1 = f1[o], b1 = f1[o + 1], c1 = f1[o + pitch + 1], d1 = f1[o + pitch];
         h0[0] = (b2 - a2) * isq24;
         h0[1] = (c2 - b2) * isq24;
-        h0[2] = -(a1 + b1 + c1) * third * isq24;
+        h0[2] = -(a1 + b1 + c1) * third * isq24 * gms;
         h1[0] = (c2 - d2) * isq24;
         h1[1] = (d2 - a2) * isq24;
-        h1[2] = -(a1 + d1 + c1) * third * isq24;
+        h1[2] = -(a1 + d1 + c1) * third * isq24 * gms;
     }
     // edge to (x+1,y): t0 of square (x,y) and t1 of square (x,y-1)
     wE = half * ((vc ? al[2 * o] : R(0)) + ((x < W - 1 && y >= 1) ? al[2 * (o - pitch) + 1] : R(0)));
@@ -816,14 +816,14 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
 
 // Cell records for every node of every pair (once per solve).
 template <typename R>
-__global__ void k_cells(const PairDesc* pairs, int pair, const R* __restrict__ f1a, const R* __restrict__ f2a,
+__global__ void k_cells(const PairDesc* pairs, int pair, R gms, const R* __restrict__ f1a, const R* __restrict__ f2a,
                         const R* __restrict__ ala, typename CellT<R>::type* __restrict__ c0a,
                         typename CellT<R>::type* __restrict__ c1a) {
     const PairDesc pd = pairs[pair];
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= pd.W) return;
     R h0[3], h1[3], wE, wN;
-    cell_records<R>(x, y, pd.W, pd.H, pd.pitch, f1a + pd.frame_off, f2a + pd.frame_off, ala + 2 * pd.frame_off, h0,
+    cell_records<R>(x, y, pd.W, pd.H, pd.pitch, gms, f1a + pd.frame_off, f2a + pd.frame_off, ala + 2 * pd.frame_off, h0,
                     wE, h1, wN);
     const long long o = pd.frame_off + (long long)y * pd.pitch + x;
     if constexpr (sizeof(R) == 4) {

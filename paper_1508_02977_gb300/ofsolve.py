@@ -28,12 +28,14 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_STAT
 OF_F32, OF_F64 = 0, 1
 OF_PREC_FP64, OF_PREC_MIXED = 0, 1
 OF_PC_SCHWARZ, OF_PC_JACOBI = 0, 1
+OF_MODEL_ILLUMINATION, OF_MODEL_CONSTANT = 0, 1
 
 
 class GridOpts(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("overlap", ctypes.c_int),
                 ("sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("lam", ctypes.c_double),
-                ("preconditioner", ctypes.c_int), ("omega", ctypes.c_double)]
+                ("preconditioner", ctypes.c_int), ("omega", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("model", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -66,6 +68,7 @@ _lib.of_setup_grid.argtypes = [_h, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
 _lib.of_set_frames.argtypes = [_h, ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int64]
 _lib.of_set_alpha.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_int]
 _lib.of_get_alpha.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_int]
+_lib.of_get_frames.argtypes = [_h, ctypes.c_int, _vp, _vp, ctypes.c_int]
 _lib.of_solve.argtypes = [_h, ctypes.POINTER(SolveOpts), ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(SolveInfo)]
 _lib.of_adapt_alpha.argtypes = [_h, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp), ctypes.c_int]
 _lib.of_adjoint.argtypes = [_h, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
@@ -84,7 +87,7 @@ for _f in ("of_create", "of_setup_grid", "of_set_frames", "of_set_alpha", "of_ge
            "of_get_profile", "of_residual_noalloc", "of_destroy"):
     getattr(_lib, _f).restype = ctypes.c_int
 
-EXPORTS = ("of_create", "of_setup_grid", "of_set_frames", "of_set_alpha", "of_get_alpha", "of_solve",
+EXPORTS = ("of_create", "of_setup_grid", "of_set_frames", "of_get_frames", "of_set_alpha", "of_get_alpha", "of_solve",
            "of_adapt_alpha", "of_adjoint", "of_apply", "of_precondition", "of_residual", "of_set_profiling",
            "of_get_profile", "of_residual_noalloc", "of_destroy", "of_last_error")
 
@@ -144,14 +147,15 @@ def of_create(device: int = 0, stream=None):
 
 
 def of_setup_grid(h, sizes, tile=(32, 32), overlap=0, sweeps=1, precision=OF_PREC_MIXED, lam=1.0,
-                  preconditioner=OF_PC_SCHWARZ, omega=1.0):
+                  preconditioner=OF_PC_SCHWARZ, omega=1.0, sigma=0.0, model=0):
     """sizes: list of (W, H); omega: relaxation factor of the local block SOR
-    sweeps, in (0, 2)."""
+    sweeps, in (0, 2); sigma: K_sigma pre-smoothing of the frames (0: none);
+    model: OF_MODEL_ILLUMINATION or OF_MODEL_CONSTANT."""
     n = len(sizes)
     Wa = (ctypes.c_int32 * n)(*[int(w) for w, _ in sizes])
     Ha = (ctypes.c_int32 * n)(*[int(hh) for _, hh in sizes])
     o = GridOpts(int(tile[0]), int(tile[1]), int(overlap), int(sweeps), int(precision), float(lam), int(preconditioner),
-                 float(omega))
+                 float(omega), float(sigma), int(model))
     return _check(h, _lib.of_setup_grid(h, n, Wa, Ha, ctypes.byref(o)))
 
 
@@ -166,6 +170,15 @@ def of_set_frames(h, pair, f1, f2):
 def of_set_alpha(h, pair, alpha=None, alpha_const=0.0):
     p, dt = _ptr_dtype(alpha)
     return _check(h, _lib.of_set_alpha(h, int(pair), _vp(p) if p else None, float(alpha_const), dt))
+
+
+def of_get_frames(h, pair, f1, f2):
+    """The stored (K_sigma-smoothed) frames into two [H][W] arrays."""
+    p1, dt = _ptr_dtype(f1)
+    p2, dt2 = _ptr_dtype(f2)
+    if dt != dt2:
+        raise TypeError("frames must share a dtype")
+    return _check(h, _lib.of_get_frames(h, int(pair), _vp(p1), _vp(p2), dt))
 
 
 def of_get_alpha(h, pair, out):

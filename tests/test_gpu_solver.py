@@ -561,6 +561,136 @@ def test_adjoint_matches_oracle_and_differences(S, oracle):
         assert abs(fd - d2[y, x]) <= 1e-5 * np.abs(d2).max()
 
 
+def test_adjoint_with_presmoothing(S, oracle):
+    """With K_sigma the frame gradients are taken w.r.t. the raw images:
+    dL/dI = S^T dL/df.  Against the oracle's adjoint gradient pulled back by
+    its own transpose, and central differences on raw pixels of I2."""
+    W, H, sigma = 22, 18, 1.2
+    I1, I2 = synth.random_frames(W, H, 211)
+    alpha = synth.random_alpha(W, H, 212)
+    gt = np.random.default_rng(213).uniform(-1, 1, (2, H, W))
+    f1o, f2o = oracle.smooth(I1, sigma), oracle.smooth(I2, sigma)
+    sysm = oracle.System.from_frames(f1o, f2o, alpha, 1.0)
+    Uo = sysm.solve_direct()
+    Lo = sysm.solve_with(oracle.mean_epe_grad(Uo, gt))
+    _, d2_o, d1_o = oracle.adjoint_grad(f1o, f2o, alpha, 1.0, Uo, Lo)
+    d2_o, d1_o = oracle.smooth_transpose(d2_o, sigma), oracle.smooth_transpose(d1_o, sigma)
+
+    def gpu(I1_, I2_, grads=True):
+        h = handle(S, [(W, H)], precision=S.OF_PREC_FP64, tile=(16, 16), sigma=sigma)
+        try:
+            S.of_set_frames(h, 0, dev(I1_), dev(I2_))
+            S.of_set_alpha(h, 0, dev(alpha))
+            U = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+            S.of_solve(h, [U], rtol=1e-14, max_inner=20000)
+            Un = U.cpu().numpy()
+            if not grads:
+                return Un, None, None
+            d2 = torch.zeros(H, W, dtype=torch.float64, device="cuda")
+            d1 = torch.zeros_like(d2)
+            S.of_adjoint(h, [dev(oracle.mean_epe_grad(Un, gt))], None, [d2], [d1])
+            return Un, d2.cpu().numpy(), d1.cpu().numpy()
+        finally:
+            S.of_destroy(h)
+
+    _, d2, d1 = gpu(I1, I2)
+    for got, want in ((d2, d2_o), (d1, d1_o)):
+        assert np.abs(got - want).max() <= 1e-8 * np.abs(want).max()
+    h_fd = 1e-4
+    rng = np.random.default_rng(214)
+    for _ in range(3):
+        y, x = rng.integers(0, H), rng.integers(0, W)
+        Ip, Im = I2.copy(), I2.copy()
+        Ip[y, x] += h_fd
+        Im[y, x] -= h_fd
+        fd = (oracle.mean_epe(gpu(I1, Ip, False)[0], gt) - oracle.mean_epe(gpu(I1, Im, False)[0], gt)) / (2 * h_fd)
+        assert abs(fd - d2[y, x]) <= 1e-5 * np.abs(d2).max()
+
+
+@pytest.mark.parametrize("prec,sigma", [(0, 1.5), (0, 0.6), (1, 2.0)])
+def test_presmoothing_matches_oracle(S, oracle, prec, sigma):
+    """Stored frames f = K_sigma * I (of_get_frames) against the oracle, on a
+    frame with ragged edges and taps wider than the border region."""
+    W, H = 131, 37
+    I1, I2 = synth.random_frames(W, H, 215)
+    dt = torch.float64 if prec == 0 else torch.float32
+    if prec == 1:
+        I1, I2 = f32(I1), f32(I2)
+    h = handle(S, [(W, H)], precision=prec, sigma=sigma)
+    try:
+        S.of_set_frames(h, 0, dev(I1, dt), dev(I2, dt))
+        g1 = torch.zeros(H, W, dtype=dt, device="cuda")
+        g2 = torch.zeros_like(g1)
+        S.of_get_frames(h, 0, g1, g2)
+        g1, g2 = g1.cpu().numpy().astype(np.float64), g2.cpu().numpy().astype(np.float64)
+    finally:
+        S.of_destroy(h)
+    tol = 1e-13 if prec == 0 else 2e-6  # FP32: a normalised sum of <= 13 x 13 positive-weight terms
+    for got, I in ((g1, I1), (g2, I2)):
+        want = oracle.smooth(I, sigma)
+        assert np.abs(got - want).max() <= tol * np.abs(want).max()
+
+
+# ------------------------------------------------ brightness constancy --
+
+def test_constant_model_fp64_matches_oracle(S, oracle):
+    """Brightness constancy (OF_MODEL_CONSTANT), FP64 path on the 64x48
+    blobs: flow equals the oracle's flow-block direct solve to 1e-10, m stays
+    0, and the indicator and the adjoint gradients match the oracle's."""
+    p = synth.blobs()
+    sysm = oracle.System.from_frames(p.f1, p.f2, p.alpha0, p.lam, model=1)
+    Ud = sysm.solve_direct()
+    gt = np.random.default_rng(301).uniform(-1, 1, (2, p.H, p.W))
+    h = handle(S, [(p.W, p.H)], tile=(16, 16), sweeps=2, omega=1.5, precision=S.OF_PREC_FP64,
+               model=S.OF_MODEL_CONSTANT)
+    try:
+        S.of_set_frames(h, 0, dev(p.f1), dev(p.f2))
+        S.of_set_alpha(h, 0, None, p.alpha0)
+        U = torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda")
+        st, info = S.of_solve(h, [U], rtol=1e-14, max_inner=20000)
+        Un = U.cpu().numpy()
+        d2 = torch.zeros(p.H, p.W, dtype=torch.float64, device="cuda")
+        d1 = torch.zeros_like(d2)
+        S.of_adjoint(h, [dev(oracle.mean_epe_grad(Un, gt))], None, [d2], [d1])
+        eta = torch.zeros(p.H - 1, p.W - 1, 2, dtype=torch.float64, device="cuda")
+        S.of_adapt_alpha(h, 4.0, 0.25, 1e-3, [eta])
+        d2, d1, eta = d2.cpu().numpy(), d1.cpu().numpy(), eta.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    assert np.abs(Un[2]).max() == 0.0
+    assert np.linalg.norm(Un - Ud) <= 1e-10 * np.linalg.norm(Ud)
+    Lo = sysm.solve_with(oracle.mean_epe_grad(Ud, gt))
+    _, d2_o, d1_o = oracle.adjoint_grad(p.f1, p.f2, p.alpha0, p.lam, Ud, Lo, model=1)
+    for got, want in ((d2, d2_o), (d1, d1_o)):
+        assert np.abs(got - want).max() <= 1e-8 * np.abs(want).max()
+    eta_o = sysm.indicator(Un)
+    assert np.abs(eta - eta_o).max() <= 1e-12 * eta_o.max()
+
+
+def test_constant_model_mixed_texture(S, oracle):
+    """Brightness constancy on the FP32 path (640x480 texture with an
+    illumination ramp the model does not describe): oracle-recomputed residual
+    <= 1e-6 and flow within 1e-4 px of the oracle's solve."""
+    p = synth.texture()
+    f1, f2 = f32(p.f1), f32(p.f2)
+    h = handle(S, [(p.W, p.H)], tile=(48, 48), sweeps=4, omega=1.6, precision=S.OF_PREC_MIXED,
+               model=S.OF_MODEL_CONSTANT)
+    try:
+        S.of_set_frames(h, 0, dev(p.f1, torch.float32), dev(p.f2, torch.float32))
+        S.of_set_alpha(h, 0, None, p.alpha0)
+        U = torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda")
+        st, info = S.of_solve(h, [U], rtol=1e-6)
+        U = U.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    assert np.abs(U[2]).max() == 0.0
+    rr = oracle.rel_residual_frames(f1, f2, p.alpha0, p.lam, U, model=1)
+    assert rr <= 1e-6
+    sysm = oracle.System.from_frames(f1, f2, np.float32(p.alpha0), p.lam, model=1)
+    Uo, _, _ = sysm.solve_pcg(tol=1e-12)
+    assert np.abs(U[:2] - Uo[:2]).max() <= 1e-4
+
+
 def test_autograd_function_matches_oracle_gradients(S, oracle):
     """torch.autograd through OFSolve (FP64 handle): gradients of the mean
     endpoint error w.r.t. alpha, f2 and f1 equal the oracle's adjoint."""

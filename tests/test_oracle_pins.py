@@ -37,24 +37,26 @@ def bary(verts):
 QPTS = [(2 / 3, 1 / 6, 1 / 6), (1 / 6, 2 / 3, 1 / 6), (1 / 6, 1 / 6, 2 / 3)]
 
 
-def element_data(f1, f2, verts):
-    """g = (grad f2_h, -f1_h(centroid)), ft = (f2_h - f1_h)(centroid)."""
+def element_data(f1, f2, verts, illumination=True):
+    """g = (grad f2_h, -f1_h(centroid)), ft = (f2_h - f1_h)(centroid); without
+    illumination (Horn and Schunck's brightness constancy) g = (grad f2_h, 0)."""
     G, _ = bary(verts)
     v2 = np.array([f2[y, x] for x, y in verts])
     v1 = np.array([f1[y, x] for x, y in verts])
     grad2 = G.T @ v2
     cen = np.array([1 / 3, 1 / 3, 1 / 3])
-    return np.array([grad2[0], grad2[1], -(cen @ v1)]), cen @ (v2 - v1)
+    gm = -(cen @ v1) if illumination else 0.0
+    return np.array([grad2[0], grad2[1], gm]), cen @ (v2 - v1)
 
 
-def bilinear(f1, f2, alpha, lam, U, V):
+def bilinear(f1, f2, alpha, lam, U, V, illumination=True):
     """int (g.U_h)(g.V_h) + sum_c Lambda_c grad U_c . grad V_c  and
     the load  -int ft g.V_h, by the 3-point rule."""
     H, W = f1.shape
     a_uv = 0.0
     l_v = 0.0
     for x, y, t, verts in triangles(W, H):
-        g, ft = element_data(f1, f2, verts)
+        g, ft = element_data(f1, f2, verts, illumination)
         G, area = bary(verts)
         Lam = np.array([alpha[y, x, t], alpha[y, x, t], lam])
         uv = np.array([[U[c, yy, xx] for c in range(3)] for xx, yy in verts])  # [vertex][c]
@@ -94,6 +96,41 @@ def test_operator_and_load_equal_weak_form(oracle, W, H):
         a_uv, l_v = bilinear(f1, f2, alpha, lam, U, V)
         assert abs(np.sum(V * S.matvec(U)) - a_uv) < 1e-12 * max(1.0, abs(a_uv))
         assert abs(S.b @ V.ravel() - l_v) < 1e-13 * max(1.0, abs(l_v))
+
+
+def test_constant_brightness_model_is_horn_schunck(oracle):
+    """Brightness constancy (model 1): U^T A V and b^T V equal the
+    Horn-Schunck weak form (Eq. BW with rho = 0: data (grad f2 . u + ft)^2,
+    alpha |grad u|^2) integrated by the independent rule, the m block is
+    decoupled from (u1, u2) and carries no load."""
+    W, H = 5, 4
+    rng = np.random.default_rng(17)
+    f1, f2 = synth.random_frames(W, H, 18)
+    alpha = synth.random_alpha(W, H, 19)
+    S = oracle.System.from_frames(f1, f2, alpha, 0.9, model=1)
+    for _ in range(3):
+        U = rng.standard_normal((3, H, W))
+        V = rng.standard_normal((3, H, W))
+        a_uv, l_v = bilinear(f1, f2, alpha, 0.9, U, V, illumination=False)
+        assert abs(np.sum(V * S.matvec(U)) - a_uv) < 1e-12 * max(1.0, abs(a_uv))
+        assert abs(S.b @ V.ravel() - l_v) < 1e-13 * max(1.0, abs(l_v))
+    A = S.dense()
+    n = W * H
+    assert np.abs(A[:2 * n, 2 * n:]).max() == 0.0
+    assert np.abs(S.b[2 * n:]).max() == 0.0
+
+
+def test_constant_brightness_solution_satisfies_system(oracle):
+    """The flow-block solve of model 1 solves A U = b with m = 0 (checked
+    with the assembled matrix) and differs from the illumination model's
+    solution (the m coupling matters)."""
+    p = synth.blobs()
+    S1 = oracle.System.from_frames(p.f1, p.f2, p.alpha0, p.lam, model=1)
+    U1 = S1.solve_direct()
+    assert np.abs(U1[2]).max() == 0.0
+    assert S1.rel_residual(U1) <= 1e-12
+    U0 = oracle.System.from_frames(p.f1, p.f2, p.alpha0, p.lam).solve_direct()
+    assert np.linalg.norm(U1[:2] - U0[:2]) > 1e-3 * np.linalg.norm(U0[:2])
 
 
 def test_assembled_matrix_symmetric_spd(oracle):
@@ -413,7 +450,8 @@ def test_alpha_update_closed_form(oracle):
 
 # ------------------------------------------------------------- adjoint ----
 
-def test_adjoint_gradient_matches_central_differences(oracle):
+@pytest.mark.parametrize("model", [0, 1])
+def test_adjoint_gradient_matches_central_differences(oracle, model):
     W, H = 7, 6
     f1, f2 = synth.random_frames(W, H, 51)
     alpha = synth.random_alpha(W, H, 52)
@@ -421,13 +459,13 @@ def test_adjoint_gradient_matches_central_differences(oracle):
     gt = np.random.default_rng(53).uniform(-1, 1, (2, H, W))
 
     def loss(f1_, f2_, a_):
-        S_ = oracle.System.from_frames(f1_, f2_, a_, lam)
+        S_ = oracle.System.from_frames(f1_, f2_, a_, lam, model)
         return oracle.mean_epe(S_.solve_direct(), gt)
 
-    S = oracle.System.from_frames(f1, f2, alpha, lam)
+    S = oracle.System.from_frames(f1, f2, alpha, lam, model)
     U = S.solve_direct()
     Lam = S.solve_with(oracle.mean_epe_grad(U, gt))
-    da, d2, d1 = oracle.adjoint_grad(f1, f2, alpha, lam, U, Lam)
+    da, d2, d1 = oracle.adjoint_grad(f1, f2, alpha, lam, U, Lam, model=model)
     h = 1e-4
     rng = np.random.default_rng(54)
     for _ in range(6):
@@ -465,6 +503,62 @@ def test_elementwise_apply_equals_csr(oracle):
 
 
 # ------------------------------------------------------------ partition ----
+
+# ------------------------------------------------------------ K_sigma --
+
+def test_smooth_brute_force_2d(oracle):
+    """Separable passes = the 2-D normalised sum written out directly."""
+    rng = np.random.default_rng(4)
+    I = rng.standard_normal((9, 13))
+    sigma = 1.3
+    r = int(np.ceil(3 * sigma))
+    want = np.zeros_like(I)
+    for y in range(9):
+        for x in range(13):
+            num = den = 0.0
+            for j in range(-r, r + 1):
+                for k in range(-r, r + 1):
+                    if 0 <= y + j < 9 and 0 <= x + k < 13:
+                        w = np.exp(-(j * j + k * k) / (2 * sigma * sigma))
+                        num += w * I[y + j, x + k]
+                        den += w
+            want[y, x] = num / den
+    assert np.abs(oracle.smooth(I, sigma) - want).max() <= 1e-13
+
+
+@pytest.mark.parametrize("sigma", [1.5, 2.0])
+def test_smooth_interior_matches_scipy(oracle, sigma):
+    """Away from the border (no truncated taps) K_sigma is scipy's Gaussian
+    filter with the same 3-sigma truncation."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    I = np.random.default_rng(5).standard_normal((40, 50))
+    r = int(np.ceil(3 * sigma))
+    ref = ndimage.gaussian_filter(I, sigma, truncate=3.0, mode="constant")
+    f = oracle.smooth(I, sigma)
+    assert np.abs(f[r:-r, r:-r] - ref[r:-r, r:-r]).max() <= 1e-12
+
+
+def test_smooth_closed_forms(oracle):
+    """Constants are preserved everywhere (normalisation); a linear ramp is
+    preserved wherever the taps are symmetric (the interior)."""
+    H, W, sigma = 30, 40, 1.7
+    r = int(np.ceil(3 * sigma))
+    assert np.abs(oracle.smooth(np.full((H, W), 0.37), sigma) - 0.37).max() <= 1e-15
+    y, x = np.mgrid[0:H, 0:W]
+    ramp = 0.3 * x - 0.7 * y + 2.0
+    f = oracle.smooth(ramp, sigma)
+    assert np.abs(f[r:-r, r:-r] - ramp[r:-r, r:-r]).max() <= 1e-12
+    assert np.abs(oracle.smooth(ramp, 0.0) - ramp).max() == 0.0
+
+
+def test_smooth_transpose_is_adjoint(oracle):
+    """<S a, b> = <a, S^T b>."""
+    rng = np.random.default_rng(6)
+    a, b = rng.standard_normal((2, 17, 23))
+    lhs = np.sum(oracle.smooth(a, 1.1) * b)
+    rhs = np.sum(a * oracle.smooth_transpose(b, 1.1))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
 
 def test_partition_ratio_worked_example():
     """Fig. ratio: 48x48 grid, twelve parts."""
