@@ -239,6 +239,20 @@ of_status of_residual_noalloc(int W, int H, const double *f1, const double *f2, 
                               double lambda, const double *U, double *r, double *norms, void *cuda_stream);
 
 /* Releases the workspace and the handle (NULL is accepted). */
+/* Upper bound of every device wait (the preconditioner's TMA staging
+ * barriers), in SM clock cycles [4e9, about 2 s].  A wait that runs out sets a
+ * device error word; the kernel stops staging, still completes, and the call
+ * returns OF_ERR_TIMEOUT with the handle usable.  cycles <= 0 restores the
+ * default. */
+of_status of_set_wait_limit(of_handle h, int64_t cycles);
+
+/* Test hook for that failure path; no counterpart in the paper.  With
+ * extra_bytes > 0 (a multiple of 16, at most 4096) every staging barrier of
+ * the preconditioner expects that many bytes more than its copies deliver:
+ * the copies complete, the barrier never does, and each wait runs out after
+ * the wait limit.  0 turns it off. */
+of_status of_debug_starve_staging(of_handle h, int extra_bytes);
+
 of_status of_destroy(of_handle h);
 
 /* Message for the last non-OK status of h (or of a failed of_create when h

@@ -19,6 +19,8 @@
 using ofk::PairDesc;
 using ofk::PairScalars;
 
+constexpr long long kDefaultWaitLimit = 4000000000LL;  // about 2 s at 2 GHz
+
 struct of_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -49,6 +51,8 @@ struct of_ctx {
     // inner PCG loop as a CUDA graph: while(any pair iterating) { apply; Schwarz }
     cudaGraph_t loop_graph = nullptr;
     cudaGraphExec_t loop_exec = nullptr;
+    long long spin_limit = kDefaultWaitLimit;  // bound of every device wait, clock64 cycles
+    int starve_bytes = 0;                      // test hook: staging waits expect this much more
     cudaGraphConditionalHandle loop_cond = 0;
     PairScalars* sc_dev = nullptr;
     PairScalars* sc_host = nullptr;  // pinned
@@ -240,7 +244,8 @@ ofl::SolveBufs solve_bufs(of_ctx* h) {
     B.omega = h->opts.omega;
     B.gms = h->opts.model == OF_MODEL_CONSTANT ? 0.0 : 1.0;
     B.fp64 = h->fp64;
-    B.spin_limit = 4000000000LL;  // ~2 s at 2 GHz
+    B.spin_limit = h->spin_limit;
+    B.tx_extra = h->starve_bytes;
     return B;
 }
 
@@ -406,6 +411,18 @@ bool build_loop_graph(of_ctx* h) {
     return true;
 }
 
+// The loop graph captures the kernels' parameters: rebuild it after they change.
+of_status rebuild_loop_graph(of_ctx* h) {
+    if (!h->loop_exec) return OF_OK;  // no grid yet, or the host loop is in use
+    CK(cudaStreamSynchronize(h->stream));
+    cudaGraphExecDestroy(h->loop_exec);
+    cudaGraphDestroy(h->loop_graph);
+    h->loop_exec = nullptr;
+    h->loop_graph = nullptr;
+    build_loop_graph(h);  // on failure the solve polls from the host
+    return OF_OK;
+}
+
 // Recomputes the preconditioner's element records if frames or alpha changed.
 of_status refresh_cells(of_ctx* h) {
     if (!h->cells_dirty) return OF_OK;
@@ -437,6 +454,7 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
     CK(cudaMemsetAsync(h->cntA, 0, sizeof(unsigned) * h->batch, st));
     CK(cudaMemsetAsync(h->cntS, 0, sizeof(unsigned) * h->batch, st));
     CK(cudaMemsetAsync(h->sc_dev, 0, sizeof(PairScalars) * h->batch, st));
+    CK(cudaMemsetAsync(h->err_dev, 0, sizeof(int), st));
     for (int pass = 0;; ++pass) {
         const int first = (pass == 0);
         double* xout = first ? nullptr : h->x[1 - cur];
@@ -472,9 +490,15 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
                 CK(cudaStreamSynchronize(st));
                 all_done = true;
                 for (int p = 0; p < h->batch; ++p) all_done = all_done && h->sc_host[p].done;
+                int errc = 0;  // a bounded wait ran out: stop launching
+                CK(cudaMemcpy(&errc, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+                if (errc) all_done = true;
                 if (it >= o.max_inner + chunk) all_done = true;
             }
         }
+        int errp = 0;  // a bounded wait ran out in this pass: no further launches
+        CK(cudaMemcpy(&errp, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+        if (errp) break;
         bool all_conv = true;
         for (int p = 0; p < h->batch; ++p) {
             const bool conv = h->sc_host[p].pad[0] != 0;
@@ -980,6 +1004,7 @@ of_status of_precondition(of_handle h, int pair, const void* r, void* z, of_dtyp
     s = refresh_cells(h);
     if (s != OF_OK) return s;
     ofl::SolveBufs B = solve_bufs(h);
+    CK(cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
     CK(ofl::launch_precond_only(B, h->tile0[pair], h->ntile[pair], h->stream));
     s = copy_out(h, (char*)h->z + d.vec_off * es, h->fp64 ? ofl::T_F64 : ofl::T_F32, d.pitch, z, dt, 3LL * d.H, d.W);
     if (s != OF_OK) return s;
@@ -1031,6 +1056,22 @@ of_status of_get_profile(of_handle h, of_profile* out) {
     *out = h->ptot;
     h->ptot = of_profile{};
     return OF_OK;
+}
+
+of_status of_set_wait_limit(of_handle h, int64_t cycles) {
+    if (!h) return OF_ERR_ARG;
+    DevGuard g(h->device);
+    h->spin_limit = cycles > 0 ? (long long)cycles : kDefaultWaitLimit;
+    return rebuild_loop_graph(h);
+}
+
+of_status of_debug_starve_staging(of_handle h, int extra_bytes) {
+    if (!h) return OF_ERR_ARG;
+    if (extra_bytes < 0 || extra_bytes % 16 || extra_bytes > 4096)
+        return fail(h, OF_ERR_ARG, "extra_bytes must be a multiple of 16 in [0, 4096]");
+    DevGuard g(h->device);
+    h->starve_bytes = extra_bytes;
+    return rebuild_loop_graph(h);
 }
 
 of_status of_destroy(of_handle h) {

@@ -132,6 +132,7 @@ static SchwarzParams schwarz_params(const SolveBufs& B) {
     S.nstage = B.sch_nstage;
     S.spin_limit = B.spin_limit;
     S.use_cond = B.use_cond;
+    S.tx_extra = B.tx_extra;
     S.cond = B.cond;
     return S;
 }

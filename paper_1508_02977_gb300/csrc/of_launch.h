@@ -50,6 +50,7 @@ struct SolveBufs {
     int fp64;            // 1: everything FP64; 0: FP32 inner with FP64 residual
     long long spin_limit;
     int use_cond;        // Schwarz launches inside the inner-loop graph set its condition
+    int tx_extra;        // test hook: bytes the staging barriers expect beyond the copies
     cudaGraphConditionalHandle cond;
 };
 

@@ -82,6 +82,8 @@ struct SchwarzParams {
     int nstage;               // 2: the next item streams in during this one; 1: after it
     long long spin_limit;     // bounded mbarrier wait, in clock64 cycles
     int use_cond;             // launched in the inner-loop graph: set its while condition
+    int tx_extra;             // test hook (0 in use): bytes each staging barrier expects beyond its
+                              // copies, so that its bounded wait runs out
     cudaGraphConditionalHandle cond;
 };
 
@@ -531,7 +533,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         // stage's earlier generic-proxy accesses before the async-proxy writes
         bulk_wait_read();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&bars[s], 2 * box_c + box_rq + (need_q ? box_rq : 0u));
+        mbar_expect_tx(&bars[s], 2 * box_c + box_rq + (need_q ? box_rq : 0u) + (unsigned)P.tx_extra);
         const int cx = (x0 - cpad) * CellT<R>::units, cy = y0 - ov - 1;
         tma_load_2d(st + L.c0, tm + TM_C0, cx, cy, &bars[s]);
         tma_load_2d(st + L.c1, tm + TM_C1, cx, cy, &bars[s]);

@@ -69,6 +69,8 @@ _lib.of_set_frames.argtypes = [_h, ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.
 _lib.of_set_alpha.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_int]
 _lib.of_get_alpha.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_int]
 _lib.of_get_frames.argtypes = [_h, ctypes.c_int, _vp, _vp, ctypes.c_int]
+_lib.of_set_wait_limit.argtypes = [_h, ctypes.c_int64]
+_lib.of_debug_starve_staging.argtypes = [_h, ctypes.c_int]
 _lib.of_solve.argtypes = [_h, ctypes.POINTER(SolveOpts), ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(SolveInfo)]
 _lib.of_adapt_alpha.argtypes = [_h, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp), ctypes.c_int]
 _lib.of_adjoint.argtypes = [_h, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
@@ -89,7 +91,8 @@ for _f in ("of_create", "of_setup_grid", "of_set_frames", "of_set_alpha", "of_ge
 
 EXPORTS = ("of_create", "of_setup_grid", "of_set_frames", "of_get_frames", "of_set_alpha", "of_get_alpha", "of_solve",
            "of_adapt_alpha", "of_adjoint", "of_apply", "of_precondition", "of_residual", "of_set_profiling",
-           "of_get_profile", "of_residual_noalloc", "of_destroy", "of_last_error")
+           "of_get_profile", "of_residual_noalloc", "of_set_wait_limit", "of_debug_starve_staging", "of_destroy",
+           "of_last_error")
 
 
 class OFError(RuntimeError):
@@ -250,6 +253,17 @@ def of_residual(h, pair, U) -> float:
     rel = ctypes.c_double(0.0)
     _check(h, _lib.of_residual(h, int(pair), _vp(pu), dt, ctypes.byref(rel)))
     return float(rel.value)
+
+
+def of_set_wait_limit(h, cycles):
+    """Bound of every device wait in SM clock cycles (<= 0: the default)."""
+    return _check(h, _lib.of_set_wait_limit(h, int(cycles)))
+
+
+def of_debug_starve_staging(h, extra_bytes):
+    """Test hook: staging barriers expect extra_bytes more than delivered, so
+    their bounded waits run out (0: off)."""
+    return _check(h, _lib.of_debug_starve_staging(h, int(extra_bytes)))
 
 
 def of_set_profiling(h, on=True):

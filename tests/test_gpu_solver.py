@@ -631,6 +631,37 @@ def test_presmoothing_matches_oracle(S, oracle, prec, sigma):
         assert np.abs(got - want).max() <= tol * np.abs(want).max()
 
 
+# ------------------------------------------------------ failure path --
+
+@pytest.mark.parametrize("host_loop", [False, True])
+def test_bounded_wait_runs_out_and_handle_recovers(S, host_loop):
+    """A staging wait that cannot complete (the test hook makes every
+    preconditioner barrier expect 16 bytes more than its copies deliver) runs
+    out after the wait limit: the call returns OF_ERR_TIMEOUT quickly, the
+    context stays usable, and the same handle then solves normally."""
+    W, H = 200, 150
+    p = synth.texture(W, H)
+    h = handle(S, [(W, H)], tile=(48, 48), sweeps=2, omega=1.5, precision=S.OF_PREC_MIXED)
+    try:
+        S.of_set_frames(h, 0, dev(p.f1, torch.float32), dev(p.f2, torch.float32))
+        S.of_set_alpha(h, 0, None, p.alpha0)
+        U = torch.zeros(3, H, W, dtype=torch.float32, device="cuda")
+        S.of_set_wait_limit(h, 2_000_000)  # about 1 ms
+        S.of_debug_starve_staging(h, 16)
+        import time
+        t = time.perf_counter()
+        st, info = S.of_solve(h, [U], raise_on=False, host_loop=host_loop)
+        torch.cuda.synchronize()
+        assert st == S.OF_ERR_TIMEOUT
+        assert time.perf_counter() - t < 30.0
+        S.of_debug_starve_staging(h, 0)
+        S.of_set_wait_limit(h, 0)
+        st, info = S.of_solve(h, [U], host_loop=host_loop)
+        assert st == S.OF_OK and info[0]["rel_residual"] <= 1e-6
+    finally:
+        S.of_destroy(h)
+
+
 # ------------------------------------------------ brightness constancy --
 
 def test_constant_model_fp64_matches_oracle(S, oracle):
