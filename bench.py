@@ -321,6 +321,23 @@ def run_ours(args):
                 "rel_residual": infos[-1]["rel_residual"], "opts": {k: v for k, v in FP64_OPTS.items()}}
         S.of_destroy(h64)
 
+    # the model options built beyond the workload's configuration, on the same
+    # pair and step: brightness constancy (no illumination unknown) and K_sigma
+    # pre-smoothing (inside each step's of_set_frames)
+    variants = None
+    if args.variant_steps > 0:
+        variants = {}
+        for name, extra, frames in (("model_constant", dict(model=1), None),
+                                    ("sigma_1.5", dict(sigma=1.5), (f1, f2))):
+            hv = make(dict(WORKLOAD_OPTS, **extra))
+            step(hv, U, frames)
+            infos.clear()
+            msv = timed(lambda: step(hv, U, frames), args.variant_steps)
+            variants[name] = {"value": whole_job_value(px, ws, args.variant_steps, msv), "unit": UNIT,
+                              "ms_per_step": msv / args.variant_steps, "inner_iters": infos[-1]["inner_iters"],
+                              "rel_residual": infos[-1]["rel_residual"], "opts": extra}
+            S.of_destroy(hv)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
@@ -344,7 +361,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (no flush)",
                        "inner_iters": iters, "rel_residual_max": relres},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "fp64_gpu": fp64,
+            "clocks": clocks, "fp64_gpu": fp64, "variants": variants,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -361,6 +378,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--variant-steps", type=int, default=5, help="steps per model variant (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-w", type=int, default=960)
     ap.add_argument("--cpu-sample-h", type=int, default=540)
