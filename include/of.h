@@ -97,6 +97,11 @@ typedef struct {
                                 Gaussian of radius ceil(3 sigma) along x then y, each pass normalised
                                 over the taps inside the image */
     of_model model;          /* [OF_MODEL_ILLUMINATION] */
+    int coarse;              /* two-level preconditioner: spacing in nodes of a coarse grid (nodes at
+                                0, s, 2s, ... and W-1, likewise in y) whose bilinear hat functions add
+                                the correction R0^T (R0 A R0^T)^{-1} R0 r to the Schwarz sweeps; at most
+                                8192 coarse unknowns per pair and 74 coarse nodes across (FP64: 51)
+                                [0: one-level] */
 } of_grid_opts;
 
 /* Solve options.  A field left at 0 takes the default in brackets. */

@@ -278,6 +278,38 @@ class System:
                 z[idx[own3]] = zi.ravel()[own3]
         return z.reshape(3, H, W)
 
+    def coarse_restriction(self, spacing):
+        """R_0: bilinear hat functions of a coarse grid with nodes at
+        x = 0, s, 2s, ... and x = W - 1 (likewise in y), one per component;
+        rows ordered (component, coarse y, coarse x).  Returns a sparse
+        [3 nc, 3 W H] matrix."""
+        import scipy.sparse as sp
+        def hats(n):
+            xs = sorted(set(list(range(0, n, spacing)) + [n - 1]))
+            Hm = np.zeros((len(xs), n))
+            for k, c in enumerate(xs):
+                for x in range(n):
+                    if x == c:
+                        Hm[k, x] = 1.0
+                    elif k > 0 and xs[k - 1] < x < c:
+                        Hm[k, x] = (x - xs[k - 1]) / (c - xs[k - 1])
+                    elif k < len(xs) - 1 and c < x < xs[k + 1]:
+                        Hm[k, x] = (xs[k + 1] - x) / (xs[k + 1] - c)
+            return Hm
+        P = sp.csr_matrix(np.kron(hats(self.H), hats(self.W)))
+        return sp.block_diag([P, P, P]).tocsr()
+
+    def two_level(self, r, tile, overlap, sweeps, omega, spacing):
+        """Additive two-level preconditioner: the restricted Schwarz sweeps
+        (schwarz_sweeps) plus the coarse correction R_0^T A_0^{-1} R_0 r with
+        the Galerkin coarse operator A_0 = R_0 A R_0^T of the bilinear coarse
+        space (coarse_restriction)."""
+        R0 = self.coarse_restriction(spacing)
+        A0 = (R0 @ self._sparse() @ R0.T).toarray()
+        r = _c(r).ravel()
+        zc = R0.T @ np.linalg.solve(A0, R0 @ r)
+        return self.schwarz_sweeps(r, tile, overlap, sweeps, omega) + zc.reshape(3, self.H, self.W)
+
     def indicator(self, U):
         L = _load()
         eta = np.zeros((self.H - 1, self.W - 1, 2))

@@ -52,6 +52,10 @@ struct of_ctx {
     cudaGraph_t loop_graph = nullptr;
     cudaGraphExec_t loop_exec = nullptr;
     long long spin_limit = kDefaultWaitLimit;  // bound of every device wait, clock64 cycles
+    // two-level preconditioner (coarse space)
+    std::vector<ofl::CoarsePair> cps;
+    ofl::CoarseBufs coarse{};
+
     int starve_bytes = 0;                      // test hook: staging waits expect this much more
     cudaGraphConditionalHandle loop_cond = 0;
     PairScalars* sc_dev = nullptr;
@@ -129,6 +133,8 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 void free_all(of_ctx* h) {
+    h->coarse = ofl::CoarseBufs{};
+    h->cps.clear();
     if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
     if (h->loop_graph) cudaGraphDestroy(h->loop_graph);
     h->loop_exec = nullptr;
@@ -246,6 +252,7 @@ ofl::SolveBufs solve_bufs(of_ctx* h) {
     B.fp64 = h->fp64;
     B.spin_limit = h->spin_limit;
     B.tx_extra = h->starve_bytes;
+    B.coarse = h->coarse;
     return B;
 }
 
@@ -434,6 +441,24 @@ of_status refresh_cells(of_ctx* h) {
         count_other(h, 1);
         (void)rb;
     }
+    if (h->coarse.on) {
+        // A_0 = R_0 A R_0^T (dense, banded), its band Cholesky factor and the
+        // dense inverse
+        const size_t es = h->fp64 ? 8 : 4;
+        const ofl::CoarsePair& last = h->cps.back();
+        CK(cudaMemsetAsync(h->coarse.Amat, 0, (size_t)(last.moff + (long long)last.n0 * last.n0) * es, h->stream));
+        CK(ofl::launch_coarse_assemble(B, h->stream));
+        count_other(h, 2);
+        for (int p = 0; p < h->batch; ++p) {
+            CK(ofl::launch_coarse_factor(B, p, h->cps[p].n0, h->cps[p].nx, h->cps[p].moff, h->stream));
+            count_other(h, 3);
+        }
+        std::vector<int> info(h->batch);
+        CK(cudaMemcpyAsync(info.data(), h->coarse.info, sizeof(int) * info.size(), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (int v : info)
+            if (v != 0) return fail(h, OF_ERR_BREAKDOWN, "coarse operator not positive definite");
+    }
     h->cells_dirty = false;
     return OF_OK;
 }
@@ -593,6 +618,7 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     if (!(opt.omega > 0 && opt.omega < 2)) return fail(h, OF_ERR_ARG, "omega must be in (0, 2)");
     if (!(opt.sigma >= 0 && opt.sigma <= 16)) return fail(h, OF_ERR_ARG, "sigma must be in [0, 16]");
     if (opt.model != OF_MODEL_ILLUMINATION && opt.model != OF_MODEL_CONSTANT) return fail(h, OF_ERR_ARG, "bad model");
+    if (opt.coarse < 0 || (opt.coarse > 0 && opt.coarse < 4)) return fail(h, OF_ERR_ARG, "coarse spacing must be 0 or >= 4");
     if (opt.tile_x < 4 || opt.tile_y < 4 || opt.tile_x % 4 || opt.tile_y % 4 || opt.tile_x > 256 || opt.tile_y > 256)
         return fail(h, OF_ERR_ARG, "tile sizes must be multiples of 4 in [4, 256]");
     if (opt.overlap < 0 || opt.overlap > 32 || opt.sweeps < 0 || opt.sweeps > 64)
@@ -729,6 +755,89 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     h->sch_nstage = nstage;
     CK(ofl::schwarz_configure(fp64, sch_npt, opt.tile_x, opt.tile_y, opt.overlap, smem));
     h->sch_grid = ofl::schwarz_max_grid(fp64, sch_npt, opt.tile_x, opt.tile_y, opt.overlap, sch_threads, smem);
+    if (opt.coarse > 0 && opt.preconditioner == OF_PC_SCHWARZ) {
+        // coarse grid of every pair: nodes at 0, s, 2s, ... and W - 1 (same in y)
+        std::vector<ofl::CoarseCell> cells;
+        long long moff = 0, items = 0, boff = 0;
+        int voff = 0, max_n0 = 0, max_nx = 0;
+        h->cps.assign(batch, ofl::CoarsePair{});
+        for (int p = 0; p < batch; ++p) {
+            auto axis = [&](int n) {
+                std::vector<int> v;
+                for (int x = 0; x < n - 1; x += opt.coarse) v.push_back(x);
+                v.push_back(n - 1);
+                return v;
+            };
+            const std::vector<int> xs = axis(W[p]), ys = axis(H[p]);
+            ofl::CoarsePair& cp = h->cps[p];
+            cp.nx = (int)xs.size();
+            cp.ny = (int)ys.size();
+            cp.nc = cp.nx * cp.ny;
+            cp.n0 = 3 * cp.nc;
+            if (cp.n0 > 8192) return fail(h, OF_ERR_ARG, "coarse grid too fine: more than 8192 coarse unknowns per pair");
+            cp.moff = moff;
+            cp.boff = boff;
+            cp.voff = voff;
+            cp.cell0 = (int)cells.size();
+            for (int l = 0; l + 1 < cp.ny; ++l)
+                for (int k = 0; k + 1 < cp.nx; ++k) cells.push_back({p, k, l, xs[k], xs[k + 1], ys[l], ys[l + 1]});
+            moff += (long long)cp.n0 * cp.n0;
+            boff += (long long)cp.n0 * (3 * cp.nx + 6);
+            voff += cp.n0;
+            max_nx = std::max(max_nx, cp.nx);
+            items += (long long)cp.nc * 81;
+            max_n0 = std::max(max_n0, cp.n0);
+        }
+        ofl::CoarseBufs& C = h->coarse;
+        const size_t ces = fp64 ? 8 : 4;
+        ofl::CoarsePair* cps_dev = nullptr;
+        ofl::CoarseCell* cells_dev = nullptr;
+        CK(dalloc(h, &cps_dev, sizeof(ofl::CoarsePair) * batch));
+        CK(dalloc(h, &cells_dev, sizeof(ofl::CoarseCell) * cells.size()));
+        CK(cudaMemcpyAsync(cps_dev, h->cps.data(), sizeof(ofl::CoarsePair) * batch, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(cells_dev, cells.data(), sizeof(ofl::CoarseCell) * cells.size(), cudaMemcpyHostToDevice, st));
+        C.cps = cps_dev;
+        C.cells = cells_dev;
+        C.ncells = (int)cells.size();
+        C.scatter_items = items;
+        if (3 * max_nx + 6 > (fp64 ? 160 : 230))
+            return fail(h, OF_ERR_ARG, "coarse grid too wide: its band factorisation window does not fit in shared memory");
+        char* blk = nullptr;
+        char* Am = nullptr;
+        char* Ai = nullptr;
+        char* Lr = nullptr;
+        char* Lc = nullptr;
+        char* part = nullptr;
+        char* yv = nullptr;
+        CK(dalloc(h, &blk, cells.size() * 144 * ces));
+        CK(dalloc(h, &Am, (size_t)moff * ces));
+        CK(dalloc(h, &Ai, (size_t)moff * ces));
+        CK(dalloc(h, &Lr, (size_t)boff * ces));
+        CK(dalloc(h, &Lc, (size_t)boff * ces));
+        CK(dalloc(h, &C.info, sizeof(int) * batch));
+        CK(dalloc(h, &part, cells.size() * 12 * ces));
+        CK(dalloc(h, &yv, (size_t)voff * ces));
+        char* gv = nullptr;
+        CK(dalloc(h, &gv, (size_t)voff * ces));
+        C.g = gv;
+        C.total_n0 = voff;
+        CK(dalloc(h, &C.gy, sizeof(double) * voff));
+        CK(dalloc(h, &C.cnt, sizeof(unsigned)));
+        CK(cudaMemsetAsync(C.cnt, 0, sizeof(unsigned), st));
+        C.blk = blk;
+        C.Amat = Am;
+        C.Ainv = Ai;
+        C.Lr = Lr;
+        C.Lc = Lc;
+        C.part = part;
+        C.y = yv;
+        C.max_n0 = max_n0;
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        C.gemv_grid = std::max(1, std::min(2 * sms, (max_n0 + 7) / 8));
+        CK(ofl::coarse_configure(fp64, max_n0, max_nx));
+        C.on = 1;
+    }
     h->cells_dirty = true;
     h->frames_set.assign(batch, 0);
     h->alpha_set.assign(batch, 0);
@@ -1005,7 +1114,7 @@ of_status of_precondition(of_handle h, int pair, const void* r, void* z, of_dtyp
     if (s != OF_OK) return s;
     ofl::SolveBufs B = solve_bufs(h);
     CK(cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
-    CK(ofl::launch_precond_only(B, h->tile0[pair], h->ntile[pair], h->stream));
+    CK(ofl::launch_precond_only(B, pair, h->tile0[pair], h->ntile[pair], h->stream));
     s = copy_out(h, (char*)h->z + d.vec_off * es, h->fp64 ? ofl::T_F64 : ofl::T_F32, d.pitch, z, dt, 3LL * d.H, d.W);
     if (s != OF_OK) return s;
     CK(cudaStreamSynchronize(h->stream));

@@ -234,10 +234,22 @@ static cudaError_t schwarz_launch(const SolveBufs& B, const SchwarzParams& S, in
     });
 }
 
+// Schwarz sweeps, then (two-level) the coarse correction, which finishes the
+// CG scalars and, inside the loop graph, sets its condition
+static cudaError_t precond(const SolveBufs& B, SchwarzParams S, int ntiles, int only_pair, cudaStream_t st) {
+    if (!B.coarse.on) return schwarz_launch(B, S, ntiles, st);
+    const int use_cond = S.use_cond;
+    S.defer = 1;
+    S.use_cond = 0;
+    cudaError_t e = schwarz_launch(B, S, ntiles, st);
+    if (e != cudaSuccess) return e;
+    return launch_coarse_apply(B, S.first, S.apply_only, use_cond, B.cond, only_pair, st);
+}
+
 cudaError_t launch_precond_first(const SolveBufs& B, cudaStream_t st) {
     SchwarzParams S = schwarz_params(B);
     S.first = 1;
-    return schwarz_launch(B, S, B.ntiles, st);
+    return precond(B, S, B.ntiles, -1, st);
 }
 
 template <typename R>
@@ -259,7 +271,7 @@ cudaError_t launch_pcg_apply(const SolveBufs& B, cudaStream_t st) {
 
 cudaError_t launch_pcg_precond(const SolveBufs& B, cudaStream_t st) {
     SchwarzParams S = schwarz_params(B);
-    return schwarz_launch(B, S, B.ntiles, st);
+    return precond(B, S, B.ntiles, -1, st);
 }
 
 template <typename R>
@@ -281,12 +293,12 @@ cudaError_t launch_apply(const SolveBufs& B, int pair, int blk0, int nblk, const
     return B.fp64 ? apply_t<double>(B, blk0, nblk, p, q, b, st) : apply_t<float>(B, blk0, nblk, p, q, b, st);
 }
 
-cudaError_t launch_precond_only(const SolveBufs& B, int tile0, int ntiles, cudaStream_t st) {
+cudaError_t launch_precond_only(const SolveBufs& B, int pair, int tile0, int ntiles, cudaStream_t st) {
     SchwarzParams S = schwarz_params(B);
     S.tiles = B.tiles + tile0;
     S.apply_only = 1;
     S.first = 1;
-    return schwarz_launch(B, S, ntiles, st);
+    return precond(B, S, ntiles, pair, st);
 }
 
 }  // namespace ofl

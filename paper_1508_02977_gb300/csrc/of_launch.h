@@ -20,6 +20,56 @@ cudaError_t copy2d(const void* src, int stype, long long spitch, void* dst, int 
 // Fill rows x cols of a strided array with a constant.
 cudaError_t fill2d(void* dst, int dtype, long long dpitch, long long rows, long long cols, double v, cudaStream_t st);
 
+// Coarse space of the two-level preconditioner (of_coarse.cu)
+struct CoarsePair {
+    int nx, ny;      // coarse nodes in x and y (x = 0, s, 2s, ..., W - 1)
+    int nc, n0;      // nodes, unknowns (3 nc, component-major)
+    long long moff;  // offset of the pair's dense n0 x n0 matrices
+    long long boff;  // offset of its band factors (n0 x (b+1), b = 3 nx + 5)
+    int voff;        // offset of the pair's coarse vectors
+    int cell0;       // first cell of the pair ((nx - 1) (ny - 1) cells, row-major)
+};
+struct CoarseCell {
+    int pair, k, l;        // cell (k, l) of the pair
+    int x0, x1, y0, y1;    // its corner coordinates (fine nodes)
+};
+struct CoarseBufs {
+    int on;                   // 0: one-level preconditioner
+    const CoarsePair* cps;    // [batch]
+    const CoarseCell* cells;  // [ncells]
+    int ncells;
+    long long scatter_items;  // work items of the dense scatter
+    void* blk;                // [ncells][144] cell blocks of A_0
+    void* Amat;               // dense A_0 (column-major, per pair; node-major unknowns)
+    void* Lr;                 // band Cholesky factor by rows and by columns
+    void* Lc;
+    int* info;                // [batch] factorisation status (0: positive definite)
+    void* Ainv;               // dense A_0^{-1}
+    void* part;               // [ncells][12] restriction partials
+    void* g;                  // R_0 r
+    void* y;                  // coarse correction
+    double* gy;               // g_i y_i per coarse unknown
+    int total_n0;             // coarse unknowns of the batch
+    unsigned* cnt;            // arrival counter of the product kernel
+    int max_n0, gemv_grid;
+};
+struct CoarseParams {
+    const ofk::PairDesc* pairs;
+    const CoarsePair* cps;
+    int npairs;
+    ofk::PairScalars* sc;
+    const double* tpart;   // Schwarz per-subdomain partials (r.r, r.z_1)
+    const void* Ainv;
+    const void* part;
+    void* g;
+    void* y;
+    double* gy;
+    unsigned* counter;
+    int* err;
+    int first, apply_only, use_cond, only_pair;
+    cudaGraphConditionalHandle cond;
+};
+
 struct SolveBufs {
     const ofk::PairDesc* pairs;
     const int4* blocks;
@@ -51,6 +101,7 @@ struct SolveBufs {
     long long spin_limit;
     int use_cond;        // Schwarz launches inside the inner-loop graph set its condition
     int tx_extra;        // test hook: bytes the staging barriers expect beyond the copies
+    CoarseBufs coarse;   // two-level preconditioner (coarse.on = 0: one level)
     cudaGraphConditionalHandle cond;
 };
 
@@ -71,7 +122,7 @@ cudaError_t launch_apply(const SolveBufs& B, int pair, int blk0, int nblk, const
                          cudaStream_t st);
 // Stand-alone preconditioner z = M r for one pair (tiles of that pair only);
 // r must already be in B.r.
-cudaError_t launch_precond_only(const SolveBufs& B, int tile0, int ntiles, cudaStream_t st);
+cudaError_t launch_precond_only(const SolveBufs& B, int pair, int tile0, int ntiles, cudaStream_t st);
 size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov, int nstage);
 // Cell records (element data of the preconditioner) of one pair, from the
 // frames and alpha in the workspace; c0, c1: [H][pitch] records.
@@ -101,6 +152,16 @@ struct AdaptBufs {
     int fp64;
 };
 cudaError_t launch_indicator(const AdaptBufs& A, int pair, int H, int W, cudaStream_t st);
+
+// two-level preconditioner: A_0 blocks and dense scatter, symmetrisation of
+// cuSOLVER's inverse, and one application z += R_0^T A_0^{-1} R_0 r (with the
+// CG scalars finished unless apply_only); only_pair >= 0 restricts it to one pair
+cudaError_t launch_coarse_assemble(const SolveBufs& B, cudaStream_t st);
+cudaError_t launch_symmetrize(void* A, int fp64, int n, cudaStream_t st);
+cudaError_t launch_coarse_apply(const SolveBufs& B, int first, int apply_only, int use_cond,
+                                cudaGraphConditionalHandle cond, int only_pair, cudaStream_t st);
+cudaError_t launch_coarse_factor(const SolveBufs& B, int pair, int n0, int nx, long long moff, cudaStream_t st);
+cudaError_t coarse_configure(int fp64, int max_n0, int max_nx);
 
 // K_sigma pre-smoothing: sampled Gaussian taps w_j of offsets j - r, j = 0..2r,
 // and the prefix sums cw[i] = w_0 + ... + w_{i-1}

@@ -82,6 +82,7 @@ struct SchwarzParams {
     int nstage;               // 2: the next item streams in during this one; 1: after it
     long long spin_limit;     // bounded mbarrier wait, in clock64 cycles
     int use_cond;             // launched in the inner-loop graph: set its while condition
+    int defer;                // two-level: leave the scalars to the coarse correction's kernel
     int tx_extra;             // test hook (0 in use): bytes each staging barrier expects beyond its
                               // copies, so that its bounded wait runs out
     cudaGraphConditionalHandle cond;
@@ -425,6 +426,29 @@ __device__ __forceinline__ double ordered_sum_rt(const double* p, int n, int str
     return block_sum_rt(s, sh);
 }
 
+
+// CG scalars of one pair after its preconditioned residual is complete:
+// t_rr = r.r, t_rz = r.z over the pair; first = start of a pass.
+__device__ __forceinline__ void precond_finalize(PairScalars* sp, double t_rr, double t_rz, int first) {
+    if (first) {
+        sp->rz = t_rz;
+        sp->rr = t_rr;
+        sp->beta = 0.0;
+        if (!isfinite(t_rr) || !isfinite(t_rz)) { sp->status = 6; sp->done = 1; }
+        else if (t_rr <= sp->tol2 || t_rr == 0.0) { sp->done = 1; }
+        else if (!(t_rz > 0.0)) { sp->status = 6; sp->done = 1; }
+    } else {
+        sp->beta = t_rz / sp->rz;
+        sp->rz = t_rz;
+        sp->rr = t_rr;
+        sp->it += 1;
+        sp->it_total += 1;
+        if (!isfinite(t_rr) || !isfinite(t_rz)) { sp->status = 6; sp->done = 1; }
+        else if (t_rr <= sp->tol2) { sp->done = 1; }
+        else if (!(t_rz > 0.0)) { sp->status = 6; sp->done = 1; }
+        else if (sp->it >= sp->max_it) { sp->status = 5; sp->done = 1; }
+    }
+}
 
 // Largest CTA the host may build a node table for (registers: the owned
 // nodes' blocks and right-hand sides live in registers).
@@ -770,7 +794,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         else if (t < P.ntiles && threadIdx.x == 0) issue(ti, 0);
     }
     if (threadIdx.x == 0) bulk_wait_all();  // the last stores have landed before the CTA leaves
-    if (P.apply_only) return;
+    if (P.apply_only || P.defer) return;    // defer: the coarse correction finishes the scalars
     // one arrival per CTA; the last CTA reduces the items of every pair that
     // took part, in item order (deterministic), and updates its scalars
     if (!arrive_last(P.counter, gridDim.x, &sh_last)) return;
@@ -781,26 +805,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         const int ntp = pd.tiles_x * pd.tiles_y;
         const double t_rr = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0, ntp, 2, sh_red);
         const double t_rz = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0 + 1, ntp, 2, sh_red);
-        if (threadIdx.x == 0) {
-            if (P.first) {
-                sp->rz = t_rz;
-                sp->rr = t_rr;
-                sp->beta = 0.0;
-                if (!isfinite(t_rr) || !isfinite(t_rz)) { sp->status = 6; sp->done = 1; }
-                else if (t_rr <= sp->tol2 || t_rr == 0.0) { sp->done = 1; }
-                else if (!(t_rz > 0.0)) { sp->status = 6; sp->done = 1; }
-            } else {
-                sp->beta = t_rz / sp->rz;
-                sp->rz = t_rz;
-                sp->rr = t_rr;
-                sp->it += 1;
-                sp->it_total += 1;
-                if (!isfinite(t_rr) || !isfinite(t_rz)) { sp->status = 6; sp->done = 1; }
-                else if (t_rr <= sp->tol2) { sp->done = 1; }
-                else if (!(t_rz > 0.0)) { sp->status = 6; sp->done = 1; }
-                else if (sp->it >= sp->max_it) { sp->status = 5; sp->done = 1; }
-            }
-        }
+        if (threadIdx.x == 0) precond_finalize(sp, t_rr, t_rz, P.first);
         __syncthreads();
     }
     if (threadIdx.x == 0) {

@@ -35,7 +35,7 @@ class GridOpts(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("overlap", ctypes.c_int),
                 ("sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("lam", ctypes.c_double),
                 ("preconditioner", ctypes.c_int), ("omega", ctypes.c_double), ("sigma", ctypes.c_double),
-                ("model", ctypes.c_int)]
+                ("model", ctypes.c_int), ("coarse", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -150,15 +150,16 @@ def of_create(device: int = 0, stream=None):
 
 
 def of_setup_grid(h, sizes, tile=(32, 32), overlap=0, sweeps=1, precision=OF_PREC_MIXED, lam=1.0,
-                  preconditioner=OF_PC_SCHWARZ, omega=1.0, sigma=0.0, model=0):
+                  preconditioner=OF_PC_SCHWARZ, omega=1.0, sigma=0.0, model=0, coarse=0):
     """sizes: list of (W, H); omega: relaxation factor of the local block SOR
     sweeps, in (0, 2); sigma: K_sigma pre-smoothing of the frames (0: none);
-    model: OF_MODEL_ILLUMINATION or OF_MODEL_CONSTANT."""
+    model: OF_MODEL_ILLUMINATION or OF_MODEL_CONSTANT; coarse: spacing of the
+    two-level preconditioner's coarse grid in nodes (0: one level)."""
     n = len(sizes)
     Wa = (ctypes.c_int32 * n)(*[int(w) for w, _ in sizes])
     Ha = (ctypes.c_int32 * n)(*[int(hh) for _, hh in sizes])
     o = GridOpts(int(tile[0]), int(tile[1]), int(overlap), int(sweeps), int(precision), float(lam), int(preconditioner),
-                 float(omega), float(sigma), int(model))
+                 float(omega), float(sigma), int(model), int(coarse))
     return _check(h, _lib.of_setup_grid(h, n, Wa, Ha, ctypes.byref(o)))
 
 

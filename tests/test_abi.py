@@ -48,8 +48,8 @@ def test_struct_layouts_match_header():
     # of_solve_opts: double, 3 ints, (pad), double, int (+ pad)
     assert ctypes.sizeof(S.GridOpts) == 64
     assert [getattr(S.GridOpts, f).offset for f in
-            ("tile_x", "sweeps", "precision", "lam", "preconditioner", "omega", "sigma", "model")] == \
-        [0, 12, 16, 24, 32, 40, 48, 56]
+            ("tile_x", "sweeps", "precision", "lam", "preconditioner", "omega", "sigma", "model", "coarse")] == \
+        [0, 12, 16, 24, 32, 40, 48, 56, 60]
     assert ctypes.sizeof(S.SolveOpts) == 40
     assert [getattr(S.SolveOpts, f).offset for f in
             ("rtol", "max_outer", "max_inner", "warm_start", "inner_rtol", "host_loop")] == [0, 8, 12, 16, 24, 32]

@@ -291,6 +291,46 @@ def test_sweep_preconditioner_symmetric_positive(oracle, sweeps, omega):
     assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
 
 
+def test_coarse_hats_partition_of_unity(oracle):
+    """The bilinear coarse functions sum to one at every fine node and are 1
+    at their own coarse node (ragged last cells included)."""
+    S = _small_system(oracle, 23, 17, 31)
+    R0 = S.coarse_restriction(5)
+    n = 23 * 17
+    ones = np.asarray(R0.T @ np.ones(R0.shape[0])).ravel()
+    assert np.abs(ones - 1.0).max() <= 1e-14
+    P = R0[: R0.shape[0] // 3, :n].toarray()
+    xs = sorted(set(list(range(0, 23, 5)) + [22]))
+    ys = sorted(set(list(range(0, 17, 5)) + [16]))
+    for l, y in enumerate(ys):
+        for k, x in enumerate(xs):
+            assert P[l * len(xs) + k, y * 23 + x] == 1.0
+
+
+def test_two_level_with_fine_coarse_grid_adds_the_exact_inverse(oracle):
+    """Coarse spacing 1 makes the coarse space the whole space (R_0 = I), so
+    the coarse correction is A^{-1} r (banded Cholesky)."""
+    S = _small_system(oracle, 9, 7, 32)
+    r = np.random.default_rng(33).standard_normal((3, 7, 9))
+    z = S.two_level(r, (4, 3), 0, 2, 1.4, 1)
+    assert np.abs(z - S.schwarz_sweeps(r, (4, 3), 0, 2, 1.4) - S.solve_with(r)).max() <= 1e-10 * np.abs(z).max()
+
+
+def test_two_level_symmetric_positive(oracle):
+    """The additive two-level preconditioner is symmetric positive definite
+    (column by column on an 11x9 grid, coarse spacing 4)."""
+    W, H = 11, 9
+    S = _small_system(oracle, W, H, 34)
+    n = 3 * W * H
+    M = np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = 1.0
+        M[:, k] = S.two_level(e.reshape(3, H, W), (4, 3), 0, 2, 1.5, 4).ravel()
+    assert np.abs(M - M.T).max() <= 1e-11 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
 def test_sweep_preconditioner_zero_sweeps_is_block_jacobi(oracle):
     """sweeps = 0: z_n = D_n^{-1} r_n with D_n the 3x3 diagonal block of the
     dense assembled matrix, whatever the tiling."""
