@@ -17,6 +17,8 @@
 // All sums run in a fixed order: the results do not depend on scheduling.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "of_common.cuh"
 #include "of_launch.h"
 #include "of_schwarz.cuh"
@@ -24,6 +26,8 @@
 namespace ofl {
 
 using namespace ofk;
+
+constexpr size_t kMaxSmem = 227 * 1024;  // opt-in shared memory per CTA
 
 // hat weights of node (x, y) inside cell [x0, x1] x [y0, y1]: corners
 // a = 0 (x0, y0), 1 (x1, y0), 2 (x0, y1), 3 (x1, y1)
@@ -213,7 +217,6 @@ __global__ void __launch_bounds__(1024) k_band_cholesky(const CoarsePair* cps, i
     };
     R nxt = fetch(0);
     __syncthreads();
-    // thread map of the trailing update: 8 threads per row offset a, columns c = 1 + t8 + 8 q
     const int ua = 1 + ((int)threadIdx.x >> 3), t8 = (int)threadIdx.x & 7;
     int sj = 0;  // j mod w
     for (int j = 0; j < n; ++j) {
@@ -237,6 +240,13 @@ __global__ void __launch_bounds__(1024) k_band_cholesky(const CoarsePair* cps, i
         const R cur = nxt;
         if (j + 1 < n) nxt = fetch(j + 1);
         __syncthreads();
+        // slot sj (row j, no longer read) takes row j + w: columns j+1 .. j+w; the
+        // update below touches rows j+1 .. j+m only
+        if ((int)threadIdx.x < w) {
+            int rc = sj + 1 + (int)threadIdx.x;
+            if (rc >= w) rc -= w;
+            Wn[sj * w + rc] = cur;
+        }
         for (int a = ua; a <= m; a += (int)(blockDim.x >> 3)) {
             int ra = sj + a;
             if (ra >= w) ra -= w;
@@ -248,116 +258,386 @@ __global__ void __launch_bounds__(1024) k_band_cholesky(const CoarsePair* cps, i
             }
         }
         __syncthreads();
-        // slot sj now takes row j + w: columns j+1 .. j+w
-        if ((int)threadIdx.x < w) {
-            int rc = sj + 1 + (int)threadIdx.x;
-            if (rc >= w) rc -= w;
-            Wn[sj * w + rc] = cur;
-        }
-        __syncthreads();
         if (++sj == w) sj = 0;
     }
     if (threadIdx.x == 0 && !bad) info[pair] = 0;
 }
 
-// Dense inverse X = A_0^{-1} = L^{-T} L^{-1}, one warp per column i:
-// forward L y = e_i (y_k = 0 for k < i), backward L^T x = y.  The last b+1
-// values of the running solution stay in a per-warp ring in shared memory;
-// each lane holds up to NPL factor entries of a row, and the next row's are
-// loaded while the current one is reduced.
+// Blocked band Cholesky (right-looking, panels of CB_NB = 32 columns), used
+// whenever its window fits in shared memory.  The window W holds rows and
+// columns J .. J+S-1 (S = 32 + b rounded up to 4) at slots g mod S (row
+// stride S + 1: column reads are free of bank conflicts).  Per panel
+// J .. J+31, held as P[k][r] = entry (J + r, J + k):
+//  1. warp 0 factors the 32 x 32 diagonal block (a pivot, a scaled column
+//     and a rank-1 update per column, lane r = row r); then every row below
+//     it solves against that block (L21 = A21 L11^{-T}) on its own;
+//  2. the L entries are written out (column band layout; the row layout is
+//     filled from it afterwards by k_band_rows);
+//  3. rank-32 update of the trailing b x b triangle, one 4 x 4 tile of
+//     products per thread; then the 32 rows that enter the window (read from
+//     the symmetric matrix at the start of the panel) are stored.
+// Shared-memory read-modify-write loops load a chunk of 8 before they store
+// it (the compiler cannot move a load above a store to the same array) and
+// are not unrolled further: fully unrolled panels overflow the instruction
+// cache, and register rows with compare-and-select indexing were slower.
+constexpr int CB_NB = 32;
+constexpr int CB_EN = 12;     // entering-row values per thread
+constexpr int CB_MAXT = 640;  // threads (launch bound): 32 S <= CB_EN CB_MAXT for S <= 224
+__host__ __device__ constexpr int cb_window(int b) { return CB_NB + ((b + 3) / 4) * 4; }
+__host__ __device__ constexpr long long cb_smem_elems(int b) {
+    return (long long)cb_window(b) * (cb_window(b) + 1) + (long long)CB_NB * cb_window(b) + 1;
+}
+static int cb_threads(int b) {
+    const int S = cb_window(b), tb = (b + 3) / 4;
+    int t = std::max(std::max(tb * (tb + 1) / 2, S), (CB_NB * S + CB_EN - 1) / CB_EN);
+    t = (t + 31) / 32 * 32;
+    return std::min(t, CB_MAXT);
+}
+
 template <typename R>
-__global__ void __launch_bounds__(256) k_band_inverse(const CoarsePair* cps, int pair, int b,
-                                                      const R* __restrict__ Lr, const R* __restrict__ Lc,
-                                                      R* __restrict__ X) {
-    constexpr int NPL = 8;  // b + 1 <= 32 NPL
-    extern __shared__ __align__(16) unsigned char rsm[];
-    const int w = b + 1, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    R* ring = reinterpret_cast<R*>(rsm) + (size_t)warp * w;
-    const CoarsePair cp = cps[pair];
-    const int n = cp.n0;
-    const int i = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (i >= n) return;
-    const R* Lrp = Lr + cp.boff;
-    const R* Lcp = Lc + cp.boff;
-    R* xcol = X + cp.moff + (long long)i * n;
-    for (int t = lane; t < w; t += 32) ring[t] = R(0);
-    __syncwarp();
-    // forward, row r: entries L[r][r-o], o = 1..min(b, r-i) (offset o by lane l + 32 q)
-    R cur[NPL], nxt[NPL];
-    auto load_f = [&](int r, R (&dst)[NPL]) {
-#pragma unroll
-        for (int q = 0; q < NPL; ++q) {
-            const int o = 1 + lane + 32 * q;
-            dst[q] = (r < n && o <= b && o <= r - i) ? Lrp[(long long)r * w + o] : R(0);
-        }
-    };
-    load_f(i, cur);
-    R diag = Lrp[(long long)i * w];
-    int rm = i % w;  // r mod w
-    for (int r = i; r < n; ++r) {
-        const R dnext = (r + 1 < n) ? Lrp[(long long)(r + 1) * w] : R(1);
-        load_f(r + 1, nxt);
-        R s = R(0);
-#pragma unroll
-        for (int q = 0; q < NPL; ++q) {
-            const int o = 1 + lane + 32 * q;
-            if (o <= b && o <= r - i) {
-                int sl = rm - o;
-                if (sl < 0) sl += w;
-                s += cur[q] * ring[sl];
-            }
-        }
-        s = warp_sum(s);
-        const R yr = ((r == i ? R(1) : R(0)) - s) / diag;
-        __syncwarp();
-        if (lane == 0) { ring[rm] = yr; xcol[r] = yr; }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < NPL; ++q) cur[q] = nxt[q];
-        diag = dnext;
-        if (++rm == w) rm = 0;
-    }
-    for (int t = lane; t < i; t += 32) xcol[t] = R(0);
-    for (int t = lane; t < w; t += 32) ring[t] = R(0);
-    __syncwarp();
-    // backward, row r: entries L[r+o][r], o = 1..min(b, n-1-r)
-    auto load_b = [&](int r, R (&dst)[NPL]) {
-#pragma unroll
-        for (int q = 0; q < NPL; ++q) {
-            const int o = 1 + lane + 32 * q;
-            dst[q] = (r >= 0 && o <= b && r + o < n) ? Lcp[(long long)r * w + o] : R(0);
-        }
-    };
-    load_b(n - 1, cur);
-    diag = Lcp[(long long)(n - 1) * w];
-    rm = (n - 1) % w;
-    for (int r = n - 1; r >= 0; --r) {
-        const R dnext = (r > 0) ? Lcp[(long long)(r - 1) * w] : R(1);
-        load_b(r - 1, nxt);
-        R s = R(0);
-#pragma unroll
-        for (int q = 0; q < NPL; ++q) {
-            const int o = 1 + lane + 32 * q;
-            if (o <= b && r + o < n) {
-                int sl = rm + o;
-                if (sl >= w) sl -= w;
-                s += cur[q] * ring[sl];
-            }
-        }
-        s = warp_sum(s);
-        const R xr = (xcol[r] - s) / diag;
-        __syncwarp();
-        if (lane == 0) { ring[rm] = xr; xcol[r] = xr; }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < NPL; ++q) cur[q] = nxt[q];
-        diag = dnext;
-        if (--rm < 0) rm = w - 1;
+__device__ __forceinline__ void load4(const R* p, R (&v)[4]) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[3];
     }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(CB_MAXT) k_band_cholesky_blk(const CoarsePair* cps, int pair, int b,
+                                                               const R* __restrict__ A, R* __restrict__ Lc,
+                                                               int* info) {
+    extern __shared__ __align__(16) unsigned char csm[];
+    const int S = cb_window(b), S1 = S + 1, w = b + 1, tb = (b + 3) / 4, ntiles = tb * (tb + 1) / 2;
+    R* P = reinterpret_cast<R*>(csm);  // [CB_NB][S] (first: 16-byte aligned rows)
+    R* W = P + (size_t)CB_NB * S;      // [S][S + 1]
+    R* flag = W + (size_t)S * S1;      // [1]: failure
+    const CoarsePair cp = cps[pair];
+    const int n = cp.n0;
+    const R* Ap = A + cp.moff;
+    R* Lcp = Lc + cp.boff;
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
+    for (int e = tid; e < S * S; e += nth) {
+        const int r = e / S, c = e - r * S;
+        W[r * S1 + c] = (r < n && c <= r && r - c <= b) ? Ap[(long long)r * n + c] : R(0);
+    }
+    __syncthreads();
+    int failed = 0;
+    for (int J = 0; J < n; J += CB_NB) {
+        const int nb = min(CB_NB, n - J);
+        const int base = J % S;
+        // the rows entering the window after this panel (g = J + S + q, columns
+        // J + 32 .. J + 32 + S - 1): loaded first, stored after the update
+        R ent[CB_EN];
+#pragma unroll
+        for (int k = 0; k < CB_EN; ++k) {
+            const int e = tid + k * nth;
+            ent[k] = R(0);
+            if (e < CB_NB * S) {
+                const int q = e / S, c = e - q * S;
+                const int g = J + S + q, cg = J + CB_NB + c;
+                if (g < n && cg <= g && g - cg <= b) ent[k] = Ap[(long long)g * n + cg];
+            }
+        }
+        // panel into P: P[k][r] = entry (J + r, J + k), zero outside the band and the matrix
+        for (int e = tid; e < CB_NB * S; e += nth) {
+            const int k = e / S, r = e - k * S;
+            int sr = base + r, sk = base + k;
+            if (sr >= S) sr -= S;
+            if (sk >= S) sk -= S;
+            P[e] = (k < nb && k <= r && J + r < n) ? W[sr * S1 + sk] : R(0);
+        }
+        __syncthreads();
+        // 1a. diagonal block, warp 0 (lane r = row r)
+        if (tid < 32) {
+            const int r = lane;
+            int badj = 0;
+            for (int jj = 0; jj < nb; ++jj) {
+                const R d = P[jj * S + jj];
+                if (!(d > R(0)) && !badj) badj = jj + 1;
+                const R l = d > R(0) ? sqrt(d) : R(1);
+                __syncwarp();
+                if (r == jj) P[jj * S + jj] = l;
+                else if (r > jj) P[jj * S + r] = P[jj * S + r] / l;
+                __syncwarp();
+                if (r > jj) {
+                    const R cj = P[jj * S + r];
+                    const int kmax = min(r, nb - 1);
+                    for (int k0 = jj + 1; k0 <= kmax; k0 += 8) {
+                        R a[8], q[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            if (k0 + u <= kmax) { a[u] = P[(k0 + u) * S + r]; q[u] = P[jj * S + k0 + u]; }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            if (k0 + u <= kmax) P[(k0 + u) * S + r] = a[u] - cj * q[u];
+                    }
+                }
+                __syncwarp();
+            }
+            if (lane == 0) flag[0] = (R)badj;
+        }
+        __syncthreads();
+        if (flag[0] != R(0)) {  // uniform
+            failed = J + (int)flag[0];
+            break;
+        }
+        // 1b. rows below the block, one per thread, column by column
+        for (int r = CB_NB + tid; r < S; r += nth) {
+            if (J + r >= n) continue;
+            for (int k = 0; k < nb; ++k) {
+                const R x = P[k * S + r] / P[k * S + k];
+                P[k * S + r] = x;
+                for (int m0 = k + 1; m0 < nb; m0 += 8) {
+                    R a[8], q[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (m0 + u < nb) { a[u] = P[(m0 + u) * S + r]; q[u] = P[k * S + m0 + u]; }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (m0 + u < nb) P[(m0 + u) * S + r] = a[u] - x * q[u];
+                }
+            }
+        }
+        __syncthreads();
+        // 2. L out: entry (J + r, J + k), r - k <= b
+        for (int k = tid >> 5; k < nb; k += nth >> 5)
+            for (int r = k + lane; r < S && r - k <= b && J + r < n; r += 32)
+                Lcp[(long long)(J + k) * w + (r - k)] = P[k * S + r];
+        // 3. trailing update of window rows/columns 32 .. S-1 (only when rows remain)
+        if (J + nb < n) {
+            for (int t = tid; t < ntiles; t += nth) {
+                int I = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+                while (I * (I + 1) / 2 > t) --I;
+                while ((I + 1) * (I + 2) / 2 <= t) ++I;
+                const int Jt = t - I * (I + 1) / 2;
+                const int r0 = CB_NB + 4 * I, c0 = CB_NB + 4 * Jt;
+                R acc[4][4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[x][y] = R(0);
+#pragma unroll 4
+                for (int k = 0; k < CB_NB; ++k) {
+                    R av[4], bv[4];
+                    load4<R>(P + k * S + r0, av);
+                    load4<R>(P + k * S + c0, bv);
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) acc[x][y] += av[x] * bv[y];
+                }
+                int sc = base + c0;
+                if (sc >= S) sc -= S;
+                int ro[4];
+                R old[4][4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    int sx = base + r0 + x;
+                    if (sx >= S) sx -= S;
+                    ro[x] = sx * S1 + sc;
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) old[x][y] = W[ro[x] + y];
+                }
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) W[ro[x] + y] = old[x][y] - acc[x][y];
+            }
+        }
+        // entering rows take the slots of rows J .. J+31
+#pragma unroll
+        for (int k = 0; k < CB_EN; ++k) {
+            const int e = tid + k * nth;
+            if (e < CB_NB * S) {
+                const int q = e / S, c = e - q * S;
+                int sg = base + q, sc = base + CB_NB + c;
+                if (sg >= S) sg -= S;
+                if (sc >= S) sc -= S;
+                if (sc >= S) sc -= S;
+                W[sg * S1 + sc] = ent[k];
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) info[pair] = failed;
+}
+
+// Row band layout from the column one: Lr[i w + t] = L[i][i-t] = Lc[(i-t) w + t].
+template <typename R>
+__global__ void k_band_rows(const CoarsePair* cps, int pair, int b, const R* __restrict__ Lc, R* __restrict__ Lr) {
+    const CoarsePair cp = cps[pair];
+    const int w = b + 1;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)cp.n0 * w) return;
+    const int i = (int)(e / w), t = (int)(e - (long long)i * w);
+    if (i - t >= 0) Lr[cp.boff + e] = Lc[cp.boff + (long long)(i - t) * w + t];
+}
+
+// Dense inverse X = A_0^{-1} = L^{-T} L^{-1}, one warp per column i:
+// forward L y = e_i, backward L^T x = y, both in blocks of 32 rows (lane t
+// <-> row t of the block).  The INV_WARPS columns of a CTA walk the same
+// blocks (the forward pass starts at the CTA's first column; rows above a
+// column's own index come out as exact zeros), so each block's factor rows
+// are staged once per CTA in shared memory by cp.async, one block ahead.
+// Per block and column:
+//  1. lane t sums the factor entries of its row that reach back before the
+//     block against a per-warp ring of the last b + 32 solution values;
+//  2. the 32 x 32 triangle inside the block: 31 dependent steps, each a
+//     shuffle broadcast of the newly final value and one FMA per lane.
+// Row stride of the staged block is a multiple of 32 words: lane t reads its
+// row at offsets t + 1 + m (step 1) and t - j (step 2), i.e. 32 distinct banks.
+constexpr int INV_WARPS = 8;
+__host__ __device__ constexpr int inv_row_stride(int w) { return ((w + 31) / 32) * 32; }
+__host__ __device__ constexpr int inv_smem_elems(int b) { return 2 * 32 * inv_row_stride(b + 1) + INV_WARPS * (b + 33); }
+
+template <typename R>
+__device__ __forceinline__ void cp_async_el(R* dst, const R* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (sizeof(R) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+
+// stage rows k = R0 + t (forward) or R0 - t (backward), t < nr, entries o <= omax(k)
+template <typename R, bool FWD>
+__device__ __forceinline__ void inv_stage(R* dst, const R* __restrict__ Lb, int w, int ws, int b, int n, int R0,
+                                          int nr) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = warp; t < 32; t += INV_WARPS) {
+        const int k = FWD ? R0 + t : R0 - t;
+        const int omax = t < nr ? (FWD ? min(b, k) : min(b, n - 1 - k)) : -1;
+        for (int o = lane; o < w; o += 32) {
+            const bool v = o <= omax;
+            cp_async_el<R>(dst + t * ws + o, v ? Lb + (long long)k * w + o : Lb, v);
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <typename R>
+__global__ void __launch_bounds__(INV_WARPS * 32) k_band_inverse(const CoarsePair* cps, int pair, int b,
+                                                                 const R* __restrict__ Lr, const R* __restrict__ Lc,
+                                                                 R* __restrict__ X) {
+    extern __shared__ __align__(16) unsigned char rsm[];
+    const int w = b + 1, ws = inv_row_stride(w), wr = b + 33, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    R* Lbuf = reinterpret_cast<R*>(rsm);                 // [2][32][ws]
+    R* ring = Lbuf + 2 * 32 * ws + (size_t)warp * wr;     // y_k at k mod wr
+    const CoarsePair cp = cps[pair];
+    const int n = cp.n0;
+    const int i0 = blockIdx.x * INV_WARPS, i = i0 + warp;
+    const bool col = i < n;
+    const R* Lrp = Lr + cp.boff;
+    const R* Lcp = Lc + cp.boff;
+    R* xcol = X + cp.moff + (long long)min(i, n - 1) * n;
+    const unsigned full = 0xffffffffu;
+    const int t = lane;
+    for (int u = lane; u < wr; u += 32) ring[u] = R(0);
+    if (col)
+        for (int u = lane; u < i0; u += 32) xcol[u] = R(0);
+    // ---- forward: row k = R0 + t, L[k][k - o] = Lr[k w + o]
+    int pb = i0 % wr;  // ring position of row R0
+    int buf = 0;
+    inv_stage<R, true>(Lbuf, Lrp, w, ws, b, n, i0, min(32, n - i0));
+    for (int R0 = i0; R0 < n; R0 += 32) {
+        const int nr = min(32, n - R0);
+        if (R0 + 32 < n) inv_stage<R, true>(Lbuf + (buf ^ 1) * 32 * ws, Lrp, w, ws, b, n, R0 + 32, min(32, n - R0 - 32));
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();
+        const R* Lt = Lbuf + buf * 32 * ws + t * ws;  // this lane's row
+        R rhs = R(0), invd = R(1);
+        if (t < nr) {
+            const int omax = min(b, R0 + t);
+            R part = R(0);
+            int pp = pb - 1;  // ring position of row R0 + t - o for o = t + 1
+            if (pp < 0) pp += wr;
+            for (int o = t + 1; o <= omax; ++o) {
+                part += Lt[o] * ring[pp];
+                if (--pp < 0) pp += wr;
+            }
+            rhs = (R0 + t == i ? R(1) : R(0)) - part;
+            invd = R(1) / Lt[0];
+        }
+        R c[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) c[j] = (t < nr && j < t && t - j <= b) ? Lt[t - j] : R(0);
+#pragma unroll
+        for (int j = 0; j < 31; ++j) {
+            const R yj = __shfl_sync(full, rhs * invd, j);
+            if (j < t) rhs -= c[j] * yj;
+        }
+        const R y = rhs * invd;
+        __syncwarp();
+        if (t < nr) {
+            int pp = pb + t;
+            if (pp >= wr) pp -= wr;
+            ring[pp] = y;
+            if (col) xcol[R0 + t] = y;
+        }
+        __syncthreads();  // ring and staged block consumed
+        pb += 32;
+        if (pb >= wr) pb -= wr;
+        buf ^= 1;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    for (int u = lane; u < wr; u += 32) ring[u] = R(0);
+    // ---- backward: row k = R0 - t, L[k + o][k] = Lc[k w + o]
+    pb = (n - 1) % wr;
+    buf = 0;
+    __syncthreads();
+    inv_stage<R, false>(Lbuf, Lcp, w, ws, b, n, n - 1, min(32, n));
+    for (int R0 = n - 1; R0 >= 0; R0 -= 32) {
+        const int nr = min(32, R0 + 1);
+        if (R0 - 32 >= 0) inv_stage<R, false>(Lbuf + (buf ^ 1) * 32 * ws, Lcp, w, ws, b, n, R0 - 32, min(32, R0 - 31));
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();
+        const R* Lt = Lbuf + buf * 32 * ws + t * ws;
+        R rhs = R(0), invd = R(1);
+        if (t < nr) {
+            const int k = R0 - t, omax = min(b, n - 1 - k);
+            R part = R(0);
+            int pp = pb - t + t + 1;  // ring position of row k + o for o = t + 1
+            if (pp >= wr) pp -= wr;
+            for (int o = t + 1; o <= omax; ++o) {
+                part += Lt[o] * ring[pp];
+                if (++pp >= wr) pp -= wr;
+            }
+            rhs = (col ? xcol[k] : R(0)) - part;
+            invd = R(1) / Lt[0];
+        }
+        R c[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) c[j] = (t < nr && j < t && t - j <= b) ? Lt[t - j] : R(0);
+#pragma unroll
+        for (int j = 0; j < 31; ++j) {
+            const R xj = __shfl_sync(full, rhs * invd, j);
+            if (j < t) rhs -= c[j] * xj;
+        }
+        const R x = rhs * invd;
+        __syncwarp();
+        if (t < nr) {
+            int pp = pb - t;
+            if (pp < 0) pp += wr;
+            ring[pp] = x;
+            if (col) xcol[R0 - t] = x;
+        }
+        __syncthreads();
+        pb -= 32;
+        if (pb < 0) pb += wr;
+        buf ^= 1;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // ---------------------------------------------------------- application --
-// g-partials of a cell: sum over its nodes of hat_a(node) r_c(node)
+// g-partials of a cell: sum over its nodes of hat_a(node) r_c(node).
+// One warp per row (rows strided by the warp count), lanes along x; the
+// hat factors separate, so a row contributes (1 - wy) S0, (1 - wy) S1,
+// wy S0, wy S1 with S0 = sum (1 - wx) r, S1 = sum wx r.
 template <typename R>
 __global__ void __launch_bounds__(256) k_coarse_restrict(const PairDesc* pairs, const CoarsePair* cps,
                                                          const CoarseCell* cells, const PairScalars* sc,
@@ -370,38 +650,31 @@ __global__ void __launch_bounds__(256) k_coarse_restrict(const PairDesc* pairs, 
     const PairDesc pd = pairs[c.pair];
     const CoarsePair cp = cps[c.pair];
     const long long plane = (long long)pd.H * pd.pitch;
-    const R* r = ra + pd.vec_off;
     int nx, ny;
     cell_nodes(c, cp, nx, ny);
+    const R ix = R(1) / R(c.x1 - c.x0), iy = R(1) / R(c.y1 - c.y0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     R acc[12];
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = R(0);
-    const int nn = nx * ny, step = blockDim.x;
-    for (int i0 = threadIdx.x; i0 < nn; i0 += 4 * step) {
-        R v[4][3];
-        long long oo[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {  // loads of four nodes first
-            const int i = i0 + u * step;
-            oo[u] = -1;
-            if (i < nn) {
-                const int x = c.x0 + i % nx, y = c.y0 + i / nx;
-                oo[u] = (long long)y * pd.pitch + x;
-                v[u][0] = r[oo[u]];
-                v[u][1] = r[oo[u] + plane];
-                v[u][2] = r[oo[u] + 2 * plane];
-            }
+    for (int yy = warp; yy < ny; yy += nw) {
+        const R* row = ra + pd.vec_off + (long long)(c.y0 + yy) * pd.pitch + c.x0;
+        R s0[3] = {R(0), R(0), R(0)}, s1[3] = {R(0), R(0), R(0)};
+#pragma unroll 4
+        for (int xx = lane; xx < nx; xx += 32) {
+            const R wx = R(xx) * ix;
+            const R v0 = row[xx], v1 = row[xx + plane], v2 = row[xx + 2 * plane];
+            s0[0] += (R(1) - wx) * v0; s1[0] += wx * v0;
+            s0[1] += (R(1) - wx) * v1; s1[1] += wx * v1;
+            s0[2] += (R(1) - wx) * v2; s1[2] += wx * v2;
         }
+        const R wy = R(yy) * iy;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u * step;
-            if (i >= nn) continue;
-            R ph[4];
-            cell_hats<R>(c.x0 + i % nx, c.y0 + i / nx, c, ph);
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int cc = 0; cc < 3; ++cc) acc[3 * a + cc] += ph[a] * v[u][cc];
+        for (int cc = 0; cc < 3; ++cc) {
+            acc[cc] += (R(1) - wy) * s0[cc];
+            acc[3 + cc] += (R(1) - wy) * s1[cc];
+            acc[6 + cc] += wy * s0[cc];
+            acc[9 + cc] += wy * s1[cc];
         }
     }
     block_sum_vec<R, 12>(acc, sh, res);
@@ -462,7 +735,20 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(const CoarseParams P) {
         for (int row = blockIdx.x * nw + warp; row < cp.n0; row += gridDim.x * nw) {
             const R* col = Ainv + cp.moff + (long long)row * cp.n0;  // symmetric: column = row
             R s = R(0);
-            for (int j = lane; j < cp.n0; j += 32) s += col[j] * gs[j];
+            if (sizeof(R) == 4 && (cp.n0 & 3) == 0 && (cp.moff & 3) == 0) {
+                // 16-byte loads, four partial sums per lane (fixed order)
+                const float4* c4 = reinterpret_cast<const float4*>(col);
+                const float4* g4 = reinterpret_cast<const float4*>(gs);
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 4
+                for (int j = lane; j < (cp.n0 >> 2); j += 32) {
+                    const float4 m = __ldg(c4 + j), q = g4[j];
+                    a0 += m.x * q.x; a1 += m.y * q.y; a2 += m.z * q.z; a3 += m.w * q.w;
+                }
+                s = (R)((a0 + a1) + (a2 + a3));
+            } else {
+                for (int j = lane; j < cp.n0; j += 32) s += col[j] * gs[j];
+            }
             s = warp_sum(s);
             if (lane == 0) {
                 yv[cp.voff + row] = s;
@@ -497,7 +783,8 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(const CoarseParams P) {
     }
 }
 
-// z += R_0^T y: bilinear interpolation of the coarse correction
+// z += R_0^T y: bilinear interpolation of the coarse correction, one warp
+// per row, lanes along x
 template <typename R>
 __global__ void __launch_bounds__(256) k_coarse_prolong(const PairDesc* pairs, const CoarsePair* cps,
                                                         const CoarseCell* cells, const PairScalars* sc,
@@ -508,7 +795,6 @@ __global__ void __launch_bounds__(256) k_coarse_prolong(const PairDesc* pairs, c
     const PairDesc pd = pairs[c.pair];
     const CoarsePair cp = cps[c.pair];
     const long long plane = (long long)pd.H * pd.pitch;
-    R* z = za + pd.vec_off;
     R yc[4][3];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -518,30 +804,24 @@ __global__ void __launch_bounds__(256) k_coarse_prolong(const PairDesc* pairs, c
     }
     int nx, ny;
     cell_nodes(c, cp, nx, ny);
-    const int nn = nx * ny, step = blockDim.x;
-    for (int i0 = threadIdx.x; i0 < nn; i0 += 4 * step) {
-        R zv[4][3];
-        long long oo[4];
+    const R ix = R(1) / R(c.x1 - c.x0), iy = R(1) / R(c.y1 - c.y0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int yy = warp; yy < ny; yy += nw) {
+        R* row = za + pd.vec_off + (long long)(c.y0 + yy) * pd.pitch + c.x0;
+        const R wy = R(yy) * iy;
+        R e0[3], e1[3];  // the coarse correction at the row's two cell edges
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {  // loads of four nodes first
-            const int i = i0 + u * step;
-            oo[u] = -1;
-            if (i < nn) {
-                oo[u] = (long long)(c.y0 + i / nx) * pd.pitch + (c.x0 + i % nx);
-#pragma unroll
-                for (int cc = 0; cc < 3; ++cc) zv[u][cc] = z[oo[u] + cc * plane];
-            }
+        for (int cc = 0; cc < 3; ++cc) {
+            e0[cc] = (R(1) - wy) * yc[0][cc] + wy * yc[2][cc];
+            e1[cc] = (R(1) - wy) * yc[1][cc] + wy * yc[3][cc];
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u * step;
-            if (i >= nn) continue;
-            R ph[4];
-            cell_hats<R>(c.x0 + i % nx, c.y0 + i / nx, c, ph);
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc)
-                z[oo[u] + cc * plane] =
-                    zv[u][cc] + (ph[0] * yc[0][cc] + ph[1] * yc[1][cc] + ph[2] * yc[2][cc] + ph[3] * yc[3][cc]);
+#pragma unroll 4
+        for (int xx = lane; xx < nx; xx += 32) {
+            const R wx = R(xx) * ix;
+            const R z0 = row[xx], z1 = row[xx + plane], z2 = row[xx + 2 * plane];
+            row[xx] = z0 + ((R(1) - wx) * e0[0] + wx * e1[0]);
+            row[xx + plane] = z1 + ((R(1) - wx) * e0[1] + wx * e1[1]);
+            row[xx + 2 * plane] = z2 + ((R(1) - wx) * e0[2] + wx * e1[2]);
         }
     }
 }
@@ -572,8 +852,21 @@ cudaError_t launch_coarse_factor(const SolveBufs& B, int pair, int n0, int nx, l
     const CoarseBufs& C = B.coarse;
     const int b = 3 * nx + 5, w = b + 1;
     const size_t es = B.fp64 ? 8 : 4;
-    const size_t smem_c = ((size_t)w * w + w) * es, smem_i = (size_t)8 * w * es;
-    if (B.fp64)
+    const size_t smem_c = ((size_t)w * w + w) * es, smem_i = (size_t)inv_smem_elems(b) * es;
+    const size_t smem_b = (size_t)cb_smem_elems(b) * es;
+    if (smem_b <= kMaxSmem) {
+        const int nt = cb_threads(b);
+        const unsigned gr = (unsigned)(((long long)n0 * w + 255) / 256);
+        if (B.fp64) {
+            k_band_cholesky_blk<double><<<1, nt, smem_b, st>>>(C.cps, pair, b, (const double*)C.Amat,
+                                                                (double*)C.Lc, C.info);
+            k_band_rows<double><<<gr, 256, 0, st>>>(C.cps, pair, b, (const double*)C.Lc, (double*)C.Lr);
+        } else {
+            k_band_cholesky_blk<float><<<1, nt, smem_b, st>>>(C.cps, pair, b, (const float*)C.Amat, (float*)C.Lc,
+                                                               C.info);
+            k_band_rows<float><<<gr, 256, 0, st>>>(C.cps, pair, b, (const float*)C.Lc, (float*)C.Lr);
+        }
+    } else if (B.fp64)
         k_band_cholesky<double><<<1, 1024, smem_c, st>>>(C.cps, pair, b, (const double*)C.Amat, (double*)C.Lr,
                                                          (double*)C.Lc, C.info);
     else
@@ -581,12 +874,12 @@ cudaError_t launch_coarse_factor(const SolveBufs& B, int pair, int n0, int nx, l
                                                         (float*)C.Lc, C.info);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const unsigned g = (unsigned)((n0 + 7) / 8);
+    const unsigned g = (unsigned)((n0 + INV_WARPS - 1) / INV_WARPS);
     if (B.fp64)
-        k_band_inverse<double><<<g, 256, smem_i, st>>>(C.cps, pair, b, (const double*)C.Lr, (const double*)C.Lc,
+        k_band_inverse<double><<<g, INV_WARPS * 32, smem_i, st>>>(C.cps, pair, b, (const double*)C.Lr, (const double*)C.Lc,
                                                        (double*)C.Ainv);
     else
-        k_band_inverse<float><<<g, 256, smem_i, st>>>(C.cps, pair, b, (const float*)C.Lr, (const float*)C.Lc,
+        k_band_inverse<float><<<g, INV_WARPS * 32, smem_i, st>>>(C.cps, pair, b, (const float*)C.Lr, (const float*)C.Lc,
                                                       (float*)C.Ainv);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -653,8 +946,14 @@ cudaError_t launch_coarse_apply(const SolveBufs& B, int first, int apply_only, i
 cudaError_t coarse_configure(int fp64, int max_n0, int max_nx) {
     const size_t es = fp64 ? 8 : 4;
     const int w = 3 * max_nx + 6;
-    const int s_gemv = (int)(max_n0 * es), s_chol = (int)(((size_t)w * w + w) * es), s_inv = (int)(8 * w * es);
+    const int s_gemv = (int)(max_n0 * es), s_chol = (int)(((size_t)w * w + w) * es), s_inv = (int)(inv_smem_elems(w - 1) * es);
     cudaError_t e = cudaSuccess;
+    const size_t s_blk = (size_t)cb_smem_elems(w - 1) * es;
+    if (s_blk <= kMaxSmem) {
+        e = fp64 ? cudaFuncSetAttribute(k_band_cholesky_blk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_blk)
+                 : cudaFuncSetAttribute(k_band_cholesky_blk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_blk);
+        if (e != cudaSuccess) return e;
+    }
     if (fp64) {
         e = cudaFuncSetAttribute(k_coarse_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s_gemv);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_band_cholesky<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s_chol);

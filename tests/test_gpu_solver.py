@@ -230,6 +230,35 @@ def test_two_level_preconditioner_matches_oracle(S, oracle, prec, tile, sw, om, 
     assert err <= (1e-9 if prec == 0 else 2e-2), err
 
 
+@pytest.mark.parametrize("prec,spacing", [(0, 10), (1, 6)])
+def test_two_level_wide_coarse_band(S, oracle, prec, spacing):
+    """A coarse grid 41 (FP64) or 68 (FP32) nodes wide: the band of A_0 is too
+    wide for the blocked factorisation's shared-memory window, so the
+    unblocked band Cholesky runs; z against the oracle as above."""
+    W, H = 400, 33
+    f1, f2 = synth.random_frames(W, H, 44)
+    alpha = synth.random_alpha(W, H, 45)
+    dt = torch.float64 if prec == 0 else torch.float32
+    if prec == 1:
+        f1, f2, alpha = f32(f1), f32(f2), f32(alpha)
+    sysm = oracle.System.from_frames(f1, f2, alpha, 1.0)
+    r = np.random.default_rng(46).standard_normal((3, H, W))
+    if prec == 1:
+        r = f32(r)
+    h = handle(S, [(W, H)], tile=(16, 16), sweeps=1, omega=1.0, precision=prec, coarse=spacing)
+    try:
+        S.of_set_frames(h, 0, dev(f1, dt), dev(f2, dt))
+        S.of_set_alpha(h, 0, dev(alpha, dt))
+        z = torch.zeros(3, H, W, dtype=dt, device="cuda")
+        S.of_precondition(h, 0, dev(r, dt), z)
+        z = z.cpu().numpy().astype(np.float64)
+    finally:
+        S.of_destroy(h)
+    want = sysm.two_level(r, (16, 16), 0, 1, 1.0, spacing)
+    err = np.abs(z - want).max() / np.abs(want).max()
+    assert err <= (1e-9 if prec == 0 else 2e-2), err
+
+
 def test_two_level_solves(S, oracle):
     """FP64 two-level solve of the blobs equals banded Cholesky to 1e-10; the
     FP32 path on the 640x480 texture reaches the residual target with fewer
