@@ -127,6 +127,29 @@ static void element_matrix(int t, const double g[3], double ft, double alpha, do
         }
 }
 
+/* Element matrix with a general symmetric data tensor (Section 1, the
+ * matrix A_rho and vector F with K_rho applied): the data block is
+ * |K|/12 (1+delta_ij) A_cd, the load |K|/3 F_c.  A6 = (A00, A01, A02, A11,
+ * A12, A22).  With A = g g^T and F = -ft g this is element_matrix. */
+static void element_matrix_el(int t, const double A6[6], const double F[3], double alpha, double lambda,
+                              double K[9][9], double bK[9])
+{
+    double gx[3], gy[3];
+    tri_grads(t, gx, gy);
+    const double Am[3][3] = {{A6[0], A6[1], A6[2]}, {A6[1], A6[3], A6[4]}, {A6[2], A6[4], A6[5]}};
+    double lam[3] = {alpha, alpha, lambda};
+    for (int i = 0; i < 3; i++)
+        for (int c = 0; c < 3; c++) {
+            for (int j = 0; j < 3; j++)
+                for (int d = 0; d < 3; d++) {
+                    double v = KAREA / 12.0 * (i == j ? 2.0 : 1.0) * Am[c][d];
+                    if (c == d) v += KAREA * lam[c] * (gx[i] * gx[j] + gy[i] * gy[j]);
+                    K[3 * i + c][3 * j + d] = v;
+                }
+            bK[3 * i + c] = KAREA / 3.0 * F[c];
+        }
+}
+
 /* ------------------------------------------------------------ assembly -- */
 
 /* Neighbour offsets of the 7-point pattern, in increasing linear order for a
@@ -194,6 +217,39 @@ int orc_assemble(int W, int H, const double *g, const double *ft, const double *
                     long e = elem_index(W, x, y, t);
                     double K[9][9], bK[9];
                     element_matrix(t, &g[3 * e], ft[e], alpha[e], lambda, K, bK);
+                    int vx[3], vy[3];
+                    tri_vertices(x, y, t, vx, vy);
+                    for (int i = 0; i < 3; i++)
+                        for (int c = 0; c < 3; c++) {
+                            int64_t r = c * N + (long)vy[i] * W + vx[i];
+                            b[r] += bK[3 * i + c];
+                            for (int j = 0; j < 3; j++)
+                                for (int d = 0; d < 3; d++)
+                                    bad += csr_add(rowptr, col, val, r, d * N + (long)vy[j] * W + vx[j],
+                                                   K[3 * i + c][3 * j + d]);
+                        }
+                }
+    }
+    return bad ? 2 : 0;
+}
+
+/* Assembly with general element data (K_rho > 0): Ael [H-1][W-1][2][6],
+ * Fel [H-1][W-1][2][3]; otherwise as orc_assemble. */
+int orc_assemble_el(int W, int H, const double *Ael, const double *Fel, const double *alpha, double lambda,
+                    const int64_t *rowptr, const int64_t *col, double *val, double *b)
+{
+    long N = (long)W * H;
+    memset(val, 0, sizeof(double) * rowptr[3 * N]);
+    memset(b, 0, sizeof(double) * 3 * N);
+    int bad = 0;
+    for (int parity = 0; parity < 2; parity++) {
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+        for (int y = parity; y < H - 1; y += 2)
+            for (int x = 0; x < W - 1; x++)
+                for (int t = 0; t < 2; t++) {
+                    long e = elem_index(W, x, y, t);
+                    double K[9][9], bK[9];
+                    element_matrix_el(t, &Ael[6 * e], &Fel[3 * e], alpha[e], lambda, K, bK);
                     int vx[3], vy[3];
                     tri_vertices(x, y, t, vx, vy);
                     for (int i = 0; i < 3; i++)
@@ -509,8 +565,8 @@ int orc_schwarz(int W, int H, const int64_t *rowptr, const int64_t *col, const d
  * elements of e, Lambda^{-1/2} applied per component inside the Euclidean
  * norm.  L2(K) by the edge-midpoint rule (exact for the quadratic
  * integrand); the jump is constant on e. */
-int orc_indicator(int W, int H, const double *g, const double *ft, const double *alpha, double lambda,
-                  const double *U, double *eta)
+static int indicator_impl(int W, int H, const double *g, const double *ft, const double *Ael, const double *Fel,
+                          const double *alpha, double lambda, const double *U, double *eta)
 {
     long N = (long)W * H;
     /* per-element flux gradients */
@@ -540,7 +596,7 @@ int orc_indicator(int W, int H, const double *g, const double *ft, const double 
         for (int x = 0; x < W - 1; x++)
             for (int t = 0; t < 2; t++) {
                 long e = elem_index(W, x, y, t);
-                const double *ge = &g[3 * e];
+                const double *ge = g ? &g[3 * e] : NULL;
                 double lamK[3] = {alpha[e], alpha[e], lambda};
                 int vx[3], vy[3];
                 tri_vertices(x, y, t, vx, vy);
@@ -549,15 +605,27 @@ int orc_indicator(int W, int H, const double *g, const double *ft, const double 
                 double integ = 0.0;
                 for (int a = 0; a < 3; a++) {
                     int bb = (a + 1) % 3;
-                    double s = ft[e];
-                    for (int c = 0; c < 3; c++) {
-                        double um = 0.5 * (U[c * N + (long)vy[a] * W + vx[a]] + U[c * N + (long)vy[bb] * W + vx[bb]]);
-                        s += ge[c] * um;
-                    }
+                    double um[3];
+                    for (int c = 0; c < 3; c++)
+                        um[c] = 0.5 * (U[c * N + (long)vy[a] * W + vx[a]] + U[c * N + (long)vy[bb] * W + vx[bb]]);
                     double q = 0.0;
-                    for (int c = 0; c < 3; c++) {
-                        double R = -ge[c] * s;
-                        q += R * R / lamK[c];
+                    if (!Ael) {
+                        /* R = F - A U = -g (g.U + ft) */
+                        double s = ft[e];
+                        for (int c = 0; c < 3; c++) s += ge[c] * um[c];
+                        for (int c = 0; c < 3; c++) {
+                            double R = -ge[c] * s;
+                            q += R * R / lamK[c];
+                        }
+                    } else {
+                        /* R = F - A U with the general element tensor */
+                        const double *A6 = &Ael[6 * e];
+                        const double Am[3][3] = {{A6[0], A6[1], A6[2]}, {A6[1], A6[3], A6[4]}, {A6[2], A6[4], A6[5]}};
+                        for (int c = 0; c < 3; c++) {
+                            double R = Fel[3 * e + c];
+                            for (int d = 0; d < 3; d++) R -= Am[c][d] * um[d];
+                            q += R * R / lamK[c];
+                        }
                     }
                     integ += KAREA / 3.0 * q;
                 }
@@ -595,6 +663,20 @@ int orc_indicator(int W, int H, const double *g, const double *ft, const double 
             }
     free(grad);
     return 0;
+}
+
+int orc_indicator(int W, int H, const double *g, const double *ft, const double *alpha, double lambda,
+                  const double *U, double *eta)
+{
+    return indicator_impl(W, H, g, ft, NULL, NULL, alpha, lambda, U, eta);
+}
+
+/* The indicator with general element data (K_rho > 0): the interior
+ * residual is F - A_rho U_h; the edge terms do not involve the data. */
+int orc_indicator_el(int W, int H, const double *Ael, const double *Fel, const double *alpha, double lambda,
+                     const double *U, double *eta)
+{
+    return indicator_impl(W, H, NULL, NULL, Ael, Fel, alpha, lambda, U, eta);
 }
 
 /* alpha update of Section 2.3:

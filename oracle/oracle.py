@@ -51,6 +51,7 @@ def _load():
         L.orc_csr_nnz.restype = i64
         L.orc_csr_pattern.argtypes = [i32, i32, _i64p, _i64p]
         L.orc_assemble.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _i64p, _i64p, _f64p, _f64p]
+        L.orc_assemble_el.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _i64p, _i64p, _f64p, _f64p]
         L.orc_csr_matvec.argtypes = [i64, _i64p, _i64p, _f64p, _f64p, _f64p]
         L.orc_csr_matvec.restype = None
         L.orc_apply_elementwise.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p, ctypes.c_void_p]
@@ -58,6 +59,7 @@ def _load():
         L.orc_pcg.argtypes = [i32, i32, _i64p, _i64p, _f64p, _f64p, _f64p, f64, i32, ctypes.POINTER(f64)]
         L.orc_schwarz.argtypes = [i32, i32, _i64p, _i64p, _f64p, _f64p, i32, i32, i32, i32, _f64p, ctypes.c_void_p]
         L.orc_indicator.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p]
+        L.orc_indicator_el.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p]
         L.orc_alpha_update.argtypes = [i64, _f64p, _f64p, f64, f64, f64]
         L.orc_adjoint_grad.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, i32]
@@ -94,14 +96,43 @@ def coefficients(f1, f2, model=0):
     return g, ft
 
 
+# index pairs (c, d) of the 6 stored entries of a symmetric 3x3 element tensor
+SYM6 = ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))
+
+
+def element_data(f1, f2, rho, model=0):
+    """Element tensor A_rho and load vector F of every element (Section 1:
+    the matrix A_rho and the vector F, whose entries are K_rho applied to
+    the products f_x^2, f_x f_y, -f_x f, ... and -f_x f_t, -f_y f_t, f f_t).
+    With g = (f_x, f_y, -f) this is A_rho = K_rho * (g g^T), F = K_rho * (-ft g).
+    K_rho is the normalised sampled Gaussian of `smooth` applied to each
+    product over the (W-1) x (H-1) lattice of one triangle family (t = 0 and
+    t = 1 separately).  Returns Ael [H-1][W-1][2][6] (entries SYM6) and
+    Fel [H-1][W-1][2][3]; rho = 0 gives g g^T and -ft g exactly."""
+    g, ft = coefficients(f1, f2, model)
+    Ael = np.stack([g[..., c] * g[..., d] for c, d in SYM6], axis=-1)
+    Fel = -ft[..., None] * g
+    if rho > 0:
+        for t in range(2):
+            for k in range(6):
+                Ael[:, :, t, k] = smooth(Ael[:, :, t, k], rho)
+            for k in range(3):
+                Fel[:, :, t, k] = smooth(Fel[:, :, t, k], rho)
+    return Ael, Fel
+
+
 class System:
     """The assembled FP64 system A U = b of one frame pair (CSR, [3][H][W]
-    unknown ordering)."""
+    unknown ordering).  With element tensors Ael, Fel (K_rho > 0) the data
+    term uses them in place of g g^T and -ft g; g, ft are still kept (the
+    preconditioner of the CUDA path is built from them)."""
 
-    def __init__(self, W, H, g, ft, alpha, lam):
+    def __init__(self, W, H, g, ft, alpha, lam, Ael=None, Fel=None):
         L = _load()
         self.W, self.H, self.lam = int(W), int(H), float(lam)
         self.g, self.ft, self.alpha = _c(g), _c(ft), _c(alpha)
+        self.Ael = None if Ael is None else _c(Ael)
+        self.Fel = None if Fel is None else _c(Fel)
         n = 3 * W * H
         nnz = int(L.orc_csr_nnz(W, H))
         self.rowptr = np.zeros(n + 1, dtype=np.int64)
@@ -109,19 +140,37 @@ class System:
         self.val = np.zeros(nnz)
         self.b = np.zeros(n)
         L.orc_csr_pattern(W, H, self.rowptr, self.col)
-        rc = L.orc_assemble(W, H, self.g, self.ft, self.alpha, self.lam, self.rowptr, self.col, self.val, self.b)
+        if self.Ael is None:
+            rc = L.orc_assemble(W, H, self.g, self.ft, self.alpha, self.lam, self.rowptr, self.col, self.val, self.b)
+        else:
+            rc = L.orc_assemble_el(W, H, self.Ael, self.Fel, self.alpha, self.lam, self.rowptr, self.col,
+                                   self.val, self.b)
         if rc:
             raise RuntimeError(f"oracle assembly failed ({rc})")
 
     @classmethod
-    def from_frames(cls, f1, f2, alpha, lam, model=0):
+    def from_frames(cls, f1, f2, alpha, lam, model=0, rho=0.0):
         f1 = _c(f1)
         H, W = f1.shape
         alpha = np.broadcast_to(np.asarray(alpha, dtype=np.float64), (H - 1, W - 1, 2))
         g, ft = coefficients(f1, f2, model)
-        S = cls(W, H, g, ft, alpha, lam)
+        if rho > 0:
+            Ael, Fel = element_data(f1, f2, rho, model)
+            S = cls(W, H, g, ft, alpha, lam, Ael, Fel)
+        else:
+            S = cls(W, H, g, ft, alpha, lam)
         S.model = int(model)
+        S.rho = float(rho)
         return S
+
+    def precond_system(self):
+        """The system whose Schwarz sweeps precondition this one on the CUDA
+        path: for K_rho > 0 the same stiffness with the unsmoothed data term
+        g g^T (an SPD operator close to A_rho; A_rho itself enters through
+        the operator only)."""
+        if self.Ael is None:
+            return self
+        return System(self.W, self.H, self.g, self.ft, self.alpha, self.lam)
 
     @property
     def n(self) -> int:
@@ -313,7 +362,10 @@ class System:
     def indicator(self, U):
         L = _load()
         eta = np.zeros((self.H - 1, self.W - 1, 2))
-        L.orc_indicator(self.W, self.H, self.g, self.ft, self.alpha, self.lam, _c(U).ravel(), eta)
+        if self.Ael is None:
+            L.orc_indicator(self.W, self.H, self.g, self.ft, self.alpha, self.lam, _c(U).ravel(), eta)
+        else:
+            L.orc_indicator_el(self.W, self.H, self.Ael, self.Fel, self.alpha, self.lam, _c(U).ravel(), eta)
         return eta
 
 
@@ -334,12 +386,14 @@ def _smooth_axis(A, axis, sigma, transpose=False):
     norm = np.zeros(n)
     for kk, wk in zip(k, w):
         lo, hi = max(0, -kk), min(n, n - kk)
-        norm[lo:hi] += wk
+        if hi > lo:  # a tap that reaches past the whole axis adds nothing
+            norm[lo:hi] += wk
     src = A / norm if transpose else A
     out = np.zeros_like(A)
     for kk, wk in zip(k, w):
         lo, hi = max(0, -kk), min(n, n - kk)
-        out[..., lo:hi] += wk * src[..., lo + kk:hi + kk]
+        if hi > lo:
+            out[..., lo:hi] += wk * src[..., lo + kk:hi + kk]
     if not transpose:
         out = out / norm
     return np.moveaxis(out, -1, axis)

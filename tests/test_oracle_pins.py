@@ -621,3 +621,157 @@ def test_metrics_closed_forms(oracle):
     U2 = np.zeros((3, 3, 4))
     U2[0] = 1.0
     assert abs(oracle.aae_deg(U2, gt) - 45.0) < 1e-12
+
+
+# ------------------------------------------------- K_rho element tensors --
+
+def _brute_rho(P, rho):
+    """2-D normalised Gaussian sum over one (H-1) x (W-1) element lattice,
+    written out directly (the K_rho of Section 1 on one triangle family)."""
+    Hh, Ww = P.shape
+    r = int(np.ceil(3 * rho))
+    out = np.zeros_like(P)
+    for y in range(Hh):
+        for x in range(Ww):
+            num = den = 0.0
+            for j in range(-r, r + 1):
+                for k in range(-r, r + 1):
+                    if 0 <= y + j < Hh and 0 <= x + k < Ww:
+                        w = np.exp(-(j * j + k * k) / (2 * rho * rho))
+                        num += w * P[y + j, x + k]
+                        den += w
+            out[y, x] = num / den
+    return out
+
+
+def test_element_tensor_is_smoothed_products(oracle):
+    """A_rho = K_rho * (g_c g_d), F = K_rho * (-ft g_c) (Section 1, matrix
+    A_rho and vector F) per triangle family, against products of the
+    independently formed element data and a brute-force 2-D Gaussian sum."""
+    W, H, rho = 9, 7, 1.2
+    f1, f2 = synth.random_frames(W, H, 61)
+    Ael, Fel = oracle.element_data(f1, f2, rho)
+    g = np.zeros((H - 1, W - 1, 2, 3))
+    ft = np.zeros((H - 1, W - 1, 2))
+    for x, y, t, verts in triangles(W, H):
+        g[y, x, t], ft[y, x, t] = element_data(f1, f2, verts)
+    for t in range(2):
+        for k, (c, d) in enumerate(oracle.SYM6):
+            want = _brute_rho(g[:, :, t, c] * g[:, :, t, d], rho)
+            assert np.abs(Ael[:, :, t, k] - want).max() <= 1e-14
+        for c in range(3):
+            want = _brute_rho(-ft[:, :, t] * g[:, :, t, c], rho)
+            assert np.abs(Fel[:, :, t, c] - want).max() <= 1e-14
+
+
+def test_element_tensor_limits(oracle):
+    """rho = 0 gives g g^T and -ft g exactly; a Gaussian far narrower than
+    the lattice (rho = 0.1: neighbour weight e^-50) the same to rounding;
+    a constant g (f1 constant, f2 affine) is left unchanged by K_rho; every
+    tensor is symmetric positive semidefinite."""
+    f1, f2 = synth.random_frames(8, 6, 62)
+    g, ft = oracle.coefficients(f1, f2)
+    A0, F0 = oracle.element_data(f1, f2, 0.0)
+    for k, (c, d) in enumerate(oracle.SYM6):
+        assert np.array_equal(A0[..., k], g[..., c] * g[..., d])
+    assert np.array_equal(F0, -ft[..., None] * g)
+    A1, F1 = oracle.element_data(f1, f2, 0.1)
+    assert np.abs(A1 - A0).max() <= 1e-15 * np.abs(A0).max()
+    assert np.abs(F1 - F0).max() <= 1e-15 * np.abs(F0).max()
+    ys, xs = np.mgrid[0:6, 0:8]
+    c1 = np.full((6, 8), 0.4)
+    c2 = 0.3 + 0.02 * xs - 0.05 * ys
+    Ac, Fc = oracle.element_data(c1, c2, 2.0)
+    gc = np.array([0.02, -0.05, -0.4])
+    ftc = (c2 - c1)  # varies: only the tensor is checked
+    for k, (c, d) in enumerate(oracle.SYM6):
+        assert np.abs(Ac[..., k] - gc[c] * gc[d]).max() <= 1e-15
+    A2, _ = oracle.element_data(f1, f2, 1.7)
+    M = np.zeros(A2.shape[:-1] + (3, 3))
+    for k, (c, d) in enumerate(oracle.SYM6):
+        M[..., c, d] = M[..., d, c] = A2[..., k]
+    ev = np.linalg.eigvalsh(M)
+    assert ev.min() >= -1e-15 * np.abs(ev).max()
+
+
+def test_general_operator_equals_weak_form(oracle):
+    """U^T A V and b^T V with the K_rho element tensors equal
+    int U_h^T A_rho V_h + stiffness and int F . V_h, by the 3-point rule."""
+    W, H, rho, lam = 5, 4, 1.3, 0.6
+    rng = np.random.default_rng(63)
+    f1, f2 = synth.random_frames(W, H, 64)
+    alpha = synth.random_alpha(W, H, 65)
+    S = oracle.System.from_frames(f1, f2, alpha, lam, rho=rho)
+    Ael, Fel = oracle.element_data(f1, f2, rho)
+    for _ in range(3):
+        U = rng.standard_normal((3, H, W))
+        V = rng.standard_normal((3, H, W))
+        a_uv = l_v = 0.0
+        for x, y, t, verts in triangles(W, H):
+            G, area = bary(verts)
+            M = np.zeros((3, 3))
+            for k, (c, d) in enumerate(oracle.SYM6):
+                M[c, d] = M[d, c] = Ael[y, x, t, k]
+            Fv = Fel[y, x, t]
+            Lam = np.array([alpha[y, x, t], alpha[y, x, t], lam])
+            uv = np.array([[U[c, yy, xx] for c in range(3)] for xx, yy in verts])
+            vv = np.array([[V[c, yy, xx] for c in range(3)] for xx, yy in verts])
+            for q in QPTS:
+                q = np.array(q)
+                a_uv += area / 3.0 * (q @ uv) @ M @ (q @ vv)
+                l_v += area / 3.0 * Fv @ (q @ vv)
+            for c in range(3):
+                a_uv += area * Lam[c] * (G.T @ uv[:, c]) @ (G.T @ vv[:, c])
+        assert abs(np.sum(V * S.matvec(U)) - a_uv) < 1e-12 * max(1.0, abs(a_uv))
+        assert abs(S.b @ V.ravel() - l_v) < 1e-13 * max(1.0, abs(l_v))
+
+
+def test_general_constant_solution_invariant(oracle):
+    """With F_K = A_K c for every element, U = c solves the system exactly
+    (the stiffness annihilates constants, the data blocks give |K|/3 A_K c)."""
+    W, H = 7, 5
+    f1, f2 = synth.random_frames(W, H, 66)
+    Ael, _ = oracle.element_data(f1, f2, 1.5)
+    cst = np.array([0.3, -0.2, 0.05])
+    M = np.zeros(Ael.shape[:-1] + (3, 3))
+    for k, (c, d) in enumerate(oracle.SYM6):
+        M[..., c, d] = M[..., d, c] = Ael[..., k]
+    Fel = M @ cst
+    g, ft = oracle.coefficients(f1, f2)
+    S = oracle.System(W, H, g, ft, synth.random_alpha(W, H, 67), 0.8, Ael, Fel)
+    U = S.solve_direct()
+    assert np.abs(U - cst[:, None, None]).max() <= 1e-11
+
+
+def test_general_indicator_reduces_and_closed_form(oracle):
+    """The indicator with element tensors equals the rank-1 one when
+    A = g g^T, F = -ft g; for U = 0 it is |Lambda^{-1/2} F| per element
+    (h_K |K|^{1/2} = 1 on these triangles, no flux jumps)."""
+    W, H = 6, 5
+    f1, f2 = synth.random_frames(W, H, 68)
+    alpha = synth.random_alpha(W, H, 69)
+    g, ft = oracle.coefficients(f1, f2)
+    A0, F0 = oracle.element_data(f1, f2, 0.0)
+    U = np.random.default_rng(70).standard_normal((3, H, W))
+    e1 = oracle.System(W, H, g, ft, alpha, 0.9).indicator(U)
+    e2 = oracle.System(W, H, g, ft, alpha, 0.9, A0, F0).indicator(U)
+    assert np.abs(e1 - e2).max() <= 1e-13 * np.abs(e1).max()
+    Ael, Fel = oracle.element_data(f1, f2, 1.4)
+    e0 = oracle.System(W, H, g, ft, alpha, 0.9, Ael, Fel).indicator(np.zeros((3, H, W)))
+    lamv = np.stack([alpha, alpha, np.full_like(alpha, 0.9)], axis=-1)
+    want = np.sqrt(np.sum(Fel ** 2 / lamv, axis=-1))
+    assert np.abs(e0 - want).max() <= 1e-14 * max(1.0, want.max())
+
+
+def test_smooth_taps_wider_than_image(oracle):
+    """A Gaussian whose taps reach past the whole image (radius 9 on a 5 x 4
+    image): still the 2-D normalised sum over the pixels inside."""
+    rng = np.random.default_rng(71)
+    I = rng.standard_normal((4, 5))
+    sigma = 3.0
+    want = np.zeros_like(I)
+    for y in range(4):
+        for x in range(5):
+            w = np.exp(-((np.arange(4)[:, None] - y) ** 2 + (np.arange(5)[None, :] - x) ** 2) / (2 * sigma ** 2))
+            want[y, x] = np.sum(w * I) / np.sum(w)
+    assert np.abs(oracle.smooth(I, sigma) - want).max() <= 1e-14
