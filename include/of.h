@@ -102,6 +102,13 @@ typedef struct {
                                 the correction R0^T (R0 A R0^T)^{-1} R0 r to the Schwarz sweeps; at most
                                 8192 coarse unknowns per pair and 74 coarse nodes across (FP64: 51)
                                 [0: one-level] */
+    double rho;              /* K_rho integration scale of the data term (Section 1: the matrix A_rho and
+                                vector F), 0 <= rho <= 16 [0: A = g g^T, F = -ft g per element]: each
+                                product g_c g_d and -ft g_c is smoothed over the lattice of its triangle
+                                family (t = 0 and t = 1 separately) by the sampled Gaussian of sigma's
+                                form, normalised inside the lattice.  The operator uses A_rho exactly; the
+                                Schwarz (and coarse) preconditioner is built from the unsmoothed g g^T.
+                                of_adjoint returns no frame gradients when rho > 0 */
 } of_grid_opts;
 
 /* Solve options.  A field left at 0 takes the default in brackets. */
@@ -148,6 +155,13 @@ of_status of_set_frames(of_handle h, int pair, const void *f1, const void *f2, o
  * as dense [H][W] arrays of dtype dt (host or device).  Returns OF_ERR_STATE
  * before of_set_frames. */
 of_status of_get_frames(of_handle h, int pair, void *f1, void *f2, of_dtype dt);
+
+/* Copies the element data of pair `pair` out as 18 dense [H-1][W-1] planes
+ * (dtype dt, host or device): plane t * 9 + k holds, for triangle family t,
+ * the entries 00, 01, 02, 11, 12, 22 of A_rho (k = 0..5) and F (k = 6..8).
+ * Returns OF_ERR_STATE when rho = 0 (no element data is stored) or before
+ * of_set_frames. */
+of_status of_get_element_data(of_handle h, int pair, void *out, of_dtype dt);
 
 /* Sets the per-element alpha of pair `pair` from `alpha` ([H-1][W-1][2],
  * dtype dt), or, if alpha is NULL, to the constant alpha_const (> 0). */

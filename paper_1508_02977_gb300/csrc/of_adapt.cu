@@ -47,7 +47,8 @@ __device__ __forceinline__ void tri_grad(int t, const R A[3], const R B[3], cons
 template <typename R, typename UT>
 __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict__ f1a, const R* __restrict__ f2a,
                             const R* __restrict__ ala, const UT* __restrict__ ua, R* __restrict__ etaa, double lam_d,
-                            double gms_d, unsigned long long* __restrict__ etamax_bits) {
+                            double gms_d, const R* __restrict__ eld, long long eld_stride,
+                            unsigned long long* __restrict__ etamax_bits) {
     const PairDesc pd = pairs[pair];
     const int W = pd.W, H = pd.H, pitch = pd.pitch;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -93,13 +94,31 @@ __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict
             // midpoints of the 3 edges: (A,V1), (V1,C), (C,A)
             R sm2 = R(0);
             const R* P0[3] = {uA, V1, uC};
-            for (int e = 0; e < 3; ++e) {
-                const R* Pa = P0[e];
-                const R* Pb = P0[(e + 1) % 3];
-                const R s = ft + R(0.5) * (g0 * (Pa[0] + Pb[0]) + g1 * (Pa[1] + Pb[1]) + g2 * (Pa[2] + Pb[2]));
-                sm2 += s * s;
+            R val;
+            if (!eld) {  // R = F - A U = -g (g.U + ft)
+                for (int e = 0; e < 3; ++e) {
+                    const R* Pa = P0[e];
+                    const R* Pb = P0[(e + 1) % 3];
+                    const R s = ft + R(0.5) * (g0 * (Pa[0] + Pb[0]) + g1 * (Pa[1] + Pb[1]) + g2 * (Pa[2] + Pb[2]));
+                    sm2 += s * s;
+                }
+                val = sq2 * sqrt(R(0.5) / R(3) * G * sm2);
+            } else {     // K_rho element data: R = F - A_rho U
+                const R* ep = eld + pd.frame_off + (long long)y * pitch + x + (long long)(9 * t) * eld_stride;
+                R a[6], fv[3];
+                for (int k = 0; k < 6; ++k) a[k] = ep[k * eld_stride];
+                for (int k = 0; k < 3; ++k) fv[k] = ep[(6 + k) * eld_stride];
+                for (int e = 0; e < 3; ++e) {
+                    const R* Pa = P0[e];
+                    const R* Pb = P0[(e + 1) % 3];
+                    const R m0 = R(0.5) * (Pa[0] + Pb[0]), m1 = R(0.5) * (Pa[1] + Pb[1]), m2 = R(0.5) * (Pa[2] + Pb[2]);
+                    const R r0 = fv[0] - (a[0] * m0 + a[1] * m1 + a[2] * m2);
+                    const R r1 = fv[1] - (a[1] * m0 + a[3] * m1 + a[4] * m2);
+                    const R r2 = fv[2] - (a[2] * m0 + a[4] * m1 + a[5] * m2);
+                    sm2 += (r0 * r0 + r1 * r1) * iLk[0] + r2 * r2 * iLk[2];
+                }
+                val = sq2 * sqrt(R(0.5) / R(3) * sm2);
             }
-            R val = sq2 * sqrt(R(0.5) / R(3) * G * sm2);
             // edges: normal, length, neighbour (square, t) or none
             for (int e = 0; e < 3; ++e) {
                 R nx, ny, he;
@@ -176,10 +195,12 @@ cudaError_t launch_indicator(const AdaptBufs& A, int pair, int H, int W, cudaStr
     if (A.fp64)
         k_indicator<double, double><<<grid, 128, 0, st>>>(A.pairs, pair, (const double*)A.f1, (const double*)A.f2,
                                                           (const double*)A.alpha, A.u, (double*)A.eta, A.lam, A.gms,
+                                                          (const double*)A.eld, A.eld_stride,
                                                           (unsigned long long*)A.etamax);
     else
         k_indicator<float, float><<<grid, 128, 0, st>>>(A.pairs, pair, (const float*)A.f1, (const float*)A.f2,
                                                         (const float*)A.alpha, A.u32, (float*)A.eta, A.lam, A.gms,
+                                                        (const float*)A.eld, A.eld_stride,
                                                         (unsigned long long*)A.etamax);
     return cudaGetLastError();
 }

@@ -28,7 +28,9 @@ struct of_ctx {
     // grid
     int batch = 0;
     of_grid_opts opts{};
-    ofl::SmoothTaps taps{};  // K_sigma (r = 0: none)
+    ofl::SmoothTaps taps{};      // K_sigma (r = 0: none)
+    ofl::SmoothTaps taps_rho{};  // K_rho (r = 0: none)
+    void* eld = nullptr;         // K_rho element data: 18 planes of frame_elems values (rho > 0)
     int fp64 = 1;
     size_t es = 8;  // storage element size (frames, alpha, inner vectors)
     std::vector<PairDesc> pd;
@@ -249,6 +251,8 @@ ofl::SolveBufs solve_bufs(of_ctx* h) {
     B.lam = h->opts.lambda;
     B.omega = h->opts.omega;
     B.gms = h->opts.model == OF_MODEL_CONSTANT ? 0.0 : 1.0;
+    B.eld = h->eld;
+    B.eld_stride = h->frame_elems;
     B.fp64 = h->fp64;
     B.spin_limit = h->spin_limit;
     B.tx_extra = h->starve_bytes;
@@ -269,6 +273,8 @@ ofl::AdaptBufs adapt_bufs(of_ctx* h) {
     A.etamax = h->etamax;
     A.lam = h->opts.lambda;
     A.gms = h->opts.model == OF_MODEL_CONSTANT ? 0.0 : 1.0;
+    A.eld = h->eld;
+    A.eld_stride = h->frame_elems;
     A.fp64 = h->fp64;
     return A;
 }
@@ -617,6 +623,7 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     if (!(opt.lambda > 0)) return fail(h, OF_ERR_ARG, "lambda must be > 0");
     if (!(opt.omega > 0 && opt.omega < 2)) return fail(h, OF_ERR_ARG, "omega must be in (0, 2)");
     if (!(opt.sigma >= 0 && opt.sigma <= 16)) return fail(h, OF_ERR_ARG, "sigma must be in [0, 16]");
+    if (!(opt.rho >= 0 && opt.rho <= 16)) return fail(h, OF_ERR_ARG, "rho must be in [0, 16]");
     if (opt.model != OF_MODEL_ILLUMINATION && opt.model != OF_MODEL_CONSTANT) return fail(h, OF_ERR_ARG, "bad model");
     if (opt.coarse < 0 || (opt.coarse > 0 && opt.coarse < 4)) return fail(h, OF_ERR_ARG, "coarse spacing must be 0 or >= 4");
     if (opt.tile_x < 4 || opt.tile_y < 4 || opt.tile_x % 4 || opt.tile_y % 4 || opt.tile_x > 256 || opt.tile_y > 256)
@@ -648,18 +655,23 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     CK(cudaStreamSynchronize(h->stream));
     free_all(h);
     h->opts = opt;
-    // K_sigma taps: w_k = exp(-k^2 / (2 sigma^2)), |k| <= ceil(3 sigma)
-    h->taps = ofl::SmoothTaps{};
-    if (opt.sigma > 0) {
-        const int r = std::min((int)std::ceil(3.0 * opt.sigma), ofl::OF_SMOOTH_RMAX);
-        h->taps.r = r;
-        h->taps.cw[0] = 0.0;
-        for (int j = 0; j <= 2 * r; ++j) {
-            const double k = j - r;
-            h->taps.w[j] = std::exp(-k * k / (2.0 * opt.sigma * opt.sigma));
-            h->taps.cw[j + 1] = h->taps.cw[j] + h->taps.w[j];
+    // K_sigma / K_rho taps: w_k = exp(-k^2 / (2 s^2)), |k| <= ceil(3 s)
+    auto make_taps = [](double sd) {
+        ofl::SmoothTaps T{};
+        if (sd > 0) {
+            const int r = std::min((int)std::ceil(3.0 * sd), ofl::OF_SMOOTH_RMAX);
+            T.r = r;
+            T.cw[0] = 0.0;
+            for (int j = 0; j <= 2 * r; ++j) {
+                const double k = j - r;
+                T.w[j] = std::exp(-k * k / (2.0 * sd * sd));
+                T.cw[j + 1] = T.cw[j] + T.w[j];
+            }
         }
-    }
+        return T;
+    };
+    h->taps = make_taps(opt.sigma);
+    h->taps_rho = make_taps(opt.rho);
     h->fp64 = fp64;
     h->es = fp64 ? 8 : 4;
     h->batch = batch;
@@ -706,6 +718,8 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     const size_t es = h->es;
     CK(dalloc(h, &h->f1, fo * es));
     CK(dalloc(h, &h->f2, fo * es));
+    h->eld = nullptr;
+    if (opt.rho > 0) CK(dalloc(h, &h->eld, 18 * fo * es));
     CK(dalloc(h, &h->alpha, 2 * fo * es));
     CK(dalloc(h, &h->eta, 2 * fo * es));
     CK(dalloc(h, &h->cell0, fo * (h->fp64 ? 32 : 8)));
@@ -867,9 +881,38 @@ of_status of_set_frames(of_handle h, int pair, const void* f1, const void* f2, o
                               h->stream));
         count_other(h, 4);
     }
+    if (h->eld) {  // K_rho element data from the stored frames
+        const int ty = h->fp64 ? ofl::T_F64 : ofl::T_F32;
+        void* scratch = (char*)h->r + d.vec_off * es;
+        CK(ofl::launch_element_data((char*)h->f1 + d.frame_off * es, (char*)h->f2 + d.frame_off * es, ty, d.W, d.H,
+                                    d.pitch, h->opts.model == OF_MODEL_CONSTANT ? 0.0 : 1.0,
+                                    (char*)h->eld + d.frame_off * es, h->frame_elems, scratch, h->taps_rho,
+                                    h->stream));
+        count_other(h, 1 + 2 * 18);
+    }
     h->frames_set[pair] = 1;
     h->solved = false;
     h->cells_dirty = true;
+    return OF_OK;
+}
+
+of_status of_get_element_data(of_handle h, int pair, void* out, of_dtype dt) {
+    of_status s = check_pair(h, pair);
+    if (s != OF_OK) return s;
+    if (!out) return fail(h, OF_ERR_ARG, "null output");
+    if (!h->eld) return fail(h, OF_ERR_STATE, "no element data (rho = 0)");
+    if (!h->frames_set[pair]) return fail(h, OF_ERR_STATE, "frames not set");
+    DevGuard g(h->device);
+    const PairDesc& d = h->pd[pair];
+    const int ty = h->fp64 ? ofl::T_F64 : ofl::T_F32;
+    const size_t oes = dt == OF_F64 ? 8 : 4;
+    const long long plane = (long long)(d.H - 1) * (d.W - 1);
+    for (int q = 0; q < 18; ++q) {
+        s = copy_out(h, (char*)h->eld + ((long long)q * h->frame_elems + d.frame_off) * h->es, ty, d.pitch,
+                     (char*)out + (size_t)q * plane * oes, dt, d.H - 1, d.W - 1);
+        if (s != OF_OK) return s;
+    }
+    CK(cudaStreamSynchronize(h->stream));
     return OF_OK;
 }
 
@@ -1003,6 +1046,10 @@ of_status of_adjoint(of_handle h, void* const* dLdU, void* const* dLdalpha, void
     if (!h) return OF_ERR_ARG;
     if (!h->solved) return fail(h, OF_ERR_STATE, "of_adjoint needs a previous of_solve");
     if (!dLdU) return fail(h, OF_ERR_ARG, "null dL/dU list");
+    if (h->eld)
+        for (int p = 0; p < h->batch; ++p)
+            if ((dLdf2 && dLdf2[p]) || (dLdf1 && dLdf1[p]))
+                return fail(h, OF_ERR_ARG, "frame gradients through K_rho (rho > 0) are not provided; pass NULL");
     DevGuard g(h->device);
     cudaStream_t st = h->stream;
     CK(cudaEventRecord(h->ev0, st));

@@ -97,6 +97,68 @@ __device__ __forceinline__ void square_contrib(const NodeVal<R>& A, const NodeVa
     }
 }
 
+// The same with general element data (K_rho > 0): per triangle the tensor
+// A (entries 00, 01, 02, 11, 12, 22) and the load vector F of Section 1.
+// Data term of vertex i: |K|/12 A (p_i + sum_j p_j); load |K|/3 F.
+template <typename R>
+__device__ __forceinline__ V3<R> sym_mv(const R* a, R x, R y, R z) {
+    return v3(a[0] * x + a[1] * y + a[2] * z, a[1] * x + a[3] * y + a[4] * z, a[2] * x + a[4] * y + a[5] * z);
+}
+
+template <typename R, bool WANT_B, bool WANT_A = true>
+__device__ __forceinline__ void square_contrib_el(const V3<R>& pA, const V3<R>& pB, const V3<R>& pC, const V3<R>& pD,
+                                                  R al0, R al1, R lam, const R (&e0)[9], const R (&e1)[9], bool valid,
+                                                  V3<R>& cA, V3<R>& cB, V3<R>& cC, V3<R>& cD, V3<R>& bA,
+                                                  V3<R>& bB, V3<R>& bC, V3<R>& bD) {
+    const R w24 = kconst<R>(1.0 / 24.0);
+    const R h = kconst<R>(OF_STIFF_HALF);
+    const R zero = kconst<R>(0.0);
+    if constexpr (!WANT_A) {
+        cA = cB = cC = cD = v3(zero, zero, zero);
+    } else {
+        // t = 0: A, B, C
+        const V3<R> S0 = pA + pB + pC;
+        const V3<R> uA = pA + S0, uB = pB + S0, uC = pC + S0;
+        const V3<R> wA = sym_mv(e0, uA.a * w24, uA.b * w24, uA.c * w24);
+        const V3<R> wB = sym_mv(e0, uB.a * w24, uB.b * w24, uB.c * w24);
+        const V3<R> wC = sym_mv(e0, uC.a * w24, uC.b * w24, uC.c * w24);
+        // t = 1: A, D, C
+        const V3<R> S1 = pA + pD + pC;
+        const V3<R> tA = pA + S1, tD = pD + S1, tC = pC + S1;
+        const V3<R> vA = sym_mv(e1, tA.a * w24, tA.b * w24, tA.c * w24);
+        const V3<R> vD = sym_mv(e1, tD.a * w24, tD.b * w24, tD.c * w24);
+        const V3<R> vC = sym_mv(e1, tC.a * w24, tC.b * w24, tC.c * w24);
+        // stiffness as in square_contrib
+        R a0 = h * al0, a1 = h * al1, l0 = h * lam;
+        V3<R> dAB = v3(pA.a - pB.a, pA.b - pB.b, pA.c - pB.c);
+        V3<R> dCB = v3(pC.a - pB.a, pC.b - pB.b, pC.c - pB.c);
+        V3<R> dAD = v3(pA.a - pD.a, pA.b - pD.b, pA.c - pD.c);
+        V3<R> dCD = v3(pC.a - pD.a, pC.b - pD.b, pC.c - pD.c);
+        cA.a = wA.a + vA.a + a0 * dAB.a + a1 * dAD.a;
+        cA.b = wA.b + vA.b + a0 * dAB.b + a1 * dAD.b;
+        cA.c = wA.c + vA.c + l0 * (dAB.c + dAD.c);
+        cB.a = wB.a - a0 * (dAB.a + dCB.a);
+        cB.b = wB.b - a0 * (dAB.b + dCB.b);
+        cB.c = wB.c - l0 * (dAB.c + dCB.c);
+        cC.a = wC.a + vC.a + a0 * dCB.a + a1 * dCD.a;
+        cC.b = wC.b + vC.b + a0 * dCB.b + a1 * dCD.b;
+        cC.c = wC.c + vC.c + l0 * (dCB.c + dCD.c);
+        cD.a = vD.a - a1 * (dAD.a + dCD.a);
+        cD.b = vD.b - a1 * (dAD.b + dCD.b);
+        cD.c = vD.c - l0 * (dAD.c + dCD.c);
+    }
+    if constexpr (WANT_B) {
+        const R sixth = kconst<R>(1.0 / 6.0);
+        V3<R> b0 = v3(sixth * e0[6], sixth * e0[7], sixth * e0[8]);
+        V3<R> b1 = v3(sixth * e1[6], sixth * e1[7], sixth * e1[8]);
+        bA = b0 + b1; bB = b0; bC = b0 + b1; bD = b1;
+    }
+    if (!valid) {
+        cA = cB = cC = cD = v3(zero, zero, zero);
+        if constexpr (WANT_B) bA = bB = bC = bD = v3(zero, zero, zero);
+    }
+}
+
 template <typename R, typename C, typename RI>
 struct ApplyParams {
     const PairDesc* pairs;
@@ -108,6 +170,8 @@ struct ApplyParams {
     const C* f1; const C* f2; const C* alpha;
     R lam;
     R gms;                     // illumination column scale (1: model with m, 0: brightness constancy)
+    const C* eld;              // K_rho element data: 18 planes (t * 9 + k), plane stride eld_stride
+    long long eld_stride;
     int rows_per_block;
     // vectors ([3][H][pitch] planes at pair vec_off)
     const R* in;        // APPLY: p;  PCG: z;  RES: x (double)
@@ -123,11 +187,12 @@ struct ApplyParams {
     int max_inner;
 };
 
-template <typename R, typename C, typename RI, int MODE, bool WANT_B, int NW, typename T = R>
+template <typename R, typename C, typename RI, int MODE, bool WANT_B, int NW, typename T = R, bool ELD = false>
 __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P) {
     // R: storage type of in/out (and of the PCG scalars); T: arithmetic of
     // the element contributions (R itself, or double-float for the residual
-    // of the FP32 path)
+    // of the FP32 path); ELD: element data from the K_rho planes instead of
+    // the frames
     constexpr int NT = NW * 32;
     __shared__ double sh_red[NT / 32];
     __shared__ int sh_last;
@@ -187,8 +252,12 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
         const bool in = (x >= 0) && (x < W) && (y >= 0) && (y < H);
         if (!in) { v.p = v3(zero, zero, zero); v.f1 = zero; v.f2 = zero; return v; }
         const long long o = (long long)y * pitch + x;
-        v.f1 = Cvt<T>::from(f1[o]);
-        v.f2 = Cvt<T>::from(f2[o]);
+        if constexpr (ELD) {
+            v.f1 = zero; v.f2 = zero;
+        } else {
+            v.f1 = Cvt<T>::from(f1[o]);
+            v.f2 = Cvt<T>::from(f2[o]);
+        }
         if (MODE == MODE_RESB) {
             v.p = v3(zero, zero, zero);
             return v;
@@ -228,8 +297,12 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
     auto shfl_node = [&](const NodeVal<T>& v) -> NodeVal<T> {
         NodeVal<T> w;
         w.p = shfl_down3(v.p);
-        w.f1 = shfl_down(v.f1, 1);
-        w.f2 = shfl_down(v.f2, 1);
+        if constexpr (ELD) {
+            w.f1 = v.f1; w.f2 = v.f2;
+        } else {
+            w.f1 = shfl_down(v.f1, 1);
+            w.f2 = shfl_down(v.f2, 1);
+        }
         return w;
     };
 
@@ -249,8 +322,20 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
         const T al0 = valid ? Cvt<T>::from(al[2 * ((long long)sy * pitch + cx)]) : zero;
         const T al1 = valid ? Cvt<T>::from(al[2 * ((long long)sy * pitch + cx) + 1]) : zero;
         V3<T> cA, cB, cC, cD, bA, bB, bC, bD;
-        square_contrib<T, WANT_B || IS_RES, MODE != MODE_RESB>(cur, ncur, nnxt, nxt, al0, al1, lam, gms, valid, cA,
-                                                                  cB, cC, cD, bA, bB, bC, bD);
+        if constexpr (ELD) {
+            T e0[9], e1[9];
+            const C* ep = P.eld + pd.frame_off + (long long)sy * pitch + cx;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                e0[k] = valid ? Cvt<T>::from(ep[k * P.eld_stride]) : zero;
+                e1[k] = valid ? Cvt<T>::from(ep[(9 + k) * P.eld_stride]) : zero;
+            }
+            square_contrib_el<T, WANT_B || IS_RES, MODE != MODE_RESB>(cur.p, ncur.p, nnxt.p, nxt.p, al0, al1, lam, e0,
+                                                                      e1, valid, cA, cB, cC, cD, bA, bB, bC, bD);
+        } else {
+            square_contrib<T, WANT_B || IS_RES, MODE != MODE_RESB>(cur, ncur, nnxt, nxt, al0, al1, lam, gms, valid,
+                                                                      cA, cB, cC, cD, bA, bB, bC, bD);
+        }
         V3<T> left = shfl_down3(cA);
         V3<T> res = carry + cB + left;  // node (cx+1, sy) complete
         V3<T> resb = v3(zero, zero, zero);

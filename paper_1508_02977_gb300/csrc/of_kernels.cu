@@ -76,6 +76,8 @@ static ApplyParams<R, C, RI> base_params(const SolveBufs& B) {
     P.alpha = (const C*)B.alpha;
     P.lam = (R)B.lam;
     P.gms = (R)B.gms;
+    P.eld = (const C*)B.eld;
+    P.eld_stride = B.eld_stride;
     P.rows_per_block = B.rows_per_block;
     return P;
 }
@@ -97,8 +99,14 @@ static cudaError_t residual_t(const SolveBufs& B, const double* xin, double* xou
     P.max_inner = max_inner;
     // the FP32 path forms A x and b in double-float: FP64-grade residual on the FP32 pipe
     using T = typename std::conditional<sizeof(C) == 4, DF, double>::type;
-    if (xin) k_apply<double, C, RI, MODE_RES, false, APPLY_NW, T><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
-    else k_apply<double, C, RI, MODE_RESB, false, APPLY_NW, T><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+    if (B.eld) {
+        if (xin) k_apply<double, C, RI, MODE_RES, false, APPLY_NW, T, true><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+        else k_apply<double, C, RI, MODE_RESB, false, APPLY_NW, T, true><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+    } else if (xin) {
+        k_apply<double, C, RI, MODE_RES, false, APPLY_NW, T><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+    } else {
+        k_apply<double, C, RI, MODE_RESB, false, APPLY_NW, T><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+    }
     return cudaGetLastError();
 }
 
@@ -260,7 +268,8 @@ static cudaError_t pcg_apply_t(const SolveBufs& B, cudaStream_t st) {
     P.p_buf1 = (R*)B.p1;
     P.dcorr = (R*)B.d;
     P.out = (R*)B.q;
-    if constexpr (sizeof(R) == 4) k_apply4<MODE_PCG><<<B.nblk, 32, apply4_smem_bytes(), st>>>(P);  // FP32: four columns per lane
+    if (B.eld) k_apply<R, R, R, MODE_PCG, false, APPLY_NW, R, true><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+    else if constexpr (sizeof(R) == 4) k_apply4<MODE_PCG><<<B.nblk, 32, apply4_smem_bytes(), st>>>(P);  // FP32: four columns per lane
     else k_apply<R, R, R, MODE_PCG, false, APPLY_NW><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
     return cudaGetLastError();
 }
@@ -281,7 +290,10 @@ static cudaError_t apply_t(const SolveBufs& B, int blk0, int nblk, const void* p
     P.in = (const R*)p;
     P.out = (R*)q;
     P.bout = (R*)b;
-    if (b) k_apply<R, R, R, MODE_APPLY, true, APPLY_NW><<<nblk, APPLY_NW * 32, 0, st>>>(P);
+    if (B.eld) {
+        if (b) k_apply<R, R, R, MODE_APPLY, true, APPLY_NW, R, true><<<nblk, APPLY_NW * 32, 0, st>>>(P);
+        else k_apply<R, R, R, MODE_APPLY, false, APPLY_NW, R, true><<<nblk, APPLY_NW * 32, 0, st>>>(P);
+    } else if (b) k_apply<R, R, R, MODE_APPLY, true, APPLY_NW><<<nblk, APPLY_NW * 32, 0, st>>>(P);
     else if constexpr (sizeof(R) == 4) k_apply4<MODE_APPLY><<<nblk, 32, apply4_smem_bytes(), st>>>(P);
     else k_apply<R, R, R, MODE_APPLY, false, APPLY_NW><<<nblk, APPLY_NW * 32, 0, st>>>(P);
     return cudaGetLastError();

@@ -97,6 +97,8 @@ struct SolveBufs {
     double lam;
     double omega;  // relaxation factor of the local block SOR sweeps
     double gms;    // illumination column scale of the element data (1 or 0, see of_model)
+    const void* eld;      // K_rho element data (18 planes, storage precision) or null (rho = 0)
+    long long eld_stride; // plane stride of eld (elements)
     int fp64;            // 1: everything FP64; 0: FP32 inner with FP64 residual
     long long spin_limit;
     int use_cond;        // Schwarz launches inside the inner-loop graph set its condition
@@ -149,6 +151,8 @@ struct AdaptBufs {
     unsigned* cnt;
     double lam;
     double gms;
+    const void* eld;      // K_rho element data or null
+    long long eld_stride;
     int fp64;
 };
 cudaError_t launch_indicator(const AdaptBufs& A, int pair, int H, int W, cudaStream_t st);
@@ -175,6 +179,11 @@ struct SmoothTaps {
 // holds H x pitch values of the same type
 cudaError_t launch_smooth(void* f, void* scratch, int type, int W, int H, long long pitch, const SmoothTaps& T,
                           bool transpose, cudaStream_t st);
+// K_rho element data of one pair: eld (+ frame_off) gets 18 planes at stride
+// `stride` (t * 9 + k: A_rho entries 00, 01, 02, 11, 12, 22, then F), each
+// smoothed by T over the (W-1) x (H-1) lattice; scratch: H x pitch values
+cudaError_t launch_element_data(const void* f1, const void* f2, int type, int W, int H, long long pitch, double gms,
+                                void* eld, long long stride, void* scratch, const SmoothTaps& T, cudaStream_t st);
 cudaError_t launch_alpha_update(const AdaptBufs& A, int pair, int H, int W, double kappa, double eta_thr,
                                 double alpha_th, cudaStream_t st);
 // adjoint gradients for one pair: u = solution, lam = adjoint state (FP64 planes)

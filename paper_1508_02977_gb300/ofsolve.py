@@ -35,7 +35,7 @@ class GridOpts(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("overlap", ctypes.c_int),
                 ("sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("lam", ctypes.c_double),
                 ("preconditioner", ctypes.c_int), ("omega", ctypes.c_double), ("sigma", ctypes.c_double),
-                ("model", ctypes.c_int), ("coarse", ctypes.c_int)]
+                ("model", ctypes.c_int), ("coarse", ctypes.c_int), ("rho", ctypes.c_double)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -69,6 +69,7 @@ _lib.of_set_frames.argtypes = [_h, ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.
 _lib.of_set_alpha.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_int]
 _lib.of_get_alpha.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_int]
 _lib.of_get_frames.argtypes = [_h, ctypes.c_int, _vp, _vp, ctypes.c_int]
+_lib.of_get_element_data.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_int]
 _lib.of_set_wait_limit.argtypes = [_h, ctypes.c_int64]
 _lib.of_debug_starve_staging.argtypes = [_h, ctypes.c_int]
 _lib.of_solve.argtypes = [_h, ctypes.POINTER(SolveOpts), ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(SolveInfo)]
@@ -84,12 +85,13 @@ _lib.of_residual_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, 
 _lib.of_destroy.argtypes = [_h]
 _lib.of_last_error.argtypes = [_h]
 _lib.of_last_error.restype = ctypes.c_char_p
-for _f in ("of_create", "of_setup_grid", "of_set_frames", "of_set_alpha", "of_get_alpha", "of_solve",
+for _f in ("of_create", "of_setup_grid", "of_set_frames", "of_get_element_data", "of_set_alpha", "of_get_alpha", "of_solve",
            "of_adapt_alpha", "of_adjoint", "of_apply", "of_precondition", "of_residual", "of_set_profiling",
            "of_get_profile", "of_residual_noalloc", "of_destroy"):
     getattr(_lib, _f).restype = ctypes.c_int
 
-EXPORTS = ("of_create", "of_setup_grid", "of_set_frames", "of_get_frames", "of_set_alpha", "of_get_alpha", "of_solve",
+EXPORTS = ("of_create", "of_setup_grid", "of_set_frames", "of_get_frames", "of_get_element_data", "of_set_alpha",
+           "of_get_alpha", "of_solve",
            "of_adapt_alpha", "of_adjoint", "of_apply", "of_precondition", "of_residual", "of_set_profiling",
            "of_get_profile", "of_residual_noalloc", "of_set_wait_limit", "of_debug_starve_staging", "of_destroy",
            "of_last_error")
@@ -150,16 +152,17 @@ def of_create(device: int = 0, stream=None):
 
 
 def of_setup_grid(h, sizes, tile=(32, 32), overlap=0, sweeps=1, precision=OF_PREC_MIXED, lam=1.0,
-                  preconditioner=OF_PC_SCHWARZ, omega=1.0, sigma=0.0, model=0, coarse=0):
+                  preconditioner=OF_PC_SCHWARZ, omega=1.0, sigma=0.0, model=0, coarse=0, rho=0.0):
     """sizes: list of (W, H); omega: relaxation factor of the local block SOR
     sweeps, in (0, 2); sigma: K_sigma pre-smoothing of the frames (0: none);
     model: OF_MODEL_ILLUMINATION or OF_MODEL_CONSTANT; coarse: spacing of the
-    two-level preconditioner's coarse grid in nodes (0: one level)."""
+    two-level preconditioner's coarse grid in nodes (0: one level); rho: K_rho
+    integration scale of the data term (0: none)."""
     n = len(sizes)
     Wa = (ctypes.c_int32 * n)(*[int(w) for w, _ in sizes])
     Ha = (ctypes.c_int32 * n)(*[int(hh) for _, hh in sizes])
     o = GridOpts(int(tile[0]), int(tile[1]), int(overlap), int(sweeps), int(precision), float(lam), int(preconditioner),
-                 float(omega), float(sigma), int(model), int(coarse))
+                 float(omega), float(sigma), int(model), int(coarse), float(rho))
     return _check(h, _lib.of_setup_grid(h, n, Wa, Ha, ctypes.byref(o)))
 
 
@@ -174,6 +177,13 @@ def of_set_frames(h, pair, f1, f2):
 def of_set_alpha(h, pair, alpha=None, alpha_const=0.0):
     p, dt = _ptr_dtype(alpha)
     return _check(h, _lib.of_set_alpha(h, int(pair), _vp(p) if p else None, float(alpha_const), dt))
+
+
+def of_get_element_data(h, pair, out):
+    """The K_rho element data of a pair into an [18][H-1][W-1] array (plane
+    t * 9 + k: A_rho entries 00, 01, 02, 11, 12, 22, then F)."""
+    p, dt = _ptr_dtype(out)
+    return _check(h, _lib.of_get_element_data(h, int(pair), _vp(p), dt))
 
 
 def of_get_frames(h, pair, f1, f2):

@@ -1,0 +1,212 @@
+"""GPU parity of the K_rho data term (Section 1: the matrix A_rho and the
+vector F): element data, operator, load, solves, indicator and the alpha
+gradient, through the C ABI against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_1508_02977_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+sp = pytest.importorskip("scipy.sparse")
+
+EPS32 = np.finfo(np.float32).eps
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1508_02977_gb300 import ofsolve
+    return ofsolve
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def handle(S, sizes, **kw):
+    h = S.of_create(0)
+    S.of_setup_grid(h, sizes, **kw)
+    return h
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def csr_abs_matvec(sysm, x):
+    A = sp.csr_matrix((np.abs(sysm.val), sysm.col, sysm.rowptr), shape=(sysm.n, sysm.n))
+    return (A @ np.abs(np.asarray(x).ravel())).reshape(3, sysm.H, sysm.W)
+
+
+def oracle_planes(oracle, f1, f2, rho, model):
+    """The oracle's element data in the [18][H-1][W-1] plane order."""
+    Ael, Fel = oracle.element_data(f1, f2, rho, model)
+    out = []
+    for t in range(2):
+        out += [Ael[:, :, t, k] for k in range(6)] + [Fel[:, :, t, k] for k in range(3)]
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("prec,model,rho", [(0, 0, 1.5), (0, 1, 2.5), (1, 0, 1.5), (0, 0, 9.0)])
+def test_element_data_matches_oracle(S, oracle, prec, model, rho):
+    """Products of the element data, K_rho over each triangle family's
+    lattice (rho = 9: taps reach past the 53-node height)."""
+    W, H = 75, 53
+    f1, f2 = synth.random_frames(W, H, 81)
+    dt = torch.float64 if prec == 0 else torch.float32
+    if prec == 1:
+        f1, f2 = f32(f1), f32(f2)
+    h = handle(S, [(W, H)], precision=prec, model=model, rho=rho)
+    try:
+        S.of_set_frames(h, 0, dev(f1, dt), dev(f2, dt))
+        out = torch.zeros(18, H - 1, W - 1, dtype=dt, device="cuda")
+        S.of_get_element_data(h, 0, out)
+        got = out.cpu().numpy().astype(np.float64)
+    finally:
+        S.of_destroy(h)
+    want = oracle_planes(oracle, f1, f2, rho, model)
+    for q in range(18):
+        scale = max(np.abs(want[q]).max(), 1e-300)
+        err = np.abs(got[q] - want[q]).max() / scale
+        assert err <= (1e-13 if prec == 0 else 2e-6), (q, err)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("W,H", [(64, 48), (7, 5), (130, 67), (2, 2)])
+def test_apply_rho_matches_oracle(S, oracle, prec, W, H):
+    rho, lam = 1.3, 0.8
+    f1, f2 = synth.random_frames(W, H, 3 * W + H)
+    alpha = synth.random_alpha(W, H, W + 2 * H)
+    p = np.random.default_rng(W * H + 5).standard_normal((3, H, W))
+    dt = torch.float64 if prec == 0 else torch.float32
+    if prec == 1:
+        f1, f2, alpha, p = f32(f1), f32(f2), f32(alpha), f32(p)
+    sysm = oracle.System.from_frames(f1, f2, alpha, lam, rho=rho)
+    h = handle(S, [(W, H)], precision=prec, lam=lam, rho=rho)
+    try:
+        S.of_set_frames(h, 0, dev(f1, dt), dev(f2, dt))
+        S.of_set_alpha(h, 0, dev(alpha, dt))
+        q = torch.zeros(3, H, W, dtype=dt, device="cuda")
+        b = torch.zeros_like(q)
+        S.of_apply(h, 0, dev(p, dt), q, b)
+        q, b = q.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)
+    finally:
+        S.of_destroy(h)
+    scale = csr_abs_matvec(sysm, p)
+    tol = 1e-13 if prec == 0 else 128 * EPS32
+    assert np.all(np.abs(q - sysm.matvec(p)) <= tol * scale + 1e-300)
+    bw = sysm.b.reshape(3, H, W)
+    assert np.abs(b - bw).max() <= (1e-13 if prec == 0 else 1e-5) * max(np.abs(bw).max(), 1e-300)
+
+
+def test_rho_preconditioner_is_the_unsmoothed_one(S, oracle):
+    """With rho > 0 the Schwarz sweeps still use the element records of
+    g g^T: z = M r equals the oracle's sweeps on the unsmoothed system."""
+    W, H = 75, 53
+    f1, f2 = synth.random_frames(W, H, 83)
+    alpha = synth.random_alpha(W, H, 84)
+    sysm = oracle.System.from_frames(f1, f2, alpha, 1.0, rho=2.0)
+    r = np.random.default_rng(85).standard_normal((3, H, W))
+    h = handle(S, [(W, H)], precision=0, tile=(16, 12), sweeps=2, omega=1.6, rho=2.0)
+    try:
+        S.of_set_frames(h, 0, dev(f1), dev(f2))
+        S.of_set_alpha(h, 0, dev(alpha))
+        z = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+        S.of_precondition(h, 0, dev(r), z)
+        z = z.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    want = sysm.precond_system().schwarz_sweeps(r, (16, 12), 0, 2, 1.6)
+    assert np.abs(z - want).max() <= 1e-11 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("coarse", [0, 12])
+def test_rho_fp64_solve_matches_direct(S, oracle, coarse):
+    p = synth.blobs()
+    sysm = oracle.System.from_frames(p.f1, p.f2, p.alpha0, p.lam, rho=1.5)
+    Ud = sysm.solve_direct()
+    h = handle(S, [(p.W, p.H)], precision=0, tile=(16, 16), sweeps=2, omega=1.5, rho=1.5, coarse=coarse)
+    try:
+        S.of_set_frames(h, 0, dev(p.f1), dev(p.f2))
+        S.of_set_alpha(h, 0, None, p.alpha0)
+        U = torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda")
+        S.of_solve(h, [U], rtol=1e-14, max_inner=20000)
+        U = U.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    assert np.linalg.norm(U - Ud) <= 1e-10 * np.linalg.norm(Ud)
+
+
+def test_rho_mixed_solve_texture(S, oracle):
+    """640x480 texture, mixed precision, rho = 1.5: the oracle's FP64
+    residual of the returned flow (oracle operator from the FP32 frames)."""
+    t = synth.texture()
+    f1, f2 = f32(t.f1), f32(t.f2)
+    h = handle(S, [(t.W, t.H)], tile=(48, 48), sweeps=4, omega=1.6, precision=1, rho=1.5)
+    try:
+        S.of_set_frames(h, 0, dev(t.f1, torch.float32), dev(t.f2, torch.float32))
+        S.of_set_alpha(h, 0, None, t.alpha0)
+        U = torch.zeros(3, t.H, t.W, dtype=torch.float64, device="cuda")
+        st, info = S.of_solve(h, [U], rtol=1e-6)
+        U = U.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    sysm = oracle.System.from_frames(f1, f2, np.float32(t.alpha0), t.lam, rho=1.5)
+    assert sysm.rel_residual(U) <= 1e-6
+
+
+def test_rho_indicator_matches_oracle(S, oracle):
+    p = synth.blobs()
+    alpha = synth.random_alpha(p.W, p.H, 86, 0.02, 0.08)
+    h = handle(S, [(p.W, p.H)], precision=0, tile=(32, 24), rho=1.5)
+    try:
+        S.of_set_frames(h, 0, dev(p.f1), dev(p.f2))
+        S.of_set_alpha(h, 0, dev(alpha))
+        U = torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda")
+        S.of_solve(h, [U], rtol=1e-12)
+        eta = torch.zeros(p.H - 1, p.W - 1, 2, dtype=torch.float64, device="cuda")
+        S.of_adapt_alpha(h, 4.0, 0.25, 1e-3, [eta])
+        U, eta = U.cpu().numpy(), eta.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    eta_o = oracle.System.from_frames(p.f1, p.f2, alpha, p.lam, rho=1.5).indicator(U)
+    assert np.abs(eta - eta_o).max() <= 1e-12 * eta_o.max()
+
+
+def test_rho_alpha_gradient_by_differences(S, oracle):
+    """dL/dalpha through the adjoint solve with the K_rho operator, for
+    L = c.U, against central differences of oracle direct solves; frame
+    gradients are refused (OF_ERR_ARG) when rho > 0."""
+    W, H, rho, lam = 16, 12, 1.2, 1.0
+    f1, f2 = synth.random_frames(W, H, 87)
+    alpha = synth.random_alpha(W, H, 88)
+    c = np.random.default_rng(89).standard_normal((3, H, W))
+    h = handle(S, [(W, H)], precision=0, tile=(8, 8), sweeps=2, rho=rho)
+    try:
+        S.of_set_frames(h, 0, dev(f1), dev(f2))
+        S.of_set_alpha(h, 0, dev(alpha))
+        U = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+        S.of_solve(h, [U], rtol=1e-14, max_inner=20000)
+        da = torch.zeros(H - 1, W - 1, 2, dtype=torch.float64, device="cuda")
+        S.of_adjoint(h, [dev(c)], [da])
+        da = da.cpu().numpy()
+        df2 = torch.zeros(H, W, dtype=torch.float64, device="cuda")
+        st, _ = S.of_adjoint(h, [dev(c)], None, [df2], raise_on=False)
+        assert st == S.OF_ERR_ARG
+    finally:
+        S.of_destroy(h)
+    hstep = 1e-5
+    for (y, x, t) in [(0, 0, 0), (5, 7, 1), (10, 14, 0), (3, 2, 1)]:
+        vals = []
+        for sgn in (1, -1):
+            a = alpha.copy()
+            a[y, x, t] += sgn * hstep
+            Us = oracle.System.from_frames(f1, f2, a, lam, rho=rho).solve_direct()
+            vals.append(np.sum(c * Us))
+        fd = (vals[0] - vals[1]) / (2 * hstep)
+        assert abs(da[y, x, t] - fd) <= 1e-6 * max(1.0, abs(fd)), (y, x, t, da[y, x, t], fd)
