@@ -322,13 +322,16 @@ def run_ours(args):
         S.of_destroy(h64)
 
     # the model options built beyond the workload's configuration, on the same
-    # pair and step: brightness constancy (no illumination unknown) and K_sigma
-    # pre-smoothing (inside each step's of_set_frames)
+    # pair and step: brightness constancy (no illumination unknown), K_sigma
+    # pre-smoothing and K_rho integration (inside each step's of_set_frames),
+    # and K_sigma with the two-level preconditioner
     variants = None
     if args.variant_steps > 0:
         variants = {}
         for name, extra, frames in (("model_constant", dict(model=1), None),
-                                    ("sigma_1.5", dict(sigma=1.5), (f1, f2))):
+                                    ("sigma_1.5", dict(sigma=1.5), (f1, f2)),
+                                    ("sigma_1.5_coarse_96", dict(sigma=1.5, coarse=96), (f1, f2)),
+                                    ("rho_1.5", dict(rho=1.5), (f1, f2))):
             hv = make(dict(WORKLOAD_OPTS, **extra))
             step(hv, U, frames)
             infos.clear()

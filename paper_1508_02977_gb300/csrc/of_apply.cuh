@@ -325,10 +325,13 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
         if constexpr (ELD) {
             T e0[9], e1[9];
             const C* ep = P.eld + pd.frame_off + (long long)sy * pitch + cx;
+            constexpr int NK = (WANT_B || IS_RES) ? 9 : 6;  // F only for the load
+            constexpr int K0 = (MODE == MODE_RESB) ? 6 : 0;  // A not needed for r = b
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
-                e0[k] = valid ? Cvt<T>::from(ep[k * P.eld_stride]) : zero;
-                e1[k] = valid ? Cvt<T>::from(ep[(9 + k) * P.eld_stride]) : zero;
+                const bool need = valid && k >= K0 && k < NK;
+                e0[k] = need ? Cvt<T>::from(ep[k * P.eld_stride]) : zero;
+                e1[k] = need ? Cvt<T>::from(ep[(9 + k) * P.eld_stride]) : zero;
             }
             square_contrib_el<T, WANT_B || IS_RES, MODE != MODE_RESB>(cur.p, ncur.p, nnxt.p, nxt.p, al0, al1, lam, e0,
                                                                       e1, valid, cA, cB, cC, cD, bA, bB, bC, bD);
