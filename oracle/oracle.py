@@ -450,8 +450,10 @@ def alpha_update(eta, alpha, kappa, eta_thr, alpha_th):
     return a
 
 
-def adjoint_grad(f1, f2, alpha, lam, U, Lam, want_f1=True, model=0):
-    """(dL/dalpha, dL/df2, dL/df1) given U and the adjoint state Lam."""
+def adjoint_grad(f1, f2, alpha, lam, U, Lam, want_f1=True, model=0, rho=0.0):
+    """(dL/dalpha, dL/df2, dL/df1) given U and the adjoint state Lam.  With
+    rho > 0 the frame gradients go through the K_rho element tensors
+    (_adjoint_frames_rho); dL/dalpha only involves the stiffness."""
     L = _load()
     f1, f2 = _c(f1), _c(f2)
     H, W = f1.shape
@@ -461,7 +463,72 @@ def adjoint_grad(f1, f2, alpha, lam, U, Lam, want_f1=True, model=0):
     d1 = np.zeros((H, W)) if want_f1 else None
     L.orc_adjoint_grad(W, H, f1, f2, alpha, float(lam), _c(U).ravel(), _c(Lam).ravel(),
                        _ptr(da), _ptr(d2), _ptr(d1), int(model))
+    if rho > 0:
+        d2, d1r = _adjoint_frames_rho(f1, f2, U, Lam, model, rho)
+        d1 = d1r if want_f1 else None
     return da, d2, d1
+
+
+def _tri_vertex_index(W, H):
+    """[H-1][W-1][2][3] (y, x) vertex coordinates of every element (Section
+    2.2 mesh: t = 0 -> (x,y), (x+1,y), (x+1,y+1); t = 1 -> (x,y), (x,y+1),
+    (x+1,y+1))."""
+    ys, xs = np.mgrid[0:H - 1, 0:W - 1]
+    vy = np.zeros((H - 1, W - 1, 2, 3), dtype=np.int64)
+    vx = np.zeros_like(vy)
+    vy[..., 0, :] = np.stack([ys, ys, ys + 1], -1)
+    vx[..., 0, :] = np.stack([xs, xs + 1, xs + 1], -1)
+    vy[..., 1, :] = np.stack([ys, ys + 1, ys + 1], -1)
+    vx[..., 1, :] = np.stack([xs, xs, xs + 1], -1)
+    return vy, vx
+
+
+def _adjoint_frames_rho(f1, f2, U, Lam, model, rho):
+    """Frame gradients with the K_rho data term.  With E = Lam^T (A U - b)
+    assembled from the element tensors, dL/dtheta = -dE/dtheta and
+      dE/dA_cd = |K|/12 (sum_i Lam_ic U_id + (sum_i Lam_ic)(sum_i U_id)),
+      dE/dF_c  = -|K|/3 sum_i Lam_ic;
+    K_rho is linear, so these go back to the unsmoothed products through
+    its transpose (smooth_transpose, per triangle family); the products
+    g_c g_d and -ft g_c then give dE/dg and dE/dft, and g, ft depend on the
+    frames through the P1 gradient of f2 and the vertex means (as in the
+    rho = 0 adjoint)."""
+    f1, f2 = _c(f1), _c(f2)
+    H, W = f1.shape
+    U, Lam = np.asarray(U, np.float64), np.asarray(Lam, np.float64)
+    vy, vx = _tri_vertex_index(W, H)
+    Ue = np.moveaxis(U[:, vy, vx], 0, -1)      # [H-1][W-1][2][3 vertices][3 comps]
+    Le = np.moveaxis(Lam[:, vy, vx], 0, -1)
+    K = 0.5
+    M = K / 12.0 * (np.einsum("...ic,...id->...cd", Le, Ue)
+                    + np.einsum("...c,...d->...cd", Le.sum(-2), Ue.sum(-2)))
+    GA = np.stack([M[..., c, c] if c == d else M[..., c, d] + M[..., d, c] for c, d in SYM6], -1)
+    GF = -K / 3.0 * Le.sum(-2)
+    for t in range(2):  # K_rho^T per family
+        for k in range(6):
+            GA[:, :, t, k] = smooth_transpose(GA[:, :, t, k], rho)
+        for k in range(3):
+            GF[:, :, t, k] = smooth_transpose(GF[:, :, t, k], rho)
+    g, ft = coefficients(f1, f2, model)
+    dEdg = np.zeros_like(g)
+    for k, (c, d) in enumerate(SYM6):
+        dEdg[..., c] += GA[..., k] * g[..., d]
+        dEdg[..., d] += GA[..., k] * g[..., c]
+    dEdg -= ft[..., None] * GF
+    dEdft = -np.sum(GF * g, axis=-1)
+    # g_x, g_y = P1 gradient of f2 on the element; g_m = -gms mean f1; ft = mean (f2 - f1)
+    gphi_x = np.array([[-1.0, 1.0, 0.0], [0.0, -1.0, 1.0]])  # d phi_i / dx, families t = 0, 1
+    gphi_y = np.array([[0.0, -1.0, 1.0], [-1.0, 1.0, 0.0]])
+    gms = 0.0 if model == 1 else 1.0
+    d2 = np.zeros((H, W))
+    d1 = np.zeros((H, W))
+    for t in range(2):
+        for i in range(3):
+            c2 = dEdg[:, :, t, 0] * gphi_x[t, i] + dEdg[:, :, t, 1] * gphi_y[t, i] + dEdft[:, :, t] / 3.0
+            c1 = -gms * dEdg[:, :, t, 2] / 3.0 - dEdft[:, :, t] / 3.0
+            np.add.at(d2, (vy[:, :, t, i], vx[:, :, t, i]), -c2)
+            np.add.at(d1, (vy[:, :, t, i], vx[:, :, t, i]), -c1)
+    return d2, d1
 
 
 def mean_epe(U, flow_gt):

@@ -775,3 +775,42 @@ def test_smooth_taps_wider_than_image(oracle):
             w = np.exp(-((np.arange(4)[:, None] - y) ** 2 + (np.arange(5)[None, :] - x) ** 2) / (2 * sigma ** 2))
             want[y, x] = np.sum(w * I) / np.sum(w)
     assert np.abs(oracle.smooth(I, sigma) - want).max() <= 1e-14
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_adjoint_frame_gradient_with_rho_matches_differences(oracle, model):
+    """Frame gradients of a flow loss through the K_rho element tensors
+    against central differences of direct solves; at rho -> 0 they equal
+    the rank-1 adjoint."""
+    W, H, rho, lam = 8, 7, 1.3, 1.0
+    f1, f2 = synth.random_frames(W, H, 72)
+    alpha = synth.random_alpha(W, H, 73)
+    gt = np.random.default_rng(74).uniform(-1, 1, (2, H, W))
+
+    def loss(f1_, f2_):
+        S_ = oracle.System.from_frames(f1_, f2_, alpha, lam, model, rho=rho)
+        return oracle.mean_epe(S_.solve_direct(), gt)
+
+    S = oracle.System.from_frames(f1, f2, alpha, lam, model, rho=rho)
+    U = S.solve_direct()
+    Lam = S.solve_with(oracle.mean_epe_grad(U, gt))
+    _, d2, d1 = oracle.adjoint_grad(f1, f2, alpha, lam, U, Lam, model=model, rho=rho)
+    h = 1e-4
+    rng = np.random.default_rng(75)
+    for which, grad in (("f2", d2), ("f1", d1)):
+        for _ in range(6):
+            y, x = rng.integers(0, H), rng.integers(0, W)
+            fp = (f1 if which == "f1" else f2).copy()
+            fm = fp.copy()
+            fp[y, x] += h
+            fm[y, x] -= h
+            fd = (loss(fp, f2) - loss(fm, f2)) / (2 * h) if which == "f1" else \
+                (loss(f1, fp) - loss(f1, fm)) / (2 * h)
+            assert abs(fd - grad[y, x]) <= 1e-5 * np.abs(grad).max(), (which, y, x, fd, grad[y, x])
+    S0 = oracle.System.from_frames(f1, f2, alpha, lam, model)
+    U0 = S0.solve_direct()
+    L0 = S0.solve_with(oracle.mean_epe_grad(U0, gt))
+    _, e2, e1 = oracle.adjoint_grad(f1, f2, alpha, lam, U0, L0, model=model)
+    _, r2, r1 = oracle.adjoint_grad(f1, f2, alpha, lam, U0, L0, model=model, rho=0.1)
+    assert np.abs(r2 - e2).max() <= 1e-12 * np.abs(e2).max()
+    assert np.abs(r1 - e1).max() <= 1e-12 * max(np.abs(e1).max(), 1e-300)
