@@ -107,8 +107,7 @@ typedef struct {
                                 product g_c g_d and -ft g_c is smoothed over the lattice of its triangle
                                 family (t = 0 and t = 1 separately) by the sampled Gaussian of sigma's
                                 form, normalised inside the lattice.  The operator uses A_rho exactly; the
-                                Schwarz (and coarse) preconditioner is built from the unsmoothed g g^T.
-                                of_adjoint returns no frame gradients when rho > 0 */
+                                Schwarz (and coarse) preconditioner is built from the unsmoothed g g^T */
 } of_grid_opts;
 
 /* Solve options.  A field left at 0 takes the default in brackets. */
@@ -192,7 +191,10 @@ of_status of_adapt_alpha(of_handle h, double kappa, double eta_thr, double alpha
  * symmetric, so the adjoint system is the same operator) with the options
  * of the last of_solve, then forms per element
  *   dL/dalpha_K = -|K| sum_{c=u1,u2} grad Lam_c . grad U_c
- * and, through g_K and ft_K, dL/df2 and dL/df1 at the nodes.  dLdU[p] is
+ * and, through g_K and ft_K, dL/df2 and dL/df1 at the nodes (with rho > 0
+ * through the K_rho element tensors: dE/dA_rho and dE/dF per element, K_rho
+ * transposed, then the products back to g_K and ft_K; with sigma > 0 the
+ * frame gradients are w.r.t. the images given to of_set_frames).  dLdU[p] is
  * [3][H][W]; dLdalpha[p] is [H-1][W-1][2]; dLdf2[p], dLdf1[p] are [H][W]
  * (row pitch W); any output array list may be NULL.  Requires a previous
  * of_solve (its U is the linearisation point).  Synchronises the stream. */

@@ -323,6 +323,119 @@ __global__ void k_adjoint_frames(const PairDesc* pairs, int pair, const R* __res
     if (df1) df1[(long long)y * W + x] = (O)a1;
 }
 
+// K_rho data term: per element (the 18 planes of the element data layout)
+//   dE/dA_cd = |K|/12 (sum_i Lam_ic U_id + (sum_i Lam_ic)(sum_i U_id))   (c = d)
+//   and its sum with the transpose for the stored off-diagonal entries,
+//   dE/dF_c  = -|K|/3 sum_i Lam_ic.
+template <typename R>
+__global__ void k_adjoint_eld(const PairDesc* pairs, int pair, const double* __restrict__ ua,
+                              const double* __restrict__ la, R* __restrict__ G, long long stride) {
+    const PairDesc pd = pairs[pair];
+    const int W = pd.W, H = pd.H, pitch = pd.pitch;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W - 1 || y >= H - 1) return;
+    UView<double, double> U{ua + pd.vec_off, (long long)H * pitch, pitch};
+    UView<double, double> L{la + pd.vec_off, (long long)H * pitch, pitch};
+    double uA[3], uB[3], uC[3], uD[3], lA[3], lB[3], lC[3], lD[3];
+    U.at(x, y, uA); U.at(x + 1, y, uB); U.at(x + 1, y + 1, uC); U.at(x, y + 1, uD);
+    L.at(x, y, lA); L.at(x + 1, y, lB); L.at(x + 1, y + 1, lC); L.at(x, y + 1, lD);
+    const double k12 = 0.5 / 12.0, k3 = 0.5 / 3.0;
+    const int sc[6] = {0, 0, 0, 1, 1, 2}, sd[6] = {0, 1, 2, 1, 2, 2};
+    R* g0 = G + pd.frame_off + (long long)y * pitch + x;
+    for (int t = 0; t < 2; ++t) {
+        const double* um = t == 0 ? uB : uD;
+        const double* lm = t == 0 ? lB : lD;
+        double M[3][3], Ls[3], Us[3];
+        for (int c = 0; c < 3; ++c) {
+            Ls[c] = lA[c] + lm[c] + lC[c];
+            Us[c] = uA[c] + um[c] + uC[c];
+        }
+        for (int c = 0; c < 3; ++c)
+            for (int d = 0; d < 3; ++d)
+                M[c][d] = k12 * (lA[c] * uA[d] + lm[c] * um[d] + lC[c] * uC[d] + Ls[c] * Us[d]);
+        R* gp = g0 + (long long)(9 * t) * stride;
+        for (int k = 0; k < 6; ++k) {
+            const int c = sc[k], d = sd[k];
+            gp[k * stride] = (R)(c == d ? M[c][c] : M[c][d] + M[d][c]);
+        }
+        for (int c = 0; c < 3; ++c) gp[(6 + c) * stride] = (R)(-k3 * Ls[c]);
+    }
+}
+
+// dL/df2, dL/df1 with K_rho: as k_adjoint_frames, but dE/dg and dE/dft of
+// each element come from the K_rho^T-smoothed planes G of k_adjoint_eld:
+//   dE/dg_m = sum_k G_k d(g_c g_d)/dg_m - ft G_F,m,   dE/dft = -sum_c G_F,c g_c.
+template <typename R, typename O>
+__global__ void k_adjoint_frames_eld(const PairDesc* pairs, int pair, const R* __restrict__ f1a,
+                                     const R* __restrict__ f2a, const R* __restrict__ G, long long stride,
+                                     O* __restrict__ df2, O* __restrict__ df1, double gms_d) {
+    const PairDesc pd = pairs[pair];
+    const R gms = (R)gms_d;
+    const int W = pd.W, H = pd.H, pitch = pd.pitch;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W) return;
+    const R* f1 = f1a + pd.frame_off;
+    const R* f2 = f2a + pd.frame_off;
+    const int sqx[6] = {x, x, x - 1, x - 1, x - 1, x};
+    const int sqy[6] = {y, y, y - 1, y - 1, y, y - 1};
+    const int sqt[6] = {0, 1, 0, 1, 0, 1};
+    const R phx[6] = {-1, 0, 0, 1, 1, -1};
+    const R phy[6] = {0, -1, 1, 0, -1, 1};
+    const R third = R(1) / R(3);
+    R a2 = R(0), a1 = R(0);
+    for (int e = 0; e < 6; ++e) {
+        const int X = sqx[e], Y = sqy[e], t = sqt[e];
+        if (X < 0 || Y < 0 || X >= W - 1 || Y >= H - 1) continue;
+        const int mx = (t == 0) ? X + 1 : X, my = (t == 0) ? Y : Y + 1;
+        const int vx[3] = {X, mx, X + 1}, vy[3] = {Y, my, Y + 1};
+        R fa[3], fb[3];
+        for (int i = 0; i < 3; ++i) {
+            fa[i] = f1[(long long)vy[i] * pitch + vx[i]];
+            fb[i] = f2[(long long)vy[i] * pitch + vx[i]];
+        }
+        R g[3];
+        if (t == 0) { g[0] = fb[1] - fb[0]; g[1] = fb[2] - fb[1]; }
+        else        { g[0] = fb[2] - fb[1]; g[1] = fb[1] - fb[0]; }
+        g[2] = -(fa[0] + fa[1] + fa[2]) * third * gms;
+        const R ft = ((fb[0] - fa[0]) + (fb[1] - fa[1]) + (fb[2] - fa[2])) * third;
+        const R* gp = G + pd.frame_off + (long long)Y * pitch + X + (long long)(9 * t) * stride;
+        R Ga[6], GF[3];
+        for (int k = 0; k < 6; ++k) Ga[k] = gp[k * stride];
+        for (int c = 0; c < 3; ++c) GF[c] = gp[(6 + c) * stride];
+        // entries 00, 01, 02, 11, 12, 22
+        R dEdg[3];
+        dEdg[0] = R(2) * Ga[0] * g[0] + Ga[1] * g[1] + Ga[2] * g[2] - ft * GF[0];
+        dEdg[1] = Ga[1] * g[0] + R(2) * Ga[3] * g[1] + Ga[4] * g[2] - ft * GF[1];
+        dEdg[2] = Ga[2] * g[0] + Ga[4] * g[1] + R(2) * Ga[5] * g[2] - ft * GF[2];
+        const R dEdft = -(GF[0] * g[0] + GF[1] * g[1] + GF[2] * g[2]);
+        a2 -= dEdg[0] * phx[e] + dEdg[1] * phy[e] + dEdft * third;
+        a1 += (dEdg[2] * gms + dEdft) * third;
+    }
+    if (df2) df2[(long long)y * W + x] = (O)a2;
+    if (df1) df1[(long long)y * W + x] = (O)a1;
+}
+
+template <typename R, typename O>
+static cudaError_t adjoint_frames_eld(const AdaptBufs& A, int pair, int H, int W, const double* lamv, void* df2,
+                                      void* df1, int type, cudaStream_t st) {
+    dim3 ge((W - 1 + 127) / 128, H - 1);
+    k_adjoint_eld<R><<<ge, 128, 0, st>>>(A.pairs, pair, A.u, lamv, (R*)A.eldg, A.eld_stride);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t es = sizeof(R);
+    for (int q = 0; q < 18; ++q) {  // K_rho^T over each plane's (W-1) x (H-1) lattice
+        e = launch_smooth((char*)A.eldg + ((size_t)q * A.eld_stride + A.frame_off) * es, A.scratch, type, W - 1, H - 1,
+                          A.pitch, *A.taps_rho, true, st);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 gf((W + 127) / 128, H);
+    k_adjoint_frames_eld<R, O><<<gf, 128, 0, st>>>(A.pairs, pair, (const R*)A.f1, (const R*)A.f2, (const R*)A.eldg,
+                                                   A.eld_stride, (O*)df2, (O*)df1, A.gms);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint_grad(const AdaptBufs& A, int pair, int H, int W, const double* lamv, void* dalpha,
                                 void* df2, void* df1, int out_type, cudaStream_t st) {
     if (dalpha) {
@@ -336,6 +449,13 @@ cudaError_t launch_adjoint_grad(const AdaptBufs& A, int pair, int H, int W, cons
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+    }
+    if ((df2 || df1) && A.eld) {
+        if (A.fp64)
+            return out_type == T_F64 ? adjoint_frames_eld<double, double>(A, pair, H, W, lamv, df2, df1, T_F64, st)
+                                     : adjoint_frames_eld<double, float>(A, pair, H, W, lamv, df2, df1, T_F64, st);
+        return out_type == T_F64 ? adjoint_frames_eld<float, double>(A, pair, H, W, lamv, df2, df1, T_F32, st)
+                                 : adjoint_frames_eld<float, float>(A, pair, H, W, lamv, df2, df1, T_F32, st);
     }
     if (df2 || df1) {
         dim3 grid((W + 127) / 128, H);

@@ -31,6 +31,7 @@ struct of_ctx {
     ofl::SmoothTaps taps{};      // K_sigma (r = 0: none)
     ofl::SmoothTaps taps_rho{};  // K_rho (r = 0: none)
     void* eld = nullptr;         // K_rho element data: 18 planes of frame_elems values (rho > 0)
+    void* eldg = nullptr;        // K_rho adjoint work, same layout
     int fp64 = 1;
     size_t es = 8;  // storage element size (frames, alpha, inner vectors)
     std::vector<PairDesc> pd;
@@ -275,6 +276,8 @@ ofl::AdaptBufs adapt_bufs(of_ctx* h) {
     A.gms = h->opts.model == OF_MODEL_CONSTANT ? 0.0 : 1.0;
     A.eld = h->eld;
     A.eld_stride = h->frame_elems;
+    A.eldg = h->eldg;
+    A.taps_rho = &h->taps_rho;
     A.fp64 = h->fp64;
     return A;
 }
@@ -719,7 +722,11 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     CK(dalloc(h, &h->f1, fo * es));
     CK(dalloc(h, &h->f2, fo * es));
     h->eld = nullptr;
-    if (opt.rho > 0) CK(dalloc(h, &h->eld, 18 * fo * es));
+    h->eldg = nullptr;
+    if (opt.rho > 0) {
+        CK(dalloc(h, &h->eld, 18 * fo * es));
+        CK(dalloc(h, &h->eldg, 18 * fo * es));
+    }
     CK(dalloc(h, &h->alpha, 2 * fo * es));
     CK(dalloc(h, &h->eta, 2 * fo * es));
     CK(dalloc(h, &h->cell0, fo * (h->fp64 ? 32 : 8)));
@@ -1046,10 +1053,6 @@ of_status of_adjoint(of_handle h, void* const* dLdU, void* const* dLdalpha, void
     if (!h) return OF_ERR_ARG;
     if (!h->solved) return fail(h, OF_ERR_STATE, "of_adjoint needs a previous of_solve");
     if (!dLdU) return fail(h, OF_ERR_ARG, "null dL/dU list");
-    if (h->eld)
-        for (int p = 0; p < h->batch; ++p)
-            if ((dLdf2 && dLdf2[p]) || (dLdf1 && dLdf1[p]))
-                return fail(h, OF_ERR_ARG, "frame gradients through K_rho (rho > 0) are not provided; pass NULL");
     DevGuard g(h->device);
     cudaStream_t st = h->stream;
     CK(cudaEventRecord(h->ev0, st));
@@ -1074,6 +1077,9 @@ of_status of_adjoint(of_handle h, void* const* dLdU, void* const* dLdalpha, void
     ofl::AdaptBufs A = adapt_bufs(h);
     for (int p = 0; p < h->batch; ++p) {
         const PairDesc& d = h->pd[p];
+        A.frame_off = d.frame_off;  // K_rho^T passes: the pair's planes, its r vector as scratch
+        A.pitch = d.pitch;
+        A.scratch = (char*)h->r + d.vec_off * h->es;
         void* da = dLdalpha ? dLdalpha[p] : nullptr;
         void* d2 = dLdf2 ? dLdf2[p] : nullptr;
         void* d1 = dLdf1 ? dLdf1[p] : nullptr;

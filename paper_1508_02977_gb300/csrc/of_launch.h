@@ -153,6 +153,11 @@ struct AdaptBufs {
     double gms;
     const void* eld;      // K_rho element data or null
     long long eld_stride;
+    void* eldg;           // K_rho adjoint: 18 planes like eld (work)
+    void* scratch;        // one [H][pitch] plane of the pair (work of the K_rho^T passes)
+    const struct SmoothTaps* taps_rho;
+    long long frame_off;  // the pair's frame offset (set per call)
+    int pitch;
     int fp64;
 };
 cudaError_t launch_indicator(const AdaptBufs& A, int pair, int H, int W, cudaStream_t st);
