@@ -18,12 +18,18 @@ class Solver:
     """A handle set up for frames of one size (W, H), kept between calls."""
 
     def __init__(self, W: int, H: int, device: int = 0, precision: int = S.OF_PREC_MIXED, tile=(48, 48),
-                 overlap: int = 0, sweeps: int = 4, lam: float = 1.0, rtol: float = 1e-6, omega: float = 1.6):
+                 overlap: int = 0, sweeps: int = 4, lam: float = 1.0, rtol: float = 1e-6, omega: float = 1.6,
+                 sigma: float = 0.0, rho: float = 0.0, model: int = S.OF_MODEL_ILLUMINATION, coarse: int = 0):
+        """sigma, rho: K_sigma pre-smoothing and K_rho integration scales of
+        Section 1 (gradients are w.r.t. the frames given to forward);
+        model: OF_MODEL_ILLUMINATION or OF_MODEL_CONSTANT; coarse: two-level
+        preconditioner spacing (0: one level)."""
         self.W, self.H, self.rtol = int(W), int(H), float(rtol)
         self.precision = precision
         self.h = S.of_create(device)
         S.of_setup_grid(self.h, [(self.W, self.H)], tile=tile, overlap=overlap, sweeps=sweeps,
-                        precision=precision, lam=lam, omega=omega)
+                        precision=precision, lam=lam, omega=omega, sigma=sigma, rho=rho, model=model,
+                        coarse=coarse)
 
     def close(self):
         if self.h is not None:

@@ -833,15 +833,17 @@ def test_constant_model_mixed_texture(S, oracle):
     assert np.abs(U[:2] - Uo[:2]).max() <= 1e-4
 
 
-def test_autograd_function_matches_oracle_gradients(S, oracle):
+@pytest.mark.parametrize("rho", [0.0, 1.2])
+def test_autograd_function_matches_oracle_gradients(S, oracle, rho):
     """torch.autograd through OFSolve (FP64 handle): gradients of the mean
-    endpoint error w.r.t. alpha, f2 and f1 equal the oracle's adjoint."""
+    endpoint error w.r.t. alpha, f2 and f1 equal the oracle's adjoint
+    (rho > 0: through the K_rho element tensors)."""
     from paper_1508_02977_gb300.autograd import Solver, ofsolve_fn
     W, H = 30, 22
     f1, f2 = synth.random_frames(W, H, 301)
     alpha = synth.random_alpha(W, H, 302)
     gt = np.random.default_rng(303).uniform(-1, 1, (2, H, W))
-    solver = Solver(W, H, precision=S.OF_PREC_FP64, tile=(16, 16), sweeps=1, rtol=1e-14)
+    solver = Solver(W, H, precision=S.OF_PREC_FP64, tile=(16, 16), sweeps=1, rtol=1e-14, rho=rho)
     try:
         t1 = dev(f1).requires_grad_(True)
         t2 = dev(f2).requires_grad_(True)
@@ -852,10 +854,10 @@ def test_autograd_function_matches_oracle_gradients(S, oracle):
         loss.backward()
     finally:
         solver.close()
-    sysm = oracle.System.from_frames(f1, f2, alpha, 1.0)
+    sysm = oracle.System.from_frames(f1, f2, alpha, 1.0, rho=rho)
     Uo = sysm.solve_direct()
     Lo = sysm.solve_with(oracle.mean_epe_grad(Uo, gt))
-    da, d2, d1 = oracle.adjoint_grad(f1, f2, alpha, 1.0, Uo, Lo)
+    da, d2, d1 = oracle.adjoint_grad(f1, f2, alpha, 1.0, Uo, Lo, rho=rho)
     for got, want in ((ta.grad, da), (t2.grad, d2), (t1.grad, d1)):
         got = got.cpu().numpy()
         assert np.abs(got - want).max() <= 1e-8 * np.abs(want).max()
