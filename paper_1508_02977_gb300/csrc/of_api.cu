@@ -855,7 +855,7 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
         C.max_n0 = max_n0;
         int sms = 152;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-        C.gemv_grid = std::max(1, std::min(2 * sms, (max_n0 + 7) / 8));
+        C.gemv_grid = std::max(1, std::min(8 * sms, (max_n0 + 7) / 8));  // one row per warp
         CK(ofl::coarse_configure(fp64, max_n0, max_nx));
         C.on = 1;
     }

@@ -713,8 +713,7 @@ __global__ void __launch_bounds__(32) k_apply4(const ApplyParams<float, float, f
         P.partial[2 * (long long)bi.w + 1] = 0.0;
     }
     if (!arrive_last(&P.counter[pair], (unsigned)pd.nblk, &sh_last)) return;
-    double t0 = 0.0;
-    for (int i = lane; i < pd.nblk; i += 32) t0 += __ldcg(P.partial + 2 * (long long)(pd.blk0 + i));
+    double t0 = strided_sum8(P.partial + 2 * (long long)pd.blk0, pd.nblk, 2, lane, 32);
     t0 = warp_sum(t0);
     if (lane == 0) {
         PairScalars* s = P.sc + pair;

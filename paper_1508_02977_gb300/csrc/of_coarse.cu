@@ -660,13 +660,24 @@ __global__ void __launch_bounds__(256) k_coarse_restrict(const PairDesc* pairs, 
     for (int yy = warp; yy < ny; yy += nw) {
         const R* row = ra + pd.vec_off + (long long)(c.y0 + yy) * pd.pitch + c.x0;
         R s0[3] = {R(0), R(0), R(0)}, s1[3] = {R(0), R(0), R(0)};
-#pragma unroll 4
-        for (int xx = lane; xx < nx; xx += 32) {
-            const R wx = R(xx) * ix;
-            const R v0 = row[xx], v1 = row[xx + plane], v2 = row[xx + 2 * plane];
-            s0[0] += (R(1) - wx) * v0; s1[0] += wx * v0;
-            s0[1] += (R(1) - wx) * v1; s1[1] += wx * v1;
-            s0[2] += (R(1) - wx) * v2; s1[2] += wx * v2;
+        for (int x0 = 0; x0 < nx; x0 += 128) {
+            R v[4][3];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {  // the row's loads first
+                const int xx = x0 + lane + 32 * u;
+                if (xx < nx) { v[u][0] = row[xx]; v[u][1] = row[xx + plane]; v[u][2] = row[xx + 2 * plane]; }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int xx = x0 + lane + 32 * u;
+                if (xx >= nx) continue;
+                const R wx = R(xx) * ix;
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    s0[cc] += (R(1) - wx) * v[u][cc];
+                    s1[cc] += wx * v[u][cc];
+                }
+            }
         }
         const R wy = R(yy) * iy;
 #pragma unroll
@@ -730,6 +741,7 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(const CoarseParams P) {
         const bool active = (P.apply_only || !P.sc[pi].done) && (P.only_pair < 0 || P.only_pair == pi);
         if (!active) continue;  // uniform over the grid
         const R* gg = reinterpret_cast<const R*>(P.g) + cp.voff;
+#pragma unroll 8
         for (int u = threadIdx.x; u < cp.n0; u += blockDim.x) gs[u] = gg[u];
         __syncthreads();
         for (int row = blockIdx.x * nw + warp; row < cp.n0; row += gridDim.x * nw) {
@@ -740,7 +752,7 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(const CoarseParams P) {
                 const float4* c4 = reinterpret_cast<const float4*>(col);
                 const float4* g4 = reinterpret_cast<const float4*>(gs);
                 float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll 4
+#pragma unroll 8
                 for (int j = lane; j < (cp.n0 >> 2); j += 32) {
                     const float4 m = __ldg(c4 + j), q = g4[j];
                     a0 += m.x * q.x; a1 += m.y * q.y; a2 += m.z * q.z; a3 += m.w * q.w;
@@ -815,13 +827,22 @@ __global__ void __launch_bounds__(256) k_coarse_prolong(const PairDesc* pairs, c
             e0[cc] = (R(1) - wy) * yc[0][cc] + wy * yc[2][cc];
             e1[cc] = (R(1) - wy) * yc[1][cc] + wy * yc[3][cc];
         }
-#pragma unroll 4
-        for (int xx = lane; xx < nx; xx += 32) {
-            const R wx = R(xx) * ix;
-            const R z0 = row[xx], z1 = row[xx + plane], z2 = row[xx + 2 * plane];
-            row[xx] = z0 + ((R(1) - wx) * e0[0] + wx * e1[0]);
-            row[xx + plane] = z1 + ((R(1) - wx) * e0[1] + wx * e1[1]);
-            row[xx + 2 * plane] = z2 + ((R(1) - wx) * e0[2] + wx * e1[2]);
+        for (int x0 = 0; x0 < nx; x0 += 128) {
+            R zv[4][3];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {  // loads of the row before its stores
+                const int xx = x0 + lane + 32 * u;
+                if (xx < nx) { zv[u][0] = row[xx]; zv[u][1] = row[xx + plane]; zv[u][2] = row[xx + 2 * plane]; }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int xx = x0 + lane + 32 * u;
+                if (xx >= nx) continue;
+                const R wx = R(xx) * ix;
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc)
+                    row[xx + cc * plane] = zv[u][cc] + ((R(1) - wx) * e0[cc] + wx * e1[cc]);
+            }
         }
     }
 }

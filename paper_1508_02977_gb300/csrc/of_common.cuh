@@ -96,10 +96,24 @@ __device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned n, int* 
 }
 
 // Sum of n doubles (stride `stride`) in fixed order by one block.
+// This thread's share of p[i * stride], i = t, t + nt, ... < n: eight
+// accumulators (element k of the share goes to accumulator k mod 8) so that
+// eight loads are in flight, combined in a fixed order.
+__device__ __forceinline__ double strided_sum8(const double* p, int n, int stride, int t, int nt) {
+    double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int i = t;
+    for (; i + 7 * nt < n; i += 8 * nt) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] += __ldcg(p + (long long)(i + u * nt) * stride);
+    }
+#pragma unroll
+    for (int u = 0; u < 7; ++u)
+        if (i + u * nt < n) a[u] += __ldcg(p + (long long)(i + u * nt) * stride);
+    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+
 template <int NT> __device__ double ordered_sum(const double* p, int n, int stride, double* sh) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += NT) s += __ldcg(p + (long long)i * stride);
-    return block_sum<NT>(s, sh);
+    return block_sum<NT>(strided_sum8(p, n, stride, threadIdx.x, NT), sh);
 }
 
 }  // namespace ofk

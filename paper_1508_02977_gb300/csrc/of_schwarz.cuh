@@ -421,9 +421,7 @@ __device__ __forceinline__ double block_sum_rt(double v, double* sh) {
 }
 
 __device__ __forceinline__ double ordered_sum_rt(const double* p, int n, int stride, double* sh) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(p + (long long)i * stride);
-    return block_sum_rt(s, sh);
+    return block_sum_rt(strided_sum8(p, n, stride, threadIdx.x, blockDim.x), sh);
 }
 
 
