@@ -15,19 +15,29 @@
 
 namespace ofl {
 
-// sum of the weights of offsets lo..hi (prefix table cw[i] = w_0 + ... + w_{i-1},
-// w_j the weight of offset j - r)
-__device__ __forceinline__ double tap_sum(const SmoothTaps& T, int lo, int hi) { return T.cw[hi + T.r + 1] - T.cw[lo + T.r]; }
+// The taps in the storage type, staged in shared memory once per block (an
+// FP64 -> FP32 conversion per tap and output would run on the FP64 pipe).
+// tap_sum: the weights of offsets lo..hi from the prefix table
+// cw[i] = w_0 + ... + w_{i-1} (w_j the weight of offset j - r).
+template <typename D>
+__device__ __forceinline__ D tap_sum(const D* cw, int r, int lo, int hi) { return cw[hi + r + 1] - cw[lo + r]; }
 
 template <typename D, bool TRANS>
 __global__ void k_smooth_axis(const D* __restrict__ in, D* __restrict__ out, int W, int H, long long pitch, int axis,
                               const SmoothTaps T) {
+    __shared__ D sw[2 * OF_SMOOTH_RMAX + 1], scw[2 * OF_SMOOTH_RMAX + 2];
+    const int r = T.r;
+    for (int j = threadIdx.x; j <= 2 * r + 1; j += blockDim.x) {
+        if (j <= 2 * r) sw[j] = (D)T.w[j];
+        scw[j] = (D)T.cw[j];
+    }
+    __syncthreads();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= W) return;
     const int n = axis == 0 ? W : H;
     for (int y = blockIdx.y; y < H; y += gridDim.y) {
         const int pos = axis == 0 ? x : y;
-        const int lo = max(-T.r, -pos), hi = min(T.r, n - 1 - pos);
+        const int lo = max(-r, -pos), hi = min(r, n - 1 - pos);
         const long long step = axis == 0 ? 1 : pitch;
         const D* src = in + (long long)y * pitch + x;
         D acc = D(0);
@@ -35,11 +45,11 @@ __global__ void k_smooth_axis(const D* __restrict__ in, D* __restrict__ out, int
             D v = src[k * step];
             if (TRANS) {
                 const int q = pos + k;  // normaliser of the output position that tap feeds
-                v = v / (D)tap_sum(T, max(-T.r, -q), min(T.r, n - 1 - q));
+                v = v / tap_sum<D>(scw, r, max(-r, -q), min(r, n - 1 - q));
             }
-            acc += (D)T.w[k + T.r] * v;
+            acc += sw[k + r] * v;
         }
-        if (!TRANS) acc = acc / (D)tap_sum(T, lo, hi);
+        if (!TRANS) acc = acc / tap_sum<D>(scw, r, lo, hi);
         out[(long long)y * pitch + x] = acc;
     }
 }
