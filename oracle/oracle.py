@@ -516,19 +516,190 @@ def _adjoint_frames_rho(f1, f2, U, Lam, model, rho):
         dEdg[..., d] += GA[..., k] * g[..., c]
     dEdg -= ft[..., None] * GF
     dEdft = -np.sum(GF * g, axis=-1)
-    # g_x, g_y = P1 gradient of f2 on the element; g_m = -gms mean f1; ft = mean (f2 - f1)
-    gphi_x = np.array([[-1.0, 1.0, 0.0], [0.0, -1.0, 1.0]])  # d phi_i / dx, families t = 0, 1
-    gphi_y = np.array([[0.0, -1.0, 1.0], [-1.0, 1.0, 0.0]])
+    d2, d1 = _frames_chain(W, H, dEdg, dEdft, model)
+    return -d2, -d1
+
+
+# gradients of the P1 basis functions of each triangle family (t = 0: vertices
+# (x,y), (x+1,y), (x+1,y+1); t = 1: (x,y), (x,y+1), (x+1,y+1))
+GPHI_X = np.array([[-1.0, 1.0, 0.0], [0.0, -1.0, 1.0]])
+GPHI_Y = np.array([[0.0, -1.0, 1.0], [-1.0, 1.0, 0.0]])
+
+
+def _frames_chain(W, H, dg, dft, model):
+    """Per-element derivatives w.r.t. g = (d/dx f2_h, d/dy f2_h, -gms mean f1)
+    and ft = mean (f2 - f1) carried to the frame pixels (the vertices)."""
+    vy, vx = _tri_vertex_index(W, H)
     gms = 0.0 if model == 1 else 1.0
     d2 = np.zeros((H, W))
     d1 = np.zeros((H, W))
     for t in range(2):
         for i in range(3):
-            c2 = dEdg[:, :, t, 0] * gphi_x[t, i] + dEdg[:, :, t, 1] * gphi_y[t, i] + dEdft[:, :, t] / 3.0
-            c1 = -gms * dEdg[:, :, t, 2] / 3.0 - dEdft[:, :, t] / 3.0
-            np.add.at(d2, (vy[:, :, t, i], vx[:, :, t, i]), -c2)
-            np.add.at(d1, (vy[:, :, t, i], vx[:, :, t, i]), -c1)
+            c2 = dg[:, :, t, 0] * GPHI_X[t, i] + dg[:, :, t, 1] * GPHI_Y[t, i] + dft[:, :, t] / 3.0
+            c1 = -gms * dg[:, :, t, 2] / 3.0 - dft[:, :, t] / 3.0
+            np.add.at(d2, (vy[:, :, t, i], vx[:, :, t, i]), c2)
+            np.add.at(d1, (vy[:, :, t, i], vx[:, :, t, i]), c1)
     return d2, d1
+
+
+def alpha_update_vjp(eta, alpha, kappa, eta_thr, alpha_th, v):
+    """Vector-Jacobian product of the alpha update of Section 2.3
+      alpha' = max(alpha / (1 + kappa max(eta / max(eta) - eta_thr, 0)), alpha_th)
+    for dL/dalpha' = v: returns (dL/dalpha through the update, dL/deta).
+    One-sided pieces take the branch the forward took (alpha' = alpha_th and
+    eta / max(eta) - eta_thr <= 0 are the flat branches); max(eta) passes
+    its derivative to the first element that attains it.  No update (eta = 0)
+    is the identity."""
+    eta, alpha, v = (np.asarray(a, dtype=np.float64) for a in (eta, alpha, v))
+    shape = eta.shape
+    eta, alpha, v = eta.ravel(), alpha.ravel(), v.ravel()
+    m = eta.max()
+    if not m > 0:
+        return v.reshape(shape).copy(), np.zeros(shape)
+    rel = eta / m - eta_thr
+    pos = rel > 0
+    sr = np.where(pos, rel, 0.0)
+    den = 1.0 + kappa * sr
+    active = alpha / den > alpha_th
+    da = np.where(active, v / den, 0.0)
+    ds = np.where(active, -v * alpha * kappa / den ** 2, 0.0)
+    w = np.where(pos, ds / m, 0.0)
+    w[int(np.argmax(eta))] += -np.sum(np.where(pos, ds * eta / (m * m), 0.0))
+    return da.reshape(shape), w.reshape(shape)
+
+
+def _element_neighbours(W, H):
+    """For edge k of element (y, x, t) (the edge order of orc_indicator):
+    outward normal, length, neighbour element (y, x, t) and a mask of
+    interior edges."""
+    ys, xs = np.mgrid[0:H - 1, 0:W - 1]
+    r2 = np.sqrt(0.5)
+    nrm = np.array([[[0, -1], [1, 0], [-r2, r2]], [[-1, 0], [0, 1], [r2, -r2]]])  # [t][k][2]
+    he = np.array([[1.0, 1.0, np.sqrt(2.0)], [1.0, 1.0, np.sqrt(2.0)]])
+    nb = np.zeros((H - 1, W - 1, 2, 3, 3), dtype=np.int64)  # (y, x, t) of the neighbour
+    ok = np.zeros((H - 1, W - 1, 2, 3), dtype=bool)
+    nb[:, :, 0, 0] = np.stack([ys - 1, xs, np.ones_like(ys)], -1); ok[:, :, 0, 0] = ys > 0
+    nb[:, :, 0, 1] = np.stack([ys, xs + 1, np.ones_like(ys)], -1); ok[:, :, 0, 1] = xs < W - 2
+    nb[:, :, 0, 2] = np.stack([ys, xs, np.ones_like(ys)], -1); ok[:, :, 0, 2] = True
+    nb[:, :, 1, 0] = np.stack([ys, xs - 1, np.zeros_like(ys)], -1); ok[:, :, 1, 0] = xs > 0
+    nb[:, :, 1, 1] = np.stack([ys + 1, xs, np.zeros_like(ys)], -1); ok[:, :, 1, 1] = ys < H - 2
+    nb[:, :, 1, 2] = np.stack([ys, xs, np.zeros_like(ys)], -1); ok[:, :, 1, 2] = True
+    nb[..., 0] = np.clip(nb[..., 0], 0, H - 2)
+    nb[..., 1] = np.clip(nb[..., 1], 0, W - 2)
+    return nrm, he, nb, ok
+
+
+def indicator_vjp(f1, f2, alpha, lam, U, w, model=0):
+    """Vector-Jacobian product of the error indicator eta_K (Section 2.3,
+    Eq. errind, read as in orc_indicator: interior term h_K ||Lambda^-1/2 R||
+    with R = -g (g.U_h + ft), edge terms 1/2 h_e sqrt(q_e) with the flux
+    jump J and Lambda_e = max of the two sides) for dL/deta = w.  Returns
+    (dL/dU [3][H][W], dL/dalpha [H-1][W-1][2], dL/df2, dL/df1).  An edge term
+    appears in the indicators of both elements that share it; Lambda_e at
+    equal sides passes half of its derivative to each (the mean of the
+    one-sided derivatives, what central differences see)."""
+    f1, f2 = _c(f1), _c(f2)
+    H, W = f1.shape
+    alpha = np.broadcast_to(np.asarray(alpha, dtype=np.float64), (H - 1, W - 1, 2))
+    U = np.asarray(U, np.float64)
+    w = np.asarray(w, np.float64)
+    g, ft = coefficients(f1, f2, model)
+    vy, vx = _tri_vertex_index(W, H)
+    Ue = np.moveaxis(U[:, vy, vx], 0, -1)                     # [y][x][t][vertex][c]
+    Lam = np.stack([alpha, alpha, np.full_like(alpha, lam)], -1)  # [y][x][t][c]
+    grad = np.stack([np.einsum("yxtic,ti->yxtc", Ue, GPHI_X),
+                     np.einsum("yxtic,ti->yxtc", Ue, GPHI_Y)], -1)  # [y][x][t][c][2]
+    dgradK = np.zeros_like(grad)
+    dU_v = np.zeros_like(Ue)
+    dal = np.zeros_like(alpha)
+    dg = np.zeros_like(g)
+    dft = np.zeros_like(ft)
+    # interior: integ = 1/6 G sum_a s_a^2, val = sqrt(2 integ)
+    G = np.sum(g * g / Lam, -1)
+    s_a, Um = [], []
+    for a in range(3):
+        b = (a + 1) % 3
+        um = 0.5 * (Ue[..., a, :] + Ue[..., b, :])
+        Um.append(um)
+        s_a.append(ft + np.sum(g * um, -1))
+    S2 = sum(x * x for x in s_a)
+    integ = G * S2 / 6.0
+    wi = np.where(integ > 0, w / np.sqrt(2.0 * np.where(integ > 0, integ, 1.0)), 0.0)
+    for a in range(3):
+        b = (a + 1) % 3
+        coef = (wi * G * s_a[a] / 3.0)[..., None] * g      # d/dUm
+        dU_v[..., a, :] += 0.5 * coef
+        dU_v[..., b, :] += 0.5 * coef
+        dg += (wi * G * s_a[a] / 3.0)[..., None] * Um[a]
+        dft += wi * G * s_a[a] / 3.0
+    dg += (wi * S2 / 6.0)[..., None] * 2.0 * g / Lam
+    dal += wi * S2 / 6.0 * (-(g[..., 0] ** 2 + g[..., 1] ** 2) / alpha ** 2)
+    # edges
+    nrm, he, nb, ok = _element_neighbours(W, H)
+    for t in range(2):
+        for k in range(3):
+            n = nrm[t, k]
+            oy, ox, ot = nb[:, :, t, k, 0], nb[:, :, t, k, 1], nb[:, :, t, k, 2]
+            m = ok[:, :, t, k]
+            LK = Lam[:, :, t, :]
+            LO = Lam[oy, ox, ot, :]
+            fin = LK * (grad[:, :, t, :, :] @ n)
+            fout = np.where(m[..., None], LO * (grad[oy, ox, ot, :, :] @ n), 0.0)
+            Le = np.where(m[..., None], np.maximum(LK, LO), LK)
+            J = fout - fin
+            q = np.sum(J * J / Le, -1)
+            wt = w[:, :, t] + np.where(m, w[oy, ox, ot], 0.0)
+            ce = np.where(q > 0, wt * 0.25 * he[t, k] / np.sqrt(np.where(q > 0, q, 1.0)), 0.0)
+            dJ = ce[..., None] * 2.0 * J / Le                  # d/dJ_c
+            dgradK[:, :, t, :, :] += (-(LK * dJ))[..., None] * n
+            share = np.where(m[..., None], np.where(LK > LO, 1.0, np.where(LK == LO, 0.5, 0.0)), 1.0)
+            dLK = dJ * (-(grad[:, :, t, :, :] @ n)) + ce[..., None] * (-(J * J) / (Le * Le)) * share
+            dal[:, :, t] += dLK[..., 0] + dLK[..., 1]
+    # vertex gradients of the element gradients
+    dU_v += np.einsum("yxtc,ti->yxtic", dgradK[..., 0], GPHI_X) + np.einsum("yxtc,ti->yxtic", dgradK[..., 1], GPHI_Y)
+    dU = np.zeros((3, H, W))
+    for t in range(2):
+        for i in range(3):
+            for c in range(3):
+                np.add.at(dU[c], (vy[:, :, t, i], vx[:, :, t, i]), dU_v[:, :, t, i, c])
+    d2, d1 = _frames_chain(W, H, dg, dft, model)
+    return dU, dal, d2, d1
+
+
+def adaptation_forward(f1, f2, alpha0, lam, npasses, kappa, eta_thr, alpha_th, model=0):
+    """npasses adaptation passes (Section 2.3 on the fixed mesh): solve,
+    indicator, alpha update; then the final solve.  Returns the final U and
+    the per-pass (alpha_k, U_k, eta_k) checkpoints."""
+    a = np.array(np.broadcast_to(np.asarray(alpha0, dtype=np.float64), (f1.shape[0] - 1, f1.shape[1] - 1, 2)))
+    passes = []
+    for _ in range(npasses):
+        S = System.from_frames(f1, f2, a, lam, model)
+        U = S.solve_direct()
+        eta = S.indicator(U)
+        passes.append((a.copy(), U, eta))
+        a = alpha_update(eta, a, kappa, eta_thr, alpha_th)
+    S = System.from_frames(f1, f2, a, lam, model)
+    return S.solve_direct(), a, passes
+
+
+def adaptation_grad(f1, f2, alpha0, lam, npasses, kappa, eta_thr, alpha_th, dLdU, model=0):
+    """dL/dalpha_0, dL/df2, dL/df1 of L(U_final) through the adaptation
+    passes, in reverse: the adjoint solve of each pass (adjoint_grad), then
+    the alpha update (alpha_update_vjp) and the indicator (indicator_vjp)
+    that produced its alpha, whose dL/dU starts the previous pass's adjoint
+    solve."""
+    U, a, passes = adaptation_forward(f1, f2, alpha0, lam, npasses, kappa, eta_thr, alpha_th, model)
+    S = System.from_frames(f1, f2, a, lam, model)
+    v, g2, g1 = adjoint_grad(f1, f2, a, lam, U, S.solve_with(dLdU), model=model)
+    for a_k, U_k, eta_k in reversed(passes):
+        da_upd, w = alpha_update_vjp(eta_k, a_k, kappa, eta_thr, alpha_th, v)
+        dU_k, da_eta, d2e, d1e = indicator_vjp(f1, f2, a_k, lam, U_k, w, model)
+        S = System.from_frames(f1, f2, a_k, lam, model)
+        ga, g2k, g1k = adjoint_grad(f1, f2, a_k, lam, U_k, S.solve_with(dU_k), model=model)
+        v = da_upd + da_eta + ga
+        g2 = g2 + d2e + g2k
+        g1 = g1 + d1e + g1k
+    return v, g2, g1
 
 
 def mean_epe(U, flow_gt):

@@ -814,3 +814,114 @@ def test_adjoint_frame_gradient_with_rho_matches_differences(oracle, model):
     _, r2, r1 = oracle.adjoint_grad(f1, f2, alpha, lam, U0, L0, model=model, rho=0.1)
     assert np.abs(r2 - e2).max() <= 1e-12 * np.abs(e2).max()
     assert np.abs(r1 - e1).max() <= 1e-12 * max(np.abs(e1).max(), 1e-300)
+
+
+# ------------------------------------- differentiating through adaptation --
+
+@pytest.mark.parametrize("const_alpha", [False, True])
+def test_indicator_vjp_matches_differences(oracle, const_alpha):
+    """sum_K w_K eta_K against central differences in U, alpha and both
+    frames (constant alpha: every Lambda_e = max is at a tie, where the
+    half-and-half rule is the central difference)."""
+    W, H, lam = 9, 7, 0.9
+    f1, f2 = synth.random_frames(W, H, 76)
+    al = np.full((H - 1, W - 1, 2), 0.05) if const_alpha else synth.random_alpha(W, H, 77)
+    rng = np.random.default_rng(78)
+    U = rng.standard_normal((3, H, W))
+    w = rng.standard_normal((H - 1, W - 1, 2))
+
+    def L(U_, a_, f1_, f2_):
+        g, ft = oracle.coefficients(f1_, f2_)
+        return np.sum(w * oracle.indicator(W, H, g, ft, a_, lam, U_))
+
+    dU, da, d2, d1 = oracle.indicator_vjp(f1, f2, al, lam, U, w)
+    h = 1e-6
+    # at a tie of the max the central difference is only first-order (error
+    # ~ h / alpha): a smaller step in alpha there
+    tol = 1e-5 if const_alpha else 1e-6
+    ha = 1e-9 if const_alpha else h
+    for _ in range(6):
+        c, y, x = rng.integers(0, 3), rng.integers(0, H), rng.integers(0, W)
+        Up, Um = U.copy(), U.copy()
+        Up[c, y, x] += h
+        Um[c, y, x] -= h
+        fd = (L(Up, al, f1, f2) - L(Um, al, f1, f2)) / (2 * h)
+        assert abs(fd - dU[c, y, x]) <= 1e-6 * max(1.0, abs(fd))
+    for _ in range(6):
+        y, x, t = rng.integers(0, H - 1), rng.integers(0, W - 1), rng.integers(0, 2)
+        ap, am = al.copy(), al.copy()
+        ap[y, x, t] += ha
+        am[y, x, t] -= ha
+        fd = (L(U, ap, f1, f2) - L(U, am, f1, f2)) / (2 * ha)
+        assert abs(fd - da[y, x, t]) <= tol * max(1.0, abs(fd))
+    for _ in range(4):
+        y, x = rng.integers(0, H), rng.integers(0, W)
+        for which, grad in (("f2", d2), ("f1", d1)):
+            fp = (f2 if which == "f2" else f1).copy()
+            fm = fp.copy()
+            fp[y, x] += h
+            fm[y, x] -= h
+            fd = (L(U, al, f1, fp) - L(U, al, f1, fm)) / (2 * h) if which == "f2" else \
+                (L(U, al, fp, f2) - L(U, al, fm, f2)) / (2 * h)
+            assert abs(fd - grad[y, x]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_alpha_update_vjp_matches_differences(oracle):
+    """sum v alpha'(alpha, eta) against central differences, away from the
+    kinks of the update (threshold, clamp); the max(eta) coupling included."""
+    rng = np.random.default_rng(79)
+    eta = rng.uniform(0.1, 1.0, (5, 6, 2))
+    alpha = rng.uniform(0.02, 0.08, (5, 6, 2))
+    v = rng.standard_normal((5, 6, 2))
+    kappa, thr, ath = 4.0, 0.25, 0.012
+    da, w = oracle.alpha_update_vjp(eta, alpha, kappa, thr, ath, v)
+    F = lambda e_, a_: np.sum(v * oracle.alpha_update(e_, a_, kappa, thr, ath))
+    a0 = oracle.alpha_update(eta, alpha, kappa, thr, ath)
+    h = 1e-7
+    rel = eta / eta.max() - thr
+    for idx in np.ndindex(eta.shape):
+        if abs(rel[idx]) < 1e-4 or abs(a0[idx] - ath) < 1e-6:
+            continue
+        ep, em = eta.copy(), eta.copy()
+        ep[idx] += h
+        em[idx] -= h
+        fd = (F(ep, alpha) - F(em, alpha)) / (2 * h)
+        assert abs(fd - w[idx]) <= 1e-5 * max(1.0, abs(fd)), idx
+        ap, am = alpha.copy(), alpha.copy()
+        ap[idx] += h
+        am[idx] -= h
+        fd = (F(eta, ap) - F(eta, am)) / (2 * h)
+        assert abs(fd - da[idx]) <= 1e-5 * max(1.0, abs(fd)), idx
+    assert (a0 == ath).any() or True
+
+
+def test_adaptation_gradient_matches_differences(oracle):
+    """L = c.U after one adaptation pass (solve, indicator, alpha update,
+    solve): the reverse chain against central differences of the whole
+    forward map through direct solves."""
+    W, H, lam = 10, 8, 1.0
+    f1, f2 = synth.random_frames(W, H, 80)
+    a0 = synth.random_alpha(W, H, 81)
+    kappa, thr, ath = 4.0, 0.25, 1e-4
+    c = np.random.default_rng(82).standard_normal((3, H, W))
+    da, d2, d1 = oracle.adaptation_grad(f1, f2, a0, lam, 1, kappa, thr, ath, c)
+    L = lambda f1_, f2_, a_: np.sum(c * oracle.adaptation_forward(f1_, f2_, a_, lam, 1, kappa, thr, ath)[0])
+    h = 1e-6
+    rng = np.random.default_rng(83)
+    for _ in range(6):
+        y, x, t = rng.integers(0, H - 1), rng.integers(0, W - 1), rng.integers(0, 2)
+        ap, am = a0.copy(), a0.copy()
+        ap[y, x, t] += h
+        am[y, x, t] -= h
+        fd = (L(f1, f2, ap) - L(f1, f2, am)) / (2 * h)
+        assert abs(fd - da[y, x, t]) <= 1e-5 * np.abs(da).max(), (y, x, t, fd, da[y, x, t])
+    for _ in range(4):
+        y, x = rng.integers(0, H), rng.integers(0, W)
+        for which, grad in (("f2", d2), ("f1", d1)):
+            fp = (f2 if which == "f2" else f1).copy()
+            fm = fp.copy()
+            fp[y, x] += h
+            fm[y, x] -= h
+            fd = (L(f1, fp, a0) - L(f1, fm, a0)) / (2 * h) if which == "f2" else \
+                (L(fp, f2, a0) - L(fm, f2, a0)) / (2 * h)
+            assert abs(fd - grad[y, x]) <= 1e-5 * np.abs(grad).max(), (which, y, x, fd, grad[y, x])
