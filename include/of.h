@@ -186,6 +186,24 @@ of_status of_solve(of_handle h, const of_solve_opts *o, void *const *U, of_dtype
  * receives eta_K before the update. */
 of_status of_adapt_alpha(of_handle h, double kappa, double eta_thr, double alpha_th, void *const *eta, of_dtype dt);
 
+/* Vector-jacobian product of one adaptation pass (Section 2.3): the map
+ * (alpha, U, f1, f2) -> alpha_new = update(alpha, eta(U, alpha, f)) of
+ * of_adapt_alpha, linearised at the current alpha and the solution of the
+ * last of_solve (which must belong to it; alpha is not changed).  Given
+ * dLdalpha_new[p] ([H-1][W-1][2]) it writes dLdalpha[p] (same shape, the
+ * part through the update and the indicator), dLdU[p] ([3][H][W]) and, if
+ * not NULL, dLdf2[p], dLdf1[p] ([H][W]; w.r.t. the images given to
+ * of_set_frames when sigma > 0).  The flat branches of the update pass
+ * nothing, max(eta) passes its derivative to the first element attaining
+ * it, and Lambda_e = max of the two sides of an edge passes half to each
+ * at a tie.  Chained with of_adjoint (dL/dU of the pass as its input), this
+ * differentiates a loss through any number of passes from per-pass
+ * checkpoints of alpha and U.  Device arrays only; rho must be 0.
+ * Synchronises the stream. */
+of_status of_adapt_alpha_vjp(of_handle h, double kappa, double eta_thr, double alpha_th,
+                             void *const *dLdalpha_new, void *const *dLdalpha, void *const *dLdU,
+                             void *const *dLdf2, void *const *dLdf1, of_dtype dt);
+
 /* Gradients of a scalar loss L(U) through the solve (implicit
  * differentiation of A(theta) U = b(theta)): solves A Lam = dL/dU (A is
  * symmetric, so the adjoint system is the same operator) with the options

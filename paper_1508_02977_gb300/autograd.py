@@ -90,3 +90,78 @@ class OFSolve(torch.autograd.Function):
 
 def ofsolve_fn(f1, f2, alpha, solver: Solver):
     return OFSolve.apply(f1, f2, alpha, solver)
+
+
+class OFAdaptSolve(torch.autograd.Function):
+    """U_K after `npasses` adaptation passes (Section 2.3 on the fixed mesh:
+    solve, error indicator, alpha update) and a final solve, differentiated
+    through every pass.  Forward keeps a checkpoint (alpha_k, U_k) per pass;
+    backward walks them in reverse: re-establish pass k (alpha_k and a warm
+    solve from U_k, which converges at once), of_adjoint for the solve, then
+    of_adapt_alpha_vjp for the indicator and update that produced
+    alpha_{k+1}; its dL/dU_k is the next adjoint's input."""
+
+    @staticmethod
+    def forward(ctx, f1, f2, alpha0, solver: Solver, npasses: int, kappa: float, eta_thr: float,
+                alpha_th: float):
+        dt = torch.float64 if solver.precision == S.OF_PREC_FP64 else torch.float32
+        dev = f1.device
+        f1c = f1.detach().to(dt).contiguous()
+        f2c = f2.detach().to(dt).contiguous()
+        S.of_set_frames(solver.h, 0, f1c, f2c)
+        a = alpha0.detach().to(torch.float64).contiguous()
+        ckpt = []
+        for _ in range(int(npasses)):
+            S.of_set_alpha(solver.h, 0, a.to(dt).contiguous())
+            Uk = torch.zeros(3, solver.H, solver.W, dtype=torch.float64, device=dev)
+            S.of_solve(solver.h, [Uk], rtol=solver.rtol)
+            S.of_adapt_alpha(solver.h, kappa, eta_thr, alpha_th)
+            a_next = torch.zeros_like(a)
+            S.of_get_alpha(solver.h, 0, a_next)
+            ckpt.append((a, Uk))
+            a = a_next
+        S.of_set_alpha(solver.h, 0, a.to(dt).contiguous())
+        U = torch.zeros(3, solver.H, solver.W, dtype=torch.float64, device=dev)
+        S.of_solve(solver.h, [U], rtol=solver.rtol)
+        ctx.solver, ctx.ckpt, ctx.final = solver, ckpt, (a, U.clone())
+        ctx.frames = (f1c, f2c)
+        ctx.params = (float(kappa), float(eta_thr), float(alpha_th))
+        ctx.in_dtypes = (f1.dtype, f2.dtype, alpha0.dtype)
+        return U.to(f1.dtype)
+
+    @staticmethod
+    def backward(ctx, gU):
+        solver = ctx.solver
+        dt = torch.float64 if solver.precision == S.OF_PREC_FP64 else torch.float32
+        dev = gU.device
+        kappa, thr, ath = ctx.params
+        S.of_set_frames(solver.h, 0, *ctx.frames)
+
+        def at_pass(a, Uk):  # alpha_k and the solution that belongs to it
+            S.of_set_alpha(solver.h, 0, a.to(dt).contiguous())
+            Uw = Uk.clone()
+            S.of_solve(solver.h, [Uw], rtol=solver.rtol, warm_start=True)
+
+        H, W = solver.H, solver.W
+        z_a = lambda: torch.zeros(H - 1, W - 1, 2, dtype=torch.float64, device=dev)
+        z_f = lambda: torch.zeros(H, W, dtype=torch.float64, device=dev)
+        a, U = ctx.final
+        at_pass(a, U)
+        v, d2, d1 = z_a(), z_f(), z_f()
+        S.of_adjoint(solver.h, [gU.detach().to(torch.float64).contiguous()], [v], [d2], [d1])
+        for a, Uk in reversed(ctx.ckpt):
+            at_pass(a, Uk)
+            da, e2, e1 = z_a(), z_f(), z_f()
+            dU = torch.zeros(3, H, W, dtype=torch.float64, device=dev)
+            S.of_adapt_alpha_vjp(solver.h, kappa, thr, ath, [v], [da], [dU], [e2], [e1])
+            ga, g2, g1 = z_a(), z_f(), z_f()
+            S.of_adjoint(solver.h, [dU], [ga], [g2], [g1])
+            v = da + ga
+            d2 = d2 + e2 + g2
+            d1 = d1 + e1 + g1
+        t1, t2, ta = ctx.in_dtypes
+        return d1.to(t1), d2.to(t2), v.to(ta), None, None, None, None, None
+
+
+def adapt_solve_fn(f1, f2, alpha0, solver: Solver, npasses: int, kappa: float, eta_thr: float, alpha_th: float):
+    return OFAdaptSolve.apply(f1, f2, alpha0, solver, npasses, kappa, eta_thr, alpha_th)

@@ -436,6 +436,271 @@ static cudaError_t adjoint_frames_eld(const AdaptBufs& A, int pair, int H, int W
     return cudaGetLastError();
 }
 
+// ------------------------------------------ through the adaptation pass --
+// Vector-Jacobian products of one adaptation pass (indicator, then alpha
+// update) for dL/dalpha_new = v, in FP64.
+//
+// Update: alpha' = max(alpha / (1 + kappa s), alpha_th), s = max(eta / m -
+// eta_thr, 0), m = max eta.  The flat branches (alpha' = alpha_th, s = 0)
+// pass nothing; m passes sum_K dL/ds_K (-eta_K / m^2) to the first element
+// that attains it.  w = dL/deta, da = dL/dalpha through the update.
+template <typename R, typename O>
+__global__ void k_update_vjp(const PairDesc* pairs, int pair, const R* __restrict__ ala, const R* __restrict__ etaa,
+                             const unsigned long long* __restrict__ etamax_bits, const O* __restrict__ v,
+                             O* __restrict__ da, double* __restrict__ wa, double kappa, double eta_thr,
+                             double alpha_th, double* __restrict__ part, unsigned long long* __restrict__ argmax) {
+    __shared__ double sh[32];
+    const PairDesc pd = pairs[pair];
+    const int W = pd.W, H = pd.H, pitch = pd.pitch;
+    const R* al_p = ala + 2 * pd.frame_off;
+    const R* eta_p = etaa + 2 * pd.frame_off;
+    double* w = wa + 2 * pd.frame_off;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const double m = __longlong_as_double((long long)etamax_bits[pair]);
+    double acc = 0.0;
+    if (x < W - 1 && y < H - 1) {
+        for (int t = 0; t < 2; ++t) {
+            const long long o = 2 * ((long long)y * pitch + x) + t;        // workspace layout
+            const long long od = 2 * ((long long)y * (W - 1) + x) + t;     // dense [H-1][W-1][2]
+            const double vv = (double)v[od];
+            if (!(m > 0.0)) {  // no update happened: identity
+                da[od] = (O)vv;
+                w[o] = 0.0;
+                continue;
+            }
+            const double eta = (double)eta_p[o], al = (double)al_p[o];
+            const double rel = eta / m - eta_thr;
+            const bool pos = rel > 0.0;
+            const double den = 1.0 + kappa * (pos ? rel : 0.0);
+            const bool active = al / den > alpha_th;
+            da[od] = (O)(active ? vv / den : 0.0);
+            const double ds = active ? -vv * al * kappa / (den * den) : 0.0;
+            w[o] = pos ? ds / m : 0.0;
+            if (pos) acc += ds * eta / (m * m);
+            if (eta == m) atomicMin(argmax, (unsigned long long)(((long long)y * (W - 1) + x) * 2 + t));
+        }
+    }
+    acc = block_sum<128>(acc, sh);
+    if (threadIdx.x == 0) part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = acc;
+}
+
+// the max(eta) term: w[argmax] -= sum of the block partials (fixed order)
+__global__ void k_update_vjp_max(const PairDesc* pairs, int pair, const unsigned long long* __restrict__ etamax_bits,
+                                 const double* __restrict__ part, int nparts,
+                                 const unsigned long long* __restrict__ argmax, double* __restrict__ wa) {
+    __shared__ double sh[32];
+    const PairDesc pd = pairs[pair];
+    const double m = __longlong_as_double((long long)etamax_bits[pair]);
+    const double s = ordered_sum<256>(part, nparts, 1, sh);
+    const unsigned long long ne = 2ULL * (pd.W - 1) * (pd.H - 1);
+    if (threadIdx.x == 0 && m > 0.0 && *argmax < ne) {
+        const unsigned long long e = *argmax, sq = e >> 1;
+        const int t = (int)(e & 1), x = (int)(sq % (pd.W - 1)), y = (int)(sq / (pd.W - 1));
+        wa[2 * (pd.frame_off + (long long)y * pd.pitch + x) + t] -= s;
+    }
+}
+
+// Indicator: per element K, its share of sum_K' w_K' eta_K' with respect to
+// its own unknowns (Eq. errind as the forward kernel reads it):
+//   interior  sqrt(2 integ), integ = G sum_a s_a^2 / 6:  d/dU of its vertices,
+//             d/dalpha_K through G, d/dg and d/dft;
+//   each edge 1/2 h_e sqrt(q_e) appears in the indicators of both elements
+//             that share it, so with c_e = (w_K + w_O) h_e / (4 sqrt(q_e))
+//             each side differentiates q_e with respect to its own flux
+//             (J = out - in) and its own alpha (in J and in Lambda_e = max,
+//             half the derivative to each side at a tie).
+// Writes per element and triangle 13 values: dL/dU at its 3 vertices (3
+// components each) and (dg_0, dg_1, dg_2, dft); adds dL/dalpha_K to da.
+template <typename R, typename O>
+__global__ void k_eta_vjp(const PairDesc* pairs, int pair, const R* __restrict__ f1a, const R* __restrict__ f2a,
+                          const R* __restrict__ ala, const double* __restrict__ ua, const double* __restrict__ w,
+                          double lam, double gms, O* __restrict__ da, double* __restrict__ buf, long long stride) {
+    const PairDesc pd = pairs[pair];
+    const int W = pd.W, H = pd.H, pitch = pd.pitch;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W - 1 || y >= H - 1) return;
+    const R* f1 = f1a + pd.frame_off;
+    const R* f2 = f2a + pd.frame_off;
+    const R* al = ala + 2 * pd.frame_off;
+    const double* wp = w + 2 * pd.frame_off;
+    UView<double, double> U{ua + pd.vec_off, (long long)H * pitch, pitch};
+    auto F1 = [&](int xx, int yy) { return (double)f1[(long long)yy * pitch + xx]; };
+    auto F2 = [&](int xx, int yy) { return (double)f2[(long long)yy * pitch + xx]; };
+    auto AL = [&](int xx, int yy, int t) { return (double)al[2 * ((long long)yy * pitch + xx) + t]; };
+    auto WW = [&](int xx, int yy, int t) { return wp[2 * ((long long)yy * pitch + xx) + t]; };
+    double uA[3], uB[3], uC[3], uD[3];
+    U.at(x, y, uA); U.at(x + 1, y, uB); U.at(x + 1, y + 1, uC); U.at(x, y + 1, uD);
+    double gxK[2][3], gyK[2][3];
+    tri_grad<double>(0, uA, uB, uC, uD, gxK[0], gyK[0]);
+    tri_grad<double>(1, uA, uB, uC, uD, gxK[1], gyK[1]);
+    const double third = 1.0 / 3.0, r2 = 0.7071067811865476, sq2 = 1.4142135623730951;
+    // basis gradients of the vertices (A, B or D, C) of each family
+    const double phx[2][3] = {{-1, 1, 0}, {0, -1, 1}}, phy[2][3] = {{0, -1, 1}, {-1, 1, 0}};
+    for (int t = 0; t < 2; ++t) {
+        const double* V[3] = {uA, t == 0 ? uB : uD, uC};
+        double g[3], ft;
+        if (t == 0) {
+            g[0] = F2(x + 1, y) - F2(x, y); g[1] = F2(x + 1, y + 1) - F2(x + 1, y);
+            g[2] = -(F1(x, y) + F1(x + 1, y) + F1(x + 1, y + 1)) * third * gms;
+            ft = ((F2(x, y) - F1(x, y)) + (F2(x + 1, y) - F1(x + 1, y)) + (F2(x + 1, y + 1) - F1(x + 1, y + 1))) * third;
+        } else {
+            g[0] = F2(x + 1, y + 1) - F2(x, y + 1); g[1] = F2(x, y + 1) - F2(x, y);
+            g[2] = -(F1(x, y) + F1(x, y + 1) + F1(x + 1, y + 1)) * third * gms;
+            ft = ((F2(x, y) - F1(x, y)) + (F2(x, y + 1) - F1(x, y + 1)) + (F2(x + 1, y + 1) - F1(x + 1, y + 1))) * third;
+        }
+        const double aK = AL(x, y, t);
+        const double LK[3] = {aK, aK, lam};
+        const double wK = WW(x, y, t);
+        double dU[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, dg[3] = {0, 0, 0}, dft = 0.0, dal = 0.0;
+        // interior
+        const double G = g[0] * g[0] / LK[0] + g[1] * g[1] / LK[1] + g[2] * g[2] / LK[2];
+        double s[3], um[3][3], S2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const int b = (a + 1) % 3;
+            for (int c = 0; c < 3; ++c) um[a][c] = 0.5 * (V[a][c] + V[b][c]);
+            s[a] = ft + g[0] * um[a][0] + g[1] * um[a][1] + g[2] * um[a][2];
+            S2 += s[a] * s[a];
+        }
+        const double integ = G * S2 / 6.0;
+        const double wi = integ > 0.0 ? wK / sqrt(2.0 * integ) : 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const int b = (a + 1) % 3;
+            const double k = wi * G * s[a] / 3.0;
+            for (int c = 0; c < 3; ++c) {
+                dU[a][c] += 0.5 * k * g[c];
+                dU[b][c] += 0.5 * k * g[c];
+                dg[c] += k * um[a][c];
+            }
+            dft += k;
+        }
+        for (int c = 0; c < 3; ++c) dg[c] += wi * S2 / 6.0 * 2.0 * g[c] / LK[c];
+        dal += wi * S2 / 6.0 * (-(g[0] * g[0] + g[1] * g[1]) / (aK * aK));
+        // edges
+        double dgx[3] = {0, 0, 0}, dgy[3] = {0, 0, 0};  // dL/d(grad U_c) of this element
+        for (int e = 0; e < 3; ++e) {
+            double nx, ny, he;
+            int nbx = 0, nby = 0, nbt = 0;
+            bool has;
+            if (t == 0) {
+                if (e == 0) { nx = 0; ny = -1; he = 1; has = y >= 1; nbx = x; nby = y - 1; nbt = 1; }
+                else if (e == 1) { nx = 1; ny = 0; he = 1; has = x + 1 <= W - 2; nbx = x + 1; nby = y; nbt = 1; }
+                else { nx = -r2; ny = r2; he = sq2; has = true; nbx = x; nby = y; nbt = 1; }
+            } else {
+                if (e == 0) { nx = -1; ny = 0; he = 1; has = x >= 1; nbx = x - 1; nby = y; nbt = 0; }
+                else if (e == 1) { nx = 0; ny = 1; he = 1; has = y + 1 <= H - 2; nbx = x; nby = y + 1; nbt = 0; }
+                else { nx = r2; ny = -r2; he = sq2; has = true; nbx = x; nby = y; nbt = 0; }
+            }
+            double ngx[3] = {0, 0, 0}, ngy[3] = {0, 0, 0}, aO = 0.0, wO = 0.0;
+            if (has) {
+                if (nbx == x && nby == y) {
+                    for (int c = 0; c < 3; ++c) { ngx[c] = gxK[nbt][c]; ngy[c] = gyK[nbt][c]; }
+                } else {
+                    double qA[3], qB[3], qC[3], qD[3];
+                    U.at(nbx, nby, qA); U.at(nbx + 1, nby, qB); U.at(nbx + 1, nby + 1, qC); U.at(nbx, nby + 1, qD);
+                    tri_grad<double>(nbt, qA, qB, qC, qD, ngx, ngy);
+                }
+                aO = AL(nbx, nby, nbt);
+                wO = WW(nbx, nby, nbt);
+            }
+            double J[3], Le[3], q = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const double lo = c < 2 ? aO : lam;
+                const double fin = LK[c] * (gxK[t][c] * nx + gyK[t][c] * ny);
+                const double fout = has ? lo * (ngx[c] * nx + ngy[c] * ny) : 0.0;
+                Le[c] = has ? (lo > LK[c] ? lo : LK[c]) : LK[c];
+                J[c] = fout - fin;
+                q += J[c] * J[c] / Le[c];
+            }
+            const double wt = wK + (has ? wO : 0.0);
+            const double ce = q > 0.0 ? wt * 0.25 * he / sqrt(q) : 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const double dJ = ce * 2.0 * J[c] / Le[c];
+                dgx[c] += -LK[c] * dJ * nx;
+                dgy[c] += -LK[c] * dJ * ny;
+                if (c < 2) {
+                    const double share = has ? (LK[c] > aO ? 1.0 : (LK[c] == aO ? 0.5 : 0.0)) : 1.0;
+                    dal += dJ * (-(gxK[t][c] * nx + gyK[t][c] * ny)) + ce * (-(J[c] * J[c]) / (Le[c] * Le[c])) * share;
+                }
+            }
+        }
+        for (int i = 0; i < 3; ++i)
+            for (int c = 0; c < 3; ++c) dU[i][c] += phx[t][i] * dgx[c] + phy[t][i] * dgy[c];
+        double* bp = buf + pd.frame_off + (long long)y * pitch + x + (long long)(13 * t) * stride;
+        for (int i = 0; i < 3; ++i)
+            for (int c = 0; c < 3; ++c) bp[(3 * i + c) * stride] = dU[i][c];
+        for (int c = 0; c < 3; ++c) bp[(9 + c) * stride] = dg[c];
+        bp[12 * stride] = dft;
+        const long long od = 2 * ((long long)y * (W - 1) + x) + t;
+        da[od] = (O)((double)da[od] + dal);
+    }
+}
+
+// per node: dL/dU (its 6 elements' vertex values) and dL/df2, dL/df1 (the
+// frame chain of their (dg, dft)), dense [3][H][W] and [H][W] outputs
+template <typename O>
+__global__ void k_eta_vjp_nodes(const PairDesc* pairs, int pair, const double* __restrict__ buf, long long stride,
+                                double gms, O* __restrict__ dU, O* __restrict__ df2, O* __restrict__ df1) {
+    const PairDesc pd = pairs[pair];
+    const int W = pd.W, H = pd.H, pitch = pd.pitch;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W) return;
+    // E1 sq(x,y).t0 vertex 0, E2 sq(x,y).t1 vertex 0, E3 sq(x-1,y-1).t0 vertex 2,
+    // E4 sq(x-1,y-1).t1 vertex 2, E5 sq(x-1,y).t0 vertex 1, E6 sq(x,y-1).t1 vertex 1
+    const int sqx[6] = {x, x, x - 1, x - 1, x - 1, x};
+    const int sqy[6] = {y, y, y - 1, y - 1, y, y - 1};
+    const int sqt[6] = {0, 1, 0, 1, 0, 1};
+    const int vtx[6] = {0, 0, 2, 2, 1, 1};
+    const double phx[6] = {-1, 0, 0, 1, 1, -1};
+    const double phy[6] = {0, -1, 1, 0, -1, 1};
+    double u[3] = {0, 0, 0}, a2 = 0.0, a1 = 0.0;
+    for (int e = 0; e < 6; ++e) {
+        const int X = sqx[e], Y = sqy[e], t = sqt[e];
+        if (X < 0 || Y < 0 || X >= W - 1 || Y >= H - 1) continue;
+        const double* bp = buf + pd.frame_off + (long long)Y * pitch + X + (long long)(13 * t) * stride;
+        for (int c = 0; c < 3; ++c) u[c] += bp[(3 * vtx[e] + c) * stride];
+        const double dg0 = bp[9 * stride], dg1 = bp[10 * stride], dg2 = bp[11 * stride], dft = bp[12 * stride];
+        a2 += dg0 * phx[e] + dg1 * phy[e] + dft / 3.0;
+        a1 += -gms * dg2 / 3.0 - dft / 3.0;
+    }
+    const long long o = (long long)y * W + x, plane = (long long)H * W;
+    if (dU) { dU[o] = (O)u[0]; dU[o + plane] = (O)u[1]; dU[o + 2 * plane] = (O)u[2]; }
+    if (df2) df2[o] = (O)a2;
+    if (df1) df1[o] = (O)a1;
+}
+
+template <typename R, typename O>
+static cudaError_t adapt_vjp_t(const AdaptBufs& A, int pair, int H, int W, double kappa, double eta_thr,
+                               double alpha_th, const void* v, void* da, void* dU, void* df2, void* df1,
+                               cudaStream_t st) {
+    const dim3 ge((W - 1 + 127) / 128, H - 1);
+    const int nparts = (int)(ge.x * ge.y);
+    cudaError_t e = cudaMemsetAsync(A.vjp_argmax, 0xff, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_update_vjp<R, O><<<ge, 128, 0, st>>>(A.pairs, pair, (const R*)A.alpha, (const R*)A.eta,
+                                           (const unsigned long long*)A.etamax, (const O*)v, (O*)da, A.vjp_w, kappa,
+                                           eta_thr, alpha_th, A.vjp_part, A.vjp_argmax);
+    k_update_vjp_max<<<1, 256, 0, st>>>(A.pairs, pair, (const unsigned long long*)A.etamax, A.vjp_part, nparts,
+                                        A.vjp_argmax, A.vjp_w);
+    k_eta_vjp<R, O><<<ge, 128, 0, st>>>(A.pairs, pair, (const R*)A.f1, (const R*)A.f2, (const R*)A.alpha, A.u,
+                                        A.vjp_w, A.lam, A.gms, (O*)da, A.vjp_buf, A.eld_stride);
+    const dim3 gn((W + 127) / 128, H);
+    k_eta_vjp_nodes<O><<<gn, 128, 0, st>>>(A.pairs, pair, A.vjp_buf, A.eld_stride, A.gms, (O*)dU, (O*)df2, (O*)df1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adapt_vjp(const AdaptBufs& A, int pair, int H, int W, double kappa, double eta_thr,
+                             double alpha_th, const void* v, void* da, void* dU, void* df2, void* df1, int out_type,
+                             cudaStream_t st) {
+    if (A.fp64)
+        return out_type == T_F64 ? adapt_vjp_t<double, double>(A, pair, H, W, kappa, eta_thr, alpha_th, v, da, dU, df2, df1, st)
+                                 : adapt_vjp_t<double, float>(A, pair, H, W, kappa, eta_thr, alpha_th, v, da, dU, df2, df1, st);
+    return out_type == T_F64 ? adapt_vjp_t<float, double>(A, pair, H, W, kappa, eta_thr, alpha_th, v, da, dU, df2, df1, st)
+                             : adapt_vjp_t<float, float>(A, pair, H, W, kappa, eta_thr, alpha_th, v, da, dU, df2, df1, st);
+}
+
 cudaError_t launch_adjoint_grad(const AdaptBufs& A, int pair, int H, int W, const double* lamv, void* dalpha,
                                 void* df2, void* df1, int out_type, cudaStream_t st) {
     if (dalpha) {

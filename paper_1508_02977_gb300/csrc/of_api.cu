@@ -32,6 +32,9 @@ struct of_ctx {
     ofl::SmoothTaps taps_rho{};  // K_rho (r = 0: none)
     void* eld = nullptr;         // K_rho element data: 18 planes of frame_elems values (rho > 0)
     void* eldg = nullptr;        // K_rho adjoint work, same layout
+    // adaptation-pass VJP work (allocated on first use)
+    double *vjp_w = nullptr, *vjp_buf = nullptr, *vjp_part = nullptr;
+    unsigned long long* vjp_argmax = nullptr;
     int fp64 = 1;
     size_t es = 8;  // storage element size (frames, alpha, inner vectors)
     std::vector<PairDesc> pd;
@@ -723,6 +726,8 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     CK(dalloc(h, &h->f2, fo * es));
     h->eld = nullptr;
     h->eldg = nullptr;
+    h->vjp_w = h->vjp_buf = h->vjp_part = nullptr;
+    h->vjp_argmax = nullptr;
     if (opt.rho > 0) {
         CK(dalloc(h, &h->eld, 18 * fo * es));
         CK(dalloc(h, &h->eldg, 18 * fo * es));
@@ -1045,6 +1050,57 @@ of_status of_adapt_alpha(of_handle h, double kappa, double eta_thr, double alpha
     CK(cudaStreamSynchronize(st));
     h->solved = false;  // alpha changed: the stored solution no longer belongs to it
     h->cells_dirty = true;
+    return OF_OK;
+}
+
+of_status of_adapt_alpha_vjp(of_handle h, double kappa, double eta_thr, double alpha_th, void* const* dLdalpha_new,
+                             void* const* dLdalpha, void* const* dLdU, void* const* dLdf2, void* const* dLdf1,
+                             of_dtype dt) {
+    if (!h) return OF_ERR_ARG;
+    if (!h->solved) return fail(h, OF_ERR_STATE, "of_adapt_alpha_vjp needs a previous of_solve at the current alpha");
+    if (!(kappa >= 0) || !(alpha_th > 0)) return fail(h, OF_ERR_ARG, "kappa must be >= 0 and alpha_th > 0");
+    if (h->eld) return fail(h, OF_ERR_ARG, "the adaptation-pass VJP is provided for rho = 0");
+    if (!dLdalpha_new || !dLdalpha || !dLdU) return fail(h, OF_ERR_ARG, "null dL/dalpha_new, dL/dalpha or dL/dU list");
+    for (int p = 0; p < h->batch; ++p) {
+        void* arr[5] = {dLdalpha_new[p], dLdalpha[p], dLdU[p], dLdf2 ? dLdf2[p] : nullptr, dLdf1 ? dLdf1[p] : nullptr};
+        for (int k = 0; k < 5; ++k) {
+            if (k < 3 && !arr[k]) return fail(h, OF_ERR_ARG, "null array");
+            if (arr[k] && !is_device_ptr(arr[k])) return fail(h, OF_ERR_ARG, "of_adapt_alpha_vjp takes device arrays");
+        }
+    }
+    DevGuard g(h->device);
+    cudaStream_t st = h->stream;
+    if (!h->vjp_w) {
+        long long maxparts = 1;
+        for (const PairDesc& d : h->pd) maxparts = std::max(maxparts, (long long)((d.W - 1 + 127) / 128) * (d.H - 1));
+        CK(dalloc(h, &h->vjp_w, 2 * h->frame_elems * sizeof(double)));
+        CK(dalloc(h, &h->vjp_buf, 26 * h->frame_elems * sizeof(double)));
+        CK(dalloc(h, &h->vjp_part, maxparts * sizeof(double)));
+        CK(dalloc(h, &h->vjp_argmax, sizeof(unsigned long long)));
+    }
+    ofl::AdaptBufs A = adapt_bufs(h);
+    A.vjp_w = h->vjp_w;
+    A.vjp_buf = h->vjp_buf;
+    A.vjp_part = h->vjp_part;
+    A.vjp_argmax = h->vjp_argmax;
+    A.eld_stride = h->frame_elems;
+    CK(cudaMemsetAsync(h->etamax, 0, sizeof(double) * h->batch, st));
+    for (int p = 0; p < h->batch; ++p) {
+        const PairDesc& d = h->pd[p];
+        if (!h->fp64)  // the indicator of the forward pass reads an FP32 copy of the solution
+            CK(cp2d(h, h->usol + d.vec_off, ofl::T_F64, d.pitch, (float*)h->z + d.vec_off, ofl::T_F32, d.pitch,
+                    3LL * d.H, d.W, st));
+        CK(ofl::launch_indicator(A, p, d.H, d.W, st));
+        CK(ofl::launch_adapt_vjp(A, p, d.H, d.W, kappa, eta_thr, alpha_th, dLdalpha_new[p], dLdalpha[p], dLdU[p],
+                                 dLdf2 ? dLdf2[p] : nullptr, dLdf1 ? dLdf1[p] : nullptr, tcode(dt), st));
+        count_other(h, 6);
+        // with K_sigma the frame gradients are w.r.t. the images given to of_set_frames
+        void* sscr = (char*)h->q + d.vec_off * h->es;
+        for (void* fgrad : {dLdf2 ? dLdf2[p] : nullptr, dLdf1 ? dLdf1[p] : nullptr})
+            if (fgrad && h->opts.sigma > 0)
+                CK(ofl::launch_smooth(fgrad, sscr, tcode(dt), d.W, d.H, d.W, h->taps, true, st));
+    }
+    CK(cudaStreamSynchronize(st));
     return OF_OK;
 }
 

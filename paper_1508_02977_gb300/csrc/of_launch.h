@@ -158,6 +158,10 @@ struct AdaptBufs {
     const struct SmoothTaps* taps_rho;
     long long frame_off;  // the pair's frame offset (set per call)
     int pitch;
+    double* vjp_w;        // adaptation-pass VJP work: dL/deta per element ([H][pitch][2] regions, FP64)
+    double* vjp_buf;      // 26 planes of frame_elems doubles (13 per triangle family)
+    double* vjp_part;     // block partials of the max(eta) term
+    unsigned long long* vjp_argmax;
     int fp64;
 };
 cudaError_t launch_indicator(const AdaptBufs& A, int pair, int H, int W, cudaStream_t st);
@@ -191,6 +195,12 @@ cudaError_t launch_element_data(const void* f1, const void* f2, int type, int W,
                                 void* eld, long long stride, void* scratch, const SmoothTaps& T, cudaStream_t st);
 cudaError_t launch_alpha_update(const AdaptBufs& A, int pair, int H, int W, double kappa, double eta_thr,
                                 double alpha_th, cudaStream_t st);
+// VJP of one adaptation pass (indicator at the stored solution, then the
+// alpha update) for dL/dalpha_new = v (dense [H-1][W-1][2]): da = dL/dalpha
+// through the pass, dU = dL/dU ([3][H][W]), df2 / df1 ([H][W], may be null)
+cudaError_t launch_adapt_vjp(const AdaptBufs& A, int pair, int H, int W, double kappa, double eta_thr,
+                             double alpha_th, const void* v, void* da, void* dU, void* df2, void* df1, int out_type,
+                             cudaStream_t st);
 // adjoint gradients for one pair: u = solution, lam = adjoint state (FP64 planes)
 cudaError_t launch_adjoint_grad(const AdaptBufs& A, int pair, int H, int W, const double* lamv, void* dalpha,
                                 void* df2, void* df1, int out_type, cudaStream_t st);

@@ -76,6 +76,9 @@ _lib.of_solve.argtypes = [_h, ctypes.POINTER(SolveOpts), ctypes.POINTER(_vp), ct
 _lib.of_adapt_alpha.argtypes = [_h, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp), ctypes.c_int]
 _lib.of_adjoint.argtypes = [_h, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                             ctypes.c_int, ctypes.POINTER(SolveInfo)]
+_lib.of_adapt_alpha_vjp.argtypes = [_h, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp),
+                                    ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                    ctypes.c_int]
 _lib.of_apply.argtypes = [_h, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int]
 _lib.of_precondition.argtypes = [_h, ctypes.c_int, _vp, _vp, ctypes.c_int]
 _lib.of_residual.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
@@ -86,15 +89,15 @@ _lib.of_destroy.argtypes = [_h]
 _lib.of_last_error.argtypes = [_h]
 _lib.of_last_error.restype = ctypes.c_char_p
 for _f in ("of_create", "of_setup_grid", "of_set_frames", "of_get_element_data", "of_set_alpha", "of_get_alpha", "of_solve",
-           "of_adapt_alpha", "of_adjoint", "of_apply", "of_precondition", "of_residual", "of_set_profiling",
-           "of_get_profile", "of_residual_noalloc", "of_destroy"):
+           "of_adapt_alpha", "of_adapt_alpha_vjp", "of_adjoint", "of_apply", "of_precondition", "of_residual",
+           "of_set_profiling", "of_get_profile", "of_residual_noalloc", "of_destroy"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 EXPORTS = ("of_create", "of_setup_grid", "of_set_frames", "of_get_frames", "of_get_element_data", "of_set_alpha",
            "of_get_alpha", "of_solve",
-           "of_adapt_alpha", "of_adjoint", "of_apply", "of_precondition", "of_residual", "of_set_profiling",
-           "of_get_profile", "of_residual_noalloc", "of_set_wait_limit", "of_debug_starve_staging", "of_destroy",
-           "of_last_error")
+           "of_adapt_alpha", "of_adapt_alpha_vjp", "of_adjoint", "of_apply", "of_precondition", "of_residual",
+           "of_set_profiling", "of_get_profile", "of_residual_noalloc", "of_set_wait_limit", "of_debug_starve_staging",
+           "of_destroy", "of_last_error")
 
 
 class OFError(RuntimeError):
@@ -244,6 +247,26 @@ def of_adjoint(h, dLdU, dLdalpha=None, dLdf2=None, dLdf1=None, raise_on=True):
     if raise_on:
         _check(h, st)
     return st, [i.as_dict() for i in info]
+
+
+def of_adapt_alpha_vjp(h, kappa, eta_thr, alpha_th, dLdalpha_new, dLdalpha, dLdU, dLdf2=None, dLdf1=None):
+    """VJP of one adaptation pass at the current alpha and solution (device
+    tensors, one per pair)."""
+    n = len(dLdalpha_new)
+
+    def lst(xs):
+        if xs is None:
+            return None, None
+        ps = [_ptr_dtype(x) for x in xs]
+        return (_vp * n)(*[p for p, _ in ps]), ps[0][1]
+
+    a_v, dt = lst(dLdalpha_new)
+    a_a, _ = lst(dLdalpha)
+    a_u, _ = lst(dLdU)
+    a_2, _ = lst(dLdf2)
+    a_1, _ = lst(dLdf1)
+    return _check(h, _lib.of_adapt_alpha_vjp(h, float(kappa), float(eta_thr), float(alpha_th), a_v, a_a, a_u, a_2,
+                                             a_1, dt))
 
 
 def of_apply(h, pair, p, q, b=None):

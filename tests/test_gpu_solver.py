@@ -942,3 +942,30 @@ def test_autotuner_picks_a_measured_candidate(S, tmp_path):
                     {"tile": (48, 48), "overlap": 0, "sweeps": 2, "omega": 1.5})
     name = torch.cuda.get_device_name(0)
     assert autotune.lookup(320, 240, 1, name, path) == best
+
+
+@pytest.mark.parametrize("npasses", [1, 2])
+def test_adaptation_pass_gradients_match_oracle(S, oracle, npasses):
+    """Differentiating through adaptation passes (FP64 handle, per-pass
+    checkpoints): of_adapt_alpha_vjp + of_adjoint chained by the autograd
+    function against the oracle's reverse chain (pinned by central
+    differences of direct solves)."""
+    from paper_1508_02977_gb300.autograd import Solver, adapt_solve_fn
+    W, H, lam = 24, 18, 1.0
+    f1, f2 = synth.random_frames(W, H, 311)
+    a0 = synth.random_alpha(W, H, 312)
+    kappa, thr, ath = 4.0, 0.25, 1e-4
+    c = np.random.default_rng(313).standard_normal((3, H, W))
+    solver = Solver(W, H, precision=S.OF_PREC_FP64, tile=(8, 8), sweeps=2, rtol=1e-14, lam=lam)
+    try:
+        t1 = dev(f1).requires_grad_(True)
+        t2 = dev(f2).requires_grad_(True)
+        ta = dev(a0).requires_grad_(True)
+        U = adapt_solve_fn(t1, t2, ta, solver, npasses, kappa, thr, ath)
+        (U * dev(c)).sum().backward()
+    finally:
+        solver.close()
+    da, d2, d1 = oracle.adaptation_grad(f1, f2, a0, lam, npasses, kappa, thr, ath, c)
+    for got, want in ((ta.grad, da), (t2.grad, d2), (t1.grad, d1)):
+        got = got.cpu().numpy()
+        assert np.abs(got - want).max() <= 1e-7 * np.abs(want).max()
