@@ -350,7 +350,7 @@ def run_ours(args):
         sizes = synth.batch_sizes(64)
         gen = {sz: synth.layers(sz[0], sz[1], seed=(synth.BASE_SEED + 4) * 1000 + k)
                for k, sz in enumerate(sorted(set(sizes)))}
-        hb = S.of_create(0)
+        hb = S.of_create(local, stream)
         S.of_setup_grid(hb, sizes, **WORKLOAD_OPTS)
         Ub = []
         for i, sz in enumerate(sizes):

@@ -969,3 +969,41 @@ def test_adaptation_pass_gradients_match_oracle(S, oracle, npasses):
     for got, want in ((ta.grad, da), (t2.grad, d2), (t1.grad, d1)):
         got = got.cpu().numpy()
         assert np.abs(got - want).max() <= 1e-7 * np.abs(want).max()
+
+
+def test_adapt_alpha_vjp_batch_matches_oracle(S, oracle):
+    """of_adapt_alpha_vjp on a batch of two pairs of different sizes (FP64):
+    each pair's dL/dalpha, dL/dU, dL/df2, dL/df1 for a random dL/dalpha_new
+    equal the oracle's update and indicator VJPs at the same solution."""
+    sizes = [(30, 22), (17, 26)]
+    lam, kappa, thr, ath = 1.0, 4.0, 0.25, 1e-4
+    data = []
+    for i, (W, H) in enumerate(sizes):
+        f1, f2 = synth.random_frames(W, H, 320 + i)
+        data.append((f1, f2, synth.random_alpha(W, H, 330 + i),
+                     np.random.default_rng(340 + i).standard_normal((H - 1, W - 1, 2))))
+    h = handle(S, sizes, precision=S.OF_PREC_FP64, tile=(8, 8), sweeps=2, lam=lam)
+    try:
+        Us = []
+        for i, (f1, f2, a, _) in enumerate(data):
+            S.of_set_frames(h, i, dev(f1), dev(f2))
+            S.of_set_alpha(h, i, dev(a))
+            Us.append(torch.zeros(3, sizes[i][1], sizes[i][0], dtype=torch.float64, device="cuda"))
+        S.of_solve(h, Us, rtol=1e-14, max_inner=20000)
+        v = [dev(d[3]) for d in data]
+        da = [torch.zeros_like(x) for x in v]
+        dU = [torch.zeros_like(u) for u in Us]
+        d2 = [torch.zeros(hh, w, dtype=torch.float64, device="cuda") for w, hh in sizes]
+        d1 = [torch.zeros_like(x) for x in d2]
+        S.of_adapt_alpha_vjp(h, kappa, thr, ath, v, da, dU, d2, d1)
+    finally:
+        S.of_destroy(h)
+    for i, (f1, f2, a, vv) in enumerate(data):
+        U = Us[i].cpu().numpy()
+        sysm = oracle.System.from_frames(f1, f2, a, lam)
+        eta = sysm.indicator(U)
+        wa, w = oracle.alpha_update_vjp(eta, a, kappa, thr, ath, vv)
+        wU, wa2, w2, w1 = oracle.indicator_vjp(f1, f2, a, lam, U, w)
+        for got, want in ((da[i], wa + wa2), (dU[i], wU), (d2[i], w2), (d1[i], w1)):
+            got = got.cpu().numpy()
+            assert np.abs(got - want).max() <= 1e-9 * max(np.abs(want).max(), 1e-300), i
