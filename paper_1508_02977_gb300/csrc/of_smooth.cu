@@ -22,9 +22,13 @@ namespace ofl {
 template <typename D>
 __device__ __forceinline__ D tap_sum(const D* cw, int r, int lo, int hi) { return cw[hi + r + 1] - cw[lo + r]; }
 
+// The pass along x: a block takes 128 columns of SMOOTH_SX rows; the taps
+// and their bounds depend on x only, so the rows accumulate side by side
+// (independent loads in flight).
+constexpr int SMOOTH_SX = 8;
 template <typename D, bool TRANS>
-__global__ void k_smooth_axis(const D* __restrict__ in, D* __restrict__ out, int W, int H, long long pitch, int axis,
-                              const SmoothTaps T) {
+__global__ void __launch_bounds__(128) k_smooth_x(const D* __restrict__ in, D* __restrict__ out, int W, int H,
+                                                  long long pitch, const SmoothTaps T) {
     __shared__ D sw[2 * OF_SMOOTH_RMAX + 1], scw[2 * OF_SMOOTH_RMAX + 2];
     const int r = T.r;
     for (int j = threadIdx.x; j <= 2 * r + 1; j += blockDim.x) {
@@ -34,21 +38,67 @@ __global__ void k_smooth_axis(const D* __restrict__ in, D* __restrict__ out, int
     __syncthreads();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= W) return;
-    const int n = axis == 0 ? W : H;
-    for (int y = blockIdx.y; y < H; y += gridDim.y) {
-        const int pos = axis == 0 ? x : y;
-        const int lo = max(-r, -pos), hi = min(r, n - 1 - pos);
-        const long long step = axis == 0 ? 1 : pitch;
-        const D* src = in + (long long)y * pitch + x;
-        D acc = D(0);
-        for (int k = lo; k <= hi; ++k) {
-            D v = src[k * step];
-            if (TRANS) {
-                const int q = pos + k;  // normaliser of the output position that tap feeds
-                v = v / tap_sum<D>(scw, r, max(-r, -q), min(r, n - 1 - q));
-            }
-            acc += sw[k + r] * v;
+    const int y0 = blockIdx.y * SMOOTH_SX, ny = min(SMOOTH_SX, H - y0);
+    const int lo = max(-r, -x), hi = min(r, W - 1 - x);
+    D acc[SMOOTH_SX];
+#pragma unroll
+    for (int u = 0; u < SMOOTH_SX; ++u) acc[u] = D(0);
+    const D* src = in + (long long)y0 * pitch + x;
+    for (int k = lo; k <= hi; ++k) {
+        D wk = sw[k + r];
+        if (TRANS) {
+            const int q = x + k;  // normaliser of the output position that tap feeds
+            wk = wk / tap_sum<D>(scw, r, max(-r, -q), min(r, W - 1 - q));
         }
+#pragma unroll
+        for (int u = 0; u < SMOOTH_SX; ++u)
+            if (u < ny) acc[u] += wk * src[(long long)u * pitch + k];
+    }
+    const D nrm = TRANS ? D(1) : tap_sum<D>(scw, r, lo, hi);
+#pragma unroll
+    for (int u = 0; u < SMOOTH_SX; ++u)
+        if (u < ny) out[(long long)(y0 + u) * pitch + x] = TRANS ? acc[u] : acc[u] / nrm;
+}
+
+// The pass along y: a block stages a strip of SMOOTH_SY rows (plus r rows
+// above and below) of 128 columns in shared memory with coalesced loads, then
+// each thread walks its column; every input is read once per strip instead
+// of once per tap.  The transposed pass divides each input by the normaliser
+// of its own position while staging it.
+constexpr int SMOOTH_SY = 64;
+template <typename D>
+__host__ __device__ constexpr size_t smooth_y_smem(int r) { return (size_t)(SMOOTH_SY + 2 * r) * 128 * sizeof(D); }
+
+template <typename D, bool TRANS>
+__global__ void __launch_bounds__(128) k_smooth_y(const D* __restrict__ in, D* __restrict__ out, int W, int H,
+                                                  long long pitch, const SmoothTaps T) {
+    extern __shared__ __align__(16) unsigned char ysm[];
+    D* tile = reinterpret_cast<D*>(ysm);  // [(SMOOTH_SY + 2 r)][128]
+    __shared__ D sw[2 * OF_SMOOTH_RMAX + 1], scw[2 * OF_SMOOTH_RMAX + 2];
+    const int r = T.r, tid = threadIdx.x;
+    for (int j = tid; j <= 2 * r + 1; j += blockDim.x) {
+        if (j <= 2 * r) sw[j] = (D)T.w[j];
+        scw[j] = (D)T.cw[j];
+    }
+    __syncthreads();
+    const int x = blockIdx.x * 128 + tid, y0 = blockIdx.y * SMOOTH_SY;
+    const int ylo = max(y0 - r, 0), yhi = min(y0 + SMOOTH_SY + r, H);
+#pragma unroll 8
+    for (int yy = ylo; yy < yhi; ++yy) {  // eight rows' loads in flight
+        D v = D(0);
+        if (x < W) {
+            v = in[(long long)yy * pitch + x];
+            if (TRANS) v = v / tap_sum<D>(scw, r, max(-r, -yy), min(r, H - 1 - yy));
+        }
+        tile[(yy - ylo) * 128 + tid] = v;
+    }
+    __syncthreads();
+    if (x >= W) return;
+    const int yend = min(y0 + SMOOTH_SY, H);
+    for (int y = y0; y < yend; ++y) {
+        const int lo = max(-r, -y), hi = min(r, H - 1 - y);
+        D acc = D(0);
+        for (int k = lo; k <= hi; ++k) acc += sw[k + r] * tile[(y + k - ylo) * 128 + tid];
         if (!TRANS) acc = acc / tap_sum<D>(scw, r, lo, hi);
         out[(long long)y * pitch + x] = acc;
     }
@@ -57,13 +107,23 @@ __global__ void k_smooth_axis(const D* __restrict__ in, D* __restrict__ out, int
 template <typename D>
 static cudaError_t smooth_t(D* f, D* scratch, int W, int H, long long pitch, const SmoothTaps& T, bool transpose,
                             cudaStream_t st) {
-    const dim3 block(128), grid((W + 127) / 128, H < 65535 ? H : 65535);
+    const dim3 block(128);
+    const dim3 gy((W + 127) / 128, (H + SMOOTH_SY - 1) / SMOOTH_SY);
+    const size_t sy = smooth_y_smem<D>(T.r);
+    static bool attr_set = false;  // the largest strip (r = OF_SMOOTH_RMAX) needs the opt-in size
+    if (!attr_set) {
+        const int mx = (int)smooth_y_smem<D>(OF_SMOOTH_RMAX);
+        cudaFuncSetAttribute(k_smooth_y<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_smooth_y<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        attr_set = true;
+    }
+    const dim3 gx((W + 127) / 128, (H + SMOOTH_SX - 1) / SMOOTH_SX);
     if (!transpose) {  // S = S_y S_x
-        k_smooth_axis<D, false><<<grid, block, 0, st>>>(f, scratch, W, H, pitch, 0, T);
-        k_smooth_axis<D, false><<<grid, block, 0, st>>>(scratch, f, W, H, pitch, 1, T);
+        k_smooth_x<D, false><<<gx, block, 0, st>>>(f, scratch, W, H, pitch, T);
+        k_smooth_y<D, false><<<gy, block, sy, st>>>(scratch, f, W, H, pitch, T);
     } else {           // S^T = S_x^T S_y^T
-        k_smooth_axis<D, true><<<grid, block, 0, st>>>(f, scratch, W, H, pitch, 1, T);
-        k_smooth_axis<D, true><<<grid, block, 0, st>>>(scratch, f, W, H, pitch, 0, T);
+        k_smooth_y<D, true><<<gy, block, sy, st>>>(f, scratch, W, H, pitch, T);
+        k_smooth_x<D, true><<<gx, block, 0, st>>>(scratch, f, W, H, pitch, T);
     }
     return cudaGetLastError();
 }
