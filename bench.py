@@ -371,13 +371,34 @@ def run_ours(args):
         binfo.clear()
         msb = timed(bstep, args.batch_steps)
         bpx = sum(w * hh for w, hh in sizes)
+        binfo_mixed = binfo[-1]
+        # the same batch solved in plain FP64 (FP64 frames, vectors and sweeps), same step and residual
+        b64 = None
+        if args.fp64_steps > 0:
+            S.of_destroy(hb)
+            hb = S.of_create(local, stream)
+            S.of_setup_grid(hb, sizes, **FP64_OPTS)
+            for i, sz in enumerate(sizes):
+                g = gen[sz]
+                S.of_set_frames(hb, i, torch.from_numpy(g.f1).to(dev, torch.float64),
+                                torch.from_numpy(g.f2).to(dev, torch.float64))
+            Ub = [torch.zeros(3, sz[1], sz[0], dtype=torch.float64, device=dev) for sz in sizes]
+            bstep()
+            binfo64 = binfo[-1]
+            ms64b = timed(bstep, args.fp64_steps)
+            b64 = {"value": ws * sum(w * hh for w, hh in sizes) * args.fp64_steps / (ms64b / 1e3) / 1e6,
+                   "unit": UNIT, "ms_per_step": ms64b / args.fp64_steps,
+                   "inner_iters_max": max(i["inner_iters"] for i in binfo64),
+                   "rel_residual_max": max(i["rel_residual"] for i in binfo64),
+                   "opts": {k: v for k, v in FP64_OPTS.items()}}
         batched = {"value": ws * bpx * args.batch_steps / (msb / 1e3) / 1e6, "unit": UNIT,
                    "ms_per_step": msb / args.batch_steps, "pairs": len(sizes), "mpixel_per_step": bpx / 1e6,
                    "sizes": {f"{w}x{hh}": sizes.count((w, hh)) for (w, hh) in sorted(set(sizes))},
-                   "inner_iters_max": max(i["inner_iters"] for i in binfo[-1]),
-                   "rel_residual_max": max(i["rel_residual"] for i in binfo[-1]),
+                   "inner_iters_max": max(i["inner_iters"] for i in binfo_mixed),
+                   "rel_residual_max": max(i["rel_residual"] for i in binfo_mixed),
                    "opts": {k: v for k, v in WORKLOAD_OPTS.items()},
-                   "data": "one layered pair generated per size, reused for the pairs of that size"}
+                   "data": "one layered pair generated per size, reused for the pairs of that size",
+                   "fp64_gpu": b64}
         S.of_destroy(hb)
 
     cpu = None
