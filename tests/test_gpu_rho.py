@@ -249,3 +249,46 @@ def test_rho_adjoint_mixed_with_presmoothing(S, oracle):
     _, w2, _ = oracle.adjoint_grad(fs1, fs2, alpha, lam, Ud, Lam, rho=rho)
     want = oracle.smooth_transpose(w2, sig)
     assert np.abs(d2 - want).max() <= 1e-3 * np.abs(want).max()
+
+
+def test_rho_batch_of_two_pairs(S, oracle):
+    """K_rho element data, operator and adjoint frame gradients of a batch of
+    two pairs of different sizes (per-pair plane offsets) against the oracle
+    pair by pair (FP64)."""
+    sizes = [(33, 21), (20, 28)]
+    rho, lam = 1.3, 1.0
+    data = []
+    for i, (W, H) in enumerate(sizes):
+        f1, f2 = synth.random_frames(W, H, 93 + i)
+        data.append((f1, f2, synth.random_alpha(W, H, 95 + i)))
+    h = handle(S, sizes, precision=0, tile=(8, 8), sweeps=2, rho=rho, lam=lam)
+    try:
+        Us, planes, qs = [], [], []
+        for i, (f1, f2, a) in enumerate(data):
+            W, H = sizes[i]
+            S.of_set_frames(h, i, dev(f1), dev(f2))
+            S.of_set_alpha(h, i, dev(a))
+            out = torch.zeros(18, H - 1, W - 1, dtype=torch.float64, device="cuda")
+            S.of_get_element_data(h, i, out)
+            planes.append(out.cpu().numpy())
+            p = np.random.default_rng(97 + i).standard_normal((3, H, W))
+            q = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+            S.of_apply(h, i, dev(p), q)
+            qs.append((p, q.cpu().numpy()))
+            Us.append(torch.zeros(3, H, W, dtype=torch.float64, device="cuda"))
+        S.of_solve(h, Us, rtol=1e-14, max_inner=20000)
+        cs = [np.random.default_rng(99 + i).standard_normal((3, H, W)) for i, (W, H) in enumerate(sizes)]
+        d2 = [torch.zeros(H, W, dtype=torch.float64, device="cuda") for W, H in sizes]
+        S.of_adjoint(h, [dev(c) for c in cs], None, d2)
+    finally:
+        S.of_destroy(h)
+    for i, (f1, f2, a) in enumerate(data):
+        want = oracle_planes(oracle, f1, f2, rho, 0)
+        assert np.abs(planes[i] - want).max() <= 1e-13 * np.abs(want).max()
+        sysm = oracle.System.from_frames(f1, f2, a, lam, rho=rho)
+        p, q = qs[i]
+        assert np.all(np.abs(q - sysm.matvec(p)) <= 1e-13 * csr_abs_matvec(sysm, p) + 1e-300)
+        U = sysm.solve_direct()
+        Lam = sysm.solve_with(cs[i])
+        _, w2, _ = oracle.adjoint_grad(f1, f2, a, lam, U, Lam, rho=rho)
+        assert np.abs(d2[i].cpu().numpy() - w2).max() <= 1e-8 * np.abs(w2).max()
