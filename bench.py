@@ -418,7 +418,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"layers {W}x{H}: 4 textured layers, rigid motions <= 6 px, occlusions, "
                                    f"gain 0.8-1.25 (one pair per GPU)",
-                       "precision": "FP32 PCG + Schwarz sweeps; outer residual b - A x in double-float (~48-bit) arithmetic; x, refinement and cross-block dots in FP64",
+                       "precision": "FP32 PCG + Schwarz sweeps; outer residual b - A x and the refinement update x += d + a p in double-float (~48-bit) arithmetic on the FP32 pipe; x stored in FP64; CG scalars and cross-block dots in FP64",
                        "rtol": RTOL, "opts": {k: v for k, v in WORKLOAD_OPTS.items()},
                        "step": "alpha reset + solve to rtol + indicator + alpha update",
                        "l2": "inputs larger than L2 (no flush)",

@@ -17,6 +17,8 @@
 //   RES   : in = x + d + a p  (x_new stored),  out r = rhs - A in,
 //           rhs = b (frames) or a given vector,  partial ||r||^2, ||rhs||^2
 #pragma once
+#include <type_traits>
+
 #include "of_common.cuh"
 #include "of_df.cuh"
 
@@ -220,6 +222,8 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
         a_prev = corr ? (R)P.sc_in[pair].a : R(0);
     }
     constexpr bool IS_RES = (MODE == MODE_RES) || (MODE == MODE_RESB);
+    DF a_df = DF{0.f, 0.f};
+    if constexpr (MODE == MODE_RES && std::is_same<T, DF>::value) a_df = Cvt<DF>::from((double)a_prev);
 
     const C* f1 = P.f1 + pd.frame_off;
     const C* f2 = P.f2 + pd.frame_off;
@@ -263,6 +267,25 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
             return v;
         }
         R p0 = vin[o], p1 = vin[o + plane], p2 = vin[o + 2 * plane];
+        if constexpr (MODE == MODE_RES && std::is_same<T, DF>::value) {
+            // FP32 path: x + (d + a p) in double-float on the FP32 pipe, stored as FP64
+            DF X[3] = {Cvt<DF>::from(p0), Cvt<DF>::from(p1), Cvt<DF>::from(p2)};
+            if (corr) {
+                const RI* d = P.dcorr + vo;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const long long oc = o + c * plane;
+                    X[c] = X[c] + (DF{(float)d[oc], 0.f} + a_df * DF{(float)pold[oc], 0.f});
+                }
+            }
+            if (owner && P.out) {
+                R* xn = P.out + vo;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) xn[o + c * plane] = (R)X[c].hi + (R)X[c].lo;
+            }
+            v.p = v3(X[0], X[1], X[2]);
+            return v;
+        }
         if (MODE == MODE_PCG) {
             if (!pcg_first) {
                 R q0 = pold[o], q1 = pold[o + plane], q2 = pold[o + 2 * plane];

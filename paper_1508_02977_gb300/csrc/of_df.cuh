@@ -48,9 +48,35 @@ __device__ __forceinline__ DF operator*(DF a, DF b) {
 }
 
 // double -> double-float: hi is x rounded to float, lo the rounded remainder
-__device__ __forceinline__ DF df_from_double(double x) {
+__device__ __forceinline__ DF df_from_double_fp64(double x) {
     const float h = __double2float_rn(x);
     return DF{h, __double2float_rn(x - (double)h)};
+}
+
+// The same from the bits of x with integer and FP32 instructions (the
+// double <-> float conversions and the subtraction above run on the FP64
+// pipe, a small fraction of the FP32 rate on this GPU).  x = (-1)^s 1.m 2^e
+// with a 53-bit significand M: hi keeps the top 24 bits rounded to nearest
+// even, and the remainder M - (top 24 bits, rounded) 2^29 (a 30-bit signed
+// integer times 2^(e - 52)) is rounded to float by the int -> float
+// conversion and scaled by an exact power of two.  Zeros are exact; values
+// whose remainder would leave the normal float range (|x| < 2^-63 or
+// |x| >= 2^127), infinities and NaNs take the FP64 route.
+__device__ __forceinline__ DF df_from_double(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned s = (unsigned)(b >> 63);
+    const int E = (int)((b >> 52) & 0x7ffULL);
+    if ((b << 1) == 0ULL) return DF{s ? -0.0f : 0.0f, 0.0f};
+    if (E < 960 || E > 1150) return df_from_double_fp64(x);
+    const unsigned long long m = (b & 0xfffffffffffffULL) | (1ULL << 52);
+    const unsigned top = (unsigned)(m >> 29);              // 24 bits, bit 23 the implicit one
+    const unsigned rest = (unsigned)(m & 0x1fffffffULL);   // 29 bits
+    const bool up = rest > (1u << 28) || (rest == (1u << 28) && (top & 1u));
+    const unsigned hb = (((unsigned)(E - 1023 + 127) << 23) + (top & 0x7fffffu) + (up ? 1u : 0u)) | (s << 31);
+    const int ri = up ? (int)rest - (1 << 29) : (int)rest;
+    const float scale = __uint_as_float((unsigned)(E - 1075 + 127) << 23);  // 2^(e - 52)
+    const float lo = __fmul_rn(__int2float_rn(ri), scale);
+    return DF{__uint_as_float(hb), s ? -lo : lo};
 }
 
 __device__ __forceinline__ DF shfl_down(DF v, int d) {
