@@ -342,7 +342,7 @@ def run_ours(args):
                               "rel_residual": infos[-1]["rel_residual"], "opts": extra}
             S.of_destroy(hv)
 
-    # the batched form (north star, config 4): 64 pairs of mixed sizes in one
+    # the batched form: 64 pairs of mixed sizes in one
     # handle, every kernel launched once for the whole batch; one layered pair
     # is generated per size and reused for every pair of that size
     batched = None
