@@ -488,11 +488,7 @@ def _adjoint_frames_rho(f1, f2, U, Lam, model, rho):
     assembled from the element tensors, dL/dtheta = -dE/dtheta and
       dE/dA_cd = |K|/12 (sum_i Lam_ic U_id + (sum_i Lam_ic)(sum_i U_id)),
       dE/dF_c  = -|K|/3 sum_i Lam_ic;
-    K_rho is linear, so these go back to the unsmoothed products through
-    its transpose (smooth_transpose, per triangle family); the products
-    g_c g_d and -ft g_c then give dE/dg and dE/dft, and g, ft depend on the
-    frames through the P1 gradient of f2 and the vertex means (as in the
-    rho = 0 adjoint)."""
+    these go back to the frames through _element_data_chain."""
     f1, f2 = _c(f1), _c(f2)
     H, W = f1.shape
     U, Lam = np.asarray(U, np.float64), np.asarray(Lam, np.float64)
@@ -504,20 +500,35 @@ def _adjoint_frames_rho(f1, f2, U, Lam, model, rho):
                     + np.einsum("...c,...d->...cd", Le.sum(-2), Ue.sum(-2)))
     GA = np.stack([M[..., c, c] if c == d else M[..., c, d] + M[..., d, c] for c, d in SYM6], -1)
     GF = -K / 3.0 * Le.sum(-2)
+    d2, d1 = _element_data_chain(f1, f2, GA, GF, model, rho)
+    return -d2, -d1
+
+
+def _element_data_chain(f1, f2, GA, GF, model, rho):
+    """Frame gradients of a function of the element data (Section 1: A_rho =
+    K_rho * (g g^T), F = K_rho * (-ft g)) given its derivatives GA with
+    respect to the 6 stored entries SYM6 of A_rho and GF with respect to F,
+    per element [H-1][W-1][2][.].  K_rho is linear, so these go back to the
+    unsmoothed products through its transpose (smooth_transpose, per
+    triangle family); the products g_c g_d and -ft g_c then give d/dg and
+    d/dft, and g, ft depend on the frames through the P1 gradient of f2 and
+    the vertex means (_frames_chain)."""
+    f1, f2 = _c(f1), _c(f2)
+    H, W = f1.shape
+    GA, GF = np.array(GA, dtype=np.float64), np.array(GF, dtype=np.float64)
     for t in range(2):  # K_rho^T per family
         for k in range(6):
             GA[:, :, t, k] = smooth_transpose(GA[:, :, t, k], rho)
         for k in range(3):
             GF[:, :, t, k] = smooth_transpose(GF[:, :, t, k], rho)
     g, ft = coefficients(f1, f2, model)
-    dEdg = np.zeros_like(g)
+    dg = np.zeros_like(g)
     for k, (c, d) in enumerate(SYM6):
-        dEdg[..., c] += GA[..., k] * g[..., d]
-        dEdg[..., d] += GA[..., k] * g[..., c]
-    dEdg -= ft[..., None] * GF
-    dEdft = -np.sum(GF * g, axis=-1)
-    d2, d1 = _frames_chain(W, H, dEdg, dEdft, model)
-    return -d2, -d1
+        dg[..., c] += GA[..., k] * g[..., d]
+        dg[..., d] += GA[..., k] * g[..., c]
+    dg -= ft[..., None] * GF
+    dft = -np.sum(GF * g, axis=-1)
+    return _frames_chain(W, H, dg, dft, model)
 
 
 # gradients of the P1 basis functions of each triangle family (t = 0: vertices
@@ -589,7 +600,7 @@ def _element_neighbours(W, H):
     return nrm, he, nb, ok
 
 
-def indicator_vjp(f1, f2, alpha, lam, U, w, model=0):
+def indicator_vjp(f1, f2, alpha, lam, U, w, model=0, rho=0.0):
     """Vector-Jacobian product of the error indicator eta_K (Section 2.3,
     Eq. errind, read as in orc_indicator: interior term h_K ||Lambda^-1/2 R||
     with R = -g (g.U_h + ft), edge terms 1/2 h_e sqrt(q_e) with the flux
@@ -597,7 +608,9 @@ def indicator_vjp(f1, f2, alpha, lam, U, w, model=0):
     (dL/dU [3][H][W], dL/dalpha [H-1][W-1][2], dL/df2, dL/df1).  An edge term
     appears in the indicators of both elements that share it; Lambda_e at
     equal sides passes half of its derivative to each (the mean of the
-    one-sided derivatives, what central differences see)."""
+    one-sided derivatives, what central differences see).  With rho > 0 the
+    interior residual is R = F - A_rho U_h (orc_indicator_el) and its frame
+    derivatives go through the element data (_element_data_chain)."""
     f1, f2 = _c(f1), _c(f2)
     H, W = f1.shape
     alpha = np.broadcast_to(np.asarray(alpha, dtype=np.float64), (H - 1, W - 1, 2))
@@ -609,11 +622,12 @@ def indicator_vjp(f1, f2, alpha, lam, U, w, model=0):
     Lam = np.stack([alpha, alpha, np.full_like(alpha, lam)], -1)  # [y][x][t][c]
     grad = np.stack([np.einsum("yxtic,ti->yxtc", Ue, GPHI_X),
                      np.einsum("yxtic,ti->yxtc", Ue, GPHI_Y)], -1)  # [y][x][t][c][2]
-    dgradK = np.zeros_like(grad)
     dU_v = np.zeros_like(Ue)
     dal = np.zeros_like(alpha)
     dg = np.zeros_like(g)
     dft = np.zeros_like(ft)
+    if rho > 0:
+        return _indicator_vjp_general(f1, f2, alpha, lam, Ue, w, model, rho, vy, vx, grad, Lam)
     # interior: integ = 1/6 G sum_a s_a^2, val = sqrt(2 integ)
     G = np.sum(g * g / Lam, -1)
     s_a, Um = [], []
@@ -634,7 +648,16 @@ def indicator_vjp(f1, f2, alpha, lam, U, w, model=0):
         dft += wi * G * s_a[a] / 3.0
     dg += (wi * S2 / 6.0)[..., None] * 2.0 * g / Lam
     dal += wi * S2 / 6.0 * (-(g[..., 0] ** 2 + g[..., 1] ** 2) / alpha ** 2)
-    # edges
+    _indicator_vjp_edges(W, H, w, Lam, grad, alpha, dU_v, dal)
+    dU = _scatter_vertices(W, H, dU_v, vy, vx)
+    d2, d1 = _frames_chain(W, H, dg, dft, model)
+    return dU, dal, d2, d1
+
+
+def _indicator_vjp_edges(W, H, w, Lam, grad, alpha, dU_v, dal):
+    """The edge terms of indicator_vjp (they do not involve the data term):
+    adds their derivatives to the per-vertex dU_v and to dal in place."""
+    dgradK = np.zeros_like(grad)
     nrm, he, nb, ok = _element_neighbours(W, H)
     for t in range(2):
         for k in range(3):
@@ -657,45 +680,91 @@ def indicator_vjp(f1, f2, alpha, lam, U, w, model=0):
             dal[:, :, t] += dLK[..., 0] + dLK[..., 1]
     # vertex gradients of the element gradients
     dU_v += np.einsum("yxtc,ti->yxtic", dgradK[..., 0], GPHI_X) + np.einsum("yxtc,ti->yxtic", dgradK[..., 1], GPHI_Y)
+
+
+def _scatter_vertices(W, H, dU_v, vy, vx):
+    """Per-element vertex values [H-1][W-1][2][3][3] summed into [3][H][W]."""
     dU = np.zeros((3, H, W))
     for t in range(2):
         for i in range(3):
             for c in range(3):
                 np.add.at(dU[c], (vy[:, :, t, i], vx[:, :, t, i]), dU_v[:, :, t, i, c])
-    d2, d1 = _frames_chain(W, H, dg, dft, model)
+    return dU
+
+
+def _indicator_vjp_general(f1, f2, alpha, lam, Ue, w, model, rho, vy, vx, grad, Lam):
+    """indicator_vjp with the K_rho element data (rho > 0).  Interior term
+    val = h_K sqrt(integ), integ = |K|/3 sum_a sum_c R_ac^2 / Lambda_c over
+    the edge midpoints m_a, R_a = F - A_rho U_h(m_a):
+      d val / d integ = h_K / (2 sqrt(integ)),
+      d integ / d R_ac = (2|K|/3) R_ac / Lambda_c,
+    and R_a is linear in F (identity), in A_rho (-U_h(m_a)) and in the
+    midpoint values (-A_rho)."""
+    H, W = np.asarray(f1).shape
+    Ael, Fel = element_data(f1, f2, rho, model)
+    Am = np.zeros(Ael.shape[:-1] + (3, 3))
+    for k, (c, d) in enumerate(SYM6):
+        Am[..., c, d] = Ael[..., k]
+        Am[..., d, c] = Ael[..., k]
+    K, hK = 0.5, np.sqrt(2.0)
+    dU_v = np.zeros_like(Ue)
+    dal = np.zeros_like(np.asarray(alpha, dtype=np.float64))
+    Um, Ra = [], []
+    for a in range(3):
+        b = (a + 1) % 3
+        um = 0.5 * (Ue[..., a, :] + Ue[..., b, :])
+        Um.append(um)
+        Ra.append(Fel - np.einsum("...cd,...d->...c", Am, um))
+    integ = K / 3.0 * sum(np.sum(R * R / Lam, -1) for R in Ra)
+    dv = np.where(integ > 0, w * hK / (2.0 * np.sqrt(np.where(integ > 0, integ, 1.0))), 0.0)
+    GAm = np.zeros_like(Am)
+    GF = np.zeros_like(Fel)
+    for a in range(3):
+        b = (a + 1) % 3
+        dR = dv[..., None] * (2.0 * K / 3.0) * Ra[a] / Lam
+        GF += dR
+        GAm -= np.einsum("...c,...d->...cd", dR, Um[a])
+        dum = -np.einsum("...cd,...c->...d", Am, dR)
+        dU_v[..., a, :] += 0.5 * dum
+        dU_v[..., b, :] += 0.5 * dum
+        dal += dv * (K / 3.0) * (-(Ra[a][..., 0] ** 2 + Ra[a][..., 1] ** 2) / np.asarray(alpha) ** 2)
+    GA = np.stack([GAm[..., c, c] if c == d else GAm[..., c, d] + GAm[..., d, c] for c, d in SYM6], -1)
+    _indicator_vjp_edges(W, H, w, Lam, grad, alpha, dU_v, dal)
+    dU = _scatter_vertices(W, H, dU_v, vy, vx)
+    d2, d1 = _element_data_chain(f1, f2, GA, GF, model, rho)
     return dU, dal, d2, d1
 
 
-def adaptation_forward(f1, f2, alpha0, lam, npasses, kappa, eta_thr, alpha_th, model=0):
+def adaptation_forward(f1, f2, alpha0, lam, npasses, kappa, eta_thr, alpha_th, model=0, rho=0.0):
     """npasses adaptation passes (Section 2.3 on the fixed mesh): solve,
     indicator, alpha update; then the final solve.  Returns the final U and
     the per-pass (alpha_k, U_k, eta_k) checkpoints."""
     a = np.array(np.broadcast_to(np.asarray(alpha0, dtype=np.float64), (f1.shape[0] - 1, f1.shape[1] - 1, 2)))
     passes = []
     for _ in range(npasses):
-        S = System.from_frames(f1, f2, a, lam, model)
+        S = System.from_frames(f1, f2, a, lam, model, rho=rho)
         U = S.solve_direct()
         eta = S.indicator(U)
         passes.append((a.copy(), U, eta))
         a = alpha_update(eta, a, kappa, eta_thr, alpha_th)
-    S = System.from_frames(f1, f2, a, lam, model)
+    S = System.from_frames(f1, f2, a, lam, model, rho=rho)
     return S.solve_direct(), a, passes
 
 
-def adaptation_grad(f1, f2, alpha0, lam, npasses, kappa, eta_thr, alpha_th, dLdU, model=0):
+def adaptation_grad(f1, f2, alpha0, lam, npasses, kappa, eta_thr, alpha_th, dLdU, model=0, rho=0.0):
     """dL/dalpha_0, dL/df2, dL/df1 of L(U_final) through the adaptation
     passes, in reverse: the adjoint solve of each pass (adjoint_grad), then
     the alpha update (alpha_update_vjp) and the indicator (indicator_vjp)
     that produced its alpha, whose dL/dU starts the previous pass's adjoint
     solve."""
-    U, a, passes = adaptation_forward(f1, f2, alpha0, lam, npasses, kappa, eta_thr, alpha_th, model)
-    S = System.from_frames(f1, f2, a, lam, model)
-    v, g2, g1 = adjoint_grad(f1, f2, a, lam, U, S.solve_with(dLdU), model=model)
+    U, a, passes = adaptation_forward(f1, f2, alpha0, lam, npasses, kappa, eta_thr, alpha_th, model, rho)
+    S = System.from_frames(f1, f2, a, lam, model, rho=rho)
+    v, g2, g1 = adjoint_grad(f1, f2, a, lam, U, S.solve_with(dLdU), model=model, rho=rho)
     for a_k, U_k, eta_k in reversed(passes):
         da_upd, w = alpha_update_vjp(eta_k, a_k, kappa, eta_thr, alpha_th, v)
-        dU_k, da_eta, d2e, d1e = indicator_vjp(f1, f2, a_k, lam, U_k, w, model)
-        S = System.from_frames(f1, f2, a_k, lam, model)
-        ga, g2k, g1k = adjoint_grad(f1, f2, a_k, lam, U_k, S.solve_with(dU_k), model=model)
+        dU_k, da_eta, d2e, d1e = indicator_vjp(f1, f2, a_k, lam, U_k, w, model, rho)
+        S = System.from_frames(f1, f2, a_k, lam, model, rho=rho)
+        ga, g2k, g1k = adjoint_grad(f1, f2, a_k, lam, U_k, S.solve_with(dU_k), model=model, rho=rho)
         v = da_upd + da_eta + ga
         g2 = g2 + d2e + g2k
         g1 = g1 + d1e + g1k

@@ -925,3 +925,83 @@ def test_adaptation_gradient_matches_differences(oracle):
             fd = (L(f1, fp, a0) - L(f1, fm, a0)) / (2 * h) if which == "f2" else \
                 (L(fp, f2, a0) - L(fm, f2, a0)) / (2 * h)
             assert abs(fd - grad[y, x]) <= 1e-5 * np.abs(grad).max(), (which, y, x, fd, grad[y, x])
+
+
+def test_indicator_vjp_with_rho_matches_differences(oracle):
+    """sum_K w_K eta_K with the K_rho element data (interior residual
+    F - A_rho U_h) against central differences in U, alpha and both frames;
+    at rho -> 0 the general form equals the rank-1 one."""
+    W, H, lam, rho = 9, 7, 0.9, 1.2
+    f1, f2 = synth.random_frames(W, H, 84)
+    al = synth.random_alpha(W, H, 85)
+    rng = np.random.default_rng(86)
+    U = rng.standard_normal((3, H, W))
+    w = rng.standard_normal((H - 1, W - 1, 2))
+
+    def L(U_, a_, f1_, f2_):
+        return np.sum(w * oracle.System.from_frames(f1_, f2_, a_, lam, rho=rho).indicator(U_))
+
+    dU, da, d2, d1 = oracle.indicator_vjp(f1, f2, al, lam, U, w, rho=rho)
+    h = 1e-6
+    for _ in range(6):
+        c, y, x = rng.integers(0, 3), rng.integers(0, H), rng.integers(0, W)
+        Up, Um = U.copy(), U.copy()
+        Up[c, y, x] += h
+        Um[c, y, x] -= h
+        fd = (L(Up, al, f1, f2) - L(Um, al, f1, f2)) / (2 * h)
+        assert abs(fd - dU[c, y, x]) <= 1e-6 * max(1.0, abs(fd))
+    for _ in range(6):
+        y, x, t = rng.integers(0, H - 1), rng.integers(0, W - 1), rng.integers(0, 2)
+        ap, am = al.copy(), al.copy()
+        ap[y, x, t] += h
+        am[y, x, t] -= h
+        fd = (L(U, ap, f1, f2) - L(U, am, f1, f2)) / (2 * h)
+        assert abs(fd - da[y, x, t]) <= 1e-6 * max(1.0, abs(fd))
+    for _ in range(4):
+        y, x = rng.integers(0, H), rng.integers(0, W)
+        for which, grad in (("f2", d2), ("f1", d1)):
+            fp = (f2 if which == "f2" else f1).copy()
+            fm = fp.copy()
+            fp[y, x] += h
+            fm[y, x] -= h
+            fd = (L(U, al, f1, fp) - L(U, al, f1, fm)) / (2 * h) if which == "f2" else \
+                (L(U, al, fp, f2) - L(U, al, fm, f2)) / (2 * h)
+            assert abs(fd - grad[y, x]) <= 1e-6 * max(1.0, abs(fd)), (which, y, x, fd, grad[y, x])
+    # rho = 0.1: the K_rho weights beyond the centre are ~1e-22, so the
+    # general interior form must reproduce the rank-1 one
+    r0 = oracle.indicator_vjp(f1, f2, al, lam, U, w)
+    r1 = oracle.indicator_vjp(f1, f2, al, lam, U, w, rho=0.1)
+    for a, b in zip(r0, r1):
+        assert np.abs(a - b).max() <= 1e-11 * np.abs(a).max()
+
+
+def test_adaptation_gradient_with_rho_matches_differences(oracle):
+    """As test_adaptation_gradient_matches_differences, with the K_rho data
+    term in every solve and in the indicator."""
+    W, H, lam, rho = 9, 8, 1.0, 1.1
+    f1, f2 = synth.random_frames(W, H, 87)
+    a0 = synth.random_alpha(W, H, 88)
+    kappa, thr, ath = 4.0, 0.25, 1e-4
+    c = np.random.default_rng(89).standard_normal((3, H, W))
+    da, d2, d1 = oracle.adaptation_grad(f1, f2, a0, lam, 1, kappa, thr, ath, c, rho=rho)
+    L = lambda f1_, f2_, a_: np.sum(c * oracle.adaptation_forward(f1_, f2_, a_, lam, 1, kappa, thr, ath,
+                                                                  rho=rho)[0])
+    h = 1e-6
+    rng = np.random.default_rng(90)
+    for _ in range(6):
+        y, x, t = rng.integers(0, H - 1), rng.integers(0, W - 1), rng.integers(0, 2)
+        ap, am = a0.copy(), a0.copy()
+        ap[y, x, t] += h
+        am[y, x, t] -= h
+        fd = (L(f1, f2, ap) - L(f1, f2, am)) / (2 * h)
+        assert abs(fd - da[y, x, t]) <= 1e-5 * np.abs(da).max(), (y, x, t, fd, da[y, x, t])
+    for _ in range(4):
+        y, x = rng.integers(0, H), rng.integers(0, W)
+        for which, grad in (("f2", d2), ("f1", d1)):
+            fp = (f2 if which == "f2" else f1).copy()
+            fm = fp.copy()
+            fp[y, x] += h
+            fm[y, x] -= h
+            fd = (L(f1, fp, a0) - L(f1, fm, a0)) / (2 * h) if which == "f2" else \
+                (L(fp, f2, a0) - L(fm, f2, a0)) / (2 * h)
+            assert abs(fd - grad[y, x]) <= 1e-5 * np.abs(grad).max(), (which, y, x, fd, grad[y, x])
