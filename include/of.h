@@ -198,8 +198,10 @@ of_status of_adapt_alpha(of_handle h, double kappa, double eta_thr, double alpha
  * it, and Lambda_e = max of the two sides of an edge passes half to each
  * at a tie.  Chained with of_adjoint (dL/dU of the pass as its input), this
  * differentiates a loss through any number of passes from per-pass
- * checkpoints of alpha and U.  Device arrays only; rho must be 0.
- * Synchronises the stream. */
+ * checkpoints of alpha and U.  With rho > 0 the indicator's interior
+ * residual is F - A_rho U_h, and its frame derivatives go back through the
+ * element data (K_rho^T, then the products), as in of_adjoint.  Device
+ * arrays only.  Synchronises the stream. */
 of_status of_adapt_alpha_vjp(of_handle h, double kappa, double eta_thr, double alpha_th,
                              void *const *dLdalpha_new, void *const *dLdalpha, void *const *dLdU,
                              void *const *dLdf2, void *const *dLdf1, of_dtype dt);

@@ -417,13 +417,13 @@ __global__ void k_adjoint_frames_eld(const PairDesc* pairs, int pair, const R* _
     if (df1) df1[(long long)y * W + x] = (O)a1;
 }
 
+// Frame gradients from per-element planes G (the layout of the element data)
+// holding minus the derivatives with respect to A_rho (6 stored entries) and F:
+// K_rho^T over each plane, then k_adjoint_frames_eld.
 template <typename R, typename O>
-static cudaError_t adjoint_frames_eld(const AdaptBufs& A, int pair, int H, int W, const double* lamv, void* df2,
-                                      void* df1, int type, cudaStream_t st) {
-    dim3 ge((W - 1 + 127) / 128, H - 1);
-    k_adjoint_eld<R><<<ge, 128, 0, st>>>(A.pairs, pair, A.u, lamv, (R*)A.eldg, A.eld_stride);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+static cudaError_t eld_frames_chain(const AdaptBufs& A, int pair, int H, int W, void* df2, void* df1, int type,
+                                    cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
     const size_t es = sizeof(R);
     for (int q = 0; q < 18; ++q) {  // K_rho^T over each plane's (W-1) x (H-1) lattice
         e = launch_smooth((char*)A.eldg + ((size_t)q * A.eld_stride + A.frame_off) * es, A.scratch, type, W - 1, H - 1,
@@ -434,6 +434,16 @@ static cudaError_t adjoint_frames_eld(const AdaptBufs& A, int pair, int H, int W
     k_adjoint_frames_eld<R, O><<<gf, 128, 0, st>>>(A.pairs, pair, (const R*)A.f1, (const R*)A.f2, (const R*)A.eldg,
                                                    A.eld_stride, (O*)df2, (O*)df1, A.gms);
     return cudaGetLastError();
+}
+
+template <typename R, typename O>
+static cudaError_t adjoint_frames_eld(const AdaptBufs& A, int pair, int H, int W, const double* lamv, void* df2,
+                                      void* df1, int type, cudaStream_t st) {
+    dim3 ge((W - 1 + 127) / 128, H - 1);
+    k_adjoint_eld<R><<<ge, 128, 0, st>>>(A.pairs, pair, A.u, lamv, (R*)A.eldg, A.eld_stride);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return eld_frames_chain<R, O>(A, pair, H, W, df2, df1, type, st);
 }
 
 // ------------------------------------------ through the adaptation pass --
@@ -512,10 +522,19 @@ __global__ void k_update_vjp_max(const PairDesc* pairs, int pair, const unsigned
 //             half the derivative to each side at a tie).
 // Writes per element and triangle 13 values: dL/dU at its 3 vertices (3
 // components each) and (dg_0, dg_1, dg_2, dft); adds dL/dalpha_K to da.
+//
+// With the K_rho element data (eld non-null) the interior residual at the
+// edge midpoints m_a is R_a = F - A_rho U_h(m_a) and
+//   integ = (|K|/3) sum_a sum_c R_ac^2 / Lambda_c,  d integ / d R_ac = R_ac / (3 Lambda_c);
+// R_a is linear in F, in A_rho (-U_h(m_a)) and in the midpoint values
+// (-A_rho).  The derivatives with respect to the element data go to eldg
+// with a minus sign (the convention of k_adjoint_eld, so that the same K_rho^T
+// chain to the frames serves both) and (dg, dft) are 0.
 template <typename R, typename O>
 __global__ void k_eta_vjp(const PairDesc* pairs, int pair, const R* __restrict__ f1a, const R* __restrict__ f2a,
                           const R* __restrict__ ala, const double* __restrict__ ua, const double* __restrict__ w,
-                          double lam, double gms, O* __restrict__ da, double* __restrict__ buf, long long stride) {
+                          double lam, double gms, O* __restrict__ da, double* __restrict__ buf, long long stride,
+                          const R* __restrict__ eld, R* __restrict__ eldg) {
     const PairDesc pd = pairs[pair];
     const int W = pd.W, H = pd.H, pitch = pd.pitch;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -554,29 +573,74 @@ __global__ void k_eta_vjp(const PairDesc* pairs, int pair, const R* __restrict__
         const double LK[3] = {aK, aK, lam};
         const double wK = WW(x, y, t);
         double dU[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, dg[3] = {0, 0, 0}, dft = 0.0, dal = 0.0;
-        // interior
-        const double G = g[0] * g[0] / LK[0] + g[1] * g[1] / LK[1] + g[2] * g[2] / LK[2];
-        double s[3], um[3][3], S2 = 0.0;
+        double um[3][3];
         for (int a = 0; a < 3; ++a) {
             const int b = (a + 1) % 3;
             for (int c = 0; c < 3; ++c) um[a][c] = 0.5 * (V[a][c] + V[b][c]);
-            s[a] = ft + g[0] * um[a][0] + g[1] * um[a][1] + g[2] * um[a][2];
-            S2 += s[a] * s[a];
         }
-        const double integ = G * S2 / 6.0;
-        const double wi = integ > 0.0 ? wK / sqrt(2.0 * integ) : 0.0;
-        for (int a = 0; a < 3; ++a) {
-            const int b = (a + 1) % 3;
-            const double k = wi * G * s[a] / 3.0;
-            for (int c = 0; c < 3; ++c) {
-                dU[a][c] += 0.5 * k * g[c];
-                dU[b][c] += 0.5 * k * g[c];
-                dg[c] += k * um[a][c];
+        // interior
+        if (eld) {
+            const long long eo = pd.frame_off + (long long)y * pitch + x + (long long)(9 * t) * stride;
+            double A6[6], F[3];
+            for (int k = 0; k < 6; ++k) A6[k] = (double)eld[eo + k * stride];
+            for (int c = 0; c < 3; ++c) F[c] = (double)eld[eo + (6 + c) * stride];
+            const double Am[3][3] = {{A6[0], A6[1], A6[2]}, {A6[1], A6[3], A6[4]}, {A6[2], A6[4], A6[5]}};
+            double Rr[3][3], integ = 0.0;
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 3; ++c) {
+                    Rr[a][c] = F[c] - (Am[c][0] * um[a][0] + Am[c][1] * um[a][1] + Am[c][2] * um[a][2]);
+                    integ += Rr[a][c] * Rr[a][c] / LK[c];
+                }
+            integ *= 0.5 / 3.0;
+            const double wi = integ > 0.0 ? wK / sqrt(2.0 * integ) : 0.0;
+            double GA[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, GF[3] = {0, 0, 0};
+            for (int a = 0; a < 3; ++a) {
+                const int b = (a + 1) % 3;
+                double dR[3];
+                for (int c = 0; c < 3; ++c) {
+                    dR[c] = wi * Rr[a][c] / (3.0 * LK[c]);
+                    GF[c] += dR[c];
+                }
+                for (int c = 0; c < 3; ++c)
+                    for (int d = 0; d < 3; ++d) GA[c][d] -= dR[c] * um[a][d];
+                for (int d = 0; d < 3; ++d) {
+                    const double dum = -(Am[0][d] * dR[0] + Am[1][d] * dR[1] + Am[2][d] * dR[2]);
+                    dU[a][d] += 0.5 * dum;
+                    dU[b][d] += 0.5 * dum;
+                }
+                dal += wi * (0.5 / 3.0) * (-(Rr[a][0] * Rr[a][0] + Rr[a][1] * Rr[a][1]) / (aK * aK));
             }
-            dft += k;
+            // entries 00, 01, 02, 11, 12, 22, then F; negated (see above)
+            R* gp = eldg + eo;
+            gp[0] = (R)(-GA[0][0]);
+            gp[stride] = (R)(-(GA[0][1] + GA[1][0]));
+            gp[2 * stride] = (R)(-(GA[0][2] + GA[2][0]));
+            gp[3 * stride] = (R)(-GA[1][1]);
+            gp[4 * stride] = (R)(-(GA[1][2] + GA[2][1]));
+            gp[5 * stride] = (R)(-GA[2][2]);
+            for (int c = 0; c < 3; ++c) gp[(6 + c) * stride] = (R)(-GF[c]);
+        } else {
+            const double G = g[0] * g[0] / LK[0] + g[1] * g[1] / LK[1] + g[2] * g[2] / LK[2];
+            double s[3], S2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                s[a] = ft + g[0] * um[a][0] + g[1] * um[a][1] + g[2] * um[a][2];
+                S2 += s[a] * s[a];
+            }
+            const double integ = G * S2 / 6.0;
+            const double wi = integ > 0.0 ? wK / sqrt(2.0 * integ) : 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const int b = (a + 1) % 3;
+                const double k = wi * G * s[a] / 3.0;
+                for (int c = 0; c < 3; ++c) {
+                    dU[a][c] += 0.5 * k * g[c];
+                    dU[b][c] += 0.5 * k * g[c];
+                    dg[c] += k * um[a][c];
+                }
+                dft += k;
+            }
+            for (int c = 0; c < 3; ++c) dg[c] += wi * S2 / 6.0 * 2.0 * g[c] / LK[c];
+            dal += wi * S2 / 6.0 * (-(g[0] * g[0] + g[1] * g[1]) / (aK * aK));
         }
-        for (int c = 0; c < 3; ++c) dg[c] += wi * S2 / 6.0 * 2.0 * g[c] / LK[c];
-        dal += wi * S2 / 6.0 * (-(g[0] * g[0] + g[1] * g[1]) / (aK * aK));
         // edges
         double dgx[3] = {0, 0, 0}, dgy[3] = {0, 0, 0};  // dL/d(grad U_c) of this element
         for (int e = 0; e < 3; ++e) {
@@ -684,11 +748,16 @@ static cudaError_t adapt_vjp_t(const AdaptBufs& A, int pair, int H, int W, doubl
                                            eta_thr, alpha_th, A.vjp_part, A.vjp_argmax);
     k_update_vjp_max<<<1, 256, 0, st>>>(A.pairs, pair, (const unsigned long long*)A.etamax, A.vjp_part, nparts,
                                         A.vjp_argmax, A.vjp_w);
+    const bool eldm = A.eld != nullptr;  // K_rho: the frame chain goes through the element data
     k_eta_vjp<R, O><<<ge, 128, 0, st>>>(A.pairs, pair, (const R*)A.f1, (const R*)A.f2, (const R*)A.alpha, A.u,
-                                        A.vjp_w, A.lam, A.gms, (O*)da, A.vjp_buf, A.eld_stride);
+                                        A.vjp_w, A.lam, A.gms, (O*)da, A.vjp_buf, A.eld_stride,
+                                        eldm ? (const R*)A.eld : nullptr, eldm ? (R*)A.eldg : nullptr);
     const dim3 gn((W + 127) / 128, H);
-    k_eta_vjp_nodes<O><<<gn, 128, 0, st>>>(A.pairs, pair, A.vjp_buf, A.eld_stride, A.gms, (O*)dU, (O*)df2, (O*)df1);
-    return cudaGetLastError();
+    k_eta_vjp_nodes<O><<<gn, 128, 0, st>>>(A.pairs, pair, A.vjp_buf, A.eld_stride, A.gms, (O*)dU,
+                                           eldm ? nullptr : (O*)df2, eldm ? nullptr : (O*)df1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !eldm || !(df2 || df1)) return e;
+    return eld_frames_chain<R, O>(A, pair, H, W, df2, df1, A.fp64 ? T_F64 : T_F32, st);
 }
 
 cudaError_t launch_adapt_vjp(const AdaptBufs& A, int pair, int H, int W, double kappa, double eta_thr,

@@ -1059,7 +1059,6 @@ of_status of_adapt_alpha_vjp(of_handle h, double kappa, double eta_thr, double a
     if (!h) return OF_ERR_ARG;
     if (!h->solved) return fail(h, OF_ERR_STATE, "of_adapt_alpha_vjp needs a previous of_solve at the current alpha");
     if (!(kappa >= 0) || !(alpha_th > 0)) return fail(h, OF_ERR_ARG, "kappa must be >= 0 and alpha_th > 0");
-    if (h->eld) return fail(h, OF_ERR_ARG, "the adaptation-pass VJP is provided for rho = 0");
     if (!dLdalpha_new || !dLdalpha || !dLdU) return fail(h, OF_ERR_ARG, "null dL/dalpha_new, dL/dalpha or dL/dU list");
     for (int p = 0; p < h->batch; ++p) {
         void* arr[5] = {dLdalpha_new[p], dLdalpha[p], dLdU[p], dLdf2 ? dLdf2[p] : nullptr, dLdf1 ? dLdf1[p] : nullptr};
@@ -1091,9 +1090,12 @@ of_status of_adapt_alpha_vjp(of_handle h, double kappa, double eta_thr, double a
             CK(cp2d(h, h->usol + d.vec_off, ofl::T_F64, d.pitch, (float*)h->z + d.vec_off, ofl::T_F32, d.pitch,
                     3LL * d.H, d.W, st));
         CK(ofl::launch_indicator(A, p, d.H, d.W, st));
+        A.frame_off = d.frame_off;  // K_rho^T passes: the pair's planes, its r vector as scratch
+        A.pitch = d.pitch;
+        A.scratch = (char*)h->r + d.vec_off * h->es;
         CK(ofl::launch_adapt_vjp(A, p, d.H, d.W, kappa, eta_thr, alpha_th, dLdalpha_new[p], dLdalpha[p], dLdU[p],
                                  dLdf2 ? dLdf2[p] : nullptr, dLdf1 ? dLdf1[p] : nullptr, tcode(dt), st));
-        count_other(h, 6);
+        count_other(h, 6 + (h->eld && (dLdf2 || dLdf1) ? 1 + 2 * 18 : 0));
         // with K_sigma the frame gradients are w.r.t. the images given to of_set_frames
         void* sscr = (char*)h->q + d.vec_off * h->es;
         for (void* fgrad : {dLdf2 ? dLdf2[p] : nullptr, dLdf1 ? dLdf1[p] : nullptr})

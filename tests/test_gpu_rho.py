@@ -292,3 +292,68 @@ def test_rho_batch_of_two_pairs(S, oracle):
         Lam = sysm.solve_with(cs[i])
         _, w2, _ = oracle.adjoint_grad(f1, f2, a, lam, U, Lam, rho=rho)
         assert np.abs(d2[i].cpu().numpy() - w2).max() <= 1e-8 * np.abs(w2).max()
+
+
+def test_rho_adapt_alpha_vjp_batch_matches_oracle(S, oracle):
+    """of_adapt_alpha_vjp with the K_rho data term (interior residual
+    F - A_rho U_h; frame derivatives through K_rho^T) on a batch of two
+    pairs of different sizes, one spanning several blocks in x and several
+    K_rho strips in y (FP64): dL/dalpha, dL/dU, dL/df2, dL/df1 equal the
+    oracle's update and indicator VJPs at the GPU's solution."""
+    sizes = [(150, 70), (17, 26)]
+    rho, lam, kappa, thr, ath = 1.3, 1.0, 4.0, 0.25, 1e-4
+    data = []
+    for i, (W, H) in enumerate(sizes):
+        f1, f2 = synth.random_frames(W, H, 350 + i)
+        data.append((f1, f2, synth.random_alpha(W, H, 360 + i),
+                     np.random.default_rng(370 + i).standard_normal((H - 1, W - 1, 2))))
+    h = handle(S, sizes, precision=0, tile=(8, 8), sweeps=2, rho=rho, lam=lam)
+    try:
+        Us = []
+        for i, (f1, f2, a, _) in enumerate(data):
+            S.of_set_frames(h, i, dev(f1), dev(f2))
+            S.of_set_alpha(h, i, dev(a))
+            Us.append(torch.zeros(3, sizes[i][1], sizes[i][0], dtype=torch.float64, device="cuda"))
+        S.of_solve(h, Us, rtol=1e-14, max_inner=20000)
+        v = [dev(d[3]) for d in data]
+        da = [torch.zeros_like(x) for x in v]
+        dU = [torch.zeros_like(u) for u in Us]
+        d2 = [torch.zeros(hh, w, dtype=torch.float64, device="cuda") for w, hh in sizes]
+        d1 = [torch.zeros_like(x) for x in d2]
+        S.of_adapt_alpha_vjp(h, kappa, thr, ath, v, da, dU, d2, d1)
+    finally:
+        S.of_destroy(h)
+    for i, (f1, f2, a, vv) in enumerate(data):
+        U = Us[i].cpu().numpy()
+        eta = oracle.System.from_frames(f1, f2, a, lam, rho=rho).indicator(U)
+        wa, w = oracle.alpha_update_vjp(eta, a, kappa, thr, ath, vv)
+        wU, wa2, w2, w1 = oracle.indicator_vjp(f1, f2, a, lam, U, w, rho=rho)
+        for got, want in ((da[i], wa + wa2), (dU[i], wU), (d2[i], w2), (d1[i], w1)):
+            got = got.cpu().numpy()
+            assert np.abs(got - want).max() <= 1e-9 * max(np.abs(want).max(), 1e-300), i
+
+
+def test_rho_adaptation_pass_gradients_match_oracle(S, oracle):
+    """Differentiating through one adaptation pass with K_rho (FP64 handle):
+    the autograd chain of of_adjoint and of_adapt_alpha_vjp against the
+    oracle's reverse chain (pinned by central differences of direct
+    solves)."""
+    from paper_1508_02977_gb300.autograd import Solver, adapt_solve_fn
+    W, H, lam, rho = 24, 18, 1.0, 1.1
+    f1, f2 = synth.random_frames(W, H, 380)
+    a0 = synth.random_alpha(W, H, 381)
+    kappa, thr, ath = 4.0, 0.25, 1e-4
+    c = np.random.default_rng(382).standard_normal((3, H, W))
+    solver = Solver(W, H, precision=0, tile=(8, 8), sweeps=2, rtol=1e-14, lam=lam, rho=rho)
+    try:
+        t1 = dev(f1).requires_grad_(True)
+        t2 = dev(f2).requires_grad_(True)
+        ta = dev(a0).requires_grad_(True)
+        U = adapt_solve_fn(t1, t2, ta, solver, 1, kappa, thr, ath)
+        (U * dev(c)).sum().backward()
+    finally:
+        solver.close()
+    da, d2, d1 = oracle.adaptation_grad(f1, f2, a0, lam, 1, kappa, thr, ath, c, rho=rho)
+    for got, want in ((ta.grad, da), (t2.grad, d2), (t1.grad, d1)):
+        got = got.cpu().numpy()
+        assert np.abs(got - want).max() <= 1e-7 * np.abs(want).max()
