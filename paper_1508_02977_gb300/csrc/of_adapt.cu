@@ -46,22 +46,22 @@ __device__ __forceinline__ void tri_grad(int t, const R A[3], const R B[3], cons
 //             outside flux 0 on the image boundary, Lambda_e = max of the two.
 template <typename R, typename UT>
 __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict__ f1a, const R* __restrict__ f2a,
-                            const R* __restrict__ ala, const UT* __restrict__ ua, R* __restrict__ etaa, double lam_d,
-                            double gms_d, const R* __restrict__ eld, long long eld_stride,
+                            const R* __restrict__ ala, const UT* __restrict__ ua, R* __restrict__ etaa, R lam, R gms,
+                            const R* __restrict__ eld, long long eld_stride,
                             unsigned long long* __restrict__ etamax_bits) {
     const PairDesc pd = pairs[pair];
     const int W = pd.W, H = pd.H, pitch = pd.pitch;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
-    double lmax = 0.0;
+    // the running max in the storage type (max is exact; one conversion per
+    // warp: FP64 instructions per element would run on the narrow FP64 pipe)
+    R lmax = R(0);
     if (x < W - 1 && y < H - 1) {
         const R* f1 = f1a + pd.frame_off;
         const R* f2 = f2a + pd.frame_off;
         const R* al = ala + 2 * pd.frame_off;
         UView<R, UT> U{ua + pd.vec_off, (long long)H * pitch, pitch};
-        const R lam = (R)lam_d;
-        const R ilam = R(1) / lam;  // Lambda^{-1} enters as products with reciprocals
-        const R gms = (R)gms_d;      // illumination column scale (of_model)
+        const R ilam = R(1) / lam;  // Lambda^{-1} enters as products with reciprocals; gms: of_model scale
         auto F1 = [&](int xx, int yy) { return f1[(long long)yy * pitch + xx]; };
         auto F2 = [&](int xx, int yy) { return f2[(long long)yy * pitch + xx]; };
         auto AL = [&](int xx, int yy, int t) { return al[2 * ((long long)yy * pitch + xx) + t]; };
@@ -161,32 +161,40 @@ __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict
                 val += R(0.5) * he * sqrt(q);
             }
             eta[2 * ((long long)y * pitch + x) + t] = val;
-            const double dv = (double)val;
-            lmax = dv > lmax ? dv : lmax;
+            lmax = val > lmax ? val : lmax;
         }
     }
     lmax = warp_max(lmax);
-    if ((threadIdx.x & 31) == 0 && lmax > 0.0) atomicMax(etamax_bits + pair, (unsigned long long)__double_as_longlong(lmax));
+    if ((threadIdx.x & 31) == 0 && lmax > R(0))
+        atomicMax(etamax_bits + pair, (unsigned long long)__double_as_longlong((double)lmax));
 }
 
+// kappa, eta_thr, alpha_th come in the storage type; 1 / max(eta) is formed
+// (in FP64, then rounded) once per block rather than per thread.
 template <typename R>
 __global__ void k_alpha_update(const PairDesc* pairs, int pair, R* __restrict__ ala, const R* __restrict__ etaa,
-                               const unsigned long long* __restrict__ etamax_bits, double kappa, double eta_thr,
-                               double alpha_th) {
+                               const unsigned long long* __restrict__ etamax_bits, R kappa, R eta_thr, R alpha_th) {
+    __shared__ R s_im;
+    __shared__ int s_on;
     const PairDesc pd = pairs[pair];
     const int W = pd.W, pitch = pd.pitch;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
-    const double m = __longlong_as_double((long long)etamax_bits[pair]);
-    if (x >= W - 1 || !(m > 0.0)) return;
+    if (threadIdx.x == 0) {
+        const double m = __longlong_as_double((long long)etamax_bits[pair]);
+        s_on = m > 0.0;
+        s_im = s_on ? (R)(1.0 / m) : R(0);
+    }
+    __syncthreads();
+    if (x >= W - 1 || !s_on) return;
     R* al = ala + 2 * pd.frame_off;
     const R* eta = etaa + 2 * pd.frame_off;
-    const R im = (R)(1.0 / m);
+    const R im = s_im;
     for (int t = 0; t < 2; ++t) {
         const long long o = 2 * ((long long)y * pitch + x) + t;
-        const R rel = eta[o] * im - (R)eta_thr;
-        const R a = al[o] / (R(1) + (R)kappa * (rel > R(0) ? rel : R(0)));
-        al[o] = a > (R)alpha_th ? a : (R)alpha_th;
+        const R rel = eta[o] * im - eta_thr;
+        const R a = al[o] / (R(1) + kappa * (rel > R(0) ? rel : R(0)));
+        al[o] = a > alpha_th ? a : alpha_th;
     }
 }
 
@@ -199,7 +207,8 @@ cudaError_t launch_indicator(const AdaptBufs& A, int pair, int H, int W, cudaStr
                                                           (unsigned long long*)A.etamax);
     else
         k_indicator<float, float><<<grid, 128, 0, st>>>(A.pairs, pair, (const float*)A.f1, (const float*)A.f2,
-                                                        (const float*)A.alpha, A.u32, (float*)A.eta, A.lam, A.gms,
+                                                        (const float*)A.alpha, A.u32, (float*)A.eta, (float)A.lam,
+                                                        (float)A.gms,
                                                         (const float*)A.eld, A.eld_stride,
                                                         (unsigned long long*)A.etamax);
     return cudaGetLastError();
@@ -213,7 +222,8 @@ cudaError_t launch_alpha_update(const AdaptBufs& A, int pair, int H, int W, doub
                                                      (const unsigned long long*)A.etamax, kappa, eta_thr, alpha_th);
     else
         k_alpha_update<float><<<grid, 128, 0, st>>>(A.pairs, pair, (float*)A.alpha, (const float*)A.eta,
-                                                    (const unsigned long long*)A.etamax, kappa, eta_thr, alpha_th);
+                                                    (const unsigned long long*)A.etamax, (float)kappa, (float)eta_thr,
+                                                    (float)alpha_th);
     return cudaGetLastError();
 }
 

@@ -79,6 +79,26 @@ __device__ __forceinline__ DF df_from_double(double x) {
     return DF{__uint_as_float(hb), s ? -lo : lo};
 }
 
+// double -> float, rounded to nearest even, from the bits of x with integer
+// instructions (the hardware conversion runs on the FP64 pipe).  A normal
+// float result (2^-126 <= |x| < 2^128 before rounding) keeps the top 24
+// bits of the significand, rounded by the 29 bits below them; a carry out of
+// the significand moves into the exponent field, which is the correctly
+// rounded result (up to infinity above the largest float).  Zeros are
+// exact; subnormal results, infinities and NaNs take the hardware route.
+__device__ __forceinline__ float f32_from_double(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned s = (unsigned)(b >> 63);
+    const int E = (int)((b >> 52) & 0x7ffULL);
+    if ((b << 1) == 0ULL) return s ? -0.0f : 0.0f;
+    if (E < 1023 - 126 || E > 1023 + 127) return __double2float_rn(x);
+    const unsigned long long m = b & 0xfffffffffffffULL;   // 52 fraction bits
+    const unsigned top = (unsigned)(m >> 29);               // 23 fraction bits kept
+    const unsigned rest = (unsigned)(m & 0x1fffffffULL);    // 29 bits dropped
+    const bool up = rest > (1u << 28) || (rest == (1u << 28) && (top & 1u));
+    return __uint_as_float(((((unsigned)(E - 1023 + 127) << 23) | top) + (up ? 1u : 0u)) | (s << 31));
+}
+
 __device__ __forceinline__ DF shfl_down(DF v, int d) {
     return DF{__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
 }

@@ -18,7 +18,10 @@ __global__ void k_copy2d(const S* __restrict__ src, long long sp, D* __restrict_
     const long long n = rows * cols;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const long long r = i / cols, c = i - r * cols;
-        dst[r * dp + c] = (D)src[r * sp + c];
+        if constexpr (std::is_same<S, double>::value && std::is_same<D, float>::value)
+            dst[r * dp + c] = f32_from_double(src[r * sp + c]);  // off the FP64 pipe
+        else
+            dst[r * dp + c] = (D)src[r * sp + c];
     }
 }
 template <typename D>

@@ -1007,3 +1007,47 @@ def test_adapt_alpha_vjp_batch_matches_oracle(S, oracle):
         for got, want in ((da[i], wa + wa2), (dU[i], wU), (d2[i], w2), (d1[i], w1)):
             got = got.cpu().numpy()
             assert np.abs(got - want).max() <= 1e-9 * max(np.abs(want).max(), 1e-300), i
+
+
+def test_double_to_float_storage_rounds_to_nearest_even(S):
+    """FP64 frames given to an FP32 handle are stored rounded to nearest even
+    (the copy forms the rounding from the bits with integer instructions):
+    bit for bit equal to numpy's IEEE conversion on random magnitudes from
+    float underflow to overflow, exact ties between adjacent floats, one
+    double ulp either side of them, carries into the next binade, zeros,
+    infinities and NaNs."""
+    rng = np.random.default_rng(400)
+    n_rand = 120_000
+    sign = rng.choice([-1.0, 1.0], n_rand)
+    rand = sign * np.ldexp(1.0 + rng.random(n_rand), rng.integers(-160, 140, n_rand))
+    f = (rng.choice([-1.0, 1.0], 60_000) * np.ldexp(1.0 + rng.random(60_000), rng.integers(-125, 127, 60_000))
+         ).astype(np.float32)
+    nxt = np.nextafter(f, np.float32(np.inf) * np.sign(f)).astype(np.float32)
+    mid = (f.astype(np.float64) + nxt.astype(np.float64)) / 2.0      # exact in FP64
+    ties = np.concatenate([mid, np.nextafter(mid, np.inf), np.nextafter(mid, -np.inf)])
+    fmax = float(np.finfo(np.float32).max)
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, fmax, -fmax, np.nextafter(fmax, np.inf),
+                        fmax * (1 + 2.0 ** -25), fmax * (1 + 2.0 ** -24), 2.0 ** -126, -(2.0 ** -126),
+                        np.nextafter(2.0 ** -126, 0.0), 2.0 ** -149, 2.0 ** -150, 3 * 2.0 ** -151,
+                        1.0 - 2.0 ** -25, 1.0 - 2.0 ** -26, 2.0 - 2.0 ** -24, 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24])
+    vals = np.concatenate([rand, ties, special])
+    W = 1000
+    H = (vals.size + W - 1) // W
+    f1 = np.zeros(W * H)
+    f1[:vals.size] = vals
+    f1 = f1.reshape(H, W)
+    f2 = np.random.default_rng(401).standard_normal((H, W))
+    h = handle(S, [(W, H)], tile=(48, 48), overlap=0, sweeps=4, precision=S.OF_PREC_MIXED)
+    try:
+        S.of_set_frames(h, 0, dev(f1), dev(f2))
+        g1 = torch.zeros(H, W, dtype=torch.float32, device="cuda")
+        g2 = torch.zeros(H, W, dtype=torch.float32, device="cuda")
+        S.of_get_frames(h, 0, g1, g2)
+        g1 = g1.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    with np.errstate(over="ignore"):
+        want = f1.astype(np.float32)
+    nan = np.isnan(want)
+    assert np.array_equal(np.isnan(g1), nan)
+    assert np.array_equal(g1[~nan].view(np.uint32), want[~nan].view(np.uint32))
