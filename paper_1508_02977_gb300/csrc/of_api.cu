@@ -580,7 +580,10 @@ of_solve_opts with_defaults(const of_solve_opts* o, int fp64) {
     if (r.rtol <= 0) r.rtol = 1e-6;
     if (r.max_outer <= 0) r.max_outer = 20;
     if (r.max_inner <= 0) r.max_inner = 2000;
-    if (r.inner_rtol <= 0) r.inner_rtol = fp64 ? 1e-12 : 1e-4;
+    // mixed: a pass may ask the FP32 PCG for a 1e-6 reduction, about what FP32
+    // arithmetic reaches in the true residual, so that the next pass has little
+    // left to do (fewer restarts of the Krylov space than with smaller steps)
+    if (r.inner_rtol <= 0) r.inner_rtol = fp64 ? 1e-12 : 1e-6;
     return r;
 }
 
