@@ -1051,3 +1051,45 @@ def test_double_to_float_storage_rounds_to_nearest_even(S):
     nan = np.isnan(want)
     assert np.array_equal(np.isnan(g1), nan)
     assert np.array_equal(g1[~nan].view(np.uint32), want[~nan].view(np.uint32))
+
+
+@pytest.mark.parametrize("rho", [0.0, 1.3])
+def test_adapt_alpha_vjp_mixed_matches_oracle(S, oracle, rho):
+    """of_adapt_alpha_vjp on the FP32 path (the default of the autograd
+    Solver): FP64 arithmetic on the FP32-stored frames and alpha, with the
+    FP32 indicator deciding the update's branches and, with K_rho, FP32
+    element data.  Against the oracle on the same rounded inputs and the
+    GPU's solution to 1e-4 of the largest entry; the inputs keep every
+    branch of the update (threshold, clamp, argmax) at least 1e-4 away from
+    its kink, so FP32 rounding of eta cannot flip one."""
+    W, H, lam, kappa, thr, ath = 40, 30, 1.0, 4.0, 0.25, 1e-4
+    f1, f2 = synth.random_frames(W, H, 408)
+    f1, f2 = f32(f1), f32(f2)
+    a = f32(synth.random_alpha(W, H, 409))
+    v = np.random.default_rng(410).standard_normal((H - 1, W - 1, 2))
+    h = handle(S, [(W, H)], precision=S.OF_PREC_MIXED, tile=(16, 16), sweeps=2, lam=lam, rho=rho)
+    try:
+        S.of_set_frames(h, 0, dev(f1, torch.float32), dev(f2, torch.float32))
+        S.of_set_alpha(h, 0, dev(a, torch.float32))
+        U = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+        S.of_solve(h, [U], rtol=1e-10)
+        da = torch.zeros(H - 1, W - 1, 2, dtype=torch.float64, device="cuda")
+        dU = torch.zeros_like(U)
+        d2 = torch.zeros(H, W, dtype=torch.float64, device="cuda")
+        d1 = torch.zeros_like(d2)
+        S.of_adapt_alpha_vjp(h, kappa, thr, ath, [dev(v)], [da], [dU], [d2], [d1])
+    finally:
+        S.of_destroy(h)
+    U = U.cpu().numpy()
+    eta = oracle.System.from_frames(f1, f2, a, lam, rho=rho).indicator(U)
+    m = eta.max()
+    rel = eta / m - thr
+    den = 1.0 + kappa * np.maximum(rel, 0.0)
+    top2 = np.sort(eta.ravel())[-2:]
+    assert np.abs(rel).min() > 1e-4 and np.abs(a / den / ath - 1.0).min() > 1e-4
+    assert (top2[1] - top2[0]) / m > 1e-4
+    wa, w = oracle.alpha_update_vjp(eta, a, kappa, thr, ath, v)
+    wU, wa2, w2, w1 = oracle.indicator_vjp(f1, f2, a, lam, U, w, rho=rho)
+    for got, want in ((da, wa + wa2), (dU, wU), (d2, w2), (d1, w1)):
+        got = got.cpu().numpy()
+        assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
