@@ -357,3 +357,51 @@ def test_rho_adaptation_pass_gradients_match_oracle(S, oracle):
     for got, want in ((ta.grad, da), (t2.grad, d2), (t1.grad, d1)):
         got = got.cpu().numpy()
         assert np.abs(got - want).max() <= 1e-7 * np.abs(want).max()
+
+
+def test_rho_constant_model_adjoint_and_vjp_match_oracle(S, oracle):
+    """Brightness constancy (OF_MODEL_CONSTANT: g = (d/dx f2, d/dy f2, 0))
+    with K_rho, FP64 path: flow = the oracle's flow-block direct solve, m
+    stays 0, and the adjoint gradients and the one-pass adaptation VJP equal
+    the oracle's."""
+    W, H, rho, lam, kappa, thr, ath = 30, 22, 1.3, 1.0, 4.0, 0.25, 1e-4
+    f1, f2 = synth.random_frames(W, H, 420)
+    a = synth.random_alpha(W, H, 421)
+    gt = np.random.default_rng(422).uniform(-1, 1, (2, H, W))
+    v = np.random.default_rng(423).standard_normal((H - 1, W - 1, 2))
+    sysm = oracle.System.from_frames(f1, f2, a, lam, model=1, rho=rho)
+    Ud = sysm.solve_direct()
+    h = handle(S, [(W, H)], precision=0, tile=(8, 8), sweeps=2, rho=rho, lam=lam, model=S.OF_MODEL_CONSTANT)
+    try:
+        S.of_set_frames(h, 0, dev(f1), dev(f2))
+        S.of_set_alpha(h, 0, dev(a))
+        U = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+        S.of_solve(h, [U], rtol=1e-14, max_inner=20000)
+        Un = U.cpu().numpy()
+        ga = torch.zeros(H - 1, W - 1, 2, dtype=torch.float64, device="cuda")
+        g2 = torch.zeros(H, W, dtype=torch.float64, device="cuda")
+        g1 = torch.zeros_like(g2)
+        S.of_adjoint(h, [dev(oracle.mean_epe_grad(Un, gt))], [ga], [g2], [g1])
+        # the adjoint solve left the pass's solution in place: re-solve, then the VJP
+        S.of_solve(h, [U], rtol=1e-14, max_inner=20000)
+        da = torch.zeros_like(ga)
+        dU = torch.zeros_like(U)
+        d2 = torch.zeros_like(g2)
+        d1 = torch.zeros_like(g2)
+        S.of_adapt_alpha_vjp(h, kappa, thr, ath, [dev(v)], [da], [dU], [d2], [d1])
+        U2 = U.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    assert np.abs(Un[2]).max() == 0.0
+    assert np.linalg.norm(Un - Ud) <= 1e-10 * np.linalg.norm(Ud)
+    Lo = sysm.solve_with(oracle.mean_epe_grad(Ud, gt))
+    wa, w2, w1 = oracle.adjoint_grad(f1, f2, a, lam, Ud, Lo, model=1, rho=rho)
+    for got, want in ((ga, wa), (g2, w2), (g1, w1)):
+        got = got.cpu().numpy()
+        assert np.abs(got - want).max() <= 1e-8 * np.abs(want).max()
+    eta = sysm.indicator(U2)
+    ua, w = oracle.alpha_update_vjp(eta, a, kappa, thr, ath, v)
+    wU, wa2, v2, v1 = oracle.indicator_vjp(f1, f2, a, lam, U2, w, model=1, rho=rho)
+    for got, want in ((da, ua + wa2), (dU, wU), (d2, v2), (d1, v1)):
+        got = got.cpu().numpy()
+        assert np.abs(got - want).max() <= 1e-9 * max(np.abs(want).max(), 1e-300)
