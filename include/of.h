@@ -140,8 +140,9 @@ of_status of_create(of_handle *h, int device, void *cuda_stream);
 /* Declares a batch of `batch` frame pairs, pair p of W[p] x H[p] nodes
  * (W, H >= 2; host arrays), and allocates the device workspace for them.
  * Frames, alpha and solutions of earlier setups are discarded.  Returns
- * OF_ERR_ARG for bad sizes or options, OF_ERR_OOM if the workspace does not
- * fit. */
+ * OF_ERR_ARG for bad sizes or options (the earlier setup then stays as it
+ * was), OF_ERR_OOM if the workspace does not fit (the handle then holds no
+ * grid: later calls return OF_ERR_STATE until a setup succeeds). */
 of_status of_setup_grid(of_handle h, int batch, const int32_t *W, const int32_t *H, const of_grid_opts *o);
 
 /* Copies the two frames of pair `pair` ([H][pitch], dtype dt, pitch >=
@@ -280,7 +281,6 @@ of_status of_get_profile(of_handle h, of_profile *out);
 of_status of_residual_noalloc(int W, int H, const double *f1, const double *f2, const double *alpha,
                               double lambda, const double *U, double *r, double *norms, void *cuda_stream);
 
-/* Releases the workspace and the handle (NULL is accepted). */
 /* Upper bound of every device wait (the preconditioner's TMA staging
  * barriers), in SM clock cycles [4e9, about 2 s].  A wait that runs out sets a
  * device error word; the kernel stops staging, still completes, and the call
@@ -295,6 +295,14 @@ of_status of_set_wait_limit(of_handle h, int64_t cycles);
  * the wait limit.  0 turns it off. */
 of_status of_debug_starve_staging(of_handle h, int extra_bytes);
 
+/* Test hook for the allocation failure path; no counterpart in the paper.
+ * With bytes > 0 the handle's device allocations fail (as out of memory)
+ * once they would hold more than `bytes` in all, so that OF_ERR_OOM can be
+ * provoked without exhausting the GPU.  0 removes the limit.  OF_ERR_ARG for
+ * bytes < 0. */
+of_status of_set_alloc_limit(of_handle h, int64_t bytes);
+
+/* Releases the workspace and the handle (NULL is accepted). */
 of_status of_destroy(of_handle h);
 
 /* Message for the last non-OK status of h (or of a failed of_create when h

@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -44,6 +45,8 @@ struct of_ctx {
     int nblk_total = 0, ntiles_total = 0, rows_per_block = 16;
     // device memory
     std::vector<void*> allocs;
+    size_t alloc_bytes = 0, alloc_limit = 0;  // bytes held; test hook: budget (0: none)
+    bool setup_started = false;               // of_setup_grid got past validation (workspace released)
     void *f1 = nullptr, *f2 = nullptr, *alpha = nullptr, *eta = nullptr;
     double *x[2] = {nullptr, nullptr}, *usol = nullptr, *cvec = nullptr;
     void *r = nullptr, *z = nullptr, *q = nullptr, *d = nullptr, *p0 = nullptr, *p1 = nullptr;
@@ -147,6 +150,7 @@ void free_all(of_ctx* h) {
     h->loop_graph = nullptr;
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
+    h->alloc_bytes = 0;
     if (h->sc_host) cudaFreeHost(h->sc_host);
     h->sc_host = nullptr;
     h->f1 = h->f2 = h->alpha = h->eta = nullptr;
@@ -159,12 +163,23 @@ void free_all(of_ctx* h) {
 template <typename T>
 cudaError_t dalloc(of_ctx* h, T** p, size_t bytes) {
     void* v = nullptr;
-    cudaError_t e = cudaMalloc(&v, bytes < 256 ? 256 : bytes);
+    if (bytes < 256) bytes = 256;
+    if (h->alloc_limit && h->alloc_bytes + bytes > h->alloc_limit) return cudaErrorMemoryAllocation;  // injected
+    cudaError_t e = cudaMalloc(&v, bytes);
     if (e != cudaSuccess) return e;
     h->allocs.push_back(v);
+    h->alloc_bytes += bytes;
     *p = (T*)v;
     return cudaSuccess;
 }
+
+// NVTX range over one entry point or phase (a no-op unless a tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 cudaEvent_t pool_event(of_ctx* h) {
     if (!h->evpool.empty()) {
@@ -493,6 +508,7 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
     CK(cudaMemsetAsync(h->sc_dev, 0, sizeof(PairScalars) * h->batch, st));
     CK(cudaMemsetAsync(h->err_dev, 0, sizeof(int), st));
     for (int pass = 0;; ++pass) {
+        NvtxRange nv_pass("refinement pass");
         const int first = (pass == 0);
         double* xout = first ? nullptr : h->x[1 - cur];
         // a cold start (x = 0) needs only the load vector for its first residual
@@ -612,7 +628,8 @@ of_status of_create(of_handle* hp, int device, void* cuda_stream) {
     return OF_OK;
 }
 
-of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t* H, const of_grid_opts* o) {
+static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const int32_t* H,
+                                 const of_grid_opts* o) {
     if (!h) return OF_ERR_ARG;
     if (batch < 1 || !W || !H) return fail(h, OF_ERR_ARG, "batch must be >= 1 with W and H arrays");
     DevGuard g(h->device);
@@ -663,6 +680,7 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
 
     CK(cudaStreamSynchronize(h->stream));
     free_all(h);
+    h->setup_started = true;
     h->opts = opt;
     // K_sigma / K_rho taps: w_k = exp(-k^2 / (2 s^2)), |k| <= ceil(3 s)
     auto make_taps = [](double sd) {
@@ -876,7 +894,26 @@ of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t*
     return OF_OK;
 }
 
+// A failure after validation leaves no grid (the old workspace is already
+// released): later calls see OF_ERR_STATE instead of half-built buffers.
+of_status of_setup_grid(of_handle h, int batch, const int32_t* W, const int32_t* H, const of_grid_opts* o) {
+    if (!h) return OF_ERR_ARG;
+    NvtxRange nv("of_setup_grid");
+    h->setup_started = false;
+    const of_status s = setup_grid_impl(h, batch, W, H, o);
+    if (s != OF_OK && h->setup_started) free_all(h);
+    return s;
+}
+
+of_status of_set_alloc_limit(of_handle h, int64_t bytes) {
+    if (!h) return OF_ERR_ARG;
+    if (bytes < 0) return fail(h, OF_ERR_ARG, "bytes must be >= 0");
+    h->alloc_limit = (size_t)bytes;
+    return OF_OK;
+}
+
 of_status of_set_frames(of_handle h, int pair, const void* f1, const void* f2, of_dtype dt, int64_t pitch) {
+    NvtxRange nv("of_set_frames");
     of_status s = check_pair(h, pair);
     if (s != OF_OK) return s;
     const PairDesc& d = h->pd[pair];
@@ -978,6 +1015,7 @@ of_status of_get_alpha(of_handle h, int pair, void* alpha, of_dtype dt) {
 }
 
 of_status of_solve(of_handle h, const of_solve_opts* o, void* const* U, of_dtype dt, of_solve_info* info) {
+    NvtxRange nv("of_solve");
     if (!h) return OF_ERR_ARG;
     if (h->batch == 0) return fail(h, OF_ERR_STATE, "of_setup_grid has not been called");
     for (int p = 0; p < h->batch; ++p)
@@ -1028,6 +1066,7 @@ of_status of_solve(of_handle h, const of_solve_opts* o, void* const* U, of_dtype
 }
 
 of_status of_adapt_alpha(of_handle h, double kappa, double eta_thr, double alpha_th, void* const* eta, of_dtype dt) {
+    NvtxRange nv("of_adapt_alpha");
     if (!h) return OF_ERR_ARG;
     if (!h->solved) return fail(h, OF_ERR_STATE, "of_adapt_alpha needs a previous of_solve");
     if (!(kappa >= 0) || !(alpha_th > 0)) return fail(h, OF_ERR_ARG, "kappa must be >= 0 and alpha_th > 0");
@@ -1059,6 +1098,7 @@ of_status of_adapt_alpha(of_handle h, double kappa, double eta_thr, double alpha
 of_status of_adapt_alpha_vjp(of_handle h, double kappa, double eta_thr, double alpha_th, void* const* dLdalpha_new,
                              void* const* dLdalpha, void* const* dLdU, void* const* dLdf2, void* const* dLdf1,
                              of_dtype dt) {
+    NvtxRange nv("of_adapt_alpha_vjp");
     if (!h) return OF_ERR_ARG;
     if (!h->solved) return fail(h, OF_ERR_STATE, "of_adapt_alpha_vjp needs a previous of_solve at the current alpha");
     if (!(kappa >= 0) || !(alpha_th > 0)) return fail(h, OF_ERR_ARG, "kappa must be >= 0 and alpha_th > 0");
@@ -1111,6 +1151,7 @@ of_status of_adapt_alpha_vjp(of_handle h, double kappa, double eta_thr, double a
 
 of_status of_adjoint(of_handle h, void* const* dLdU, void* const* dLdalpha, void* const* dLdf2, void* const* dLdf1,
                      of_dtype dt, of_solve_info* info) {
+    NvtxRange nv("of_adjoint");
     if (!h) return OF_ERR_ARG;
     if (!h->solved) return fail(h, OF_ERR_STATE, "of_adjoint needs a previous of_solve");
     if (!dLdU) return fail(h, OF_ERR_ARG, "null dL/dU list");

@@ -71,6 +71,7 @@ _lib.of_get_alpha.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_int]
 _lib.of_get_frames.argtypes = [_h, ctypes.c_int, _vp, _vp, ctypes.c_int]
 _lib.of_get_element_data.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_int]
 _lib.of_set_wait_limit.argtypes = [_h, ctypes.c_int64]
+_lib.of_set_alloc_limit.argtypes = [_h, ctypes.c_int64]
 _lib.of_debug_starve_staging.argtypes = [_h, ctypes.c_int]
 _lib.of_solve.argtypes = [_h, ctypes.POINTER(SolveOpts), ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(SolveInfo)]
 _lib.of_adapt_alpha.argtypes = [_h, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp), ctypes.c_int]
@@ -97,6 +98,7 @@ EXPORTS = ("of_create", "of_setup_grid", "of_set_frames", "of_get_frames", "of_g
            "of_get_alpha", "of_solve",
            "of_adapt_alpha", "of_adapt_alpha_vjp", "of_adjoint", "of_apply", "of_precondition", "of_residual",
            "of_set_profiling", "of_get_profile", "of_residual_noalloc", "of_set_wait_limit", "of_debug_starve_staging",
+           "of_set_alloc_limit",
            "of_destroy", "of_last_error")
 
 
@@ -287,6 +289,12 @@ def of_residual(h, pair, U) -> float:
     rel = ctypes.c_double(0.0)
     _check(h, _lib.of_residual(h, int(pair), _vp(pu), dt, ctypes.byref(rel)))
     return float(rel.value)
+
+
+def of_set_alloc_limit(h, nbytes):
+    """Test hook: the handle's device allocations fail as out of memory past
+    nbytes in all (0: no limit)."""
+    return _check(h, _lib.of_set_alloc_limit(h, int(nbytes)))
 
 
 def of_set_wait_limit(h, cycles):

@@ -74,5 +74,7 @@ def test_create_without_gpu_reports_an_error(lib):
 def test_null_handle_calls_return_arg_error(lib):
     lib.of_solve.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     assert lib.of_solve(None, None, None, 0, None) == 1  # OF_ERR_ARG
+    lib.of_set_alloc_limit.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    assert lib.of_set_alloc_limit(None, 0) == 1
     lib.of_destroy.argtypes = [ctypes.c_void_p]
     assert lib.of_destroy(None) == 0

@@ -1093,3 +1093,78 @@ def test_adapt_alpha_vjp_mixed_matches_oracle(S, oracle, rho):
     for got, want in ((da, wa + wa2), (dU, wU), (d2, w2), (d1, w1)):
         got = got.cpu().numpy()
         assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
+
+
+def test_injected_allocation_failure_leaves_no_grid(S):
+    """OF_ERR_OOM through the allocation budget test hook (no real memory
+    pressure): the failed setup leaves the handle without a grid, so later
+    calls report OF_ERR_STATE instead of touching half-built buffers, and
+    the handle sets up and solves once the budget is lifted."""
+    W, H = 640, 480
+    f1, f2 = synth.random_frames(W, H, 430)
+    h = S.of_create(0)
+    try:
+        S.of_setup_grid(h, [(64, 48)], tile=(16, 16), precision=S.OF_PREC_MIXED)
+        S.of_set_alloc_limit(h, 1 << 20)  # 1 MiB: the 640x480 workspace does not fit
+        with pytest.raises(S.OFError) as e:
+            S.of_setup_grid(h, [(W, H)], tile=(48, 48), sweeps=4, omega=1.6, precision=S.OF_PREC_MIXED)
+        assert e.value.status == S.OF_ERR_OOM
+        U = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+        with pytest.raises(S.OFError) as e:
+            S.of_set_frames(h, 0, dev(f1), dev(f2))
+        assert e.value.status == S.OF_ERR_STATE
+        with pytest.raises(S.OFError) as e:
+            S.of_solve(h, [U])
+        assert e.value.status == S.OF_ERR_STATE
+        with pytest.raises(S.OFError) as e:
+            S.of_set_alloc_limit(h, -1)
+        assert e.value.status == S.OF_ERR_ARG
+        S.of_set_alloc_limit(h, 0)
+        S.of_setup_grid(h, [(W, H)], tile=(48, 48), sweeps=4, omega=1.6, precision=S.OF_PREC_MIXED)
+        S.of_set_frames(h, 0, dev(f1), dev(f2))
+        S.of_set_alpha(h, 0, None, 0.05)
+        st, info = S.of_solve(h, [U])
+        assert st == S.OF_OK and info[0]["rel_residual"] <= 1e-6
+    finally:
+        S.of_destroy(h)
+
+
+def test_solves_are_bitwise_repeatable(S):
+    """Deterministic reductions: the same mixed solve, adaptation pass and
+    adjoint, run twice in one handle and once in a fresh handle, give
+    bit-identical solutions, alpha fields, gradients and iteration counts."""
+    t = synth.texture()
+    W, H = t.W, t.H
+    f1, f2 = dev(t.f1, torch.float32), dev(t.f2, torch.float32)
+    c = dev(np.random.default_rng(431).standard_normal((3, H, W)))
+
+    def run(h):
+        S.of_set_frames(h, 0, f1, f2)
+        S.of_set_alpha(h, 0, None, t.alpha0)
+        U = torch.zeros(3, H, W, dtype=torch.float64, device="cuda")
+        _, info = S.of_solve(h, [U], rtol=1e-6)
+        da = torch.zeros(H - 1, W - 1, 2, dtype=torch.float64, device="cuda")
+        d2 = torch.zeros(H, W, dtype=torch.float64, device="cuda")
+        S.of_adjoint(h, [c], [da], [d2])
+        S.of_adapt_alpha(h, 4.0, 0.25, 5e-4)
+        a = torch.zeros(H - 1, W - 1, 2, dtype=torch.float64, device="cuda")
+        S.of_get_alpha(h, 0, a)
+        return [x.cpu().numpy() for x in (U, da, d2, a)], (info[0]["inner_iters"], info[0]["outer_iters"],
+                                                            info[0]["rel_residual"])
+
+    opts = dict(tile=(48, 48), sweeps=4, omega=1.6, precision=S.OF_PREC_MIXED)
+    h1 = handle(S, [(W, H)], **opts)
+    try:
+        r1, i1 = run(h1)
+        r2, i2 = run(h1)
+    finally:
+        S.of_destroy(h1)
+    h2 = handle(S, [(W, H)], **opts)
+    try:
+        r3, i3 = run(h2)
+    finally:
+        S.of_destroy(h2)
+    assert i1 == i2 == i3
+    for a, b, cc in zip(r1, r2, r3):
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+        assert np.array_equal(a.view(np.uint64), cc.view(np.uint64))
