@@ -313,22 +313,40 @@ int orc_apply_elementwise(int W, int H, const double *g, const double *ft, const
 
 /* ---------------------------------------------------- banded Cholesky -- */
 
-/* Solves A x = b for the CSR matrix of a W x H grid by banded Cholesky.
- * Unknowns are renumbered node-major with the shorter grid side as the fast
- * index, giving half-bandwidth 3*(min(W,H)+1)+2.  Returns 3 if A is not
- * positive definite, 4 on allocation failure. */
-int orc_band_cholesky_solve(int W, int H, const int64_t *rowptr, const int64_t *col, const double *val,
-                            const double *b, double *x)
+/* Banded Cholesky factor of the CSR matrix of a W x H grid.  Unknowns are
+ * renumbered node-major with the shorter grid side as the fast index, giving
+ * half-bandwidth bw = 3*(min(W,H)+1)+2; L is stored by rows, entry (i, j),
+ * j <= i, at L[i*(bw+1) + (i-j)]. */
+typedef struct {
+    long n, bw;
+    long *perm; /* perm[global] = banded index */
+    double *L;
+} band_t;
+
+static void band_free(band_t *F)
+{
+    free(F->perm);
+    free(F->L);
+    F->perm = NULL;
+    F->L = NULL;
+}
+
+/* Returns 0, 3 if A is not positive definite, 4 on allocation failure, 5 if
+ * an entry lies outside the band. */
+static int band_factor(int W, int H, const int64_t *rowptr, const int64_t *col, const double *val, band_t *F)
 {
     long N = (long)W * H;
     long n = 3 * N;
     int fastW = (W <= H);
     long fast = fastW ? W : H;
     long bw = 3 * (fast + 1) + 2;
-    long *perm = malloc(sizeof(long) * n); /* perm[global] = banded index */
-    double *L = calloc((size_t)n * (bw + 1), sizeof(double));
-    double *z = malloc(sizeof(double) * n);
-    if (!perm || !L || !z) { free(perm); free(L); free(z); return 4; }
+    F->n = n;
+    F->bw = bw;
+    F->perm = malloc(sizeof(long) * n);
+    F->L = calloc((size_t)n * (bw + 1), sizeof(double));
+    if (!F->perm || !F->L) { band_free(F); return 4; }
+    long *perm = F->perm;
+    double *L = F->L;
     for (int c = 0; c < 3; c++)
         for (int y = 0; y < H; y++)
             for (int xx = 0; xx < W; xx++) {
@@ -340,7 +358,7 @@ int orc_band_cholesky_solve(int W, int H, const int64_t *rowptr, const int64_t *
         for (int64_t p = rowptr[r]; p < rowptr[r + 1]; p++) {
             long i = perm[r], j = perm[col[p]];
             if (j <= i) {
-                if (i - j > bw) { free(perm); free(L); free(z); return 5; }
+                if (i - j > bw) { band_free(F); return 5; }
                 L[i * (bw + 1) + (i - j)] = val[p];
             }
         }
@@ -348,7 +366,7 @@ int orc_band_cholesky_solve(int W, int H, const int64_t *rowptr, const int64_t *
         double d = L[j * (bw + 1)];
         long k0 = j - bw > 0 ? j - bw : 0;
         for (long k = k0; k < j; k++) { double v = L[j * (bw + 1) + (j - k)]; d -= v * v; }
-        if (!(d > 0.0)) { free(perm); free(L); free(z); return 3; }
+        if (!(d > 0.0)) { band_free(F); return 3; }
         d = sqrt(d);
         L[j * (bw + 1)] = d;
         long i1 = j + bw < n - 1 ? j + bw : n - 1;
@@ -359,7 +377,16 @@ int orc_band_cholesky_solve(int W, int H, const int64_t *rowptr, const int64_t *
             L[i * (bw + 1) + (i - j)] = s / d;
         }
     }
-    /* forward: L z = Pb ; backward: L^T w = z */
+    return 0;
+}
+
+/* x = A^{-1} b from the factor: forward L z = P b, backward L^T w = z.  z is
+ * work space of n doubles. */
+static void band_solve(const band_t *F, const double *b, double *x, double *z)
+{
+    const long n = F->n, bw = F->bw;
+    const long *perm = F->perm;
+    const double *L = F->L;
     for (long r = 0; r < n; r++) z[perm[r]] = b[r];
     for (long i = 0; i < n; i++) {
         double s = z[i];
@@ -374,7 +401,21 @@ int orc_band_cholesky_solve(int W, int H, const int64_t *rowptr, const int64_t *
         z[i] = s / L[i * (bw + 1)];
     }
     for (long r = 0; r < n; r++) x[r] = z[perm[r]];
-    free(perm); free(L); free(z);
+}
+
+/* Solves A x = b for the CSR matrix of a W x H grid by banded Cholesky.
+ * Returns 3 if A is not positive definite, 4 on allocation failure. */
+int orc_band_cholesky_solve(int W, int H, const int64_t *rowptr, const int64_t *col, const double *val,
+                            const double *b, double *x)
+{
+    band_t F = {0, 0, NULL, NULL};
+    int rc = band_factor(W, H, rowptr, col, val, &F);
+    if (rc) return rc;
+    double *z = malloc(sizeof(double) * F.n);
+    if (!z) { band_free(&F); return 4; }
+    band_solve(&F, b, x, z);
+    free(z);
+    band_free(&F);
     return 0;
 }
 
@@ -551,6 +592,148 @@ int orc_schwarz(int W, int H, const int64_t *rowptr, const int64_t *col, const d
     }
     free(Unew);
     return rc;
+}
+
+/* ------------------------------- PCG with additive Schwarz (large grids) -- */
+
+/* The rows and columns of A inside the extended tile ext = [x0,x1) x [y0,y1),
+ * stored as the CSR matrix of a w x h grid (local unknown c*w*h + (y-y0)*w +
+ * (x-x0)): the local matrix A_i = R_i A R_i^T of a subdomain with zero
+ * Dirichlet values outside it. */
+static int local_matrix(int W, int H, const int64_t *rowptr, const int64_t *col, const double *val,
+                        const int ext[4], int64_t *rp, int64_t *cl, double *vl)
+{
+    long N = (long)W * H;
+    int w = ext[1] - ext[0], h = ext[3] - ext[2];
+    long wh = (long)w * h;
+    orc_csr_pattern(w, h, rp, cl);
+    memset(vl, 0, sizeof(double) * rp[3 * wh]);
+    for (int c = 0; c < 3; c++)
+        for (int y = ext[2]; y < ext[3]; y++)
+            for (int x = ext[0]; x < ext[1]; x++) {
+                long r = c * N + (long)y * W + x;
+                long lr = c * wh + (long)(y - ext[2]) * w + (x - ext[0]);
+                for (int64_t p = rowptr[r]; p < rowptr[r + 1]; p++) {
+                    long gc = col[p], nd = gc % N;
+                    int d = (int)(gc / N), yy = (int)(nd / W), xx = (int)(nd % W);
+                    if (xx < ext[0] || xx >= ext[1] || yy < ext[2] || yy >= ext[3]) continue;
+                    long lc = d * wh + (long)(yy - ext[2]) * w + (xx - ext[0]);
+                    if (csr_add(rp, cl, vl, lr, lc, val[p])) return 2;
+                }
+            }
+    return 0;
+}
+
+/* Conjugate gradients with the one-level additive Schwarz preconditioner
+ * with exact subdomain solves (the textbook ASM):
+ *     z = sum_i R_i^T A_i^{-1} R_i r,
+ * R_i the restriction to the extended tile i of a px x py partition (tiles
+ * of near-equal size, extended by ov node layers where not on the image
+ * boundary: the subdomains of orc_schwarz), A_i = R_i A R_i^T factored once
+ * by banded Cholesky.  The sum is symmetric positive definite, so CG applies.
+ * The local solves run in parallel into separate buffers and are added in
+ * tile order (deterministic).  Starts from x, stops when ||b - A x||_2 <=
+ * tol ||b||_2 (the recursive residual; *relres is recomputed as b - A x).
+ * Returns the iteration count, -1 on breakdown or a failed factorisation,
+ * -2 on allocation failure. */
+int orc_asm_pcg(int W, int H, const int64_t *rowptr, const int64_t *col, const double *val,
+                const double *b, double *x, int px, int py, int ov, double tol, int maxit, double *relres)
+{
+    long N = (long)W * H, n = 3 * N;
+    int nsub = px * py;
+    band_t *F = calloc(nsub, sizeof(band_t));
+    long *off = malloc(sizeof(long) * (nsub + 1));
+    int (*ext)[4] = malloc(sizeof(int[4]) * nsub);
+    if (!F || !off || !ext) { free(F); free(off); free(ext); return -2; }
+    long maxm = 0;
+    off[0] = 0;
+    for (int s = 0; s < nsub; s++) {
+        int own[4];
+        subdomain(W, H, px, py, s, ov, own, ext[s]);
+        long m = 3L * (ext[s][1] - ext[s][0]) * (ext[s][3] - ext[s][2]);
+        off[s + 1] = off[s] + m;
+        if (m > maxm) maxm = m;
+    }
+    int fail = 0;
+#pragma omp parallel for schedule(dynamic) reduction(| : fail)
+    for (int s = 0; s < nsub; s++) {
+        int w = ext[s][1] - ext[s][0], h = ext[s][3] - ext[s][2];
+        int64_t nnzl = orc_csr_nnz(w, h);
+        long m = 3L * w * h;
+        int64_t *rp = malloc(sizeof(int64_t) * (m + 1)), *cl = malloc(sizeof(int64_t) * nnzl);
+        double *vl = malloc(sizeof(double) * nnzl);
+        if (!rp || !cl || !vl) fail |= 4;
+        else if (local_matrix(W, H, rowptr, col, val, ext[s], rp, cl, vl)) fail |= 2;
+        else if (band_factor(w, h, rp, cl, vl, &F[s])) fail |= 1;
+        free(rp); free(cl); free(vl);
+    }
+    double *r = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
+    double *p = malloc(sizeof(double) * n), *q = malloc(sizeof(double) * n);
+    double *loc = malloc(sizeof(double) * (off[nsub] > 0 ? off[nsub] : 1));
+    int it = 0;
+    if (fail || !r || !z || !p || !q || !loc) {
+        it = (fail & 4) || !r || !z || !p || !q || !loc ? -2 : -1;
+        goto done;
+    }
+    orc_csr_matvec(n, rowptr, col, val, x, q);
+    for (long i = 0; i < n; i++) r[i] = b[i] - q[i];
+    double nb = sqrt(dot(n, b, b));
+    if (nb == 0.0) nb = 1.0;
+    double rz = 0.0;
+    double rn = sqrt(dot(n, r, r));
+    while (rn > tol * nb && it < maxit) {
+        /* z = M r: local solves of R_i r, then the sum of R_i^T z_i */
+        int afail = 0;
+#pragma omp parallel reduction(| : afail)
+        {
+            double *rhs = malloc(sizeof(double) * maxm), *wk = malloc(sizeof(double) * maxm);
+            if (!rhs || !wk) afail |= 1;
+#pragma omp for schedule(dynamic)
+            for (int s = 0; s < nsub; s++) {
+                if (!rhs || !wk) continue;
+                int w = ext[s][1] - ext[s][0], h = ext[s][3] - ext[s][2];
+                long wh = (long)w * h;
+                for (int c = 0; c < 3; c++)
+                    for (int y = ext[s][2]; y < ext[s][3]; y++)
+                        for (int xx = ext[s][0]; xx < ext[s][1]; xx++)
+                            rhs[c * wh + (long)(y - ext[s][2]) * w + (xx - ext[s][0])] = r[c * N + (long)y * W + xx];
+                band_solve(&F[s], rhs, loc + off[s], wk);
+            }
+            free(rhs); free(wk);
+        }
+        if (afail) { it = -2; goto done; }
+        memset(z, 0, sizeof(double) * n);
+        for (int s = 0; s < nsub; s++) {
+            int w = ext[s][1] - ext[s][0], h = ext[s][3] - ext[s][2];
+            long wh = (long)w * h;
+            const double *zl = loc + off[s];
+            for (int c = 0; c < 3; c++)
+                for (int y = ext[s][2]; y < ext[s][3]; y++)
+                    for (int xx = ext[s][0]; xx < ext[s][1]; xx++)
+                        z[c * N + (long)y * W + xx] += zl[c * wh + (long)(y - ext[s][2]) * w + (xx - ext[s][0])];
+        }
+        double rz_new = dot(n, r, z);
+        if (it == 0) memcpy(p, z, sizeof(double) * n);
+        else {
+            double beta = rz_new / rz;
+            for (long i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
+        }
+        rz = rz_new;
+        orc_csr_matvec(n, rowptr, col, val, p, q);
+        double pq = dot(n, p, q);
+        if (!(pq > 0.0)) { it = -1; goto done; }
+        double a = rz / pq;
+        for (long i = 0; i < n; i++) { x[i] += a * p[i]; r[i] -= a * q[i]; }
+        rn = sqrt(dot(n, r, r));
+        it++;
+    }
+    orc_csr_matvec(n, rowptr, col, val, x, q);
+    for (long i = 0; i < n; i++) r[i] = b[i] - q[i];
+    if (relres) *relres = sqrt(dot(n, r, r)) / nb;
+done:
+    for (int s = 0; s < nsub; s++) band_free(&F[s]);
+    free(F); free(off); free(ext); free(r); free(z); free(p); free(q); free(loc);
+    return it;
 }
 
 /* --------------------------------------- error indicator (Eq. errind) -- */

@@ -57,6 +57,8 @@ def _load():
         L.orc_apply_elementwise.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p, ctypes.c_void_p]
         L.orc_band_cholesky_solve.argtypes = [i32, i32, _i64p, _i64p, _f64p, _f64p, _f64p]
         L.orc_pcg.argtypes = [i32, i32, _i64p, _i64p, _f64p, _f64p, _f64p, f64, i32, ctypes.POINTER(f64)]
+        L.orc_asm_pcg.argtypes = [i32, i32, _i64p, _i64p, _f64p, _f64p, _f64p, i32, i32, i32, f64, i32,
+                                  ctypes.POINTER(f64)]
         L.orc_schwarz.argtypes = [i32, i32, _i64p, _i64p, _f64p, _f64p, i32, i32, i32, i32, _f64p, ctypes.c_void_p]
         L.orc_indicator.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p]
         L.orc_indicator_el.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p]
@@ -236,6 +238,23 @@ class System:
         it = L.orc_pcg(self.W, self.H, self.rowptr, self.col, self.val, b, x, tol, maxit, ctypes.byref(rr))
         if it < 0:
             raise RuntimeError("oracle PCG breakdown")
+        return x.reshape(3, self.H, self.W), int(it), float(rr.value)
+
+    def solve_asm_pcg(self, parts, overlap, tol=1e-12, maxit=100000, x0=None, rhs=None):
+        """PCG with the exact-subdomain additive Schwarz preconditioner on a
+        parts = (px, py) partition extended by `overlap` node layers (the
+        solver for grids too large for banded Cholesky); returns (U,
+        iterations, final relative residual recomputed as b - A U)."""
+        L = _load()
+        x = np.zeros(self.n) if x0 is None else _c(x0).ravel().copy()
+        b = self.b if rhs is None else _c(rhs).ravel()
+        rr = ctypes.c_double(0.0)
+        it = L.orc_asm_pcg(self.W, self.H, self.rowptr, self.col, self.val, b, x, int(parts[0]), int(parts[1]),
+                           int(overlap), tol, maxit, ctypes.byref(rr))
+        if it == -2:
+            raise MemoryError("oracle ASM-PCG: allocation failed")
+        if it < 0:
+            raise RuntimeError("oracle ASM-PCG breakdown (a subdomain matrix is not positive definite)")
         return x.reshape(3, self.H, self.W), int(it), float(rr.value)
 
     def solve_with(self, rhs, direct=True, tol=1e-13):

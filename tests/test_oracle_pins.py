@@ -223,6 +223,71 @@ def test_pcg_matches_direct_on_blobs(oracle):
     assert np.linalg.norm(Up - Ud) <= 1e-10 * np.linalg.norm(Ud)
 
 
+def test_asm_pcg_matches_direct_on_blobs(oracle):
+    """PCG with the exact-subdomain additive Schwarz preconditioner (the
+    large-grid solver) on the 64x48 blobs pair, 2x2 parts, 4-node overlap:
+    the banded-Cholesky solution."""
+    p = synth.blobs()
+    S = oracle.System.from_frames(p.f1, p.f2, p.alpha0, p.lam)
+    Ud = S.solve_direct()
+    U, it, rr = S.solve_asm_pcg((2, 2), 4, tol=1e-13)
+    assert rr <= 1e-13
+    assert np.linalg.norm(U - Ud) <= 1e-10 * np.linalg.norm(Ud)
+
+
+def test_asm_pcg_limits(oracle):
+    """One subdomain: the preconditioner is A^{-1} and CG stops after one
+    step at the direct solution.  One node per subdomain, no overlap: it is
+    the node-block Jacobi preconditioner, so CG takes the same iterates as
+    the block-Jacobi PCG."""
+    S = _small_system(oracle, 23, 17, 11)
+    Ud = S.solve_direct()
+    U1, it1, _ = S.solve_asm_pcg((1, 1), 0, tol=1e-12)
+    assert it1 == 1
+    assert np.linalg.norm(U1 - Ud) <= 1e-12 * np.linalg.norm(Ud)
+    Ua, ita, _ = S.solve_asm_pcg((23, 17), 0, tol=1e-12)
+    Ub, itb, _ = S.solve_pcg(tol=1e-12)
+    assert ita == itb
+    assert np.linalg.norm(Ua - Ub) <= 1e-12 * np.linalg.norm(Ub)
+
+
+def test_asm_pcg_first_step_from_dense_blocks(oracle):
+    """The first CG step from zero is x1 = (b.z / z.A z) z with z = M b and
+    M = sum_i R_i^T A_i^{-1} R_i over the extended tiles (near-equal tiles,
+    boundary k at floor(k W / px), extended by the overlap and clipped);
+    here M b is formed from dense sub-blocks of the assembled matrix and
+    LAPACK solves."""
+    W, H, px, py, ov = 19, 14, 3, 2, 2
+    S = _small_system(oracle, W, H, 13)
+    A = S.dense()
+    b = S.b
+    z = np.zeros(S.n)
+    for iy in range(py):
+        for ix in range(px):
+            x0, x1 = ix * W // px, (ix + 1) * W // px
+            y0, y1 = iy * H // py, (iy + 1) * H // py
+            ex0, ex1, ey0, ey1 = max(x0 - ov, 0), min(x1 + ov, W), max(y0 - ov, 0), min(y1 + ov, H)
+            ys, xs = np.mgrid[ey0:ey1, ex0:ex1]
+            idx = np.concatenate([c * W * H + ys.ravel() * W + xs.ravel() for c in range(3)])
+            z[idx] += np.linalg.solve(A[np.ix_(idx, idx)], b[idx])
+    x1 = (b @ z) / (z @ (A @ z)) * z
+    U, it, _ = S.solve_asm_pcg((px, py), ov, tol=1e-30, maxit=1)
+    assert it == 1
+    assert np.abs(U.ravel() - x1).max() <= 1e-12 * np.abs(x1).max()
+
+
+def test_asm_pcg_matches_block_jacobi_pcg_640x480(oracle):
+    """640x480 texture: the ASM-PCG (16x16 tiles, 1-node overlap) and the
+    block-Jacobi PCG, both to 1e-12, give the same solution."""
+    p = synth.texture()
+    S = oracle.System.from_frames(p.f1.astype(np.float64), p.f2.astype(np.float64), p.alpha0, p.lam)
+    Ua, ita, ra = S.solve_asm_pcg((40, 30), 1, tol=1e-12)
+    Ub, itb, rb = S.solve_pcg(tol=1e-12)
+    assert ra <= 1e-12 and rb <= 1e-12
+    assert ita < itb / 3
+    assert np.linalg.norm(Ua - Ub) <= 1e-9 * np.linalg.norm(Ub)
+
+
 def test_schwarz_fixed_point_is_global_solution(oracle):
     """Eq. schwarz: the subdomain iterates converge to the global solution
     (2x2 parts, 4-node overlap, 64x48 blobs)."""
