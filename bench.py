@@ -37,6 +37,7 @@ WORKLOAD_W, WORKLOAD_H = 3840, 2160
 WORKLOAD_OPTS = dict(tile=(48, 48), overlap=0, sweeps=4, precision=1, omega=1.6)
 FP64_OPTS = dict(tile=(32, 16), overlap=0, sweeps=3, precision=0, omega=1.6)
 RTOL = 1e-6
+SMS = 152  # streaming multiprocessors of a GB300
 # algorithmic bytes per pixel of one launch of each solve kernel (FP32 inner
 # vectors; each word read or written once):
 #   pcg_apply: read z, p_old, d (3 x 12) + f1, f2, alpha (16); write p, q, d (3 x 12)
@@ -63,9 +64,9 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def recorded_traffic(kind: str):
-    """DRAM bytes per pixel of a kernel from the committed ncu summary, if it
-    was taken on the current kernel sources."""
+def recorded_metric(kind: str, key: str):
+    """A per-pixel figure of a kernel (DRAM bytes, warp instructions) from the
+    committed ncu summary, if it was taken on the current kernel sources."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -73,7 +74,11 @@ def recorded_traffic(kind: str):
     if d.get("source_hash") != kernel_source_hash():
         return None
     k = d.get("kernels", {}).get(kind)
-    return None if k is None else float(k["dram_bytes_per_px"])
+    return None if k is None or k.get(key) is None else float(k[key])
+
+
+def recorded_traffic(kind: str):
+    return recorded_metric(kind, "dram_bytes_per_px")
 
 
 class ClockSampler:
@@ -101,7 +106,18 @@ class ClockSampler:
             if len(parts) >= 8:
                 self.rows.append(parts)
 
-    def stop(self):
+    def wait_first(self, timeout=10.0):
+        """Blocks until the first sample has arrived, so that the sampler's
+        start-up (process launch, NVML initialisation) ends before any timed
+        region begins."""
+        t0 = time.time()
+        while self.proc and not self.rows and time.time() - t0 < timeout and self.proc.poll() is None:
+            time.sleep(0.02)
+
+    def mark(self):
+        return len(self.rows)
+
+    def stop(self, since=0):
         if not self.proc:
             return None
         self.proc.terminate()
@@ -110,12 +126,13 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.t.join(timeout=2)
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        rows = self.rows[since:]
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i] == "Active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows)}
 
 
 def dist_env():
@@ -257,20 +274,34 @@ def run_ours(args):
         barrier()
         return max_over_ranks(e0.elapsed_time(e1), ws, dev)
 
+    gpu_id = torch.cuda.get_device_properties(dev).uuid
+    gpu_id = f"GPU-{gpu_id}" if not str(gpu_id).startswith("GPU-") else str(gpu_id)
+    # the clock sampler starts before the warm-up and has delivered its first
+    # sample before any timed region: its start-up never overlaps the timing
+    clk = ClockSampler(gpu_id)
+    clk.wait_first()
     for _ in range(args.warmup):
         step(h, U)
     infos.clear()
-    gpu_id = torch.cuda.get_device_properties(dev).uuid
-    gpu_id = f"GPU-{gpu_id}" if not str(gpu_id).startswith("GPU-") else str(gpu_id)
-    # timed region: the production path (inner loop as one CUDA graph per pass)
-    S.of_set_profiling(h, False)  # clears the launch counters
-    clk = ClockSampler(gpu_id)
-    ms = timed(lambda: step(h, U), args.steps)
-    clocks = clk.stop()
-    launches = sum(v["launches"] for v in S.of_get_profile(h).values())
+    # timed region: the production path (inner loop as one CUDA graph per
+    # pass), `repeats` back-to-back regions of `steps` steps; value = median
+    mark = clk.mark()
+    reps = []
+    launches = None
+    for _ in range(max(1, args.repeats)):
+        S.of_set_profiling(h, False)  # clears the launch counters
+        reps.append(timed(lambda: step(h, U), args.steps))
+        if launches is None:
+            launches = sum(v["launches"] for v in S.of_get_profile(h).values())
+    clocks = clk.stop(mark)
+    ms = statistics.median(reps)
     value = whole_job_value(px, ws, args.steps, ms)
+    spread = {"repeats": len(reps), "value_min": whole_job_value(px, ws, args.steps, max(reps)),
+              "value_max": whole_job_value(px, ws, args.steps, min(reps)),
+              "ms_per_step": [r / args.steps for r in reps]}
     iters = [i["inner_iters"] for i in infos]
     relres = max(i["rel_residual"] for i in infos)
+    U_mixed = U.to(torch.float64)  # the last timed step's solution (alpha = alpha_0)
 
     # per-kernel launch times (CUDA events on the solver stream, kernel by
     # kernel) from a profiling pass over the same steps: the roofline of the
@@ -293,6 +324,18 @@ def run_ours(args):
                                    "GBps": (ALG_BYTES_PER_PX[k] * px / (prof[k]["ms"] / prof[k]["launches"] / 1e3) / 1e9)
                                    if prof[k]["launches"] else None}
                                for k in ("pcg_apply", "schwarz", "residual")}}
+    # one PCG iteration = one apply + one preconditioner launch
+    if prof["pcg_apply"]["launches"] and prof["schwarz"]["launches"]:
+        roofline["ms_per_pcg_iteration"] = (prof["pcg_apply"]["ms"] / prof["pcg_apply"]["launches"]
+                                            + prof["schwarz"]["ms"] / prof["schwarz"]["launches"])
+    # the preconditioner against the instruction-issue roof: warp
+    # instructions per pixel from the committed ncu capture (same sources)
+    ipx = recorded_metric("schwarz", "warp_inst_per_px")
+    if ipx is not None and prof["schwarz"]["launches"] and clocks and clocks.get("sm_mhz"):
+        t = prof["schwarz"]["ms"] / prof["schwarz"]["launches"] / 1e3
+        issue_peak = SMS * 4 * clocks["sm_mhz"] * 1e6  # warp instructions / s (4 schedulers per SM)
+        roofline["schwarz_issue"] = {"warp_inst_per_px": ipx, "achieved_winst_per_s": ipx * px / t,
+                                     "peak_winst_per_s": issue_peak, "frac": ipx * px / t / issue_peak}
     if dom == "schwarz":
         roofline["note"] = ("the preconditioner's block-SOR sweeps run in shared memory: bound by instruction "
                             "latency at 12 warps per SM (ncu: issue active 50 %, L1/shared 46 %) and shared-memory "
@@ -321,6 +364,22 @@ def run_ours(args):
                 "ms_per_step": ms64 / args.fp64_steps, "inner_iters": infos[-1]["inner_iters"],
                 "rel_residual": infos[-1]["rel_residual"], "opts": {k: v for k, v in FP64_OPTS.items()}}
         S.of_destroy(h64)
+
+    # flow error of the timed mixed result: against the FP64 GPU path solved
+    # far below the target (rel. residual 1e-12), alpha = alpha_0 as in the
+    # timed step's solve (outside every timed region)
+    flow_err = None
+    if not args.no_flow_check:
+        h64 = make(FP64_OPTS)
+        S.of_set_alpha(h64, 0, None, p.alpha0)
+        Uref = torch.zeros(3, H, W, dtype=torch.float64, device=dev)
+        st, inf = S.of_solve(h64, [Uref], rtol=1e-12, max_inner=20000)
+        S.of_destroy(h64)
+        d = (U_mixed - Uref).abs()
+        flow_err = {"max_px": float(d[:2].max()), "m_max": float(d[2].max()),
+                    "reference": "FP64 GPU solve to rel. residual %.1e (%d iterations)" % (
+                        inf[0]["rel_residual"], inf[0]["inner_iters"]),
+                    "target_px": 1e-4}
 
     # the model options built beyond the workload's configuration, on the same
     # pair and step: brightness constancy (no illumination unknown), K_sigma
@@ -422,7 +481,8 @@ def run_ours(args):
                        "rtol": RTOL, "opts": {k: v for k, v in WORKLOAD_OPTS.items()},
                        "step": "alpha reset + solve to rtol + indicator + alpha update",
                        "l2": "inputs larger than L2 (no flush)",
-                       "inner_iters": iters, "rel_residual_max": relres},
+                       "inner_iters": iters, "rel_residual_max": relres, "flow_error": flow_err,
+                       "spread": spread},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "fp64_gpu": fp64, "variants": variants, "batched": batched,
         }
@@ -441,6 +501,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--repeats", type=int, default=3, help="timed regions of --steps steps (value = median)")
+    ap.add_argument("--no-flow-check", action="store_true", help="skip the FP64 flow-error reference solve")
     ap.add_argument("--variant-steps", type=int, default=5, help="steps per model variant (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3, help="steps of the 64-pair mixed-size batch (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -117,8 +117,8 @@ typedef struct {
     int max_outer;     /* refinement passes (mixed) [20] */
     int max_inner;     /* PCG iterations per pass (mixed) or in total (FP64) [2000] */
     int warm_start;    /* 1: start from the U passed in; 0: start from U = 0 */
-    double inner_rtol; /* mixed: a pass asks the inner PCG to bring its starting residual down to half
-                          the outer tolerance, but by no more than this factor [1e-6] */
+    double inner_rtol; /* mixed: a pass asks the inner PCG to bring its starting residual down to a
+                          quarter of the outer tolerance, but by no more than this factor [1e-6] */
     int host_loop;     /* 1: drive the inner PCG loop from the host (launch by launch, polling
                           convergence); 0: one CUDA graph per pass whose while-node the device
                           ends [0] */

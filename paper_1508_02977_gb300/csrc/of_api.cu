@@ -117,6 +117,16 @@ of_status fail(of_ctx* h, of_status s, const std::string& m) {
         }                                                                                            \
     } while (0)
 
+// Reads the pair scalars and the device error word back (one stream-ordered
+// copy) and waits for it.  Returns the error word.
+of_status read_scalars(of_ctx* h, cudaStream_t st, int* errw) {
+    CK(cudaMemcpyAsync(h->sc_host, h->sc_dev, sizeof(PairScalars) * h->batch + sizeof(int), cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaStreamSynchronize(st));
+    *errw = *reinterpret_cast<const int*>(h->sc_host + h->batch);
+    return OF_OK;
+}
+
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -502,6 +512,7 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
     // host-driven loop: poll every 8 iterations; when timing kernels, after
     // every iteration so that no launch past convergence enters the averages
     const int chunk = h->prof ? 1 : 8;
+    int errw = 0;  // device error word, read back with the scalars
     passes_out.assign(h->batch, 0);
     CK(cudaMemsetAsync(h->cntA, 0, sizeof(unsigned) * h->batch, st));
     CK(cudaMemsetAsync(h->cntS, 0, sizeof(unsigned) * h->batch, st));
@@ -516,16 +527,16 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
         CK(timed(h, 2, [&] { return ofl::launch_residual(B, xin, xout, rhs, first, o.rtol, o.inner_rtol, o.max_inner, st); }));
         if (!first) cur = 1 - cur;
         if (pass == o.max_outer) {
-            CK(cudaMemcpyAsync(h->sc_host, h->sc_dev, sizeof(PairScalars) * h->batch, cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
+            of_status rs = read_scalars(h, st, &errw);
+            if (rs != OF_OK) return rs;
             break;
         }
         CK(timed(h, 1, [&] { return ofl::launch_precond_first(B, st); }));
         if (h->loop_exec && !h->prof && !o.host_loop) {
             // the whole inner loop on the device; one read-back per pass
             CK(cudaGraphLaunch(h->loop_exec, st));
-            CK(cudaMemcpyAsync(h->sc_host, h->sc_dev, sizeof(PairScalars) * h->batch, cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
+            of_status rs = read_scalars(h, st, &errw);
+            if (rs != OF_OK) return rs;
             int body = 0;  // loop iterations = the most iterations any pair took in this pass
             for (int p = 0; p < h->batch; ++p) body = std::max(body, h->sc_host[p].it);
             body = (body + kLoopUnroll - 1) / kLoopUnroll * kLoopUnroll;  // whole bodies run
@@ -539,19 +550,15 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
                     CK(timed(h, 0, [&] { return ofl::launch_pcg_apply(B, st); }));
                     CK(timed(h, 1, [&] { return ofl::launch_pcg_precond(B, st); }));
                 }
-                CK(cudaMemcpyAsync(h->sc_host, h->sc_dev, sizeof(PairScalars) * h->batch, cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
+                of_status rs = read_scalars(h, st, &errw);
+                if (rs != OF_OK) return rs;
                 all_done = true;
                 for (int p = 0; p < h->batch; ++p) all_done = all_done && h->sc_host[p].done;
-                int errc = 0;  // a bounded wait ran out: stop launching
-                CK(cudaMemcpy(&errc, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
-                if (errc) all_done = true;
+                if (errw) all_done = true;  // a bounded wait ran out: stop launching
                 if (it >= o.max_inner + chunk) all_done = true;
             }
         }
-        int errp = 0;  // a bounded wait ran out in this pass: no further launches
-        CK(cudaMemcpy(&errp, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
-        if (errp) break;
+        if (errw) break;  // a bounded wait ran out in this pass: no further launches
         bool all_conv = true;
         for (int p = 0; p < h->batch; ++p) {
             const bool conv = h->sc_host[p].pad[0] != 0;
@@ -565,8 +572,6 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
     }
     *cur_out = cur;
     prof_flush(h);
-    int errw = 0;
-    CK(cudaMemcpy(&errw, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
     if (errw) return fail(h, OF_ERR_TIMEOUT, "a bounded device wait (TMA staging) ran out");
     return OF_OK;
 }
@@ -769,16 +774,18 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
     CK(dalloc(h, &h->pd_dev, sizeof(PairDesc) * batch));
     CK(dalloc(h, &h->blocks_dev, sizeof(int4) * h->blocks.size()));
     CK(dalloc(h, &h->tiles_dev, sizeof(int4) * h->tiles.size()));
-    CK(dalloc(h, &h->sc_dev, sizeof(PairScalars) * batch));
+    // the device error word sits right after the pair scalars, so that one
+    // stream-ordered copy per refinement pass reads both back
+    CK(dalloc(h, &h->sc_dev, sizeof(PairScalars) * batch + 16));
+    h->err_dev = reinterpret_cast<int*>(h->sc_dev + batch);
     CK(dalloc(h, &h->partA, sizeof(double) * 2 * h->blocks.size()));
     CK(dalloc(h, &h->partS, sizeof(double) * 2 * h->tiles.size()));
     CK(dalloc(h, &h->etamax, sizeof(double) * batch));
     CK(dalloc(h, &h->cntA, sizeof(unsigned) * batch));
     CK(dalloc(h, &h->cntS, sizeof(unsigned) * batch));
-    CK(dalloc(h, &h->err_dev, sizeof(int)));
     CK(dalloc(h, &h->staging, stage));
     h->staging_bytes = stage;
-    CK(cudaMallocHost((void**)&h->sc_host, sizeof(PairScalars) * batch));
+    CK(cudaMallocHost((void**)&h->sc_host, sizeof(PairScalars) * batch + 16));
     cudaStream_t st = h->stream;
     CK(cudaMemcpyAsync(h->pd_dev, h->pd.data(), sizeof(PairDesc) * batch, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(h->blocks_dev, h->blocks.data(), sizeof(int4) * h->blocks.size(), cudaMemcpyHostToDevice, st));
@@ -1272,9 +1279,9 @@ of_status of_precondition(of_handle h, int pair, const void* r, void* z, of_dtyp
     CK(ofl::launch_precond_only(B, pair, h->tile0[pair], h->ntile[pair], h->stream));
     s = copy_out(h, (char*)h->z + d.vec_off * es, h->fp64 ? ofl::T_F64 : ofl::T_F32, d.pitch, z, dt, 3LL * d.H, d.W);
     if (s != OF_OK) return s;
-    CK(cudaStreamSynchronize(h->stream));
     int errw = 0;
-    CK(cudaMemcpy(&errw, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    s = read_scalars(h, h->stream, &errw);
+    if (s != OF_OK) return s;
     if (errw) return fail(h, OF_ERR_TIMEOUT, "a bounded device wait (TMA staging) ran out");
     return OF_OK;
 }
