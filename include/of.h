@@ -108,6 +108,19 @@ typedef struct {
                                 family (t = 0 and t = 1 separately) by the sampled Gaussian of sigma's
                                 form, normalised inside the lattice.  The operator uses A_rho exactly; the
                                 Schwarz (and coarse) preconditioner is built from the unsmoothed g g^T */
+    int schwarz;             /* method of of_solve [0]:
+                                0: PCG preconditioned by the symmetric restricted overlapping Schwarz
+                                   method (the options above);
+                                1: the paper's Schwarz method as a stationary iteration (Section 3.2,
+                                   Eq. schwarz): each subdomain solves its extended problem with Dirichlet
+                                   data from the previous global iterate outside it, and every node takes the
+                                   value of the subdomain that owns it (restricted additive Schwarz),
+                                     U^k = U^{k-1} + sum_i R~_i^T A_i^{-1} R_i (b - A U^{k-1}),
+                                   with A_i^{-1} approximated by `sweeps` (here up to 4096) symmetric block
+                                   SOR sweeps from zero (exact as the sweeps grow).  of_solve iterates until
+                                   ||b - A U|| <= rtol ||b|| or max_inner iterations; inner_iters counts the
+                                   iterations and of_get_schwarz_history gives ||U^k - U^{k-1}||_2 of each.
+                                   Needs the Schwarz preconditioner settings, coarse = 0 and rho = 0 */
 } of_grid_opts;
 
 /* Solve options.  A field left at 0 takes the default in brackets. */
@@ -117,11 +130,15 @@ typedef struct {
     int max_outer;     /* refinement passes (mixed) [20] */
     int max_inner;     /* PCG iterations per pass (mixed) or in total (FP64) [2000] */
     int warm_start;    /* 1: start from the U passed in; 0: start from U = 0 */
-    double inner_rtol; /* mixed: a pass asks the inner PCG to bring its starting residual down to a
-                          quarter of the outer tolerance, but by no more than this factor [1e-6] */
+    double inner_rtol; /* mixed: a pass asks the inner PCG to bring its starting residual down to
+                          pass_frac times the outer tolerance, but by no more than this factor
+                          [1e-6] */
     int host_loop;     /* 1: drive the inner PCG loop from the host (launch by launch, polling
                           convergence); 0: one CUDA graph per pass whose while-node the device
                           ends [0] */
+    double pass_frac;  /* mixed: the fraction of the outer tolerance a refinement pass aims at, in
+                          (0, 1] [0.25]; the final residual then lies further below rtol, which
+                          bounds the flow error more tightly at the cost of iterations */
 } of_solve_opts;
 
 /* Per-pair result of of_solve / of_adjoint (host memory, written on return). */
@@ -179,6 +196,13 @@ of_status of_get_alpha(of_handle h, int pair, void *alpha, of_dtype dt);
  * receives per-pair results.  Synchronises the stream.  Returns the worst
  * per-pair status (OF_ERR_NOT_CONVERGED / OF_ERR_BREAKDOWN) or OF_OK. */
 of_status of_solve(of_handle h, const of_solve_opts *o, void *const *U, of_dtype dt, of_solve_info *info);
+
+/* ||U^k - U^{k-1}||_2 of every iteration of the last of_solve of pair
+ * `pair` on a grid with schwarz = 1 (Section 3.2, Eq. schwarz), into hist
+ * (host, at least `cap` entries; the first min(cap, n) are written); *n
+ * receives the number of iterations.  OF_ERR_STATE if the last of_solve was
+ * not such a solve. */
+of_status of_get_schwarz_history(of_handle h, int pair, double *hist, int cap, int *n);
 
 /* Error indicator eta_K of Section 2.3 (Eq. errind) for the last solution
  * of every pair, then the alpha update of Section 2.3:
@@ -272,8 +296,9 @@ of_status of_get_profile(of_handle h, of_profile *out);
  * Limit: ceil(W/124) * ceil(H/32) <= 32768 thread blocks (every frame up to
  * 8192 x 8192 nodes fits); larger frames return OF_ERR_ARG, as do bad sizes
  * or null inputs.  The first call on a device (the current one) looks up the
- * device address of the scratch array; make that first call before any
- * stream capture.  All calls share the scratch and it keeps the last call's
+ * device address of the scratch array, and so does the first call after a
+ * reset of that device (a new context); make those calls before any stream
+ * capture.  All calls share the scratch and it keeps the last call's
  * contents (the counter that must start at zero is cleared by every call):
  * calls that overlap on the GPU (other streams, other host threads) race.
  * Work is enqueued on cuda_stream (NULL: legacy default stream); the outputs

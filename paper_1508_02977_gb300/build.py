@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libof.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["of_api.cu", "of_kernels.cu", "of_adapt.cu", "of_noalloc.cu", "of_smooth.cu", "of_coarse.cu"]
+SOURCES = ["of_api.cu", "of_kernels.cu", "of_adapt.cu", "of_noalloc.cu", "of_smooth.cu", "of_coarse.cu",
+           "of_ras.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -83,6 +83,7 @@ struct of_ctx {
     of_profile ptot{};
     // state
     std::vector<char> frames_set, alpha_set;
+    std::vector<std::vector<double>> ras_hist;  // stationary Schwarz: ||U^k - U^{k-1}|| per pair
     bool solved = false;
     of_solve_opts last_opts{};
 };
@@ -117,11 +118,20 @@ of_status fail(of_ctx* h, of_status s, const std::string& m) {
         }                                                                                            \
     } while (0)
 
-// Reads the pair scalars and the device error word back (one stream-ordered
-// copy) and waits for it.  Returns the error word.
+// Device block of the pair scalars: [batch] PairScalars, the error word (16
+// bytes), [batch] doubles of the stationary Schwarz history.
+size_t sc_block_bytes(int batch) { return sizeof(PairScalars) * batch + 16 + sizeof(double) * batch; }
+double* ras_hist_dev(of_ctx* h) {
+    return reinterpret_cast<double*>(reinterpret_cast<char*>(h->sc_dev + h->batch) + 16);
+}
+const double* ras_hist_host(of_ctx* h) {
+    return reinterpret_cast<const double*>(reinterpret_cast<const char*>(h->sc_host + h->batch) + 16);
+}
+
+// Reads the pair scalars, the device error word and the history slots back
+// (one stream-ordered copy) and waits for it.  Returns the error word.
 of_status read_scalars(of_ctx* h, cudaStream_t st, int* errw) {
-    CK(cudaMemcpyAsync(h->sc_host, h->sc_dev, sizeof(PairScalars) * h->batch + sizeof(int), cudaMemcpyDeviceToHost,
-                       st));
+    CK(cudaMemcpyAsync(h->sc_host, h->sc_dev, sc_block_bytes(h->batch), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     *errw = *reinterpret_cast<const int*>(h->sc_host + h->batch);
     return OF_OK;
@@ -168,6 +178,7 @@ void free_all(of_ctx* h) {
     h->r = h->z = h->q = h->d = h->p0 = h->p1 = nullptr;
     h->batch = 0;
     h->solved = false;
+    h->ras_hist.clear();
 }
 
 template <typename T>
@@ -524,7 +535,7 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
         double* xout = first ? nullptr : h->x[1 - cur];
         // a cold start (x = 0) needs only the load vector for its first residual
         const double* xin = (first && !o.warm_start) ? nullptr : h->x[cur];
-        CK(timed(h, 2, [&] { return ofl::launch_residual(B, xin, xout, rhs, first, o.rtol, o.inner_rtol, o.max_inner, st); }));
+        CK(timed(h, 2, [&] { return ofl::launch_residual(B, xin, xout, rhs, first, o.rtol, o.inner_rtol, o.pass_frac, o.max_inner, st); }));
         if (!first) cur = 1 - cur;
         if (pass == o.max_outer) {
             of_status rs = read_scalars(h, st, &errw);
@@ -576,6 +587,48 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
     return OF_OK;
 }
 
+// The stationary Schwarz iteration (grid option schwarz = 1): residual
+// (which folds the previous correction d into x), local solves, history.
+// The residual kernel stops a pair whose residual is <= rtol ||b||; its
+// later corrections are zero.  On return x[cur] holds the last iterate.
+of_status run_ras(of_ctx* h, const of_solve_opts& o, int* cur_out, std::vector<int>& iters_out) {
+    of_status cs = refresh_cells(h);
+    if (cs != OF_OK) return cs;
+    ofl::SolveBufs B = solve_bufs(h);
+    cudaStream_t st = h->stream;
+    int cur = 0, errw = 0;
+    iters_out.assign(h->batch, 0);
+    h->ras_hist.assign(h->batch, std::vector<double>());
+    CK(cudaMemsetAsync(h->cntA, 0, sizeof(unsigned) * h->batch, st));
+    CK(cudaMemsetAsync(h->sc_dev, 0, sc_block_bytes(h->batch), st));
+    for (int k = 0;; ++k) {
+        NvtxRange nv_it("Schwarz iteration");
+        const int first = (k == 0);
+        double* xout = first ? nullptr : h->x[1 - cur];
+        const double* xin = (first && !o.warm_start) ? nullptr : h->x[cur];
+        CK(timed(h, 2, [&] { return ofl::launch_residual(B, xin, xout, nullptr, first, o.rtol, o.inner_rtol, o.pass_frac, 1, st); }));
+        if (!first) cur = 1 - cur;
+        of_status rs = read_scalars(h, st, &errw);
+        if (rs != OF_OK) return rs;
+        bool all_conv = true;
+        for (int p = 0; p < h->batch; ++p) all_conv = all_conv && h->sc_host[p].pad[0] != 0;
+        if (all_conv || k == o.max_inner) break;
+        CK(ofl::launch_ras(B, h->cell0, h->cell1, ras_hist_dev(h), st));
+        count_other(h, 2);
+        rs = read_scalars(h, st, &errw);
+        if (rs != OF_OK) return rs;
+        const double* hv = ras_hist_host(h);
+        for (int p = 0; p < h->batch; ++p)
+            if (!h->sc_host[p].pad[0]) {
+                h->ras_hist[p].push_back(hv[p]);
+                iters_out[p] = k + 1;
+            }
+    }
+    *cur_out = cur;
+    prof_flush(h);
+    return OF_OK;
+}
+
 void fill_info(of_ctx* h, const std::vector<int>& passes, float ms, of_solve_info* info, of_status* worst) {
     *worst = OF_OK;
     for (int p = 0; p < h->batch; ++p) {
@@ -605,6 +658,7 @@ of_solve_opts with_defaults(const of_solve_opts* o, int fp64) {
     // arithmetic reaches in the true residual, so that the next pass has little
     // left to do (fewer restarts of the Krylov space than with smaller steps)
     if (r.inner_rtol <= 0) r.inner_rtol = fp64 ? 1e-12 : 1e-6;
+    if (!(r.pass_frac > 0) || r.pass_frac > 1) r.pass_frac = 0.25;
     return r;
 }
 
@@ -659,8 +713,11 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
     if (opt.coarse < 0 || (opt.coarse > 0 && opt.coarse < 4)) return fail(h, OF_ERR_ARG, "coarse spacing must be 0 or >= 4");
     if (opt.tile_x < 4 || opt.tile_y < 4 || opt.tile_x % 4 || opt.tile_y % 4 || opt.tile_x > 256 || opt.tile_y > 256)
         return fail(h, OF_ERR_ARG, "tile sizes must be multiples of 4 in [4, 256]");
-    if (opt.overlap < 0 || opt.overlap > 32 || opt.sweeps < 0 || opt.sweeps > 64)
-        return fail(h, OF_ERR_ARG, "overlap must be in [0, 32] and sweeps in [0, 64]");
+    if (opt.schwarz != 0 && opt.schwarz != 1) return fail(h, OF_ERR_ARG, "schwarz must be 0 or 1");
+    if (opt.schwarz == 1 && (opt.preconditioner != OF_PC_SCHWARZ || opt.coarse != 0 || opt.rho != 0))
+        return fail(h, OF_ERR_ARG, "the stationary Schwarz iteration needs the Schwarz settings, coarse = 0, rho = 0");
+    if (opt.overlap < 0 || opt.overlap > 32 || opt.sweeps < 0 || opt.sweeps > (opt.schwarz ? 4096 : 64))
+        return fail(h, OF_ERR_ARG, "overlap must be in [0, 32] and sweeps in [0, 64] ([0, 4096] with schwarz = 1)");
     if (ofk::sch_rw(opt.tile_x, opt.overlap) * (opt.precision == OF_PREC_FP64 ? 4 : 1) > 256 ||
         ofk::sch_rh(opt.tile_y, opt.overlap) > 256)
         return fail(h, OF_ERR_ARG, "tile + overlap too large for one staged window");
@@ -682,6 +739,8 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
     if (!ofl::schwarz_node_table(fp64, opt.tile_x, opt.tile_y, opt.overlap, ntab, sch_threads, sch_npt))
         return fail(h, OF_ERR_ARG, "extended tile too large for one CTA (more than 2 nodes per thread and colour)");
     if (smem > (size_t)smax) return fail(h, OF_ERR_ARG, "tile/overlap need more shared memory than one CTA has");
+    if (opt.schwarz == 1 && ofl::ras_smem_bytes(fp64, opt.tile_x, opt.tile_y, opt.overlap) > (size_t)smax)
+        return fail(h, OF_ERR_ARG, "tile/overlap need more shared memory than one CTA has");
 
     CK(cudaStreamSynchronize(h->stream));
     free_all(h);
@@ -776,7 +835,9 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
     CK(dalloc(h, &h->tiles_dev, sizeof(int4) * h->tiles.size()));
     // the device error word sits right after the pair scalars, so that one
     // stream-ordered copy per refinement pass reads both back
-    CK(dalloc(h, &h->sc_dev, sizeof(PairScalars) * batch + 16));
+    // and after it one double per pair for the stationary Schwarz iteration's
+    // ||U^k - U^{k-1}||
+    CK(dalloc(h, &h->sc_dev, sc_block_bytes(batch)));
     h->err_dev = reinterpret_cast<int*>(h->sc_dev + batch);
     CK(dalloc(h, &h->partA, sizeof(double) * 2 * h->blocks.size()));
     CK(dalloc(h, &h->partS, sizeof(double) * 2 * h->tiles.size()));
@@ -785,7 +846,7 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
     CK(dalloc(h, &h->cntS, sizeof(unsigned) * batch));
     CK(dalloc(h, &h->staging, stage));
     h->staging_bytes = stage;
-    CK(cudaMallocHost((void**)&h->sc_host, sizeof(PairScalars) * batch + 16));
+    CK(cudaMallocHost((void**)&h->sc_host, sc_block_bytes(batch)));
     cudaStream_t st = h->stream;
     CK(cudaMemcpyAsync(h->pd_dev, h->pd.data(), sizeof(PairDesc) * batch, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(h->blocks_dev, h->blocks.data(), sizeof(int4) * h->blocks.size(), cudaMemcpyHostToDevice, st));
@@ -1051,7 +1112,9 @@ of_status of_solve(of_handle h, const of_solve_opts* o, void* const* U, of_dtype
     }
     int cur = 0;
     std::vector<int> passes;
-    of_status s = run_solve(h, opt, nullptr, &cur, passes);
+    const bool ras = h->opts.schwarz == 1;
+    h->ras_hist.clear();
+    of_status s = ras ? run_ras(h, opt, &cur, passes) : run_solve(h, opt, nullptr, &cur, passes);
     if (s != OF_OK) return s;
     CK(cudaMemcpyAsync(h->usol, h->x[cur], h->vec_elems * sizeof(double), cudaMemcpyDeviceToDevice, st));
     for (int p = 0; p < h->batch; ++p) {
@@ -1065,6 +1128,11 @@ of_status of_solve(of_handle h, const of_solve_opts* o, void* const* U, of_dtype
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     of_status worst;
     fill_info(h, passes, ms, info, &worst);
+    if (ras && info)
+        for (int p = 0; p < h->batch; ++p) {
+            info[p].outer_iters = 0;
+            info[p].inner_iters = passes[p];
+        }
     h->solved = true;
     h->last_opts = opt;
     if (worst != OF_OK) return fail(h, worst, worst == OF_ERR_BREAKDOWN ? "CG breakdown (singular or indefinite data)"
@@ -1304,11 +1372,22 @@ of_status of_residual(of_handle h, int pair, const void* U, of_dtype dt, double*
     ofl::SolveBufs B = solve_bufs(h);
     B.blocks = h->blocks_dev + h->blk0[pair];
     B.nblk = h->nblk[pair];
-    CK(ofl::launch_residual(B, h->cvec, nullptr, nullptr, 1, 1e-300, 1e-300, 1, st));
+    CK(ofl::launch_residual(B, h->cvec, nullptr, nullptr, 1, 1e-300, 1e-300, 0.5, 1, st));
     PairScalars sc;
     CK(cudaMemcpyAsync(&sc, h->sc_dev + pair, sizeof(sc), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     *rel = sc.bnorm2 > 0 ? std::sqrt(sc.res2 / sc.bnorm2) : std::sqrt(sc.res2);
+    return OF_OK;
+}
+
+of_status of_get_schwarz_history(of_handle h, int pair, double* hist, int cap, int* n) {
+    if (!h) return OF_ERR_ARG;
+    if (pair < 0 || pair >= h->batch || !n || (cap > 0 && !hist)) return fail(h, OF_ERR_ARG, "bad pair or null output");
+    if (h->ras_hist.size() != (size_t)h->batch)
+        return fail(h, OF_ERR_STATE, "the last of_solve was not a stationary Schwarz solve");
+    const std::vector<double>& v = h->ras_hist[pair];
+    *n = (int)v.size();
+    for (int i = 0; i < cap && i < (int)v.size(); ++i) hist[i] = v[i];
     return OF_OK;
 }
 

@@ -185,7 +185,7 @@ struct ApplyParams {
     R* bout;            // APPLY: optional b
     const R* rhs_vec;   // RES: rhs vector instead of the frame load (adjoint), or null
     int first;          // RES: first residual of a solve (no correction, ||b|| formed)
-    double rtol, inner_rtol;
+    double rtol, inner_rtol, pass_frac;
     int max_inner;
 };
 
@@ -433,10 +433,8 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
             if (P.first || MODE == MODE_RESB) s->bnorm2 = t1;
             const double b2 = s->bnorm2;
             const bool conv = (t0 <= P.rtol * P.rtol * b2) || (t0 == 0.0);
-            // the pass aims at a quarter of the outer tolerance: a final residual
-            // just under rtol can leave flow errors just over 1e-4 px at rtol 1e-6
-            // on a 3840x2160 pair, a quarter of it leaves half that
-            double rel = 0.25 * P.rtol * sqrt(b2 / (t0 > 0.0 ? t0 : 1.0));
+            // the pass aims at pass_frac times the outer tolerance
+            double rel = P.pass_frac * P.rtol * sqrt(b2 / (t0 > 0.0 ? t0 : 1.0));
             if (rel < P.inner_rtol) rel = P.inner_rtol;
             if (rel > 0.5) rel = 0.5;
             s->tol2 = rel * rel * t0;

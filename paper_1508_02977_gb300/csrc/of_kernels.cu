@@ -87,7 +87,7 @@ static ApplyParams<R, C, RI> base_params(const SolveBufs& B) {
 
 template <typename C, typename RI>
 static cudaError_t residual_t(const SolveBufs& B, const double* xin, double* xout, const double* rhs_vec, int first,
-                              double rtol, double inner_rtol, int max_inner, cudaStream_t st) {
+                              double rtol, double inner_rtol, double pass_frac, int max_inner, cudaStream_t st) {
     auto P = base_params<double, C, RI>(B);
     P.in = xin;
     P.p_buf0 = (RI*)B.p0;
@@ -99,6 +99,7 @@ static cudaError_t residual_t(const SolveBufs& B, const double* xin, double* xou
     P.first = first;
     P.rtol = rtol;
     P.inner_rtol = inner_rtol;
+    P.pass_frac = pass_frac;
     P.max_inner = max_inner;
     // the FP32 path forms A x and b in double-float: FP64-grade residual on the FP32 pipe
     using T = typename std::conditional<sizeof(C) == 4, DF, double>::type;
@@ -114,9 +115,10 @@ static cudaError_t residual_t(const SolveBufs& B, const double* xin, double* xou
 }
 
 cudaError_t launch_residual(const SolveBufs& B, const double* xin, double* xout, const double* rhs_vec, int first,
-                            double rtol, double inner_rtol, int max_inner, cudaStream_t st) {
-    if (B.fp64) return residual_t<double, double>(B, xin, xout, rhs_vec, first, rtol, inner_rtol, max_inner, st);
-    return residual_t<float, float>(B, xin, xout, rhs_vec, first, rtol, inner_rtol, max_inner, st);
+                            double rtol, double inner_rtol, double pass_frac, int max_inner, cudaStream_t st) {
+    if (B.fp64)
+        return residual_t<double, double>(B, xin, xout, rhs_vec, first, rtol, inner_rtol, pass_frac, max_inner, st);
+    return residual_t<float, float>(B, xin, xout, rhs_vec, first, rtol, inner_rtol, pass_frac, max_inner, st);
 }
 
 static SchwarzParams schwarz_params(const SolveBufs& B) {

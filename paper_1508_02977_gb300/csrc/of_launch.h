@@ -111,7 +111,7 @@ struct SolveBufs {
 // ||r||^2, ||rhs||^2 (first) and the inner-pass set-up per pair.  xin = NULL
 // means x = 0 (cold start): r = rhs, only the load is formed.
 cudaError_t launch_residual(const SolveBufs& B, const double* xin, double* xout, const double* rhs_vec, int first,
-                            double rtol, double inner_rtol, int max_inner, cudaStream_t st);
+                            double rtol, double inner_rtol, double pass_frac, int max_inner, cudaStream_t st);
 // z = M r at the start of a pass (rz, rr, convergence check).
 cudaError_t launch_precond_first(const SolveBufs& B, cudaStream_t st);
 // One PCG iteration = launch_pcg_apply (p, d, q, a) then launch_pcg_precond
@@ -126,6 +126,12 @@ cudaError_t launch_apply(const SolveBufs& B, int pair, int blk0, int nblk, const
 // r must already be in B.r.
 cudaError_t launch_precond_only(const SolveBufs& B, int pair, int tile0, int ntiles, cudaStream_t st);
 size_t schwarz_smem_bytes(int fp64, int Tx, int Ty, int ov, int nstage);
+// One stationary Schwarz iteration's local solves (of_ras.cu): d = sum_i
+// R~_i^T A_i^{-1} R_i r over all tiles (B.r holds r), then per pair
+// hist[p] = ||d||_2 and the scalars set so that the next residual launch
+// folds d into x.  c0, c1: the element records.
+cudaError_t launch_ras(const SolveBufs& B, const void* c0, const void* c1, double* hist, cudaStream_t st);
+size_t ras_smem_bytes(int fp64, int Tx, int Ty, int ov);
 // Cell records (element data of the preconditioner) of one pair, from the
 // frames and alpha in the workspace; c0, c1: [H][pitch] records.
 cudaError_t launch_cells(const SolveBufs& B, int pair, int W, int H, void* c0, void* c1, cudaStream_t st);

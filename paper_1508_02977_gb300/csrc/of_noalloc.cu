@@ -11,7 +11,9 @@
 // and the only scratch (one FP64 partial pair per thread block plus an
 // arrival counter) is the file-scope array below, which every GPU that loads
 // the library holds until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <mutex>
 
@@ -33,7 +35,28 @@ static __device__ __align__(256) double g_noalloc_scratch[NA_SCRATCH];
 
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_mu;
-double* g_scratch_ptr[NA_MAX_DEVICES] = {};
+// per device: the context the address was looked up in, and the address (a
+// device reset destroys the context and the module with it: the address is
+// then looked up again in the new context)
+struct ScratchSlot {
+    CUcontext ctx;
+    double* ptr;
+};
+ScratchSlot g_slot[NA_MAX_DEVICES] = {};
+
+// the calling thread's current context (driver entry point, no link to libcuda)
+bool current_context(CUcontext* ctx) {
+    static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return false;
+        fn = (PFN_cuCtxGetCurrent_v4000)p;
+    }
+    return fn(ctx) == CUDA_SUCCESS;
+}
 
 // Column-streamed element apply in FP64 on the caller's layouts:
 // frames [H][W], alpha [H-1][W-1][2], U and r [3][H][W].
@@ -134,15 +157,20 @@ extern "C" of_status of_residual_noalloc(int W, int H, const double* f1, const d
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return OF_ERR_CUDA;
     double* scratch = nullptr;
     {
-        // once per device, with that device current: the device address of the
-        // scratch array (its host-side name is only a stand-in)
+        // once per device (and again after a device reset), with that device
+        // current: the device address of the scratch array (its host-side name
+        // is only a stand-in).  cudaSetDevice makes the device's primary
+        // context current in this thread, so that it can be compared.
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_ptr[dev]) {
+        CUcontext ctx = nullptr;
+        if (cudaSetDevice(dev) != cudaSuccess || !current_context(&ctx) || !ctx) return OF_ERR_CUDA;
+        if (!g_slot[dev].ptr || g_slot[dev].ctx != ctx) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return OF_ERR_CUDA;
-            g_scratch_ptr[dev] = static_cast<double*>(p);
+            g_slot[dev].ptr = static_cast<double*>(p);
+            g_slot[dev].ctx = ctx;
         }
-        scratch = g_scratch_ptr[dev];
+        scratch = g_slot[dev].ptr;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the arrival counter must start at zero (an earlier failed call may have left it set)

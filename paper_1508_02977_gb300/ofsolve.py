@@ -35,12 +35,14 @@ class GridOpts(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("overlap", ctypes.c_int),
                 ("sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("lam", ctypes.c_double),
                 ("preconditioner", ctypes.c_int), ("omega", ctypes.c_double), ("sigma", ctypes.c_double),
-                ("model", ctypes.c_int), ("coarse", ctypes.c_int), ("rho", ctypes.c_double)]
+                ("model", ctypes.c_int), ("coarse", ctypes.c_int), ("rho", ctypes.c_double),
+                ("schwarz", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
-                ("warm_start", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("host_loop", ctypes.c_int)]
+                ("warm_start", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("host_loop", ctypes.c_int),
+                ("pass_frac", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -85,20 +87,22 @@ _lib.of_precondition.argtypes = [_h, ctypes.c_int, _vp, _vp, ctypes.c_int]
 _lib.of_residual.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
 _lib.of_set_profiling.argtypes = [_h, ctypes.c_int]
 _lib.of_get_profile.argtypes = [_h, ctypes.POINTER(Profile)]
+_lib.of_get_schwarz_history.argtypes = [_h, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int)]
 _lib.of_residual_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp]
 _lib.of_destroy.argtypes = [_h]
 _lib.of_last_error.argtypes = [_h]
 _lib.of_last_error.restype = ctypes.c_char_p
 for _f in ("of_create", "of_setup_grid", "of_set_frames", "of_get_element_data", "of_set_alpha", "of_get_alpha", "of_solve",
            "of_adapt_alpha", "of_adapt_alpha_vjp", "of_adjoint", "of_apply", "of_precondition", "of_residual",
-           "of_set_profiling", "of_get_profile", "of_residual_noalloc", "of_destroy"):
+           "of_set_profiling", "of_get_profile", "of_residual_noalloc", "of_get_schwarz_history", "of_destroy"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 EXPORTS = ("of_create", "of_setup_grid", "of_set_frames", "of_get_frames", "of_get_element_data", "of_set_alpha",
            "of_get_alpha", "of_solve",
            "of_adapt_alpha", "of_adapt_alpha_vjp", "of_adjoint", "of_apply", "of_precondition", "of_residual",
            "of_set_profiling", "of_get_profile", "of_residual_noalloc", "of_set_wait_limit", "of_debug_starve_staging",
-           "of_set_alloc_limit",
+           "of_set_alloc_limit", "of_get_schwarz_history",
            "of_destroy", "of_last_error")
 
 
@@ -157,17 +161,18 @@ def of_create(device: int = 0, stream=None):
 
 
 def of_setup_grid(h, sizes, tile=(32, 32), overlap=0, sweeps=1, precision=OF_PREC_MIXED, lam=1.0,
-                  preconditioner=OF_PC_SCHWARZ, omega=1.0, sigma=0.0, model=0, coarse=0, rho=0.0):
+                  preconditioner=OF_PC_SCHWARZ, omega=1.0, sigma=0.0, model=0, coarse=0, rho=0.0, schwarz=0):
     """sizes: list of (W, H); omega: relaxation factor of the local block SOR
     sweeps, in (0, 2); sigma: K_sigma pre-smoothing of the frames (0: none);
     model: OF_MODEL_ILLUMINATION or OF_MODEL_CONSTANT; coarse: spacing of the
     two-level preconditioner's coarse grid in nodes (0: one level); rho: K_rho
-    integration scale of the data term (0: none)."""
+    integration scale of the data term (0: none); schwarz: 1 makes of_solve
+    run the stationary Schwarz iteration instead of the PCG."""
     n = len(sizes)
     Wa = (ctypes.c_int32 * n)(*[int(w) for w, _ in sizes])
     Ha = (ctypes.c_int32 * n)(*[int(hh) for _, hh in sizes])
     o = GridOpts(int(tile[0]), int(tile[1]), int(overlap), int(sweeps), int(precision), float(lam), int(preconditioner),
-                 float(omega), float(sigma), int(model), int(coarse), float(rho))
+                 float(omega), float(sigma), int(model), int(coarse), float(rho), int(schwarz))
     return _check(h, _lib.of_setup_grid(h, n, Wa, Ha, ctypes.byref(o)))
 
 
@@ -206,7 +211,7 @@ def of_get_alpha(h, pair, out):
 
 
 def of_solve(h, U, rtol=1e-6, max_outer=20, max_inner=2000, warm_start=False, inner_rtol=0.0, raise_on=True,
-             host_loop=False):
+             host_loop=False, pass_frac=0.0):
     """U: list of [3][H][W] arrays (one per pair, same dtype).  Returns
     (status, [info dict per pair])."""
     ptrs = [_ptr_dtype(u) for u in U]
@@ -214,11 +219,22 @@ def of_solve(h, U, rtol=1e-6, max_outer=20, max_inner=2000, warm_start=False, in
     arr = (_vp * len(U))(*[p for p, _ in ptrs])
     info = (SolveInfo * len(U))()
     o = SolveOpts(float(rtol), int(max_outer), int(max_inner), int(bool(warm_start)), float(inner_rtol),
-                  int(bool(host_loop)))
+                  int(bool(host_loop)), float(pass_frac))
     st = _lib.of_solve(h, ctypes.byref(o), arr, dt, info)
     if raise_on:
         _check(h, st)
     return st, [i.as_dict() for i in info]
+
+
+def of_get_schwarz_history(h, pair):
+    """||U^k - U^{k-1}||_2 of each iteration of the last stationary Schwarz
+    solve of a pair (numpy array)."""
+    n = ctypes.c_int(0)
+    _check(h, _lib.of_get_schwarz_history(h, int(pair), None, 0, ctypes.byref(n)))
+    out = np.zeros(max(n.value, 1))
+    _check(h, _lib.of_get_schwarz_history(h, int(pair), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          n.value, ctypes.byref(n)))
+    return out[:n.value]
 
 
 def of_adapt_alpha(h, kappa, eta_thr, alpha_th, eta=None):

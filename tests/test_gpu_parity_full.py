@@ -110,19 +110,20 @@ def test_batch_every_size_class(S, oracle):
 
 
 # Gradient tolerance of the mixed path (derivation).  Both solves (U and the
-# adjoint state lambda) stop at a relative residual <= 1e-6.  The flow error
-# that leaves is measured above to be <= 1e-4 px; relative to the flow it is
-# ~1e-5 or less.  The gradients are bilinear in (U, lambda): dL/dalpha_K =
-# -|K| sum_c grad(lambda_c).grad(U_c), dL/df2 through g_K and ft_K.  The
-# loss's own gradient dL/dU = (u - u_gt) / (N EPE) changes by |du| / (N EPE)
-# at a pixel, so the adjoint right-hand side inherits the flow error divided
-# by the local endpoint error; its relative 2-norm change is the rms of
-# |du| / EPE, which for EPE >~ 1e-2 px and |du| <= 1e-4 px is <= 1e-2 at
-# single pixels and far less in the mean.  lambda = A^{-1} (dL/dU) smooths
-# these pixel-local changes.  Hence the relative 2-norm of the gradient
-# error is bounded by ~1e-3, and each entry by ~1e-2 of the largest entry.
-GRAD_REL2 = 1e-3
-GRAD_MAX = 1e-2
+# adjoint state lambda) stop at a relative residual r <= pass_frac * 1e-6 =
+# 2.5e-7 (the last refinement pass aims at a quarter of the tolerance).  The
+# relative error of a solution is at most kappa_eff * r, kappa_eff the ratio
+# of relative error to relative residual; on these scenes it is ~30 (flow
+# error 4e-5 px on flows of ~6 px at r = 2.3e-7 on the 3840x2160 pair).  The
+# gradients are bilinear in (U, lambda): dL/dalpha_K = -|K| sum_c
+# grad(lambda_c).grad(U_c), and dL/df2 through g_K and ft_K, so their relative
+# error is at most the sum of those of U and lambda, 2 * 30 * 2.5e-7 = 1.5e-5
+# in the 2-norm.  (The loss's own gradient dL/dU = (u - u_gt) / (N EPE) moves
+# by |du| / EPE at a pixel; with EPE >~ 1e-2 px on this smooth flow that is
+# within the same bound.)  Single entries, where cancellation between the
+# two fields is strongest, get ten times that against the largest entry.
+GRAD_REL2 = 2e-5
+GRAD_MAX = 1e-4
 
 
 def test_adjoint_batch_8x512_mixed(S, oracle):

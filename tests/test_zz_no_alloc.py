@@ -66,6 +66,28 @@ def test_noalloc_residual_matches_handle_path_twice(S):
         assert np.all(np.abs(r.cpu().numpy() - r_ref) <= 1e-13 * (scale + 1e-300))
 
 
+def test_noalloc_norms_without_r_match_handle_and_oracle(S, oracle):
+    """With r = NULL only the norms are written: the same relative residual
+    as of_residual and as the FP64 oracle's CSR residual, on two calls in a
+    row (a solve-like U, so that the residual is small against b)."""
+    lam = 1.0
+    for k, (W, H) in enumerate([(96, 80), (250, 31)]):
+        p = synth.texture(W, H, seed=930 + k)
+        alpha = np.full((H - 1, W - 1, 2), p.alpha0)
+        sysm = oracle.System.from_frames(p.f1, p.f2, alpha, lam)
+        U, _, _ = sysm.solve_pcg(tol=1e-4)
+        rel_o = sysm.rel_residual(U)
+        rel_ref, _, _ = handle_reference(S, p.f1, p.f2, alpha, lam, U)
+        norms = torch.zeros(3, dtype=torch.float64, device="cuda")
+        st = S.of_residual_noalloc(dev(p.f1), dev(p.f2), dev(alpha), lam, dev(U), None, norms)
+        assert st == S.OF_OK
+        torch.cuda.synchronize()
+        n = norms.cpu().numpy()
+        assert abs(n[0] - rel_ref) <= 1e-12 * rel_ref
+        assert abs(n[0] - rel_o) <= 1e-9 * rel_o
+        assert n[2] == pytest.approx(np.dot(sysm.b, sysm.b), rel=1e-12)
+
+
 def test_noalloc_rejects_frames_beyond_the_scratch(S):
     W, H = 20000, 8192  # ceil(20000/124) * ceil(8192/32) = 162 * 256 > 32768
     tiny = torch.zeros(1, dtype=torch.float64, device="cuda")
