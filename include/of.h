@@ -132,13 +132,13 @@ typedef struct {
     int warm_start;    /* 1: start from the U passed in; 0: start from U = 0 */
     double inner_rtol; /* mixed: a pass asks the inner PCG to bring its starting residual down to
                           pass_frac times the outer tolerance, but by no more than this factor
-                          [1e-6] */
+                          [5e-7] */
     int host_loop;     /* 1: drive the inner PCG loop from the host (launch by launch, polling
                           convergence); 0: one CUDA graph per pass whose while-node the device
                           ends [0] */
     double pass_frac;  /* mixed: the fraction of the outer tolerance a refinement pass aims at, in
-                          (0, 1] [0.25]; the final residual then lies further below rtol, which
-                          bounds the flow error more tightly at the cost of iterations */
+                          (0, 1] [0.5]; a smaller fraction leaves the final residual further below
+                          rtol, which bounds the flow error more tightly at the cost of iterations */
 } of_solve_opts;
 
 /* Per-pair result of of_solve / of_adjoint (host memory, written on return). */
