@@ -44,7 +44,7 @@ SMS = 152  # streaming multiprocessors of a GB300
 #   schwarz:   read r, q (2 x 12) + f1, f2, alpha (16);         write r, z (2 x 12)
 #   residual:  read x (24), d, p (2 x 12), f1, f2, alpha (16);  write x (24), r (12)
 ALG_BYTES_PER_PX = {"pcg_apply": 88, "schwarz": 64, "residual": 100}
-KERNEL_NAMES = {"pcg_apply": "k_apply4<MODE_PCG>", "schwarz": "k_schwarz<float,2,48,48,0>",
+KERNEL_NAMES = {"pcg_apply": "k_apply4<MODE_PCG>", "schwarz": "k_schwarz_h2<48,48,0> (FP16 paired sweeps)",
                 "residual": "k_apply<double,float,float,MODE_RES,DF>"}
 
 

@@ -121,6 +121,13 @@ typedef struct {
                                    ||b - A U|| <= rtol ||b|| or max_inner iterations; inner_iters counts the
                                    iterations and of_get_schwarz_history gives ||U^k - U^{k-1}||_2 of each.
                                    Needs the Schwarz preconditioner settings, coarse = 0 and rho = 0 */
+    int half_sweeps;         /* mixed path, PCG: local sweeps of the Schwarz preconditioner in packed FP16
+                                arithmetic, two nodes per instruction [0]: 0 = wherever the tile allows
+                                (sweeps >= 1, extended tile height 2 HP with HP a multiple of 3, at most
+                                384 node pairs per colour), 1 = required (OF_ERR_ARG where not allowed),
+                                -1 = FP32 sweeps.  The right-hand side of each local solve is scaled by its
+                                first Jacobi step's largest entry, the diagonal blocks and the residual
+                                update stay FP32, and r.z is formed in FP32 */
 } of_grid_opts;
 
 /* Solve options.  A field left at 0 takes the default in brackets. */

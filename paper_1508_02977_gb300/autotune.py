@@ -15,11 +15,16 @@ import time
 
 from . import partition
 
-# (tile, overlap, sweeps[, omega]); omega defaults to 1 (block Gauss-Seidel)
+# (tile, overlap, sweeps[, omega]); omega defaults to 1 (block Gauss-Seidel).
+# Tiles 32..128 and overlaps 0..16 as far as one CTA holds the extended tile
+# (at most 2304 nodes: 48 x 48, or 64 x 36, 96 x 24, 128 x 18 without overlap);
+# extended heights of 6k nodes also run the FP16 paired sweeps.
 DEFAULT_CANDIDATES = (
     ((48, 48), 0, 4, 1.6), ((48, 48), 0, 3, 1.6), ((48, 48), 0, 3, 1.0), ((48, 48), 0, 2, 1.5),
-    ((48, 48), 0, 4, 1.7), ((32, 32), 0, 3, 1.6), ((64, 32), 0, 3, 1.6), ((40, 40), 0, 3, 1.6),
-    ((32, 32), 2, 2, 1.0), ((32, 32), 0, 1, 1.0),
+    ((48, 48), 0, 4, 1.7), ((48, 48), 0, 5, 1.7), ((32, 32), 0, 3, 1.6), ((64, 32), 0, 3, 1.6),
+    ((64, 36), 0, 4, 1.6), ((96, 24), 0, 4, 1.6), ((128, 18), 0, 4, 1.6), ((40, 40), 0, 3, 1.6),
+    ((44, 44), 2, 4, 1.6), ((40, 40), 4, 4, 1.6), ((36, 36), 6, 4, 1.6), ((32, 32), 8, 4, 1.6),
+    ((32, 32), 8, 6, 1.6), ((16, 16), 16, 4, 1.6), ((32, 32), 2, 2, 1.0), ((32, 32), 0, 1, 1.0),
 )
 FALLBACK = {"tile": (48, 48), "overlap": 0, "sweeps": 4, "omega": 1.6}
 

@@ -16,6 +16,7 @@
 #include "of.h"
 #include "of_launch.h"
 #include "of_schwarz.cuh"
+#include "of_schwarz_h2.cuh"
 
 using ofk::PairDesc;
 using ofk::PairScalars;
@@ -41,7 +42,7 @@ struct of_ctx {
     std::vector<PairDesc> pd;
     std::vector<int4> blocks, tiles;
     std::vector<int> blk0, nblk, tile0, ntile;
-    long long frame_elems = 0, vec_elems = 0;
+    long long frame_elems = 0, vec_elems = 0, pair_elems = 0;
     int nblk_total = 0, ntiles_total = 0, rows_per_block = 16;
     // device memory
     std::vector<void*> allocs;
@@ -56,6 +57,8 @@ struct of_ctx {
     uint32_t* ntab_dev = nullptr;
     int sch_threads = 0, sch_npt = 1, sch_grid = 1, sch_nstage = 2;
     void *cell0 = nullptr, *cell1 = nullptr;  // preconditioner element records [H][pitch]
+    int h2 = 0;                                // FP16 paired sweeps (mixed path)
+    void *cp0 = nullptr, *cp1 = nullptr;       // their paired records [H][pitch] (16 bytes each)
     bool cells_dirty = true;
     // inner PCG loop as a CUDA graph: while(any pair iterating) { apply; Schwarz }
     cudaGraph_t loop_graph = nullptr;
@@ -297,6 +300,9 @@ ofl::SolveBufs solve_bufs(of_ctx* h) {
     B.spin_limit = h->spin_limit;
     B.tx_extra = h->starve_bytes;
     B.coarse = h->coarse;
+    B.h2 = h->h2;
+    B.cp0 = h->cp0;
+    B.cp1 = h->cp1;
     return B;
 }
 
@@ -385,6 +391,21 @@ of_status encode_maps(of_ctx* h) {
                                   str, box, es1, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
                 if (rc != CUDA_SUCCESS) return fail(h, OF_ERR_CUDA, "tensor map (cells) encoding failed");
+            }
+        }
+        if (h->h2) {  // paired records of the FP16 sweeps: 16 bytes = two 8-byte units per record
+            const int RW = ofk::sch_rw(Tx, ov), HP = ofk::h2_hp(Ty, ov);
+            // ov + 1 extra rows on top: a tile's box starts at row y0 >= 0 and
+            // never in the fill region (whose lane-B half would be lost)
+            const cuuint64_t dims[2] = {(cuuint64_t)d.W * 2, (cuuint64_t)(d.H + ov + 1)};
+            const cuuint64_t str[1] = {(cuuint64_t)d.pitch * 16};
+            const cuuint32_t box[2] = {(cuuint32_t)(RW * 2), (cuuint32_t)(HP + 1)};
+            for (int k = 0; k < 2; ++k) {
+                char* base = (char*)(k == 0 ? h->cp0 : h->cp1) + d.pair_off * 16;
+                CUresult rc = enc(&m[k == 0 ? ofk::TM_P0 : ofk::TM_P1], CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, base, dims,
+                                  str, box, es1, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (rc != CUDA_SUCCESS) return fail(h, OF_ERR_CUDA, "tensor map (paired records) encoding failed");
             }
         }
         {  // r and q planes
@@ -744,6 +765,25 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
     if (smem > (size_t)smax) return fail(h, OF_ERR_ARG, "tile/overlap need more shared memory than one CTA has");
     if (opt.schwarz == 1 && ofl::ras_smem_bytes(fp64, opt.tile_x, opt.tile_y, opt.overlap) > (size_t)smax)
         return fail(h, OF_ERR_ARG, "tile/overlap need more shared memory than one CTA has");
+    // FP16 paired sweeps on the mixed path: by default wherever the tile can be
+    // paired (half the extended height a multiple of 3, one pair per thread)
+    if (opt.half_sweeps < -1 || opt.half_sweeps > 1) return fail(h, OF_ERR_ARG, "half_sweeps must be -1, 0 or 1");
+    std::vector<uint32_t> ntab_h2;
+    int h2_threads = 0, nstage_h2 = 2;
+    size_t smem_h2 = 0;
+    bool h2 = false;
+    if (!fp64 && opt.half_sweeps >= 0 && opt.preconditioner == OF_PC_SCHWARZ && opt.sweeps >= 1 && opt.schwarz == 0 &&
+        ofl::schwarz_h2_node_table(opt.tile_x, opt.tile_y, opt.overlap, ntab_h2, h2_threads)) {
+        smem_h2 = ofl::schwarz_h2_smem_bytes(opt.tile_x, opt.tile_y, opt.overlap, 2);
+        if (smem_h2 > (size_t)smax) {
+            nstage_h2 = 1;
+            smem_h2 = ofl::schwarz_h2_smem_bytes(opt.tile_x, opt.tile_y, opt.overlap, 1);
+        }
+        h2 = smem_h2 <= (size_t)smax;
+    }
+    if (opt.half_sweeps == 1 && !h2)
+        return fail(h, OF_ERR_ARG, "FP16 paired sweeps need the mixed path, the Schwarz preconditioner with sweeps >= 1 "
+                                   "and an extended tile height of 6k nodes (k <= 8)");
 
     CK(cudaStreamSynchronize(h->stream));
     free_all(h);
@@ -776,7 +816,7 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
     h->nblk.assign(batch, 0);
     h->tile0.assign(batch, 0);
     h->ntile.assign(batch, 0);
-    long long fo = 0, vo = 0;
+    long long fo = 0, vo = 0, po = 0;
     size_t stage = 0;
     const int cols_per_block = 31 * 4;
     for (int p = 0; p < batch; ++p) {
@@ -801,11 +841,14 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
         h->nblk[p] = d.nblk;
         h->tile0[p] = d.tile0;
         h->ntile[p] = d.tiles_x * d.tiles_y;
+        d.pair_off = po;
         fo += (long long)H[p] * d.pitch;
+        po += (long long)(H[p] + opt.overlap + 1) * d.pitch;
         vo += 3LL * H[p] * d.pitch;
         stage = std::max(stage, (size_t)3 * W[p] * H[p] * 8);
     }
     h->frame_elems = fo;
+    h->pair_elems = po;
     h->vec_elems = vo;
     h->nblk_total = (int)h->blocks.size();
     h->ntiles_total = (int)h->tiles.size();
@@ -824,6 +867,12 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
     CK(dalloc(h, &h->eta, 2 * fo * es));
     CK(dalloc(h, &h->cell0, fo * (h->fp64 ? 32 : 8)));
     CK(dalloc(h, &h->cell1, fo * (h->fp64 ? 32 : 8)));
+    h->h2 = h2 ? 1 : 0;
+    h->cp0 = h->cp1 = nullptr;
+    if (h2) {
+        CK(dalloc(h, &h->cp0, h->pair_elems * 16));
+        CK(dalloc(h, &h->cp1, h->pair_elems * 16));
+    }
     for (int k = 0; k < 2; ++k) CK(dalloc(h, &h->x[k], vo * sizeof(double)));
     CK(dalloc(h, &h->usol, vo * sizeof(double)));
     CK(dalloc(h, &h->cvec, vo * sizeof(double)));
@@ -866,13 +915,22 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
     CK(cudaMemsetAsync(h->err_dev, 0, sizeof(int), st));
     of_status s = encode_maps(h);
     if (s != OF_OK) return s;
-    CK(dalloc(h, &h->ntab_dev, ntab.size() * sizeof(uint32_t)));
+    CK(dalloc(h, &h->ntab_dev, std::max(ntab.size(), ntab_h2.size()) * sizeof(uint32_t)));
     CK(cudaMemcpyAsync(h->ntab_dev, ntab.data(), ntab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     h->sch_threads = sch_threads;
     h->sch_npt = sch_npt;
     h->sch_nstage = nstage;
     CK(ofl::schwarz_configure(fp64, sch_npt, opt.tile_x, opt.tile_y, opt.overlap, smem));
     h->sch_grid = ofl::schwarz_max_grid(fp64, sch_npt, opt.tile_x, opt.tile_y, opt.overlap, sch_threads, smem);
+    if (h2) {
+        // the paired sweeps replace the FP32 sweeps of the PCG preconditioner
+        CK(cudaMemcpyAsync(h->ntab_dev, ntab_h2.data(), ntab_h2.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+        h->sch_threads = h2_threads;
+        h->sch_npt = 1;
+        h->sch_nstage = nstage_h2;
+        CK(ofl::schwarz_h2_configure(opt.tile_x, opt.tile_y, opt.overlap, smem_h2));
+        h->sch_grid = ofl::schwarz_h2_max_grid(opt.tile_x, opt.tile_y, opt.overlap, h2_threads, smem_h2);
+    }
     if (opt.coarse > 0 && opt.preconditioner == OF_PC_SCHWARZ) {
         // coarse grid of every pair: nodes at 0, s, 2s, ... and W - 1 (same in y)
         std::vector<ofl::CoarseCell> cells;

@@ -27,6 +27,8 @@ struct PairDesc {
     int blk0, nblk;         // first apply block of this pair, number of apply blocks
     long long frame_off;    // element offset of this pair's frames in the frame arrays
     long long vec_off;      // element offset of this pair's planes in the vector arrays
+    long long pair_off;     // element offset of this pair's paired element records (FP16 sweeps):
+                            // [H + ov + 1][pitch], row k holding the records of image row k - ov - 1
 };
 
 // Per-pair scalars of the Krylov loop (device memory, FP64).

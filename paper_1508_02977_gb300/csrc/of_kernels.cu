@@ -4,6 +4,7 @@
 #include "of_apply.cuh"
 #include "of_launch.h"
 #include "of_schwarz.cuh"
+#include "of_schwarz_h2.cuh"
 
 namespace ofl {
 
@@ -163,6 +164,58 @@ static cudaError_t with_schwarz(int tx, int ty, int ov, F f) {
     return f(k_schwarz<R, NPT, 0, 0, 0>);
 }
 
+// FP16 paired sweeps: the tuned shape with a compile-time geometry
+template <typename F>
+static cudaError_t with_schwarz_h2(int tx, int ty, int ov, F f) {
+    if (tx == 48 && ty == 48 && ov == 0) return f(k_schwarz_h2<48, 48, 0>);
+    return f(k_schwarz_h2<0, 0, 0>);
+}
+
+size_t schwarz_h2_smem_bytes(int Tx, int Ty, int ov, int nstage) { return h2_smem_bytes(Tx, Ty, ov, nstage); }
+
+cudaError_t schwarz_h2_configure(int tx, int ty, int ov, size_t smem) {
+    return with_schwarz_h2(tx, ty, ov, [&](auto kern) {
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+}
+
+int schwarz_h2_max_grid(int tx, int ty, int ov, int threads, size_t smem) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    with_schwarz_h2(tx, ty, ov, [&](auto kern) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem);
+    });
+    if (per < 1) per = 1;
+    return per * (sms > 0 ? sms : 1);
+}
+
+bool schwarz_h2_node_table(int Tx, int Ty, int ov, std::vector<uint32_t>& tab, int& threads) {
+    if (!h2_shape_ok(Ty, ov)) return false;
+    const int Ex = Tx + 2 * ov, HP = h2_hp(Ty, ov), RW = sch_rw(Tx, ov), cpad = sch_cpad(ov);
+    std::vector<std::vector<uint32_t>> slots[3];
+    int maxslots = 0;
+    for (int c = 0; c < 3; ++c) {
+        std::vector<std::vector<uint32_t>> bucket(32);
+        for (int j = 0; j < HP; ++j)
+            for (int i = 0; i < Ex; ++i)
+                if ((i + j) % 3 == c) bucket[((j + 1) * RW + (i + cpad - ov)) % 32].push_back((uint32_t)i | ((uint32_t)j << 16));
+        size_t ns = 0;
+        for (auto& b : bucket) ns = std::max(ns, b.size());
+        slots[c].assign(ns, std::vector<uint32_t>(32, 0xffffffffu));
+        for (int b = 0; b < 32; ++b)
+            for (size_t k = 0; k < bucket[b].size(); ++k) slots[c][k][b] = bucket[b][k];
+        maxslots = std::max(maxslots, (int)slots[c].size());
+    }
+    if (maxslots < 1 || maxslots > 12) return false;  // one pair per thread and colour, at most 384 threads
+    threads = 32 * maxslots;
+    tab.assign((size_t)3 * threads, 0xffffffffu);
+    for (int c = 0; c < 3; ++c)
+        for (size_t s = 0; s < slots[c].size(); ++s)
+            for (int l = 0; l < 32; ++l) tab[(size_t)c * threads + s * 32 + l] = slots[c][s][l];
+    return true;
+}
+
 template <typename F>
 static cudaError_t with_schwarz_all(int fp64, int npt, int tx, int ty, int ov, F f) {
     if (fp64) return npt == 1 ? with_schwarz<double, 1>(tx, ty, ov, f) : with_schwarz<double, 2>(tx, ty, ov, f);
@@ -194,8 +247,41 @@ static cudaError_t cells_t(const SolveBufs& B, int pair, int W, int H, void* c0,
     return cudaGetLastError();
 }
 
+namespace {
+using namespace ofk;
+// Paired element records of one pair from the FP16 records of k_cells:
+// row k of the paired plane holds image row y = k - R (R = ov + 1 rows above
+// the image, so that no tile's box starts above the plane), lane by lane
+// (rec(x, y), rec(x, y + HP)) (see RecH2), each half zero where its row lies
+// outside the image.
+__global__ void k_cells_h2(const PairDesc* pairs, int pair, int HP, int R, const uint2* __restrict__ c0a,
+                           const uint2* __restrict__ c1a, uint4* __restrict__ p0a, uint4* __restrict__ p1a) {
+    const PairDesc pd = pairs[pair];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (x >= pd.W) return;
+    const int y = k - R;
+    const long long o = pd.frame_off + (long long)y * pd.pitch + x;
+    const bool has_a = y >= 0 && y < pd.H, has_b = y + HP >= 0 && y + HP < pd.H;
+    const long long ob = o + (long long)HP * pd.pitch;
+    // record words: x = (h0, h1), y = (h2, w); pair the low and the high halves
+    auto pack = [](uint2 a, uint2 b) {
+        return make_uint4(__byte_perm(a.x, b.x, 0x5410), __byte_perm(a.x, b.x, 0x7632),
+                          __byte_perm(a.y, b.y, 0x5410), __byte_perm(a.y, b.y, 0x7632));
+    };
+    const uint2 zero = make_uint2(0u, 0u);
+    const long long po = pd.pair_off + (long long)k * pd.pitch + x;
+    p0a[po] = pack(has_a ? c0a[o] : zero, has_b ? c0a[ob] : zero);
+    p1a[po] = pack(has_a ? c1a[o] : zero, has_b ? c1a[ob] : zero);
+}
+}  // namespace
+
 cudaError_t launch_cells(const SolveBufs& B, int pair, int W, int H, void* c0, void* c1, cudaStream_t st) {
-    return B.fp64 ? cells_t<double>(B, pair, W, H, c0, c1, st) : cells_t<float>(B, pair, W, H, c0, c1, st);
+    cudaError_t e = B.fp64 ? cells_t<double>(B, pair, W, H, c0, c1, st) : cells_t<float>(B, pair, W, H, c0, c1, st);
+    if (e != cudaSuccess || !B.h2) return e;
+    dim3 grid((W + 127) / 128, H + B.ov + 1);
+    k_cells_h2<<<grid, 128, 0, st>>>(B.pairs, pair, h2_hp(B.Ty, B.ov), B.ov + 1, (const uint2*)c0,
+                                     (const uint2*)c1, (uint4*)B.cp0, (uint4*)B.cp1);
+    return cudaGetLastError();
 }
 
 bool schwarz_node_table(int fp64, int Tx, int Ty, int ov, std::vector<uint32_t>& tab, int& threads, int& npt) {
@@ -235,12 +321,19 @@ bool schwarz_node_table(int fp64, int Tx, int Ty, int ov, std::vector<uint32_t>&
 }
 
 static cudaError_t schwarz_launch(const SolveBufs& B, const SchwarzParams& S, int ntiles, cudaStream_t st) {
-    const size_t smem = schwarz_smem_bytes(B.fp64, B.Tx, B.Ty, B.ov, B.sch_nstage);
     const int nt = B.sch_threads;
     const int grid = ntiles < B.sch_grid ? ntiles : B.sch_grid;
     if (grid <= 0) return cudaSuccess;
     SchwarzParams S2 = S;
     S2.ntiles = ntiles;
+    if (B.h2) {
+        const size_t smem = h2_smem_bytes(B.Tx, B.Ty, B.ov, B.sch_nstage);
+        return with_schwarz_h2(B.Tx, B.Ty, B.ov, [&](auto kern) {
+            kern<<<grid, nt, smem, st>>>(S2);
+            return cudaGetLastError();
+        });
+    }
+    const size_t smem = schwarz_smem_bytes(B.fp64, B.Tx, B.Ty, B.ov, B.sch_nstage);
     return with_schwarz_all(B.fp64, B.sch_npt, B.Tx, B.Ty, B.ov, [&](auto kern) {
         kern<<<grid, nt, smem, st>>>(S2);
         return cudaGetLastError();

@@ -104,6 +104,9 @@ struct SolveBufs {
     int use_cond;        // Schwarz launches inside the inner-loop graph set its condition
     int tx_extra;        // test hook: bytes the staging barriers expect beyond the copies
     CoarseBufs coarse;   // two-level preconditioner (coarse.on = 0: one level)
+    int h2;              // mixed path: FP16 paired sweeps (of_schwarz_h2.cuh)
+    void* cp0;           // their paired element records [H][pitch] (16 bytes each)
+    void* cp1;
     cudaGraphConditionalHandle cond;
 };
 
@@ -138,10 +141,17 @@ cudaError_t launch_cells(const SolveBufs& B, int pair, int W, int H, void* c0, v
 // Persistent CTAs of the Schwarz kernel that fit on the device at once.
 int schwarz_max_grid(int fp64, int npt, int tx, int ty, int ov, int threads, size_t smem);
 cudaError_t schwarz_configure(int fp64, int npt, int tx, int ty, int ov, size_t smem);
+int schwarz_h2_max_grid(int tx, int ty, int ov, int threads, size_t smem);
+cudaError_t schwarz_h2_configure(int tx, int ty, int ov, size_t smem);
 // Host-built assignment of the extended tile's nodes to (colour, slot,
 // thread) such that the 32 lanes of a warp touch 32 distinct shared-memory
 // banks.  Returns false if a tile needs more than 2 slots per thread.
 bool schwarz_node_table(int fp64, int Tx, int Ty, int ov, std::vector<uint32_t>& tab, int& threads, int& npt);
+// The same for the FP16 paired sweeps: the node pairs (i, j), j < HP, of the
+// extended tile, one pair per thread and colour, 32 distinct banks per warp.
+// Returns false if the shape cannot be paired or needs more than 384 threads.
+bool schwarz_h2_node_table(int Tx, int Ty, int ov, std::vector<uint32_t>& tab, int& threads);
+size_t schwarz_h2_smem_bytes(int Tx, int Ty, int ov, int nstage);
 
 // ---- adaptation (of_adapt.cu)
 struct AdaptBufs {

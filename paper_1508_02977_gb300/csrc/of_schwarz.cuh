@@ -59,7 +59,9 @@
 
 namespace ofk {
 
-enum { TM_C0 = 0, TM_C1 = 1, TM_R = 2, TM_Q = 3, TM_Z = 4, TM_PER_PAIR = 5 };
+// tensor maps of a pair: element records, r, q, z, and the paired records of
+// the FP16 sweeps (of_schwarz_h2.cuh)
+enum { TM_C0 = 0, TM_C1 = 1, TM_R = 2, TM_Q = 3, TM_Z = 4, TM_P0 = 5, TM_P1 = 6, TM_PER_PAIR = 7 };
 
 struct SchwarzParams {
     const PairDesc* pairs;

@@ -1,0 +1,530 @@
+// Overlapping Schwarz preconditioner, FP16 paired form (mixed path).
+//
+// The same operator as k_schwarz (of_schwarz.cuh): symmetric restricted
+// Schwarz on extended tiles, local solves by s symmetric 3-colour block SOR
+// sweeps from zero (Section 3.2, Eq. schwarz), but the sweeps run in packed
+// half-precision arithmetic on two nodes at once.  The extended tile of
+// Ex x Ey nodes is cut into a top half (rows 0 .. HP-1) and a bottom half
+// (rows HP .. 2HP-1), HP = Ey / 2 a multiple of 3, so that node (i, j) and
+// node (i, j + HP) have the same colour; they share one half2 lane pair in
+// every shared-memory word (lane A: top, lane B: bottom) and one thread
+// updates both with the same instructions.  One 32-bit load then serves two
+// node updates, the element records need no conversion, and every FMA works
+// on two nodes.
+//
+// Range: the local solve is linear, so it is run on the scaled right-hand
+// side b / m, m = max over the tile of |D_n^{-1} b_n| (the first Jacobi
+// step), which keeps the iterates of order one, and the result is scaled
+// back in FP32.  The residual update r <- r - a q, the diagonal blocks and
+// their LDL^T factors are formed in FP32 (the factors are then rounded to
+// FP16), and r.z is accumulated in FP32 from the FP32 residual, so only the
+// sweep arithmetic is in half precision.
+//
+// Seam: the top half's last row (HP-1) and the bottom half's first row (HP)
+// are stencil neighbours.  Their values are also kept in two ghost rows of
+// the paired array: paired row -1, lane B holds node row HP-1 (the south
+// neighbour of lane B's paired row 0), paired row HP, lane A holds node row
+// HP (the north neighbour of lane A's paired row HP-1); the other lanes of
+// those rows are the Dirichlet ring (zero).  A node on a seam row writes its
+// ghost in the same colour step as itself, so the colour schedule that makes
+// the sweeps race-free covers the ghosts as well.
+#pragma once
+#include <cuda_fp16.h>
+
+#include "of_schwarz.cuh"
+
+namespace ofk {
+
+// paired element record of one square: (h0, h1, h2, w) of the top node's
+// square (lane A) and of the square HP rows below it (lane B)
+struct RecH2 {
+    __half2 h0, h1, h2, w;
+};
+
+struct H2Layout {
+    size_t bar, stage0, stage_bytes, p0, p1, rs, qs, zs, total;
+};
+
+__host__ __device__ inline int h2_hp(int Ty, int ov) { return (Ty + 2 * ov) / 2; }
+
+// Records of the window: RW x (HP + 1) per triangle family (ext rows -1 .. HP-1
+// in lane A); z: 3 planes of RW x (HP + 2) half2 (paired rows -1 .. HP).
+__host__ __device__ inline H2Layout h2_layout(int Tx, int Ty, int ov, int nstage) {
+    auto al = [](size_t b) { return (b + 127) & ~(size_t)127; };
+    const int HP = h2_hp(Ty, ov), RW = sch_rw(Tx, ov);
+    const size_t nr = (size_t)RW * (HP + 1), nz = (size_t)RW * (HP + 2);
+    H2Layout L;
+    L.bar = 0;
+    L.p0 = 0;
+    L.p1 = al(nr * sizeof(RecH2));
+    L.rs = L.p1 + al(nr * sizeof(RecH2));
+    L.qs = L.rs + al(3 * (size_t)Tx * Ty * sizeof(float));
+    L.stage_bytes = L.qs + al(3 * (size_t)Tx * Ty * sizeof(float));
+    L.stage0 = 128;
+    L.zs = L.stage0 + (size_t)nstage * L.stage_bytes;
+    L.total = L.zs + al(3 * nz * sizeof(__half2)) + 128;
+    return L;
+}
+
+__host__ __device__ inline size_t h2_smem_bytes(int Tx, int Ty, int ov, int nstage) {
+    return h2_layout(Tx, Ty, ov, nstage).total;
+}
+
+// Whether a tile shape can use the paired form: an even extended height whose
+// half is a multiple of 3 (the two lanes of a word then have one colour).
+__host__ __device__ inline bool h2_shape_ok(int Ty, int ov) {
+    const int Ey = Ty + 2 * ov;
+    return Ey % 2 == 0 && (Ey / 2) % 3 == 0;
+}
+
+__device__ __forceinline__ float h_lo(__half2 v) { return __low2float(v); }
+__device__ __forceinline__ float h_hi(__half2 v) { return __high2float(v); }
+__device__ __forceinline__ float h_lane(__half2 v, int L) { return L ? __high2float(v) : __low2float(v); }
+
+// LDL^T factors of a pair of 3x3 diagonal blocks (as Blk<float>, lane-packed)
+struct BlkH2 {
+    __half2 i0, l10, l20, i1, l21, i2;
+};
+
+__device__ __forceinline__ void block_solve_h2(const BlkH2& B, __half2 b0, __half2 b1, __half2 b2, __half2& x0,
+                                               __half2& x1, __half2& x2) {
+    const __half2 y1 = __hfma2(__hneg2(B.l10), b0, b1);
+    const __half2 y2 = __hfma2(__hneg2(B.l21), y1, __hfma2(__hneg2(B.l20), b0, b2));
+    x2 = __hmul2(y2, B.i2);
+    x1 = __hfma2(__hneg2(B.l21), x2, __hmul2(y1, B.i1));
+    x0 = __hfma2(__hneg2(B.l20), x2, __hfma2(__hneg2(B.l10), x1, __hmul2(b0, B.i0)));
+}
+
+// b <- b - h (h . (za + zb)) for one element, both lanes
+__device__ __forceinline__ void elem_h2(const RecH2& r, __half2 za0, __half2 za1, __half2 za2, __half2 zb0,
+                                        __half2 zb1, __half2 zb2, __half2& b0, __half2& b1, __half2& b2) {
+    const __half2 s0 = __hadd2(za0, zb0), s1 = __hadd2(za1, zb1), s2 = __hadd2(za2, zb2);
+    const __half2 s = __hfma2(r.h2, s2, __hfma2(r.h1, s1, __hmul2(r.h0, s0)));
+    const __half2 ns = __hneg2(s);
+    b0 = __hfma2(ns, r.h0, b0);
+    b1 = __hfma2(ns, r.h1, b1);
+    b2 = __hfma2(ns, r.h2, b2);
+}
+
+// Per-thread state of one node pair (one colour): the cell index (-1: no
+// pair), the scaled right-hand sides, the factors, the current values, and
+// the lambda weights of the E/W and N/S legs (1/2 lambda per triangle on the
+// leg: lambda on interior legs, lambda/2 along the image border).
+struct PairState {
+    int c;
+    int seam;  // 1: paired row HP-1 (writes the lane-A ghost), 2: paired row 0 (lane-B ghost)
+    __half2 b0, b1, b2;
+    BlkH2 B;
+    __half2 z0, z1, z2;
+    __half2 lew, lns;
+};
+
+// One relaxed block update of a node pair:
+//   x = D^{-1} (b - sum_K h_K (h_K . (z_j + z_k)) + sum_e w_e z_e),
+//   z <- z + omega (x - z),
+// the six elements as in node_sweep (E1 t0(x,y), E2 t1(x,y), E3 t0(x-1,y-1),
+// E4 t1(x-1,y-1), E5 t0(x-1,y), E6 t1(x,y-1)); records P0/P1 and values Z
+// share the cell index (row k = paired row k - 1).
+__device__ __forceinline__ void pair_update(const RecH2* __restrict__ P0, const RecH2* __restrict__ P1,
+                                            __half2* __restrict__ Z, int zp, int RW, int HPRW, __half2 om,
+                                            PairState& n) {
+    if (n.c < 0) return;
+    const int c = n.c;
+    const __half2* z0 = Z;
+    const __half2* z1 = Z + zp;
+    const __half2* z2 = Z + 2 * zp;
+    const int iE = c + 1, iW = c - 1, iN = c + RW, iS = c - RW, iNE = c + RW + 1, iSW = c - RW - 1;
+    const __half2 zE0 = z0[iE], zE1 = z1[iE], zE2 = z2[iE];
+    const __half2 zW0 = z0[iW], zW1 = z1[iW], zW2 = z2[iW];
+    const __half2 zN0 = z0[iN], zN1 = z1[iN], zN2 = z2[iN];
+    const __half2 zS0 = z0[iS], zS1 = z1[iS], zS2 = z2[iS];
+    const __half2 zNE0 = z0[iNE], zNE1 = z1[iNE], zNE2 = z2[iNE];
+    const __half2 zSW0 = z0[iSW], zSW1 = z1[iSW], zSW2 = z2[iSW];
+    __half2 b0 = n.b0, b1 = n.b1, b2 = n.b2;
+    const RecH2 e1 = P0[c], e2 = P1[c], e3 = P0[c - RW - 1], e4 = P1[c - RW - 1], e5 = P0[c - 1], e6 = P1[c - RW];
+    elem_h2(e1, zE0, zE1, zE2, zNE0, zNE1, zNE2, b0, b1, b2);
+    elem_h2(e2, zN0, zN1, zN2, zNE0, zNE1, zNE2, b0, b1, b2);
+    elem_h2(e3, zSW0, zSW1, zSW2, zS0, zS1, zS2, b0, b1, b2);
+    elem_h2(e4, zSW0, zSW1, zSW2, zW0, zW1, zW2, b0, b1, b2);
+    elem_h2(e5, zW0, zW1, zW2, zN0, zN1, zN2, b0, b1, b2);
+    elem_h2(e6, zS0, zS1, zS2, zE0, zE1, zE2, b0, b1, b2);
+    // alpha edge weights: n-E = w of t0(x,y), n-N = w of t1(x,y), n-W = w of
+    // t0(x-1,y), n-S = w of t1(x,y-1)
+    b0 = __hfma2(e1.w, zE0, __hfma2(e2.w, zN0, __hfma2(e5.w, zW0, __hfma2(e6.w, zS0, b0))));
+    b1 = __hfma2(e1.w, zE1, __hfma2(e2.w, zN1, __hfma2(e5.w, zW1, __hfma2(e6.w, zS1, b1))));
+    b2 = __hfma2(n.lew, __hadd2(zE2, zW2), __hfma2(n.lns, __hadd2(zN2, zS2), b2));
+    __half2 x0, x1, x2;
+    block_solve_h2(n.B, b0, b1, b2, x0, x1, x2);
+    n.z0 = __hfma2(om, __hsub2(x0, n.z0), n.z0);
+    n.z1 = __hfma2(om, __hsub2(x1, n.z1), n.z1);
+    n.z2 = __hfma2(om, __hsub2(x2, n.z2), n.z2);
+    Z[c] = n.z0;
+    Z[c + zp] = n.z1;
+    Z[c + 2 * zp] = n.z2;
+    if (n.seam) {
+        // the seam ghost (the other lane of the ghost word is the zero ring)
+        const __half zero = __float2half(0.f);
+        const int g = n.seam == 1 ? c - HPRW : c + HPRW;
+        auto gh = [&](__half2 v) {
+            return n.seam == 1 ? __halves2half2(zero, __low2half(v)) : __halves2half2(__high2half(v), zero);
+        };
+        Z[g] = gh(n.z0);
+        Z[g + zp] = gh(n.z1);
+        Z[g + 2 * zp] = gh(n.z2);
+    }
+}
+
+// Writes the paired values of a node pair (and their seam ghosts).
+__device__ __forceinline__ void pair_store(__half2* __restrict__ Z, int zp, int HPRW, int c, int seam, __half2 v0,
+                                           __half2 v1, __half2 v2) {
+    Z[c] = v0;
+    Z[c + zp] = v1;
+    Z[c + 2 * zp] = v2;
+    if (seam) {
+        const __half zero = __float2half(0.f);
+        const int g = seam == 1 ? c - HPRW : c + HPRW;
+        auto gh = [&](__half2 v) {
+            return seam == 1 ? __halves2half2(zero, __low2half(v)) : __halves2half2(__high2half(v), zero);
+        };
+        Z[g] = gh(v0);
+        Z[g + zp] = gh(v1);
+        Z[g + 2 * zp] = gh(v2);
+    }
+}
+
+// FP32 element data of one lane of a node pair: the six elements' h and the
+// four alpha edge weights.
+__device__ __forceinline__ void lane_records(const RecH2* P0, const RecH2* P1, int c, int RW, int L, float h[6][3],
+                                             float& wE, float& wN, float& wW, float& wS) {
+    const RecH2 r[6] = {P0[c], P1[c], P0[c - RW - 1], P1[c - RW - 1], P0[c - 1], P1[c - RW]};
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        h[e][0] = h_lane(r[e].h0, L);
+        h[e][1] = h_lane(r[e].h1, L);
+        h[e][2] = h_lane(r[e].h2, L);
+    }
+    wE = h_lane(r[0].w, L);
+    wN = h_lane(r[1].w, L);
+    wW = h_lane(r[4].w, L);
+    wS = h_lane(r[5].w, L);
+}
+
+template <int TXC, int TYC, int OVC>
+__global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ double sh_red[32];
+    __shared__ float sh_max[16];
+    __shared__ int sh_last, sh_fail;
+    const int NT = blockDim.x;
+    const int Tx = TXC ? TXC : P.Tx, Ty = TXC ? TYC : P.Ty, ov = TXC ? OVC : P.ov;
+    const int RW = sch_rw(Tx, ov), HP = h2_hp(Ty, ov), cpad = sch_cpad(ov);
+    const int nz = RW * (HP + 2), nr = RW * (HP + 1), HPRW = HP * RW;
+    const int nstage = P.nstage;
+    const H2Layout L = h2_layout(Tx, Ty, ov, nstage);
+    unsigned char* base = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bar);
+    __half2* Zs = reinterpret_cast<__half2*>(base + L.zs);
+    const unsigned box_rq = (unsigned)(3 * (size_t)Tx * Ty * sizeof(float));
+    const unsigned box_p = (unsigned)(nr * sizeof(RecH2));
+
+    if (threadIdx.x == 0) {
+        sh_fail = 0;
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    // the ring (and the other lane of each ghost word) is never written: the
+    // Dirichlet zeros of every item
+    for (int i = threadIdx.x; i < 3 * nz; i += NT) Zs[i] = __float2half2_rn(0.f);
+    __syncthreads();
+
+    auto issue = [&](const int4 ti, int s) {
+        const CUtensorMap* tm = P.tmaps + (size_t)ti.x * TM_PER_PAIR;
+        const int x0 = ti.y * Tx, y0 = ti.z * Ty;
+        const bool need_q = !P.first && !P.apply_only;
+        unsigned char* st = base + L.stage0 + (size_t)s * L.stage_bytes;
+        bulk_wait_read();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bars[s], 2 * box_p + box_rq + (need_q ? box_rq : 0u) + (unsigned)P.tx_extra);
+        // records as pairs of 8-byte units; row k of the plane is image row k - ov - 1
+        const int cx = (x0 - cpad) * 2, cy = y0;
+        tma_load_2d(st + L.p0, tm + TM_P0, cx, cy, &bars[s]);
+        tma_load_2d(st + L.p1, tm + TM_P1, cx, cy, &bars[s]);
+        tma_load_3d(st + L.rs, tm + TM_R, x0, y0, 0, &bars[s]);
+        if (need_q) tma_load_3d(st + L.qs, tm + TM_Q, x0, y0, 0, &bars[s]);
+    };
+    const int G = gridDim.x;
+    unsigned done_mask = 0u;
+    if (!P.apply_only && P.npairs <= 32) {
+        const int l = threadIdx.x & 31;
+        done_mask = __ballot_sync(0xffffffffu, l < P.npairs && P.sc[l].done != 0);
+    }
+    auto pair_done = [&](int pair) -> bool {
+        if (P.apply_only) return false;
+        if (P.npairs <= 32) return (done_mask >> pair) & 1u;
+        return P.sc[pair].done != 0;
+    };
+    auto advance = [&](int t, int4& ti) {
+        while (t < P.ntiles) {
+            ti = P.tiles[t];
+            if (!pair_done(ti.x)) return t;
+            t += G;
+        }
+        return t;
+    };
+    uint32_t tab[3];
+#pragma unroll
+    for (int col = 0; col < 3; ++col) tab[col] = P.ntab[col * NT + threadIdx.x];
+
+    int4 ti = make_int4(0, 0, 0, 0), tin = make_int4(0, 0, 0, 0);
+    int t = advance(blockIdx.x, ti);
+    int tn = (t < P.ntiles) ? advance(t + G, tin) : P.ntiles;
+    if (t < P.ntiles && threadIdx.x == 0) issue(ti, 0);
+    unsigned phase[2] = {0u, 0u};
+    int s = 0;
+    for (; t < P.ntiles;) {
+        const int tc = tn + G;
+        int4 tic = make_int4(0, 0, 0, 0);
+        if (tn < P.ntiles && tc < P.ntiles) tic = P.tiles[tc];
+        if (threadIdx.x == 0 && !mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit)) {
+            sh_fail = 1;
+            atomicOr(P.err, 1);
+        }
+        __syncthreads();
+        if (sh_fail) {
+            if (threadIdx.x == 0) mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit);
+            break;
+        }
+        if (!mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit)) atomicOr(P.err, 1);
+        phase[s] ^= 1u;
+        unsigned char* st = base + L.stage0 + (size_t)s * L.stage_bytes;
+        const RecH2* P0s = reinterpret_cast<const RecH2*>(st + L.p0);
+        const RecH2* P1s = reinterpret_cast<const RecH2*>(st + L.p1);
+        float* Rs = reinterpret_cast<float*>(st + L.rs);
+        const float* Qs = reinterpret_cast<const float*>(st + L.qs);
+        const int pair = ti.x;
+        const PairDesc pd = P.pairs[pair];
+        const int W = pd.W, H = pd.H;
+        const int x0 = ti.y * Tx, y0 = ti.z * Ty;
+        const int tw = min(Tx, W - x0), th = min(Ty, H - y0);
+        const int ex0 = max(x0 - ov, 0), ex1 = min(x0 + tw + ov, W);
+        const int ey0 = max(y0 - ov, 0), ey1 = min(y0 + th + ov, H);
+        const bool need_q = !P.first && !P.apply_only;
+        const float a = need_q ? (float)P.sc[pair].a : 0.f;
+        const float hl = 0.5f * (float)P.lam;
+        const float om = (float)P.omega;
+        const int plane = Tx * Ty;
+        // ---- setup in FP32: diagonal blocks, right-hand sides (r <- r - a q on
+        // the owned nodes), the first Jacobi step and its largest entry
+        float rr = 0.f, zmax = 0.f;
+        PairState ns[3];
+        float bf[3][2][3];
+        float xj[2][3];
+#pragma unroll
+        for (int col = 0; col < 3; ++col) {
+            PairState& n = ns[col];
+            const uint32_t e = tab[col];
+            n.c = -1;
+            n.seam = 0;
+            float fac[2][6], lewf[2] = {0.f, 0.f}, lnsf[2] = {0.f, 0.f};
+#pragma unroll
+            for (int Ln = 0; Ln < 2; ++Ln) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) fac[Ln][k] = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    bf[col][Ln][k] = 0.f;
+                    if (col == 0) xj[Ln][k] = 0.f;
+                }
+            }
+            if (e != 0xffffffffu) {
+                const int li = (int)(e & 0xffffu), lj = (int)(e >> 16);
+                const int c = (lj + 1) * RW + (li + cpad - ov);
+                n.c = c;
+                n.seam = (lj == HP - 1) ? 1 : (lj == 0 ? 2 : 0);
+#pragma unroll
+                for (int Ln = 0; Ln < 2; ++Ln) {
+                    const int gx = x0 - ov + li, gy = y0 - ov + lj + Ln * HP;
+                    if (gx < ex0 || gx >= ex1 || gy < ey0 || gy >= ey1) continue;  // clipped: stays zero
+                    float h[6][3], wE, wN, wW, wS;
+                    lane_records(P0s, P1s, c, RW, Ln, h, wE, wN, wW, wS);
+                    const int vc = (gx < W - 1 && gy < H - 1), vsw = (gx >= 1 && gy >= 1);
+                    const int vw = (gx >= 1 && gy < H - 1), vs = (gx < W - 1 && gy >= 1);
+                    const int legs = (vc + vs) + (vc + vw) + (vsw + vw) + (vsw + vs);
+                    float D00 = 0.f, D01 = 0.f, D02 = 0.f, D11 = 0.f, D12 = 0.f, D22 = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        D00 += 2.f * h[k][0] * h[k][0]; D01 += 2.f * h[k][0] * h[k][1];
+                        D02 += 2.f * h[k][0] * h[k][2]; D11 += 2.f * h[k][1] * h[k][1];
+                        D12 += 2.f * h[k][1] * h[k][2]; D22 += 2.f * h[k][2] * h[k][2];
+                    }
+                    const float ws = wE + wN + wW + wS;
+                    const Blk<float> B = ldl3<float>(D00 + ws, D01, D02, D11 + ws, D12, D22 + hl * (float)legs);
+                    fac[Ln][0] = B.i0; fac[Ln][1] = B.l10; fac[Ln][2] = B.l20;
+                    fac[Ln][3] = B.i1; fac[Ln][4] = B.l21; fac[Ln][5] = B.i2;
+                    lewf[Ln] = hl * ((gy == 0 || gy == H - 1) ? 1.f : 2.f);
+                    lnsf[Ln] = hl * ((gx == 0 || gx == W - 1) ? 1.f : 2.f);
+                    if (gx >= x0 && gx < x0 + tw && gy >= y0 && gy < y0 + th) {
+                        const int si = (gy - y0) * Tx + (gx - x0);
+                        float v0 = Rs[si], v1 = Rs[si + plane], v2 = Rs[si + 2 * plane];
+                        if (need_q) {
+                            v0 -= a * Qs[si];
+                            v1 -= a * Qs[si + plane];
+                            v2 -= a * Qs[si + 2 * plane];
+                            Rs[si] = v0;
+                            Rs[si + plane] = v1;
+                            Rs[si + 2 * plane] = v2;
+                        }
+                        bf[col][Ln][0] = v0;
+                        bf[col][Ln][1] = v1;
+                        bf[col][Ln][2] = v2;
+                        rr += v0 * v0 + v1 * v1 + v2 * v2;
+                        float q0, q1, q2;
+                        block_solve<float>(B, v0, v1, v2, q0, q1, q2);
+                        zmax = fmaxf(zmax, fmaxf(fabsf(q0), fmaxf(fabsf(q1), fabsf(q2))));
+                        if (col == 0) {
+                            xj[Ln][0] = q0;
+                            xj[Ln][1] = q1;
+                            xj[Ln][2] = q2;
+                        }
+                    }
+                }
+            }
+            n.B.i0 = __floats2half2_rn(fac[0][0], fac[1][0]);
+            n.B.l10 = __floats2half2_rn(fac[0][1], fac[1][1]);
+            n.B.l20 = __floats2half2_rn(fac[0][2], fac[1][2]);
+            n.B.i1 = __floats2half2_rn(fac[0][3], fac[1][3]);
+            n.B.l21 = __floats2half2_rn(fac[0][4], fac[1][4]);
+            n.B.i2 = __floats2half2_rn(fac[0][5], fac[1][5]);
+            n.lew = __floats2half2_rn(lewf[0], lewf[1]);
+            n.lns = __floats2half2_rn(lnsf[0], lnsf[1]);
+        }
+        // the tile's scale: the largest entry of the first Jacobi step
+        {
+            const float wm = warp_max(zmax);
+            if ((threadIdx.x & 31) == 0) sh_max[threadIdx.x >> 5] = wm;
+        }
+        __syncthreads();
+        float m = 0.f;
+        for (int w = 0; w < (NT >> 5); ++w) m = fmaxf(m, sh_max[w]);
+        const bool mok = m > 0.f && m <= 3.0e38f;  // false for 0, inf and NaN
+        const float scl = mok ? 1.f / m : 1.f, unscl = mok ? m : 1.f;
+        const float omj = P.sweeps > 0 ? om : 1.f;
+#pragma unroll
+        for (int col = 0; col < 3; ++col) {
+            PairState& n = ns[col];
+            n.b0 = __floats2half2_rn(bf[col][0][0] * scl, bf[col][1][0] * scl);
+            n.b1 = __floats2half2_rn(bf[col][0][1] * scl, bf[col][1][1] * scl);
+            n.b2 = __floats2half2_rn(bf[col][0][2] * scl, bf[col][1][2] * scl);
+            if (col == 0) {
+                // the first colour step from z = 0: (relaxed) block Jacobi
+                n.z0 = __floats2half2_rn(omj * xj[0][0] * scl, omj * xj[1][0] * scl);
+                n.z1 = __floats2half2_rn(omj * xj[0][1] * scl, omj * xj[1][1] * scl);
+                n.z2 = __floats2half2_rn(omj * xj[0][2] * scl, omj * xj[1][2] * scl);
+            } else {
+                n.z0 = n.z1 = n.z2 = __float2half2_rn(0.f);
+            }
+            if (n.c >= 0) pair_store(Zs, nz, HPRW, n.c, n.seam, n.z0, n.z1, n.z2);
+        }
+        __syncthreads();
+        if (nstage == 2 && tn < P.ntiles && threadIdx.x == 0) issue(tin, s ^ 1);
+
+        // ---- sweeps (colour order 0,1,2,1,0,...,0; the first 0 was the Jacobi
+        // step above); the last visit of each colour writes the owned z,
+        // scaled back, into this stage's q buffer and accumulates r.z in FP32
+        const __half2 om2 = __float2half2_rn(om);
+        float rz = 0.f;
+        float* zo = reinterpret_cast<float*>(st + L.qs);
+        auto emit = [&](const PairState& n) {
+            if (n.c < 0) return;
+            const int row = n.c / RW;
+            const int li = n.c - row * RW - cpad + ov, lj = row - 1;
+#pragma unroll
+            for (int Ln = 0; Ln < 2; ++Ln) {
+                const int ox = li - ov, oy = lj + Ln * HP - ov;
+                if (ox < 0 || ox >= tw || oy < 0 || oy >= th) continue;
+                const int si = oy * Tx + ox;
+                const float v0 = h_lane(n.z0, Ln) * unscl, v1 = h_lane(n.z1, Ln) * unscl,
+                            v2 = h_lane(n.z2, Ln) * unscl;
+                zo[si] = v0;
+                zo[si + plane] = v1;
+                zo[si + 2 * plane] = v2;
+                rz += Rs[si] * v0 + Rs[si + plane] * v1 + Rs[si + 2 * plane] * v2;
+            }
+        };
+#define OF_H2STEP(col, last)                                              \
+    {                                                                     \
+        pair_update(P0s, P1s, Zs, nz, RW, HPRW, om2, ns[col]);            \
+        if (last) emit(ns[col]);                                          \
+        __syncthreads();                                                  \
+    }
+        OF_H2STEP(1, false)
+        OF_H2STEP(2, P.sweeps == 1)
+        OF_H2STEP(1, P.sweeps == 1)
+        for (int sw = 1; sw < P.sweeps; ++sw) {
+            const bool lastsw = (sw == P.sweeps - 1);
+            OF_H2STEP(0, false)
+            OF_H2STEP(1, false)
+            OF_H2STEP(2, lastsw)
+            OF_H2STEP(1, lastsw)
+        }
+        OF_H2STEP(0, true)
+#undef OF_H2STEP
+
+        const float wrr = warp_sum(rr), wrz = warp_sum(rz);
+        if ((threadIdx.x & 31) == 0) {
+            sh_red[threadIdx.x >> 5] = (double)wrr;
+            sh_red[16 + (threadIdx.x >> 5)] = (double)wrz;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const CUtensorMap* tm = P.tmaps + (size_t)pair * TM_PER_PAIR;
+            tma_store_3d(tm + TM_Z, x0, y0, 0, zo);
+            if (need_q) tma_store_3d(tm + TM_R, x0, y0, 0, Rs);
+            bulk_commit();
+        }
+        if (!P.apply_only && threadIdx.x < 32) {
+            const int l = threadIdx.x;
+            const bool w = l < (NT >> 5);
+            const double a2 = warp_sum(w ? sh_red[l] : 0.0), b2 = warp_sum(w ? sh_red[16 + l] : 0.0);
+            if (l == 0) {
+                P.partial[2 * (long long)ti.w] = a2;
+                P.partial[2 * (long long)ti.w + 1] = b2;
+            }
+        }
+        __syncthreads();
+        t = tn;
+        ti = tin;
+        tn = tc;
+        tin = tic;
+        if (tn < P.ntiles && pair_done(tin.x)) tn = advance(tn + G, tin);
+        if (nstage == 2) s ^= 1;
+        else if (t < P.ntiles && threadIdx.x == 0) issue(ti, 0);
+    }
+    if (threadIdx.x == 0) bulk_wait_all();
+    if (P.apply_only || P.defer) return;
+    if (!arrive_last(P.counter, gridDim.x, &sh_last)) return;
+    for (int pi = 0; pi < P.npairs; ++pi) {
+        PairScalars* sp = P.sc + pi;
+        if (sp->done) continue;
+        const PairDesc pd = P.pairs[pi];
+        const int ntp = pd.tiles_x * pd.tiles_y;
+        const double t_rr = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0, ntp, 2, sh_red);
+        const double t_rz = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0 + 1, ntp, 2, sh_red);
+        if (threadIdx.x == 0) precond_finalize(sp, t_rr, t_rz, P.first);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (P.use_cond) {
+            int more = 0;
+            for (int pi = 0; pi < P.npairs; ++pi) more |= !P.sc[pi].done;
+            if (*(volatile int*)P.err) more = 0;
+            cudaGraphSetConditional(P.cond, more ? 1u : 0u);
+        }
+        __threadfence();
+        *P.counter = 0u;
+    }
+}
+
+}  // namespace ofk

@@ -36,7 +36,7 @@ class GridOpts(ctypes.Structure):
                 ("sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("lam", ctypes.c_double),
                 ("preconditioner", ctypes.c_int), ("omega", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("model", ctypes.c_int), ("coarse", ctypes.c_int), ("rho", ctypes.c_double),
-                ("schwarz", ctypes.c_int)]
+                ("schwarz", ctypes.c_int), ("half_sweeps", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -161,18 +161,21 @@ def of_create(device: int = 0, stream=None):
 
 
 def of_setup_grid(h, sizes, tile=(32, 32), overlap=0, sweeps=1, precision=OF_PREC_MIXED, lam=1.0,
-                  preconditioner=OF_PC_SCHWARZ, omega=1.0, sigma=0.0, model=0, coarse=0, rho=0.0, schwarz=0):
+                  preconditioner=OF_PC_SCHWARZ, omega=1.0, sigma=0.0, model=0, coarse=0, rho=0.0, schwarz=0,
+                  half_sweeps=0):
     """sizes: list of (W, H); omega: relaxation factor of the local block SOR
     sweeps, in (0, 2); sigma: K_sigma pre-smoothing of the frames (0: none);
     model: OF_MODEL_ILLUMINATION or OF_MODEL_CONSTANT; coarse: spacing of the
     two-level preconditioner's coarse grid in nodes (0: one level); rho: K_rho
     integration scale of the data term (0: none); schwarz: 1 makes of_solve
-    run the stationary Schwarz iteration instead of the PCG."""
+    run the stationary Schwarz iteration instead of the PCG; half_sweeps:
+    FP16 paired local sweeps on the mixed path (0: where the tile allows, 1:
+    required, -1: off)."""
     n = len(sizes)
     Wa = (ctypes.c_int32 * n)(*[int(w) for w, _ in sizes])
     Ha = (ctypes.c_int32 * n)(*[int(hh) for _, hh in sizes])
     o = GridOpts(int(tile[0]), int(tile[1]), int(overlap), int(sweeps), int(precision), float(lam), int(preconditioner),
-                 float(omega), float(sigma), int(model), int(coarse), float(rho), int(schwarz))
+                 float(omega), float(sigma), int(model), int(coarse), float(rho), int(schwarz), int(half_sweeps))
     return _check(h, _lib.of_setup_grid(h, n, Wa, Ha, ctypes.byref(o)))
 
 

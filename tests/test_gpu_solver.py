@@ -172,19 +172,23 @@ def test_schwarz_preconditioner_matches_oracle_fp64(S, oracle, tile, ov, sw, om)
     assert err <= 1e-11, err
 
 
-def test_schwarz_preconditioner_matches_oracle_mixed(S, oracle):
-    """FP32 path (element records rounded to FP16, FP32 sweeps): the same
-    preconditioner up to the records' rounding.  A relative perturbation e of
-    the local operator moves z by about cond * e; with e ~ 2^-11 the bound
-    used here is 2 % of max |z|, far below what a wrong colour, sign or
-    neighbour would give (O(1))."""
+@pytest.mark.parametrize("half", [-1, 1])
+def test_schwarz_preconditioner_matches_oracle_mixed(S, oracle, half):
+    """FP32 path (element records rounded to FP16; sweeps in FP32, half = -1,
+    or in packed FP16 on node pairs, half = 1): the same preconditioner up to
+    rounding.  A relative perturbation e of the local operator or of the
+    iterates moves z by about cond * e; with e ~ 2^-11 (FP16 records, and in
+    the packed form the FP16 iterates) the bound used here is 2 % of max |z|,
+    far below what a wrong colour, sign, neighbour or seam row would give
+    (O(1)).  130 x 100 with 48 x 48 tiles also clips tiles on both sides."""
     W, H = 130, 100
     f1, f2 = synth.random_frames(W, H, 23)
     f1, f2 = f32(f1), f32(f2)
     alpha = f32(synth.random_alpha(W, H, 24))
     sysm = oracle.System.from_frames(f1, f2, alpha, 1.0)
     r = f32(np.random.default_rng(5).standard_normal((3, H, W)))
-    h = handle(S, [(W, H)], tile=(48, 48), overlap=0, sweeps=4, precision=S.OF_PREC_MIXED, omega=1.6)
+    h = handle(S, [(W, H)], tile=(48, 48), overlap=0, sweeps=4, precision=S.OF_PREC_MIXED, omega=1.6,
+               half_sweeps=half)
     try:
         S.of_set_frames(h, 0, dev(f1, torch.float32), dev(f2, torch.float32))
         S.of_set_alpha(h, 0, dev(alpha, torch.float32))
@@ -196,6 +200,42 @@ def test_schwarz_preconditioner_matches_oracle_mixed(S, oracle):
     want = sysm.schwarz_sweeps(r, (48, 48), 0, 4, 1.6)
     err = np.abs(z - want).max() / np.abs(want).max()
     assert err <= 2e-2, err
+
+
+def test_fp16_paired_sweeps_solve_like_fp32(S, oracle):
+    """Mixed solves of a 640x480 texture with 48x48 tiles (four sweeps,
+    omega 1.6): FP16 paired sweeps and FP32 sweeps both reach the oracle's
+    residual 1e-6 with flows within 1e-4 px of the oracle's solution, the
+    FP16 form in at most 10 % more PCG iterations; a tile that cannot be
+    paired is refused when the FP16 form is required."""
+    p = synth.texture()
+    f1, f2 = f32(p.f1), f32(p.f2)
+    sysm = oracle.System.from_frames(f1, f2, p.alpha0, p.lam)
+    Uo, _, _ = sysm.solve_pcg(tol=1e-12)
+    its = {}
+    for half in (-1, 1):
+        h = handle(S, [(p.W, p.H)], tile=(48, 48), overlap=0, sweeps=4, omega=1.6, precision=S.OF_PREC_MIXED,
+                   half_sweeps=half)
+        try:
+            S.of_set_frames(h, 0, dev(p.f1, torch.float32), dev(p.f2, torch.float32))
+            S.of_set_alpha(h, 0, None, p.alpha0)
+            U = torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda")
+            st, info = S.of_solve(h, [U], rtol=1e-6)
+            U = U.cpu().numpy()
+        finally:
+            S.of_destroy(h)
+        assert sysm.rel_residual(U) <= 1e-6
+        assert np.abs(U[:2] - Uo[:2]).max() <= 1e-4
+        its[half] = info[0]["inner_iters"]
+    assert its[1] <= 1.1 * its[-1] + 1, its
+    h = S.of_create(0)
+    try:
+        for tile, half in (((32, 32), 1), ((48, 48), 2)):
+            with pytest.raises(S.OFError) as e:
+                S.of_setup_grid(h, [(100, 80)], tile=tile, sweeps=2, precision=S.OF_PREC_MIXED, half_sweeps=half)
+            assert e.value.status == S.OF_ERR_ARG
+    finally:
+        S.of_destroy(h)
 
 
 @pytest.mark.parametrize("prec,tile,sw,om,spacing", [(0, (16, 12), 2, 1.6, 8), (0, (16, 16), 1, 1.0, 20),
