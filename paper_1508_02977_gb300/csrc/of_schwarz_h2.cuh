@@ -37,7 +37,7 @@ namespace ofk {
 
 // paired element record of one square: (h0, h1, h2, w) of the top node's
 // square (lane A) and of the square HP rows below it (lane B)
-struct RecH2 {
+struct __align__(16) RecH2 {
     __half2 h0, h1, h2, w;
 };
 
@@ -123,11 +123,12 @@ struct PairState {
 //   x = D^{-1} (b - sum_K h_K (h_K . (z_j + z_k)) + sum_e w_e z_e),
 //   z <- z + omega (x - z),
 // the six elements as in node_sweep (E1 t0(x,y), E2 t1(x,y), E3 t0(x-1,y-1),
-// E4 t1(x-1,y-1), E5 t0(x-1,y), E6 t1(x,y-1)); records P0/P1 and values Z
-// share the cell index (row k = paired row k - 1).
-__device__ __forceinline__ void pair_update(const RecH2* __restrict__ P0, const RecH2* __restrict__ P1,
-                                            __half2* __restrict__ Z, int zp, int RW, int HPRW, __half2 om,
-                                            PairState& n) {
+// E4 t1(x-1,y-1), E5 t0(x-1,y), E6 t1(x,y-1)), their paired records in e[];
+// the values Z are indexed by the cell (row k = paired row k - 1).  The sums
+// run in two independent chains (elements 1, 3, 5 and the E, W legs;
+// elements 2, 4, 6 and the N, S legs) that are added at the end.
+__device__ __forceinline__ void pair_update(const RecH2 (&e)[6], __half2* __restrict__ Z, int zp, int RW, int HPRW,
+                                            __half2 om, PairState& n) {
     if (n.c < 0) return;
     const int c = n.c;
     const __half2* z0 = Z;
@@ -140,21 +141,33 @@ __device__ __forceinline__ void pair_update(const RecH2* __restrict__ P0, const 
     const __half2 zS0 = z0[iS], zS1 = z1[iS], zS2 = z2[iS];
     const __half2 zNE0 = z0[iNE], zNE1 = z1[iNE], zNE2 = z2[iNE];
     const __half2 zSW0 = z0[iSW], zSW1 = z1[iSW], zSW2 = z2[iSW];
-    __half2 b0 = n.b0, b1 = n.b1, b2 = n.b2;
-    const RecH2 e1 = P0[c], e2 = P1[c], e3 = P0[c - RW - 1], e4 = P1[c - RW - 1], e5 = P0[c - 1], e6 = P1[c - RW];
-    elem_h2(e1, zE0, zE1, zE2, zNE0, zNE1, zNE2, b0, b1, b2);
-    elem_h2(e2, zN0, zN1, zN2, zNE0, zNE1, zNE2, b0, b1, b2);
-    elem_h2(e3, zSW0, zSW1, zSW2, zS0, zS1, zS2, b0, b1, b2);
-    elem_h2(e4, zSW0, zSW1, zSW2, zW0, zW1, zW2, b0, b1, b2);
-    elem_h2(e5, zW0, zW1, zW2, zN0, zN1, zN2, b0, b1, b2);
-    elem_h2(e6, zS0, zS1, zS2, zE0, zE1, zE2, b0, b1, b2);
+    // -h . (z_j + z_k) of each element
+    auto dotn = [](const RecH2& r, __half2 a0, __half2 a1, __half2 a2, __half2 c0, __half2 c1, __half2 c2) {
+        const __half2 s = __hfma2(r.h2, __hadd2(a2, c2), __hfma2(r.h1, __hadd2(a1, c1), __hmul2(r.h0, __hadd2(a0, c0))));
+        return __hneg2(s);
+    };
+    const __half2 s1 = dotn(e[0], zE0, zE1, zE2, zNE0, zNE1, zNE2);
+    const __half2 s2 = dotn(e[1], zN0, zN1, zN2, zNE0, zNE1, zNE2);
+    const __half2 s3 = dotn(e[2], zSW0, zSW1, zSW2, zS0, zS1, zS2);
+    const __half2 s4 = dotn(e[3], zSW0, zSW1, zSW2, zW0, zW1, zW2);
+    const __half2 s5 = dotn(e[4], zW0, zW1, zW2, zN0, zN1, zN2);
+    const __half2 s6 = dotn(e[5], zS0, zS1, zS2, zE0, zE1, zE2);
     // alpha edge weights: n-E = w of t0(x,y), n-N = w of t1(x,y), n-W = w of
     // t0(x-1,y), n-S = w of t1(x,y-1)
-    b0 = __hfma2(e1.w, zE0, __hfma2(e2.w, zN0, __hfma2(e5.w, zW0, __hfma2(e6.w, zS0, b0))));
-    b1 = __hfma2(e1.w, zE1, __hfma2(e2.w, zN1, __hfma2(e5.w, zW1, __hfma2(e6.w, zS1, b1))));
-    b2 = __hfma2(n.lew, __hadd2(zE2, zW2), __hfma2(n.lns, __hadd2(zN2, zS2), b2));
+    __half2 a0 = __hfma2(s5, e[4].h0, __hfma2(s3, e[2].h0, __hfma2(s1, e[0].h0, n.b0)));
+    __half2 a1 = __hfma2(s5, e[4].h1, __hfma2(s3, e[2].h1, __hfma2(s1, e[0].h1, n.b1)));
+    __half2 a2 = __hfma2(s5, e[4].h2, __hfma2(s3, e[2].h2, __hfma2(s1, e[0].h2, n.b2)));
+    __half2 c0 = __hfma2(s6, e[5].h0, __hfma2(s4, e[3].h0, __hmul2(s2, e[1].h0)));
+    __half2 c1 = __hfma2(s6, e[5].h1, __hfma2(s4, e[3].h1, __hmul2(s2, e[1].h1)));
+    __half2 c2 = __hfma2(s6, e[5].h2, __hfma2(s4, e[3].h2, __hmul2(s2, e[1].h2)));
+    a0 = __hfma2(e[0].w, zE0, __hfma2(e[4].w, zW0, a0));
+    a1 = __hfma2(e[0].w, zE1, __hfma2(e[4].w, zW1, a1));
+    a2 = __hfma2(n.lew, __hadd2(zE2, zW2), a2);
+    c0 = __hfma2(e[1].w, zN0, __hfma2(e[5].w, zS0, c0));
+    c1 = __hfma2(e[1].w, zN1, __hfma2(e[5].w, zS1, c1));
+    c2 = __hfma2(n.lns, __hadd2(zN2, zS2), c2);
     __half2 x0, x1, x2;
-    block_solve_h2(n.B, b0, b1, b2, x0, x1, x2);
+    block_solve_h2(n.B, __hadd2(a0, c0), __hadd2(a1, c1), __hadd2(a2, c2), x0, x1, x2);
     n.z0 = __hfma2(om, __hsub2(x0, n.z0), n.z0);
     n.z1 = __hfma2(om, __hsub2(x1, n.z1), n.z1);
     n.z2 = __hfma2(om, __hsub2(x2, n.z2), n.z2);
@@ -172,6 +185,17 @@ __device__ __forceinline__ void pair_update(const RecH2* __restrict__ P0, const 
         Z[g + zp] = gh(n.z1);
         Z[g + 2 * zp] = gh(n.z2);
     }
+}
+
+// The six paired records (E1..E6) of the node pair at cell c.
+__device__ __forceinline__ void pair_records(const RecH2* __restrict__ P0, const RecH2* __restrict__ P1, int c,
+                                             int RW, RecH2 (&e)[6]) {
+    e[0] = P0[c];
+    e[1] = P1[c];
+    e[2] = P0[c - RW - 1];
+    e[3] = P1[c - RW - 1];
+    e[4] = P0[c - 1];
+    e[5] = P1[c - RW];
 }
 
 // Writes the paired values of a node pair (and their seam ghosts).
@@ -192,11 +216,10 @@ __device__ __forceinline__ void pair_store(__half2* __restrict__ Z, int zp, int 
     }
 }
 
-// FP32 element data of one lane of a node pair: the six elements' h and the
-// four alpha edge weights.
-__device__ __forceinline__ void lane_records(const RecH2* P0, const RecH2* P1, int c, int RW, int L, float h[6][3],
-                                             float& wE, float& wN, float& wW, float& wS) {
-    const RecH2 r[6] = {P0[c], P1[c], P0[c - RW - 1], P1[c - RW - 1], P0[c - 1], P1[c - RW]};
+// FP32 element data of one lane of a node pair from its six paired records
+// (E1..E6): the elements' h and the four alpha edge weights.
+__device__ __forceinline__ void lane_records(const RecH2 r[6], int L, float h[6][3], float& wE, float& wN,
+                                             float& wW, float& wS) {
 #pragma unroll
     for (int e = 0; e < 6; ++e) {
         h[e][0] = h_lane(r[e].h0, L);
@@ -318,6 +341,7 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
         // the owned nodes), the first Jacobi step and its largest entry
         float rr = 0.f, zmax = 0.f;
         PairState ns[3];
+        RecH2 rec1[6];
         float bf[3][2][3];
         float xj[2][3];
 #pragma unroll
@@ -342,12 +366,18 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
                 const int c = (lj + 1) * RW + (li + cpad - ov);
                 n.c = c;
                 n.seam = (lj == HP - 1) ? 1 : (lj == 0 ? 2 : 0);
+                RecH2 rec[6];
+                pair_records(P0s, P1s, c, RW, rec);
+                if (col == 1) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) rec1[k] = rec[k];  // colour 1 (half the visits) keeps its records
+                }
 #pragma unroll
                 for (int Ln = 0; Ln < 2; ++Ln) {
                     const int gx = x0 - ov + li, gy = y0 - ov + lj + Ln * HP;
                     if (gx < ex0 || gx >= ex1 || gy < ey0 || gy >= ey1) continue;  // clipped: stays zero
                     float h[6][3], wE, wN, wW, wS;
-                    lane_records(P0s, P1s, c, RW, Ln, h, wE, wN, wW, wS);
+                    lane_records(rec, Ln, h, wE, wN, wW, wS);
                     const int vc = (gx < W - 1 && gy < H - 1), vsw = (gx >= 1 && gy >= 1);
                     const int vw = (gx >= 1 && gy < H - 1), vs = (gx < W - 1 && gy >= 1);
                     const int legs = (vc + vs) + (vc + vw) + (vsw + vw) + (vsw + vs);
@@ -452,11 +482,18 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
                 rz += Rs[si] * v0 + Rs[si + plane] * v1 + Rs[si + 2 * plane] * v2;
             }
         };
-#define OF_H2STEP(col, last)                                              \
-    {                                                                     \
-        pair_update(P0s, P1s, Zs, nz, RW, HPRW, om2, ns[col]);            \
-        if (last) emit(ns[col]);                                          \
-        __syncthreads();                                                  \
+// colour 1 (half of all visits) keeps its records in registers (set up above)
+#define OF_H2STEP(col, last)                                                  \
+    {                                                                         \
+        if (col == 1) {                                                       \
+            pair_update(rec1, Zs, nz, RW, HPRW, om2, ns[1]);                  \
+        } else if (ns[col].c >= 0) {                                          \
+            RecH2 e_[6];                                                      \
+            pair_records(P0s, P1s, ns[col].c, RW, e_);                        \
+            pair_update(e_, Zs, nz, RW, HPRW, om2, ns[col]);                  \
+        }                                                                     \
+        if (last) emit(ns[col]);                                              \
+        __syncthreads();                                                      \
     }
         OF_H2STEP(1, false)
         OF_H2STEP(2, P.sweeps == 1)
