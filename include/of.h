@@ -39,7 +39,11 @@
  *
  * Errors: every entry point returns an of_status; no entry point aborts,
  * traps or prints.  of_last_error gives a message for the last non-OK status
- * of a handle.  A CUDA error inside a call returns OF_ERR_CUDA.
+ * of a handle.  A CUDA error inside a call returns OF_ERR_CUDA.  A build of
+ * the library compiled with -DOF_BOUNDS_CHECK checks the device indices of
+ * its kernels against their buffers; a violation skips the access, sets a
+ * bit of the device error word, and the entry point returns OF_ERR_CUDA
+ * ("a device index check failed").
  */
 #ifndef OF_H_
 #define OF_H_

@@ -140,6 +140,14 @@ of_status read_scalars(of_ctx* h, cudaStream_t st, int* errw) {
     return OF_OK;
 }
 
+// Status of a nonzero device error word: bit 0 a bounded wait ran out, bit 2
+// a device index check failed (bounds-check build only).
+of_status err_status(of_ctx* h, int errw) {
+    if (errw & ofk::OF_ERR_BIT_BOUNDS)
+        return fail(h, OF_ERR_CUDA, "a device index check failed (library built with OF_BOUNDS_CHECK)");
+    return fail(h, OF_ERR_TIMEOUT, "a bounded device wait (TMA staging) ran out");
+}
+
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -604,7 +612,7 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
     }
     *cur_out = cur;
     prof_flush(h);
-    if (errw) return fail(h, OF_ERR_TIMEOUT, "a bounded device wait (TMA staging) ran out");
+    if (errw) return err_status(h, errw);
     return OF_OK;
 }
 
@@ -647,6 +655,7 @@ of_status run_ras(of_ctx* h, const of_solve_opts& o, int* cur_out, std::vector<i
     }
     *cur_out = cur;
     prof_flush(h);
+    if (errw) return err_status(h, errw);
     return OF_OK;
 }
 
@@ -1380,6 +1389,7 @@ of_status of_apply(of_handle h, int pair, const void* p, void* q, void* b, of_dt
     s = copy_in(h, p, dt, d.W, zin, d.pitch, 3LL * d.H, d.W);
     if (s != OF_OK) return s;
     ofl::SolveBufs B = solve_bufs(h);
+    CK(cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
     CK(ofl::launch_apply(B, pair, h->blk0[pair], h->nblk[pair], h->z, h->q, b ? h->d : nullptr, h->stream));
     s = copy_out(h, (char*)h->q + d.vec_off * es, wt, d.pitch, q, dt, 3LL * d.H, d.W);
     if (s != OF_OK) return s;
@@ -1387,7 +1397,10 @@ of_status of_apply(of_handle h, int pair, const void* p, void* q, void* b, of_dt
         s = copy_out(h, (char*)h->d + d.vec_off * es, wt, d.pitch, b, dt, 3LL * d.H, d.W);
         if (s != OF_OK) return s;
     }
-    CK(cudaStreamSynchronize(h->stream));
+    int errw = 0;
+    s = read_scalars(h, h->stream, &errw);
+    if (s != OF_OK) return s;
+    if (errw) return err_status(h, errw);
     return OF_OK;
 }
 
@@ -1411,7 +1424,7 @@ of_status of_precondition(of_handle h, int pair, const void* r, void* z, of_dtyp
     int errw = 0;
     s = read_scalars(h, h->stream, &errw);
     if (s != OF_OK) return s;
-    if (errw) return fail(h, OF_ERR_TIMEOUT, "a bounded device wait (TMA staging) ran out");
+    if (errw) return err_status(h, errw);
     return OF_OK;
 }
 

@@ -187,6 +187,7 @@ struct ApplyParams {
     int first;          // RES: first residual of a solve (no correction, ||b|| formed)
     double rtol, inner_rtol, pass_frac;
     int max_inner;
+    int* err;           // device error word (index checks of the bounds-check build)
 };
 
 template <typename R, typename C, typename RI, int MODE, bool WANT_B, int NW, typename T = R, bool ELD = false>
@@ -253,7 +254,8 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
     // update; side effects (p_new, d, x_new) only for owned nodes
     auto load = [&](int x, int y, bool owner) -> NodeVal<T> {
         NodeVal<T> v;
-        const bool in = (x >= 0) && (x < W) && (y >= 0) && (y < H);
+        const bool in = (x >= 0) && (x < W) && (y >= 0) && (y < H) &&
+                        OF_CHECK(P.err, (long long)y * pitch + x, plane);
         if (!in) { v.p = v3(zero, zero, zero); v.f1 = zero; v.f2 = zero; return v; }
         const long long o = (long long)y * pitch + x;
         if constexpr (ELD) {
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
         V3<T> resb = v3(zero, zero, zero);
         constexpr bool NEED_B = WANT_B || IS_RES;
         if constexpr (NEED_B) resb = carry_b + bB + shfl_down3(bA);
-        if (sy >= Y0 && out_col) {
+        if (sy >= Y0 && out_col && OF_CHECK(P.err, (long long)sy * pitch + (cx + 1), plane)) {
             const long long o = (long long)sy * pitch + (cx + 1);
             if constexpr (MODE == MODE_APPLY || MODE == MODE_PCG) {
                 R* q = P.out + vo;
@@ -565,7 +567,7 @@ __global__ void __launch_bounds__(32) k_apply4(const ApplyParams<float, float, f
     // node row j (y = Y0 - 1 + j) and square row y of alpha into stage j mod 3
     auto issue = [&](int j) {
         const int s = j % A4_NS, y = Y0 - 1 + j;
-        const bool rv = y >= 0 && y < H && c0 >= 0 && c0 < W;
+        const bool rv = y >= 0 && y < H && c0 >= 0 && c0 < W && OF_CHECK(P.err, (long long)y * pitch + c0 + 3, plane);
         const long long o = rv ? (long long)y * pitch + c0 : 0;
         cp_async16(slot(s, A4_F1), f1 + o, rv);
         cp_async16(slot(s, A4_F2), f2 + o, rv);
@@ -583,14 +585,15 @@ __global__ void __launch_bounds__(32) k_apply4(const ApplyParams<float, float, f
             }
         }
         if (j < nrows - 1) {  // square row y is used
-            const bool av = y >= 0 && y < H - 1 && c0 >= 0 && c0 < W - 1;
+            const bool av = y >= 0 && y < H - 1 && c0 >= 0 && c0 < W - 1 &&
+                            OF_CHECK(P.err, 2 * ((long long)y * pitch + c0) + 7, 2 * plane);
             const long long oa = av ? 2 * ((long long)y * pitch + c0) : 0;
             cp_async16(slot(s, A4_AL0), al + oa, av);
             cp_async16(slot(s, A4_AL1), al + oa + 4, av);
         }
         if (lane == 31) {
             const int x = c0 + 4;
-            const bool ev = y >= 0 && y < H && x < W;
+            const bool ev = y >= 0 && y < H && x < W && OF_CHECK(P.err, (long long)y * pitch + x, plane);
             const long long oe = ev ? (long long)y * pitch + x : 0;
             float* e = extra + s * A4_EXTRA;
             cp_async4(e + 0, f1 + oe, ev);
@@ -625,7 +628,7 @@ __global__ void __launch_bounds__(32) k_apply4(const ApplyParams<float, float, f
         a = mask4(a, c0, W);
         b = mask4(b, c0, W);
         c = mask4(c, c0, W);
-        if (MODE == MODE_PCG && own && y >= Y0 && y < Y1) {
+        if (MODE == MODE_PCG && own && y >= Y0 && y < Y1 && OF_CHECK(P.err, (long long)y * pitch + c0 + 3, plane)) {
             const long long o = (long long)y * pitch + c0;
             if (use_q) {
                 *reinterpret_cast<float4*>(dcor + o) = fma4(a_prev, qa, *slot(s, A4_D0));
@@ -706,7 +709,7 @@ __global__ void __launch_bounds__(32) k_apply4(const ApplyParams<float, float, f
             out[0] = carry[0] + cA[0] + pB;
 #pragma unroll
             for (int k = 1; k < 4; ++k) out[k] = carry[k] + cA[k] + cB[k - 1];
-            if (sy >= Y0 && own) {
+            if (sy >= Y0 && own && OF_CHECK(P.err, (long long)sy * pitch + c0 + 3, plane)) {
                 const long long o = (long long)sy * pitch + c0;
                 float* q = P.out + vo;
                 *reinterpret_cast<float4*>(q + o) = make_float4(out[0].a, out[1].a, out[2].a, out[3].a);

@@ -52,6 +52,23 @@ struct PairScalars {
 
 #define OF_STIFF_HALF 0.5   // |K| * |grad phi|^2 weight of a triangle leg
 
+// Device index checks, compiled in with -DOF_BOUNDS_CHECK (a separate build of
+// the library that the tests run): an index outside [0, n) sets bit 2 of the
+// device error word and the access it guards is skipped (no trap); the entry
+// point then returns OF_ERR_CUDA.  Without the flag a check is the constant
+// true and costs nothing.
+constexpr int OF_ERR_BIT_BOUNDS = 4;
+#ifdef OF_BOUNDS_CHECK
+__device__ __forceinline__ bool of_in_range(int* err, long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    if (err) atomicOr(err, OF_ERR_BIT_BOUNDS);
+    return false;
+}
+#define OF_CHECK(err, i, n) ofk::of_in_range((err), (long long)(i), (long long)(n))
+#else
+#define OF_CHECK(err, i, n) true
+#endif
+
 template <typename T> __device__ __forceinline__ T ld_or0(const T* p, bool ok) { return ok ? *p : T(0); }
 
 __device__ __forceinline__ float shfl_down(float v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }

@@ -83,6 +83,7 @@ static ApplyParams<R, C, RI> base_params(const SolveBufs& B) {
     P.eld = (const C*)B.eld;
     P.eld_stride = B.eld_stride;
     P.rows_per_block = B.rows_per_block;
+    P.err = B.err;
     return P;
 }
 
@@ -255,13 +256,15 @@ using namespace ofk;
 // (rec(x, y), rec(x, y + HP)) (see RecH2), each half zero where its row lies
 // outside the image.
 __global__ void k_cells_h2(const PairDesc* pairs, int pair, int HP, int R, const uint2* __restrict__ c0a,
-                           const uint2* __restrict__ c1a, uint4* __restrict__ p0a, uint4* __restrict__ p1a) {
+                           const uint2* __restrict__ c1a, uint4* __restrict__ p0a, uint4* __restrict__ p1a, int* err) {
     const PairDesc pd = pairs[pair];
     const int x = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
     if (x >= pd.W) return;
     const int y = k - R;
     const long long o = pd.frame_off + (long long)y * pd.pitch + x;
-    const bool has_a = y >= 0 && y < pd.H, has_b = y + HP >= 0 && y + HP < pd.H;
+    const long long plane = (long long)pd.H * pd.pitch, lo = (long long)y * pd.pitch + x;
+    const bool has_a = y >= 0 && y < pd.H && OF_CHECK(err, lo, plane);
+    const bool has_b = y + HP >= 0 && y + HP < pd.H && OF_CHECK(err, lo + (long long)HP * pd.pitch, plane);
     const long long ob = o + (long long)HP * pd.pitch;
     // record words: x = (h0, h1), y = (h2, w); pair the low and the high halves
     auto pack = [](uint2 a, uint2 b) {
@@ -269,6 +272,7 @@ __global__ void k_cells_h2(const PairDesc* pairs, int pair, int HP, int R, const
                           __byte_perm(a.y, b.y, 0x5410), __byte_perm(a.y, b.y, 0x7632));
     };
     const uint2 zero = make_uint2(0u, 0u);
+    if (!OF_CHECK(err, (long long)k * pd.pitch + x, (long long)(pd.H + R) * pd.pitch)) return;
     const long long po = pd.pair_off + (long long)k * pd.pitch + x;
     p0a[po] = pack(has_a ? c0a[o] : zero, has_b ? c0a[ob] : zero);
     p1a[po] = pack(has_a ? c1a[o] : zero, has_b ? c1a[ob] : zero);
@@ -280,7 +284,7 @@ cudaError_t launch_cells(const SolveBufs& B, int pair, int W, int H, void* c0, v
     if (e != cudaSuccess || !B.h2) return e;
     dim3 grid((W + 127) / 128, H + B.ov + 1);
     k_cells_h2<<<grid, 128, 0, st>>>(B.pairs, pair, h2_hp(B.Ty, B.ov), B.ov + 1, (const uint2*)c0,
-                                     (const uint2*)c1, (uint4*)B.cp0, (uint4*)B.cp1);
+                                     (const uint2*)c1, (uint4*)B.cp0, (uint4*)B.cp1, B.err);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ struct RasParams {
     void* d;                   // out: owned part of the local corrections
     const PairScalars* sc;     // a pair with done set contributes d = 0
     double* partial;           // [ntiles]: ||d||^2 of the owned tile
+    int* err;                  // device error word (index checks of the bounds-check build)
     double lam, omega;
     int Tx, Ty, ov, sweeps;
 };
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_ras(cons
     for (int i = threadIdx.x; i < nc; i += NT) {
         const int cx = x0 - cpad + i % RW, cy = y0 - ov - 1 + i / RW;
         Rec a{}, b{};
-        if (!skip && cx >= 0 && cx < W && cy >= 0 && cy < H) {
+        if (!skip && cx >= 0 && cx < W && cy >= 0 && cy < H && OF_CHECK(P.err, (long long)cy * pitch + cx, plane)) {
             a = g0[(long long)cy * pitch + cx];
             b = g1[(long long)cy * pitch + cx];
         }
@@ -94,6 +95,9 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_ras(cons
             const int gx = x0 - ov + li, gy = y0 - ov + lj;
             const int c = (lj + 1) * RW + (li + cpad - ov);
             if (gx < ex0 || gx >= ex1 || gy < ey0 || gy >= ey1) continue;  // clipped: stays 0
+            if (!OF_CHECK(P.err, c - RW - 1, nc) || !OF_CHECK(P.err, c + RW + 1, nc) ||
+                !OF_CHECK(P.err, (long long)gy * pitch + gx, plane))
+                continue;
             const int vc = (gx < W - 1 && gy < H - 1), vsw = (gx >= 1 && gy >= 1);
             const int vw = (gx >= 1 && gy < H - 1), vs = (gx < W - 1 && gy >= 1);
             const int nE = vc + vs, nN = vc + vw, nW = vsw + vw, nS = vsw + vs;
@@ -143,6 +147,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_ras(cons
         const int gx = x0 + i % tw, gy = y0 + i / tw;
         const int c = (gy - y0 + ov + 1) * RW + (gx - x0 + cpad);
         const long long o = (long long)gy * pitch + gx;
+        if (!OF_CHECK(P.err, o, plane) || !OF_CHECK(P.err, c, nc)) continue;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const R v = skip ? R(0) : Zs[c + k * nc];
@@ -197,6 +202,7 @@ static cudaError_t ras_t(const SolveBufs& B, const void* c0, const void* c1, dou
     P.d = B.d;
     P.sc = B.sc;
     P.partial = B.partS;
+    P.err = B.err;
     P.lam = B.lam;
     P.omega = B.omega;
     P.Tx = B.Tx;

@@ -468,11 +468,13 @@ struct ZOut {
     R* zo;       // [3][Ty][Tx] tile of z
     int Tx, plane, tw, th, ov, cpad, RW;
     R rz;
+    int* err;
     __device__ __forceinline__ void emit(const NodeState<R>& n, R x0, R x1, R x2) {
         const int c = n.c & 0xffffff;
         const int row = c / RW;                      // lj + 1
         const int ox = c - row * RW - cpad, oy = row - 1 - ov;  // position in the owned tile
         if (ox < 0 || ox >= tw || oy < 0 || oy >= th) return;
+        if (!OF_CHECK(err, oy * Tx + ox, plane)) return;
         const int si = oy * Tx + ox;
         zo[si] = x0;
         zo[si + plane] = x1;
@@ -658,6 +660,9 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
                 const int li = (int)(e & 0xffffu), lj = (int)(e >> 16);
                 const int gx = x0 - ov + li, gy = y0 - ov + lj;
                 const int c = (lj + 1) * RW + (li + cpad - ov);
+                // every access of the node's sweeps lies in [c - RW - 1, c + RW + 1] of
+                // each z plane and of the record planes
+                if (!OF_CHECK(P.err, c - RW - 1, nc) || !OF_CHECK(P.err, c + RW + 1, nc)) continue;
                 if (gx < ex0 || gx >= ex1 || gy < ey0 || gy >= ey1) {
                     Zs[c] = R(0);
                     Zs[c + nc] = R(0);
@@ -670,7 +675,8 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
                 const int nE = vc + vs, nN = vc + vw, nW = vsw + vw, nS = vsw + vs;
                 n.c = c | (nE << 24) | (nN << 26) | (nW << 28) | (nS << 30);
                 node_block<R>(C, c, RW, hl * R(nE), hl * R(nN), hl * R(nW), hl * R(nS), n.B);
-                if (gx >= x0 && gx < x0 + tw && gy >= y0 && gy < y0 + th) {
+                if (gx >= x0 && gx < x0 + tw && gy >= y0 && gy < y0 + th &&
+                    OF_CHECK(P.err, (gy - y0) * Tx + (gx - x0), Tx * Ty)) {
                     const int si = (gy - y0) * Tx + (gx - x0);
                     R v0 = Rs[si], v1 = Rs[si + Tx * Ty], v2 = Rs[si + 2 * Tx * Ty];
                     if (need_q) {
@@ -709,6 +715,7 @@ __global__ void __launch_bounds__(sch_max_threads(sizeof(R) == 8), 1) k_schwarz(
         zout.cpad = cpad;
         zout.RW = RW;
         zout.rz = R(0);
+        zout.err = P.err;
 #define OF_STEP(col, FRESH, LAST)                                                 \
     {                                                                             \
         _Pragma("unroll") for (int k = 0; k < NPT; ++k)                           \

@@ -364,6 +364,12 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
             if (e != 0xffffffffu) {
                 const int li = (int)(e & 0xffffu), lj = (int)(e >> 16);
                 const int c = (lj + 1) * RW + (li + cpad - ov);
+                // the pair's z accesses lie in [c - RW - 1, c + RW + 1] of each plane,
+                // its ghost at c -+ HP RW, its records in [c - RW - 1, c]
+                if (!OF_CHECK(P.err, c - RW - 1, nr) || !OF_CHECK(P.err, c, nr) ||
+                    !OF_CHECK(P.err, c + RW + 1, nz) || (lj == HP - 1 && !OF_CHECK(P.err, c - HPRW, nz)) ||
+                    (lj == 0 && !OF_CHECK(P.err, c + HPRW, nz)))
+                    continue;
                 n.c = c;
                 n.seam = (lj == HP - 1) ? 1 : (lj == 0 ? 2 : 0);
                 RecH2 rec[6];
@@ -394,7 +400,8 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
                     fac[Ln][3] = B.i1; fac[Ln][4] = B.l21; fac[Ln][5] = B.i2;
                     lewf[Ln] = hl * ((gy == 0 || gy == H - 1) ? 1.f : 2.f);
                     lnsf[Ln] = hl * ((gx == 0 || gx == W - 1) ? 1.f : 2.f);
-                    if (gx >= x0 && gx < x0 + tw && gy >= y0 && gy < y0 + th) {
+                    if (gx >= x0 && gx < x0 + tw && gy >= y0 && gy < y0 + th &&
+                        OF_CHECK(P.err, (gy - y0) * Tx + (gx - x0), plane)) {
                         const int si = (gy - y0) * Tx + (gx - x0);
                         float v0 = Rs[si], v1 = Rs[si + plane], v2 = Rs[si + 2 * plane];
                         if (need_q) {
@@ -472,7 +479,7 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
 #pragma unroll
             for (int Ln = 0; Ln < 2; ++Ln) {
                 const int ox = li - ov, oy = lj + Ln * HP - ov;
-                if (ox < 0 || ox >= tw || oy < 0 || oy >= th) continue;
+                if (ox < 0 || ox >= tw || oy < 0 || oy >= th || !OF_CHECK(P.err, oy * Tx + ox, plane)) continue;
                 const int si = oy * Tx + ox;
                 const float v0 = h_lane(n.z0, Ln) * unscl, v1 = h_lane(n.z1, Ln) * unscl,
                             v2 = h_lane(n.z2, Ln) * unscl;

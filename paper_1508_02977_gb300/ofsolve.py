@@ -15,7 +15,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libof.so")
+# OFSOLVE_LIB selects another build of the same library (the bounds-check build)
+LIB_PATH = os.environ.get("OFSOLVE_LIB") or os.path.join(_HERE, "libof.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
