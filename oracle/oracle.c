@@ -199,9 +199,14 @@ static int csr_add(const int64_t *rowptr, const int64_t *col, double *val, int64
     return 1; /* entry not in the pattern: a bug, reported to the caller */
 }
 
-/* Element-by-element assembly of A (values on the pattern above) and b. */
+/* lambda of element e: the per-element field when given (Section 1: Lambda
+ * piecewise constant per element), else the constant */
+#define LAMBDA_OF(lamel, lambda, e) ((lamel) ? (lamel)[e] : (lambda))
+
+/* Element-by-element assembly of A (values on the pattern above) and b;
+ * lamel (may be NULL) is a per-element lambda [H-1][W-1][2]. */
 int orc_assemble(int W, int H, const double *g, const double *ft, const double *alpha, double lambda,
-                 const int64_t *rowptr, const int64_t *col, double *val, double *b)
+                 const double *lamel, const int64_t *rowptr, const int64_t *col, double *val, double *b)
 {
     long N = (long)W * H;
     memset(val, 0, sizeof(double) * rowptr[3 * N]);
@@ -216,7 +221,7 @@ int orc_assemble(int W, int H, const double *g, const double *ft, const double *
                 for (int t = 0; t < 2; t++) {
                     long e = elem_index(W, x, y, t);
                     double K[9][9], bK[9];
-                    element_matrix(t, &g[3 * e], ft[e], alpha[e], lambda, K, bK);
+                    element_matrix(t, &g[3 * e], ft[e], alpha[e], LAMBDA_OF(lamel, lambda, e), K, bK);
                     int vx[3], vy[3];
                     tri_vertices(x, y, t, vx, vy);
                     for (int i = 0; i < 3; i++)
@@ -236,7 +241,7 @@ int orc_assemble(int W, int H, const double *g, const double *ft, const double *
 /* Assembly with general element data (K_rho > 0): Ael [H-1][W-1][2][6],
  * Fel [H-1][W-1][2][3]; otherwise as orc_assemble. */
 int orc_assemble_el(int W, int H, const double *Ael, const double *Fel, const double *alpha, double lambda,
-                    const int64_t *rowptr, const int64_t *col, double *val, double *b)
+                    const double *lamel, const int64_t *rowptr, const int64_t *col, double *val, double *b)
 {
     long N = (long)W * H;
     memset(val, 0, sizeof(double) * rowptr[3 * N]);
@@ -249,7 +254,7 @@ int orc_assemble_el(int W, int H, const double *Ael, const double *Fel, const do
                 for (int t = 0; t < 2; t++) {
                     long e = elem_index(W, x, y, t);
                     double K[9][9], bK[9];
-                    element_matrix_el(t, &Ael[6 * e], &Fel[3 * e], alpha[e], lambda, K, bK);
+                    element_matrix_el(t, &Ael[6 * e], &Fel[3 * e], alpha[e], LAMBDA_OF(lamel, lambda, e), K, bK);
                     int vx[3], vy[3];
                     tri_vertices(x, y, t, vx, vy);
                     for (int i = 0; i < 3; i++)
@@ -280,7 +285,7 @@ void orc_csr_matvec(int64_t n, const int64_t *rowptr, const int64_t *col, const 
 /* y = A x and, if b != NULL, r = b - A x, formed element by element without
  * storing A (for grids too large for the CSR). */
 int orc_apply_elementwise(int W, int H, const double *g, const double *ft, const double *alpha, double lambda,
-                          const double *x, double *y, double *b)
+                          const double *lamel, const double *x, double *y, double *b)
 {
     long N = (long)W * H;
     memset(y, 0, sizeof(double) * 3 * N);
@@ -292,7 +297,7 @@ int orc_apply_elementwise(int W, int H, const double *g, const double *ft, const
                 for (int t = 0; t < 2; t++) {
                     long e = elem_index(W, xx, yy, t);
                     double K[9][9], bK[9];
-                    element_matrix(t, &g[3 * e], ft[e], alpha[e], lambda, K, bK);
+                    element_matrix(t, &g[3 * e], ft[e], alpha[e], LAMBDA_OF(lamel, lambda, e), K, bK);
                     int vx[3], vy[3];
                     tri_vertices(xx, yy, t, vx, vy);
                     double xl[9];
@@ -749,7 +754,7 @@ done:
  * norm.  L2(K) by the edge-midpoint rule (exact for the quadratic
  * integrand); the jump is constant on e. */
 static int indicator_impl(int W, int H, const double *g, const double *ft, const double *Ael, const double *Fel,
-                          const double *alpha, double lambda, const double *U, double *eta)
+                          const double *alpha, double lambda, const double *lamel, const double *U, double *eta)
 {
     long N = (long)W * H;
     /* per-element flux gradients */
@@ -780,7 +785,7 @@ static int indicator_impl(int W, int H, const double *g, const double *ft, const
             for (int t = 0; t < 2; t++) {
                 long e = elem_index(W, x, y, t);
                 const double *ge = g ? &g[3 * e] : NULL;
-                double lamK[3] = {alpha[e], alpha[e], lambda};
+                double lamK[3] = {alpha[e], alpha[e], LAMBDA_OF(lamel, lambda, e)};
                 int vx[3], vy[3];
                 tri_vertices(x, y, t, vx, vy);
                 /* interior term: integrate |Lambda^{-1/2} R|^2 over K by the
@@ -832,7 +837,7 @@ static int indicator_impl(int W, int H, const double *g, const double *ft, const
                         double out = 0.0, lamE = lamK[c];
                         if (nbr[k] >= 0) {
                             long o = nbr[k];
-                            double lamO = c < 2 ? alpha[o] : lambda;
+                            double lamO = c < 2 ? alpha[o] : LAMBDA_OF(lamel, lambda, o);
                             out = lamO * (grad[6 * o + 2 * c] * nx[k] + grad[6 * o + 2 * c + 1] * ny[k]);
                             lamE = lamO > lamE ? lamO : lamE;
                         }
@@ -849,17 +854,17 @@ static int indicator_impl(int W, int H, const double *g, const double *ft, const
 }
 
 int orc_indicator(int W, int H, const double *g, const double *ft, const double *alpha, double lambda,
-                  const double *U, double *eta)
+                  const double *lamel, const double *U, double *eta)
 {
-    return indicator_impl(W, H, g, ft, NULL, NULL, alpha, lambda, U, eta);
+    return indicator_impl(W, H, g, ft, NULL, NULL, alpha, lambda, lamel, U, eta);
 }
 
 /* The indicator with general element data (K_rho > 0): the interior
  * residual is F - A_rho U_h; the edge terms do not involve the data. */
 int orc_indicator_el(int W, int H, const double *Ael, const double *Fel, const double *alpha, double lambda,
-                     const double *U, double *eta)
+                     const double *lamel, const double *U, double *eta)
 {
-    return indicator_impl(W, H, NULL, NULL, Ael, Fel, alpha, lambda, U, eta);
+    return indicator_impl(W, H, NULL, NULL, Ael, Fel, alpha, lambda, lamel, U, eta);
 }
 
 /* alpha update of Section 2.3:
@@ -886,7 +891,8 @@ int orc_alpha_update(int64_t ne, const double *eta, double *alpha, double kappa,
  * Outputs dL/dalpha [H-1][W-1][2], dL/df2 and dL/df1 [H][W] (either may be
  * NULL).  Frames enter through g_K and ft_K (see orc_coefficients). */
 int orc_adjoint_grad(int W, int H, const double *f1, const double *f2, const double *alpha, double lambda,
-                     const double *U, const double *Lam, double *dalpha, double *df2, double *df1, int model)
+                     const double *U, const double *Lam, double *dalpha, double *df2, double *df1, double *dlam,
+                     int model)
 {
     /* model 1 (brightness constancy): the data term has no illumination
      * column, g = (f2_x, f2_y, 0), so f1 enters through f_t only */
@@ -925,6 +931,15 @@ int orc_adjoint_grad(int W, int H, const double *f1, const double *f2, const dou
                         s += lx * ux + ly * uy;
                     }
                     dalpha[e] = -KAREA * s;
+                }
+                /* per-element lambda: d/dlambda_K of Lam^T S_K U (the m component) */
+                if (dlam) {
+                    double lx = 0, ly = 0, ux = 0, uy = 0;
+                    for (int i = 0; i < 3; i++) {
+                        lx += l[i][2] * gx[i]; ly += l[i][2] * gy[i];
+                        ux += u[i][2] * gx[i]; uy += u[i][2] * gy[i];
+                    }
+                    dlam[e] = -KAREA * (lx * ux + ly * uy);
                 }
                 if (!df2 && !df1) continue;
                 /* data part E = |K|/12 sum_ij (1+d_ij) t_i s_j + |K|/3 ft sum_i t_i,

@@ -50,21 +50,22 @@ def _load():
         L.orc_csr_nnz.argtypes = [i32, i32]
         L.orc_csr_nnz.restype = i64
         L.orc_csr_pattern.argtypes = [i32, i32, _i64p, _i64p]
-        L.orc_assemble.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _i64p, _i64p, _f64p, _f64p]
-        L.orc_assemble_el.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _i64p, _i64p, _f64p, _f64p]
+        vp = ctypes.c_void_p
+        L.orc_assemble.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, vp, _i64p, _i64p, _f64p, _f64p]
+        L.orc_assemble_el.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, vp, _i64p, _i64p, _f64p, _f64p]
         L.orc_csr_matvec.argtypes = [i64, _i64p, _i64p, _f64p, _f64p, _f64p]
         L.orc_csr_matvec.restype = None
-        L.orc_apply_elementwise.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p, ctypes.c_void_p]
+        L.orc_apply_elementwise.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, vp, _f64p, _f64p, ctypes.c_void_p]
         L.orc_band_cholesky_solve.argtypes = [i32, i32, _i64p, _i64p, _f64p, _f64p, _f64p]
         L.orc_pcg.argtypes = [i32, i32, _i64p, _i64p, _f64p, _f64p, _f64p, f64, i32, ctypes.POINTER(f64)]
         L.orc_asm_pcg.argtypes = [i32, i32, _i64p, _i64p, _f64p, _f64p, _f64p, i32, i32, i32, f64, i32,
                                   ctypes.POINTER(f64)]
         L.orc_schwarz.argtypes = [i32, i32, _i64p, _i64p, _f64p, _f64p, i32, i32, i32, i32, _f64p, ctypes.c_void_p]
-        L.orc_indicator.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p]
-        L.orc_indicator_el.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p]
+        L.orc_indicator.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, vp, _f64p, _f64p]
+        L.orc_indicator_el.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, vp, _f64p, _f64p]
         L.orc_alpha_update.argtypes = [i64, _f64p, _f64p, f64, f64, f64]
         L.orc_adjoint_grad.argtypes = [i32, i32, _f64p, _f64p, _f64p, f64, _f64p, _f64p,
-                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, i32]
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, i32]
         L.orc_num_threads.restype = i32
         _lib = L
         return L
@@ -129,10 +130,13 @@ class System:
     term uses them in place of g g^T and -ft g; g, ft are still kept (the
     preconditioner of the CUDA path is built from them)."""
 
-    def __init__(self, W, H, g, ft, alpha, lam, Ael=None, Fel=None):
+    def __init__(self, W, H, g, ft, alpha, lam, Ael=None, Fel=None, lamel=None):
         L = _load()
         self.W, self.H, self.lam = int(W), int(H), float(lam)
         self.g, self.ft, self.alpha = _c(g), _c(ft), _c(alpha)
+        # per-element lambda [H-1][W-1][2] (None: the constant lam everywhere)
+        self.lamel = None if lamel is None else _c(np.broadcast_to(np.asarray(lamel, dtype=np.float64),
+                                                                    (H - 1, W - 1, 2)))
         self.Ael = None if Ael is None else _c(Ael)
         self.Fel = None if Fel is None else _c(Fel)
         n = 3 * W * H
@@ -143,24 +147,25 @@ class System:
         self.b = np.zeros(n)
         L.orc_csr_pattern(W, H, self.rowptr, self.col)
         if self.Ael is None:
-            rc = L.orc_assemble(W, H, self.g, self.ft, self.alpha, self.lam, self.rowptr, self.col, self.val, self.b)
+            rc = L.orc_assemble(W, H, self.g, self.ft, self.alpha, self.lam, _ptr(self.lamel), self.rowptr,
+                                self.col, self.val, self.b)
         else:
-            rc = L.orc_assemble_el(W, H, self.Ael, self.Fel, self.alpha, self.lam, self.rowptr, self.col,
-                                   self.val, self.b)
+            rc = L.orc_assemble_el(W, H, self.Ael, self.Fel, self.alpha, self.lam, _ptr(self.lamel), self.rowptr,
+                                   self.col, self.val, self.b)
         if rc:
             raise RuntimeError(f"oracle assembly failed ({rc})")
 
     @classmethod
-    def from_frames(cls, f1, f2, alpha, lam, model=0, rho=0.0):
+    def from_frames(cls, f1, f2, alpha, lam, model=0, rho=0.0, lamel=None):
         f1 = _c(f1)
         H, W = f1.shape
         alpha = np.broadcast_to(np.asarray(alpha, dtype=np.float64), (H - 1, W - 1, 2))
         g, ft = coefficients(f1, f2, model)
         if rho > 0:
             Ael, Fel = element_data(f1, f2, rho, model)
-            S = cls(W, H, g, ft, alpha, lam, Ael, Fel)
+            S = cls(W, H, g, ft, alpha, lam, Ael, Fel, lamel=lamel)
         else:
-            S = cls(W, H, g, ft, alpha, lam)
+            S = cls(W, H, g, ft, alpha, lam, lamel=lamel)
         S.model = int(model)
         S.rho = float(rho)
         return S
@@ -172,7 +177,7 @@ class System:
         the operator only)."""
         if self.Ael is None:
             return self
-        return System(self.W, self.H, self.g, self.ft, self.alpha, self.lam)
+        return System(self.W, self.H, self.g, self.ft, self.alpha, self.lam, lamel=self.lamel)
 
     @property
     def n(self) -> int:
@@ -382,9 +387,11 @@ class System:
         L = _load()
         eta = np.zeros((self.H - 1, self.W - 1, 2))
         if self.Ael is None:
-            L.orc_indicator(self.W, self.H, self.g, self.ft, self.alpha, self.lam, _c(U).ravel(), eta)
+            L.orc_indicator(self.W, self.H, self.g, self.ft, self.alpha, self.lam, _ptr(self.lamel), _c(U).ravel(),
+                            eta)
         else:
-            L.orc_indicator_el(self.W, self.H, self.Ael, self.Fel, self.alpha, self.lam, _c(U).ravel(), eta)
+            L.orc_indicator_el(self.W, self.H, self.Ael, self.Fel, self.alpha, self.lam, _ptr(self.lamel),
+                               _c(U).ravel(), eta)
         return eta
 
 
@@ -434,32 +441,52 @@ def smooth_transpose(G, sigma):
     return _smooth_axis(_smooth_axis(G, 0, sigma, True), 1, sigma, True)
 
 
-def apply_elementwise(W, H, g, ft, alpha, lam, U, with_rhs=False):
-    """A U (and b) without storing A, for grids too large for the CSR."""
+def _lamel(lamel, W, H):
+    return None if lamel is None else _c(np.broadcast_to(np.asarray(lamel, dtype=np.float64), (H - 1, W - 1, 2)))
+
+
+def apply_elementwise(W, H, g, ft, alpha, lam, U, with_rhs=False, lamel=None):
+    """A U (and b) without storing A, for grids too large for the CSR
+    (lamel: per-element lambda, None for the constant lam)."""
     L = _load()
+    lamel = _lamel(lamel, W, H)
     y = np.zeros(3 * W * H)
     b = np.zeros(3 * W * H) if with_rhs else None
     alpha = _c(np.broadcast_to(np.asarray(alpha, dtype=np.float64), (H - 1, W - 1, 2)))
-    L.orc_apply_elementwise(W, H, _c(g), _c(ft), alpha, float(lam), _c(U).ravel(), y, _ptr(b))
+    L.orc_apply_elementwise(W, H, _c(g), _c(ft), alpha, float(lam), _ptr(lamel), _c(U).ravel(), y, _ptr(b))
     y = y.reshape(3, H, W)
     return (y, b.reshape(3, H, W)) if with_rhs else y
 
 
-def rel_residual_frames(f1, f2, alpha, lam, U, model=0) -> float:
+def rel_residual_frames(f1, f2, alpha, lam, U, model=0, lamel=None) -> float:
     """||b - A U||_2 / ||b||_2 of a frame pair, formed element by element."""
     f1 = _c(f1)
     H, W = f1.shape
     g, ft = coefficients(f1, f2, model)
-    AU, b = apply_elementwise(W, H, g, ft, alpha, lam, U, with_rhs=True)
+    AU, b = apply_elementwise(W, H, g, ft, alpha, lam, U, with_rhs=True, lamel=lamel)
     return float(np.linalg.norm(b - AU) / np.linalg.norm(b))
 
 
-def indicator(W, H, g, ft, alpha, lam, U):
+def indicator(W, H, g, ft, alpha, lam, U, lamel=None):
     L = _load()
+    lamel = _lamel(lamel, W, H)
     eta = np.zeros((H - 1, W - 1, 2))
     alpha = _c(np.broadcast_to(np.asarray(alpha, dtype=np.float64), (H - 1, W - 1, 2)))
-    L.orc_indicator(W, H, _c(g), _c(ft), alpha, float(lam), _c(U).ravel(), eta)
+    L.orc_indicator(W, H, _c(g), _c(ft), alpha, float(lam), _ptr(lamel), _c(U).ravel(), eta)
     return eta
+
+
+def adjoint_grad_lambda(f1, f2, alpha, lam, U, Lam):
+    """dL/dlambda_K = -|K| grad(Lam_m) . grad(U_m) per element (the derivative
+    of the m stiffness w.r.t. a per-element lambda), given U and the adjoint
+    state Lam."""
+    L = _load()
+    f1, f2 = _c(f1), _c(f2)
+    H, W = f1.shape
+    alpha = _c(np.broadcast_to(np.asarray(alpha, dtype=np.float64), (H - 1, W - 1, 2)))
+    dl = np.zeros((H - 1, W - 1, 2))
+    L.orc_adjoint_grad(W, H, f1, f2, alpha, float(lam), _c(U).ravel(), _c(Lam).ravel(), None, None, None, _ptr(dl), 0)
+    return dl
 
 
 def alpha_update(eta, alpha, kappa, eta_thr, alpha_th):
@@ -481,7 +508,7 @@ def adjoint_grad(f1, f2, alpha, lam, U, Lam, want_f1=True, model=0, rho=0.0):
     d2 = np.zeros((H, W))
     d1 = np.zeros((H, W)) if want_f1 else None
     L.orc_adjoint_grad(W, H, f1, f2, alpha, float(lam), _c(U).ravel(), _c(Lam).ravel(),
-                       _ptr(da), _ptr(d2), _ptr(d1), int(model))
+                       _ptr(da), _ptr(d2), _ptr(d1), None, int(model))
     if rho > 0:
         d2, d1r = _adjoint_frames_rho(f1, f2, U, Lam, model, rho)
         d1 = d1r if want_f1 else None

@@ -58,7 +58,7 @@ def bilinear(f1, f2, alpha, lam, U, V, illumination=True):
     for x, y, t, verts in triangles(W, H):
         g, ft = element_data(f1, f2, verts, illumination)
         G, area = bary(verts)
-        Lam = np.array([alpha[y, x, t], alpha[y, x, t], lam])
+        Lam = np.array([alpha[y, x, t], alpha[y, x, t], lam[y, x, t] if np.ndim(lam) else lam])
         uv = np.array([[U[c, yy, xx] for c in range(3)] for xx, yy in verts])  # [vertex][c]
         vv = np.array([[V[c, yy, xx] for c in range(3)] for xx, yy in verts])
         for q in QPTS:
@@ -71,6 +71,56 @@ def bilinear(f1, f2, alpha, lam, U, V, illumination=True):
 
 
 # ------------------------------------------------------------ assembly ----
+
+def test_per_element_lambda_operator_equals_weak_form(oracle):
+    """With a per-element lambda (Section 1: Lambda piecewise constant on the
+    elements) U^T A V equals the weak form with lambda_K on each element, by
+    the independent rule; a constant field gives the constant-lambda matrix
+    bit for bit."""
+    W, H = 5, 4
+    rng = np.random.default_rng(57)
+    f1, f2 = synth.random_frames(W, H, 58)
+    alpha = synth.random_alpha(W, H, 59)
+    lamel = 0.2 + rng.random((H - 1, W - 1, 2)) * 3.0
+    S = oracle.System.from_frames(f1, f2, alpha, 1.0, lamel=lamel)
+    for _ in range(3):
+        U = rng.standard_normal((3, H, W))
+        V = rng.standard_normal((3, H, W))
+        a_uv, l_v = bilinear(f1, f2, alpha, lamel, U, V)
+        assert abs(np.sum(V * S.matvec(U)) - a_uv) < 1e-12 * max(1.0, abs(a_uv))
+        assert abs(S.b @ V.ravel() - l_v) < 1e-13 * max(1.0, abs(l_v))
+    S1 = oracle.System.from_frames(f1, f2, alpha, 0.7)
+    S2 = oracle.System.from_frames(f1, f2, alpha, 123.0, lamel=np.full((H - 1, W - 1, 2), 0.7))
+    assert np.array_equal(S1.val, S2.val) and np.array_equal(S1.b, S2.b)
+
+
+def test_lambda_gradient_matches_central_differences(oracle):
+    """dL/dlambda_K = -|K| grad(Lam_m) . grad(U_m) (the adjoint of the m
+    stiffness) against central differences of L(U(lambda)) through direct
+    solves, L = 1/2 |U - U_t|^2."""
+    W, H = 7, 6
+    rng = np.random.default_rng(61)
+    f1, f2 = synth.random_frames(W, H, 62)
+    alpha = synth.random_alpha(W, H, 63)
+    lamel = 0.5 + rng.random((H - 1, W - 1, 2))
+    Ut = rng.standard_normal((3, H, W))
+
+    def solve(lm):
+        return oracle.System.from_frames(f1, f2, alpha, 1.0, lamel=lm).solve_direct()
+
+    S = oracle.System.from_frames(f1, f2, alpha, 1.0, lamel=lamel)
+    U = S.solve_direct()
+    Lam = S.solve_with(U - Ut)
+    dl = oracle.adjoint_grad_lambda(f1, f2, alpha, 1.0, U, Lam)
+    h = 1e-5
+    for _ in range(5):
+        y, x, t = rng.integers(0, H - 1), rng.integers(0, W - 1), rng.integers(0, 2)
+        lp, lm = lamel.copy(), lamel.copy()
+        lp[y, x, t] += h
+        lm[y, x, t] -= h
+        fd = (0.5 * np.sum((solve(lp) - Ut) ** 2) - 0.5 * np.sum((solve(lm) - Ut) ** 2)) / (2 * h)
+        assert abs(fd - dl[y, x, t]) <= 1e-6 * np.abs(dl).max(), (fd, dl[y, x, t])
+
 
 def test_coefficients_match_p1_interpolant(oracle):
     f1, f2 = synth.random_frames(6, 5, 11)
@@ -458,7 +508,7 @@ def indicator_independent(f1, f2, alpha, lam, U):
     for x, y, t, verts in tris:
         g, ft = element_data(f1, f2, verts)
         G, area = bary(verts)
-        Lam = np.array([alpha[y, x, t], alpha[y, x, t], lam])
+        Lam = np.array([alpha[y, x, t], alpha[y, x, t], lam[y, x, t] if np.ndim(lam) else lam])
         uv = np.array([[U[c, yy, xx] for c in range(3)] for xx, yy in verts])
         grads = np.array([G.T @ uv[:, c] for c in range(3)])  # [c][2]
         info.append((g, ft, area, Lam, uv, grads, verts))
@@ -505,6 +555,19 @@ def test_indicator_matches_independent_route(oracle):
     U = np.random.default_rng(43).standard_normal((3, H, W))
     S = oracle.System.from_frames(f1, f2, alpha, 0.6)
     np.testing.assert_allclose(S.indicator(U), indicator_independent(f1, f2, alpha, 0.6, U), rtol=1e-12, atol=1e-14)
+
+
+def test_per_element_lambda_indicator_matches_independent_route(oracle):
+    """Per-element lambda (Lambda = (alpha_K, alpha_K, lambda_K); Lambda_e the
+    componentwise max of the two sides) by the independent route."""
+    W, H = 6, 5
+    f1, f2 = synth.random_frames(W, H, 46)
+    alpha = synth.random_alpha(W, H, 47)
+    lamel = 0.3 + synth.random_alpha(W, H, 48) * 10.0
+    U = np.random.default_rng(49).standard_normal((3, H, W))
+    S = oracle.System.from_frames(f1, f2, alpha, 0.6, lamel=lamel)
+    np.testing.assert_allclose(S.indicator(U), indicator_independent(f1, f2, alpha, lamel, U), rtol=1e-12,
+                               atol=1e-14)
 
 
 def test_indicator_closed_forms(oracle):
