@@ -125,6 +125,13 @@ typedef struct {
                                    ||b - A U|| <= rtol ||b|| or max_inner iterations; inner_iters counts the
                                    iterations and of_get_schwarz_history gives ||U^k - U^{k-1}||_2 of each.
                                    Needs the Schwarz preconditioner settings, coarse = 0 and rho = 0 */
+    double lambda_min;       /* 0: lambda constant, as the paper keeps it (Section 2.3) [0]; > 0: lambda per
+                                element (Section 1: Lambda piecewise constant), initialised to `lambda`, set by
+                                of_set_lambda, and adapted by of_adapt_alpha with the rule of alpha (the same
+                                eta_K) and this threshold (<= lambda).  The operator, the residual and the
+                                indicator use the per-element lambda (Lambda_e = max of the two sides); the
+                                Schwarz preconditioner keeps the constant `lambda`; needs rho = 0; the
+                                adaptation-pass VJP is not provided with it */
     int half_sweeps;         /* mixed path, PCG: local sweeps of the Schwarz preconditioner in packed FP16
                                 arithmetic, two nodes per instruction [0]: 0 = wherever the tile allows
                                 (sweeps >= 1, extended tile height 2 HP with HP a multiple of 3, at most
@@ -198,6 +205,13 @@ of_status of_set_alpha(of_handle h, int pair, const void *alpha, double alpha_co
 
 /* Copies the current per-element alpha of a pair out ([H-1][W-1][2]). */
 of_status of_get_alpha(of_handle h, int pair, void *alpha, of_dtype dt);
+
+/* Per-element lambda (grid option lambda_min > 0, Section 1): sets that of
+ * pair `pair` from `lam` ([H-1][W-1][2], dtype dt) or, if lam is NULL, to the
+ * constant lam_const (> 0); of_get_lambda copies it out.  OF_ERR_STATE on a
+ * grid with a constant lambda. */
+of_status of_set_lambda(of_handle h, int pair, const void *lam, double lam_const, of_dtype dt);
+of_status of_get_lambda(of_handle h, int pair, void *lam, of_dtype dt);
 
 /* Solves A U = b for every pair (Section 2.2, Eq. discret-form): PCG with
  * the overlapping Schwarz preconditioner of Section 3.2 (Eq. schwarz, one

@@ -47,7 +47,7 @@ __device__ __forceinline__ void tri_grad(int t, const R A[3], const R B[3], cons
 template <typename R, typename UT>
 __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict__ f1a, const R* __restrict__ f2a,
                             const R* __restrict__ ala, const UT* __restrict__ ua, R* __restrict__ etaa, R lam, R gms,
-                            const R* __restrict__ eld, long long eld_stride,
+                            const R* __restrict__ eld, long long eld_stride, const R* __restrict__ lama,
                             unsigned long long* __restrict__ etamax_bits) {
     const PairDesc pd = pairs[pair];
     const int W = pd.W, H = pd.H, pitch = pd.pitch;
@@ -65,6 +65,9 @@ __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict
         auto F1 = [&](int xx, int yy) { return f1[(long long)yy * pitch + xx]; };
         auto F2 = [&](int xx, int yy) { return f2[(long long)yy * pitch + xx]; };
         auto AL = [&](int xx, int yy, int t) { return al[2 * ((long long)yy * pitch + xx) + t]; };
+        // lambda of an element: the per-element field when given, else the constant
+        const R* la = lama ? lama + 2 * pd.frame_off : nullptr;
+        auto LA = [&](int xx, int yy, int t) { return la ? la[2 * ((long long)yy * pitch + xx) + t] : lam; };
         R uA[3], uB[3], uC[3], uD[3];
         U.at(x, y, uA); U.at(x + 1, y, uB); U.at(x + 1, y + 1, uC); U.at(x, y + 1, uD);
         R gxK[2][3], gyK[2][3];
@@ -87,10 +90,11 @@ __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict
                 g2 = -(F1(x, y) + F1(x, y + 1) + F1(x + 1, y + 1)) * third * gms;
                 ft = ((F2(x, y) - F1(x, y)) + (F2(x, y + 1) - F1(x, y + 1)) + (F2(x + 1, y + 1) - F1(x + 1, y + 1))) * third;
             }
-            const R Lk[3] = {aK[t], aK[t], lam};
+            const R lK = la ? LA(x, y, t) : lam, ilK = la ? R(1) / lK : ilam;
+            const R Lk[3] = {aK[t], aK[t], lK};
             const R iaK = R(1) / aK[t];
-            const R iLk[3] = {iaK, iaK, ilam};
-            const R G = (g0 * g0 + g1 * g1) * iaK + g2 * g2 * ilam;
+            const R iLk[3] = {iaK, iaK, ilK};
+            const R G = (g0 * g0 + g1 * g1) * iaK + g2 * g2 * ilK;
             // midpoints of the 3 edges: (A,V1), (V1,C), (C,A)
             R sm2 = R(0);
             const R* P0[3] = {uA, V1, uC};
@@ -134,7 +138,7 @@ __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict
                     else { nx = R(0.7071067811865476); ny = -R(0.7071067811865476); he = sq2; has = true; nbx = x; nby = y; nbt = 0; }
                 }
                 R ngx[3] = {0, 0, 0}, ngy[3] = {0, 0, 0};
-                R aO = R(0), iaO = R(0);
+                R aO = R(0), iaO = R(0), lO = lam, ilO = ilam;
                 if (has) {
                     R qA[3], qB[3], qC[3], qD[3];
                     if (nbx == x && nby == y) {
@@ -145,15 +149,19 @@ __global__ void k_indicator(const PairDesc* pairs, int pair, const R* __restrict
                     }
                     aO = AL(nbx, nby, nbt);
                     iaO = R(1) / aO;
+                    if (la) {
+                        lO = LA(nbx, nby, nbt);
+                        ilO = R(1) / lO;
+                    }
                 }
                 R q = R(0);
                 for (int c = 0; c < 3; ++c) {
                     const R lk = Lk[c];
-                    const R lo = (c < 2) ? aO : lam;
+                    const R lo = (c < 2) ? aO : lO;
                     const R fin = lk * (gxK[t][c] * nx + gyK[t][c] * ny);
                     const R fout = has ? lo * (ngx[c] * nx + ngy[c] * ny) : R(0);
                     // 1 / max(lo, lk) = min(1/lo, 1/lk)
-                    const R ilo = (c < 2) ? iaO : ilam;
+                    const R ilo = (c < 2) ? iaO : ilO;
                     const R ile = has ? (ilo < iLk[c] ? ilo : iLk[c]) : iLk[c];
                     const R J = fout - fin;
                     q += J * J * ile;
@@ -203,25 +211,28 @@ cudaError_t launch_indicator(const AdaptBufs& A, int pair, int H, int W, cudaStr
     if (A.fp64)
         k_indicator<double, double><<<grid, 128, 0, st>>>(A.pairs, pair, (const double*)A.f1, (const double*)A.f2,
                                                           (const double*)A.alpha, A.u, (double*)A.eta, A.lam, A.gms,
-                                                          (const double*)A.eld, A.eld_stride,
+                                                          (const double*)A.eld, A.eld_stride, (const double*)A.lamel,
                                                           (unsigned long long*)A.etamax);
     else
         k_indicator<float, float><<<grid, 128, 0, st>>>(A.pairs, pair, (const float*)A.f1, (const float*)A.f2,
                                                         (const float*)A.alpha, A.u32, (float*)A.eta, (float)A.lam,
                                                         (float)A.gms,
-                                                        (const float*)A.eld, A.eld_stride,
+                                                        (const float*)A.eld, A.eld_stride, (const float*)A.lamel,
                                                         (unsigned long long*)A.etamax);
     return cudaGetLastError();
 }
 
 cudaError_t launch_alpha_update(const AdaptBufs& A, int pair, int H, int W, double kappa, double eta_thr,
-                                double alpha_th, cudaStream_t st) {
+                                double alpha_th, cudaStream_t st, void* field) {
+    // field: the per-element parameter updated by the rule (alpha, or the
+    // per-element lambda with its own threshold)
+    void* f = field ? field : A.alpha;
     dim3 grid((W - 1 + 127) / 128, H - 1);
     if (A.fp64)
-        k_alpha_update<double><<<grid, 128, 0, st>>>(A.pairs, pair, (double*)A.alpha, (const double*)A.eta,
+        k_alpha_update<double><<<grid, 128, 0, st>>>(A.pairs, pair, (double*)f, (const double*)A.eta,
                                                      (const unsigned long long*)A.etamax, kappa, eta_thr, alpha_th);
     else
-        k_alpha_update<float><<<grid, 128, 0, st>>>(A.pairs, pair, (float*)A.alpha, (const float*)A.eta,
+        k_alpha_update<float><<<grid, 128, 0, st>>>(A.pairs, pair, (float*)f, (const float*)A.eta,
                                                     (const unsigned long long*)A.etamax, (float)kappa, (float)eta_thr,
                                                     (float)alpha_th);
     return cudaGetLastError();

@@ -49,6 +49,7 @@ struct of_ctx {
     size_t alloc_bytes = 0, alloc_limit = 0;  // bytes held; test hook: budget (0: none)
     bool setup_started = false;               // of_setup_grid got past validation (workspace released)
     void *f1 = nullptr, *f2 = nullptr, *alpha = nullptr, *eta = nullptr;
+    void* lamel = nullptr;  // per-element lambda [H][pitch][2] (grid option lambda_min > 0), else null
     double *x[2] = {nullptr, nullptr}, *usol = nullptr, *cvec = nullptr;
     void *r = nullptr, *z = nullptr, *q = nullptr, *d = nullptr, *p0 = nullptr, *p1 = nullptr;
     PairDesc* pd_dev = nullptr;
@@ -185,6 +186,7 @@ void free_all(of_ctx* h) {
     if (h->sc_host) cudaFreeHost(h->sc_host);
     h->sc_host = nullptr;
     h->f1 = h->f2 = h->alpha = h->eta = nullptr;
+    h->lamel = nullptr;
     h->x[0] = h->x[1] = h->usol = h->cvec = nullptr;
     h->r = h->z = h->q = h->d = h->p0 = h->p1 = nullptr;
     h->batch = 0;
@@ -309,6 +311,7 @@ ofl::SolveBufs solve_bufs(of_ctx* h) {
     B.tx_extra = h->starve_bytes;
     B.coarse = h->coarse;
     B.h2 = h->h2;
+    B.lamel = h->lamel;
     B.cp0 = h->cp0;
     B.cp1 = h->cp1;
     return B;
@@ -322,6 +325,7 @@ ofl::AdaptBufs adapt_bufs(of_ctx* h) {
     A.f2 = h->f2;
     A.alpha = h->alpha;
     A.u = h->usol;
+    A.lamel = h->lamel;
     A.u32 = h->fp64 ? nullptr : (const float*)h->z;  // filled by of_adapt_alpha (z is free after a solve)
     A.eta = h->eta;
     A.etamax = h->etamax;
@@ -747,6 +751,10 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
     if (opt.tile_x < 4 || opt.tile_y < 4 || opt.tile_x % 4 || opt.tile_y % 4 || opt.tile_x > 256 || opt.tile_y > 256)
         return fail(h, OF_ERR_ARG, "tile sizes must be multiples of 4 in [4, 256]");
     if (opt.schwarz != 0 && opt.schwarz != 1) return fail(h, OF_ERR_ARG, "schwarz must be 0 or 1");
+    if (!(opt.lambda_min >= 0) || (opt.lambda_min > 0 && !(opt.lambda_min <= opt.lambda)))
+        return fail(h, OF_ERR_ARG, "lambda_min must be 0 (constant lambda) or in (0, lambda]");
+    if (opt.lambda_min > 0 && opt.rho > 0)
+        return fail(h, OF_ERR_ARG, "a per-element lambda needs rho = 0");
     if (opt.schwarz == 1 && (opt.preconditioner != OF_PC_SCHWARZ || opt.coarse != 0 || opt.rho != 0))
         return fail(h, OF_ERR_ARG, "the stationary Schwarz iteration needs the Schwarz settings, coarse = 0, rho = 0");
     if (opt.overlap < 0 || opt.overlap > 32 || opt.sweeps < 0 || opt.sweeps > (opt.schwarz ? 4096 : 64))
@@ -873,6 +881,7 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
         CK(dalloc(h, &h->eldg, 18 * fo * es));
     }
     CK(dalloc(h, &h->alpha, 2 * fo * es));
+    if (opt.lambda_min > 0) CK(dalloc(h, &h->lamel, 2 * fo * es));
     CK(dalloc(h, &h->eta, 2 * fo * es));
     CK(dalloc(h, &h->cell0, fo * (h->fp64 ? 32 : 8)));
     CK(dalloc(h, &h->cell1, fo * (h->fp64 ? 32 : 8)));
@@ -918,6 +927,7 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
     CK(cudaMemsetAsync(h->f1, 0, fo * es, st));
     CK(cudaMemsetAsync(h->f2, 0, fo * es, st));
     CK(cudaMemsetAsync(h->alpha, 0, 2 * fo * es, st));
+    if (h->lamel) CK(ofl::fill2d(h->lamel, fp64 ? ofl::T_F64 : ofl::T_F32, 2 * fo, 1, 2 * fo, opt.lambda, st));
     CK(cudaMemsetAsync(h->sc_dev, 0, sizeof(PairScalars) * batch, st));
     CK(cudaMemsetAsync(h->cntA, 0, sizeof(unsigned) * batch, st));
     CK(cudaMemsetAsync(h->cntS, 0, sizeof(unsigned) * batch, st));
@@ -1142,6 +1152,36 @@ of_status of_set_alpha(of_handle h, int pair, const void* alpha, double alpha_co
     return OF_OK;
 }
 
+of_status of_set_lambda(of_handle h, int pair, const void* lam, double lam_const, of_dtype dt) {
+    of_status s = check_pair(h, pair);
+    if (s != OF_OK) return s;
+    if (!h->lamel) return fail(h, OF_ERR_STATE, "the grid has a constant lambda (lambda_min = 0)");
+    const PairDesc& d = h->pd[pair];
+    DevGuard g(h->device);
+    void* dst = (char*)h->lamel + 2 * d.frame_off * h->es;
+    if (!lam) {
+        if (!(lam_const > 0) || !std::isfinite(lam_const)) return fail(h, OF_ERR_ARG, "lam_const must be > 0");
+        CK(fl2d(h, dst, h->fp64 ? ofl::T_F64 : ofl::T_F32, 2LL * d.pitch, d.H - 1, 2LL * (d.W - 1), lam_const,
+                h->stream));
+    } else {
+        s = copy_in(h, lam, dt, 2LL * (d.W - 1), dst, 2LL * d.pitch, d.H - 1, 2LL * (d.W - 1));
+        if (s != OF_OK) return s;
+    }
+    h->solved = false;
+    return OF_OK;
+}
+
+of_status of_get_lambda(of_handle h, int pair, void* lam, of_dtype dt) {
+    of_status s = check_pair(h, pair);
+    if (s != OF_OK) return s;
+    if (!lam) return fail(h, OF_ERR_ARG, "null lambda");
+    if (!h->lamel) return fail(h, OF_ERR_STATE, "the grid has a constant lambda (lambda_min = 0)");
+    const PairDesc& d = h->pd[pair];
+    DevGuard g(h->device);
+    return copy_out(h, (char*)h->lamel + 2 * d.frame_off * h->es, h->fp64 ? ofl::T_F64 : ofl::T_F32, 2LL * d.pitch,
+                    lam, dt, d.H - 1, 2LL * (d.W - 1));
+}
+
 of_status of_get_alpha(of_handle h, int pair, void* alpha, of_dtype dt) {
     of_status s = check_pair(h, pair);
     if (s != OF_OK) return s;
@@ -1233,6 +1273,10 @@ of_status of_adapt_alpha(of_handle h, double kappa, double eta_thr, double alpha
         }
         CK(ofl::launch_alpha_update(A, p, d.H, d.W, kappa, eta_thr, alpha_th, st));
         count_other(h, 1);
+        if (h->lamel) {  // the per-element lambda by the same rule, with its own threshold
+            CK(ofl::launch_alpha_update(A, p, d.H, d.W, kappa, eta_thr, h->opts.lambda_min, st, h->lamel));
+            count_other(h, 1);
+        }
     }
     CK(cudaStreamSynchronize(st));
     h->solved = false;  // alpha changed: the stored solution no longer belongs to it
@@ -1243,6 +1287,8 @@ of_status of_adapt_alpha(of_handle h, double kappa, double eta_thr, double alpha
 of_status of_adapt_alpha_vjp(of_handle h, double kappa, double eta_thr, double alpha_th, void* const* dLdalpha_new,
                              void* const* dLdalpha, void* const* dLdU, void* const* dLdf2, void* const* dLdf1,
                              of_dtype dt) {
+    if (h && h->lamel)
+        return fail(h, OF_ERR_STATE, "the adaptation-pass VJP is not provided with a per-element lambda (lambda_min > 0)");
     NvtxRange nv("of_adapt_alpha_vjp");
     if (!h) return OF_ERR_ARG;
     if (!h->solved) return fail(h, OF_ERR_STATE, "of_adapt_alpha_vjp needs a previous of_solve at the current alpha");

@@ -99,6 +99,28 @@ __device__ __forceinline__ void square_contrib(const NodeVal<R>& A, const NodeVa
     }
 }
 
+// square_contrib with a per-element lambda (lam0 on t = 0, lam1 on t = 1)
+// instead of the constant: the m stiffness is added per triangle.
+template <typename R, bool WANT_B, bool WANT_A = true>
+__device__ __forceinline__ void square_contrib_l(const NodeVal<R>& A, const NodeVal<R>& B, const NodeVal<R>& C,
+                                                 const NodeVal<R>& D, R al0, R al1, R lam0, R lam1, R gms, bool valid,
+                                                 V3<R>& cA, V3<R>& cB, V3<R>& cC, V3<R>& cD,
+                                                 V3<R>& bA, V3<R>& bB, V3<R>& bC, V3<R>& bD) {
+    const R zero = kconst<R>(0.0);
+    square_contrib<R, WANT_B, WANT_A>(A, B, C, D, al0, al1, zero, gms, valid, cA, cB, cC, cD, bA, bB, bC, bD);
+    if constexpr (WANT_A) {
+        if (valid) {
+            const R h = kconst<R>(OF_STIFF_HALF);
+            const R l0 = h * lam0, l1 = h * lam1;
+            const R dAB = A.p.c - B.p.c, dCB = C.p.c - B.p.c, dAD = A.p.c - D.p.c, dCD = C.p.c - D.p.c;
+            cA.c = cA.c + (l0 * dAB + l1 * dAD);
+            cB.c = cB.c - l0 * (dAB + dCB);
+            cC.c = cC.c + (l0 * dCB + l1 * dCD);
+            cD.c = cD.c - l1 * (dAD + dCD);
+        }
+    }
+}
+
 // The same with general element data (K_rho > 0): per triangle the tensor
 // A (entries 00, 01, 02, 11, 12, 22) and the load vector F of Section 1.
 // Data term of vertex i: |K|/12 A (p_i + sum_j p_j); load |K|/3 F.
@@ -170,6 +192,7 @@ struct ApplyParams {
     double* partial;           // [nblocks][2]
     unsigned* counter;         // [batch]
     const C* f1; const C* f2; const C* alpha;
+    const C* lamel;            // per-element lambda [H][pitch][2] like alpha, or null (the constant lam)
     R lam;
     R gms;                     // illumination column scale (1: model with m, 0: brightness constancy)
     const C* eld;              // K_rho element data: 18 planes (t * 9 + k), plane stride eld_stride
@@ -360,6 +383,12 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
             }
             square_contrib_el<T, WANT_B || IS_RES, MODE != MODE_RESB>(cur.p, ncur.p, nnxt.p, nxt.p, al0, al1, lam, e0,
                                                                       e1, valid, cA, cB, cC, cD, bA, bB, bC, bD);
+        } else if (P.lamel) {
+            const C* la = P.lamel + 2 * pd.frame_off;
+            const T la0 = valid ? Cvt<T>::from(la[2 * ((long long)sy * pitch + cx)]) : zero;
+            const T la1 = valid ? Cvt<T>::from(la[2 * ((long long)sy * pitch + cx) + 1]) : zero;
+            square_contrib_l<T, WANT_B || IS_RES, MODE != MODE_RESB>(cur, ncur, nnxt, nxt, al0, al1, la0, la1, gms,
+                                                                        valid, cA, cB, cC, cD, bA, bB, bC, bD);
         } else {
             square_contrib<T, WANT_B || IS_RES, MODE != MODE_RESB>(cur, ncur, nnxt, nxt, al0, al1, lam, gms, valid,
                                                                       cA, cB, cC, cD, bA, bB, bC, bD);

@@ -81,6 +81,7 @@ static ApplyParams<R, C, RI> base_params(const SolveBufs& B) {
     P.lam = (R)B.lam;
     P.gms = (R)B.gms;
     P.eld = (const C*)B.eld;
+    P.lamel = (const C*)B.lamel;
     P.eld_stride = B.eld_stride;
     P.rows_per_block = B.rows_per_block;
     P.err = B.err;
@@ -371,6 +372,7 @@ static cudaError_t pcg_apply_t(const SolveBufs& B, cudaStream_t st) {
     P.dcorr = (R*)B.d;
     P.out = (R*)B.q;
     if (B.eld) k_apply<R, R, R, MODE_PCG, false, APPLY_NW, R, true><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+    else if (B.lamel) k_apply<R, R, R, MODE_PCG, false, APPLY_NW><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);  // per-element lambda
     else if constexpr (sizeof(R) == 4) k_apply4<MODE_PCG><<<B.nblk, 32, apply4_smem_bytes(), st>>>(P);  // FP32: four columns per lane
     else k_apply<R, R, R, MODE_PCG, false, APPLY_NW><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
     return cudaGetLastError();
@@ -396,6 +398,7 @@ static cudaError_t apply_t(const SolveBufs& B, int blk0, int nblk, const void* p
         if (b) k_apply<R, R, R, MODE_APPLY, true, APPLY_NW, R, true><<<nblk, APPLY_NW * 32, 0, st>>>(P);
         else k_apply<R, R, R, MODE_APPLY, false, APPLY_NW, R, true><<<nblk, APPLY_NW * 32, 0, st>>>(P);
     } else if (b) k_apply<R, R, R, MODE_APPLY, true, APPLY_NW><<<nblk, APPLY_NW * 32, 0, st>>>(P);
+    else if (B.lamel) k_apply<R, R, R, MODE_APPLY, false, APPLY_NW><<<nblk, APPLY_NW * 32, 0, st>>>(P);
     else if constexpr (sizeof(R) == 4) k_apply4<MODE_APPLY><<<nblk, 32, apply4_smem_bytes(), st>>>(P);
     else k_apply<R, R, R, MODE_APPLY, false, APPLY_NW><<<nblk, APPLY_NW * 32, 0, st>>>(P);
     return cudaGetLastError();

@@ -98,6 +98,7 @@ struct SolveBufs {
     double omega;  // relaxation factor of the local block SOR sweeps
     double gms;    // illumination column scale of the element data (1 or 0, see of_model)
     const void* eld;      // K_rho element data (18 planes, storage precision) or null (rho = 0)
+    const void* lamel;    // per-element lambda [H][pitch][2] (storage precision) or null (constant)
     long long eld_stride; // plane stride of eld (elements)
     int fp64;            // 1: everything FP64; 0: FP32 inner with FP64 residual
     long long spin_limit;
@@ -169,6 +170,7 @@ struct AdaptBufs {
     double gms;
     const void* eld;      // K_rho element data or null
     long long eld_stride;
+    const void* lamel;    // per-element lambda or null (constant)
     void* eldg;           // K_rho adjoint: 18 planes like eld (work)
     void* scratch;        // one [H][pitch] plane of the pair (work of the K_rho^T passes)
     const struct SmoothTaps* taps_rho;
@@ -209,8 +211,10 @@ cudaError_t launch_smooth(void* f, void* scratch, int type, int W, int H, long l
 // smoothed by T over the (W-1) x (H-1) lattice; scratch: H x pitch values
 cudaError_t launch_element_data(const void* f1, const void* f2, int type, int W, int H, long long pitch, double gms,
                                 void* eld, long long stride, void* scratch, const SmoothTaps& T, cudaStream_t st);
+// the update rule of Section 2.3 on alpha, or on `field` (the per-element
+// lambda) when it is not null
 cudaError_t launch_alpha_update(const AdaptBufs& A, int pair, int H, int W, double kappa, double eta_thr,
-                                double alpha_th, cudaStream_t st);
+                                double alpha_th, cudaStream_t st, void* field = nullptr);
 // VJP of one adaptation pass (indicator at the stored solution, then the
 // alpha update) for dL/dalpha_new = v (dense [H-1][W-1][2]): da = dL/dalpha
 // through the pass, dU = dL/dU ([3][H][W]), df2 / df1 ([H][W], may be null)

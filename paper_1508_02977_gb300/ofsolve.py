@@ -37,7 +37,7 @@ class GridOpts(ctypes.Structure):
                 ("sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("lam", ctypes.c_double),
                 ("preconditioner", ctypes.c_int), ("omega", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("model", ctypes.c_int), ("coarse", ctypes.c_int), ("rho", ctypes.c_double),
-                ("schwarz", ctypes.c_int), ("half_sweeps", ctypes.c_int)]
+                ("schwarz", ctypes.c_int), ("lambda_min", ctypes.c_double), ("half_sweeps", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -71,6 +71,8 @@ _lib.of_setup_grid.argtypes = [_h, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
 _lib.of_set_frames.argtypes = [_h, ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int64]
 _lib.of_set_alpha.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_int]
 _lib.of_get_alpha.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_int]
+_lib.of_set_lambda.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_int]
+_lib.of_get_lambda.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_int]
 _lib.of_get_frames.argtypes = [_h, ctypes.c_int, _vp, _vp, ctypes.c_int]
 _lib.of_get_element_data.argtypes = [_h, ctypes.c_int, _vp, ctypes.c_int]
 _lib.of_set_wait_limit.argtypes = [_h, ctypes.c_int64]
@@ -96,14 +98,15 @@ _lib.of_last_error.argtypes = [_h]
 _lib.of_last_error.restype = ctypes.c_char_p
 for _f in ("of_create", "of_setup_grid", "of_set_frames", "of_get_element_data", "of_set_alpha", "of_get_alpha", "of_solve",
            "of_adapt_alpha", "of_adapt_alpha_vjp", "of_adjoint", "of_apply", "of_precondition", "of_residual",
-           "of_set_profiling", "of_get_profile", "of_residual_noalloc", "of_get_schwarz_history", "of_destroy"):
+           "of_set_profiling", "of_get_profile", "of_residual_noalloc", "of_get_schwarz_history", "of_set_lambda",
+           "of_get_lambda", "of_destroy"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 EXPORTS = ("of_create", "of_setup_grid", "of_set_frames", "of_get_frames", "of_get_element_data", "of_set_alpha",
            "of_get_alpha", "of_solve",
            "of_adapt_alpha", "of_adapt_alpha_vjp", "of_adjoint", "of_apply", "of_precondition", "of_residual",
            "of_set_profiling", "of_get_profile", "of_residual_noalloc", "of_set_wait_limit", "of_debug_starve_staging",
-           "of_set_alloc_limit", "of_get_schwarz_history",
+           "of_set_alloc_limit", "of_get_schwarz_history", "of_set_lambda", "of_get_lambda",
            "of_destroy", "of_last_error")
 
 
@@ -163,7 +166,7 @@ def of_create(device: int = 0, stream=None):
 
 def of_setup_grid(h, sizes, tile=(32, 32), overlap=0, sweeps=1, precision=OF_PREC_MIXED, lam=1.0,
                   preconditioner=OF_PC_SCHWARZ, omega=1.0, sigma=0.0, model=0, coarse=0, rho=0.0, schwarz=0,
-                  half_sweeps=0):
+                  half_sweeps=0, lambda_min=0.0):
     """sizes: list of (W, H); omega: relaxation factor of the local block SOR
     sweeps, in (0, 2); sigma: K_sigma pre-smoothing of the frames (0: none);
     model: OF_MODEL_ILLUMINATION or OF_MODEL_CONSTANT; coarse: spacing of the
@@ -171,12 +174,14 @@ def of_setup_grid(h, sizes, tile=(32, 32), overlap=0, sweeps=1, precision=OF_PRE
     integration scale of the data term (0: none); schwarz: 1 makes of_solve
     run the stationary Schwarz iteration instead of the PCG; half_sweeps:
     FP16 paired local sweeps on the mixed path (0: where the tile allows, 1:
-    required, -1: off)."""
+    required, -1: off); lambda_min > 0: a per-element lambda, adapted by
+    of_adapt_alpha with this threshold."""
     n = len(sizes)
     Wa = (ctypes.c_int32 * n)(*[int(w) for w, _ in sizes])
     Ha = (ctypes.c_int32 * n)(*[int(hh) for _, hh in sizes])
     o = GridOpts(int(tile[0]), int(tile[1]), int(overlap), int(sweeps), int(precision), float(lam), int(preconditioner),
-                 float(omega), float(sigma), int(model), int(coarse), float(rho), int(schwarz), int(half_sweeps))
+                 float(omega), float(sigma), int(model), int(coarse), float(rho), int(schwarz), float(lambda_min),
+                 int(half_sweeps))
     return _check(h, _lib.of_setup_grid(h, n, Wa, Ha, ctypes.byref(o)))
 
 
@@ -207,6 +212,17 @@ def of_get_frames(h, pair, f1, f2):
     if dt != dt2:
         raise TypeError("frames must share a dtype")
     return _check(h, _lib.of_get_frames(h, int(pair), _vp(p1), _vp(p2), dt))
+
+
+def of_set_lambda(h, pair, lam=None, lam_const=0.0):
+    """Per-element lambda of a pair ([H-1][W-1][2]) or a constant (grids with lambda_min > 0)."""
+    p, dt = _ptr_dtype(lam)
+    return _check(h, _lib.of_set_lambda(h, int(pair), _vp(p) if p else None, float(lam_const), dt))
+
+
+def of_get_lambda(h, pair, out):
+    p, dt = _ptr_dtype(out)
+    return _check(h, _lib.of_get_lambda(h, int(pair), _vp(p), dt))
 
 
 def of_get_alpha(h, pair, out):

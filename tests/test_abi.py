@@ -44,12 +44,13 @@ def test_binding_wraps_every_export(lib):
 
 def test_struct_layouts_match_header():
     from paper_1508_02977_gb300 import ofsolve as S
-    # of_grid_opts: 4 ints, enum, (pad), double, enum, (pad), double, double, enum, int, double, int, int;
+    # of_grid_opts: 4 ints, enum, (pad), double, enum, (pad), double, double, enum, int, double, int, (pad),
+    # double, int (+ pad);
     # of_solve_opts: double, 3 ints, (pad), double, int (+ pad)
-    assert ctypes.sizeof(S.GridOpts) == 80
+    assert ctypes.sizeof(S.GridOpts) == 96
     assert [getattr(S.GridOpts, f).offset for f in
             ("tile_x", "sweeps", "precision", "lam", "preconditioner", "omega", "sigma", "model", "coarse",
-             "rho", "schwarz", "half_sweeps")] == [0, 12, 16, 24, 32, 40, 48, 56, 60, 64, 72, 76]
+             "rho", "schwarz", "lambda_min", "half_sweeps")] == [0, 12, 16, 24, 32, 40, 48, 56, 60, 64, 72, 80, 88]
     assert ctypes.sizeof(S.SolveOpts) == 48
     assert [getattr(S.SolveOpts, f).offset for f in
             ("rtol", "max_outer", "max_inner", "warm_start", "inner_rtol", "host_loop", "pass_frac")] == \
