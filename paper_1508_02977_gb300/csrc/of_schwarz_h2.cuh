@@ -119,6 +119,65 @@ struct PairState {
     __half2 lew, lns;
 };
 
+// LDL^T factors of the two diagonal blocks of a node pair and the lambda
+// weights of its legs, both lanes, in FP32 (zero for a clipped lane).
+struct FacF2 {
+    float2 i0, l10, l20, i1, l21, i2, lew, lns;
+};
+
+// The factors of the node pair at (gx, gyA) / (gx, gyB) from its six paired
+// records: D = sum_K 2 h_K h_K^T + the alpha edge weights on the (u1, u2)
+// diagonal + the lambda legs on the m diagonal, both lanes in packed FP32
+// arithmetic; vA, vB: the lane's node lies in the extended tile.
+__device__ __forceinline__ FacF2 pair_factors(const RecH2 (&rec)[6], int gx, int gyA, int gyB, bool vA, bool vB,
+                                              int W, int H, float hl) {
+    const float2 zero2 = make_float2(0.f, 0.f);
+    float2 S00 = zero2, S01 = zero2, S02 = zero2, S11 = zero2, S12 = zero2, S22 = zero2;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float2 a0 = __half22float2(rec[k].h0), a1 = __half22float2(rec[k].h1), a2 = __half22float2(rec[k].h2);
+        S00 = __ffma2_rn(a0, a0, S00);
+        S01 = __ffma2_rn(a0, a1, S01);
+        S02 = __ffma2_rn(a0, a2, S02);
+        S11 = __ffma2_rn(a1, a1, S11);
+        S12 = __ffma2_rn(a1, a2, S12);
+        S22 = __ffma2_rn(a2, a2, S22);
+    }
+    // alpha edge weights E, N, W, S: w of E1, E2, E5, E6
+    const float2 ws = __fadd2_rn(__fadd2_rn(__half22float2(rec[0].w), __half22float2(rec[1].w)),
+                                 __fadd2_rn(__half22float2(rec[4].w), __half22float2(rec[5].w)));
+    // lambda legs: 1/2 lambda per triangle on each of the four legs
+    auto legs = [&](int gy) {
+        const int vc = (gx < W - 1 && gy < H - 1), vsw = (gx >= 1 && gy >= 1);
+        const int vw = (gx >= 1 && gy < H - 1), vs = (gx < W - 1 && gy >= 1);
+        return (float)((vc + vs) + (vc + vw) + (vsw + vw) + (vsw + vs));
+    };
+    const float2 two = make_float2(2.f, 2.f);
+    const float2 D00 = __ffma2_rn(two, S00, ws), D01 = __fmul2_rn(two, S01), D02 = __fmul2_rn(two, S02),
+                 D11 = __ffma2_rn(two, S11, ws), D12 = __fmul2_rn(two, S12);
+    const float2 D22 = __ffma2_rn(two, S22, make_float2(hl * legs(gyA), hl * legs(gyB)));
+    auto neg = [](float2 v) { return make_float2(-v.x, -v.y); };
+    const float2 i0 = make_float2(rcp(D00.x), rcp(D00.y));
+    const float2 l10 = __fmul2_rn(D01, i0), l20 = __fmul2_rn(D02, i0);
+    const float2 d1 = __ffma2_rn(neg(l10), D01, D11);
+    const float2 i1 = make_float2(rcp(d1.x), rcp(d1.y));
+    const float2 l21 = __fmul2_rn(__ffma2_rn(neg(l20), D01, D12), i1);
+    const float2 d2 = __ffma2_rn(neg(l21), __fmul2_rn(l21, d1), __ffma2_rn(neg(l20), D02, D22));
+    const float2 i2 = make_float2(rcp(d2.x), rcp(d2.y));
+    auto mask = [&](float2 v) { return make_float2(vA ? v.x : 0.f, vB ? v.y : 0.f); };
+    FacF2 f;
+    f.i0 = mask(i0);
+    f.l10 = mask(l10);
+    f.l20 = mask(l20);
+    f.i1 = mask(i1);
+    f.l21 = mask(l21);
+    f.i2 = mask(i2);
+    f.lew = mask(make_float2(hl * ((gyA == 0 || gyA == H - 1) ? 1.f : 2.f), hl * ((gyB == 0 || gyB == H - 1) ? 1.f : 2.f)));
+    const float ln = hl * ((gx == 0 || gx == W - 1) ? 1.f : 2.f);
+    f.lns = mask(make_float2(ln, ln));
+    return f;
+}
+
 // One relaxed block update of a node pair:
 //   x = D^{-1} (b - sum_K h_K (h_K . (z_j + z_k)) + sum_e w_e z_e),
 //   z <- z + omega (x - z),
@@ -216,22 +275,6 @@ __device__ __forceinline__ void pair_store(__half2* __restrict__ Z, int zp, int 
     }
 }
 
-// FP32 element data of one lane of a node pair from its six paired records
-// (E1..E6): the elements' h and the four alpha edge weights.
-__device__ __forceinline__ void lane_records(const RecH2 r[6], int L, float h[6][3], float& wE, float& wN,
-                                             float& wW, float& wS) {
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-        h[e][0] = h_lane(r[e].h0, L);
-        h[e][1] = h_lane(r[e].h1, L);
-        h[e][2] = h_lane(r[e].h2, L);
-    }
-    wE = h_lane(r[0].w, L);
-    wN = h_lane(r[1].w, L);
-    wW = h_lane(r[4].w, L);
-    wS = h_lane(r[5].w, L);
-}
-
 template <int TXC, int TYC, int OVC>
 __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -299,16 +342,61 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
 #pragma unroll
     for (int col = 0; col < 3; ++col) tab[col] = P.ntab[col * NT + threadIdx.x];
 
+    // the pair's size and the step a of a work item, read one item ahead
+    struct ItemScalars {
+        int W, H;
+        float a;
+    };
+    auto item_scalars = [&](const int4 w) {
+        ItemScalars r;
+        r.W = P.pairs[w.x].W;
+        r.H = P.pairs[w.x].H;
+        r.a = (!P.first && !P.apply_only) ? (float)P.sc[w.x].a : 0.f;
+        return r;
+    };
+    // the store of an item's z (and updated r) and its partial sums run after
+    // the first barrier of the next item (with two stages), when every
+    // thread's writes to them are complete
+    struct Pending {
+        int pair, x0, y0, w, stage;
+        bool need_q;
+    };
+    Pending pend;
+    pend.pair = -1;
+    auto flush = [&](const Pending& q) {
+        unsigned char* sq = base + L.stage0 + (size_t)q.stage * L.stage_bytes;
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const CUtensorMap* tm = P.tmaps + (size_t)q.pair * TM_PER_PAIR;
+            tma_store_3d(tm + TM_Z, q.x0, q.y0, 0, sq + L.qs);
+            if (q.need_q) tma_store_3d(tm + TM_R, q.x0, q.y0, 0, sq + L.rs);
+            bulk_commit();
+        }
+        // per-warp sums of r.r and r.z in fixed order (warp 1: thread 0 issues the stores)
+        if (!P.apply_only && (threadIdx.x >> 5) == 1) {
+            const int l = threadIdx.x & 31;
+            const bool w = l < (NT >> 5);
+            const double a2 = warp_sum(w ? sh_red[l] : 0.0), b2 = warp_sum(w ? sh_red[16 + l] : 0.0);
+            if (l == 0) {
+                P.partial[2 * (long long)q.w] = a2;
+                P.partial[2 * (long long)q.w + 1] = b2;
+            }
+        }
+    };
+
     int4 ti = make_int4(0, 0, 0, 0), tin = make_int4(0, 0, 0, 0);
     int t = advance(blockIdx.x, ti);
     int tn = (t < P.ntiles) ? advance(t + G, tin) : P.ntiles;
     if (t < P.ntiles && threadIdx.x == 0) issue(ti, 0);
+    ItemScalars cur = {0, 0, 0.f}, nxt = {0, 0, 0.f};
+    if (t < P.ntiles) cur = item_scalars(ti);
     unsigned phase[2] = {0u, 0u};
     int s = 0;
     for (; t < P.ntiles;) {
         const int tc = tn + G;
         int4 tic = make_int4(0, 0, 0, 0);
         if (tn < P.ntiles && tc < P.ntiles) tic = P.tiles[tc];
+        if (tn < P.ntiles) nxt = item_scalars(tin);
         if (threadIdx.x == 0 && !mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit)) {
             sh_fail = 1;
             atomicOr(P.err, 1);
@@ -320,121 +408,120 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
         }
         if (!mbar_wait_phase_bounded(&bars[s], phase[s], P.spin_limit)) atomicOr(P.err, 1);
         phase[s] ^= 1u;
+        if (pend.pair >= 0) {
+            flush(pend);
+            pend.pair = -1;
+        }
         unsigned char* st = base + L.stage0 + (size_t)s * L.stage_bytes;
         const RecH2* P0s = reinterpret_cast<const RecH2*>(st + L.p0);
         const RecH2* P1s = reinterpret_cast<const RecH2*>(st + L.p1);
         float* Rs = reinterpret_cast<float*>(st + L.rs);
         const float* Qs = reinterpret_cast<const float*>(st + L.qs);
         const int pair = ti.x;
-        const PairDesc pd = P.pairs[pair];
-        const int W = pd.W, H = pd.H;
+        const int W = cur.W, H = cur.H;
         const int x0 = ti.y * Tx, y0 = ti.z * Ty;
         const int tw = min(Tx, W - x0), th = min(Ty, H - y0);
         const int ex0 = max(x0 - ov, 0), ex1 = min(x0 + tw + ov, W);
         const int ey0 = max(y0 - ov, 0), ey1 = min(y0 + th + ov, H);
         const bool need_q = !P.first && !P.apply_only;
-        const float a = need_q ? (float)P.sc[pair].a : 0.f;
+        const float a = cur.a;
         const float hl = 0.5f * (float)P.lam;
         const float om = (float)P.omega;
         const int plane = Tx * Ty;
-        // ---- setup in FP32: diagonal blocks, right-hand sides (r <- r - a q on
-        // the owned nodes), the first Jacobi step and its largest entry
+        // ---- setup in FP32, both lanes of a pair at once in packed (float2)
+        // arithmetic: diagonal blocks and their LDL^T factors, right-hand sides
+        // (r <- r - a q on the owned nodes), the first Jacobi step and its
+        // largest entry
         float rr = 0.f, zmax = 0.f;
         PairState ns[3];
         RecH2 rec1[6];
-        float bf[3][2][3];
-        float xj[2][3];
+        float2 bf[3][3];
+        float2 xj[3];
+        const float2 zero2 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int col = 0; col < 3; ++col) {
             PairState& n = ns[col];
             const uint32_t e = tab[col];
             n.c = -1;
             n.seam = 0;
-            float fac[2][6], lewf[2] = {0.f, 0.f}, lnsf[2] = {0.f, 0.f};
+            const __half2 hz = __float2half2_rn(0.f);
+            n.B.i0 = n.B.l10 = n.B.l20 = n.B.i1 = n.B.l21 = n.B.i2 = n.lew = n.lns = hz;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                bf[col][k] = zero2;
+                if (col == 0) xj[k] = zero2;
+            }
+            if (e == 0xffffffffu) continue;
+            const int li = (int)(e & 0xffffu), lj = (int)(e >> 16);
+            const int c = (lj + 1) * RW + (li + cpad - ov);
+            // the pair's z accesses lie in [c - RW - 1, c + RW + 1] of each plane,
+            // its ghost at c -+ HP RW, its records in [c - RW - 1, c]
+            if (!OF_CHECK(P.err, c - RW - 1, nr) || !OF_CHECK(P.err, c, nr) || !OF_CHECK(P.err, c + RW + 1, nz) ||
+                (lj == HP - 1 && !OF_CHECK(P.err, c - HPRW, nz)) || (lj == 0 && !OF_CHECK(P.err, c + HPRW, nz)))
+                continue;
+            n.c = c;
+            n.seam = (lj == HP - 1) ? 1 : (lj == 0 ? 2 : 0);
+            RecH2 rec[6];
+            pair_records(P0s, P1s, c, RW, rec);
+            if (col == 1) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) rec1[k] = rec[k];  // colour 1 (half the visits) keeps its records
+            }
+            const int gx = x0 - ov + li, gyA = y0 - ov + lj, gyB = gyA + HP;
+            const bool inx = gx >= ex0 && gx < ex1;
+            const bool vA = inx && gyA >= ey0 && gyA < ey1, vB = inx && gyB >= ey0 && gyB < ey1;
+            if (!vA && !vB) continue;  // clipped: factors and values stay zero
+            const FacF2 f = pair_factors(rec, gx, gyA, gyB, vA, vB, W, H, hl);
+            n.B.i0 = __float22half2_rn(f.i0);
+            n.B.l10 = __float22half2_rn(f.l10);
+            n.B.l20 = __float22half2_rn(f.l20);
+            n.B.i1 = __float22half2_rn(f.i1);
+            n.B.l21 = __float22half2_rn(f.l21);
+            n.B.i2 = __float22half2_rn(f.i2);
+            n.lew = __float22half2_rn(f.lew);
+            n.lns = __float22half2_rn(f.lns);
+            // right-hand sides on the owned nodes (r <- r - a q)
+            float bv[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+            bool any = false;
 #pragma unroll
             for (int Ln = 0; Ln < 2; ++Ln) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) fac[Ln][k] = 0.f;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    bf[col][Ln][k] = 0.f;
-                    if (col == 0) xj[Ln][k] = 0.f;
+                const int gy = Ln ? gyB : gyA;
+                if (!(gx >= x0 && gx < x0 + tw && gy >= y0 && gy < y0 + th)) continue;
+                if (!OF_CHECK(P.err, (gy - y0) * Tx + (gx - x0), plane)) continue;
+                const int si = (gy - y0) * Tx + (gx - x0);
+                float v0 = Rs[si], v1 = Rs[si + plane], v2 = Rs[si + 2 * plane];
+                if (need_q) {
+                    v0 -= a * Qs[si];
+                    v1 -= a * Qs[si + plane];
+                    v2 -= a * Qs[si + 2 * plane];
+                    Rs[si] = v0;
+                    Rs[si + plane] = v1;
+                    Rs[si + 2 * plane] = v2;
                 }
+                bv[Ln][0] = v0;
+                bv[Ln][1] = v1;
+                bv[Ln][2] = v2;
+                rr += v0 * v0 + v1 * v1 + v2 * v2;
+                any = true;
             }
-            if (e != 0xffffffffu) {
-                const int li = (int)(e & 0xffffu), lj = (int)(e >> 16);
-                const int c = (lj + 1) * RW + (li + cpad - ov);
-                // the pair's z accesses lie in [c - RW - 1, c + RW + 1] of each plane,
-                // its ghost at c -+ HP RW, its records in [c - RW - 1, c]
-                if (!OF_CHECK(P.err, c - RW - 1, nr) || !OF_CHECK(P.err, c, nr) ||
-                    !OF_CHECK(P.err, c + RW + 1, nz) || (lj == HP - 1 && !OF_CHECK(P.err, c - HPRW, nz)) ||
-                    (lj == 0 && !OF_CHECK(P.err, c + HPRW, nz)))
-                    continue;
-                n.c = c;
-                n.seam = (lj == HP - 1) ? 1 : (lj == 0 ? 2 : 0);
-                RecH2 rec[6];
-                pair_records(P0s, P1s, c, RW, rec);
-                if (col == 1) {
+            if (!any) continue;
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) rec1[k] = rec[k];  // colour 1 (half the visits) keeps its records
-                }
-#pragma unroll
-                for (int Ln = 0; Ln < 2; ++Ln) {
-                    const int gx = x0 - ov + li, gy = y0 - ov + lj + Ln * HP;
-                    if (gx < ex0 || gx >= ex1 || gy < ey0 || gy >= ey1) continue;  // clipped: stays zero
-                    float h[6][3], wE, wN, wW, wS;
-                    lane_records(rec, Ln, h, wE, wN, wW, wS);
-                    const int vc = (gx < W - 1 && gy < H - 1), vsw = (gx >= 1 && gy >= 1);
-                    const int vw = (gx >= 1 && gy < H - 1), vs = (gx < W - 1 && gy >= 1);
-                    const int legs = (vc + vs) + (vc + vw) + (vsw + vw) + (vsw + vs);
-                    float D00 = 0.f, D01 = 0.f, D02 = 0.f, D11 = 0.f, D12 = 0.f, D22 = 0.f;
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) {
-                        D00 += 2.f * h[k][0] * h[k][0]; D01 += 2.f * h[k][0] * h[k][1];
-                        D02 += 2.f * h[k][0] * h[k][2]; D11 += 2.f * h[k][1] * h[k][1];
-                        D12 += 2.f * h[k][1] * h[k][2]; D22 += 2.f * h[k][2] * h[k][2];
-                    }
-                    const float ws = wE + wN + wW + wS;
-                    const Blk<float> B = ldl3<float>(D00 + ws, D01, D02, D11 + ws, D12, D22 + hl * (float)legs);
-                    fac[Ln][0] = B.i0; fac[Ln][1] = B.l10; fac[Ln][2] = B.l20;
-                    fac[Ln][3] = B.i1; fac[Ln][4] = B.l21; fac[Ln][5] = B.i2;
-                    lewf[Ln] = hl * ((gy == 0 || gy == H - 1) ? 1.f : 2.f);
-                    lnsf[Ln] = hl * ((gx == 0 || gx == W - 1) ? 1.f : 2.f);
-                    if (gx >= x0 && gx < x0 + tw && gy >= y0 && gy < y0 + th &&
-                        OF_CHECK(P.err, (gy - y0) * Tx + (gx - x0), plane)) {
-                        const int si = (gy - y0) * Tx + (gx - x0);
-                        float v0 = Rs[si], v1 = Rs[si + plane], v2 = Rs[si + 2 * plane];
-                        if (need_q) {
-                            v0 -= a * Qs[si];
-                            v1 -= a * Qs[si + plane];
-                            v2 -= a * Qs[si + 2 * plane];
-                            Rs[si] = v0;
-                            Rs[si + plane] = v1;
-                            Rs[si + 2 * plane] = v2;
-                        }
-                        bf[col][Ln][0] = v0;
-                        bf[col][Ln][1] = v1;
-                        bf[col][Ln][2] = v2;
-                        rr += v0 * v0 + v1 * v1 + v2 * v2;
-                        float q0, q1, q2;
-                        block_solve<float>(B, v0, v1, v2, q0, q1, q2);
-                        zmax = fmaxf(zmax, fmaxf(fabsf(q0), fmaxf(fabsf(q1), fabsf(q2))));
-                        if (col == 0) {
-                            xj[Ln][0] = q0;
-                            xj[Ln][1] = q1;
-                            xj[Ln][2] = q2;
-                        }
-                    }
-                }
+            for (int k = 0; k < 3; ++k) bf[col][k] = make_float2(bv[0][k], bv[1][k]);
+            // the first Jacobi step z = D^{-1} b, both lanes
+            auto neg = [](float2 v) { return make_float2(-v.x, -v.y); };
+            const float2 b0 = bf[col][0], b1 = bf[col][1], b2 = bf[col][2];
+            const float2 y1 = __ffma2_rn(neg(f.l10), b0, b1);
+            const float2 y2 = __ffma2_rn(neg(f.l21), y1, __ffma2_rn(neg(f.l20), b0, b2));
+            const float2 q2 = __fmul2_rn(y2, f.i2);
+            const float2 q1 = __ffma2_rn(neg(f.l21), q2, __fmul2_rn(y1, f.i1));
+            const float2 q0 = __ffma2_rn(neg(f.l20), q2, __ffma2_rn(neg(f.l10), q1, __fmul2_rn(b0, f.i0)));
+            zmax = fmaxf(zmax, fmaxf(fmaxf(fabsf(q0.x), fabsf(q0.y)),
+                                     fmaxf(fmaxf(fabsf(q1.x), fabsf(q1.y)), fmaxf(fabsf(q2.x), fabsf(q2.y)))));
+            if (col == 0) {
+                xj[0] = q0;
+                xj[1] = q1;
+                xj[2] = q2;
             }
-            n.B.i0 = __floats2half2_rn(fac[0][0], fac[1][0]);
-            n.B.l10 = __floats2half2_rn(fac[0][1], fac[1][1]);
-            n.B.l20 = __floats2half2_rn(fac[0][2], fac[1][2]);
-            n.B.i1 = __floats2half2_rn(fac[0][3], fac[1][3]);
-            n.B.l21 = __floats2half2_rn(fac[0][4], fac[1][4]);
-            n.B.i2 = __floats2half2_rn(fac[0][5], fac[1][5]);
-            n.lew = __floats2half2_rn(lewf[0], lewf[1]);
-            n.lns = __floats2half2_rn(lnsf[0], lnsf[1]);
         }
         // the tile's scale: the largest entry of the first Jacobi step
         {
@@ -450,14 +537,15 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
 #pragma unroll
         for (int col = 0; col < 3; ++col) {
             PairState& n = ns[col];
-            n.b0 = __floats2half2_rn(bf[col][0][0] * scl, bf[col][1][0] * scl);
-            n.b1 = __floats2half2_rn(bf[col][0][1] * scl, bf[col][1][1] * scl);
-            n.b2 = __floats2half2_rn(bf[col][0][2] * scl, bf[col][1][2] * scl);
+            const float2 sc2 = make_float2(scl, scl), oj2 = make_float2(omj * scl, omj * scl);
+            n.b0 = __float22half2_rn(__fmul2_rn(bf[col][0], sc2));
+            n.b1 = __float22half2_rn(__fmul2_rn(bf[col][1], sc2));
+            n.b2 = __float22half2_rn(__fmul2_rn(bf[col][2], sc2));
             if (col == 0) {
                 // the first colour step from z = 0: (relaxed) block Jacobi
-                n.z0 = __floats2half2_rn(omj * xj[0][0] * scl, omj * xj[1][0] * scl);
-                n.z1 = __floats2half2_rn(omj * xj[0][1] * scl, omj * xj[1][1] * scl);
-                n.z2 = __floats2half2_rn(omj * xj[0][2] * scl, omj * xj[1][2] * scl);
+                n.z0 = __float22half2_rn(__fmul2_rn(xj[0], oj2));
+                n.z1 = __float22half2_rn(__fmul2_rn(xj[1], oj2));
+                n.z2 = __float22half2_rn(__fmul2_rn(xj[2], oj2));
             } else {
                 n.z0 = n.z1 = n.z2 = __float2half2_rn(0.f);
             }
@@ -490,7 +578,7 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
             }
         };
 // colour 1 (half of all visits) keeps its records in registers (set up above)
-#define OF_H2STEP(col, last)                                                  \
+#define OF_H2STEP(col, last, sync)                                            \
     {                                                                         \
         if (col == 1) {                                                       \
             pair_update(rec1, Zs, nz, RW, HPRW, om2, ns[1]);                  \
@@ -500,19 +588,21 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
             pair_update(e_, Zs, nz, RW, HPRW, om2, ns[col]);                  \
         }                                                                     \
         if (last) emit(ns[col]);                                              \
-        __syncthreads();                                                      \
+        if (sync) __syncthreads();                                            \
     }
-        OF_H2STEP(1, false)
-        OF_H2STEP(2, P.sweeps == 1)
-        OF_H2STEP(1, P.sweeps == 1)
+        OF_H2STEP(1, false, true)
+        OF_H2STEP(2, P.sweeps == 1, true)
+        OF_H2STEP(1, P.sweeps == 1, true)
         for (int sw = 1; sw < P.sweeps; ++sw) {
             const bool lastsw = (sw == P.sweeps - 1);
-            OF_H2STEP(0, false)
-            OF_H2STEP(1, false)
-            OF_H2STEP(2, lastsw)
-            OF_H2STEP(1, lastsw)
+            OF_H2STEP(0, false, true)
+            OF_H2STEP(1, false, true)
+            OF_H2STEP(2, lastsw, true)
+            OF_H2STEP(1, lastsw, true)
         }
-        OF_H2STEP(0, true)
+        // the last step's barrier is the next item's first one (or the one
+        // before the flush below)
+        OF_H2STEP(0, true, false)
 #undef OF_H2STEP
 
         const float wrr = warp_sum(rr), wrz = warp_sum(rz);
@@ -520,31 +610,30 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
             sh_red[threadIdx.x >> 5] = (double)wrr;
             sh_red[16 + (threadIdx.x >> 5)] = (double)wrz;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            const CUtensorMap* tm = P.tmaps + (size_t)pair * TM_PER_PAIR;
-            tma_store_3d(tm + TM_Z, x0, y0, 0, zo);
-            if (need_q) tma_store_3d(tm + TM_R, x0, y0, 0, Rs);
-            bulk_commit();
+        pend.pair = pair;
+        pend.x0 = x0;
+        pend.y0 = y0;
+        pend.w = ti.w;
+        pend.stage = s;
+        pend.need_q = need_q;
+        if (nstage == 1) {
+            // one stage: the store must leave it before the next item's loads
+            __syncthreads();
+            flush(pend);
+            pend.pair = -1;
         }
-        if (!P.apply_only && threadIdx.x < 32) {
-            const int l = threadIdx.x;
-            const bool w = l < (NT >> 5);
-            const double a2 = warp_sum(w ? sh_red[l] : 0.0), b2 = warp_sum(w ? sh_red[16 + l] : 0.0);
-            if (l == 0) {
-                P.partial[2 * (long long)ti.w] = a2;
-                P.partial[2 * (long long)ti.w + 1] = b2;
-            }
-        }
-        __syncthreads();
         t = tn;
         ti = tin;
         tn = tc;
+        cur = nxt;
         tin = tic;
         if (tn < P.ntiles && pair_done(tin.x)) tn = advance(tn + G, tin);
         if (nstage == 2) s ^= 1;
         else if (t < P.ntiles && threadIdx.x == 0) issue(ti, 0);
+    }
+    if (pend.pair >= 0) {
+        __syncthreads();
+        flush(pend);
     }
     if (threadIdx.x == 0) bulk_wait_all();
     if (P.apply_only || P.defer) return;
