@@ -384,14 +384,17 @@ def run_ours(args):
     # the model options built beyond the workload's configuration, on the same
     # pair and step: brightness constancy (no illumination unknown), K_sigma
     # pre-smoothing and K_rho integration (inside each step's of_set_frames),
-    # and K_sigma with the two-level preconditioner
+    # K_sigma with the two-level preconditioner, and overlapping subdomains
+    # (32 x 32 tiles extended by 8 nodes per side: 48 x 48, the largest
+    # extended tile one CTA holds, nearest to 64 x 64 tiles with overlap 8)
     variants = None
     if args.variant_steps > 0:
         variants = {}
         for name, extra, frames in (("model_constant", dict(model=1), None),
                                     ("sigma_1.5", dict(sigma=1.5), (f1, f2)),
                                     ("sigma_1.5_coarse_96", dict(sigma=1.5, coarse=96), (f1, f2)),
-                                    ("rho_1.5", dict(rho=1.5), (f1, f2))):
+                                    ("rho_1.5", dict(rho=1.5), (f1, f2)),
+                                    ("tile_32x32_overlap_8", dict(tile=(32, 32), overlap=8), None)):
             hv = make(dict(WORKLOAD_OPTS, **extra))
             step(hv, U, frames)
             infos.clear()

@@ -558,7 +558,7 @@ of_status run_solve(of_ctx* h, const of_solve_opts& o, const double* rhs, int* c
     const int chunk = h->prof ? 1 : 8;
     int errw = 0;  // device error word, read back with the scalars
     passes_out.assign(h->batch, 0);
-    CK(cudaMemsetAsync(h->cntA, 0, sizeof(unsigned) * h->batch, st));
+    CK(cudaMemsetAsync(h->cntA, 0, sizeof(unsigned) * (h->batch + h->nblk_total), st));
     CK(cudaMemsetAsync(h->cntS, 0, sizeof(unsigned) * h->batch, st));
     CK(cudaMemsetAsync(h->sc_dev, 0, sizeof(PairScalars) * h->batch, st));
     CK(cudaMemsetAsync(h->err_dev, 0, sizeof(int), st));
@@ -632,7 +632,7 @@ of_status run_ras(of_ctx* h, const of_solve_opts& o, int* cur_out, std::vector<i
     int cur = 0, errw = 0;
     iters_out.assign(h->batch, 0);
     h->ras_hist.assign(h->batch, std::vector<double>());
-    CK(cudaMemsetAsync(h->cntA, 0, sizeof(unsigned) * h->batch, st));
+    CK(cudaMemsetAsync(h->cntA, 0, sizeof(unsigned) * (h->batch + h->nblk_total), st));
     CK(cudaMemsetAsync(h->sc_dev, 0, sc_block_bytes(h->batch), st));
     for (int k = 0;; ++k) {
         NvtxRange nv_it("Schwarz iteration");
@@ -912,7 +912,8 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
     CK(dalloc(h, &h->partA, sizeof(double) * 2 * h->blocks.size()));
     CK(dalloc(h, &h->partS, sizeof(double) * 2 * h->tiles.size()));
     CK(dalloc(h, &h->etamax, sizeof(double) * batch));
-    CK(dalloc(h, &h->cntA, sizeof(unsigned) * batch));
+    // per pair, then per apply block (the group counters of the FP32 apply's reduction)
+    CK(dalloc(h, &h->cntA, sizeof(unsigned) * (batch + h->nblk_total)));
     CK(dalloc(h, &h->cntS, sizeof(unsigned) * batch));
     CK(dalloc(h, &h->staging, stage));
     h->staging_bytes = stage;
@@ -929,7 +930,7 @@ static of_status setup_grid_impl(of_handle h, int batch, const int32_t* W, const
     CK(cudaMemsetAsync(h->alpha, 0, 2 * fo * es, st));
     if (h->lamel) CK(ofl::fill2d(h->lamel, fp64 ? ofl::T_F64 : ofl::T_F32, 2 * fo, 1, 2 * fo, opt.lambda, st));
     CK(cudaMemsetAsync(h->sc_dev, 0, sizeof(PairScalars) * batch, st));
-    CK(cudaMemsetAsync(h->cntA, 0, sizeof(unsigned) * batch, st));
+    CK(cudaMemsetAsync(h->cntA, 0, sizeof(unsigned) * (batch + h->nblk_total), st));
     CK(cudaMemsetAsync(h->cntS, 0, sizeof(unsigned) * batch, st));
     CK(cudaMemsetAsync(h->err_dev, 0, sizeof(int), st));
     of_status s = encode_maps(h);

@@ -191,6 +191,7 @@ struct ApplyParams {
     PairScalars* sc;           // scalars written by the last block
     double* partial;           // [nblocks][2]
     unsigned* counter;         // [batch]
+    unsigned* gcounter;        // [blocks]: FP32 PCG apply, arrivals of each group of 32 blocks (at its first block)
     const C* f1; const C* f2; const C* alpha;
     const C* lamel;            // per-element lambda [H][pitch][2] like alpha, or null (the constant lam)
     R lam;
@@ -551,7 +552,7 @@ constexpr int A4_EXTRA = 8;  // floats of column X0 + 124 per stage: f1, f2, z0.
 __host__ __device__ constexpr int apply4_smem_bytes() { return A4_NS * (A4_NARR * 32 * 16 + A4_EXTRA * 4); }
 
 template <int MODE>
-__global__ void __launch_bounds__(32) k_apply4(const ApplyParams<float, float, float> P) {
+__global__ void __launch_bounds__(32, 16) k_apply4(const ApplyParams<float, float, float> P) {
     extern __shared__ float4 a4_ring[];
     const int4 bi = P.blocks[blockIdx.x];
     const int pair = bi.x;
@@ -760,28 +761,41 @@ __global__ void __launch_bounds__(32) k_apply4(const ApplyParams<float, float, f
         rcur = rnxt;
     }
     if (MODE == MODE_APPLY) return;
-    // warp partial (FP32 within the warp), then the pair's last block reduces
-    // the block partials in order in FP64
+    // p.q in two levels, so that no block reads more than one partial per
+    // lane and round: the warp partial (FP32 within the warp) goes to the
+    // block's slot; the last block of each group of 32 consecutive blocks sums
+    // the group's partials in order into the group slot (the odd slot of the
+    // group's first block); the pair's last group sums the group slots in
+    // order (double-float arithmetic throughout)
     const float s0 = warp_sum(acc);
     __shared__ int sh_last;
-    if (lane == 0) {
-        P.partial[2 * (long long)bi.w] = (double)s0;
-        P.partial[2 * (long long)bi.w + 1] = 0.0;
+    if (lane == 0) P.partial[2 * (long long)bi.w] = (double)s0;
+    const int g = (bi.w - pd.blk0) >> 5;
+    const int gfirst = pd.blk0 + 32 * g, gsize = min(32, pd.nblk - 32 * g);
+    if (!arrive_last(&P.gcounter[gfirst], (unsigned)gsize, &sh_last)) return;
+    {
+        const DF v = lane < gsize ? df_from_double(__ldcg(P.partial + 2 * (long long)(gfirst + lane))) : DF{0.f, 0.f};
+        const DF sg = df_warp_sum(v);
+        if (lane == 0) {
+            P.partial[2 * (long long)gfirst + 1] = df_to_double(sg);
+            P.gcounter[gfirst] = 0u;
+        }
     }
-    if (!arrive_last(&P.counter[pair], (unsigned)pd.nblk, &sh_last)) return;
-    double t0 = strided_sum8(P.partial + 2 * (long long)pd.blk0, pd.nblk, 2, lane, 32);
-    t0 = warp_sum(t0);
+    const int ngroups = (pd.nblk + 31) >> 5;
+    if (!arrive_last(&P.counter[pair], (unsigned)ngroups, &sh_last)) return;
+    PairScalars* s = P.sc + pair;
+    const double rz = s->rz;  // loaded alongside the group slots
+    const DF t0d = df_warp_sum(df_strided_sum<8>(P.partial + 2 * (long long)pd.blk0 + 1, ngroups, 64, lane, 32));
     if (lane == 0) {
-        PairScalars* s = P.sc + pair;
+        const double t0 = df_to_double(t0d);
         s->pq = t0;
-        if (!(t0 > 0.0) || !isfinite(t0) || !isfinite(s->rz)) {
+        if (!(t0 > 0.0) || !isfinite(t0) || !isfinite(rz)) {
             s->a = 0.0;
             s->done = 1;
             s->status = 6;
         } else {
-            s->a = s->rz / t0;
+            s->a = rz / t0;
         }
-        __threadfence();
         P.counter[pair] = 0u;
     }
 }

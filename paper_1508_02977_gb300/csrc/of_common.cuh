@@ -102,16 +102,19 @@ template <int NT> __device__ __forceinline__ double block_sum(double v, double* 
 // and bumps the pair counter; the block that sees count == n-1 reduces all
 // partials of the pair in index order (deterministic) and resets the
 // counter for the next launch.
+// The arrival is one acquire-release atomic at GPU scope by thread 0: its
+// release covers the block's writes (ordered before it by the barrier), its
+// acquire the other blocks' writes for every thread of the last block
+// (ordered after it by the second barrier).
 __device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned n, int* sh_flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned prev = atomicAdd(counter, 1u);
+        unsigned prev;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(prev) : "l"(counter), "r"(1u) : "memory");
         *sh_flag = (prev == n - 1) ? 1 : 0;
     }
     __syncthreads();
-    if (*sh_flag) { __threadfence(); return true; }
-    return false;
+    return *sh_flag != 0;
 }
 
 // Sum of n doubles (stride `stride`) in fixed order by one block.

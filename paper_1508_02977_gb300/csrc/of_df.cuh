@@ -118,6 +118,105 @@ struct Cvt<DF> {
     __device__ __forceinline__ static DF from(DF x) { return x; }
 };
 
+// ---- Fixed-order reductions of FP64 partial sums in double-float ----------
+// (the FP64 pipe of this GPU runs at a small fraction of the FP32 rate; the
+// partials are read with df_from_double, integer and FP32 instructions only)
+
+__device__ __forceinline__ DF df_warp_sum(DF v) {
+    for (int o = 16; o > 0; o >>= 1)
+        v = v + DF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    return v;
+}
+
+__device__ __forceinline__ double df_to_double(DF v) { return (double)v.hi + (double)v.lo; }
+
+// This thread's share of sum_i p[i * stride], i = t, t + nt, ... < n, in K
+// accumulators (element k of the share into accumulator k mod K, so that K
+// loads are in flight), combined in a fixed order.
+template <int K>
+__device__ __forceinline__ DF df_strided_sum(const double* p, int n, int stride, int t, int nt) {
+    DF a[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) a[u] = DF{0.f, 0.f};
+    int i = t;
+    for (; i + (K - 1) * nt < n; i += K * nt) {
+        double v[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u) v[u] = __ldcg(p + (long long)(i + u * nt) * stride);
+#pragma unroll
+        for (int u = 0; u < K; ++u) a[u] = a[u] + df_from_double(v[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < K - 1; ++u)
+        if (i + u * nt < n) a[u] = a[u] + df_from_double(__ldcg(p + (long long)(i + u * nt) * stride));
+#pragma unroll
+    for (int w = 1; w < K; w <<= 1)
+#pragma unroll
+        for (int u = 0; u + w < K; u += 2 * w) a[u] = a[u] + a[u + w];
+    return a[0];
+}
+
+// The sums of the two interleaved streams p[2 i] and p[2 i + 1], i < n (p
+// 16-byte aligned), in a fixed order by one block: per thread as in
+// df_strided_sum (K accumulators per stream, one 16-byte load per i), then a
+// fixed tree over each warp and over the warps.  Every thread of the block
+// calls it; the results are those of thread 0.  sh: 64 DF of shared memory,
+// free on entry.
+template <int K>
+__device__ __forceinline__ void df_ordered_sum2(const double* p, int n, double& s0, double& s1, DF* sh) {
+    const int nt = blockDim.x, t = threadIdx.x;
+    const double2* q = reinterpret_cast<const double2*>(p);
+    DF a[K], b[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) a[u] = b[u] = DF{0.f, 0.f};
+    int i = t;
+    for (; i + (K - 1) * nt < n; i += K * nt) {
+        double2 v[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u) v[u] = __ldcg(q + i + u * nt);
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            a[u] = a[u] + df_from_double(v[u].x);
+            b[u] = b[u] + df_from_double(v[u].y);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < K - 1; ++u)
+        if (i + u * nt < n) {
+            const double2 v = __ldcg(q + i + u * nt);
+            a[u] = a[u] + df_from_double(v.x);
+            b[u] = b[u] + df_from_double(v.y);
+        }
+#pragma unroll
+    for (int w = 1; w < K; w <<= 1)
+#pragma unroll
+        for (int u = 0; u + w < K; u += 2 * w) {
+            a[u] = a[u] + a[u + w];
+            b[u] = b[u] + b[u + w];
+        }
+    DF x = a[0], y = b[0];
+    x = df_warp_sum(x);
+    y = df_warp_sum(y);
+    const int w = t >> 5, l = t & 31;
+    __syncthreads();
+    if (l == 0) {
+        sh[w] = x;
+        sh[32 + w] = y;
+    }
+    __syncthreads();
+    if (t < 32) {
+        const int nw = (nt + 31) >> 5;
+        x = l < nw ? sh[l] : DF{0.f, 0.f};
+        y = l < nw ? sh[32 + l] : DF{0.f, 0.f};
+        x = df_warp_sum(x);
+        y = df_warp_sum(y);
+        if (t == 0) {
+            s0 = df_to_double(x);
+            s1 = df_to_double(y);
+        }
+    }
+}
+
 // A constant in type T, folded at compile time (x is a literal).
 template <typename T> __device__ __forceinline__ T kconst(double x) { return (T)x; }
 template <> __device__ __forceinline__ DF kconst<DF>(double x) {

@@ -75,6 +75,7 @@ static ApplyParams<R, C, RI> base_params(const SolveBufs& B) {
     P.sc = B.sc;
     P.partial = B.partA;
     P.counter = B.cntA;
+    P.gcounter = B.cntA + B.npairs;
     P.f1 = (const C*)B.f1;
     P.f2 = (const C*)B.f2;
     P.alpha = (const C*)B.alpha;

@@ -31,6 +31,7 @@
 #pragma once
 #include <cuda_fp16.h>
 
+#include "of_df.cuh"
 #include "of_schwarz.cuh"
 
 namespace ofk {
@@ -278,9 +279,10 @@ __device__ __forceinline__ void pair_store(__half2* __restrict__ Z, int zp, int 
 template <int TXC, int TYC, int OVC>
 __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ double sh_red[32];
+    __shared__ DF sh_red[64];
     __shared__ float sh_max[16];
-    __shared__ int sh_last, sh_fail;
+    __shared__ float sh_part[32];  // per-warp r.r (0..15) and r.z (16..31) of the pending item
+    __shared__ int sh_last, sh_fail, sh_more;
     const int NT = blockDim.x;
     const int Tx = TXC ? TXC : P.Tx, Ty = TXC ? TYC : P.Ty, ov = TXC ? OVC : P.ov;
     const int RW = sch_rw(Tx, ov), HP = h2_hp(Ty, ov), cpad = sch_cpad(ov);
@@ -341,6 +343,9 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
     uint32_t tab[3];
 #pragma unroll
     for (int col = 0; col < 3; ++col) tab[col] = P.ntab[col * NT + threadIdx.x];
+    const float hl = 0.5f * (float)P.lam;
+    const float om = (float)P.omega;
+    const __half2 om2 = __float2half2_rn(om);
 
     // the pair's size and the step a of a work item, read one item ahead
     struct ItemScalars {
@@ -351,7 +356,10 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
         ItemScalars r;
         r.W = P.pairs[w.x].W;
         r.H = P.pairs[w.x].H;
-        r.a = (!P.first && !P.apply_only) ? (float)P.sc[w.x].a : 0.f;
+        // one FP64 conversion per warp (the FP64 pipe is narrow), broadcast
+        float a = 0.f;
+        if ((threadIdx.x & 31) == 0 && !P.first && !P.apply_only) a = (float)P.sc[w.x].a;
+        r.a = __shfl_sync(0xffffffffu, a, 0);
         return r;
     };
     // the store of an item's z (and updated r) and its partial sums run after
@@ -372,14 +380,16 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
             if (q.need_q) tma_store_3d(tm + TM_R, q.x0, q.y0, 0, sq + L.rs);
             bulk_commit();
         }
-        // per-warp sums of r.r and r.z in fixed order (warp 1: thread 0 issues the stores)
+        // the item's r.r and r.z from the per-warp sums in fixed order, in
+        // FP32 (the FP64 pipe is narrow; the items' partials are summed in
+        // FP64) (warp 1: thread 0 issues the stores)
         if (!P.apply_only && (threadIdx.x >> 5) == 1) {
             const int l = threadIdx.x & 31;
             const bool w = l < (NT >> 5);
-            const double a2 = warp_sum(w ? sh_red[l] : 0.0), b2 = warp_sum(w ? sh_red[16 + l] : 0.0);
+            const float a2 = warp_sum(w ? sh_part[l] : 0.f), b2 = warp_sum(w ? sh_part[16 + l] : 0.f);
             if (l == 0) {
-                P.partial[2 * (long long)q.w] = a2;
-                P.partial[2 * (long long)q.w + 1] = b2;
+                P.partial[2 * (long long)q.w] = (double)a2;
+                P.partial[2 * (long long)q.w + 1] = (double)b2;
             }
         }
     };
@@ -425,8 +435,6 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
         const int ey0 = max(y0 - ov, 0), ey1 = min(y0 + th + ov, H);
         const bool need_q = !P.first && !P.apply_only;
         const float a = cur.a;
-        const float hl = 0.5f * (float)P.lam;
-        const float om = (float)P.omega;
         const int plane = Tx * Ty;
         // ---- setup in FP32, both lanes of a pair at once in packed (float2)
         // arithmetic: diagonal blocks and their LDL^T factors, right-hand sides
@@ -557,7 +565,6 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
         // ---- sweeps (colour order 0,1,2,1,0,...,0; the first 0 was the Jacobi
         // step above); the last visit of each colour writes the owned z,
         // scaled back, into this stage's q buffer and accumulates r.z in FP32
-        const __half2 om2 = __float2half2_rn(om);
         float rz = 0.f;
         float* zo = reinterpret_cast<float*>(st + L.qs);
         auto emit = [&](const PairState& n) {
@@ -607,8 +614,8 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
 
         const float wrr = warp_sum(rr), wrz = warp_sum(rz);
         if ((threadIdx.x & 31) == 0) {
-            sh_red[threadIdx.x >> 5] = (double)wrr;
-            sh_red[16 + (threadIdx.x >> 5)] = (double)wrz;
+            sh_part[threadIdx.x >> 5] = wrr;
+            sh_part[16 + (threadIdx.x >> 5)] = wrz;
         }
         pend.pair = pair;
         pend.x0 = x0;
@@ -638,24 +645,58 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
     if (threadIdx.x == 0) bulk_wait_all();
     if (P.apply_only || P.defer) return;
     if (!arrive_last(P.counter, gridDim.x, &sh_last)) return;
-    for (int pi = 0; pi < P.npairs; ++pi) {
-        PairScalars* sp = P.sc + pi;
-        if (sp->done) continue;
-        const PairDesc pd = P.pairs[pi];
-        const int ntp = pd.tiles_x * pd.tiles_y;
-        const double t_rr = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0, ntp, 2, sh_red);
-        const double t_rz = ordered_sum_rt(P.partial + 2 * (long long)pd.tile0 + 1, ntp, 2, sh_red);
-        if (threadIdx.x == 0) precond_finalize(sp, t_rr, t_rz, P.first);
+    // the last CTA: r.r and r.z of each pair from its items' partials (fixed
+    // order, double-float), the pair's CG scalars, the loop condition.  The
+    // scalars and the error word are read before the partials so that their
+    // loads overlap; no other CTA of this launch writes them any more.
+    const int err_now = (threadIdx.x == 0) ? *(volatile int*)P.err : 0;
+    if (P.npairs == 1) {
+        PairScalars s0;
+        if (threadIdx.x == 0) s0 = P.sc[0];
+        double t_rr = 0.0, t_rz = 0.0;
+        df_ordered_sum2<4>(P.partial, P.pairs[0].tiles_x * P.pairs[0].tiles_y, t_rr, t_rz, sh_red);
+        if (threadIdx.x == 0) {
+            if (!s0.done) {
+                precond_finalize(&s0, t_rr, t_rz, P.first);
+                P.sc[0] = s0;
+            }
+            sh_more = s0.done ? 0 : 1;  // another iteration
+        }
+    } else {
+        // one warp per pair
+        if (threadIdx.x == 0) sh_more = 0;
+        __syncthreads();
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = NT >> 5;
+        for (int pi = w; pi < P.npairs; pi += nw) {
+            PairScalars* sp = P.sc + pi;
+            if (sp->done) continue;
+            const PairDesc pd = P.pairs[pi];
+            const int ntp = pd.tiles_x * pd.tiles_y;
+            const double2* q = reinterpret_cast<const double2*>(P.partial) + pd.tile0;
+            DF a0{0.f, 0.f}, a1{0.f, 0.f}, b0{0.f, 0.f}, b1{0.f, 0.f};
+            int i = l;
+            for (; i + 32 < ntp; i += 64) {
+                const double2 u = __ldcg(q + i), v = __ldcg(q + i + 32);
+                a0 = a0 + df_from_double(u.x);
+                b0 = b0 + df_from_double(u.y);
+                a1 = a1 + df_from_double(v.x);
+                b1 = b1 + df_from_double(v.y);
+            }
+            if (i < ntp) {
+                const double2 u = __ldcg(q + i);
+                a0 = a0 + df_from_double(u.x);
+                b0 = b0 + df_from_double(u.y);
+            }
+            const DF x = df_warp_sum(a0 + a1), y = df_warp_sum(b0 + b1);
+            if (l == 0) {
+                precond_finalize(sp, df_to_double(x), df_to_double(y), P.first);
+                if (!sp->done) atomicOr(&sh_more, 1);
+            }
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        if (P.use_cond) {
-            int more = 0;
-            for (int pi = 0; pi < P.npairs; ++pi) more |= !P.sc[pi].done;
-            if (*(volatile int*)P.err) more = 0;
-            cudaGraphSetConditional(P.cond, more ? 1u : 0u);
-        }
-        __threadfence();
+        if (P.use_cond) cudaGraphSetConditional(P.cond, (sh_more && !err_now) ? 1u : 0u);
         *P.counter = 0u;
     }
 }
