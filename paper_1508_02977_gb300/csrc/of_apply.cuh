@@ -214,12 +214,14 @@ struct ApplyParams {
     int* err;           // device error word (index checks of the bounds-check build)
 };
 
-template <typename R, typename C, typename RI, int MODE, bool WANT_B, int NW, typename T = R, bool ELD = false>
+template <typename R, typename C, typename RI, int MODE, bool WANT_B, int NW, typename T = R, bool ELD = false,
+          bool LAM = true>
 __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P) {
     // R: storage type of in/out (and of the PCG scalars); T: arithmetic of
     // the element contributions (R itself, or double-float for the residual
     // of the FP32 path); ELD: element data from the K_rho planes instead of
-    // the frames
+    // the frames; LAM: a per-element lambda may be set (false: the constant
+    // lambda only, without the registers of that branch)
     constexpr int NT = NW * 32;
     __shared__ double sh_red[NT / 32];
     __shared__ int sh_last;
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
             if (owner && P.out) {
                 R* xn = P.out + vo;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) xn[o + c * plane] = (R)X[c].hi + (R)X[c].lo;
+                for (int c = 0; c < 3; ++c) xn[o + c * plane] = df_to_double_bits(X[c]);
             }
             v.p = v3(X[0], X[1], X[2]);
             return v;
@@ -384,7 +386,7 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
             }
             square_contrib_el<T, WANT_B || IS_RES, MODE != MODE_RESB>(cur.p, ncur.p, nnxt.p, nxt.p, al0, al1, lam, e0,
                                                                       e1, valid, cA, cB, cC, cD, bA, bB, bC, bD);
-        } else if (P.lamel) {
+        } else if (LAM && P.lamel) {
             const C* la = P.lamel + 2 * pd.frame_off;
             const T la0 = valid ? Cvt<T>::from(la[2 * ((long long)sy * pitch + cx)]) : zero;
             const T la1 = valid ? Cvt<T>::from(la[2 * ((long long)sy * pitch + cx) + 1]) : zero;
@@ -438,6 +440,12 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
     double s0, s1 = 0.0;
     if constexpr (MODE == MODE_PCG) {
         s0 = block_sum<NT>((double)acc, sh_red);
+    } else if constexpr (std::is_same<T, DF>::value) {
+        // double-float block sums (the FP64 pipe is narrow), one conversion
+        const DF r2 = df_block_sum<NT>(acc_r, reinterpret_cast<DF*>(sh_red));
+        const DF b2 = df_block_sum<NT>(acc_b, reinterpret_cast<DF*>(sh_red));
+        s0 = threadIdx.x == 0 ? df_to_double(r2) : 0.0;
+        s1 = threadIdx.x == 0 ? df_to_double(b2) : 0.0;
     } else {
         s0 = block_sum<NT>(Cvt<double>::from(acc_r), sh_red);
         s1 = block_sum<NT>(Cvt<double>::from(acc_b), sh_red);

@@ -130,6 +130,54 @@ __device__ __forceinline__ DF df_warp_sum(DF v) {
 
 __device__ __forceinline__ double df_to_double(DF v) { return (double)v.hi + (double)v.lo; }
 
+// hi + lo as a double from the bits of the two floats, with integer
+// instructions.  hi = (-1)^s m_h 2^(e_h - 150) with a 24-bit m_h; in units of
+// 2^(e_h - 179) it is m_h 2^29, a 53-bit significand, and lo (|lo| <= ulp(hi)
+// / 2, so e_l <= e_h - 24) is m_l 2^(e_l - e_h + 29), added with its sign
+// (the bits of lo below the unit are dropped: an error below 2^-52 |hi|, far
+// under the 2^-46 of the double-float itself).  The sum lies in [2^52 - 2^28,
+// 2^53); below 2^52 it is shifted up one place.  A zero hi gives zero; a
+// subnormal, infinite or NaN hi, or a lo that is not a normal float or zero,
+// takes the FP64 route.
+__device__ __forceinline__ double df_to_double_bits(DF v) {
+    const unsigned uh = __float_as_uint(v.hi), ul = __float_as_uint(v.lo);
+    const int eh = (int)((uh >> 23) & 0xffu), el = (int)((ul >> 23) & 0xffu);
+    const bool lo_zero = (ul << 1) == 0u;
+    if ((uh << 1) == 0u) return 0.0;
+    if (eh == 0 || eh == 0xff || (!lo_zero && (el == 0 || el == 0xff))) return df_to_double(v);
+    long long M = (long long)((uh & 0x7fffffu) | 0x800000u) << 29;
+    if (!lo_zero) {
+        const long long ml = (long long)((ul & 0x7fffffu) | 0x800000u);
+        const int sh = el - eh + 29;
+        const long long add = sh >= 0 ? (ml << sh) : (sh > -25 ? (ml >> (-sh)) : 0LL);
+        M = ((uh ^ ul) >> 31) ? M - add : M + add;
+    }
+    int e = eh - 127 + 1023;
+    if (M < (1LL << 52)) {
+        M <<= 1;
+        e -= 1;
+    }
+    const unsigned long long bits = ((unsigned long long)(uh >> 31) << 63) | ((unsigned long long)e << 52) |
+                                    ((unsigned long long)M & 0xfffffffffffffULL);
+    return __longlong_as_double((long long)bits);
+}
+
+// Deterministic block sum of one double-float per thread (fixed tree order);
+// the result is valid in thread 0.  sh: NT / 32 DF of shared memory.
+template <int NT> __device__ __forceinline__ DF df_block_sum(DF v, DF* sh) {
+    v = df_warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    DF s{0.f, 0.f};
+    if (threadIdx.x < 32) {
+        s = (l < NT / 32) ? sh[l] : DF{0.f, 0.f};
+        s = df_warp_sum(s);
+    }
+    return s;
+}
+
 // This thread's share of sum_i p[i * stride], i = t, t + nt, ... < n, in K
 // accumulators (element k of the share into accumulator k mod K, so that K
 // loads are in flight), combined in a fixed order.

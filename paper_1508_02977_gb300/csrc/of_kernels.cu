@@ -110,10 +110,13 @@ static cudaError_t residual_t(const SolveBufs& B, const double* xin, double* xou
     if (B.eld) {
         if (xin) k_apply<double, C, RI, MODE_RES, false, APPLY_NW, T, true><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
         else k_apply<double, C, RI, MODE_RESB, false, APPLY_NW, T, true><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+    } else if (B.lamel) {
+        if (xin) k_apply<double, C, RI, MODE_RES, false, APPLY_NW, T><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+        else k_apply<double, C, RI, MODE_RESB, false, APPLY_NW, T><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
     } else if (xin) {
-        k_apply<double, C, RI, MODE_RES, false, APPLY_NW, T><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+        k_apply<double, C, RI, MODE_RES, false, APPLY_NW, T, false, false><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
     } else {
-        k_apply<double, C, RI, MODE_RESB, false, APPLY_NW, T><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+        k_apply<double, C, RI, MODE_RESB, false, APPLY_NW, T, false, false><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
     }
     return cudaGetLastError();
 }
@@ -375,7 +378,7 @@ static cudaError_t pcg_apply_t(const SolveBufs& B, cudaStream_t st) {
     if (B.eld) k_apply<R, R, R, MODE_PCG, false, APPLY_NW, R, true><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
     else if (B.lamel) k_apply<R, R, R, MODE_PCG, false, APPLY_NW><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);  // per-element lambda
     else if constexpr (sizeof(R) == 4) k_apply4<MODE_PCG><<<B.nblk, 32, apply4_smem_bytes(), st>>>(P);  // FP32: four columns per lane
-    else k_apply<R, R, R, MODE_PCG, false, APPLY_NW><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+    else k_apply<R, R, R, MODE_PCG, false, APPLY_NW, R, false, false><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
     return cudaGetLastError();
 }
 
@@ -401,7 +404,7 @@ static cudaError_t apply_t(const SolveBufs& B, int blk0, int nblk, const void* p
     } else if (b) k_apply<R, R, R, MODE_APPLY, true, APPLY_NW><<<nblk, APPLY_NW * 32, 0, st>>>(P);
     else if (B.lamel) k_apply<R, R, R, MODE_APPLY, false, APPLY_NW><<<nblk, APPLY_NW * 32, 0, st>>>(P);
     else if constexpr (sizeof(R) == 4) k_apply4<MODE_APPLY><<<nblk, 32, apply4_smem_bytes(), st>>>(P);
-    else k_apply<R, R, R, MODE_APPLY, false, APPLY_NW><<<nblk, APPLY_NW * 32, 0, st>>>(P);
+    else k_apply<R, R, R, MODE_APPLY, false, APPLY_NW, R, false, false><<<nblk, APPLY_NW * 32, 0, st>>>(P);
     return cudaGetLastError();
 }
 
