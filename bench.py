@@ -337,9 +337,10 @@ def run_ours(args):
         roofline["schwarz_issue"] = {"warp_inst_per_px": ipx, "achieved_winst_per_s": ipx * px / t,
                                      "peak_winst_per_s": issue_peak, "frac": ipx * px / t / issue_peak}
     if dom == "schwarz":
-        roofline["note"] = ("the preconditioner's block-SOR sweeps run in shared memory: bound by instruction "
-                            "latency at 12 warps per SM (ncu: issue active 50 %, L1/shared 46 %) and shared-memory "
-                            "wavefronts, not by HBM; per_kernel gives the apply's HBM rate")
+        roofline["note"] = ("the preconditioner's FP16 block-SOR sweeps run in shared memory: bound by each warp's "
+                            "dependent update chain at 12 warps per SM (ncu: issue active 41 %, L1/shared 43 %, "
+                            "12 cycles of barrier wait per colour step), not by HBM; schwarz_issue gives the "
+                            "instruction rate against the issue peak, per_kernel the apply's HBM rate")
 
     # end to end through the C ABI with host buffers (pinned)
     f1h = torch.from_numpy(p.f1).pin_memory()
