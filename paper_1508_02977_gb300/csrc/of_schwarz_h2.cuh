@@ -371,6 +371,19 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
     };
     Pending pend;
     pend.pair = -1;
+    // Unless a coarse level reads the items' partials: one partial per pair
+    // and CTA, the sum over the CTA's items of the pair (in their order, in
+    // double-float), in the slot of the CTA's first item of the pair.  The
+    // CTA with index c takes the items c, c + G, c + 2G, ... (done pairs
+    // skipped), so a pair's slots are its first min(items, G) item indices
+    // and the last CTA sums at most G values per pair.
+    const bool per_cta = !P.defer;
+    DF cta_rr{0.f, 0.f}, cta_rz{0.f, 0.f};
+    int cta_pair = -1, cta_slot = 0;
+    auto cta_write = [&]() {
+        P.partial[2 * (long long)cta_slot] = df_to_double(cta_rr);
+        P.partial[2 * (long long)cta_slot + 1] = df_to_double(cta_rz);
+    };
     auto flush = [&](const Pending& q) {
         unsigned char* sq = base + L.stage0 + (size_t)q.stage * L.stage_bytes;
         if (threadIdx.x == 0) {
@@ -381,15 +394,29 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
             bulk_commit();
         }
         // the item's r.r and r.z from the per-warp sums in fixed order, in
-        // FP32 (the FP64 pipe is narrow; the items' partials are summed in
-        // FP64) (warp 1: thread 0 issues the stores)
+        // FP32 (the FP64 pipe is narrow) (warp 1: thread 0 issues the
+        // stores); with one pair they are summed over the CTA's items (in
+        // double-float, in the items' order) and written once at the end
         if (!P.apply_only && (threadIdx.x >> 5) == 1) {
             const int l = threadIdx.x & 31;
             const bool w = l < (NT >> 5);
             const float a2 = warp_sum(w ? sh_part[l] : 0.f), b2 = warp_sum(w ? sh_part[16 + l] : 0.f);
             if (l == 0) {
-                P.partial[2 * (long long)q.w] = (double)a2;
-                P.partial[2 * (long long)q.w + 1] = (double)b2;
+                if (per_cta) {
+                    if (q.pair != cta_pair) {
+                        if (cta_pair >= 0) cta_write();
+                        cta_pair = q.pair;
+                        cta_slot = q.w;
+                        cta_rr = DF{a2, 0.f};
+                        cta_rz = DF{b2, 0.f};
+                    } else {
+                        cta_rr = cta_rr + DF{a2, 0.f};
+                        cta_rz = cta_rz + DF{b2, 0.f};
+                    }
+                } else {
+                    P.partial[2 * (long long)q.w] = (double)a2;
+                    P.partial[2 * (long long)q.w + 1] = (double)b2;
+                }
             }
         }
     };
@@ -642,6 +669,7 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
         __syncthreads();
         flush(pend);
     }
+    if (per_cta && !P.apply_only && threadIdx.x == 32 && cta_pair >= 0) cta_write();
     if (threadIdx.x == 0) bulk_wait_all();
     if (P.apply_only || P.defer) return;
     if (!arrive_last(P.counter, gridDim.x, &sh_last)) return;
@@ -654,7 +682,7 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
         PairScalars s0;
         if (threadIdx.x == 0) s0 = P.sc[0];
         double t_rr = 0.0, t_rz = 0.0;
-        df_ordered_sum2<4>(P.partial, P.pairs[0].tiles_x * P.pairs[0].tiles_y, t_rr, t_rz, sh_red);
+        df_ordered_sum2<4>(P.partial, min(P.ntiles, (int)gridDim.x), t_rr, t_rz, sh_red);  // the CTAs' partials
         if (threadIdx.x == 0) {
             if (!s0.done) {
                 precond_finalize(&s0, t_rr, t_rz, P.first);
@@ -671,7 +699,7 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
             PairScalars* sp = P.sc + pi;
             if (sp->done) continue;
             const PairDesc pd = P.pairs[pi];
-            const int ntp = pd.tiles_x * pd.tiles_y;
+            const int ntp = min(pd.tiles_x * pd.tiles_y, (int)gridDim.x);  // the pair's CTA partials
             const double2* q = reinterpret_cast<const double2*>(P.partial) + pd.tile0;
             DF a0{0.f, 0.f}, a1{0.f, 0.f}, b0{0.f, 0.f}, b1{0.f, 0.f};
             int i = l;
