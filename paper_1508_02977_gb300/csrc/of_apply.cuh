@@ -44,10 +44,10 @@ __device__ __forceinline__ void square_contrib(const NodeVal<R>& A, const NodeVa
                                                const NodeVal<R>& D, R al0, R al1, R lam, R gms, bool valid,
                                                V3<R>& cA, V3<R>& cB, V3<R>& cC, V3<R>& cD,
                                                V3<R>& bA, V3<R>& bB, V3<R>& bC, V3<R>& bD) {
-    const R third = kconst<R>(1.0 / 3.0);
-    const R w24 = kconst<R>(1.0 / 24.0);
-    const R h = kconst<R>(OF_STIFF_HALF);
-    const R zero = kconst<R>(0.0);
+    constexpr R third = kconst<R>(1.0 / 3.0);
+    constexpr R w24 = kconst<R>(1.0 / 24.0);
+    constexpr R h = kconst<R>(OF_STIFF_HALF);
+    constexpr R zero = kconst<R>(0.0);
     // ---- t = 0: A, B, C
     R g0x = B.f2 - A.f2, g0y = C.f2 - B.f2, g0m = -(A.f1 + B.f1 + C.f1) * third * gms;
     R g1x = C.f2 - D.f2, g1y = D.f2 - A.f2, g1m = -(A.f1 + D.f1 + C.f1) * third * gms;
@@ -85,7 +85,7 @@ __device__ __forceinline__ void square_contrib(const NodeVal<R>& A, const NodeVa
     cD.c = vD * g1m - l0 * (dAD.c + dCD.c);
     }
     if constexpr (WANT_B) {
-        const R sixth = kconst<R>(1.0 / 6.0);
+        constexpr R sixth = kconst<R>(1.0 / 6.0);
         R ft0 = ((A.f2 - A.f1) + (B.f2 - B.f1) + (C.f2 - C.f1)) * third;
         R ft1 = ((A.f2 - A.f1) + (D.f2 - D.f1) + (C.f2 - C.f1)) * third;
         R k0 = -sixth * ft0, k1 = -sixth * ft1;
@@ -106,11 +106,11 @@ __device__ __forceinline__ void square_contrib_l(const NodeVal<R>& A, const Node
                                                  const NodeVal<R>& D, R al0, R al1, R lam0, R lam1, R gms, bool valid,
                                                  V3<R>& cA, V3<R>& cB, V3<R>& cC, V3<R>& cD,
                                                  V3<R>& bA, V3<R>& bB, V3<R>& bC, V3<R>& bD) {
-    const R zero = kconst<R>(0.0);
+    constexpr R zero = kconst<R>(0.0);
     square_contrib<R, WANT_B, WANT_A>(A, B, C, D, al0, al1, zero, gms, valid, cA, cB, cC, cD, bA, bB, bC, bD);
     if constexpr (WANT_A) {
         if (valid) {
-            const R h = kconst<R>(OF_STIFF_HALF);
+            constexpr R h = kconst<R>(OF_STIFF_HALF);
             const R l0 = h * lam0, l1 = h * lam1;
             const R dAB = A.p.c - B.p.c, dCB = C.p.c - B.p.c, dAD = A.p.c - D.p.c, dCD = C.p.c - D.p.c;
             cA.c = cA.c + (l0 * dAB + l1 * dAD);
@@ -134,9 +134,9 @@ __device__ __forceinline__ void square_contrib_el(const V3<R>& pA, const V3<R>& 
                                                   R al0, R al1, R lam, const R (&e0)[9], const R (&e1)[9], bool valid,
                                                   V3<R>& cA, V3<R>& cB, V3<R>& cC, V3<R>& cD, V3<R>& bA,
                                                   V3<R>& bB, V3<R>& bC, V3<R>& bD) {
-    const R w24 = kconst<R>(1.0 / 24.0);
-    const R h = kconst<R>(OF_STIFF_HALF);
-    const R zero = kconst<R>(0.0);
+    constexpr R w24 = kconst<R>(1.0 / 24.0);
+    constexpr R h = kconst<R>(OF_STIFF_HALF);
+    constexpr R zero = kconst<R>(0.0);
     if constexpr (!WANT_A) {
         cA = cB = cC = cD = v3(zero, zero, zero);
     } else {
@@ -172,7 +172,7 @@ __device__ __forceinline__ void square_contrib_el(const V3<R>& pA, const V3<R>& 
         cD.c = vD.c - l0 * (dAD.c + dCD.c);
     }
     if constexpr (WANT_B) {
-        const R sixth = kconst<R>(1.0 / 6.0);
+        constexpr R sixth = kconst<R>(1.0 / 6.0);
         V3<R> b0 = v3(sixth * e0[6], sixth * e0[7], sixth * e0[8]);
         V3<R> b1 = v3(sixth * e1[6], sixth * e1[7], sixth * e1[8]);
         bA = b0 + b1; bB = b0; bC = b0 + b1; bD = b1;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
     const bool out_col = (lane < 31) && (cx + 1 < W);
     const T lam = Cvt<T>::from(P.lam);
     const T gms = Cvt<T>::from(P.gms);
-    const T zero = kconst<T>(0.0);
+    constexpr T zero = kconst<T>(0.0);
 
     // load node (x, y) of the input vector + frames, with the mode's fused
     // update; side effects (p_new, d, x_new) only for owned nodes

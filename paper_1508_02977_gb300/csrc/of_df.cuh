@@ -53,6 +53,12 @@ __device__ __forceinline__ DF df_from_double_fp64(double x) {
     return DF{h, __double2float_rn(x - (double)h)};
 }
 
+// Out-of-line forms of the FP64 routes below, for the rare inputs they
+// serve: inlined, the compiler may execute them under a predicate for every
+// input, which puts FP64 instructions on every call.
+static __device__ __noinline__ DF df_from_double_slow(double x) { return df_from_double_fp64(x); }
+static __device__ __noinline__ float f32_from_double_slow(double x) { return __double2float_rn(x); }
+
 // The same from the bits of x with integer and FP32 instructions (the
 // double <-> float conversions and the subtraction above run on the FP64
 // pipe, a small fraction of the FP32 rate on this GPU).  x = (-1)^s 1.m 2^e
@@ -67,7 +73,7 @@ __device__ __forceinline__ DF df_from_double(double x) {
     const unsigned s = (unsigned)(b >> 63);
     const int E = (int)((b >> 52) & 0x7ffULL);
     if ((b << 1) == 0ULL) return DF{s ? -0.0f : 0.0f, 0.0f};
-    if (E < 960 || E > 1150) return df_from_double_fp64(x);
+    if (E < 960 || E > 1150) return df_from_double_slow(x);
     const unsigned long long m = (b & 0xfffffffffffffULL) | (1ULL << 52);
     const unsigned top = (unsigned)(m >> 29);              // 24 bits, bit 23 the implicit one
     const unsigned rest = (unsigned)(m & 0x1fffffffULL);   // 29 bits
@@ -91,7 +97,7 @@ __device__ __forceinline__ float f32_from_double(double x) {
     const unsigned s = (unsigned)(b >> 63);
     const int E = (int)((b >> 52) & 0x7ffULL);
     if ((b << 1) == 0ULL) return s ? -0.0f : 0.0f;
-    if (E < 1023 - 126 || E > 1023 + 127) return __double2float_rn(x);
+    if (E < 1023 - 126 || E > 1023 + 127) return f32_from_double_slow(x);
     const unsigned long long m = b & 0xfffffffffffffULL;   // 52 fraction bits
     const unsigned top = (unsigned)(m >> 29);               // 23 fraction bits kept
     const unsigned rest = (unsigned)(m & 0x1fffffffULL);    // 29 bits dropped
@@ -129,6 +135,7 @@ __device__ __forceinline__ DF df_warp_sum(DF v) {
 }
 
 __device__ __forceinline__ double df_to_double(DF v) { return (double)v.hi + (double)v.lo; }
+static __device__ __noinline__ double df_to_double_slow(DF v) { return df_to_double(v); }
 
 // hi + lo as a double from the bits of the two floats, with integer
 // instructions.  hi = (-1)^s m_h 2^(e_h - 150) with a 24-bit m_h; in units of
@@ -144,7 +151,7 @@ __device__ __forceinline__ double df_to_double_bits(DF v) {
     const int eh = (int)((uh >> 23) & 0xffu), el = (int)((ul >> 23) & 0xffu);
     const bool lo_zero = (ul << 1) == 0u;
     if ((uh << 1) == 0u) return 0.0;
-    if (eh == 0 || eh == 0xff || (!lo_zero && (el == 0 || el == 0xff))) return df_to_double(v);
+    if (eh == 0 || eh == 0xff || (!lo_zero && (el == 0 || el == 0xff))) return df_to_double_slow(v);
     long long M = (long long)((uh & 0x7fffffu) | 0x800000u) << 29;
     if (!lo_zero) {
         const long long ml = (long long)((ul & 0x7fffffu) | 0x800000u);
@@ -265,11 +272,11 @@ __device__ __forceinline__ void df_ordered_sum2(const double* p, int n, double& 
     }
 }
 
-// A constant in type T, folded at compile time (x is a literal).
-template <typename T> __device__ __forceinline__ T kconst(double x) { return (T)x; }
-template <> __device__ __forceinline__ DF kconst<DF>(double x) {
-    const float h = (float)x;
-    return DF{h, (float)(x - (double)h)};
+// A constant in type T, evaluated by the compiler (the callers bind it to a
+// constexpr variable, so that no FP64 instruction forms it at run time).
+template <typename T> __host__ __device__ constexpr T kconst(double x) { return (T)x; }
+template <> __host__ __device__ constexpr DF kconst<DF>(double x) {
+    return DF{(float)x, (float)(x - (double)(float)x)};
 }
 
 }  // namespace ofk

@@ -505,6 +505,35 @@ def test_batch_of_mixed_sizes_equals_single_solves(S):
             S.of_destroy(h)
 
 
+@pytest.mark.parametrize("tile", [(48, 48), (32, 16)])
+def test_mixed_refinement_reaches_fp64_accuracy(S, oracle, tile):
+    """Iterative refinement on the FP32 path keeps x in double-float (x + d +
+    a p formed in double-float, stored as FP64 built from the two floats'
+    bits): solved to rtol 1e-12, the oracle's FP64 residual of the result is
+    <= 1e-9, three orders below what an x held to FP32 precision (~6e-8
+    relative, with terms of A x ~1e3 times b on this scene) could reach; the
+    residual the GPU reports agrees to the double-float floor (2^-46 times
+    the sum of the magnitudes of the terms, ~1e-11 of b here).  48 x 48 tiles
+    run the FP16 paired sweeps, 32 x 16 the FP32 sweeps."""
+    p = synth.blobs()
+    f1, f2 = f32(p.f1), f32(p.f2)
+    sysm = oracle.System.from_frames(f1, f2, p.alpha0, p.lam)
+    Ud = sysm.solve_direct()
+    h = handle(S, [(p.W, p.H)], tile=tile, overlap=0, sweeps=4, omega=1.6, precision=S.OF_PREC_MIXED)
+    try:
+        S.of_set_frames(h, 0, dev(f1, torch.float32), dev(f2, torch.float32))
+        S.of_set_alpha(h, 0, None, p.alpha0)
+        U = torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda")
+        st, info = S.of_solve(h, [U], rtol=1e-12, max_outer=12)
+        U = U.cpu().numpy()
+    finally:
+        S.of_destroy(h)
+    rr = sysm.rel_residual(U)
+    assert rr <= 1e-9, (rr, info)
+    assert abs(rr - info[0]["rel_residual"]) <= 1e-10, (rr, info)
+    assert np.linalg.norm(U - Ud) <= 1e-6 * np.linalg.norm(Ud), info
+
+
 def test_host_buffers_round_trip(S, oracle):
     """Host (numpy) inputs and outputs go through the same path."""
     W, H = 40, 30
