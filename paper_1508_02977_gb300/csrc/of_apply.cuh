@@ -366,9 +366,19 @@ __global__ void __launch_bounds__(NW * 32) k_apply(const ApplyParams<R, C, RI> P
     V3<T> carry = v3(zero, zero, zero), carry_b = v3(zero, zero, zero);
     for (int sy = Y0 - 1; sy < Y1; ++sy) {
         const bool row_owned = (sy + 1 >= Y0) && (sy + 1 < Y1);
-        NodeVal<T> nxt = load(cx, sy + 1, mycol_owned && row_owned);
-        NodeVal<T> nnxt = shfl_node(nxt);
-        if (lane == 31) nnxt = load(cx + 1, sy + 1, false);
+        // lane 31 also loads the node right of its column (no lane holds it);
+        // one copy of the load's code serves both (a smaller loop body)
+        NodeVal<T> nxt, nnxt;
+#pragma unroll 1
+        for (int k = 0; k < (lane == 31 ? 2 : 1); ++k) {
+            const NodeVal<T> v = load(cx + k, sy + 1, k == 0 && mycol_owned && row_owned);
+            if (k == 0) nxt = v;
+            else nnxt = v;
+        }
+        {
+            const NodeVal<T> sh = shfl_node(nxt);
+            if (lane != 31) nnxt = sh;
+        }
         const bool valid = (cx >= 0) && (cx < W - 1) && (sy >= 0) && (sy < H - 1);
         const T al0 = valid ? Cvt<T>::from(al[2 * ((long long)sy * pitch + cx)]) : zero;
         const T al1 = valid ? Cvt<T>::from(al[2 * ((long long)sy * pitch + cx) + 1]) : zero;
