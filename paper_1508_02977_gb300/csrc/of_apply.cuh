@@ -192,6 +192,7 @@ struct ApplyParams {
     double* partial;           // [nblocks][2]
     unsigned* counter;         // [batch]
     unsigned* gcounter;        // [blocks]: FP32 PCG apply, arrivals of each group of 32 blocks (at its first block)
+    int pq_fixed;              // FP32 PCG apply, one pair: p.q into PairScalars::pq_fix, a formed by the preconditioner
     const C* f1; const C* f2; const C* alpha;
     const C* lamel;            // per-element lambda [H][pitch][2] like alpha, or null (the constant lam)
     R lam;
@@ -582,8 +583,8 @@ __global__ void __launch_bounds__(32, 16) k_apply4(const ApplyParams<float, floa
     bool first = false;
     if (MODE == MODE_PCG) {
         if (P.sc_in[pair].done) return;
-        beta = (float)P.sc_in[pair].beta;
-        a_prev = (float)P.sc_in[pair].a;
+        beta = f32_from_double(P.sc_in[pair].beta);  // integer conversions: the FP64 pipe is narrow
+        a_prev = f32_from_double(P.sc_in[pair].a);
         it = P.sc_in[pair].it;
         first = (it == 0);
     }
@@ -786,6 +787,22 @@ __global__ void __launch_bounds__(32, 16) k_apply4(const ApplyParams<float, floa
     // group's first block); the pair's last group sums the group slots in
     // order (double-float arithmetic throughout)
     const float s0 = warp_sum(acc);
+    if (P.pq_fixed) {
+        // one pair: the fixed-point sum (no arrival, no serial tail; see pq_fix_shift)
+        if (lane == 0) {
+            PairScalars* sp = P.sc + pair;
+            const int k = pq_fix_shift(P.sc_in[pair].rz);
+            const float v = __fmul_rn(s0, __int_as_float((127 + k) << 23));  // exact: a power of two
+            // 2^62 (false for NaN and infinities); the sum overflows only if the
+            // partials' magnitudes add up to 2^23 |r.z| (a < 1e-7), reported
+            // like a non-finite p.q: as a breakdown
+            if (fabsf(v) < 4.611686e18f)
+                atomicAdd(reinterpret_cast<unsigned long long*>(&sp->pq_fix), (unsigned long long)__float2ll_rn(v));
+            else
+                atomicOr(&sp->pad[1], 1);
+        }
+        return;
+    }
     __shared__ int sh_last;
     if (lane == 0) P.partial[2 * (long long)bi.w] = (double)s0;
     const int g = (bi.w - pd.blk0) >> 5;

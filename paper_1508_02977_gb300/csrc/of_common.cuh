@@ -47,8 +47,24 @@ struct PairScalars {
     int done;         // inner loop finished (converged, capped or broken down)
     int status;       // 0 ok, 5 not converged, 6 breakdown
     int max_it;       // inner iteration cap of this pass
-    int pad[3];
+    int pad[3];       // pad[0]: outer convergence; pad[1]: a p.q partial was not finite or too large
+    long long pq_fix; // FP32 path, one pair: p.q as a fixed-point integer sum (pq_fix_shift)
 };
+
+// p.q of the FP32 PCG apply as a sum of 64-bit integers (one pair, FP16
+// sweeps): each apply block adds its FP32 partial times 2^k, rounded to an
+// integer, k = 40 minus the binary exponent of r.z (clamped to the range of a
+// float power of two).  Integer addition is exact and independent of the
+// order, so the sum is deterministic without a reduction tree or an arrival
+// count; the preconditioner kernel that follows reads it after the launch
+// boundary.  The rounding error of the sum is below (blocks / 2) 2^-40 |r.z|;
+// it overflows only when the partials' magnitudes add up to 2^22 |r.z| (p.q =
+// r.z / a with a of order one for a preconditioned system).
+__device__ __forceinline__ int pq_fix_shift(double rz) {
+    const int e = (int)(((unsigned long long)__double_as_longlong(rz) >> 52) & 0x7ffULL) - 1023;
+    const int k = 40 - e;
+    return k < -126 ? -126 : (k > 127 ? 127 : k);
+}
 
 #define OF_STIFF_HALF 0.5   // |K| * |grad phi|^2 weight of a triangle leg
 

@@ -128,6 +128,13 @@ cudaError_t launch_residual(const SolveBufs& B, const double* xin, double* xout,
     return residual_t<float, float>(B, xin, xout, rhs_vec, first, rtol, inner_rtol, pass_frac, max_inner, st);
 }
 
+// One pair on the FP32 path with FP16 sweeps, one level and the four-column
+// apply: the apply sums p.q as fixed-point integers (PairScalars::pq_fix),
+// and every CTA of the Schwarz kernel that follows forms a = r.z / p.q.
+static bool pq_fixed_point(const SolveBufs& B) {
+    return B.h2 && !B.fp64 && B.npairs == 1 && !B.coarse.on && !B.eld && !B.lamel;
+}
+
 static SchwarzParams schwarz_params(const SolveBufs& B) {
     SchwarzParams S;
     memset(&S, 0, sizeof(S));
@@ -154,6 +161,7 @@ static SchwarzParams schwarz_params(const SolveBufs& B) {
     S.use_cond = B.use_cond;
     S.tx_extra = B.tx_extra;
     S.cond = B.cond;
+    S.pq_fixed = pq_fixed_point(B) ? 1 : 0;
     return S;
 }
 
@@ -375,6 +383,7 @@ static cudaError_t pcg_apply_t(const SolveBufs& B, cudaStream_t st) {
     P.p_buf1 = (R*)B.p1;
     P.dcorr = (R*)B.d;
     P.out = (R*)B.q;
+    P.pq_fixed = pq_fixed_point(B) ? 1 : 0;
     if (B.eld) k_apply<R, R, R, MODE_PCG, false, APPLY_NW, R, true><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
     else if (B.lamel) k_apply<R, R, R, MODE_PCG, false, APPLY_NW><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);  // per-element lambda
     else if constexpr (sizeof(R) == 4) k_apply4<MODE_PCG><<<B.nblk, 32, apply4_smem_bytes(), st>>>(P);  // FP32: four columns per lane

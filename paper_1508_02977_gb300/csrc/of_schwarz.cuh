@@ -87,6 +87,7 @@ struct SchwarzParams {
     int defer;                // two-level: leave the scalars to the coarse correction's kernel
     int tx_extra;             // test hook (0 in use): bytes each staging barrier expects beyond its
                               // copies, so that its bounded wait runs out
+    int pq_fixed;             // FP16 sweeps, one pair: a = r.z / p.q from PairScalars::pq_fix, formed here
     cudaGraphConditionalHandle cond;
 };
 

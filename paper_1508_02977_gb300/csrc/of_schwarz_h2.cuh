@@ -283,6 +283,7 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
     __shared__ float sh_max[16];
     __shared__ float sh_part[32];  // per-warp r.r (0..15) and r.z (16..31) of the pending item
     __shared__ int sh_last, sh_fail, sh_more;
+    __shared__ float sh_a;
     const int NT = blockDim.x;
     const int Tx = TXC ? TXC : P.Tx, Ty = TXC ? TYC : P.Ty, ov = TXC ? OVC : P.ov;
     const int RW = sch_rw(Tx, ov), HP = h2_hp(Ty, ov), cpad = sch_cpad(ov);
@@ -352,14 +353,20 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
         int W, H;
         float a;
     };
+    // one pair: the step a = r.z / p.q from the apply's fixed-point p.q
+    // (pq_fix_shift), formed by thread 0 of every CTA (all take the same a);
+    // the last CTA stores p.q and a and clears the sum
+    const bool pq_here = P.pq_fixed && !P.first && !P.apply_only && P.npairs == 1;
+    double pq_val = 0.0, a_val = 0.0;  // thread 0
+    int pq_bad = 0;
     auto item_scalars = [&](const int4 w) {
         ItemScalars r;
         r.W = P.pairs[w.x].W;
         r.H = P.pairs[w.x].H;
         // one FP64 conversion per warp (the FP64 pipe is narrow), broadcast
         float a = 0.f;
-        if ((threadIdx.x & 31) == 0 && !P.first && !P.apply_only) a = (float)P.sc[w.x].a;
-        r.a = __shfl_sync(0xffffffffu, a, 0);
+        if ((threadIdx.x & 31) == 0 && !P.first && !P.apply_only && !pq_here) a = (float)P.sc[w.x].a;
+        r.a = pq_here ? sh_a : __shfl_sync(0xffffffffu, a, 0);
         return r;
     };
     // the store of an item's z (and updated r) and its partial sums run after
@@ -425,6 +432,18 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
     int t = advance(blockIdx.x, ti);
     int tn = (t < P.ntiles) ? advance(t + G, tin) : P.ntiles;
     if (t < P.ntiles && threadIdx.x == 0) issue(ti, 0);
+    if (pq_here) {  // while the first item's copies are in flight
+        if (threadIdx.x == 0) {
+            const PairScalars* s0 = P.sc;
+            const double rz = s0->rz;
+            const long long fix = s0->pq_fix;
+            pq_bad = s0->pad[1];
+            pq_val = (double)fix * __longlong_as_double((long long)(1023 - pq_fix_shift(rz)) << 52);
+            a_val = (!pq_bad && pq_val > 0.0 && isfinite(rz)) ? rz / pq_val : 0.0;
+            sh_a = (float)a_val;
+        }
+        __syncthreads();
+    }
     ItemScalars cur = {0, 0, 0.f}, nxt = {0, 0, 0.f};
     if (t < P.ntiles) cur = item_scalars(ti);
     unsigned phase[2] = {0u, 0u};
@@ -685,9 +704,21 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
         df_ordered_sum2<4>(P.partial, min(P.ntiles, (int)gridDim.x), t_rr, t_rz, sh_red);  // the CTAs' partials
         if (threadIdx.x == 0) {
             if (!s0.done) {
-                precond_finalize(&s0, t_rr, t_rz, P.first);
-                P.sc[0] = s0;
+                if (pq_here) {
+                    // the step of this iteration (what the apply's own reduction stores otherwise)
+                    s0.pq = pq_val;
+                    s0.a = a_val;
+                    if (pq_bad || !(pq_val > 0.0) || !isfinite(s0.rz)) {
+                        s0.a = 0.0;
+                        s0.done = 1;
+                        s0.status = 6;
+                    }
+                }
+                if (!s0.done) precond_finalize(&s0, t_rr, t_rz, P.first);
             }
+            s0.pq_fix = 0;  // the next apply's sum starts from zero
+            s0.pad[1] = 0;
+            P.sc[0] = s0;
             sh_more = s0.done ? 0 : 1;  // another iteration
         }
     } else {
