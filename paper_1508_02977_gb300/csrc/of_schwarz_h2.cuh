@@ -402,8 +402,9 @@ __global__ void __launch_bounds__(384, 1) k_schwarz_h2(const SchwarzParams P) {
         }
         // the item's r.r and r.z from the per-warp sums in fixed order, in
         // FP32 (the FP64 pipe is narrow) (warp 1: thread 0 issues the
-        // stores); with one pair they are summed over the CTA's items (in
-        // double-float, in the items' order) and written once at the end
+        // stores); they are summed per pair over the CTA's items (in
+        // double-float, in the items' order) and written when the CTA moves
+        // on to another pair and at its end
         if (!P.apply_only && (threadIdx.x >> 5) == 1) {
             const int l = threadIdx.x & 31;
             const bool w = l < (NT >> 5);
