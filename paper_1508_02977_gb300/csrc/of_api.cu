@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "of.h"
@@ -1227,10 +1228,12 @@ of_status of_solve(of_handle h, const of_solve_opts* o, void* const* U, of_dtype
     h->ras_hist.clear();
     of_status s = ras ? run_ras(h, opt, &cur, passes) : run_solve(h, opt, nullptr, &cur, passes);
     if (s != OF_OK) return s;
-    CK(cudaMemcpyAsync(h->usol, h->x[cur], h->vec_elems * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // the solution becomes the kept one by exchanging the buffers (the next
+    // solve rewrites its iterate buffers before reading them; no graph holds them)
+    std::swap(h->usol, h->x[cur]);
     for (int p = 0; p < h->batch; ++p) {
         const PairDesc& d = h->pd[p];
-        s = copy_out(h, h->x[cur] + d.vec_off, ofl::T_F64, d.pitch, U[p], dt, 3LL * d.H, d.W);
+        s = copy_out(h, h->usol + d.vec_off, ofl::T_F64, d.pitch, U[p], dt, 3LL * d.H, d.W);
         if (s != OF_OK) return s;
     }
     CK(cudaEventRecord(h->ev1, st));

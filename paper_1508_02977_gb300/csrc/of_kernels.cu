@@ -116,7 +116,11 @@ static cudaError_t residual_t(const SolveBufs& B, const double* xin, double* xou
     } else if (xin) {
         k_apply<double, C, RI, MODE_RES, false, APPLY_NW, T, false, false><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
     } else {
-        k_apply<double, C, RI, MODE_RESB, false, APPLY_NW, T, false, false><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
+        // cold start (x = 0): r = b only seeds the first inner solve, whose
+        // result the next residual (double-float) corrects, so the FP32 path
+        // forms it in FP32 arithmetic (and ||b|| to FP32 accuracy)
+        using TB = typename std::conditional<sizeof(C) == 4, float, double>::type;
+        k_apply<double, C, RI, MODE_RESB, false, APPLY_NW, TB, false, false><<<B.nblk, APPLY_NW * 32, 0, st>>>(P);
     }
     return cudaGetLastError();
 }
