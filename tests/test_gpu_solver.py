@@ -534,6 +534,41 @@ def test_mixed_refinement_reaches_fp64_accuracy(S, oracle, tile):
     assert np.linalg.norm(U - Ud) <= 1e-6 * np.linalg.norm(Ud), info
 
 
+def test_fp16_path_capped_solve_leaves_no_state(S):
+    """One pair on the FP16-sweep path (p.q summed as fixed-point integers by
+    the apply, the step formed by the Schwarz kernel): a solve stopped by the
+    inner iteration cap reports OF_ERR_NOT_CONVERGED, and the next solve in
+    the same handle is bit-identical to a solve in a fresh handle."""
+    t = synth.texture(240, 192, seed=77)
+    f1, f2 = dev(t.f1, torch.float32), dev(t.f2, torch.float32)
+    kw = dict(tile=(48, 48), overlap=0, sweeps=4, omega=1.6, precision=S.OF_PREC_MIXED)
+
+    def solve(h, **o):
+        U = torch.zeros(3, t.H, t.W, dtype=torch.float64, device="cuda")
+        st, info = S.of_solve(h, [U], raise_on=False, **o)
+        return st, info, U.cpu().numpy()
+
+    h = handle(S, [(t.W, t.H)], **kw)
+    try:
+        S.of_set_frames(h, 0, f1, f2)
+        S.of_set_alpha(h, 0, None, t.alpha0)
+        st, info, _ = solve(h, max_outer=1, max_inner=3)
+        assert st == S.OF_ERR_NOT_CONVERGED and info[0]["inner_iters"] == 3, info
+        st, info, U1 = solve(h)
+        assert st == S.OF_OK and info[0]["rel_residual"] <= 1e-6, info
+    finally:
+        S.of_destroy(h)
+    h = handle(S, [(t.W, t.H)], **kw)
+    try:
+        S.of_set_frames(h, 0, f1, f2)
+        S.of_set_alpha(h, 0, None, t.alpha0)
+        st, info2, U2 = solve(h)
+    finally:
+        S.of_destroy(h)
+    assert info2[0]["inner_iters"] == info[0]["inner_iters"]
+    assert np.array_equal(U1.view(np.uint64), U2.view(np.uint64))
+
+
 def test_host_buffers_round_trip(S, oracle):
     """Host (numpy) inputs and outputs go through the same path."""
     W, H = 40, 30
