@@ -569,6 +569,37 @@ def test_fp16_path_capped_solve_leaves_no_state(S):
     assert np.array_equal(U1.view(np.uint64), U2.view(np.uint64))
 
 
+def test_fp16_path_fixed_point_pq_agrees_with_batched_reduction(S):
+    """p.q of the PCG apply: one pair on the FP16-sweep path sums it as
+    fixed-point integers (the step formed by the Schwarz kernel), a batch of
+    two pairs by the two-level reduction of the block partials.  The same
+    pair solved both ways takes the same number of iterations (to one) and
+    agrees to the solve tolerance (both reach rel. residual 1e-6; solutions
+    within 1e-4 of each other, relative: an error in either p.q would change
+    every CG step)."""
+    t = synth.texture(240, 192, seed=91)
+    o = synth.texture(160, 96, seed=92)
+    kw = dict(tile=(48, 48), overlap=0, sweeps=4, omega=1.6, precision=S.OF_PREC_MIXED)
+    sols, infos = [], []
+    for sizes, pairs in (([(t.W, t.H)], [t]), ([(t.W, t.H), (o.W, o.H)], [t, o])):
+        h = handle(S, sizes, **kw)
+        try:
+            Us = []
+            for i, p in enumerate(pairs):
+                S.of_set_frames(h, i, dev(p.f1, torch.float32), dev(p.f2, torch.float32))
+                S.of_set_alpha(h, i, None, p.alpha0)
+                Us.append(torch.zeros(3, p.H, p.W, dtype=torch.float64, device="cuda"))
+            st, info = S.of_solve(h, Us)
+            assert st == S.OF_OK
+            sols.append(Us[0].cpu().numpy())
+            infos.append(info[0])
+        finally:
+            S.of_destroy(h)
+    assert abs(infos[0]["inner_iters"] - infos[1]["inner_iters"]) <= 1, infos
+    assert max(i["rel_residual"] for i in infos) <= 1e-6, infos
+    assert np.linalg.norm(sols[0] - sols[1]) <= 1e-4 * np.linalg.norm(sols[0]), infos
+
+
 def test_host_buffers_round_trip(S, oracle):
     """Host (numpy) inputs and outputs go through the same path."""
     W, H = 40, 30
