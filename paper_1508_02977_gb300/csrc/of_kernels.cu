@@ -1,4 +1,5 @@
 // Kernel instantiations and launchers of the solve path.
+#include <functional>
 #include <type_traits>
 
 #include "of_apply.cuh"
@@ -208,6 +209,68 @@ int schwarz_h2_max_grid(int tx, int ty, int ov, int threads, size_t smem) {
     return per * (sms > 0 ? sms : 1);
 }
 
+// Lane l of every warp takes a node whose z word lies in bank l (the sweeps'
+// accesses), and within each warp the owned nodes are chosen so that their
+// words of the dense Tx-wide r, q and z-out tiles also lie in distinct banks
+// (the setup's and the emission's accesses): per colour, the nodes are the
+// edges of a bipartite graph between z banks and tile banks, and each warp
+// takes one matching of it (augmenting paths; the graph is regular for the
+// tuned shapes, so every warp's matching is perfect; a node that cannot be
+// matched is placed anyway, at the cost of a conflict).  Nodes of the overlap
+// (not owned) touch no tile and match freely.
+static void h2_assign_warps(const std::vector<std::vector<uint32_t>>& bucket, int Tx, int ov, int ns,
+                            std::vector<std::vector<uint32_t>>& slots) {
+    auto tile_bank = [&](uint32_t e) -> int {
+        const int li = (int)(e & 0xffffu) - ov, lj = (int)(e >> 16) - ov;
+        if (li < 0 || li >= Tx || lj < 0) return -1;  // not owned (lanes beyond the owned rows are checked in the kernel)
+        return (int)(((long long)lj * Tx + li) % 32);
+    };
+    std::vector<std::vector<uint32_t>> left = bucket;  // remaining nodes per z bank
+    slots.assign(ns, std::vector<uint32_t>(32, 0xffffffffu));
+    for (int k = 0; k < ns; ++k) {
+        // right vertices: 32 tile banks; owner[r] = the z bank matched to tile bank r, pick[b] = node index
+        int owner[32], pick[32];
+        for (int r = 0; r < 32; ++r) owner[r] = -1;
+        for (int b = 0; b < 32; ++b) pick[b] = -1;
+        for (int b = 0; b < 32; ++b) {
+            if (left[b].empty()) continue;
+            // a node of the overlap needs no tile bank
+            for (size_t q = 0; q < left[b].size() && pick[b] < 0; ++q)
+                if (tile_bank(left[b][q]) < 0) pick[b] = (int)q;
+            if (pick[b] >= 0) continue;
+            bool seen[32];
+            std::function<bool(int)> augment = [&](int bb) -> bool {
+                for (size_t q = 0; q < left[bb].size(); ++q) {
+                    const int r = tile_bank(left[bb][q]);
+                    if (r < 0 || seen[r]) continue;
+                    seen[r] = true;
+                    if (owner[r] < 0 || augment(owner[r])) {
+                        owner[r] = bb;
+                        pick[bb] = (int)q;
+                        return true;
+                    }
+                }
+                return false;
+            };
+            for (int r = 0; r < 32; ++r) seen[r] = false;
+            if (!augment(b)) pick[b] = 0;  // unmatched: any node (a bank conflict)
+        }
+        for (int b = 0; b < 32; ++b) {
+            if (pick[b] < 0) continue;
+            slots[k][b] = left[b][pick[b]];
+            left[b].erase(left[b].begin() + pick[b]);
+        }
+    }
+    // anything left (never for the tuned shapes) goes to the first free lane slots of its z bank
+    for (int b = 0; b < 32; ++b)
+        for (uint32_t e : left[b])
+            for (int k = 0; k < ns; ++k)
+                if (slots[k][b] == 0xffffffffu) {
+                    slots[k][b] = e;
+                    break;
+                }
+}
+
 bool schwarz_h2_node_table(int Tx, int Ty, int ov, std::vector<uint32_t>& tab, int& threads) {
     if (!h2_shape_ok(Ty, ov)) return false;
     const int Ex = Tx + 2 * ov, HP = h2_hp(Ty, ov), RW = sch_rw(Tx, ov), cpad = sch_cpad(ov);
@@ -220,9 +283,7 @@ bool schwarz_h2_node_table(int Tx, int Ty, int ov, std::vector<uint32_t>& tab, i
                 if ((i + j) % 3 == c) bucket[((j + 1) * RW + (i + cpad - ov)) % 32].push_back((uint32_t)i | ((uint32_t)j << 16));
         size_t ns = 0;
         for (auto& b : bucket) ns = std::max(ns, b.size());
-        slots[c].assign(ns, std::vector<uint32_t>(32, 0xffffffffu));
-        for (int b = 0; b < 32; ++b)
-            for (size_t k = 0; k < bucket[b].size(); ++k) slots[c][k][b] = bucket[b][k];
+        h2_assign_warps(bucket, Tx, ov, (int)ns, slots[c]);
         maxslots = std::max(maxslots, (int)slots[c].size());
     }
     if (maxslots < 1 || maxslots > 12) return false;  // one pair per thread and colour, at most 384 threads
